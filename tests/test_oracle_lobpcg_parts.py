@@ -1,0 +1,137 @@
+"""Pins for the oracle's pieces of one LOBPCG iteration: block inner product, linear
+combination, block-diagonal preconditioner (eq. 11), Rayleigh-Ritz (eq. 9), and the
+paper's initial-guess statements of Section 3.3.1 (eqs. 12, 13)."""
+import numpy as np
+import pytest
+
+import oracle
+from test_oracle_sparse import dense_by_indexing, random_upper
+
+
+def test_gram_and_lincomb_integer_exact():
+    rng = np.random.default_rng(11)
+    A = rng.integers(-8, 9, (500, 7)).astype(np.float64)
+    B = rng.integers(-8, 9, (500, 5)).astype(np.float64)
+    C = rng.integers(-8, 9, (7, 4)).astype(np.float64)
+    assert np.array_equal(oracle.gram(A, B), A.T @ B)
+    assert np.array_equal(oracle.lincomb(A, C), A @ C)
+
+
+def test_block_precond_bp1_is_jacobi():
+    """With 1x1 blocks, eq. 11 reduces to w_ij = r_ij / (h_ii - mu_j)."""
+    rng = np.random.default_rng(12)
+    H = random_upper(50, 0.2, rng)
+    A = dense_by_indexing(H)
+    mu = np.array([-3.0, 0.5, 7.0])
+    R = rng.standard_normal((50, 3))
+    W = oracle.block_precond(H, oracle.uniform_bounds(50, 1), mu, R)
+    expect = R / (np.diag(A)[:, None] - mu[None, :])
+    assert np.abs(W - expect).max() <= 1e-14 * np.abs(expect).max()
+
+
+@pytest.mark.parametrize("n,bp", [(64, 32), (70, 32), (100, 7)])
+def test_block_precond_solves_each_block(n, bp):
+    rng = np.random.default_rng(n + bp)
+    H = random_upper(n, 0.3, rng)
+    A = dense_by_indexing(H)
+    mu = np.array([0.1, -2.0])
+    R = rng.standard_normal((n, 2))
+    bounds = oracle.uniform_bounds(n, bp)
+    W = oracle.block_precond(H, bounds, mu, R)
+    for i in range(len(bounds) - 1):
+        s = slice(bounds[i], bounds[i + 1])
+        blk = A[s, s]
+        for j in range(2):
+            res = (blk - mu[j] * np.eye(blk.shape[0])) @ W[s, j] - R[s, j]
+            assert np.linalg.norm(res) <= 1e-11 * np.abs(blk).sum() * max(np.linalg.norm(W[s, j]), 1.0)
+
+
+def test_rayleigh_ritz_recovers_eigenpairs():
+    rng = np.random.default_rng(13)
+    n = 80
+    H = random_upper(n, 0.2, rng)
+    A = dense_by_indexing(H)
+    w, Z = oracle.syev(A)
+    Y = Z[:, :6] @ np.linalg.qr(rng.standard_normal((6, 6)))[0] * 3.0  # non-orthonormal basis of the span
+    theta, C = oracle.rayleigh_ritz(Y.T @ A @ Y, Y.T @ Y)
+    assert np.abs(theta - w[:6]).max() <= 1e-12 * np.abs(w).max()
+    assert np.abs(C.T @ (Y.T @ Y) @ C - np.eye(6)).max() <= 1e-12
+
+
+def test_rayleigh_ritz_interlacing_random_subspace():
+    """Ritz values from an m-dimensional subspace bound the eigenvalues from above:
+    theta_i >= lambda_i (Courant-Fischer), and G C = M C Theta."""
+    rng = np.random.default_rng(14)
+    n, m = 100, 9
+    H = random_upper(n, 0.15, rng)
+    A = dense_by_indexing(H)
+    w, _ = oracle.syev(A)
+    Y = rng.standard_normal((n, m))
+    G, M = Y.T @ A @ Y, Y.T @ Y
+    theta, C = oracle.rayleigh_ritz(G, M)
+    assert np.all(theta >= w[:m] - 1e-10)
+    assert np.all(theta <= w[-m:] + 1e-10)
+    assert np.abs(G @ C - M @ C * theta).max() <= 1e-9 * np.abs(G).max()
+
+
+def test_rayleigh_ritz_rejects_singular_gram():
+    Y = np.zeros((10, 2))
+    Y[0] = 1.0  # two identical columns: Y^T Y = [[1, 1], [1, 1]], last pivot exactly 0
+    with pytest.raises(np.linalg.LinAlgError):
+        oracle.rayleigh_ritz(Y.T @ Y, Y.T @ Y)
+
+
+def two_level(n1, n2, eps, rng):
+    """Symmetric H = [[H11, eps*H21^T], [eps*H21, H22]] with H22's spectrum well above H11's."""
+    n = n1 + n2
+    A = np.zeros((n, n))
+    B = rng.standard_normal((n1, n1)); A[:n1, :n1] = B + B.T
+    D = rng.standard_normal((n2, n2)); A[n1:, n1:] = D + D.T + 40.0 * np.eye(n2)
+    C = rng.standard_normal((n2, n1)); A[n1:, :n1] = eps * C; A[:n1, n1:] = eps * C.T
+    r, c = np.nonzero(np.triu(A) != 0)
+    return oracle.Coo(n, r, c, A[r, c]), A
+
+
+def test_eq12_zero_padded_guess_residual_bound():
+    """X0 = [X1; 0] with H11 X1 = X1 Theta1: r_j = H21 x_j and ||r_j|| <= ||H21|| (eq. 12)."""
+    rng = np.random.default_rng(21)
+    n1, n2 = 20, 60
+    H, A = two_level(n1, n2, 0.3, rng)
+    w1, Z1 = oracle.syev(A[:n1, :n1])
+    X0 = np.zeros((n1 + n2, 4)); X0[:n1] = Z1[:, :4]
+    R = oracle.spmm(H, X0) - X0 * w1[:4]
+    assert np.abs(R[:n1]).max() <= 1e-12 * np.abs(A).max()
+    assert np.allclose(R[n1:], A[n1:, :n1] @ Z1[:, :4], atol=1e-12)
+    norm21 = np.linalg.norm(A[n1:, :n1], 2)
+    assert np.all(np.linalg.norm(R, axis=0) <= norm21 * (1 + 1e-12))
+
+
+def test_eq13_block_diag_precond_gives_correction_and_eps_squared():
+    """With T_j = diag{H11, H22} - theta_j I applied to the eq.-12 residual, the paper states
+    W0 = -[0; Y1] where Y1 solves the second block row exactly: Y1 = -(H22 - theta I)^{-1} H21 X1
+    (Section 3.3.1). Then span{X0, W0} contains the eq.-13 guess, so one Rayleigh-Ritz step on it
+    leaves a residual of order eps^2: halving the coupling quarters the residual."""
+    rng = np.random.default_rng(22)
+    n1, n2 = 16, 48
+    res = []
+    for eps in [0.02, 0.01, 0.005]:
+        H, A = two_level(n1, n2, eps, np.random.default_rng(22))
+        w1, Z1 = oracle.syev(A[:n1, :n1])
+        x1, th = Z1[:, 0], w1[0]
+        X0 = np.zeros((n1 + n2, 1)); X0[:n1, 0] = x1
+        R = oracle.spmm(H, X0) - X0 * th
+        # exact-arithmetic residual of eq. 12 is [0; H21 x1]; the first block is only rounding
+        # noise, and H11 - theta I is singular there, so take the exact zero as the paper does
+        R[:n1] = 0.0
+        W0 = oracle.block_precond(H, np.array([0, n1, n1 + n2]), np.array([th]), R)
+        Y1 = -np.linalg.solve(A[n1:, n1:] - th * np.eye(n2), A[n1:, :n1] @ x1)
+        assert np.abs(W0[:n1]).max() <= 1e-13
+        assert np.abs(W0[n1:, 0] + Y1).max() <= 1e-10 * np.abs(Y1).max()
+        S = np.hstack([X0, W0])
+        theta, C = oracle.rayleigh_ritz(S.T @ oracle.spmm(H, S), S.T @ S)
+        x = S @ C[:, 0]
+        r = oracle.spmm(H, x[:, None])[:, 0] - theta[0] * x
+        res.append(np.linalg.norm(r) / np.linalg.norm(x))
+    r1 = res[0] / res[1]
+    r2 = res[1] / res[2]
+    assert 3.0 < r1 < 5.0 and 3.0 < r2 < 5.0, res
