@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Benchmark: time to the k smallest eigenpairs with the preconditioned block LOBPCG.
+
+Workload (default): the n = 500,000 precision-study matrix -- levels 0..10 with sizes ~2.2^q,
+graded diagonal 10 q + U(-1,1), ~200 nonzeros per row coupling levels |dq| <= 2, seed 1 --
+k = 8, nb = 16, block-diagonal preconditioner with 32 x 32 blocks, initial guess from the
+leading levels {0, 1} (eq. 12), residual tolerance 1e-8 ||H||. One step = one complete solve
+(every row of the hot path: SpMM, Gram, Rayleigh-Ritz, update, residual, preconditioner,
+initial guess, FP64 refinement) with the matrix already resident in HBM.
+
+Prints one JSON line. Also reported: SpMM effective HBM bandwidth against the measured peak
+(roofline), the plain FP64 solver's time on the same workload, eigenvalue error against the
+FP64 oracle, an end-to-end time from host buffers, and the oracle timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU (torchrun): independent replicas, one seeded instance per rank ("replicas only").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "c2": dict(name="n=500000 levels 0..10, ~200 nnz/row, k=8, nb=16, b_p=32, tol 1e-8", cfg="c2", k=8, nb=16,
+               bp=32, tol=1e-8),
+    "c1": dict(name="n=1536 levels 0..6, ~30 nnz/row, k=5, nb=8, b_p=32, tol 1e-8", cfg="c1", k=5, nb=8, bp=32,
+               tol=1e-8),
+}
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def golden_eigs(cfg):
+    path = os.path.join(ROOT, "tests", "golden", f"{cfg}_eigs.txt")
+    if not os.path.exists(path):
+        return None, None
+    vals, steps = [], None
+    for line in open(path):
+        if line.startswith("#"):
+            if " steps" in line:
+                try:
+                    steps = int(line.split(" steps")[0].split(",")[-1].strip())
+                except ValueError:
+                    pass
+            continue
+        if line.strip():
+            vals.append(float(line))
+    return np.array(vals), steps
+
+
+_ORACLE_H = {}
+
+
+def oracle_sample(cfg, layout):
+    """The oracle (plain single-threaded FP64 Lanczos, full reorthogonalisation) on a bounded
+    sample of the same workload: two short runs of s1 < s2 Lanczos steps fix the per-step cost
+    a + b j (SpMV plus reorthogonalisation against j vectors); the time to the converged step
+    count N of the full oracle run (stored with the reference eigenvalues) is N a + N^2 b / 2."""
+    import oracle
+    import synth
+
+    key = (cfg, int(layout.seed))
+    if key not in _ORACLE_H:
+        r, c, v = synth.generate(layout)
+        H = oracle.Coo(layout.n, r, c, v)
+        _ORACLE_H[key] = (H, oracle.norm_inf(H))
+    H, nH = _ORACLE_H[key]
+    _, N = golden_eigs(cfg)
+    s1, s2 = 10, 30
+    t = []
+    for s in (s1, s2):
+        t0 = time.perf_counter()
+        oracle.lanczos(H, 1, 1e-300, nH, max_steps=s)
+        t.append(time.perf_counter() - t0)
+    # t(s) = a s + b s^2 / 2
+    A = np.array([[s1, s1 * s1 / 2.0], [s2, s2 * s2 / 2.0]])
+    a, b = np.linalg.solve(A, np.array(t))
+    a, b = max(a, 0.0), max(b, 0.0)
+    if N is None:
+        N = 300
+    est = N * a + N * N * b / 2.0
+    return est * 1e3, dict(kind="oracle", cores=1, sample=(
+        f"oracle Lanczos (FP64, full reorthogonalisation, 1 thread) on the same matrix: {s1} and {s2} steps timed "
+        f"({t[0]:.2f} s, {t[1]:.2f} s), per-step cost a + b j fitted, extrapolated to the {N} steps the full oracle "
+        f"run needs to reach Ritz residual 1e-12 ||H||"))
+
+
+def run_reference(args, wl):
+    import synth
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    layout = synth.config_layout(wl["cfg"])
+    vals = []
+    desc = None
+    for _ in range(args.warmup + args.steps):
+        ms, desc = oracle_sample(wl["cfg"], layout)
+        vals.append(ms)
+    v = float(np.mean(vals[args.warmup:]))
+    line = {"impl": "reference", "metric": "time-to-k-eigenpairs", "value": v, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "n": int(layout.n)},
+            "cpu_baseline": dict(desc, value=v, unit="ms"),
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+
+    import paper_1609_01689_gb300 as lob
+    import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- setup (not timed): generate on the device, build the tile store and preconditioner
+    base = synth.CONFIGS[wl["cfg"]]
+    layout = synth.config_layout(wl["cfg"], seed=base["seed"] + rank)
+    n = int(layout.n)
+    rows, cols, vals = synth.generate_device(layout)
+    t0 = time.perf_counter()
+    M = lob.Matrix(n, rows, cols, vals, precond_block=wl["bp"])
+    torch.cuda.synchronize()
+    create_ms = (time.perf_counter() - t0) * 1e3
+    info = M.info()
+    n_small = int(synth.level_starts(layout)[2])
+    k, nb, tol = wl["k"], wl["nb"], wl["tol"]
+    X = torch.empty((n, nb), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def solve(mode):
+        return M.solve(k, nb, tol, mode=mode, precond=True, n_small=n_small, X_out=X)
+
+    for _ in range(args.warmup):
+        solve("mixed")
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = lob.kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    stats = []
+    lam = None
+    for _ in range(args.steps):
+        lam, _, st, rc = solve("mixed")
+        stats.append((st, rc))
+    ev1.record(stream)
+    barrier()
+    launches = lob.kernel_launches() - launches0
+    clocks = sampler.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+
+    # SpMM roofline: algorithmic bytes / SpMM launch time, over the timed solves
+    spmm_bytes = sum(s["spmm_bytes"] for s, _ in stats)
+    spmm_ms = sum(s["phase_ms"]["spmm"] for s, _ in stats)
+    spmm_calls = sum(s["spmm_calls"] for s, _ in stats)
+    peak, peak_src = read_peaks()
+    achieved = spmm_bytes / (spmm_ms * 1e-3) / 1e9 if spmm_ms > 0 else 0.0
+
+    out = {"metric": "time-to-k-eigenpairs", "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "mixed: f32 SpMM, f64/double-float blocks, f64 refinement",
+           "data": "synthetic",
+           "config": {"workload": wl["name"], "n": n, "nnz_stored": int(info["nnz"]), "ntiles": int(info["ntiles"]),
+                      "k": k, "nb": nb, "b_p": wl["bp"], "tol": tol, "mode": "mixed+fp64 refinement",
+                      "l2": "inputs larger than L2 (tile store %.2f GB)" % (info["store_bytes"] / 1e9),
+                      "parallelism": f"replicas x{world}"},
+           "roofline": {"bound": "hbm", "kernel": "symmetric SpMM (mixed)", "achieved": achieved, "peak": peak,
+                        "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                        "launches": spmm_calls, "avg_launch_ms": spmm_ms / max(spmm_calls, 1),
+                        "bytes_per_launch": spmm_bytes / max(spmm_calls, 1)},
+           "clocks": clocks, "gpu_launches": launches}
+    st0 = stats[-1][0]
+    out["solve"] = {"iterations": st0["iterations"], "refine_iterations": st0["refine_iterations"],
+                    "status": int(stats[-1][1]), "phase_ms": st0["phase_ms"], "create_ms": create_ms,
+                    "max_relres": max(st0["residual"][:k])}
+    gold, _ = golden_eigs(wl["cfg"])
+    if gold is not None and rank == 0 and lam is not None:
+        err = np.abs(lam - gold[:k]) / np.maximum(np.abs(gold[:k]), 1.0)
+        out["eig_err_vs_oracle"] = float(err.max())
+
+    # ---- plain FP64 solver on the same workload (not in the timed region)
+    if not args.no_fp64:
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lam64, _, st64, rc64 = solve("fp64")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1)
+        fp = {"ms": t64, "iterations": st64["iterations"], "status": int(rc64),
+              "speedup_mixed_over_fp64": t64 / ms_step}
+        if gold is not None:
+            fp["eig_err_vs_oracle"] = float((np.abs(lam64 - gold[:k]) / np.maximum(np.abs(gold[:k]), 1.0)).max())
+        out["fp64_solver"] = fp
+
+    # ---- end to end through the public API from pinned host buffers
+    if not args.no_e2e:
+        hr = rows.cpu().pin_memory(); hc = cols.cpu().pin_memory(); hv = vals.cpu().pin_memory()
+        Xh = torch.empty((n, nb), dtype=torch.float64).pin_memory()
+        steps_e2e = max(1, min(2, args.steps))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(steps_e2e):
+            Me = lob.Matrix(n, hr.numpy(), hc.numpy(), hv.numpy(), precond_block=wl["bp"])
+            lam_e, Xd, _, _ = Me.solve(k, nb, tol, mode="mixed", precond=True, n_small=n_small)
+            Xh.copy_(Xd)
+            torch.cuda.synchronize()
+            Me.close()
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / steps_e2e
+        out["e2e"] = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(hr.numel() * 24),
+                      "d2h_bytes_per_step": int(n * nb * 8 + k * 8),
+                      "includes": "H2D of the COO, tile build + preconditioner setup, solve, D2H of X and lambda"}
+
+    if rank == 0 and not args.no_cpu:
+        ms_cpu, desc = oracle_sample(wl["cfg"], layout)
+        out["cpu_baseline"] = dict(desc, value=ms_cpu, unit="ms")
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,185 @@
+/* lob.h -- C ABI of the GB300 block eigensolver library (liblob.so).
+ *
+ * The library computes the k smallest eigenpairs of a large sparse symmetric matrix H with
+ * the preconditioned block LOBPCG method of Shao et al. (Section 3, Algorithm 1). Its hot
+ * path is the symmetric sparse-matrix-times-block product Y = H X with only the upper
+ * triangle of H stored in CSB-style tiles, each stored tile applied as H_ij and H_ij^T in
+ * one pass (Sections 4.1-4.2).
+ *
+ * Conventions for every entry point:
+ *  - Return value: LOB_OK (0) on success, otherwise a negative LOB_ERR_* code; no exception
+ *    or abort crosses the ABI. lob_strerror() gives a message for a code.
+ *  - "device" pointers are CUDA device (or managed) memory of the current device; "host"
+ *    pointers are ordinary CPU memory. The caller owns every buffer it passes in; the library
+ *    owns what lob_create allocates, until lob_destroy.
+ *  - Block vectors are n x nb, row-major, leading dimension nb (element (i, j) at i*nb + j),
+ *    FP64, as the paper stores its vector blocks (Section 4.2, row-major storage).
+ *  - stream is a cudaStream_t (NULL = legacy default stream). Calls are asynchronous on it
+ *    unless stated; host outputs are valid on return.
+ *  - Not thread-safe on one lob_matrix; distinct matrices may be used concurrently.
+ */
+#ifndef LOB_H
+#define LOB_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LOB_OK 0
+#define LOB_ERR_ARG (-1)       /* bad argument: sizes, null pointers, entry below the diagonal,
+                                  out of range or duplicated, unsupported option */
+#define LOB_ERR_NOMEM (-2)     /* device allocation failed (or an admission budget refused it) */
+#define LOB_ERR_CUDA (-3)      /* a CUDA call failed; the CUDA error is logged to stderr */
+#define LOB_ERR_NOCONV (-4)    /* iteration limit reached; outputs still hold the last iterate */
+#define LOB_ERR_BREAKDOWN (-5) /* the projected Gram matrix stayed indefinite after the restarts */
+
+typedef struct lob_matrix lob_matrix; /* opaque; owns the device tile store */
+
+/* Upper triangle (row <= col) of symmetric H, including the diagonal, as COO. Entries may
+ * come in any order; an entry below the diagonal, outside [0, n) or repeated is an error
+ * (LOB_ERR_ARG), never summed. on_device = 1: the three arrays are device pointers. */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int64_t* row;
+  const int64_t* col;
+  const double* val;
+  int32_t on_device;
+} lob_coo;
+
+/* Which value copies the tile store keeps. FP64 is needed by LOB_SPMM_FP64 and by the
+ * FP64-class (refinement) products; FP32 by LOB_SPMM_MIXED (Section 4.4, footnote 5). */
+#define LOB_VALUES_FP64 1
+#define LOB_VALUES_FP32 2
+#define LOB_VALUES_BOTH 3
+
+typedef struct {
+  int32_t tile;          /* CSB tile size b; 0 = 256. Must be 256 in this version. */
+  int32_t values;        /* LOB_VALUES_*; 0 = BOTH */
+  int32_t precond_block; /* b_p of the block-diagonal preconditioner (eq. 11), 1..64; 0 = none */
+  int32_t reserved;
+  void* stream;          /* cudaStream_t for the build */
+} lob_create_opts;
+
+/* Build the device tile store of H (Section 2.2 CSB blocks with fixed b x b tiles; Section
+ * 4.2 COO inside each tile with 16-bit in-tile offsets packed as (r << 16) | c), the norm
+ * ||H||_inf, and, if precond_block > 0, the block-diagonal preconditioner of eq. 11 (the
+ * diagonal b_p x b_p blocks of H, each eigendecomposed once). Synchronous. *out receives the
+ * handle. Errors: LOB_ERR_ARG (n < 1, nnz < 1, bad entry, duplicate, tile != 256,
+ * precond_block outside [0, 64]), LOB_ERR_NOMEM, LOB_ERR_CUDA. */
+int lob_create(const lob_coo* H, const lob_create_opts* opts, lob_matrix** out);
+
+/* Free everything lob_create allocated. NULL is accepted. */
+int lob_destroy(lob_matrix* m);
+
+typedef struct {
+  int64_t n, nnz, ntiles, n_tile_rows;
+  int32_t tile, values, precond_block, reserved;
+  double norm_inf;          /* max_i sum_j |h_ij| over the full symmetric H */
+  int64_t store_bytes;      /* device bytes of the tile store (indices + values kept) */
+  int64_t precond_bytes;    /* device bytes of the preconditioner */
+} lob_matrix_info;
+
+int lob_matrix_info_get(const lob_matrix* m, lob_matrix_info* out);
+
+/* Copy the canonical tile store to host arrays (caller-allocated, sizes from
+ * lob_matrix_info_get): tile_rowptr[n_tile_rows+1] (int64), tile_col[ntiles] (int32),
+ * tile_ptr[ntiles+1] (int64), rc[nnz] (uint32), v64[nnz] (double, needs FP64 values),
+ * v32[nnz] (float, needs FP32 values). Any pointer may be NULL to skip that array. */
+int lob_export_tiles(const lob_matrix* m, int64_t* tile_rowptr, int32_t* tile_col, int64_t* tile_ptr, uint32_t* rc,
+                     double* v64, float* v32);
+
+/* Arithmetic of a product (Section 4.4, footnote 5 sets the paper's pattern). */
+#define LOB_SPMM_FP64 0  /* FP64 values, FP64 X, FP64 products and sums (plain FP64) */
+#define LOB_SPMM_MIXED 1 /* FP32 values, X rounded to FP32, FP32 products and in-tile sums,
+                            tile partials summed across tiles in FP64, FP64 result */
+
+/* Y = H X (Section 4.1: U_i = H_ij W_j and U_j = H_ij^T W_i for every stored tile, here in one
+ * pass over the tiles). X, Y: device, n x nb, row-major FP64, must not overlap. 1 <= nb <= 64.
+ * The requested value copy must have been kept at create. Errors: LOB_ERR_ARG, LOB_ERR_CUDA. */
+int lob_spmm(lob_matrix* m, int32_t mode, const double* X, double* Y, int32_t nb, void* stream);
+
+/* ---- the pieces of one LOBPCG iteration, each exposed for testing and reuse ---- */
+
+/* Block inner product G = A^T B (Section 4.4, the tall-skinny X^T Y): A is n x p (leading
+ * dimension lda), B is n x q (ldb), G is p x q row-major. All device. p, q <= 192.
+ * mode: LOB_SPMM_FP64 for native FP64, LOB_SPMM_MIXED for FP64-class double-float
+ * arithmetic on the FP32 pipes (about 2^-44 relative). */
+int lob_gram(int64_t n, int32_t p, const double* A, int32_t lda, int32_t q, const double* B, int32_t ldb, double* G,
+             int32_t mode, void* stream);
+
+/* Linear combination Y = A C (Section 4.4, eq. 7): A n x p (lda), C p x q row-major, Y n x q
+ * (ldy). Device. p, q <= 192. Y must not overlap A. mode as lob_gram. */
+int lob_lincomb(int64_t n, int32_t p, const double* A, int32_t lda, int32_t q, const double* C, double* Y,
+                int32_t ldy, int32_t mode, void* stream);
+
+/* Block-diagonal preconditioner apply of eq. 11: for each diagonal block [i*b_p, (i+1)*b_p)
+ * of H and each column j, W_[i](:, j) = (H~_[i] - mu_j I)^{-1} R_[i](:, j), through the
+ * eigendecomposition H~_[i] = Q diag(lambda) Q^T made at create; a shifted eigenvalue with
+ * |lambda - mu_j| < 1e-8 ||H|| is replaced by +-1e-8 ||H|| keeping its sign. Arithmetic FP32
+ * (footnote 5), inputs/outputs FP64. R, W: device n x nb; mu: device, nb. Needs
+ * precond_block > 0 at create. */
+int lob_precond_apply(lob_matrix* m, const double* mu, const double* R, double* W, int32_t nb, void* stream);
+
+/* Rayleigh-Ritz of eq. 9 on the GPU, FP64: solve G c = theta M c for symmetric G and
+ * positive-definite M (m x m, device, row-major; only the upper triangles are read) by
+ * Cholesky M = L L^T, the standard problem L^{-1} G L^{-T}, and cyclic Jacobi. theta (device,
+ * m) ascending, C (device, m x m) with C^T M C = I. *info (device int): 0, or j+1 if the
+ * Cholesky pivot j was not positive. m <= 192. */
+int lob_rayleigh_ritz(int32_t m, const double* G, const double* M, double* theta, double* C, int32_t* info,
+                      void* stream);
+
+/* ---- the solver (Algorithm 1) ---- */
+
+#define LOB_MODE_FP64 0  /* every product in FP64 (the plain solver) */
+#define LOB_MODE_MIXED 1 /* FP32-value SpMM, FP64-class block products, then FP64 refinement */
+
+typedef struct {
+  int32_t mode;            /* LOB_MODE_* */
+  int32_t precond;         /* 1: block-diagonal preconditioner (needs precond_block at create) */
+  int32_t max_iter;        /* 0 = 500 */
+  int32_t refine_iter;     /* MIXED: max FP64 refinement iterations; 0 = 50 */
+  double norm_H;           /* 0: use ||H||_inf */
+  int64_t n_small;         /* X0 == NULL: if > 0, the initial guess of eq. 12 from the leading
+                              n_small x n_small block (the smaller configuration space,
+                              Section 3.3.1); else seeded random vectors */
+  uint64_t seed;           /* seed of the random vectors the method draws */
+  int32_t precond_shift;   /* 0: mu_j = theta_j; 1: the per-column rules of Section 4.3 */
+  int32_t verbose;
+  double mixed_tol;        /* MIXED: relative residual at which the FP32-value phase stops
+                              (0 = max(tol, 1e-6)) */
+  void* stream;
+} lob_solve_opts;
+
+typedef struct {
+  int32_t iterations;       /* total LOBPCG iterations (both phases) */
+  int32_t refine_iterations;/* of which FP64 refinement iterations (MIXED) */
+  int32_t spmm_calls;
+  int32_t restarts;         /* times P was dropped after an indefinite Gram matrix */
+  double time_ms;           /* wall time of lob_solve */
+  double phase_ms[8];       /* device time per phase: spmm, gram, rr, update, precond,
+                               residual, orth, guess */
+  double spmm_bytes;        /* algorithmic bytes moved by all SpMMs */
+  double residual[64];      /* final ||H x_j - theta_j x_j|| / (||H|| ||x_j||), FP64 */
+} lob_stats;
+
+/* k smallest eigenpairs of H (Section 3.1 eq. 6; Algorithm 1). 1 <= k <= nb <= 32 (nb - k
+ * extra guard vectors, Section 5.2). tol: stop when every one of the first k columns has
+ * ||H x_j - theta_j x_j|| <= tol ||H|| ||x_j|| (Section 5). X0: device n x nb or NULL (see
+ * n_small). lambda: host, k values ascending. X: device n x nb; columns 0..k-1 are the
+ * eigenvectors (unit 2-norm). st may be NULL. Synchronous. Errors: LOB_ERR_ARG,
+ * LOB_ERR_NOMEM, LOB_ERR_CUDA, LOB_ERR_NOCONV (outputs hold the last iterate),
+ * LOB_ERR_BREAKDOWN. */
+int lob_solve(lob_matrix* m, int32_t k, int32_t nb, double tol, const double* X0, const lob_solve_opts* opts,
+              double* lambda, double* X, lob_stats* st);
+
+const char* lob_strerror(int code);
+
+/* Number of CUDA kernels this library has launched in this process so far (all devices,
+ * all threads). Diagnostic: a benchmark reads it before and after a timed region. */
+long long lob_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,277 @@
+"""Python binding of liblob.so, the GB300 block eigensolver (C ABI in include/lob.h).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels. PyTorch provides device memory and the current stream. There is no CPU path:
+if the library is missing, importing the binding raises.
+
+Main objects:
+  Matrix(n, rows, cols, vals, precond_block=0)  tile store of the upper triangle (lob_create)
+  Matrix.spmm(X, mode)                          Y = H X (lob_spmm)
+  Matrix.solve(k, nb, tol, ...)                 k smallest eigenpairs by LOBPCG (lob_solve)
+  gram, lincomb, rayleigh_ritz, Matrix.precond_apply   the pieces of one iteration
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+LOB_OK = 0
+LOB_ERR_ARG = -1
+LOB_ERR_NOMEM = -2
+LOB_ERR_CUDA = -3
+LOB_ERR_NOCONV = -4
+LOB_ERR_BREAKDOWN = -5
+
+VALUES_FP64, VALUES_FP32, VALUES_BOTH = 1, 2, 3
+SPMM_FP64, SPMM_MIXED = 0, 1
+MODE_FP64, MODE_MIXED = 0, 1
+_MODES = {"fp64": 0, "mixed": 1, 0: 0, 1: 1}
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+
+
+class Coo(ctypes.Structure):
+    _fields_ = [("n", _I64), ("nnz", _I64), ("row", _P), ("col", _P), ("val", _P), ("on_device", _I32)]
+
+
+class CreateOpts(ctypes.Structure):
+    _fields_ = [("tile", _I32), ("values", _I32), ("precond_block", _I32), ("reserved", _I32), ("stream", _P)]
+
+
+class MatrixInfo(ctypes.Structure):
+    _fields_ = [("n", _I64), ("nnz", _I64), ("ntiles", _I64), ("n_tile_rows", _I64), ("tile", _I32),
+                ("values", _I32), ("precond_block", _I32), ("reserved", _I32), ("norm_inf", _D),
+                ("store_bytes", _I64), ("precond_bytes", _I64)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("mode", _I32), ("precond", _I32), ("max_iter", _I32), ("refine_iter", _I32), ("norm_H", _D),
+                ("n_small", _I64), ("seed", ctypes.c_uint64), ("precond_shift", _I32), ("verbose", _I32),
+                ("mixed_tol", _D), ("stream", _P)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", _I32), ("refine_iterations", _I32), ("spmm_calls", _I32), ("restarts", _I32),
+                ("time_ms", _D), ("phase_ms", _D * 8), ("spmm_bytes", _D), ("residual", _D * 64)]
+
+    PHASES = ("spmm", "gram", "rr", "update", "precond", "residual", "orth", "guess")
+
+    def to_dict(self, nb):
+        return dict(iterations=self.iterations, refine_iterations=self.refine_iterations,
+                    spmm_calls=self.spmm_calls, restarts=self.restarts, time_ms=self.time_ms,
+                    phase_ms={p: self.phase_ms[i] for i, p in enumerate(self.PHASES)},
+                    spmm_bytes=self.spmm_bytes, residual=[self.residual[j] for j in range(nb)])
+
+
+class LobError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+def _load():
+    path = os.path.join(_HERE, "liblob.so")
+    if not os.path.exists(path):
+        raise ImportError(f"liblob.so is not built ({path}); run paper_1609_01689_gb300._build.build()")
+    L = ctypes.CDLL(path)
+    L.lob_create.argtypes = [ctypes.POINTER(Coo), ctypes.POINTER(CreateOpts), ctypes.POINTER(_P)]
+    L.lob_destroy.argtypes = [_P]
+    L.lob_matrix_info_get.argtypes = [_P, ctypes.POINTER(MatrixInfo)]
+    L.lob_export_tiles.argtypes = [_P, _P, _P, _P, _P, _P, _P]
+    L.lob_spmm.argtypes = [_P, _I32, _P, _P, _I32, _P]
+    L.lob_gram.argtypes = [_I64, _I32, _P, _I32, _I32, _P, _I32, _P, _I32, _P]
+    L.lob_lincomb.argtypes = [_I64, _I32, _P, _I32, _I32, _P, _P, _I32, _I32, _P]
+    L.lob_precond_apply.argtypes = [_P, _P, _P, _P, _I32, _P]
+    L.lob_rayleigh_ritz.argtypes = [_I32, _P, _P, _P, _P, _P, _P]
+    L.lob_solve.argtypes = [_P, _I32, _I32, _D, _P, ctypes.POINTER(SolveOpts), _P, _P, ctypes.POINTER(Stats)]
+    L.lob_kernel_launches.argtypes = []
+    L.lob_kernel_launches.restype = ctypes.c_longlong
+    L.lob_strerror.argtypes = [ctypes.c_int]
+    L.lob_strerror.restype = ctypes.c_char_p
+    for f in ("lob_create", "lob_destroy", "lob_matrix_info_get", "lob_export_tiles", "lob_spmm", "lob_gram",
+              "lob_lincomb", "lob_precond_apply", "lob_rayleigh_ritz", "lob_solve"):
+        getattr(L, f).restype = ctypes.c_int
+    return L
+
+
+_lib = None
+
+
+def lib():
+    """The loaded liblob.so (raises ImportError if it has not been built)."""
+    global _lib
+    if _lib is None:
+        _lib = _load()
+    return _lib
+
+
+def build(force=False):
+    """Compile liblob.so for sm_103a (nvcc) and load it."""
+    global _lib
+    _build.build(force=force)
+    _lib = None
+    return lib()
+
+
+def kernel_launches():
+    """Kernels this library has launched in this process (lob_kernel_launches)."""
+    return int(lib().lob_kernel_launches())
+
+
+def strerror(code):
+    return lib().lob_strerror(code).decode()
+
+
+def _check(rc, what):
+    if rc != LOB_OK:
+        raise LobError(rc, what)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream():
+    return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+
+
+def _dev_f64(x):
+    torch = _torch()
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64))
+    x = x.to(device="cuda", dtype=torch.float64)
+    return x.contiguous()
+
+
+class Matrix:
+    """Device tile store of a symmetric H given by its upper triangle (lob_create)."""
+
+    def __init__(self, n, rows, cols, vals, precond_block=0, values=VALUES_BOTH):
+        torch = _torch()
+        self._keep = []
+        if isinstance(rows, np.ndarray):
+            r = np.ascontiguousarray(rows, dtype=np.int64)
+            c = np.ascontiguousarray(cols, dtype=np.int64)
+            v = np.ascontiguousarray(vals, dtype=np.float64)
+            coo = Coo(n, len(r), r.ctypes.data, c.ctypes.data, v.ctypes.data, 0)
+            self._keep += [r, c, v]
+        else:
+            r = rows.to(device="cuda", dtype=torch.int64).contiguous()
+            c = cols.to(device="cuda", dtype=torch.int64).contiguous()
+            v = vals.to(device="cuda", dtype=torch.float64).contiguous()
+            coo = Coo(n, r.numel(), r.data_ptr(), c.data_ptr(), v.data_ptr(), 1)
+            self._keep += [r, c, v]
+        opts = CreateOpts(0, values, precond_block, 0, _stream())
+        h = _P()
+        _check(lib().lob_create(ctypes.byref(coo), ctypes.byref(opts), ctypes.byref(h)), "lob_create")
+        self._h = h
+        self._keep = []
+        self.n = int(n)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lob_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        inf = MatrixInfo()
+        _check(lib().lob_matrix_info_get(self._h, ctypes.byref(inf)), "lob_matrix_info_get")
+        return {f: getattr(inf, f) for f, _ in MatrixInfo._fields_}
+
+    def export_tiles(self):
+        inf = self.info()
+        nt, ntl, nnz = inf["n_tile_rows"], inf["ntiles"], inf["nnz"]
+        rp = np.empty(nt + 1, np.int64)
+        tc = np.empty(ntl, np.int32)
+        tp = np.empty(ntl + 1, np.int64)
+        rc = np.empty(nnz, np.uint32)
+        v64 = np.empty(nnz, np.float64) if inf["values"] & VALUES_FP64 else None
+        v32 = np.empty(nnz, np.float32) if inf["values"] & VALUES_FP32 else None
+        _check(lib().lob_export_tiles(self._h, rp.ctypes.data, tc.ctypes.data, tp.ctypes.data, rc.ctypes.data,
+                                      v64.ctypes.data if v64 is not None else None,
+                                      v32.ctypes.data if v32 is not None else None), "lob_export_tiles")
+        return dict(tile_rowptr=rp, tile_col=tc, tile_ptr=tp, rc=rc, v64=v64, v32=v32, ntiles=ntl)
+
+    def spmm(self, X, mode="fp64", out=None):
+        X = _dev_f64(X)
+        nb = 1 if X.dim() == 1 else X.shape[1]
+        Y = out if out is not None else _torch().empty_like(X)
+        _check(lib().lob_spmm(self._h, _MODES[mode], X.data_ptr(), Y.data_ptr(), nb, _stream()), "lob_spmm")
+        return Y
+
+    def precond_apply(self, mu, R):
+        R = _dev_f64(R)
+        mu = _dev_f64(mu)
+        W = _torch().empty_like(R)
+        _check(lib().lob_precond_apply(self._h, mu.data_ptr(), R.data_ptr(), W.data_ptr(), R.shape[1], _stream()),
+               "lob_precond_apply")
+        return W
+
+    def solve(self, k, nb, tol, X0=None, mode="fp64", precond=False, n_small=0, max_iter=0, refine_iter=0,
+              seed=1, precond_shift=0, mixed_tol=0.0, norm_H=0.0, X_out=None):
+        """k smallest eigenpairs (lob_solve). Returns (lam, X, stats, status)."""
+        torch = _torch()
+        X = X_out if X_out is not None else torch.empty((self.n, nb), dtype=torch.float64, device="cuda")
+        x0 = _dev_f64(X0) if X0 is not None else None
+        lam = np.zeros(k, np.float64)
+        st = Stats()
+        o = SolveOpts(_MODES[mode], int(bool(precond)), max_iter, refine_iter, norm_H, n_small, seed, precond_shift,
+                      0, mixed_tol, _stream())
+        rc = lib().lob_solve(self._h, k, nb, tol, x0.data_ptr() if x0 is not None else None, ctypes.byref(o),
+                             lam.ctypes.data, X.data_ptr(), ctypes.byref(st))
+        if rc not in (LOB_OK, LOB_ERR_NOCONV):
+            raise LobError(rc, "lob_solve")
+        return lam, X, st.to_dict(nb), rc
+
+
+def gram(A, B, mode="fp64"):
+    """A^T B for tall-skinny device blocks (lob_gram)."""
+    A = _dev_f64(A); B = _dev_f64(B)
+    G = _torch().empty((A.shape[1], B.shape[1]), dtype=_torch().float64, device="cuda")
+    _check(lib().lob_gram(A.shape[0], A.shape[1], A.data_ptr(), A.shape[1], B.shape[1], B.data_ptr(), B.shape[1],
+                          G.data_ptr(), _MODES[mode], _stream()), "lob_gram")
+    return G
+
+
+def lincomb(A, C, mode="fp64"):
+    """A C for a tall-skinny device block (lob_lincomb)."""
+    A = _dev_f64(A); C = _dev_f64(C)
+    Y = _torch().empty((A.shape[0], C.shape[1]), dtype=_torch().float64, device="cuda")
+    _check(lib().lob_lincomb(A.shape[0], A.shape[1], A.data_ptr(), A.shape[1], C.shape[1], C.data_ptr(), Y.data_ptr(),
+                             C.shape[1], _MODES[mode], _stream()), "lob_lincomb")
+    return Y
+
+
+def rayleigh_ritz(G, M):
+    """theta, C with G C = M C diag(theta) (lob_rayleigh_ritz); raises on an indefinite M."""
+    torch = _torch()
+    G = _dev_f64(G); M = _dev_f64(M)
+    m = G.shape[0]
+    theta = torch.empty(m, dtype=torch.float64, device="cuda")
+    C = torch.empty((m, m), dtype=torch.float64, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    _check(lib().lob_rayleigh_ritz(m, G.data_ptr(), M.data_ptr(), theta.data_ptr(), C.data_ptr(), info.data_ptr(),
+                                   _stream()), "lob_rayleigh_ritz")
+    if int(info.item()) != 0:
+        raise np.linalg.LinAlgError(f"Gram matrix not positive definite (pivot {int(info.item())})")
+    return theta, C

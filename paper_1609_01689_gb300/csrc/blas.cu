@@ -1,0 +1,186 @@
+// Tall-skinny block kernels of one LOBPCG iteration (Section 4.4): the block inner product
+// G = A^T B ("X^T Y") and the linear combination Y = A C (eq. 7).
+//
+// The paper splits the tall matrices into row blocks, forms small products per block and
+// aggregates them (Section 4.4). Here each CTA owns a chunk of rows and a 48 x 48 tile of G,
+// keeps its partial in registers (3 x 3 per thread), and a second kernel sums the chunk
+// partials in a fixed order, so the result is deterministic.
+//
+// Arithmetic (mode): LOB_SPMM_FP64 -- native FP64 fused multiply-adds.
+//                    LOB_SPMM_MIXED -- double-float (df.cuh) on the FP32 pipes: operands split
+//                    on load (|x - (hi+lo)| <= 2^-48 |x|), products exact in their hi parts,
+//                    sums error-free in hi; relative error per accumulated term ~2^-46.
+#include "common.cuh"
+#include "df.cuh"
+
+namespace {
+
+constexpr int TG = 48;  // output tile edge
+constexpr int RB = 16;  // rows staged per step
+
+template <bool DF>
+struct Ar;
+template <>
+struct Ar<false> {
+  using in_t = double;
+  struct acc_t { double v; };
+  __device__ static in_t load(double x) { return x; }
+  __device__ static in_t zero_in() { return 0.0; }
+  __device__ static void zero(acc_t& a) { a.v = 0.0; }
+  __device__ static void mac(acc_t& a, in_t x, in_t y) { a.v = fma(x, y, a.v); }
+  __device__ static double out(acc_t a) { return a.v; }
+};
+template <>
+struct Ar<true> {
+  using in_t = float2;
+  struct acc_t { float hi, lo; };
+  __device__ static in_t load(double x) { return df_split(x); }
+  __device__ static in_t zero_in() { return make_float2(0.f, 0.f); }
+  __device__ static void zero(acc_t& a) { a.hi = 0.f; a.lo = 0.f; }
+  __device__ static void mac(acc_t& a, in_t x, in_t y) { df_mac(a.hi, a.lo, x.x, x.y, y.x, y.y); }
+  __device__ static double out(acc_t a) { df_renorm(a.hi, a.lo); return df_join(a.hi, a.lo); }
+};
+
+template <bool DF>
+__global__ void __launch_bounds__(256) k_gram(int64_t n, int p, const double* __restrict__ A, int lda, int q,
+                                              const double* __restrict__ B, int ldb, double* __restrict__ part,
+                                              int64_t rpc) {
+  using R = Ar<DF>;
+  using in_t = typename R::in_t;
+  __shared__ in_t As[RB][TG];
+  __shared__ in_t Bs[RB][TG];
+  const int chunk = blockIdx.x;
+  const int a0 = blockIdx.y * TG, b0 = blockIdx.z * TG;
+  const int64_t r0 = (int64_t)chunk * rpc;
+  const int64_t r1 = (r0 + rpc) < n ? (r0 + rpc) : n;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  typename R::acc_t acc[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; i++)
+#pragma unroll
+    for (int j = 0; j < 3; j++) R::zero(acc[i][j]);
+  for (int64_t rr = r0; rr < r1; rr += RB) {
+    for (int idx = tid; idx < RB * TG; idx += 256) {
+      const int i = idx / TG, a = idx % TG;
+      const int64_t r = rr + i;
+      As[i][a] = (r < r1 && a0 + a < p) ? R::load(A[r * lda + a0 + a]) : R::zero_in();
+      Bs[i][a] = (r < r1 && b0 + a < q) ? R::load(B[r * ldb + b0 + a]) : R::zero_in();
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int i = 0; i < RB; i++) {
+      in_t av[3], bv[3];
+#pragma unroll
+      for (int u = 0; u < 3; u++) { av[u] = As[i][ty + 16 * u]; bv[u] = Bs[i][tx + 16 * u]; }
+#pragma unroll
+      for (int u = 0; u < 3; u++)
+#pragma unroll
+        for (int v = 0; v < 3; v++) R::mac(acc[u][v], av[u], bv[v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 3; u++)
+#pragma unroll
+    for (int v = 0; v < 3; v++) {
+      const int a = a0 + ty + 16 * u, b = b0 + tx + 16 * v;
+      if (a < p && b < q) part[(int64_t)chunk * p * q + (int64_t)a * q + b] = R::out(acc[u][v]);
+    }
+}
+
+// G[e] = sum over chunks of part[chunk][e], one warp per entry, fixed order.
+__global__ void k_gram_reduce(int nchunks, int pq, const double* __restrict__ part, double* __restrict__ G) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+  if (warp >= pq) return;
+  double s = 0.0;
+  for (int c = lane; c < nchunks; c += 32) s += part[(int64_t)c * pq + warp];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+  if (lane == 0) G[warp] = s;
+}
+
+template <bool DF>
+__global__ void __launch_bounds__(256) k_lincomb(int64_t n, int p, const double* __restrict__ A, int lda, int q,
+                                                 const double* __restrict__ C, double* __restrict__ Y, int ldy) {
+  using R = Ar<DF>;
+  using in_t = typename R::in_t;
+  extern __shared__ __align__(16) unsigned char sm[];
+  in_t* As = reinterpret_cast<in_t*>(sm);  // [16][p]
+  in_t* Cs = As + 16 * p;                  // [p][16]
+  const int64_t r0 = (int64_t)blockIdx.x * 16;
+  const int j0 = blockIdx.y * 16;
+  const int tid = threadIdx.x, rl = tid / 16, j = tid % 16;
+  for (int idx = tid; idx < 16 * p; idx += 256) {
+    const int i = idx / p, a = idx % p;
+    const int64_t r = r0 + i;
+    As[idx] = r < n ? R::load(A[r * lda + a]) : R::zero_in();
+  }
+  for (int idx = tid; idx < 16 * p; idx += 256) {
+    const int a = idx / 16, jj = idx % 16;
+    Cs[idx] = (j0 + jj < q) ? R::load(C[(int64_t)a * q + j0 + jj]) : R::zero_in();
+  }
+  __syncthreads();
+  typename R::acc_t acc;
+  R::zero(acc);
+  for (int a = 0; a < p; a++) R::mac(acc, As[rl * p + a], Cs[a * 16 + j]);
+  const int64_t r = r0 + rl;
+  if (r < n && j0 + j < q) Y[r * ldy + j0 + j] = R::out(acc);
+}
+
+inline int nchunks_for(int64_t n, int tiles) {
+  int64_t c = (4 * 152 + tiles - 1) / tiles;
+  int64_t maxc = (n + 63) / 64;
+  if (c > maxc) c = maxc;
+  return (int)(c < 1 ? 1 : c);
+}
+
+}  // namespace
+
+size_t lob_gram_work_doubles(int64_t n, int p, int q) {
+  const int tiles = ((p + TG - 1) / TG) * ((q + TG - 1) / TG);
+  return (size_t)nchunks_for(n, tiles) * p * q;
+}
+
+int lob_gram_launch_ws(int64_t n, int p, const double* A, int lda, int q, const double* B, int ldb, double* G,
+                       int mode, double* work, cudaStream_t st) {
+  const int ta = (p + TG - 1) / TG, tb = (q + TG - 1) / TG;
+  const int nch = nchunks_for(n, ta * tb);
+  const int64_t rpc = (n + nch - 1) / nch;
+  dim3 grid(nch, ta, tb);
+  if (mode == LOB_SPMM_MIXED)
+    (k_gram<true><<<grid, 256, 0, st>>>(n, p, A, lda, q, B, ldb, work, rpc), LOB_LAUNCHED());
+  else
+    (k_gram<false><<<grid, 256, 0, st>>>(n, p, A, lda, q, B, ldb, work, rpc), LOB_LAUNCHED());
+  const int pq = p * q;
+  (k_gram_reduce<<<(pq * 32 + 255) / 256, 256, 0, st>>>(nch, pq, work, G), LOB_LAUNCHED());
+  LOB_CUDA(cudaGetLastError());
+  return LOB_OK;
+}
+
+int lob_gram_launch(int64_t n, int p, const double* A, int lda, int q, const double* B, int ldb, double* G, int mode,
+                    cudaStream_t st) {
+  if (n < 1 || p < 1 || q < 1 || p > 192 || q > 192 || lda < p || ldb < q || !A || !B || !G) return LOB_ERR_ARG;
+  if (mode != LOB_SPMM_FP64 && mode != LOB_SPMM_MIXED) return LOB_ERR_ARG;
+  double* work = nullptr;
+  LOB_CUDA(cudaMallocAsync((void**)&work, lob_gram_work_doubles(n, p, q) * sizeof(double), st));
+  int rc = lob_gram_launch_ws(n, p, A, lda, q, B, ldb, G, mode, work, st);
+  cudaFreeAsync(work, st);
+  return rc;
+}
+
+int lob_lincomb_launch(int64_t n, int p, const double* A, int lda, int q, const double* C, double* Y, int ldy,
+                       int mode, cudaStream_t st) {
+  if (n < 1 || p < 1 || q < 1 || p > 192 || q > 192 || lda < p || ldy < q || !A || !C || !Y) return LOB_ERR_ARG;
+  if (mode != LOB_SPMM_FP64 && mode != LOB_SPMM_MIXED) return LOB_ERR_ARG;
+  dim3 grid((unsigned)((n + 15) / 16), (q + 15) / 16);
+  const size_t smem = 2ull * 16 * p * (mode == LOB_SPMM_MIXED ? sizeof(float2) : sizeof(double));
+  if (mode == LOB_SPMM_MIXED) {
+    LOB_CUDA(cudaFuncSetAttribute(k_lincomb<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    (k_lincomb<true><<<grid, 256, smem, st>>>(n, p, A, lda, q, C, Y, ldy), LOB_LAUNCHED());
+  } else {
+    LOB_CUDA(cudaFuncSetAttribute(k_lincomb<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    (k_lincomb<false><<<grid, 256, smem, st>>>(n, p, A, lda, q, C, Y, ldy), LOB_LAUNCHED());
+  }
+  LOB_CUDA(cudaGetLastError());
+  return LOB_OK;
+}

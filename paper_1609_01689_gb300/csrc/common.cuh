@@ -1,0 +1,90 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <atomic>
+#include <vector>
+
+#include "lob.h"
+
+#define LOB_TILE 256
+#define LOB_TILE_LOG 8
+
+// Report a failed CUDA call and return LOB_ERR_CUDA from the enclosing function.
+#define LOB_CUDA(call)                                                                          \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess) {                                                                    \
+      fprintf(stderr, "lob: CUDA error %s at %s:%d (%s)\n", cudaGetErrorString(e_), __FILE__,   \
+              __LINE__, #call);                                                                 \
+      return LOB_ERR_CUDA;                                                                      \
+    }                                                                                           \
+  } while (0)
+
+// Count of kernel launches made by this library (diagnostic, lob_kernel_launches()).
+extern std::atomic<long long> g_lob_launches;
+#define LOB_LAUNCHED() g_lob_launches.fetch_add(1, std::memory_order_relaxed)
+
+#define LOB_TRY(expr)       \
+  do {                      \
+    int rc_ = (expr);       \
+    if (rc_ != LOB_OK) return rc_; \
+  } while (0)
+
+// Device tile store (canonical order: tiles by (tile row, tile col), entries by (r, c)).
+struct lob_tiles {
+  int64_t n = 0, nnz = 0, ntiles = 0, nt = 0;  // nt = number of tile rows
+  int64_t* rowptr = nullptr;   // [nt+1] first tile of each tile row
+  int32_t* tcol = nullptr;     // [ntiles] tile column
+  int32_t* trow = nullptr;     // [ntiles] tile row (derived, for per-tile launches)
+  int64_t* tptr = nullptr;     // [ntiles+1] first entry of each tile
+  uint32_t* rc = nullptr;      // [nnz] (r << 16) | c
+  double* v64 = nullptr;       // [nnz] FP64 values (may be null)
+  float* v32 = nullptr;        // [nnz] FP32 values (may be null)
+};
+
+// Block-diagonal preconditioner of eq. 11: per block i (rows [i*bp, i*bp + m_i)),
+// H~_[i] = Q_i diag(lam_i) Q_i^T; Q stored FP32, column-major per block (bp x bp slots).
+struct lob_precond {
+  int32_t bp = 0;
+  int64_t nblk = 0;
+  float* Q = nullptr;      // [nblk * bp * bp]
+  float* lam = nullptr;    // [nblk * bp]
+  double* dblk = nullptr;  // [nblk * bp * bp] dense FP64 blocks (kept for the oracle-free self test)
+};
+
+struct lob_matrix {
+  lob_tiles T;
+  std::vector<int64_t> h_rowptr;  // host copy of T.rowptr
+  lob_precond P;
+  int32_t values = LOB_VALUES_BOTH;
+  double norm_inf = 0.0;
+  int device = 0;
+};
+
+// ---- internal launchers (return LOB_OK or an error code) ----
+int lob_build_tiles(const lob_coo* H, int values, cudaStream_t st, lob_tiles* T, double* norm_inf);
+void lob_free_tiles(lob_tiles* T);
+int lob_build_precond(const lob_coo* Hdev, int bp, int64_t n, cudaStream_t st, lob_precond* P);
+void lob_free_precond(lob_precond* P);
+
+// Y = H X over the active leading n_act x n_act block (n_act <= n; rows/cols >= n_act are
+// treated as absent). Y is fully written (rows >= n_act get 0).
+int lob_spmm_launch(const lob_matrix* m, int mode, const double* X, double* Y, int nb, int64_t n_act,
+                    cudaStream_t st);
+int lob_gram_launch(int64_t n, int p, const double* A, int lda, int q, const double* B, int ldb, double* G, int mode,
+                    cudaStream_t st);
+int lob_lincomb_launch(int64_t n, int p, const double* A, int lda, int q, const double* C, double* Y, int ldy,
+                       int mode, cudaStream_t st);
+int lob_precond_launch(const lob_matrix* m, const double* mu, const double* R, double* W, int nb, int64_t n_act,
+                       cudaStream_t st);
+int lob_rr_launch(int m, const double* G, const double* M, double* theta, double* C, int32_t* info, double* work,
+                  cudaStream_t st);
+size_t lob_rr_work_doubles(int m);
+size_t lob_gram_work_doubles(int64_t n, int p, int q);
+int lob_gram_launch_ws(int64_t n, int p, const double* A, int lda, int q, const double* B, int ldb, double* G,
+                       int mode, double* work, cudaStream_t st);
+int lob_solve_impl(lob_matrix* m, int32_t k, int32_t nb, double tol, const double* X0,
+                              const lob_solve_opts* o, double* lambda, double* X, lob_stats* st, int64_t n_act);

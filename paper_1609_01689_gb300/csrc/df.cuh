@@ -1,0 +1,93 @@
+// Double-float ("df") arithmetic: a value is an unevaluated sum hi + lo of two FP32 numbers,
+// giving about 48 significant bits on the FP32 pipes. The FP64 pipe of this GPU runs at
+// 1/70 of the FP32 rate, so the FP64-class block products (Section 4.4, footnote 5) use
+// this representation; their error bounds are stated where they are used.
+//
+// Building blocks (error-free transformations):
+//   TwoSum(a, b) = (s, t) with s = fl(a + b) and a + b = s + t exactly (Knuth);
+//   TwoProd(a, b) = (p, e) with p = fl(a * b) and a * b = p + e exactly, e = fma(a, b, -p).
+// The intrinsics __fadd_rn / __fmul_rn / __fsub_rn are never contracted or reassociated.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+// x = hi + lo with hi = x truncated to 24 significant bits (exact in FP32) and lo = the
+// remainder rounded to FP32, so |x - (hi + lo)| <= 2^-48 |x|. Integer and FP32 operations
+// only, for 2^-74 <= |x| < 2^128; other magnitudes (including 0) take the conversion path.
+__device__ __forceinline__ float2 df_split(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e < 949 || e > 1150) {
+    const float hi = __double2float_rn(x);
+    const float lo = __double2float_rn(x - (double)hi);
+    return make_float2(hi, lo);
+  }
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const float hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu));
+  const unsigned m = (unsigned)(b & 0x1FFFFFFFull);  // low 29 bits of the significand
+  const float mh = __fsub_rn(__uint_as_float(0x4B000000u | (m >> 6)), 8388608.0f);   // exact
+  const float ml = __fsub_rn(__uint_as_float(0x4B000000u | (m & 63u)), 8388608.0f);  // exact
+  const float mf = __fmaf_rn(mh, 64.0f, ml);  // m, correctly rounded to 24 bits
+  const float lo = __fmul_rn(mf, __uint_as_float((unsigned)(e - 948) << 23));  // * 2^(e-1075), exact
+  return make_float2(hi, __uint_as_float(__float_as_uint(lo) | sign));
+}
+
+// hi + lo rounded to FP64.
+__device__ __forceinline__ double df_join(float hi, float lo) { return (double)hi + (double)lo; }
+
+// Renormalise so that |lo| <= ulp(hi)/2 (Fast2Sum; valid because |lo| is small against hi
+// or hi == 0).
+__device__ __forceinline__ void df_renorm(float& hi, float& lo) {
+  const float s = __fadd_rn(hi, lo);
+  lo = __fsub_rn(lo, __fsub_rn(s, hi));
+  hi = s;
+}
+
+// a += x * y with x = (xh, xl), y = (yh, yl). The hi-hi product is exact (TwoProd), the
+// cross products are added to the low part (their own rounding is ~2^-48 relative), the
+// lo*lo term (~2^-48) is dropped, and the addition into a.hi is error-free (TwoSum) with its
+// error kept in a.lo. a.lo is not renormalised here; call df_renorm at the end.
+__device__ __forceinline__ void df_mac(float& ahi, float& alo, float xh, float xl, float yh, float yl) {
+  const float p = __fmul_rn(xh, yh);
+  float e = __fmaf_rn(xh, yh, -p);
+  e = __fmaf_rn(xh, yl, e);
+  e = __fmaf_rn(xl, yh, e);
+  const float s = __fadd_rn(ahi, p);
+  const float bb = __fsub_rn(s, ahi);
+  const float t = __fadd_rn(__fsub_rn(ahi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  ahi = s;
+  alo = __fadd_rn(alo, __fadd_rn(t, e));
+}
+
+// a += b for two df numbers (TwoSum on the high parts, low parts summed).
+__device__ __forceinline__ void df_add(float& ahi, float& alo, float bh, float bl) {
+  const float s = __fadd_rn(ahi, bh);
+  const float bb = __fsub_rn(s, ahi);
+  const float t = __fadd_rn(__fsub_rn(ahi, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+  ahi = s;
+  alo = __fadd_rn(alo, __fadd_rn(t, bl));
+}
+
+// x rounded toward zero to FP32 using integer operations in the normal range (2^-126 <= |x|
+// < 2^128); other magnitudes use the conversion instruction.
+__device__ __forceinline__ float f64_to_f32_rz(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e < 897 || e > 1150) return __double2float_rz(x);
+  return __uint_as_float(((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)(e - 896) << 23) |
+                         (unsigned)((b >> 29) & 0x7FFFFFu));
+}
+
+// Exact widening of an FP32 value to FP64 with integer operations (normal numbers and zero);
+// subnormal, infinite and NaN inputs use the conversion instruction.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) {
+    if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)((unsigned long long)(u & 0x80000000u) << 32));
+    return (double)f;
+  }
+  const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                  ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)bits);
+}

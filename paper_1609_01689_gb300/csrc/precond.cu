@@ -1,0 +1,199 @@
+// Block-diagonal preconditioner T_j = H~ - mu_j I of Section 3.2 (eq. 11), with H~ the
+// diagonal b_p x b_p blocks of H (Section 4.3 builds it from diagonal tiles; here fixed-size
+// blocks, the last one partial).
+//
+// Setup, once per matrix: gather each diagonal block (both triangles) densely and compute
+// H~_[i] = Q_i diag(lambda_i) Q_i^T by cyclic Jacobi, one CTA per block, in FP32 -- the paper
+// runs the preconditioner in single precision (footnote 5 of Section 4.4). A direct solve of
+// eq. 11 for every shift is then W_[i] = Q_i (Lambda_i - mu_j I)^{-1} Q_i^T R_[i], which needs
+// no factorisation per shift: two small products per block and a scaling.
+#include "common.cuh"
+#include "df.cuh"
+
+namespace {
+
+__global__ void k_gather_blocks(int64_t nnz, const int64_t* __restrict__ row, const int64_t* __restrict__ col,
+                                const double* __restrict__ val, int bp, double* __restrict__ blk) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nnz) return;
+  const int64_t i = row[t], j = col[t];
+  const int64_t b = i / bp;
+  if (j / bp != b) return;
+  const int64_t o = b * bp;
+  double* B = blk + b * (int64_t)bp * bp;
+  B[(i - o) * bp + (j - o)] = val[t];
+  B[(j - o) * bp + (i - o)] = val[t];
+}
+
+// One CTA per block: FP32 cyclic Jacobi (round-robin order) on the bp x bp block in shared
+// memory. Q (column k = eigenvector k) and lambda written per block.
+__global__ void __launch_bounds__(256) k_block_eig(int bp, const double* __restrict__ blk, float* __restrict__ Q,
+                                                   float* __restrict__ lam) {
+  extern __shared__ float sm[];
+  float* A = sm;            // bp x bp
+  float* V = A + bp * bp;   // bp x bp
+  __shared__ float cs_c[32], cs_s[32];
+  __shared__ int pr_p[32], pr_q[32];
+  __shared__ float red[8];
+  __shared__ float s_off, s_fro;
+  const int64_t b = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x, mm = bp * bp;
+  const double* B = blk + b * (int64_t)mm;
+  for (int e = tid; e < mm; e += nt) {
+    A[e] = __double2float_rn(B[e]);
+    V[e] = (e / bp == e % bp) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  const int mp = bp + (bp & 1), np = mp / 2;
+  for (int sweep = 0; sweep < 30; sweep++) {
+    float off = 0.f, fro = 0.f;
+    for (int e = tid; e < mm; e += nt) {
+      const float x = A[e];
+      fro += x * x;
+      if (e / bp != e % bp) off += x * x;
+    }
+    for (int o = 16; o > 0; o >>= 1) { off += __shfl_down_sync(0xFFFFFFFFu, off, o); fro += __shfl_down_sync(0xFFFFFFFFu, fro, o); }
+    if (tid % 32 == 0) red[tid / 32] = off;
+    __syncthreads();
+    if (tid == 0) { float s = 0; for (int w = 0; w < nt / 32; w++) s += red[w]; s_off = s; }
+    __syncthreads();
+    if (tid % 32 == 0) red[tid / 32] = fro;
+    __syncthreads();
+    if (tid == 0) { float s = 0; for (int w = 0; w < nt / 32; w++) s += red[w]; s_fro = s; }
+    __syncthreads();
+    if (s_off <= 1e-13f * s_fro || s_off == 0.f) break;
+    for (int round = 0; round < mp - 1; round++) {
+      for (int k = tid; k < np; k += nt) {
+        int p = k == 0 ? 0 : 1 + (k - 1 + round) % (mp - 1);
+        const int pos = mp - 1 - k;
+        int q = pos == 0 ? 0 : 1 + (pos - 1 + round) % (mp - 1);
+        if (p > q) { int t = p; p = q; q = t; }
+        float c = 1.f, s = 0.f;
+        if (q < bp) {
+          const float apq = A[p * bp + q];
+          if (apq != 0.f) {
+            const float tau = (A[q * bp + q] - A[p * bp + p]) / (2.f * apq);
+            const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+            c = rsqrtf(1.f + t * t);
+            s = t * c;
+          }
+        }
+        pr_p[k] = p; pr_q[k] = q; cs_c[k] = c; cs_s[k] = s;
+      }
+      __syncthreads();
+      for (int e = tid; e < np * bp; e += nt) {
+        const int k = e / bp, col = e % bp, p = pr_p[k], q = pr_q[k];
+        if (q >= bp || cs_s[k] == 0.f) continue;
+        const float c = cs_c[k], s = cs_s[k], ap = A[p * bp + col], aq = A[q * bp + col];
+        A[p * bp + col] = c * ap - s * aq;
+        A[q * bp + col] = s * ap + c * aq;
+      }
+      __syncthreads();
+      for (int e = tid; e < np * bp; e += nt) {
+        const int k = e / bp, r = e % bp, p = pr_p[k], q = pr_q[k];
+        if (q >= bp || cs_s[k] == 0.f) continue;
+        const float c = cs_c[k], s = cs_s[k];
+        const float ap = A[r * bp + p], aq = A[r * bp + q];
+        A[r * bp + p] = c * ap - s * aq;
+        A[r * bp + q] = s * ap + c * aq;
+        const float vp = V[r * bp + p], vq = V[r * bp + q];
+        V[r * bp + p] = c * vp - s * vq;
+        V[r * bp + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  float* Qb = Q + b * (int64_t)mm;
+  for (int e = tid; e < mm; e += nt) {
+    const int k = e / bp, i = e % bp;  // column-major: Qb[k*bp + i] = V[i][k]
+    Qb[e] = V[i * bp + k];
+  }
+  for (int k = tid; k < bp; k += nt) lam[b * bp + k] = A[k * bp + k];
+}
+
+// W_[i] = Q (Lambda - mu_j)^{-1} Q^T R_[i]; one CTA per block, FP32 arithmetic.
+__global__ void __launch_bounds__(256) k_block_apply(int bp, int64_t n_act, const float* __restrict__ Q,
+                                                     const float* __restrict__ lam, const double* __restrict__ mu,
+                                                     float guard, const double* __restrict__ R, double* __restrict__ W,
+                                                     int nb) {
+  extern __shared__ float sm[];
+  float* Qs = sm;             // bp x bp, column-major (Qs[k*bp + i])
+  float* Rs = Qs + bp * bp;   // bp x nb
+  float* Ts = Rs + bp * nb;   // bp x nb
+  const int64_t b = blockIdx.x;
+  const int64_t o = b * bp;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const float* Qb = Q + b * (int64_t)bp * bp;
+  for (int e = tid; e < bp * bp; e += nt) Qs[e] = Qb[e];
+  for (int e = tid; e < bp * nb; e += nt) {
+    const int i = e / nb, j = e % nb;
+    Rs[e] = (o + i < n_act) ? f64_to_f32_rz(R[(o + i) * nb + j]) : 0.f;
+  }
+  __syncthreads();
+  for (int e = tid; e < bp * nb; e += nt) {  // T = diag(1/(lambda - mu)) Q^T R
+    const int k = e / nb, j = e % nb;
+    float s = 0.f;
+    for (int i = 0; i < bp; i++) s = fmaf(Qs[k * bp + i], Rs[i * nb + j], s);
+    const float2 m = df_split(mu[j]);
+    float d = __fsub_rn(__fsub_rn(lam[b * bp + k], m.x), m.y);
+    if (fabsf(d) < guard) d = d < 0.f ? -guard : guard;
+    Ts[e] = s / d;
+  }
+  __syncthreads();
+  for (int e = tid; e < bp * nb; e += nt) {  // W = Q T
+    const int i = e / nb, j = e % nb;
+    if (o + i >= n_act) continue;
+    float s = 0.f;
+    for (int k = 0; k < bp; k++) s = fmaf(Qs[k * bp + i], Ts[k * nb + j], s);
+    W[(o + i) * nb + j] = f32_to_f64(s);
+  }
+}
+
+}  // namespace
+
+void lob_free_precond(lob_precond* P) {
+  cudaFree(P->Q); cudaFree(P->lam); cudaFree(P->dblk);
+  *P = lob_precond();
+}
+
+int lob_build_precond(const lob_coo* H, int bp, int64_t n, cudaStream_t st, lob_precond* P) {
+  if (bp < 1 || bp > 64 || !H->on_device) return LOB_ERR_ARG;
+  lob_precond R;
+  R.bp = bp;
+  R.nblk = (n + bp - 1) / bp;
+  const size_t mm = (size_t)bp * bp;
+  if (cudaMalloc(&R.dblk, R.nblk * mm * 8) != cudaSuccess || cudaMalloc(&R.Q, R.nblk * mm * 4) != cudaSuccess ||
+      cudaMalloc(&R.lam, R.nblk * bp * 4) != cudaSuccess) {
+    cudaGetLastError();
+    lob_free_precond(&R);
+    return LOB_ERR_NOMEM;
+  }
+  cudaMemsetAsync(R.dblk, 0, R.nblk * mm * 8, st);
+  (k_gather_blocks<<<(unsigned)((H->nnz + 255) / 256), 256, 0, st>>>(H->nnz, H->row, H->col, H->val, bp, R.dblk), LOB_LAUNCHED());
+  const size_t smem = 2 * mm * sizeof(float);
+  (k_block_eig<<<(unsigned)R.nblk, 256, smem, st>>>(bp, R.dblk, R.Q, R.lam), LOB_LAUNCHED());
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+    fprintf(stderr, "lob: preconditioner setup failed: %s\n", cudaGetErrorString(e));
+    lob_free_precond(&R);
+    return LOB_ERR_CUDA;
+  }
+  cudaFree(R.dblk);  // the dense blocks are only needed for the factorisation
+  R.dblk = nullptr;
+  *P = R;
+  return LOB_OK;
+}
+
+int lob_precond_launch(const lob_matrix* m, const double* mu, const double* R, double* W, int nb, int64_t n_act,
+                       cudaStream_t st) {
+  const lob_precond& P = m->P;
+  if (P.bp < 1 || nb < 1 || nb > 64) return LOB_ERR_ARG;
+  const int bp = P.bp;
+  const size_t smem = ((size_t)bp * bp + 2ull * bp * nb) * sizeof(float);
+  const int64_t nblk = (n_act + bp - 1) / bp;
+  if (n_act < m->T.n) LOB_CUDA(cudaMemsetAsync(W + n_act * nb, 0, (size_t)(m->T.n - n_act) * nb * 8, st));
+  if (nblk > 0)
+    (k_block_apply<<<(unsigned)nblk, 256, smem, st>>>(bp, n_act, P.Q, P.lam, mu, (float)(1e-8 * m->norm_inf), R, W, nb), LOB_LAUNCHED());
+  LOB_CUDA(cudaGetLastError());
+  return LOB_OK;
+}

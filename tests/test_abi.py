@@ -1,0 +1,57 @@
+"""The C ABI library builds for sm_103a, loads, and exports every function include/ declares.
+No compute calls (no GPU needed)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+from conftest import ROOT
+
+
+def declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            text = open(os.path.join(inc, f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            for m in re.finditer(r"^\s*(?:int|const char\*|int64_t|void)\s+(lob_\w+)\s*\(", text, flags=re.M):
+                names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def built_lib():
+    from paper_1609_01689_gb300 import _build
+    return _build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for f in ("lob_create", "lob_spmm", "lob_solve", "lob_destroy", "lob_strerror", "lob_gram", "lob_lincomb",
+              "lob_precond_apply", "lob_rayleigh_ritz", "lob_export_tiles", "lob_matrix_info_get"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol(built_lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", built_lib], capture_output=True, text=True, check=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    missing = declared_functions() - exported
+    assert not missing, missing
+
+
+def test_library_loads_and_reports_errors(built_lib):
+    import paper_1609_01689_gb300 as lob
+    lib = lob.build()
+    assert lob.strerror(lob.LOB_ERR_ARG) == "invalid argument"
+    assert lob.strerror(lob.LOB_ERR_NOCONV).startswith("iteration limit")
+    # argument checks happen before any device work
+    assert lib.lob_spmm(None, 0, None, None, 8, None) == lob.LOB_ERR_ARG
+    assert lib.lob_gram(0, 1, None, 1, 1, None, 1, None, 0, None) == lob.LOB_ERR_ARG
+    assert lib.lob_destroy(None) == lob.LOB_OK
+
+
+def test_synth_device_library_builds():
+    import synth
+    assert os.path.exists(synth.build_device())

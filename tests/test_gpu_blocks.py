@@ -1,0 +1,118 @@
+"""The pieces of one LOBPCG iteration on the GPU against the oracle: block inner product and
+linear combination (Section 4.4) in FP64 and double-float, the block-diagonal preconditioner
+(eq. 11) and the Rayleigh-Ritz step (eq. 9)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import random_upper
+
+pytestmark = pytest.mark.gpu
+
+
+def t(x):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("n,p,q", [(1, 1, 1), (1000, 16, 16), (4097, 48, 48), (3000, 8, 100), (20000, 49, 17)])
+def test_gram_integer_exact(mode, n, p, q):
+    import paper_1609_01689_gb300 as lob
+    rng = np.random.default_rng(n + p + q)
+    A = rng.integers(-8, 9, (n, p)).astype(np.float64)
+    B = rng.integers(-8, 9, (n, q)).astype(np.float64)
+    G = lob.gram(t(A), t(B), mode).cpu().numpy()
+    assert np.array_equal(G, oracle.gram(A, B))
+
+
+@pytest.mark.parametrize("mode,rel", [("fp64", 4.0 * 2.0 ** -53), ("mixed", 2.0 ** -44)])
+def test_gram_random_bound(mode, rel):
+    """|G - G*| <= c n u |A|^T |B| with c = 4 (FP64) and a double-float unit of 2^-44."""
+    import paper_1609_01689_gb300 as lob
+    rng = np.random.default_rng(1)
+    n = 200_000
+    A = rng.standard_normal((n, 48)); B = rng.standard_normal((n, 48)) * 1e3
+    G = lob.gram(t(A), t(B), mode).cpu().numpy()
+    ref = oracle.gram(A, B)
+    bound = np.abs(A).T @ np.abs(B) * rel * np.sqrt(n) * 4
+    assert np.all(np.abs(G - ref) <= bound)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("n,p,q", [(1, 1, 1), (5000, 48, 16), (4097, 32, 16), (300, 96, 40)])
+def test_lincomb_exact_and_bound(mode, n, p, q):
+    import paper_1609_01689_gb300 as lob
+    rng = np.random.default_rng(n * 3 + p)
+    A = rng.integers(-8, 9, (n, p)).astype(np.float64)
+    C = rng.integers(-8, 9, (p, q)).astype(np.float64)
+    assert np.array_equal(lob.lincomb(t(A), t(C), mode).cpu().numpy(), oracle.lincomb(A, C))
+    A = rng.standard_normal((n, p)); C = rng.standard_normal((p, q))
+    Y = lob.lincomb(t(A), t(C), mode).cpu().numpy()
+    rel = 2 * p * 2.0 ** -53 if mode == "fp64" else 2.0 ** -44 * p
+    assert np.all(np.abs(Y - oracle.lincomb(A, C)) <= rel * (np.abs(A) @ np.abs(C)) + 1e-300)
+
+
+@pytest.mark.parametrize("bp", [1, 32, 64])
+def test_precond_matches_block_solve(bp):
+    """FP32 arithmetic (footnote 5): the FP32 eigendecomposition is backward stable, H~ + E with
+    ||E|| ~ b_p u32 ||H~||, and (H~ + E - mu)^{-1} - (H~ - mu)^{-1} ~ (H~ - mu)^{-1} E (H~ - mu)^{-1},
+    so the relative error is bounded by ~ b_p u32 kappa_j with kappa_j = ||H~|| / min|lambda - mu_j|
+    over the blocks; bound 4 b_p u32 kappa_j."""
+    import paper_1609_01689_gb300 as lob
+    L = synth.layout(3000, 7, 40, 4)
+    r, c, v = synth.generate(L)
+    H = oracle.Coo(L.n, r, c, v)
+    M = lob.Matrix(L.n, r, c, v, precond_block=bp)
+    rng = np.random.default_rng(bp)
+    R = rng.standard_normal((L.n, 8))
+    mu = np.array([-5.0, -3.3, 4.9, 15.1, 24.7, 36.0, 45.2, 200.0])
+    W = M.precond_apply(t(mu), t(R)).cpu().numpy()
+    ref = oracle.block_precond(H, oracle.uniform_bounds(L.n, bp), mu, R)
+    err = np.abs(W - ref).max(axis=0) / np.abs(ref).max(axis=0)
+    bounds = oracle.uniform_bounds(L.n, bp)
+    A = oracle.dense(H)
+    kappa = np.ones(8)
+    for i in range(len(bounds) - 1):
+        lam_b = np.linalg.eigvalsh(A[bounds[i]:bounds[i + 1], bounds[i]:bounds[i + 1]])
+        d = np.abs(lam_b[:, None] - mu[None, :])
+        kappa = np.maximum(kappa, np.abs(lam_b).max() / d.min(axis=0))
+    assert np.all(err <= 4 * bp * 2.0 ** -24 * kappa), (err, kappa)
+
+
+def test_precond_bp1_is_jacobi_formula():
+    import paper_1609_01689_gb300 as lob
+    rng = np.random.default_rng(3)
+    H = random_upper(700, 0.02, rng)
+    H.vals[H.rows == H.cols] += 10.0
+    M = lob.Matrix(H.n, H.rows, H.cols, H.vals, precond_block=1)
+    R = rng.standard_normal((700, 4))
+    mu = np.array([0.5, -1.0, 2.0, 30.0])
+    W = M.precond_apply(t(mu), t(R)).cpu().numpy()
+    dia = np.zeros(700); dia[H.rows[H.rows == H.cols]] = H.vals[H.rows == H.cols]
+    expect = R / (dia[:, None] - mu[None, :])
+    assert np.abs(W - expect).max() <= 1e-6 * np.abs(expect).max()
+
+
+@pytest.mark.parametrize("m", [1, 8, 24, 48, 96])
+def test_rayleigh_ritz_matches_oracle(m):
+    import paper_1609_01689_gb300 as lob
+    rng = np.random.default_rng(m)
+    Y = rng.standard_normal((400, m))
+    A = oracle.dense(random_upper(400, 0.05, rng))
+    G, Mm = Y.T @ A @ Y, Y.T @ Y
+    th, C = lob.rayleigh_ritz(t(G), t(Mm))
+    th, C = th.cpu().numpy(), C.cpu().numpy()
+    th_ref, _ = oracle.rayleigh_ritz(G, Mm)
+    scale = np.abs(th_ref).max()
+    assert np.abs(th - th_ref).max() <= 1e-11 * scale
+    assert np.abs(C.T @ Mm @ C - np.eye(m)).max() <= 1e-10
+    assert np.abs(G @ C - Mm @ C * th).max() <= 1e-10 * np.abs(G).max()
+
+
+def test_rayleigh_ritz_reports_indefinite():
+    import paper_1609_01689_gb300 as lob
+    Mm = np.array([[1.0, 1.0], [1.0, 1.0]])
+    with pytest.raises(np.linalg.LinAlgError):
+        lob.rayleigh_ritz(t(np.eye(2)), t(Mm))

@@ -1,0 +1,89 @@
+"""lob_solve (Algorithm 1) against the oracle's eigenpairs.
+
+Acceptance: eigenvalues within 1e-9 (FP64 path) or 1e-8 (mixed path after refinement) in the
+measure |lambda - lambda*| / max(|lambda*|, 1); residuals ||H x - lambda x|| <= tol ||H||;
+eigenvectors equal to the oracle's up to sign where the eigenvalue is separated."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def c1():
+    L = synth.config_layout("c1")
+    r, c, v = synth.generate(L)
+    H = oracle.Coo(L.n, r, c, v)
+    lam, X, steps, ok = oracle.lanczos(H, 8, 1e-13)
+    assert ok
+    return L, H, lam, X
+
+
+def check(H, L, lam, Xg, lam_ref, X_ref, k, tol_lam, tol_res):
+    nH = oracle.norm_inf(H)
+    rel = np.abs(lam - lam_ref[:k]) / np.maximum(np.abs(lam_ref[:k]), 1.0)
+    assert rel.max() <= tol_lam, rel
+    X = Xg.cpu().numpy()[:, :k]
+    res = oracle.residual_norms(H, X, lam)
+    assert res.max() <= tol_res * nH, res / nH
+    assert np.abs(np.linalg.norm(X, axis=0) - 1).max() < 1e-10
+    gaps = np.diff(lam_ref)
+    for j in range(k):
+        g = min(gaps[j - 1] if j > 0 else np.inf, gaps[j] if j < len(gaps) else np.inf)
+        if g > 1e-3:
+            assert abs(abs(X[:, j] @ X_ref[:, j]) - 1) < 1e-7
+
+
+@pytest.mark.parametrize("precond,guess", [(True, True), (False, True), (True, False), (False, False)])
+def test_solve_fp64_c1(c1, precond, guess):
+    import paper_1609_01689_gb300 as lob
+    L, H, lam_ref, X_ref = c1
+    M = lob.Matrix(L.n, H.rows, H.cols, H.vals, precond_block=32)
+    n_small = int(synth.level_starts(L)[2]) if guess else 0
+    lam, X, st, rc = M.solve(5, 8, 1e-8, mode="fp64", precond=precond, n_small=n_small, max_iter=400)
+    assert rc == lob.LOB_OK
+    check(H, L, lam, X, lam_ref, X_ref, 5, 1e-9, 1e-8)
+
+
+def test_solve_mixed_c1(c1):
+    import paper_1609_01689_gb300 as lob
+    L, H, lam_ref, X_ref = c1
+    M = lob.Matrix(L.n, H.rows, H.cols, H.vals, precond_block=32)
+    n_small = int(synth.level_starts(L)[2])
+    lam, X, st, rc = M.solve(5, 8, 1e-8, mode="mixed", precond=True, n_small=n_small)
+    assert rc == lob.LOB_OK
+    assert st["refine_iterations"] >= 1
+    check(H, L, lam, X, lam_ref, X_ref, 5, 1e-8, 1e-8)
+
+
+def test_solve_paper_shift_rules(c1):
+    import paper_1609_01689_gb300 as lob
+    L, H, lam_ref, X_ref = c1
+    M = lob.Matrix(L.n, H.rows, H.cols, H.vals, precond_block=32)
+    lam, X, st, rc = M.solve(5, 8, 1e-8, mode="fp64", precond=True, n_small=24, precond_shift=1)
+    assert rc == lob.LOB_OK
+    check(H, L, lam, X, lam_ref, X_ref, 5, 1e-9, 1e-8)
+
+
+def test_solve_user_x0_and_iteration_limit(c1):
+    import paper_1609_01689_gb300 as lob
+    L, H, lam_ref, X_ref = c1
+    M = lob.Matrix(L.n, H.rows, H.cols, H.vals)
+    X0 = np.zeros((L.n, 8)); X0[:, :8] = X_ref  # the answer itself: converges at once
+    lam, X, st, rc = M.solve(5, 8, 1e-8, X0=X0)
+    assert rc == lob.LOB_OK and st["iterations"] <= 2
+    lam2, X2, st2, rc2 = M.solve(5, 8, 1e-12, max_iter=2, n_small=0)
+    assert rc2 == lob.LOB_ERR_NOCONV
+
+
+def test_solve_rejects_bad_args(c1):
+    import paper_1609_01689_gb300 as lob
+    L, H, _, _ = c1
+    M = lob.Matrix(L.n, H.rows, H.cols, H.vals)
+    with pytest.raises(lob.LobError):
+        M.solve(9, 8, 1e-8)  # k > nb
+    with pytest.raises(lob.LobError):
+        M.solve(5, 8, 1e-8, precond=True)  # no preconditioner built

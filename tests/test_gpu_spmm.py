@@ -1,0 +1,99 @@
+"""Symmetric SpMM Y = H X (Section 4.1) against the oracle, in FP64 and in the mixed
+arithmetic (FP32 values and products, FP64 sums across tiles; footnote 5 of Section 4.4).
+
+Bounds: FP64 -- |Y - Y*| <= 2 (m + 2) u64 (|H||X|) per entry, m = nonzeros in the row.
+        MIXED -- X and values rounded to FP32 (2 u32 each), FP32 products and in-tile sums
+        (m u32): |Y - Y*| <= 2 (m + 4) u32 (|H||X|)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import abs_coo, random_upper, row_counts
+
+pytestmark = pytest.mark.gpu
+U64 = 2.0 ** -53
+U32 = 2.0 ** -24
+
+
+def run(M, X, mode):
+    import torch
+    return M.spmm(torch.from_numpy(np.ascontiguousarray(X)).cuda(), mode).cpu().numpy()
+
+
+@pytest.mark.parametrize("nb", [1, 3, 8, 16, 17, 64])
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_spmm_integer_exact(nb, mode):
+    """Small integers: every product and partial sum is exact in both arithmetics."""
+    import paper_1609_01689_gb300 as lob
+    rng = np.random.default_rng(nb + 100 * (mode == "mixed"))
+    H = random_upper(700, 0.05, rng, integer=True)
+    X = rng.integers(-8, 9, (700, nb)).astype(np.float64)
+    M = lob.Matrix(H.n, H.rows, H.cols, H.vals)
+    assert np.array_equal(run(M, X, mode), oracle.spmm(H, X))
+
+
+@pytest.mark.parametrize("n,nb", [(1, 1), (255, 4), (256, 8), (257, 16), (3000, 16), (5000, 2)])
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_spmm_random_within_bound(n, nb, mode):
+    import paper_1609_01689_gb300 as lob
+    rng = np.random.default_rng(n * 7 + nb)
+    H = random_upper(n, min(0.05, 40.0 / n), rng)
+    X = rng.standard_normal((n, nb))
+    M = lob.Matrix(H.n, H.rows, H.cols, H.vals)
+    Y = run(M, X, mode)
+    Yref = oracle.spmm(H, X)
+    bound_base = oracle.spmm(abs_coo(H), np.abs(X))
+    m = row_counts(H)[:, None]
+    bound = (2 * (m + 2) * U64 if mode == "fp64" else 2 * (m + 4) * U32) * bound_base + 1e-300
+    assert np.all(np.abs(Y - Yref) <= bound)
+
+
+def test_spmm_unit_vectors_and_symmetry():
+    import paper_1609_01689_gb300 as lob
+    rng = np.random.default_rng(5)
+    H = random_upper(600, 0.03, rng)
+    M = lob.Matrix(H.n, H.rows, H.cols, H.vals)
+    cols = [0, 255, 256, 599]
+    E = np.zeros((600, len(cols)))
+    E[cols, range(len(cols))] = 1.0
+    A = oracle.dense(H)
+    assert np.array_equal(run(M, E, "fp64"), A[:, cols])
+    X = rng.standard_normal((600, 4)); Z = rng.standard_normal((600, 4))
+    lhs = X.T @ run(M, Z, "fp64"); rhs = run(M, X, "fp64").T @ Z
+    assert np.abs(lhs - rhs).max() <= 1e-12 * np.abs(lhs).max()
+
+
+def test_spmm_diagonal_only_and_single_entry():
+    import paper_1609_01689_gb300 as lob
+    d = np.arange(1.0, 301.0)
+    M = lob.Matrix(300, np.arange(300), np.arange(300), d)
+    X = np.ones((300, 2))
+    assert np.array_equal(run(M, X, "fp64"), d[:, None] * X)
+    M1 = lob.Matrix(600, np.array([10]), np.array([590]), np.array([2.5]))
+    Y = run(M1, np.ones((600, 1)), "fp64")
+    expect = np.zeros((600, 1)); expect[10] = 2.5; expect[590] = 2.5
+    assert np.array_equal(Y, expect)
+
+
+@pytest.fixture(scope="module")
+def c2():
+    L = synth.config_layout("c2")
+    r, c, v = synth.generate(L)
+    return L, oracle.Coo(L.n, r, c, v)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_spmm_full_size_500k(c2, mode):
+    """The n = 500,000, nb = 16 workload in the launch configuration the benchmark times."""
+    import paper_1609_01689_gb300 as lob
+    L, H = c2
+    M = lob.Matrix(H.n, H.rows, H.cols, H.vals)
+    rng = np.random.default_rng(16)
+    X = rng.standard_normal((H.n, 16))
+    Y = run(M, X, mode)
+    Yref = oracle.spmm(H, X)
+    bound_base = oracle.spmm(abs_coo(H), np.abs(X))
+    m = row_counts(H)[:, None]
+    bound = (2 * (m + 2) * U64 if mode == "fp64" else 2 * (m + 4) * U32) * bound_base
+    assert np.all(np.abs(Y - Yref) <= bound)
