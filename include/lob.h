@@ -89,6 +89,13 @@ int lob_matrix_info_get(const lob_matrix* m, lob_matrix_info* out);
 int lob_export_tiles(const lob_matrix* m, int64_t* tile_rowptr, int32_t* tile_col, int64_t* tile_ptr, uint32_t* rc,
                      double* v64, float* v32);
 
+/* Copy the kernel-private column-order permutation to a host uint16 array of nnz entries.
+ * The SpMM walks each tile in chunks of 4096 entries (the last chunk of a tile may be shorter);
+ * for the chunk starting at entry b, perm[b + j] is the chunk-local index of the j-th entry of
+ * the chunk in (column, row) order. Derived from the canonical store at create time; exposed
+ * so tests can check it against the canonical order. */
+int lob_export_perm(const lob_matrix* m, uint16_t* perm);
+
 /* Arithmetic of a product (Section 4.4, footnote 5 sets the paper's pattern). */
 #define LOB_SPMM_FP64 0  /* FP64 values, FP64 X, FP64 products and sums (plain FP64) */
 #define LOB_SPMM_MIXED 1 /* FP32 values, X rounded to FP32, FP32 products and in-tile sums,

@@ -87,6 +87,7 @@ def _load():
     L.lob_destroy.argtypes = [_P]
     L.lob_matrix_info_get.argtypes = [_P, ctypes.POINTER(MatrixInfo)]
     L.lob_export_tiles.argtypes = [_P, _P, _P, _P, _P, _P, _P]
+    L.lob_export_perm.argtypes = [_P, _P]
     L.lob_spmm.argtypes = [_P, _I32, _P, _P, _I32, _P]
     L.lob_gram.argtypes = [_I64, _I32, _P, _I32, _I32, _P, _I32, _P, _I32, _P]
     L.lob_lincomb.argtypes = [_I64, _I32, _P, _I32, _I32, _P, _P, _I32, _I32, _P]
@@ -97,7 +98,8 @@ def _load():
     L.lob_kernel_launches.restype = ctypes.c_longlong
     L.lob_strerror.argtypes = [ctypes.c_int]
     L.lob_strerror.restype = ctypes.c_char_p
-    for f in ("lob_create", "lob_destroy", "lob_matrix_info_get", "lob_export_tiles", "lob_spmm", "lob_gram",
+    for f in ("lob_create", "lob_destroy", "lob_matrix_info_get", "lob_export_tiles", "lob_export_perm", "lob_spmm",
+              "lob_gram",
               "lob_lincomb", "lob_precond_apply", "lob_rayleigh_ritz", "lob_solve"):
         getattr(L, f).restype = ctypes.c_int
     return L
@@ -211,6 +213,12 @@ class Matrix:
                                       v64.ctypes.data if v64 is not None else None,
                                       v32.ctypes.data if v32 is not None else None), "lob_export_tiles")
         return dict(tile_rowptr=rp, tile_col=tc, tile_ptr=tp, rc=rc, v64=v64, v32=v32, ntiles=ntl)
+
+    def export_perm(self):
+        """The kernel-private column-order permutation (lob_export_perm)."""
+        perm = np.empty(self.info()["nnz"], np.uint16)
+        _check(lib().lob_export_perm(self._h, perm.ctypes.data), "lob_export_perm")
+        return perm
 
     def spmm(self, X, mode="fp64", out=None):
         X = _dev_f64(X)

@@ -72,6 +72,7 @@ int lob_create(const lob_coo* H, const lob_create_opts* opts, lob_matrix** out) 
 
 int lob_destroy(lob_matrix* m) {
   if (!m) return LOB_OK;
+  cudaFree(m->xs);
   lob_free_tiles(&m->T);
   lob_free_precond(&m->P);
   delete m;
@@ -101,6 +102,12 @@ int lob_export_tiles(const lob_matrix* m, int64_t* tile_rowptr, int32_t* tile_co
   if (rc) LOB_CUDA(cudaMemcpy(rc, T.rc, T.nnz * 4, cudaMemcpyDeviceToHost));
   if (v64) LOB_CUDA(cudaMemcpy(v64, T.v64, T.nnz * 8, cudaMemcpyDeviceToHost));
   if (v32) LOB_CUDA(cudaMemcpy(v32, T.v32, T.nnz * 4, cudaMemcpyDeviceToHost));
+  return LOB_OK;
+}
+
+int lob_export_perm(const lob_matrix* m, uint16_t* perm) {
+  if (!m || !perm || !m->T.cperm) return LOB_ERR_ARG;
+  LOB_CUDA(cudaMemcpy(perm, m->T.cperm, m->T.nnz * 2, cudaMemcpyDeviceToHost));
   return LOB_OK;
 }
 

@@ -11,6 +11,7 @@
 
 #define LOB_TILE 256
 #define LOB_TILE_LOG 8
+#define LOB_PERM_CHUNK 4096  // entries per SpMM chunk (column-order permutation granularity)
 
 // Report a failed CUDA call and return LOB_ERR_CUDA from the enclosing function.
 #define LOB_CUDA(call)                                                                          \
@@ -43,6 +44,12 @@ struct lob_tiles {
   uint32_t* rc = nullptr;      // [nnz] (r << 16) | c
   double* v64 = nullptr;       // [nnz] FP64 values (may be null)
   float* v32 = nullptr;        // [nnz] FP32 values (may be null)
+  uint16_t* cperm = nullptr;   // [nnz] kernel-private: per chunk of LOB_PERM_CHUNK entries of a tile,
+                               // the chunk-local indices of its entries in (c, r) order
+  int64_t nchunks = 0;
+  int32_t* tchunk = nullptr;   // [ntiles+1] first chunk id of each tile
+  uint16_t* cptrs = nullptr;   // [nchunks][2][257] kernel-private: start of each in-tile row in the
+                               // chunk's (r, c) order, then of each in-tile column in (c, r) order
 };
 
 // Block-diagonal preconditioner of eq. 11: per block i (rows [i*bp, i*bp + m_i)),
@@ -62,6 +69,8 @@ struct lob_matrix {
   int32_t values = LOB_VALUES_BOTH;
   double norm_inf = 0.0;
   int device = 0;
+  void* xs = nullptr;      // SpMM scratch: X rounded/staged per call (rows padded to whole tiles)
+  size_t xs_bytes = 0;
 };
 
 // ---- internal launchers (return LOB_OK or an error code) ----

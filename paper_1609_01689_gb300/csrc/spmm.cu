@@ -2,104 +2,331 @@
 //
 // Every stored tile T_IJ contributes Y_I += T_IJ X_J and, off the diagonal tile, also
 // Y_J += T_IJ^T X_I -- the paper's row pass and column pass over the CSB pointer array,
-// here fused into a single pass over the tiles so the matrix streams from HBM once. On a
-// diagonal tile the entries with r != c are applied both ways and the diagonal once.
+// fused here into a single pass so each tile streams from HBM once. On a diagonal tile the
+// entries with r != c are applied both ways and the diagonal once.
 //
-// One CTA per tile. The two 256-row slices of X the tile touches are staged in shared
-// memory, the tile's entries stream from global memory with one group of NBC lanes per
-// entry (one lane per vector column), and both products accumulate into shared-memory
-// partials which are flushed to Y with one global atomic per touched (row, column).
+// Schedule: one CTA per tile row I. X_I (256 rows) stays in shared memory for the whole row;
+// the row's tiles are streamed in chunks of up to 4096 entries -- the records, the chunk's
+// column-order permutation, the chunk's row and column start pointers (both derived once at
+// create time from the canonical store), and X_J for a new tile -- with cp.async, the next
+// chunk loading while the current one computes. A lane group of NB/VW lanes (VW elements =
+// 16 bytes, one 16-byte slice of a row of X per lane) owns in-tile row a and column a for all
+// tiles of the row:
+//   row pass    Y_I[a] += sum_c v X_J[c] over row a's entries, summed in registers;
+//   column pass Y_J[a] += sum_r v X_I[r] over column a's entries (via the permutation).
+// No shared-memory accumulators and no shared-memory atomics (FP32 ones are emulated on this
+// GPU). Column partials go to Y with FP64 atomics in L2 after each tile; row partials are
+// summed across the row's tiles in registers and written once per tile row, so every sum
+// across tiles is done in FP64 (or double-float) and the order of all sums is fixed.
 //
-// MIXED: FP32 values, X rounded to FP32, FP32 products and in-tile sums; the tile partials
-// are converted to FP64 and summed across tiles in FP64 (footnote 5 of Section 4.4).
-// FP64: every operation in FP64.
+// MIXED: FP32 values, X rounded to FP32 (once per call), FP32 products and in-tile sums; the
+// row side's tile partials are summed across the tiles of the row in double-float, and all
+// cross-tile sums in Y are FP64 (footnote 5 of Section 4.4). FP64: every operation in FP64.
 #include "common.cuh"
+#include "df.cuh"
 
 namespace {
 
-template <typename S>
-__device__ __forceinline__ void smem_add(S* p, S v) { atomicAdd(p, v); }
+template <bool MIXED>
+struct Elt;
+template <>
+struct Elt<true> {
+  using T = float;
+  using V = float4;  // 16-byte slice: 4 vector columns
+  static constexpr int VW = 4;
+};
+template <>
+struct Elt<false> {
+  using T = double;
+  using V = double2;
+  static constexpr int VW = 2;
+};
 
-template <bool MIXED, int NBC>
-__global__ void __launch_bounds__(256) k_spmm_tile(const int32_t* __restrict__ trow, const int32_t* __restrict__ tcol,
-                                                   const int64_t* __restrict__ tptr, const uint32_t* __restrict__ rc,
-                                                   const double* __restrict__ v64, const float* __restrict__ v32,
-                                                   const double* __restrict__ X, double* __restrict__ Y, int nb,
-                                                   int64_t n_act) {
-  using S = typename std::conditional<MIXED, float, double>::type;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* XI = reinterpret_cast<S*>(smem_raw);
-  S* XJ = XI + LOB_TILE * NBC;
-  S* YI = XJ + LOB_TILE * NBC;
-  S* YJ = YI + LOB_TILE * NBC;
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
-  const int t = blockIdx.x;
-  const int64_t I = trow[t], J = tcol[t];
-  if (J * LOB_TILE >= n_act) return;  // tile entirely outside the active leading block
-  const int64_t p0 = tptr[t], p1 = tptr[t + 1];
-  const bool diag = (I == J);
+__device__ __forceinline__ void fma_v(float4& a, float v, const float4& x) {
+  a.x = fmaf(v, x.x, a.x); a.y = fmaf(v, x.y, a.y); a.z = fmaf(v, x.z, a.z); a.w = fmaf(v, x.w, a.w);
+}
+__device__ __forceinline__ void fma_v(double2& a, double v, const double2& x) {
+  a.x = fma(v, x.x, a.x); a.y = fma(v, x.y, a.y);
+}
+__device__ __forceinline__ void zero_v(float4& a) { a = make_float4(0.f, 0.f, 0.f, 0.f); }
+__device__ __forceinline__ void zero_v(double2& a) { a = make_double2(0.0, 0.0); }
+__device__ __forceinline__ void mul_v(float4& a, float v, const float4& x) {
+  a.x = v * x.x; a.y = v * x.y; a.z = v * x.z; a.w = v * x.w;
+}
+__device__ __forceinline__ void mul_v(double2& a, double v, const double2& x) { a.x = v * x.x; a.y = v * x.y; }
+
+// FP64 -> FP32 round-to-nearest-even with integer operations (normal FP32 range; other
+// magnitudes take the conversion instruction).
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e < 897 || e > 1149) return __double2float_rn(x);
+  const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned long long r = mag + 0x0FFFFFFFull + ((mag >> 29) & 1ull);  // ties to even at bit 29
+  const unsigned bits = (unsigned)(r >> 29) - (896u << 23);
+  return __uint_as_float(bits | ((unsigned)(b >> 32) & 0x80000000u));
+}
+
+// Columns [c0, c0 + w) of X (n x nb FP64) -> Xs (rows x NB, element type T); zero in padded
+// columns and in rows >= n_act.
+template <typename T>
+__global__ void k_stage_x(int64_t rows, int64_t n_act, int nb, int c0, int w, int NB, const double* __restrict__ X,
+                          T* __restrict__ Xs) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * NB) return;
+  const int64_t i = t / NB;
+  const int j = (int)(t % NB);
+  const double v = (j < w && i < n_act) ? X[i * nb + c0 + j] : 0.0;
+  if constexpr (sizeof(T) == 4)
+    Xs[t] = f64_to_f32_rn(v);
+  else
+    Xs[t] = v;
+}
+
+// Launch shape and shared-memory layout (byte offsets) of the SpMM kernel. A lane group of
+// G = NB / VW lanes handles one entry at a time; the CTA has NG = THREADS / G groups and group g
+// owns the in-tile rows and columns g, g + NG, ... (RPG of each) for every tile of its tile row.
+template <bool MIXED, int NB>
+struct Cfg {
+  using T = typename Elt<MIXED>::T;
+  static constexpr int VW = Elt<MIXED>::VW;
+  static constexpr int G = NB / VW;
+  static constexpr int THREADS = (LOB_TILE * G) < 1024 ? (LOB_TILE * G) : 1024;
+  static constexpr int NG = THREADS / G;
+  static constexpr int RPG = LOB_TILE / NG;
+  static constexpr int CH = LOB_PERM_CHUNK;
+  static constexpr int PTRS = 2 * (LOB_TILE + 1);  // row starts then column starts, uint16
+  static constexpr size_t XV = sizeof(T) * LOB_TILE * NB;
+  static constexpr size_t XI = 0;
+  static constexpr size_t XJ = XI + XV;               // 2 buffers
+  static constexpr size_t RC = XJ + 2 * XV;           // 2 x CH uint32
+  static constexpr size_t VV = RC + 2 * 4 * CH;       // 2 x CH values
+  static constexpr size_t PM = VV + 2 * sizeof(T) * CH;    // 2 x (CH + 8) uint16
+  static constexpr size_t PT = PM + 2 * 2 * (CH + 8);      // 2 x PTRS uint16
+  static constexpr size_t BYTES = PT + 2 * 2 * PTRS;
+};
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+
+__device__ __forceinline__ void atomic_out(double* y, float v) { if (v != 0.f) atomicAdd(y, f32_to_f64(v)); }
+__device__ __forceinline__ void atomic_out(double* y, double v) { if (v != 0.0) atomicAdd(y, v); }
+
+// One CTA per tile row I (see the file comment). Group g, for each owned in-tile index a:
+//   row pass    acc_t[a] += v X_J[c] over the entries of row a (chunk order (r, c)), FP32 in MIXED;
+//               at tile end acc_t is added to the row accumulator (double-float in MIXED);
+//   column pass acc_c[a] += v X_I[r] over the entries of column a (order (c, r)); at tile end
+//               it goes to Y_J with FP64 atomics, or, on the diagonal tile, into the row
+//               accumulator (row a and column a have the same owner).
+// Nothing is accumulated in shared memory and no shared-memory atomics are used.
+template <bool MIXED, int NB>
+__global__ void __launch_bounds__(Cfg<MIXED, NB>::THREADS, 1)
+    k_spmm4(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ tcol, const int64_t* __restrict__ tptr,
+            const int32_t* __restrict__ tchunk, const uint32_t* __restrict__ rc,
+            const typename Elt<MIXED>::T* __restrict__ vals, const uint16_t* __restrict__ cperm,
+            const uint16_t* __restrict__ cptrs, const typename Elt<MIXED>::T* __restrict__ Xs,
+            double* __restrict__ Y, int ldy, int c0, int w, int64_t n_act) {
+  using C = Cfg<MIXED, NB>;
+  using T = typename C::T;
+  using V = typename Elt<MIXED>::V;
+  constexpr int VW = C::VW, G = C::G, NG = C::NG, RPG = C::RPG, CH = C::CH, THREADS = C::THREADS;
+  constexpr int XN = LOB_TILE * NB;
+  constexpr int EPT = 16 / (int)sizeof(T);  // elements per 16-byte copy
+  extern __shared__ __align__(16) unsigned char sm[];
+  T* XI = reinterpret_cast<T*>(sm + C::XI);
+  T* XJb = reinterpret_cast<T*>(sm + C::XJ);
+  uint32_t* RCb = reinterpret_cast<uint32_t*>(sm + C::RC);
+  T* VVb = reinterpret_cast<T*>(sm + C::VV);
+  uint16_t* PMb = reinterpret_cast<uint16_t*>(sm + C::PM);
+  uint16_t* PTb = reinterpret_cast<uint16_t*>(sm + C::PT);
+
+  const int64_t I = blockIdx.x;
+  const int64_t row0 = I * LOB_TILE;
   const int tid = threadIdx.x;
-  const int lane_k = tid % NBC;  // vector column handled by this lane
-  const int group = tid / NBC;
-  constexpr int GROUPS = 256 / NBC;
+  const int g = tid / G, gl = tid % G;
+  const int64_t t0 = rowptr[I];
+  int64_t t1 = rowptr[I + 1];
+  while (t1 > t0 && (int64_t)tcol[t1 - 1] * LOB_TILE >= n_act) t1--;  // tiles outside the active block
 
-  for (int c0 = 0; c0 < nb; c0 += NBC) {
-    const int w = (nb - c0) < NBC ? (nb - c0) : NBC;
-    for (int idx = tid; idx < LOB_TILE * NBC; idx += 256) {
-      const int r = idx / NBC, k = idx % NBC;
-      const int64_t gj = J * LOB_TILE + r, gi = I * LOB_TILE + r;
-      double xj = (k < w && gj < n_act) ? X[gj * nb + c0 + k] : 0.0;
-      XJ[idx] = (S)xj;
-      if (!diag) {
-        double xi = (k < w && gi < n_act) ? X[gi * nb + c0 + k] : 0.0;
-        XI[idx] = (S)xi;
-      }
-      YI[idx] = (S)0;
-      YJ[idx] = (S)0;
+  for (int e = tid * EPT; e < XN; e += THREADS * EPT) cp_async16(&XI[e], &Xs[row0 * NB + e]);
+  cp_async_commit();
+
+  auto issue = [&](int64_t t, int64_t k, int buf, int xbuf) {
+    const int64_t J = tcol[t];
+    if (k == 0 && J != I) {
+      T* XJ = XJb + xbuf * XN;
+      const T* src = Xs + J * LOB_TILE * NB;
+      for (int e = tid * EPT; e < XN; e += THREADS * EPT) cp_async16(&XJ[e], &src[e]);
     }
+    const int64_t base = tptr[t] + k * CH;
+    const int64_t rem = tptr[t + 1] - base;
+    const int cnt = (int)(rem < CH ? rem : CH);
+    uint32_t* RCs = RCb + buf * CH;
+    T* VVs = VVb + buf * CH;
+    for (int i = tid; i < cnt; i += THREADS) {
+      cp_async4(&RCs[i], &rc[base + i]);
+      if (MIXED) cp_async4(&VVs[i], &vals[base + i]); else cp_async8(&VVs[i], &vals[base + i]);
+    }
+    uint32_t* PM32 = reinterpret_cast<uint32_t*>(PMb + buf * (CH + 8));
+    const int64_t wb = base & ~(int64_t)1;
+    const int nwords = (int)((base + cnt - wb + 1) / 2);
+    const uint32_t* src32 = reinterpret_cast<const uint32_t*>(cperm + wb);
+    for (int i = tid; i < nwords; i += THREADS) cp_async4(&PM32[i], &src32[i]);
+    uint32_t* PT32 = reinterpret_cast<uint32_t*>(PTb + buf * C::PTRS);
+    const uint32_t* srcp = reinterpret_cast<const uint32_t*>(cptrs + (int64_t)(tchunk[t] + k) * C::PTRS);
+    for (int i = tid; i < C::PTRS / 2; i += THREADS) cp_async4(&PT32[i], &srcp[i]);
+    cp_async_commit();
+  };
+
+  // accumulators of the owned rows/columns
+  V acc_t[RPG], acc_c[RPG];
+  float rh[RPG][VW], rl[RPG][VW];  // MIXED: row accumulator (double-float)
+  double rd[RPG][VW];              // FP64: row accumulator
+#pragma unroll
+  for (int a = 0; a < RPG; a++) {
+    zero_v(acc_t[a]); zero_v(acc_c[a]);
+#pragma unroll
+    for (int q = 0; q < VW; q++) { rh[a][q] = 0.f; rl[a][q] = 0.f; rd[a][q] = 0.0; }
+  }
+
+  int64_t t = t0, k = 0;
+  int tl = 0, buf = 0;
+  if (t < t1) issue(t, 0, 0, 0);
+  while (t < t1) {
+    const int64_t J = tcol[t];
+    const bool diag = (J == I);
+    const bool last = (tptr[t] + (k + 1) * CH >= tptr[t + 1]);
+    int64_t tn = t, kn = k + 1;
+    int tln = tl;
+    if (last) { tn = t + 1; kn = 0; tln = tl + 1; }
+    if (tn < t1) { issue(tn, kn, buf ^ 1, tln & 1); cp_async_wait_1(); } else { cp_async_wait_all(); }
     __syncthreads();
-    const S* xi_src = diag ? XJ : XI;
-    if (lane_k < w) {
-      for (int64_t e = p0 + group; e < p1; e += GROUPS) {
-        const uint32_t p = rc[e];
-        const int r = (int)(p >> 16), c = (int)(p & 0xFFFFu);
-        if (I * LOB_TILE + r >= n_act || J * LOB_TILE + c >= n_act) continue;
-        const S v = MIXED ? (S)v32[e] : (S)v64[e];
-        smem_add(&YI[r * NBC + lane_k], v * XJ[c * NBC + lane_k]);
-        if (!diag || r != c) smem_add(&YJ[c * NBC + lane_k], v * xi_src[r * NBC + lane_k]);
+    const uint32_t* RCs = RCb + buf * CH;
+    const T* VVs = VVb + buf * CH;
+    const uint16_t* PM = PMb + buf * (CH + 8) + (int)((tptr[t] + k * CH) & 1);
+    const uint16_t* PR = PTb + buf * C::PTRS;
+    const uint16_t* PC = PR + (LOB_TILE + 1);
+    const T* xj = diag ? XI : XJb + (tl & 1) * XN;
+#pragma unroll
+    for (int a = 0; a < RPG; a++) {
+      const int idx = g + a * NG;
+      // row pass
+      {
+        const int s = PR[idx], e = PR[idx + 1];
+        V acc = acc_t[a];
+#pragma unroll 4
+        for (int i = s; i < e; i++) {
+          const int c = (int)(RCs[i] & 0xFFFFu);
+          const V x = *reinterpret_cast<const V*>(&xj[c * NB + gl * VW]);
+          fma_v(acc, VVs[i], x);
+        }
+        acc_t[a] = acc;
+      }
+      // column pass
+      {
+        const int s = PC[idx], e = PC[idx + 1];
+        V acc = acc_c[a];
+#pragma unroll 4
+        for (int i = s; i < e; i++) {
+          const int q = PM[i] & (CH - 1);  // a chunk-local index (mask keeps a stray value inside the chunk)
+          const int r = (int)(RCs[q] >> 16);
+          if (diag && r == idx) continue;  // the diagonal entry is applied once (row pass)
+          const V xi = *reinterpret_cast<const V*>(&XI[r * NB + gl * VW]);
+          fma_v(acc, VVs[q], xi);
+        }
+        acc_c[a] = acc;
       }
     }
-    __syncthreads();
-    for (int idx = tid; idx < LOB_TILE * NBC; idx += 256) {
-      const int r = idx / NBC, k = idx % NBC;
-      if (k >= w) continue;
-      if (diag) {
-        const int64_t g = I * LOB_TILE + r;
-        const double s = (double)YI[idx] + (double)YJ[idx];
-        if (g < n_act && s != 0.0) atomicAdd(&Y[g * nb + c0 + k], s);
+    if (last) {
+#pragma unroll
+      for (int a = 0; a < RPG; a++) {
+        const int idx = g + a * NG;
+        const T* ta = reinterpret_cast<const T*>(&acc_t[a]);
+        const T* ca = reinterpret_cast<const T*>(&acc_c[a]);
+#pragma unroll
+        for (int q = 0; q < VW; q++) {
+          if (MIXED) {
+            df_add(rh[a][q], rl[a][q], (float)ta[q], 0.f);
+            if (diag) df_add(rh[a][q], rl[a][q], (float)ca[q], 0.f);
+          } else {
+            rd[a][q] += (double)ta[q];
+            if (diag) rd[a][q] += (double)ca[q];
+          }
+          const int kk = gl * VW + q;
+          const int64_t gr = J * LOB_TILE + idx;
+          if (!diag && kk < w && gr < n_act) atomic_out(&Y[gr * ldy + c0 + kk], ca[q]);
+        }
+        zero_v(acc_t[a]);
+        zero_v(acc_c[a]);
+      }
+    }
+    __syncthreads();  // this buffer is refilled two chunks from now
+    t = tn; k = kn; tl = tln; buf ^= 1;
+  }
+  cp_async_wait_all();
+#pragma unroll
+  for (int a = 0; a < RPG; a++) {
+    const int64_t gr = row0 + g + a * NG;
+#pragma unroll
+    for (int q = 0; q < VW; q++) {
+      const int kk = gl * VW + q;
+      if (kk >= w || gr >= n_act) continue;
+      if (MIXED) {
+        if (rh[a][q] != 0.f) atomicAdd(&Y[gr * ldy + c0 + kk], f32_to_f64(rh[a][q]));
+        if (rl[a][q] != 0.f) atomicAdd(&Y[gr * ldy + c0 + kk], f32_to_f64(rl[a][q]));
       } else {
-        const int64_t gi = I * LOB_TILE + r, gj = J * LOB_TILE + r;
-        const double si = (double)YI[idx], sj = (double)YJ[idx];
-        if (gi < n_act && si != 0.0) atomicAdd(&Y[gi * nb + c0 + k], si);
-        if (gj < n_act && sj != 0.0) atomicAdd(&Y[gj * nb + c0 + k], sj);
+        if (rd[a][q] != 0.0) atomicAdd(&Y[gr * ldy + c0 + kk], rd[a][q]);
       }
     }
-    __syncthreads();
   }
 }
 
-template <bool MIXED, int NBC>
+template <bool MIXED, int NB>
 int launch(const lob_matrix* m, const double* X, double* Y, int nb, int64_t n_act, cudaStream_t st) {
-  using S = typename std::conditional<MIXED, float, double>::type;
-  const size_t smem = 4ull * LOB_TILE * NBC * sizeof(S);
-  auto kern = k_spmm_tile<MIXED, NBC>;
-  LOB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const lob_tiles& T = m->T;
-  // tiles of the tile rows that intersect the active leading block
+  using C = Cfg<MIXED, NB>;
+  using T = typename Elt<MIXED>::T;
+  static_assert(C::BYTES <= 227 * 1024, "shared memory budget");
+  const lob_tiles& TS = m->T;
   const int64_t nt_act = (n_act + LOB_TILE - 1) / LOB_TILE;
-  const int64_t ntl = m->h_rowptr[nt_act];
-  if (ntl > 0)
-    (kern<<<(unsigned)ntl, 256, smem, st>>>(T.trow, T.tcol, T.tptr, T.rc, T.v64, T.v32, X, Y, nb, n_act), LOB_LAUNCHED());
+  if (nt_act == 0) return LOB_OK;
+  // staged X: rows padded to whole tiles, NB columns (scratch owned by the matrix)
+  const int64_t rows_pad = TS.nt * LOB_TILE;
+  const size_t need = (size_t)rows_pad * NB * sizeof(T);
+  lob_matrix* mm = const_cast<lob_matrix*>(m);
+  if (mm->xs_bytes < need) {
+    cudaFree(mm->xs);
+    mm->xs = nullptr;
+    mm->xs_bytes = 0;
+    if (cudaMalloc(&mm->xs, need) != cudaSuccess) { cudaGetLastError(); return LOB_ERR_NOMEM; }
+    mm->xs_bytes = need;
+  }
+  T* Xs = reinterpret_cast<T*>(mm->xs);
+  auto kern = k_spmm4<MIXED, NB>;
+  LOB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES));
+  for (int c0 = 0; c0 < nb; c0 += NB) {
+    const int w = (nb - c0) < NB ? (nb - c0) : NB;
+    (k_stage_x<T><<<(unsigned)((rows_pad * NB + 255) / 256), 256, 0, st>>>(rows_pad, n_act, nb, c0, w, NB, X, Xs),
+     LOB_LAUNCHED());
+    (kern<<<(unsigned)nt_act, C::THREADS, C::BYTES, st>>>(
+         TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rc,
+         MIXED ? (const T*)(const void*)TS.v32 : (const T*)(const void*)TS.v64, TS.cperm, TS.cptrs, Xs, Y, nb, c0, w,
+         n_act),
+     LOB_LAUNCHED());
+  }
   LOB_CUDA(cudaGetLastError());
   return LOB_OK;
 }
@@ -113,6 +340,13 @@ int lob_spmm_launch(const lob_matrix* m, int mode, const double* X, double* Y, i
   if (mode == LOB_SPMM_FP64 && !m->T.v64) return LOB_ERR_ARG;
   if (mode != LOB_SPMM_MIXED && mode != LOB_SPMM_FP64) return LOB_ERR_ARG;
   LOB_CUDA(cudaMemsetAsync(Y, 0, (size_t)m->T.n * nb * sizeof(double), st));
-  if (mode == LOB_SPMM_MIXED) return nb <= 8 ? launch<true, 8>(m, X, Y, nb, n_act, st) : launch<true, 16>(m, X, Y, nb, n_act, st);
-  return nb <= 8 ? launch<false, 8>(m, X, Y, nb, n_act, st) : launch<false, 16>(m, X, Y, nb, n_act, st);
+  if (mode == LOB_SPMM_MIXED) {
+    if (nb <= 4) return launch<true, 4>(m, X, Y, nb, n_act, st);
+    if (nb <= 8) return launch<true, 8>(m, X, Y, nb, n_act, st);
+    return launch<true, 16>(m, X, Y, nb, n_act, st);
+  }
+  if (nb <= 2) return launch<false, 2>(m, X, Y, nb, n_act, st);
+  if (nb <= 4) return launch<false, 4>(m, X, Y, nb, n_act, st);
+  if (nb <= 8) return launch<false, 8>(m, X, Y, nb, n_act, st);
+  return launch<false, 16>(m, X, Y, nb, n_act, st);
 }

@@ -92,6 +92,64 @@ __global__ void k_rowptr(int64_t nt, int64_t ntiles, const int32_t* __restrict__
   if (r == 0) tptr[ntiles] = nnz;
 }
 
+// Key of entry k for the column-order permutation of its chunk: chunks are CH consecutive
+// entries of a tile, starting at the tile's first entry; within a chunk, order by (c, r).
+__global__ void k_perm_keys(int64_t nnz, const int32_t* __restrict__ flag, const int32_t* __restrict__ tid,
+                            const int64_t* __restrict__ tptr, const uint32_t* __restrict__ rc,
+                            uint64_t* __restrict__ keys, uint16_t* __restrict__ vals) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nnz) return;
+  const int64_t t0 = tptr[tid[k] + flag[k] - 1];  // tile of entry k (tid is the exclusive count of tile starts)
+  const int64_t base = t0 + ((k - t0) / LOB_PERM_CHUNK) * LOB_PERM_CHUNK;
+  const uint32_t p = rc[k];
+  const uint64_t c = p & 0xFFFFu, r = p >> 16;
+  keys[k] = ((uint64_t)base << 16) | (c << 8) | r;
+  vals[k] = (uint16_t)(k - base);
+}
+
+// Number of SpMM chunks of each tile and the first chunk id of every tile.
+__global__ void k_chunk_counts(int64_t ntiles, const int64_t* __restrict__ tptr, int32_t* __restrict__ cnt) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  cnt[t] = (int32_t)((tptr[t + 1] - tptr[t] + LOB_PERM_CHUNK - 1) / LOB_PERM_CHUNK);
+}
+
+// One CTA per chunk: where each in-tile row starts in the chunk's (r, c) order and where each
+// in-tile column starts in its (c, r) order (exclusive prefix sums of the row and column counts).
+__global__ void k_chunk_ptrs(int64_t ntiles, const int64_t* __restrict__ tptr, const int32_t* __restrict__ tchunk,
+                             const uint32_t* __restrict__ rc, uint16_t* __restrict__ ptrs) {
+  __shared__ int hr[LOB_TILE], hc[LOB_TILE];
+  const int64_t ch = blockIdx.x;
+  // tile of this chunk: last t with tchunk[t] <= ch
+  int64_t lo = 0, hi = ntiles - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (tchunk[mid] <= ch) lo = mid; else hi = mid - 1;
+  }
+  const int64_t t = lo;
+  const int64_t b = tptr[t] + (ch - tchunk[t]) * (int64_t)LOB_PERM_CHUNK;
+  const int64_t e = (tptr[t + 1] - b) < LOB_PERM_CHUNK ? tptr[t + 1] : b + LOB_PERM_CHUNK;
+  for (int i = threadIdx.x; i < LOB_TILE; i += blockDim.x) { hr[i] = 0; hc[i] = 0; }
+  __syncthreads();
+  for (int64_t k = b + threadIdx.x; k < e; k += blockDim.x) {
+    const uint32_t p = rc[k];
+    atomicAdd(&hr[p >> 16], 1);
+    atomicAdd(&hc[p & 0xFFFFu], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint16_t* pr = ptrs + ch * (2 * (LOB_TILE + 1));
+    uint16_t* pc = pr + (LOB_TILE + 1);
+    int sr = 0, sc = 0;
+    for (int i = 0; i < LOB_TILE; i++) {
+      pr[i] = (uint16_t)sr; sr += hr[i];
+      pc[i] = (uint16_t)sc; sc += hc[i];
+    }
+    pr[LOB_TILE] = (uint16_t)sr;
+    pc[LOB_TILE] = (uint16_t)sc;
+  }
+}
+
 __global__ void k_absrow(int64_t nnz, const int64_t* __restrict__ row, const int64_t* __restrict__ col,
                          const double* __restrict__ val, double* __restrict__ s) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -107,7 +165,8 @@ inline unsigned nblocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs
 
 void lob_free_tiles(lob_tiles* T) {
   cudaFree(T->rowptr); cudaFree(T->tcol); cudaFree(T->trow); cudaFree(T->tptr);
-  cudaFree(T->rc); cudaFree(T->v64); cudaFree(T->v32);
+  cudaFree(T->rc); cudaFree(T->v64); cudaFree(T->v32); cudaFree(T->cperm);
+  cudaFree(T->tchunk); cudaFree(T->cptrs);
   *T = lob_tiles();
 }
 
@@ -178,6 +237,58 @@ int lob_build_tiles(const lob_coo* H, int values, cudaStream_t st, lob_tiles* T,
   (k_fill<<<nblocks(nnz, bs), bs, 0, st>>>(nnz, skeys, sidx, (const int32_t*)flag.p, (const int32_t*)tid.p, val,
                                           bits_t, R.rc, R.v64, R.v32, R.tptr, R.tcol, R.trow), LOB_LAUNCHED());
   (k_rowptr<<<nblocks(nt + 1, bs), bs, 0, st>>>(nt, ntiles, R.trow, R.rowptr, R.tptr, nnz), LOB_LAUNCHED());
+
+  // kernel-private column-order permutation of every chunk (derived from the canonical store)
+  // (+8 entries: the SpMM stages the permutation in 4-byte words and may read one past the end)
+  if (cudaMalloc(&R.cperm, (nnz + 8) * 2) != cudaSuccess) { cudaGetLastError(); lob_free_tiles(&R); return LOB_ERR_NOMEM; }
+  {
+    // reuse the sort buffers: keys0/keys1 (uint64) and idx0/idx1 (32-bit slots, used as uint16)
+    uint64_t* pk0 = (uint64_t*)keys0.p;
+    uint64_t* pk1 = (uint64_t*)keys1.p;
+    uint16_t* pv0 = (uint16_t*)idx0.p;
+    uint16_t* pv1 = (uint16_t*)idx1.p;
+    // the sorted keys/indices still referenced above are no longer needed after k_fill
+    LOB_CUDA(cudaStreamSynchronize(st));
+    (k_perm_keys<<<nblocks(nnz, bs), bs, 0, st>>>(nnz, (const int32_t*)flag.p, (const int32_t*)tid.p, R.tptr, R.rc, pk0, pv0), LOB_LAUNCHED());
+    int ebits = 16;
+    while (ebits < 64 && (((uint64_t)nnz) << 16) >> ebits) ebits++;
+    cub::DoubleBuffer<uint64_t> pk(pk0, pk1);
+    cub::DoubleBuffer<uint16_t> pv(pv0, pv1);
+    size_t tp = 0;
+    LOB_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tp, pk, pv, (int)nnz, 0, ebits, st));
+    DevBuf tmp2;
+    if (tp > tb) { if (dalloc<char>(tmp2, tp) != LOB_OK) { lob_free_tiles(&R); return LOB_ERR_NOMEM; } }
+    void* tpp = tp > tb ? tmp2.p : tmp.p;
+    size_t tpb = tp > tb ? tp : tb;
+    LOB_CUDA(cub::DeviceRadixSort::SortPairs(tpp, tpb, pk, pv, (int)nnz, 0, ebits, st));
+    LOB_CUDA(cudaMemcpyAsync(R.cperm, pv.Current(), nnz * 2, cudaMemcpyDeviceToDevice, st));
+    LOB_CUDA(cudaStreamSynchronize(st));
+  }
+  // per-chunk row and column start pointers (kernel-private, derived from the canonical store)
+  {
+    DevBuf ccount;
+    if (dalloc<int32_t>(ccount, ntiles) != LOB_OK || cudaMalloc(&R.tchunk, (ntiles + 1) * 4) != cudaSuccess) {
+      cudaGetLastError(); lob_free_tiles(&R); return LOB_ERR_NOMEM;
+    }
+    (k_chunk_counts<<<nblocks(ntiles, bs), bs, 0, st>>>(ntiles, R.tptr, (int32_t*)ccount.p), LOB_LAUNCHED());
+    size_t ts = 0;
+    LOB_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, ts, (int32_t*)ccount.p, R.tchunk, (int)ntiles, st));
+    DevBuf tmp3;
+    if (dalloc<char>(tmp3, ts) != LOB_OK) { lob_free_tiles(&R); return LOB_ERR_NOMEM; }
+    LOB_CUDA(cub::DeviceScan::ExclusiveSum(tmp3.p, ts, (int32_t*)ccount.p, R.tchunk, (int)ntiles, st));
+    int32_t lastc = 0, lastt = 0;
+    LOB_CUDA(cudaMemcpyAsync(&lastc, (int32_t*)ccount.p + ntiles - 1, 4, cudaMemcpyDeviceToHost, st));
+    LOB_CUDA(cudaMemcpyAsync(&lastt, R.tchunk + ntiles - 1, 4, cudaMemcpyDeviceToHost, st));
+    LOB_CUDA(cudaStreamSynchronize(st));
+    const int32_t total_chunks = lastc + lastt;
+    R.nchunks = total_chunks;
+    LOB_CUDA(cudaMemcpyAsync(R.tchunk + ntiles, &total_chunks, 4, cudaMemcpyHostToDevice, st));
+    if (cudaMalloc(&R.cptrs, (size_t)R.nchunks * 2 * (LOB_TILE + 1) * 2) != cudaSuccess) {
+      cudaGetLastError(); lob_free_tiles(&R); return LOB_ERR_NOMEM;
+    }
+    (k_chunk_ptrs<<<(unsigned)R.nchunks, 256, 0, st>>>(ntiles, R.tptr, R.tchunk, R.rc, R.cptrs), LOB_LAUNCHED());
+    LOB_CUDA(cudaStreamSynchronize(st));
+  }
 
   // ||H||_inf over the full symmetric matrix
   if (dalloc<double>(rows_abs, n) != LOB_OK || dalloc<double>(dmax, 1) != LOB_OK) { lob_free_tiles(&R); return LOB_ERR_NOMEM; }
