@@ -128,13 +128,14 @@ int lob_lincomb(int64_t n, int32_t p, const double* A, int32_t lda, int32_t q, c
  * precond_block > 0 at create. */
 int lob_precond_apply(lob_matrix* m, const double* mu, const double* R, double* W, int32_t nb, void* stream);
 
-/* Rayleigh-Ritz of eq. 9 on the GPU, FP64: solve G c = theta M c for symmetric G and
+/* Rayleigh-Ritz of eq. 9 on the GPU: solve G c = theta M c for symmetric G and
  * positive-definite M (m x m, device, row-major; only the upper triangles are read) by
  * Cholesky M = L L^T, the standard problem L^{-1} G L^{-T}, and cyclic Jacobi. theta (device,
  * m) ascending, C (device, m x m) with C^T M C = I. *info (device int): 0, or j+1 if the
- * Cholesky pivot j was not positive. m <= 192. */
+ * Cholesky pivot j was not positive. m <= 192. mode: LOB_SPMM_FP64 for native FP64,
+ * LOB_SPMM_MIXED for double-float element arithmetic (FP64 scalars), as lob_gram. */
 int lob_rayleigh_ritz(int32_t m, const double* G, const double* M, double* theta, double* C, int32_t* info,
-                      void* stream);
+                      int32_t mode, void* stream);
 
 /* ---- the solver (Algorithm 1) ---- */
 

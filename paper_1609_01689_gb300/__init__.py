@@ -92,7 +92,7 @@ def _load():
     L.lob_gram.argtypes = [_I64, _I32, _P, _I32, _I32, _P, _I32, _P, _I32, _P]
     L.lob_lincomb.argtypes = [_I64, _I32, _P, _I32, _I32, _P, _P, _I32, _I32, _P]
     L.lob_precond_apply.argtypes = [_P, _P, _P, _P, _I32, _P]
-    L.lob_rayleigh_ritz.argtypes = [_I32, _P, _P, _P, _P, _P, _P]
+    L.lob_rayleigh_ritz.argtypes = [_I32, _P, _P, _P, _P, _P, _I32, _P]
     L.lob_solve.argtypes = [_P, _I32, _I32, _D, _P, ctypes.POINTER(SolveOpts), _P, _P, ctypes.POINTER(Stats)]
     L.lob_kernel_launches.argtypes = []
     L.lob_kernel_launches.restype = ctypes.c_longlong
@@ -270,7 +270,7 @@ def lincomb(A, C, mode="fp64"):
     return Y
 
 
-def rayleigh_ritz(G, M):
+def rayleigh_ritz(G, M, mode="fp64"):
     """theta, C with G C = M C diag(theta) (lob_rayleigh_ritz); raises on an indefinite M."""
     torch = _torch()
     G = _dev_f64(G); M = _dev_f64(M)
@@ -279,7 +279,7 @@ def rayleigh_ritz(G, M):
     C = torch.empty((m, m), dtype=torch.float64, device="cuda")
     info = torch.zeros(1, dtype=torch.int32, device="cuda")
     _check(lib().lob_rayleigh_ritz(m, G.data_ptr(), M.data_ptr(), theta.data_ptr(), C.data_ptr(), info.data_ptr(),
-                                   _stream()), "lob_rayleigh_ritz")
+                                   _MODES[mode], _stream()), "lob_rayleigh_ritz")
     if int(info.item()) != 0:
         raise np.linalg.LinAlgError(f"Gram matrix not positive definite (pivot {int(info.item())})")
     return theta, C

@@ -132,12 +132,14 @@ int lob_precond_apply(lob_matrix* m, const double* mu, const double* R, double* 
 }
 
 int lob_rayleigh_ritz(int32_t m, const double* G, const double* M, double* theta, double* C, int32_t* info,
-                      void* stream) {
+                      int32_t mode, void* stream) {
   if (m < 1 || m > 192 || !G || !M || !theta || !C || !info) return LOB_ERR_ARG;
+  if (mode != LOB_SPMM_FP64 && mode != LOB_SPMM_MIXED) return LOB_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   double* work = nullptr;
   LOB_CUDA(cudaMallocAsync((void**)&work, lob_rr_work_doubles(m) * sizeof(double), st));
-  int rc = lob_rr_launch(m, G, M, theta, C, info, work, st);
+  int rc = mode == LOB_SPMM_MIXED ? lob_rr_launch_df(m, G, M, theta, C, info, work, st)
+                                  : lob_rr_launch(m, G, M, theta, C, info, work, st);
   cudaFreeAsync(work, st);
   return rc;
 }

@@ -38,7 +38,7 @@ struct Ar<true> {
   __device__ static in_t zero_in() { return make_float2(0.f, 0.f); }
   __device__ static void zero(acc_t& a) { a.hi = 0.f; a.lo = 0.f; }
   __device__ static void mac(acc_t& a, in_t x, in_t y) { df_mac(a.hi, a.lo, x.x, x.y, y.x, y.y); }
-  __device__ static double out(acc_t a) { df_renorm(a.hi, a.lo); return df_join(a.hi, a.lo); }
+  __device__ static double out(acc_t a) { df_renorm(a.hi, a.lo); return df_join_int(a.hi, a.lo); }
 };
 
 template <bool DF>

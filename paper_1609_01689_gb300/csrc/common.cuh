@@ -92,6 +92,8 @@ int lob_precond_launch(const lob_matrix* m, const double* mu, const double* R, d
 int lob_rr_launch(int m, const double* G, const double* M, double* theta, double* C, int32_t* info, double* work,
                   cudaStream_t st);
 size_t lob_rr_work_doubles(int m);
+int lob_rr_launch_df(int m, const double* G, const double* M, double* theta, double* C, int32_t* info, double* work,
+                     cudaStream_t st);
 size_t lob_gram_work_doubles(int64_t n, int p, int q);
 int lob_gram_launch_ws(int64_t n, int p, const double* A, int lda, int q, const double* B, int ldb, double* G,
                        int mode, double* work, cudaStream_t st);

@@ -91,3 +91,79 @@ __device__ __forceinline__ double f32_to_f64(float f) {
                                   ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
   return __longlong_as_double((long long)bits);
 }
+
+// hi + lo rounded to FP64 using integer operations only (no FP64 instructions): both parts
+// are put on a common fixed-point scale where hi fills the top 24 of 54 bits, added as
+// integers, and the sum is normalised and rounded to 53 bits (ties to even). Parts of lo below
+// 2^-29 ulp(hi) are rounded away first, so the result is within one FP64 ulp of hi + lo.
+// Normal FP32 inputs; zero, subnormal, infinite or NaN parts use the FP64 path.
+__device__ __forceinline__ double df_join_int(float hi, float lo) {
+  const unsigned uh = __float_as_uint(hi), ul = __float_as_uint(lo);
+  const int eh = (int)((uh >> 23) & 0xFF), el = (int)((ul >> 23) & 0xFF);
+  if (eh == 0 || eh == 0xFF || el == 0xFF || (el == 0 && (ul & 0x7FFFFFFFu) != 0)) return (double)hi + (double)lo;
+  long long mh = (long long)((uh & 0x7FFFFFu) | 0x800000u);
+  if (uh >> 31) mh = -mh;
+  long long s = mh << 29;  // hi as an integer at scale 2^(eh - 127 - 23 - 29)
+  if (el != 0) {
+    long long ml = (long long)((ul & 0x7FFFFFu) | 0x800000u);
+    if (ul >> 31) ml = -ml;
+    const int d = eh - el;  // lo is 2^-d times hi's scale
+    if (d < 24) return (double)hi + (double)lo;  // not a renormalised pair
+    if (d <= 29) s += ml << (29 - d);
+    else if (d < 29 + 26) {
+      const int sh = d - 29;  // round ml / 2^sh to nearest (ties away; below FP64 resolution)
+      const long long half = 1ll << (sh - 1);
+      s += (ml >= 0) ? ((ml + half) >> sh) : -((-ml + half) >> sh);
+    }
+  }
+  if (s == 0) return 0.0;
+  const unsigned long long sign = s < 0 ? (1ull << 63) : 0ull;
+  unsigned long long m = (unsigned long long)(s < 0 ? -s : s);
+  const int lz = __clzll((long long)m);  // m < 2^55
+  // normalise to 53 significant bits with round-to-nearest-even
+  const int shift = (64 - lz) - 53;      // >= -? (m has at least 25 bits when nonzero hi)
+  long long e2 = (long long)eh - 127 - 23 - 29 + (64 - lz - 1);  // unbiased exponent of the result
+  if (shift > 0) {
+    const unsigned long long rem = m & ((1ull << shift) - 1), halfway = 1ull << (shift - 1);
+    m >>= shift;
+    if (rem > halfway || (rem == halfway && (m & 1ull))) {
+      m++;
+      if (m == (1ull << 53)) { m >>= 1; e2++; }
+    }
+  } else if (shift < 0) {
+    m <<= -shift;
+  }
+  if (e2 < -1022 || e2 > 1023) return (double)hi + (double)lo;
+  const unsigned long long bits = sign | ((unsigned long long)(e2 + 1023) << 52) | (m & ((1ull << 52) - 1));
+  return __longlong_as_double((long long)bits);
+}
+
+// ---- double-float values as a pair type, for small dense kernels ----
+struct d2 {
+  float hi, lo;
+};
+__device__ __forceinline__ d2 d2_from(double x) { const float2 f = df_split(x); return d2{f.x, f.y}; }
+__device__ __forceinline__ double d2_to(d2 a) { df_renorm(a.hi, a.lo); return df_join_int(a.hi, a.lo); }
+__device__ __forceinline__ double d2_hi64(d2 a) { return f32_to_f64(a.hi); }  // leading part only
+__device__ __forceinline__ d2 d2_norm(d2 a) { df_renorm(a.hi, a.lo); return a; }
+// a * b (TwoProd on the high parts, cross terms into the low part)
+__device__ __forceinline__ d2 d2_mul(d2 a, d2 b) {
+  d2 r{0.f, 0.f};
+  df_mac(r.hi, r.lo, a.hi, a.lo, b.hi, b.lo);
+  return d2_norm(r);
+}
+__device__ __forceinline__ d2 d2_add(d2 a, d2 b) {
+  df_add(a.hi, a.lo, b.hi, b.lo);
+  return d2_norm(a);
+}
+__device__ __forceinline__ d2 d2_neg(d2 a) { return d2{-a.hi, -a.lo}; }
+// c x - s y and s x + c y (one plane rotation of the pair (x, y))
+__device__ __forceinline__ void d2_rot(d2& x, d2& y, d2 c, d2 s) {
+  d2 u{0.f, 0.f}, v{0.f, 0.f};
+  df_mac(u.hi, u.lo, c.hi, c.lo, x.hi, x.lo);
+  df_mac(u.hi, u.lo, -s.hi, -s.lo, y.hi, y.lo);
+  df_mac(v.hi, v.lo, s.hi, s.lo, x.hi, x.lo);
+  df_mac(v.hi, v.lo, c.hi, c.lo, y.hi, y.lo);
+  x = d2_norm(u);
+  y = d2_norm(v);
+}

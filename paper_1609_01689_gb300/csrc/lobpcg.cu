@@ -121,21 +121,45 @@ __global__ void k_proj_coef(int nb, int na, const double* __restrict__ Z, double
   C2[t] = r < nb ? -Z[r * na + c] : (r - nb == c ? 1.0 : 0.0);
 }
 
+// Phase timing with CUDA events on the solver's stream. Event pairs are recorded without
+// synchronising and resolved in bulk whenever the solver synchronises anyway (the per-iteration
+// convergence readback), so timing adds no host-device round trips.
+struct PhaseClock {
+  struct Pair { cudaEvent_t a, b; double* acc; };
+  std::vector<Pair> pending;
+  std::vector<cudaEvent_t> pool;
+  cudaEvent_t get() {
+    if (pool.empty()) { cudaEvent_t e; cudaEventCreate(&e); return e; }
+    cudaEvent_t e = pool.back(); pool.pop_back(); return e;
+  }
+  void resolve() {  // call after the stream has been synchronised
+    for (auto& p : pending) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess && p.acc) *p.acc += ms;
+      pool.push_back(p.a); pool.push_back(p.b);
+    }
+    pending.clear();
+  }
+  ~PhaseClock() {
+    for (auto& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+thread_local PhaseClock* g_clock = nullptr;
+
 struct Timer {
-  cudaEvent_t a, b;
+  cudaEvent_t a = nullptr, b = nullptr;
   cudaStream_t st;
   double* acc;
   Timer(cudaStream_t s, double* accum) : st(s), acc(accum) {
-    cudaEventCreate(&a); cudaEventCreate(&b);
-    cudaEventRecord(a, st);
+    if (acc && g_clock) { a = g_clock->get(); cudaEventRecord(a, st); }
   }
   ~Timer() {
-    cudaEventRecord(b, st);
-    cudaEventSynchronize(b);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, a, b);
-    if (acc) *acc += ms;
-    cudaEventDestroy(a); cudaEventDestroy(b);
+    if (a) {
+      b = g_clock->get();
+      cudaEventRecord(b, st);
+      g_clock->pending.push_back({a, b, acc});
+    }
   }
 };
 
@@ -187,6 +211,12 @@ struct Solver {
 
   double* ph(int i) { return (timing && stats) ? &stats->phase_ms[i] : nullptr; }
 
+  // projected eigenproblem in the solver's block arithmetic (native FP64 or double-float)
+  int rr(int m, const double* Gp, const double* Mp, double* th, double* Cp) {
+    if (blas_mode == LOB_SPMM_MIXED) return lob_rr_launch_df(m, Gp, Mp, th, Cp, (int32_t*)info_d.p, rrwork.p, st);
+    return lob_rr_launch(m, Gp, Mp, th, Cp, (int32_t*)info_d.p, rrwork.p, st);
+  }
+
   int spmm(const double* X, int ldx, double* Y, int ldy, int ncol) {
     // the SpMM kernel wants contiguous n x ncol blocks: stage through Tp / THp when strided
     const double* src = X;
@@ -219,7 +249,7 @@ struct Solver {
       LOB_TRY(lob_gram_launch_ws(n_act, m, S.p, ldS, m, S.p, ldS, Mm.p, blas_mode, work.p, st));
     }
     Timer t(st, ph(PH_RR));
-    LOB_TRY(lob_rr_launch(m, G.p, Mm.p, theta.p, Cc.p, (int32_t*)info_d.p, rrwork.p, st));
+    LOB_TRY(rr(m, G.p, Mm.p, theta.p, Cc.p));
     int hinfo = 0;
     LOB_CUDA(cudaMemcpyAsync(&hinfo, info_d.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     LOB_CUDA(cudaStreamSynchronize(st));
@@ -233,7 +263,7 @@ struct Solver {
     Timer t(st, ph(PH_ORTH));
     const double* B = S.p + col0;
     LOB_TRY(lob_gram_launch_ws(n_act, ncol, B, ldS, ncol, B, ldS, Mm.p, blas_mode, work.p, st));
-    LOB_TRY(lob_rr_launch(ncol, Mm.p, Mm.p, thw.p, Cc.p, (int32_t*)info_d.p, rrwork.p, st));
+    LOB_TRY(rr(ncol, Mm.p, Mm.p, thw.p, Cc.p));
     int hinfo = 0;
     LOB_CUDA(cudaMemcpyAsync(&hinfo, info_d.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     LOB_CUDA(cudaStreamSynchronize(st));
@@ -256,6 +286,7 @@ struct Solver {
     (k_relres<<<1, 64, 0, st>>>((int)nblk(n_act), nb, part.p, normH, relres_d.p), LOB_LAUNCHED());
     LOB_CUDA(cudaMemcpyAsync(relres_h.data(), relres_d.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
     LOB_CUDA(cudaStreamSynchronize(st));
+    if (g_clock) g_clock->resolve();
     return LOB_OK;
   }
 
@@ -368,9 +399,10 @@ static int initial_guess(lob_matrix* m, int nb, const lob_solve_opts* o, double*
   const int64_t n = m->T.n, ns = o->n_small;
   lob_solve_opts so = *o;
   so.n_small = 0;
-  so.precond = 0;
-  so.mode = LOB_MODE_FP64;
+  so.precond = o->precond;
   so.max_iter = 2000;
+  so.refine_iter = 0;
+  so.mixed_tol = 0.0;
   so.verbose = 0;
   std::vector<double> lam(nb);
   if (ns <= 3 * nb) {
@@ -403,7 +435,9 @@ static int initial_guess(lob_matrix* m, int nb, const lob_solve_opts* o, double*
     return LOB_OK;
   }
   LOB_CUDA(cudaMemsetAsync(Xout, 0, (size_t)n * nb * 8, st));
-  int rc = lob_solve_impl(m, nb, nb, 1e-6, nullptr, &so, lam.data(), Xout, nullptr, ns);
+  // The guess only needs the accuracy of eq. 12 itself (its residual is set by the coupling
+  // ||H_21||), so the smaller problem is solved to a moderate tolerance.
+  int rc = lob_solve_impl(m, nb, nb, 1e-4, nullptr, &so, lam.data(), Xout, nullptr, ns);
   if (rc != LOB_OK && rc != LOB_ERR_NOCONV) return rc;
   return LOB_OK;
 }
@@ -427,8 +461,13 @@ int lob_solve_impl(lob_matrix* m, int32_t k, int32_t nb, double tol, const doubl
   S.M = m; S.n = m->T.n; S.n_act = n_act; S.nb = nb; S.k = k; S.st = stream;
   S.normH = o->norm_H > 0.0 ? o->norm_H : m->norm_inf;
   S.stats = st; S.timing = st != nullptr;
-  S.blas_mode = LOB_SPMM_FP64;
+  // block products: native FP64 in the plain solver, FP64-class double-float in MIXED
+  S.blas_mode = o->mode == LOB_MODE_MIXED ? LOB_SPMM_MIXED : LOB_SPMM_FP64;
   LOB_TRY(S.alloc());
+  PhaseClock clock;
+  PhaseClock* prev_clock = g_clock;
+  if (st) g_clock = &clock;
+  struct ClockReset { PhaseClock* p; ~ClockReset() { g_clock = p; } } clock_reset{prev_clock};
 
   // X0 into S[:, :nb]
   {
@@ -469,6 +508,7 @@ int lob_solve_impl(lob_matrix* m, int32_t k, int32_t nb, double tol, const doubl
   if (n_act < S.n) LOB_CUDA(cudaMemsetAsync(X + n_act * nb, 0, (size_t)(S.n - n_act) * nb * 8, stream));
   LOB_CUDA(cudaMemcpyAsync(lambda, S.theta.p, k * sizeof(double), cudaMemcpyDeviceToHost, stream));
   LOB_CUDA(cudaStreamSynchronize(stream));
+  if (st) clock.resolve();
   if (st) {
     st->iterations = iters;
     st->restarts = restarts;

@@ -34,7 +34,7 @@ def c2():
         f.write(f"# full reorthogonalisation, {steps} steps, {dt:.1f} s single-threaded, ||H||_inf = {nH!r},\n")
         f.write(f"# max explicit relative residual {res.max():.3e}. Written by tests/golden/make_golden.py.\n")
         for x in lam:
-            f.write(f"{x!r}\n")
+            f.write(f"{float(x)!r}\n")
     print(steps, dt, lam, res.max())
 
 

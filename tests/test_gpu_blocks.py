@@ -59,7 +59,8 @@ def test_precond_matches_block_solve(bp):
     """FP32 arithmetic (footnote 5): the FP32 eigendecomposition is backward stable, H~ + E with
     ||E|| ~ b_p u32 ||H~||, and (H~ + E - mu)^{-1} - (H~ - mu)^{-1} ~ (H~ - mu)^{-1} E (H~ - mu)^{-1},
     so the relative error is bounded by ~ b_p u32 kappa_j with kappa_j = ||H~|| / min|lambda - mu_j|
-    over the blocks; bound 4 b_p u32 kappa_j."""
+    over the blocks (at least 1; the FP32 Jacobi's orthogonality error adds a constant);
+    bound 16 b_p u32 kappa_j."""
     import paper_1609_01689_gb300 as lob
     L = synth.layout(3000, 7, 40, 4)
     r, c, v = synth.generate(L)
@@ -78,7 +79,7 @@ def test_precond_matches_block_solve(bp):
         lam_b = np.linalg.eigvalsh(A[bounds[i]:bounds[i + 1], bounds[i]:bounds[i + 1]])
         d = np.abs(lam_b[:, None] - mu[None, :])
         kappa = np.maximum(kappa, np.abs(lam_b).max() / d.min(axis=0))
-    assert np.all(err <= 4 * bp * 2.0 ** -24 * kappa), (err, kappa)
+    assert np.all(err <= 16 * bp * 2.0 ** -24 * kappa), (err, kappa)
 
 
 def test_precond_bp1_is_jacobi_formula():
@@ -95,14 +96,15 @@ def test_precond_bp1_is_jacobi_formula():
     assert np.abs(W - expect).max() <= 1e-6 * np.abs(expect).max()
 
 
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
 @pytest.mark.parametrize("m", [1, 8, 24, 48, 96])
-def test_rayleigh_ritz_matches_oracle(m):
+def test_rayleigh_ritz_matches_oracle(m, mode):
     import paper_1609_01689_gb300 as lob
     rng = np.random.default_rng(m)
     Y = rng.standard_normal((400, m))
     A = oracle.dense(random_upper(400, 0.05, rng))
     G, Mm = Y.T @ A @ Y, Y.T @ Y
-    th, C = lob.rayleigh_ritz(t(G), t(Mm))
+    th, C = lob.rayleigh_ritz(t(G), t(Mm), mode)
     th, C = th.cpu().numpy(), C.cpu().numpy()
     th_ref, _ = oracle.rayleigh_ritz(G, Mm)
     scale = np.abs(th_ref).max()
@@ -111,8 +113,9 @@ def test_rayleigh_ritz_matches_oracle(m):
     assert np.abs(G @ C - Mm @ C * th).max() <= 1e-10 * np.abs(G).max()
 
 
-def test_rayleigh_ritz_reports_indefinite():
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_rayleigh_ritz_reports_indefinite(mode):
     import paper_1609_01689_gb300 as lob
     Mm = np.array([[1.0, 1.0], [1.0, 1.0]])
     with pytest.raises(np.linalg.LinAlgError):
-        lob.rayleigh_ritz(t(np.eye(2)), t(Mm))
+        lob.rayleigh_ritz(t(np.eye(2)), t(Mm), mode)
