@@ -100,6 +100,9 @@ int lob_export_perm(const lob_matrix* m, uint16_t* perm);
 #define LOB_SPMM_FP64 0  /* FP64 values, FP64 X, FP64 products and sums (plain FP64) */
 #define LOB_SPMM_MIXED 1 /* FP32 values, X rounded to FP32, FP32 products and in-tile sums,
                             tile partials summed across tiles in FP64, FP64 result */
+#define LOB_SPMM_DF64 2  /* FP64-class: values and X as double-float pairs (~48 bits), every
+                            product and sum in double-float on the FP32 pipes, FP64 result.
+                            Needs LOB_VALUES_BOTH. (lob_spmm only.) */
 
 /* Y = H X (Section 4.1: U_i = H_ij W_j and U_j = H_ij^T W_i for every stored tile, here in one
  * pass over the tiles). X, Y: device, n x nb, row-major FP64, must not overlap. 1 <= nb <= 64.
@@ -168,6 +171,9 @@ typedef struct {
   double phase_ms[8];       /* device time per phase: spmm, gram, rr, update, precond,
                                residual, orth, guess */
   double spmm_bytes;        /* algorithmic bytes moved by all SpMMs */
+  int32_t spmm_calls_mode[4];   /* per SpMM arithmetic (LOB_SPMM_*): launches, */
+  double spmm_ms_mode[4];       /* device time (the Y reset, X staging and kernel), */
+  double spmm_bytes_mode[4];    /* and algorithmic bytes */
   double residual[64];      /* final ||H x_j - theta_j x_j|| / (||H|| ||x_j||), FP64 */
 } lob_stats;
 

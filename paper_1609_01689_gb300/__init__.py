@@ -29,9 +29,9 @@ LOB_ERR_NOCONV = -4
 LOB_ERR_BREAKDOWN = -5
 
 VALUES_FP64, VALUES_FP32, VALUES_BOTH = 1, 2, 3
-SPMM_FP64, SPMM_MIXED = 0, 1
+SPMM_FP64, SPMM_MIXED, SPMM_DF64 = 0, 1, 2
 MODE_FP64, MODE_MIXED = 0, 1
-_MODES = {"fp64": 0, "mixed": 1, 0: 0, 1: 1}
+_MODES = {"fp64": 0, "mixed": 1, "df64": 2, 0: 0, 1: 1, 2: 2}
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -61,7 +61,8 @@ class SolveOpts(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", _I32), ("refine_iterations", _I32), ("spmm_calls", _I32), ("restarts", _I32),
-                ("time_ms", _D), ("phase_ms", _D * 8), ("spmm_bytes", _D), ("residual", _D * 64)]
+                ("time_ms", _D), ("phase_ms", _D * 8), ("spmm_bytes", _D), ("spmm_calls_mode", _I32 * 4),
+                ("spmm_ms_mode", _D * 4), ("spmm_bytes_mode", _D * 4), ("residual", _D * 64)]
 
     PHASES = ("spmm", "gram", "rr", "update", "precond", "residual", "orth", "guess")
 
@@ -69,7 +70,11 @@ class Stats(ctypes.Structure):
         return dict(iterations=self.iterations, refine_iterations=self.refine_iterations,
                     spmm_calls=self.spmm_calls, restarts=self.restarts, time_ms=self.time_ms,
                     phase_ms={p: self.phase_ms[i] for i, p in enumerate(self.PHASES)},
-                    spmm_bytes=self.spmm_bytes, residual=[self.residual[j] for j in range(nb)])
+                    spmm_bytes=self.spmm_bytes,
+                    spmm_by_mode={m: dict(calls=self.spmm_calls_mode[i], ms=self.spmm_ms_mode[i],
+                                          bytes=self.spmm_bytes_mode[i])
+                                  for i, m in enumerate(("fp64", "mixed", "df64"))},
+                    residual=[self.residual[j] for j in range(nb)])
 
 
 class LobError(RuntimeError):

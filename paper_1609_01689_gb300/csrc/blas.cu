@@ -15,7 +15,7 @@
 
 namespace {
 
-constexpr int TG = 48;  // output tile edge
+constexpr int TG = 48;  // largest output tile edge
 constexpr int RB = 16;  // rows staged per step
 
 template <bool DF>
@@ -41,27 +41,30 @@ struct Ar<true> {
   __device__ static double out(acc_t a) { df_renorm(a.hi, a.lo); return df_join_int(a.hi, a.lo); }
 };
 
-template <bool DF>
+// U = tile edge / 16 outputs per thread along each dimension (1, 2 or 3): small Gram matrices
+// (16 x 16, 32 x 32) use a matching tile instead of a zero-padded 48 x 48 one.
+template <bool DF, int U>
 __global__ void __launch_bounds__(256) k_gram(int64_t n, int p, const double* __restrict__ A, int lda, int q,
                                               const double* __restrict__ B, int ldb, double* __restrict__ part,
                                               int64_t rpc) {
   using R = Ar<DF>;
   using in_t = typename R::in_t;
-  __shared__ in_t As[RB][TG];
-  __shared__ in_t Bs[RB][TG];
+  constexpr int TGU = 16 * U;
+  __shared__ in_t As[RB][TGU];
+  __shared__ in_t Bs[RB][TGU];
   const int chunk = blockIdx.x;
-  const int a0 = blockIdx.y * TG, b0 = blockIdx.z * TG;
+  const int a0 = blockIdx.y * TGU, b0 = blockIdx.z * TGU;
   const int64_t r0 = (int64_t)chunk * rpc;
   const int64_t r1 = (r0 + rpc) < n ? (r0 + rpc) : n;
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  typename R::acc_t acc[3][3];
+  typename R::acc_t acc[U][U];
 #pragma unroll
-  for (int i = 0; i < 3; i++)
+  for (int i = 0; i < U; i++)
 #pragma unroll
-    for (int j = 0; j < 3; j++) R::zero(acc[i][j]);
+    for (int j = 0; j < U; j++) R::zero(acc[i][j]);
   for (int64_t rr = r0; rr < r1; rr += RB) {
-    for (int idx = tid; idx < RB * TG; idx += 256) {
-      const int i = idx / TG, a = idx % TG;
+    for (int idx = tid; idx < RB * TGU; idx += 256) {
+      const int i = idx / TGU, a = idx % TGU;
       const int64_t r = rr + i;
       As[i][a] = (r < r1 && a0 + a < p) ? R::load(A[r * lda + a0 + a]) : R::zero_in();
       Bs[i][a] = (r < r1 && b0 + a < q) ? R::load(B[r * ldb + b0 + a]) : R::zero_in();
@@ -69,20 +72,20 @@ __global__ void __launch_bounds__(256) k_gram(int64_t n, int p, const double* __
     __syncthreads();
 #pragma unroll 4
     for (int i = 0; i < RB; i++) {
-      in_t av[3], bv[3];
+      in_t av[U], bv[U];
 #pragma unroll
-      for (int u = 0; u < 3; u++) { av[u] = As[i][ty + 16 * u]; bv[u] = Bs[i][tx + 16 * u]; }
+      for (int u = 0; u < U; u++) { av[u] = As[i][ty + 16 * u]; bv[u] = Bs[i][tx + 16 * u]; }
 #pragma unroll
-      for (int u = 0; u < 3; u++)
+      for (int u = 0; u < U; u++)
 #pragma unroll
-        for (int v = 0; v < 3; v++) R::mac(acc[u][v], av[u], bv[v]);
+        for (int v = 0; v < U; v++) R::mac(acc[u][v], av[u], bv[v]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int u = 0; u < 3; u++)
+  for (int u = 0; u < U; u++)
 #pragma unroll
-    for (int v = 0; v < 3; v++) {
+    for (int v = 0; v < U; v++) {
       const int a = a0 + ty + 16 * u, b = b0 + tx + 16 * v;
       if (a < p && b < q) part[(int64_t)chunk * p * q + (int64_t)a * q + b] = R::out(acc[u][v]);
     }
@@ -136,21 +139,34 @@ inline int nchunks_for(int64_t n, int tiles) {
 
 }  // namespace
 
+static int gram_edge(int p, int q) {
+  const int mx = p > q ? p : q;
+  return mx <= 16 ? 16 : (mx <= 32 ? 32 : TG);
+}
+
 size_t lob_gram_work_doubles(int64_t n, int p, int q) {
-  const int tiles = ((p + TG - 1) / TG) * ((q + TG - 1) / TG);
+  const int e = gram_edge(p, q);
+  const int tiles = ((p + e - 1) / e) * ((q + e - 1) / e);
   return (size_t)nchunks_for(n, tiles) * p * q;
+}
+
+template <bool DF>
+static void gram_go(dim3 grid, cudaStream_t st, int U, int64_t n, int p, const double* A, int lda, int q,
+                    const double* B, int ldb, double* work, int64_t rpc) {
+  if (U == 1) (k_gram<DF, 1><<<grid, 256, 0, st>>>(n, p, A, lda, q, B, ldb, work, rpc), LOB_LAUNCHED());
+  else if (U == 2) (k_gram<DF, 2><<<grid, 256, 0, st>>>(n, p, A, lda, q, B, ldb, work, rpc), LOB_LAUNCHED());
+  else (k_gram<DF, 3><<<grid, 256, 0, st>>>(n, p, A, lda, q, B, ldb, work, rpc), LOB_LAUNCHED());
 }
 
 int lob_gram_launch_ws(int64_t n, int p, const double* A, int lda, int q, const double* B, int ldb, double* G,
                        int mode, double* work, cudaStream_t st) {
-  const int ta = (p + TG - 1) / TG, tb = (q + TG - 1) / TG;
+  const int e = gram_edge(p, q);
+  const int ta = (p + e - 1) / e, tb = (q + e - 1) / e;
   const int nch = nchunks_for(n, ta * tb);
   const int64_t rpc = (n + nch - 1) / nch;
   dim3 grid(nch, ta, tb);
-  if (mode == LOB_SPMM_MIXED)
-    (k_gram<true><<<grid, 256, 0, st>>>(n, p, A, lda, q, B, ldb, work, rpc), LOB_LAUNCHED());
-  else
-    (k_gram<false><<<grid, 256, 0, st>>>(n, p, A, lda, q, B, ldb, work, rpc), LOB_LAUNCHED());
+  if (mode == LOB_SPMM_MIXED) gram_go<true>(grid, st, e / 16, n, p, A, lda, q, B, ldb, work, rpc);
+  else gram_go<false>(grid, st, e / 16, n, p, A, lda, q, B, ldb, work, rpc);
   const int pq = p * q;
   (k_gram_reduce<<<(pq * 32 + 255) / 256, 256, 0, st>>>(nch, pq, work, G), LOB_LAUNCHED());
   LOB_CUDA(cudaGetLastError());

@@ -44,6 +44,7 @@ struct lob_tiles {
   uint32_t* rc = nullptr;      // [nnz] (r << 16) | c
   double* v64 = nullptr;       // [nnz] FP64 values (may be null)
   float* v32 = nullptr;        // [nnz] FP32 values (may be null)
+  float* v32lo = nullptr;      // [nnz] kernel-private: v64 - v32 rounded to FP32 (with both copies)
   uint16_t* cperm = nullptr;   // [nnz] kernel-private: per chunk of LOB_PERM_CHUNK entries of a tile,
                                // the chunk-local indices of its entries in (c, r) order
   int64_t nchunks = 0;
@@ -90,10 +91,10 @@ int lob_lincomb_launch(int64_t n, int p, const double* A, int lda, int q, const 
 int lob_precond_launch(const lob_matrix* m, const double* mu, const double* R, double* W, int nb, int64_t n_act,
                        cudaStream_t st);
 int lob_rr_launch(int m, const double* G, const double* M, double* theta, double* C, int32_t* info, double* work,
-                  cudaStream_t st);
+                  cudaStream_t st, int chol_only = 0);
 size_t lob_rr_work_doubles(int m);
 int lob_rr_launch_df(int m, const double* G, const double* M, double* theta, double* C, int32_t* info, double* work,
-                     cudaStream_t st);
+                     cudaStream_t st, int chol_only = 0);
 size_t lob_gram_work_doubles(int64_t n, int p, int q);
 int lob_gram_launch_ws(int64_t n, int p, const double* A, int lda, int q, const double* B, int ldb, double* G,
                        int mode, double* work, cudaStream_t st);

@@ -12,23 +12,134 @@
 
 namespace {
 
-constexpr int RR_THREADS = 512;
+constexpr int RR_THREADS = 1024;
 
 __device__ __forceinline__ int rr_player(int pos, int round, int mp) {
   // circle method: position 0 holds player 0; the others rotate by one each round
   return pos == 0 ? 0 : 1 + (pos - 1 + round) % (mp - 1);
 }
 
+
+// ---- cyclic Jacobi with 2x2-block updates (both kernels) ----
+// Round r of the round-robin order pairs the indices as (p_k, q_k), k < m/2, all disjoint.
+// A <- J^T A J with J the product of the round's rotations; for the 2x2 block of rows {p1, q1}
+// and columns {p2, q2} the new values depend only on that block, so one thread updates a whole
+// block (left rotation k1, then right rotation k2) and the round needs no barrier between its
+// row and column halves: angles (one thread per pair) | barrier | blocks of A and pairs of
+// columns of V | barrier.
+__device__ __forceinline__ void rot2(double& x, double& y, double c, double s) {
+  const double u = c * x - s * y, v = s * x + c * y;
+  x = u;
+  y = v;
+}
+__device__ __forceinline__ void rot2(d2& x, d2& y, d2 c, d2 s) { d2_rot(x, y, c, s); }
+__device__ __forceinline__ double hi64(double x) { return x; }
+__device__ __forceinline__ double hi64(d2 x) { return d2_hi64(x); }
+__device__ __forceinline__ bool nonzero(double x) { return x != 0.0; }
+__device__ __forceinline__ bool nonzero(d2 x) { return x.hi != 0.f; }
+__device__ __forceinline__ double ident_one(double) { return 1.0; }
+__device__ __forceinline__ d2 ident_one(d2) { return d2{1.f, 0.f}; }
+__device__ __forceinline__ double ident_zero(double) { return 0.0; }
+__device__ __forceinline__ d2 ident_zero(d2) { return d2{0.f, 0.f}; }
+
+// rotation (c, s) that zeros a_pq (GVL 8.5: tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) /
+// (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c). FP64: all in FP64. Double-float:
+// the angle in FP32 from a double-float difference, then c, s in double-float from that exact t.
+__device__ __forceinline__ void jac_angle(double app, double aqq, double apq, double& c, double& s) {
+  c = 1.0; s = 0.0;
+  if (apq == 0.0) return;
+  const double tau = (aqq - app) / (2.0 * apq);
+  const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+  c = 1.0 / sqrt(1.0 + t * t);
+  s = t * c;
+}
+__device__ __forceinline__ void jac_angle(d2 app, d2 aqq, d2 apq, d2& c, d2& s) {
+  c = d2{1.f, 0.f}; s = d2{0.f, 0.f};
+  apq = d2_norm(apq);
+  if (apq.hi == 0.f) return;
+  const d2 diff = d2_add(aqq, d2_neg(app));
+  const float tau = diff.hi / (2.f * apq.hi);
+  const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+  if (t == 0.f) return;
+  const d2 tt{t, 0.f};
+  c = d2_rsqrt(d2_add(d2{1.f, 0.f}, d2_mul(tt, tt)));
+  s = d2_mul(tt, c);
+}
+
+template <typename E>
+__device__ void jacobi_blocks(int m, E* A, E* V, double stop_ratio, E* cs_c, E* cs_s, int* pr_p, int* pr_q,
+                              double* red, double* s_off, double* s_fro) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int mm = m * m;
+  const int mp = m + (m & 1), np = mp / 2;
+  for (int sweep = 0; sweep < 40; sweep++) {
+    double off = 0.0, fro = 0.0;
+    for (int e = tid; e < mm; e += nt) {
+      const double x = hi64(A[e]);
+      fro += x * x;
+      if (e / m != e % m) off += x * x;
+    }
+    for (int o = 16; o > 0; o >>= 1) { off += __shfl_down_sync(0xFFFFFFFFu, off, o); fro += __shfl_down_sync(0xFFFFFFFFu, fro, o); }
+    if (tid % 32 == 0) { red[tid / 32] = off; red[32 + tid / 32] = fro; }
+    __syncthreads();
+    if (tid == 0) {
+      double so = 0, sf = 0;
+      for (int w = 0; w < nt / 32; w++) { so += red[w]; sf += red[32 + w]; }
+      *s_off = so; *s_fro = sf;
+    }
+    __syncthreads();
+    if (*s_off <= stop_ratio * *s_fro || *s_off == 0.0) break;
+    for (int round = 0; round < mp - 1; round++) {
+      for (int k = tid; k < np; k += nt) {
+        int p = rr_player(k, round, mp), q = rr_player(mp - 1 - k, round, mp);
+        if (p > q) { const int t = p; p = q; q = t; }
+        E c = ident_one(E{}), sn = ident_zero(E{});
+        if (q < m) jac_angle(A[p * m + p], A[q * m + q], A[p * m + q], c, sn);
+        pr_p[k] = p; pr_q[k] = q; cs_c[k] = c; cs_s[k] = sn;
+      }
+      __syncthreads();
+      // 2x2 blocks of A: block (k1, k2) = rows {p1, q1} x columns {p2, q2}
+      for (int b = tid; b < np * np; b += nt) {
+        const int k1 = b / np, k2 = b % np;
+        const int p1 = pr_p[k1], q1 = pr_q[k1], p2 = pr_p[k2], q2 = pr_q[k2];
+        const bool r1 = q1 < m, r2 = q2 < m;  // second index valid (not the dummy)
+        E a11 = A[p1 * m + p2];
+        E a12 = r2 ? A[p1 * m + q2] : ident_zero(E{});
+        E a21 = r1 ? A[q1 * m + p2] : ident_zero(E{});
+        E a22 = (r1 && r2) ? A[q1 * m + q2] : ident_zero(E{});
+        if (r1 && nonzero(cs_s[k1])) { rot2(a11, a21, cs_c[k1], cs_s[k1]); rot2(a12, a22, cs_c[k1], cs_s[k1]); }
+        if (r2 && nonzero(cs_s[k2])) { rot2(a11, a12, cs_c[k2], cs_s[k2]); rot2(a21, a22, cs_c[k2], cs_s[k2]); }
+        A[p1 * m + p2] = a11;
+        if (r2) A[p1 * m + q2] = a12;
+        if (r1) A[q1 * m + p2] = a21;
+        if (r1 && r2) A[q1 * m + q2] = a22;
+      }
+      // columns p, q of V
+      for (int e = tid; e < np * m; e += nt) {
+        const int k = e / m, row = e % m;
+        if (pr_q[k] >= m || !nonzero(cs_s[k])) continue;
+        rot2(V[row * m + pr_p[k]], V[row * m + pr_q[k]], cs_c[k], cs_s[k]);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// SMEM: the matrices live in dynamic shared memory (the address space is a compile-time
+// property, so every access is a shared-memory instruction); otherwise in the global workspace.
+template <bool SMEM>
 __global__ void __launch_bounds__(RR_THREADS) k_rayleigh_ritz(int m, const double* __restrict__ G,
                                                               const double* __restrict__ Mi, double* __restrict__ theta,
                                                               double* __restrict__ C, int32_t* __restrict__ info,
-                                                              double* __restrict__ work) {
-  double* A = work;          // m x m
-  double* L = work + m * m;  // m x m, lower Cholesky factor
+                                                              double* __restrict__ work, int chol_only) {
+  extern __shared__ __align__(16) unsigned char rr_sm[];
+  double* base = SMEM ? reinterpret_cast<double*>(rr_sm) : work;
+  double* A = base;          // m x m
+  double* L = base + m * m;  // m x m, lower Cholesky factor
   double* V = L + m * m;     // m x m, eigenvectors
   __shared__ double cs_c[96], cs_s[96];
   __shared__ int pr_p[96], pr_q[96];
-  __shared__ double red[RR_THREADS / 32];
+  __shared__ double red[64];
   __shared__ int s_fail;
   __shared__ double s_off, s_fro;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -68,6 +179,18 @@ __global__ void __launch_bounds__(RR_THREADS) k_rayleigh_ritz(int m, const doubl
     if (tid == 0) *info = s_fail;
     return;
   }
+  if (chol_only) {  // Cholesky-QR: C = L^{-T} (columns of the identity through the back substitution)
+    for (int j = tid; j < m; j += nt) {
+      theta[j] = 1.0;
+      for (int i = m - 1; i >= 0; i--) {
+        double s = (i == j) ? 1.0 : 0.0;
+        for (int t = i + 1; t < m; t++) s -= L[t * m + i] * C[t * m + j];
+        C[i * m + j] = s / L[i * m + i];
+      }
+    }
+    if (tid == 0) *info = 0;
+    return;
+  }
   // 2a. A <- L^{-1} A: forward substitution, one column per thread
   for (int c = tid; c < m; c += nt)
     for (int i = 0; i < m; i++) {
@@ -94,71 +217,8 @@ __global__ void __launch_bounds__(RR_THREADS) k_rayleigh_ritz(int m, const doubl
   }
   __syncthreads();
 
-  // 3. parallel cyclic Jacobi
-  const int mp = m + (m & 1);  // players incl. a dummy when m is odd
-  const int npairs = mp / 2;
-  for (int sweep = 0; sweep < 40; sweep++) {
-    // convergence: off-diagonal Frobenius norm vs the whole
-    double off = 0.0, fro = 0.0;
-    for (int e = tid; e < mm; e += nt) {
-      const double x = A[e];
-      fro += x * x;
-      if (e / m != e % m) off += x * x;
-    }
-    for (int o = 16; o > 0; o >>= 1) { off += __shfl_down_sync(0xFFFFFFFFu, off, o); fro += __shfl_down_sync(0xFFFFFFFFu, fro, o); }
-    if (tid % 32 == 0) red[tid / 32] = off;
-    __syncthreads();
-    if (tid == 0) { double s = 0; for (int w = 0; w < nt / 32; w++) s += red[w]; s_off = s; }
-    __syncthreads();
-    if (tid % 32 == 0) red[tid / 32] = fro;
-    __syncthreads();
-    if (tid == 0) { double s = 0; for (int w = 0; w < nt / 32; w++) s += red[w]; s_fro = s; }
-    __syncthreads();
-    if (s_off <= 1e-30 * s_fro || s_off == 0.0) break;
-    for (int round = 0; round < mp - 1; round++) {
-      for (int k = tid; k < npairs; k += nt) {
-        int p = rr_player(k, round, mp), q = rr_player(mp - 1 - k, round, mp);
-        if (p > q) { int t = p; p = q; q = t; }
-        double c = 1.0, s = 0.0;
-        if (q < m) {
-          const double apq = A[p * m + q];
-          if (apq != 0.0) {
-            const double tau = (A[q * m + q] - A[p * m + p]) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
-          }
-        }
-        pr_p[k] = p; pr_q[k] = q; cs_c[k] = c; cs_s[k] = s;
-      }
-      __syncthreads();
-      // rows p, q of A
-      for (int e = tid; e < npairs * m; e += nt) {
-        const int k = e / m, col = e % m;
-        const int p = pr_p[k], q = pr_q[k];
-        if (q >= m || cs_s[k] == 0.0) continue;
-        const double c = cs_c[k], s = cs_s[k];
-        const double ap = A[p * m + col], aq = A[q * m + col];
-        A[p * m + col] = c * ap - s * aq;
-        A[q * m + col] = s * ap + c * aq;
-      }
-      __syncthreads();
-      // columns p, q of A and of V
-      for (int e = tid; e < npairs * m; e += nt) {
-        const int k = e / m, row = e % m;
-        const int p = pr_p[k], q = pr_q[k];
-        if (q >= m || cs_s[k] == 0.0) continue;
-        const double c = cs_c[k], s = cs_s[k];
-        const double ap = A[row * m + p], aq = A[row * m + q];
-        A[row * m + p] = c * ap - s * aq;
-        A[row * m + q] = s * ap + c * aq;
-        const double vp = V[row * m + p], vq = V[row * m + q];
-        V[row * m + p] = c * vp - s * vq;
-        V[row * m + q] = s * vp + c * vq;
-      }
-      __syncthreads();
-    }
-  }
+  // 3. cyclic Jacobi (round-robin order, 2x2-block updates)
+  jacobi_blocks<double>(m, A, V, 1e-30, cs_c, cs_s, pr_p, pr_q, red, &s_off, &s_fro);
   // 4. rank sort (ties by index), C = L^{-T} V in the sorted order
   for (int j = tid; j < m; j += nt) {
     const double wj = A[j * m + j];
@@ -182,17 +242,20 @@ __global__ void __launch_bounds__(RR_THREADS) k_rayleigh_ritz(int m, const doubl
 // pipes with ~48-bit significands; only scalar work per pivot or per rotation (square roots,
 // reciprocals, rotation angles, convergence sums) is done in FP64. The workspace holds the
 // three m x m matrices as (hi, lo) pairs.
+template <bool SMEM>
 __global__ void __launch_bounds__(RR_THREADS) k_rayleigh_ritz_df(int m, const double* __restrict__ G,
                                                                  const double* __restrict__ Mi,
                                                                  double* __restrict__ theta, double* __restrict__ C,
-                                                                 int32_t* __restrict__ info, double* __restrict__ work) {
-  d2* A = reinterpret_cast<d2*>(work);
+                                                                 int32_t* __restrict__ info, double* __restrict__ work,
+                                                                 int chol_only) {
+  extern __shared__ __align__(16) unsigned char rr_sm[];
+  d2* A = SMEM ? reinterpret_cast<d2*>(rr_sm) : reinterpret_cast<d2*>(work);
   d2* L = A + m * m;
   d2* V = L + m * m;
   __shared__ d2 cs_c[96], cs_s[96];
   __shared__ int pr_p[96], pr_q[96];
   __shared__ d2 inv[192];
-  __shared__ double red[RR_THREADS / 32];
+  __shared__ double red[64];
   __shared__ int s_fail;
   __shared__ double s_off, s_fro;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -209,12 +272,12 @@ __global__ void __launch_bounds__(RR_THREADS) k_rayleigh_ritz_df(int m, const do
   // 1. Cholesky (right-looking); inv[j] = 1 / L_jj
   for (int j = 0; j < m; j++) {
     if (tid == 0) {
-      const double d = d2_to(L[j * m + j]);
-      if (!(d > 0.0)) s_fail = j + 1;
+      const d2 d = d2_norm(L[j * m + j]);
+      if (!(d.hi > 0.f)) s_fail = j + 1;
       else {
-        const double sq = sqrt(d);
-        L[j * m + j] = d2_from(sq);
-        inv[j] = d2_from(1.0 / sq);
+        const d2 ri = d2_rsqrt(d);  // 1 / sqrt(d)
+        L[j * m + j] = d2_mul(d, ri);
+        inv[j] = ri;
       }
     }
     __syncthreads();
@@ -236,6 +299,22 @@ __global__ void __launch_bounds__(RR_THREADS) k_rayleigh_ritz_df(int m, const do
   }
   if (s_fail) {
     if (tid == 0) *info = s_fail;
+    return;
+  }
+  if (chol_only) {  // Cholesky-QR: C = L^{-T}
+    for (int j = tid; j < m; j += nt) {
+      theta[j] = 1.0;
+      for (int i = m - 1; i >= 0; i--) {
+        d2 s{(i == j) ? 1.f : 0.f, 0.f};
+        for (int t = i + 1; t < m; t++) {
+          const d2 l = L[t * m + i], x = V[t * m + j];
+          df_mac(s.hi, s.lo, -l.hi, -l.lo, x.hi, x.lo);
+        }
+        V[i * m + j] = d2_mul(d2_norm(s), inv[i]);
+      }
+      for (int i = 0; i < m; i++) C[i * m + j] = d2_to(V[i * m + j]);
+    }
+    if (tid == 0) *info = 0;
     return;
   }
   // 2a. A <- L^{-1} A (columns), 2b. A <- A L^{-T} (rows)
@@ -263,59 +342,11 @@ __global__ void __launch_bounds__(RR_THREADS) k_rayleigh_ritz_df(int m, const do
     }
   }
   __syncthreads();
-  // 3. parallel cyclic Jacobi, rotations computed in FP64 and applied in double-float
-  const int mp = m + (m & 1), npairs = mp / 2;
-  for (int sweep = 0; sweep < 40; sweep++) {
-    double off = 0.0, fro = 0.0;
-    for (int e = tid; e < mm; e += nt) {
-      const double x = d2_hi64(A[e]);
-      fro += x * x;
-      if (e / m != e % m) off += x * x;
-    }
-    for (int o = 16; o > 0; o >>= 1) { off += __shfl_down_sync(0xFFFFFFFFu, off, o); fro += __shfl_down_sync(0xFFFFFFFFu, fro, o); }
-    if (tid % 32 == 0) red[tid / 32] = off;
-    __syncthreads();
-    if (tid == 0) { double s = 0; for (int w = 0; w < nt / 32; w++) s += red[w]; s_off = s; }
-    __syncthreads();
-    if (tid % 32 == 0) red[tid / 32] = fro;
-    __syncthreads();
-    if (tid == 0) { double s = 0; for (int w = 0; w < nt / 32; w++) s += red[w]; s_fro = s; }
-    __syncthreads();
-    if (s_off <= 1e-30 * s_fro || s_off == 0.0) break;
-    for (int round = 0; round < mp - 1; round++) {
-      for (int k = tid; k < npairs; k += nt) {
-        int p = rr_player(k, round, mp), q = rr_player(mp - 1 - k, round, mp);
-        if (p > q) { int t = p; p = q; q = t; }
-        double c = 1.0, s = 0.0;
-        if (q < m) {
-          const double apq = d2_to(A[p * m + q]);
-          if (apq != 0.0) {
-            const double tau = (d2_to(A[q * m + q]) - d2_to(A[p * m + p])) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
-            s = t * c;
-          }
-        }
-        pr_p[k] = p; pr_q[k] = q; cs_c[k] = d2_from(c); cs_s[k] = d2_from(s);
-      }
-      __syncthreads();
-      for (int e = tid; e < npairs * m; e += nt) {
-        const int k = e / m, col = e % m;
-        const int p = pr_p[k], q = pr_q[k];
-        if (q >= m || cs_s[k].hi == 0.f) continue;
-        d2_rot(A[p * m + col], A[q * m + col], cs_c[k], cs_s[k]);
-      }
-      __syncthreads();
-      for (int e = tid; e < npairs * m; e += nt) {
-        const int k = e / m, row = e % m;
-        const int p = pr_p[k], q = pr_q[k];
-        if (q >= m || cs_s[k].hi == 0.f) continue;
-        d2_rot(A[row * m + p], A[row * m + q], cs_c[k], cs_s[k]);
-        d2_rot(V[row * m + p], V[row * m + q], cs_c[k], cs_s[k]);
-      }
-      __syncthreads();
-    }
-  }
+  // 3. cyclic Jacobi (round-robin order, 2x2-block updates) in double-float. Double-float carries
+  // ~48 significant bits, so the off-diagonal part cannot fall much below 2^-46 of the whole;
+  // stop at ||off|| <= 1e-10 ||A|| (quadratic convergence: the Ritz values then carry errors of
+  // order ||off||^2 / gap, far below the FP64 target).
+  jacobi_blocks<d2>(m, A, V, 1e-20, cs_c, cs_s, pr_p, pr_q, red, &s_off, &s_fro);
   // 4. rank sort, C = L^{-T} V
   for (int j = tid; j < m; j += nt) {
     const double wj = d2_to(A[j * m + j]);
@@ -341,10 +372,21 @@ __global__ void __launch_bounds__(RR_THREADS) k_rayleigh_ritz_df(int m, const do
 
 }  // namespace
 
+// The three m x m matrices live in shared memory when they fit (m <= 64), else in the
+// caller's global workspace (L1-cached).
+static size_t rr_smem_bytes(int m) { return 3ull * m * m * 8; }
+static const size_t RR_SMEM_MAX = 200 * 1024;
+
 int lob_rr_launch_df(int m, const double* G, const double* M, double* theta, double* C, int32_t* info, double* work,
-                     cudaStream_t st) {
+                     cudaStream_t st, int chol_only) {
   if (m < 1 || m > 192) return LOB_ERR_ARG;
-  (k_rayleigh_ritz_df<<<1, RR_THREADS, 0, st>>>(m, G, M, theta, C, info, work), LOB_LAUNCHED());
+  const size_t sb = rr_smem_bytes(m);
+  if (sb <= RR_SMEM_MAX) {
+    LOB_CUDA(cudaFuncSetAttribute(k_rayleigh_ritz_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
+    (k_rayleigh_ritz_df<true><<<1, RR_THREADS, sb, st>>>(m, G, M, theta, C, info, work, chol_only), LOB_LAUNCHED());
+  } else {
+    (k_rayleigh_ritz_df<false><<<1, RR_THREADS, 0, st>>>(m, G, M, theta, C, info, work, chol_only), LOB_LAUNCHED());
+  }
   LOB_CUDA(cudaGetLastError());
   return LOB_OK;
 }
@@ -352,9 +394,15 @@ int lob_rr_launch_df(int m, const double* G, const double* M, double* theta, dou
 size_t lob_rr_work_doubles(int m) { return 3ull * m * m; }
 
 int lob_rr_launch(int m, const double* G, const double* M, double* theta, double* C, int32_t* info, double* work,
-                  cudaStream_t st) {
+                  cudaStream_t st, int chol_only) {
   if (m < 1 || m > 192) return LOB_ERR_ARG;
-  (k_rayleigh_ritz<<<1, RR_THREADS, 0, st>>>(m, G, M, theta, C, info, work), LOB_LAUNCHED());
+  const size_t sb = rr_smem_bytes(m);
+  if (sb <= RR_SMEM_MAX) {
+    LOB_CUDA(cudaFuncSetAttribute(k_rayleigh_ritz<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
+    (k_rayleigh_ritz<true><<<1, RR_THREADS, sb, st>>>(m, G, M, theta, C, info, work, chol_only), LOB_LAUNCHED());
+  } else {
+    (k_rayleigh_ritz<false><<<1, RR_THREADS, 0, st>>>(m, G, M, theta, C, info, work, chol_only), LOB_LAUNCHED());
+  }
   LOB_CUDA(cudaGetLastError());
   return LOB_OK;
 }

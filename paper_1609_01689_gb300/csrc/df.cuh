@@ -167,3 +167,12 @@ __device__ __forceinline__ void d2_rot(d2& x, d2& y, d2 c, d2 s) {
   x = d2_norm(u);
   y = d2_norm(v);
 }
+// 1/sqrt(x) for x > 0 in double-float: FP32 estimate refined by one Newton step done in
+// double-float (y1 = y0 + y0 (1 - x y0^2) / 2; relative error ~ (3/2) e0^2 ~ 2^-43).
+__device__ __forceinline__ d2 d2_rsqrt(d2 x) {
+  const float y0 = rsqrtf(x.hi);
+  const d2 y2 = d2_mul(d2{y0, 0.f}, d2{y0, 0.f});
+  const d2 r = d2_add(d2{1.f, 0.f}, d2_neg(d2_mul(x, y2)));
+  const d2 corr = d2_mul(d2{0.5f * y0, 0.f}, r);
+  return d2_add(d2{y0, 0.f}, corr);
+}

@@ -212,9 +212,10 @@ struct Solver {
   double* ph(int i) { return (timing && stats) ? &stats->phase_ms[i] : nullptr; }
 
   // projected eigenproblem in the solver's block arithmetic (native FP64 or double-float)
-  int rr(int m, const double* Gp, const double* Mp, double* th, double* Cp) {
-    if (blas_mode == LOB_SPMM_MIXED) return lob_rr_launch_df(m, Gp, Mp, th, Cp, (int32_t*)info_d.p, rrwork.p, st);
-    return lob_rr_launch(m, Gp, Mp, th, Cp, (int32_t*)info_d.p, rrwork.p, st);
+  int rr(int m, const double* Gp, const double* Mp, double* th, double* Cp, int chol_only = 0) {
+    if (blas_mode == LOB_SPMM_MIXED)
+      return lob_rr_launch_df(m, Gp, Mp, th, Cp, (int32_t*)info_d.p, rrwork.p, st, chol_only);
+    return lob_rr_launch(m, Gp, Mp, th, Cp, (int32_t*)info_d.p, rrwork.p, st, chol_only);
   }
 
   int spmm(const double* X, int ldx, double* Y, int ldy, int ncol) {
@@ -228,14 +229,17 @@ struct Solver {
     if (ldy != ncol) dst = THp.p;
     {
       Timer t(st, ph(PH_SPMM));  // the SpMM launch itself (zeroing of Y and the kernel)
+      Timer tm(st, (timing && stats) ? &stats->spmm_ms_mode[spmm_mode] : nullptr);
       LOB_TRY(lob_spmm_launch(M, spmm_mode, src, dst, ncol, n_act, st));
     }
     if (ldy != ncol) (k_copy_cols<<<nblk(n * ncol), BS, 0, st>>>(n, ncol, THp.p, ncol, nullptr, Y, ldy), LOB_LAUNCHED());
     if (stats) {
       stats->spmm_calls++;
-      const double vb = spmm_mode == LOB_SPMM_MIXED ? 4.0 : 8.0;
-      stats->spmm_bytes += (double)M->T.nnz * (vb + 4.0) + (double)M->T.ntiles * 12.0 +
-                           (double)n * ncol * 16.0;
+      const double vb = spmm_mode == LOB_SPMM_MIXED ? 4.0 : 8.0;  // FP32 or FP64 (split pair) values
+      const double bytes = (double)M->T.nnz * (vb + 4.0) + (double)M->T.ntiles * 12.0 + (double)n * ncol * 16.0;
+      stats->spmm_bytes += bytes;
+      stats->spmm_bytes_mode[spmm_mode] += bytes;
+      stats->spmm_calls_mode[spmm_mode]++;
     }
     LOB_CUDA(cudaGetLastError());
     return LOB_OK;
@@ -263,7 +267,7 @@ struct Solver {
     Timer t(st, ph(PH_ORTH));
     const double* B = S.p + col0;
     LOB_TRY(lob_gram_launch_ws(n_act, ncol, B, ldS, ncol, B, ldS, Mm.p, blas_mode, work.p, st));
-    LOB_TRY(rr(ncol, Mm.p, Mm.p, thw.p, Cc.p));
+    LOB_TRY(rr(ncol, Mm.p, Mm.p, thw.p, Cc.p, 1));
     int hinfo = 0;
     LOB_CUDA(cudaMemcpyAsync(&hinfo, info_d.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     LOB_CUDA(cudaStreamSynchronize(st));
@@ -491,7 +495,7 @@ int lob_solve_impl(lob_matrix* m, int32_t k, int32_t nb, double tol, const doubl
     status = S.run(tol1, max_iter, o->precond != 0, o->precond_shift, &iters, &restarts);
     if (status != LOB_OK && status != LOB_ERR_NOCONV) return status;
     int it2 = 0, rs2 = 0;
-    S.spmm_mode = LOB_SPMM_FP64;
+    S.spmm_mode = m->T.v32lo ? LOB_SPMM_DF64 : LOB_SPMM_FP64;  // FP64-class refinement products
     const int max2 = o->refine_iter > 0 ? o->refine_iter : 50;
     status = S.run(tol, max2, o->precond != 0, o->precond_shift, &it2, &rs2);
     if (st) st->refine_iterations = it2;

@@ -295,6 +295,220 @@ __global__ void __launch_bounds__(Cfg<MIXED, NB>::THREADS, 1)
   }
 }
 
+// FP64-class variant (LOB_SPMM_DF64): values as (hi, lo) FP32 pairs (hi = the FP32 value,
+// lo = the rounded remainder, ~48 significant bits together), X staged as (hi, lo) pairs, every
+// product and sum in double-float (df.cuh) on the FP32 pipes. Same schedule as k_spmm4: lane
+// group g owns in-tile rows/columns g, g + NG, ...; each lane holds VW = 2 vector columns.
+template <int NB>
+struct CfgDF {
+  static constexpr int VW = 2;
+  static constexpr int G = NB / VW;
+  static constexpr int THREADS = (LOB_TILE * G) < 1024 ? (LOB_TILE * G) : 1024;
+  static constexpr int NG = THREADS / G;
+  static constexpr int RPG = LOB_TILE / NG;
+  static constexpr int CH = LOB_PERM_CHUNK;
+  static constexpr int PTRS = 2 * (LOB_TILE + 1);
+  static constexpr size_t XV = sizeof(float2) * LOB_TILE * NB;
+  static constexpr size_t XI = 0;
+  static constexpr size_t XJ = XI + XV;
+  static constexpr size_t RC = XJ + 2 * XV;
+  static constexpr size_t VH = RC + 2 * 4 * CH;
+  static constexpr size_t VL = VH + 2 * 4 * CH;
+  static constexpr size_t PM = VL + 2 * 4 * CH;
+  static constexpr size_t PT = PM + 2 * 2 * (CH + 8);
+  static constexpr size_t BYTES = PT + 2 * 2 * PTRS;
+};
+
+__global__ void k_stage_x_df(int64_t rows, int64_t n_act, int nb, int c0, int w, int NB, const double* __restrict__ X,
+                             float2* __restrict__ Xs) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= rows * NB) return;
+  const int64_t i = t / NB;
+  const int j = (int)(t % NB);
+  const double v = (j < w && i < n_act) ? X[i * nb + c0 + j] : 0.0;
+  Xs[t] = df_split(v);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(CfgDF<NB>::THREADS, 1)
+    k_spmm4df(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ tcol, const int64_t* __restrict__ tptr,
+              const int32_t* __restrict__ tchunk, const uint32_t* __restrict__ rc, const float* __restrict__ vhi,
+              const float* __restrict__ vlo, const uint16_t* __restrict__ cperm, const uint16_t* __restrict__ cptrs,
+              const float2* __restrict__ Xs, double* __restrict__ Y, int ldy, int c0, int w, int64_t n_act) {
+  using C = CfgDF<NB>;
+  constexpr int VW = C::VW, G = C::G, NG = C::NG, RPG = C::RPG, CH = C::CH, THREADS = C::THREADS;
+  constexpr int XN = LOB_TILE * NB;
+  extern __shared__ __align__(16) unsigned char sm[];
+  float2* XI = reinterpret_cast<float2*>(sm + C::XI);
+  float2* XJb = reinterpret_cast<float2*>(sm + C::XJ);
+  uint32_t* RCb = reinterpret_cast<uint32_t*>(sm + C::RC);
+  float* VHb = reinterpret_cast<float*>(sm + C::VH);
+  float* VLb = reinterpret_cast<float*>(sm + C::VL);
+  uint16_t* PMb = reinterpret_cast<uint16_t*>(sm + C::PM);
+  uint16_t* PTb = reinterpret_cast<uint16_t*>(sm + C::PT);
+
+  const int64_t I = blockIdx.x;
+  const int64_t row0 = I * LOB_TILE;
+  const int tid = threadIdx.x;
+  const int g = tid / G, gl = tid % G;
+  const int64_t t0 = rowptr[I];
+  int64_t t1 = rowptr[I + 1];
+  while (t1 > t0 && (int64_t)tcol[t1 - 1] * LOB_TILE >= n_act) t1--;
+
+  for (int e = tid * 2; e < XN; e += THREADS * 2) cp_async16(&XI[e], &Xs[row0 * NB + e]);
+  cp_async_commit();
+
+  auto issue = [&](int64_t t, int64_t k, int buf, int xbuf) {
+    const int64_t J = tcol[t];
+    if (k == 0 && J != I) {
+      float2* XJ = XJb + xbuf * XN;
+      const float2* src = Xs + J * LOB_TILE * NB;
+      for (int e = tid * 2; e < XN; e += THREADS * 2) cp_async16(&XJ[e], &src[e]);
+    }
+    const int64_t base = tptr[t] + k * CH;
+    const int64_t rem = tptr[t + 1] - base;
+    const int cnt = (int)(rem < CH ? rem : CH);
+    for (int i = tid; i < cnt; i += THREADS) {
+      cp_async4(&RCb[buf * CH + i], &rc[base + i]);
+      cp_async4(&VHb[buf * CH + i], &vhi[base + i]);
+      cp_async4(&VLb[buf * CH + i], &vlo[base + i]);
+    }
+    uint32_t* PM32 = reinterpret_cast<uint32_t*>(PMb + buf * (CH + 8));
+    const int64_t wb = base & ~(int64_t)1;
+    const int nwords = (int)((base + cnt - wb + 1) / 2);
+    const uint32_t* src32 = reinterpret_cast<const uint32_t*>(cperm + wb);
+    for (int i = tid; i < nwords; i += THREADS) cp_async4(&PM32[i], &src32[i]);
+    uint32_t* PT32 = reinterpret_cast<uint32_t*>(PTb + buf * C::PTRS);
+    const uint32_t* srcp = reinterpret_cast<const uint32_t*>(cptrs + (int64_t)(tchunk[t] + k) * C::PTRS);
+    for (int i = tid; i < C::PTRS / 2; i += THREADS) cp_async4(&PT32[i], &srcp[i]);
+    cp_async_commit();
+  };
+
+  // per owned index a and lane column q: tile row partial, column partial, row accumulator (all df)
+  float th[RPG][VW], tlo[RPG][VW], chh[RPG][VW], clo[RPG][VW], rh[RPG][VW], rl[RPG][VW];
+#pragma unroll
+  for (int a = 0; a < RPG; a++)
+#pragma unroll
+    for (int q = 0; q < VW; q++) { th[a][q] = tlo[a][q] = chh[a][q] = clo[a][q] = rh[a][q] = rl[a][q] = 0.f; }
+
+  int64_t t = t0, k = 0;
+  int tl = 0, buf = 0;
+  if (t < t1) issue(t, 0, 0, 0);
+  while (t < t1) {
+    const int64_t J = tcol[t];
+    const bool diag = (J == I);
+    const bool last = (tptr[t] + (k + 1) * CH >= tptr[t + 1]);
+    int64_t tn = t, kn = k + 1;
+    int tln = tl;
+    if (last) { tn = t + 1; kn = 0; tln = tl + 1; }
+    if (tn < t1) { issue(tn, kn, buf ^ 1, tln & 1); cp_async_wait_1(); } else { cp_async_wait_all(); }
+    __syncthreads();
+    const uint32_t* RCs = RCb + buf * CH;
+    const float* VH = VHb + buf * CH;
+    const float* VL = VLb + buf * CH;
+    const uint16_t* PM = PMb + buf * (CH + 8) + (int)((tptr[t] + k * CH) & 1);
+    const uint16_t* PR = PTb + buf * C::PTRS;
+    const uint16_t* PC = PR + (LOB_TILE + 1);
+    const float2* xj = diag ? XI : XJb + (tl & 1) * XN;
+#pragma unroll
+    for (int a = 0; a < RPG; a++) {
+      const int idx = g + a * NG;
+      {
+        const int s = PR[idx], e = PR[idx + 1];
+        for (int i = s; i < e; i++) {
+          const int c = (int)(RCs[i] & 0xFFFFu);
+          const float4 x = *reinterpret_cast<const float4*>(&xj[c * NB + gl * VW]);  // (h0, l0, h1, l1)
+          const float vh = VH[i], vl = VL[i];
+          df_mac(th[a][0], tlo[a][0], vh, vl, x.x, x.y);
+          df_mac(th[a][1], tlo[a][1], vh, vl, x.z, x.w);
+        }
+      }
+      {
+        const int s = PC[idx], e = PC[idx + 1];
+        for (int i = s; i < e; i++) {
+          const int q = PM[i] & (CH - 1);
+          const int r = (int)(RCs[q] >> 16);
+          if (diag && r == idx) continue;
+          const float4 x = *reinterpret_cast<const float4*>(&XI[r * NB + gl * VW]);
+          const float vh = VH[q], vl = VL[q];
+          df_mac(chh[a][0], clo[a][0], vh, vl, x.x, x.y);
+          df_mac(chh[a][1], clo[a][1], vh, vl, x.z, x.w);
+        }
+      }
+    }
+    if (last) {
+#pragma unroll
+      for (int a = 0; a < RPG; a++) {
+        const int idx = g + a * NG;
+#pragma unroll
+        for (int q = 0; q < VW; q++) {
+          df_renorm(th[a][q], tlo[a][q]);
+          df_renorm(chh[a][q], clo[a][q]);
+          df_add(rh[a][q], rl[a][q], th[a][q], tlo[a][q]);
+          if (diag) {
+            df_add(rh[a][q], rl[a][q], chh[a][q], clo[a][q]);
+          } else {
+            const int kk = gl * VW + q;
+            const int64_t gr = J * LOB_TILE + idx;
+            if (kk < w && gr < n_act) {
+              atomic_out(&Y[gr * ldy + c0 + kk], chh[a][q]);
+              atomic_out(&Y[gr * ldy + c0 + kk], clo[a][q]);
+            }
+          }
+          th[a][q] = tlo[a][q] = chh[a][q] = clo[a][q] = 0.f;
+        }
+      }
+    }
+    __syncthreads();
+    t = tn; k = kn; tl = tln; buf ^= 1;
+  }
+  cp_async_wait_all();
+#pragma unroll
+  for (int a = 0; a < RPG; a++) {
+    const int64_t gr = row0 + g + a * NG;
+#pragma unroll
+    for (int q = 0; q < VW; q++) {
+      const int kk = gl * VW + q;
+      if (kk >= w || gr >= n_act) continue;
+      df_renorm(rh[a][q], rl[a][q]);
+      atomic_out(&Y[gr * ldy + c0 + kk], rh[a][q]);
+      atomic_out(&Y[gr * ldy + c0 + kk], rl[a][q]);
+    }
+  }
+}
+
+template <int NB>
+int launch_df(const lob_matrix* m, const double* X, double* Y, int nb, int64_t n_act, cudaStream_t st) {
+  using C = CfgDF<NB>;
+  static_assert(C::BYTES <= 227 * 1024, "shared memory budget");
+  const lob_tiles& TS = m->T;
+  const int64_t nt_act = (n_act + LOB_TILE - 1) / LOB_TILE;
+  if (nt_act == 0) return LOB_OK;
+  const int64_t rows_pad = TS.nt * LOB_TILE;
+  const size_t need = (size_t)rows_pad * NB * sizeof(float2);
+  lob_matrix* mm = const_cast<lob_matrix*>(m);
+  if (mm->xs_bytes < need) {
+    cudaFree(mm->xs);
+    mm->xs = nullptr;
+    mm->xs_bytes = 0;
+    if (cudaMalloc(&mm->xs, need) != cudaSuccess) { cudaGetLastError(); return LOB_ERR_NOMEM; }
+    mm->xs_bytes = need;
+  }
+  float2* Xs = reinterpret_cast<float2*>(mm->xs);
+  auto kern = k_spmm4df<NB>;
+  LOB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES));
+  for (int c0 = 0; c0 < nb; c0 += NB) {
+    const int w = (nb - c0) < NB ? (nb - c0) : NB;
+    (k_stage_x_df<<<(unsigned)((rows_pad * NB + 255) / 256), 256, 0, st>>>(rows_pad, n_act, nb, c0, w, NB, X, Xs),
+     LOB_LAUNCHED());
+    (kern<<<(unsigned)nt_act, C::THREADS, C::BYTES, st>>>(TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rc, TS.v32,
+                                                           TS.v32lo, TS.cperm, TS.cptrs, Xs, Y, nb, c0, w, n_act),
+     LOB_LAUNCHED());
+  }
+  LOB_CUDA(cudaGetLastError());
+  return LOB_OK;
+}
+
 template <bool MIXED, int NB>
 int launch(const lob_matrix* m, const double* X, double* Y, int nb, int64_t n_act, cudaStream_t st) {
   using C = Cfg<MIXED, NB>;
@@ -338,8 +552,15 @@ int lob_spmm_launch(const lob_matrix* m, int mode, const double* X, double* Y, i
   if (nb < 1 || nb > 64 || n_act < 0 || n_act > m->T.n) return LOB_ERR_ARG;
   if (mode == LOB_SPMM_MIXED && !m->T.v32) return LOB_ERR_ARG;
   if (mode == LOB_SPMM_FP64 && !m->T.v64) return LOB_ERR_ARG;
-  if (mode != LOB_SPMM_MIXED && mode != LOB_SPMM_FP64) return LOB_ERR_ARG;
+  if (mode == LOB_SPMM_DF64 && !m->T.v32lo) return LOB_ERR_ARG;
+  if (mode != LOB_SPMM_MIXED && mode != LOB_SPMM_FP64 && mode != LOB_SPMM_DF64) return LOB_ERR_ARG;
   LOB_CUDA(cudaMemsetAsync(Y, 0, (size_t)m->T.n * nb * sizeof(double), st));
+  if (mode == LOB_SPMM_DF64) {
+    if (nb <= 2) return launch_df<2>(m, X, Y, nb, n_act, st);
+    if (nb <= 4) return launch_df<4>(m, X, Y, nb, n_act, st);
+    if (nb <= 8) return launch_df<8>(m, X, Y, nb, n_act, st);
+    return launch_df<16>(m, X, Y, nb, n_act, st);
+  }
   if (mode == LOB_SPMM_MIXED) {
     if (nb <= 4) return launch<true, 4>(m, X, Y, nb, n_act, st);
     if (nb <= 8) return launch<true, 8>(m, X, Y, nb, n_act, st);

@@ -150,6 +150,14 @@ __global__ void k_chunk_ptrs(int64_t ntiles, const int64_t* __restrict__ tptr, c
   }
 }
 
+// Low parts of the values: v64 - v32, rounded to FP32 (so v32 + v32lo carries ~48 bits).
+__global__ void k_value_lo(int64_t nnz, const double* __restrict__ v64, const float* __restrict__ v32,
+                           float* __restrict__ lo) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nnz) return;
+  lo[k] = __double2float_rn(v64[k] - (double)v32[k]);
+}
+
 __global__ void k_absrow(int64_t nnz, const int64_t* __restrict__ row, const int64_t* __restrict__ col,
                          const double* __restrict__ val, double* __restrict__ s) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -166,7 +174,7 @@ inline unsigned nblocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs
 void lob_free_tiles(lob_tiles* T) {
   cudaFree(T->rowptr); cudaFree(T->tcol); cudaFree(T->trow); cudaFree(T->tptr);
   cudaFree(T->rc); cudaFree(T->v64); cudaFree(T->v32); cudaFree(T->cperm);
-  cudaFree(T->tchunk); cudaFree(T->cptrs);
+  cudaFree(T->tchunk); cudaFree(T->cptrs); cudaFree(T->v32lo);
   *T = lob_tiles();
 }
 
@@ -288,6 +296,11 @@ int lob_build_tiles(const lob_coo* H, int values, cudaStream_t st, lob_tiles* T,
     }
     (k_chunk_ptrs<<<(unsigned)R.nchunks, 256, 0, st>>>(ntiles, R.tptr, R.tchunk, R.rc, R.cptrs), LOB_LAUNCHED());
     LOB_CUDA(cudaStreamSynchronize(st));
+  }
+
+  if (R.v64 && R.v32) {
+    if (cudaMalloc(&R.v32lo, nnz * 4) != cudaSuccess) { cudaGetLastError(); lob_free_tiles(&R); return LOB_ERR_NOMEM; }
+    (k_value_lo<<<nblocks(nnz, bs), bs, 0, st>>>(nnz, R.v64, R.v32, R.v32lo), LOB_LAUNCHED());
   }
 
   // ||H||_inf over the full symmetric matrix

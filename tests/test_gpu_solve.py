@@ -87,3 +87,33 @@ def test_solve_rejects_bad_args(c1):
         M.solve(9, 8, 1e-8)  # k > nb
     with pytest.raises(lob.LobError):
         M.solve(5, 8, 1e-8, precond=True)  # no preconditioner built
+
+
+@pytest.fixture(scope="module")
+def c2_golden():
+    """Reference eigenvalues of the n = 500,000 workload, stored by tests/golden/make_golden.py
+    from the oracle's FP64 Lanczos."""
+    import os
+    from conftest import golden_path
+    vals = [float(x) for x in open(golden_path("c2_eigs.txt")) if x.strip() and not x.startswith("#")]
+    return np.array(vals)
+
+
+@pytest.mark.parametrize("mode,tol_lam", [("mixed", 1e-8), ("fp64", 1e-9)])
+def test_solve_full_size_500k(c2_golden, mode, tol_lam):
+    """The n = 500,000 workload (k = 8, nb = 16, b_p = 32, eq. 12 guess from levels {0, 1}):
+    eigenvalues against the stored oracle values, residuals against the oracle's SpMM."""
+    import torch
+    import paper_1609_01689_gb300 as lob
+    L = synth.config_layout("c2")
+    r, c, v = synth.generate_device(L)
+    M = lob.Matrix(L.n, r, c, v, precond_block=32)
+    n_small = int(synth.level_starts(L)[2])
+    lam, X, st, rc = M.solve(8, 16, 1e-8, mode=mode, precond=True, n_small=n_small)
+    assert rc == lob.LOB_OK
+    rel = np.abs(lam - c2_golden[:8]) / np.maximum(np.abs(c2_golden[:8]), 1.0)
+    assert rel.max() <= tol_lam, rel
+    rows, cols, vals = synth.generate(L)
+    H = oracle.Coo(L.n, rows, cols, vals)
+    res = oracle.residual_norms(H, X.cpu().numpy()[:, :8], lam) / oracle.norm_inf(H)
+    assert res.max() <= 1e-8, res

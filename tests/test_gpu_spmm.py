@@ -97,3 +97,21 @@ def test_spmm_full_size_500k(c2, mode):
     m = row_counts(H)[:, None]
     bound = (2 * (m + 2) * U64 if mode == "fp64" else 2 * (m + 4) * U32) * bound_base
     assert np.all(np.abs(Y - Yref) <= bound)
+
+
+@pytest.mark.parametrize("nb", [1, 2, 5, 8, 16, 24])
+def test_spmm_df64_integer_exact_and_fp64_class(nb):
+    """FP64-class double-float products (LOB_SPMM_DF64): exact on small integers; on random data
+    within the FP64 bound with a double-float unit: |Y - Y*| <= 2 (m + 2) 2^-46 (|H||X|)."""
+    import paper_1609_01689_gb300 as lob
+    rng = np.random.default_rng(300 + nb)
+    H = random_upper(900, 0.04, rng, integer=True)
+    X = rng.integers(-8, 9, (900, nb)).astype(np.float64)
+    M = lob.Matrix(H.n, H.rows, H.cols, H.vals)
+    assert np.array_equal(run(M, X, "df64"), oracle.spmm(H, X))
+    H = random_upper(900, 0.04, rng)
+    X = rng.standard_normal((900, nb))
+    M = lob.Matrix(H.n, H.rows, H.cols, H.vals)
+    Y = run(M, X, "df64")
+    bound = 2 * (row_counts(H)[:, None] + 2) * 2.0 ** -46 * oracle.spmm(abs_coo(H), np.abs(X))
+    assert np.all(np.abs(Y - oracle.spmm(H, X)) <= bound)
