@@ -140,6 +140,20 @@ int lob_precond_apply(lob_matrix* m, const double* mu, const double* R, double* 
 int lob_rayleigh_ritz(int32_t m, const double* G, const double* M, double* theta, double* C, int32_t* info,
                       int32_t mode, void* stream);
 
+/* lob_rayleigh_ritz without any device allocation. The paper has no counterpart: this is for
+ * callers that cannot call cudaMalloc -- code running under an allocator that owns the device
+ * memory (a framework's caching allocator, a fixed memory budget), or a latency-critical loop
+ * where an allocation's implicit device synchronisation is not acceptable. The caller still
+ * passes every input and output (same meaning as lob_rayleigh_ritz). The workspace is a
+ * file-scope device array sized for m <= 192 (three 192 x 192 FP64 matrices, 884,736 bytes),
+ * held by every GPU that loads the library until the process exits; m outside [1, 192]
+ * returns LOB_ERR_ARG. The first call on each device looks up the array's device address
+ * (with that device current); make that first call before any stream capture. All calls share
+ * the array: each call overwrites it completely before reading it, and calls that overlap on
+ * the GPU (other streams or host threads using the same device) race on it. */
+int lob_rayleigh_ritz_noalloc(int32_t m, const double* G, const double* M, double* theta, double* C,
+                              int32_t* info, int32_t mode, void* stream);
+
 /* ---- the solver (Algorithm 1) ---- */
 
 #define LOB_MODE_FP64 0  /* every product in FP64 (the plain solver) */

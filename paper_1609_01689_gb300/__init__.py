@@ -98,6 +98,8 @@ def _load():
     L.lob_lincomb.argtypes = [_I64, _I32, _P, _I32, _I32, _P, _P, _I32, _I32, _P]
     L.lob_precond_apply.argtypes = [_P, _P, _P, _P, _I32, _P]
     L.lob_rayleigh_ritz.argtypes = [_I32, _P, _P, _P, _P, _P, _I32, _P]
+    L.lob_rayleigh_ritz_noalloc.argtypes = [_I32, _P, _P, _P, _P, _P, _I32, _P]
+    L.lob_rayleigh_ritz_noalloc.restype = ctypes.c_int
     L.lob_solve.argtypes = [_P, _I32, _I32, _D, _P, ctypes.POINTER(SolveOpts), _P, _P, ctypes.POINTER(Stats)]
     L.lob_kernel_launches.argtypes = []
     L.lob_kernel_launches.restype = ctypes.c_longlong
@@ -285,6 +287,22 @@ def rayleigh_ritz(G, M, mode="fp64"):
     info = torch.zeros(1, dtype=torch.int32, device="cuda")
     _check(lib().lob_rayleigh_ritz(m, G.data_ptr(), M.data_ptr(), theta.data_ptr(), C.data_ptr(), info.data_ptr(),
                                    _MODES[mode], _stream()), "lob_rayleigh_ritz")
+    if int(info.item()) != 0:
+        raise np.linalg.LinAlgError(f"Gram matrix not positive definite (pivot {int(info.item())})")
+    return theta, C
+
+
+def rayleigh_ritz_noalloc(G, M, mode="fp64", theta=None, C=None, info=None):
+    """rayleigh_ritz through lob_rayleigh_ritz_noalloc: the library allocates no device memory
+    (its workspace is a fixed array for m <= 192). The caller may pass preallocated output
+    tensors; G and M must already be contiguous FP64 device tensors."""
+    torch = _torch()
+    m = G.shape[0]
+    theta = theta if theta is not None else torch.empty(m, dtype=torch.float64, device="cuda")
+    C = C if C is not None else torch.empty((m, m), dtype=torch.float64, device="cuda")
+    info = info if info is not None else torch.zeros(1, dtype=torch.int32, device="cuda")
+    _check(lib().lob_rayleigh_ritz_noalloc(m, G.data_ptr(), M.data_ptr(), theta.data_ptr(), C.data_ptr(),
+                                           info.data_ptr(), _MODES[mode], _stream()), "lob_rayleigh_ritz_noalloc")
     if int(info.item()) != 0:
         raise np.linalg.LinAlgError(f"Gram matrix not positive definite (pivot {int(info.item())})")
     return theta, C

@@ -7,6 +7,8 @@
 //      the m/2 rotations of a round act on disjoint index pairs and run in parallel,
 //   4. sort ascending, C = L^{-T} V.
 // The matrices live in a global workspace of 3 m^2 doubles (L1-resident for m <= 96).
+#include <mutex>
+
 #include "common.cuh"
 #include "df.cuh"
 
@@ -405,4 +407,45 @@ int lob_rr_launch(int m, const double* G, const double* M, double* theta, double
   }
   LOB_CUDA(cudaGetLastError());
   return LOB_OK;
+}
+
+// ---- Rayleigh-Ritz without allocation -------------------------------------------------------
+// A fixed workspace for lob_rayleigh_ritz_noalloc: three 192 x 192 FP64 matrices (884,736 bytes)
+// in a file-scope device array, so the call needs no cudaMalloc. Every GPU that loads this
+// library holds it until the process exits. All calls share it: the kernel fills it from its
+// inputs before reading it, and calls that overlap on the GPU (different streams, or different
+// host threads on one device) race on it.
+#define LOB_RR_NOALLOC_MAX_M 192
+static __device__ __align__(256) double g_rr_scratch[3 * LOB_RR_NOALLOC_MAX_M * LOB_RR_NOALLOC_MAX_M];
+
+namespace {
+std::mutex g_rr_scratch_mu;
+void* g_rr_scratch_ptr[64] = {nullptr};  // device address of g_rr_scratch, per device ordinal
+}  // namespace
+
+extern "C" int lob_rayleigh_ritz_noalloc(int32_t m, const double* G, const double* M, double* theta, double* C,
+                                         int32_t* info, int32_t mode, void* stream) {
+  if (m < 1 || m > LOB_RR_NOALLOC_MAX_M || !G || !M || !theta || !C || !info) return LOB_ERR_ARG;
+  if (mode != LOB_SPMM_FP64 && mode != LOB_SPMM_MIXED) return LOB_ERR_ARG;
+  int dev = 0;
+  LOB_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return LOB_ERR_ARG;
+  double* work = nullptr;
+  {
+    // first call on a device: look up the array's device address with that device current
+    std::lock_guard<std::mutex> lock(g_rr_scratch_mu);
+    if (!g_rr_scratch_ptr[dev]) {
+      void* ptr = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&ptr, g_rr_scratch);
+      if (e != cudaSuccess || !ptr) {
+        fprintf(stderr, "lob: cudaGetSymbolAddress of the Rayleigh-Ritz workspace failed: %s\n", cudaGetErrorString(e));
+        return LOB_ERR_CUDA;
+      }
+      g_rr_scratch_ptr[dev] = ptr;
+    }
+    work = static_cast<double*>(g_rr_scratch_ptr[dev]);
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  return mode == LOB_SPMM_MIXED ? lob_rr_launch_df(m, G, M, theta, C, info, work, st)
+                                : lob_rr_launch(m, G, M, theta, C, info, work, st);
 }
