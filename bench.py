@@ -154,6 +154,117 @@ def oracle_sample(cfg, layout):
         f"run needs to reach Ritz residual 1e-12 ||H||"))
 
 
+def replica_layout(cfg, rank):
+    """Replicas only: rank r solves its own seeded instance of the workload (seed + r)."""
+    import synth
+    base = synth.CONFIGS[cfg]
+    return synth.config_layout(cfg, seed=base["seed"] + rank)
+
+
+def reduce_max(x, dist, device):
+    """The slowest rank's time (every rank gets it); x unchanged without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def serving_requests(count, rate, seed=2024):
+    """The serving workload: Poisson arrivals (mean `rate` per second), sizes log-uniform in
+    [2,000, 200,000], k uniform in {1..8}, nb the next power of two >= k, ~30 nonzeros per row,
+    levels interpolated from the size, one generator seed per request."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, count))
+    n = np.exp(rng.uniform(np.log(2000), np.log(200000), count)).astype(np.int64)
+    k = rng.integers(1, 9, count)
+    nb = np.array([1 << int(np.ceil(np.log2(x))) for x in k])
+    return [dict(t=float(t[i]), n=int(n[i]), k=int(k[i]), nb=int(nb[i]), seed=1000 + i) for i in range(count)]
+
+
+def run_serving(args, lob, synth, torch):
+    """Continuous-batching server (lob_server_*) on the serving workload, mixed precision,
+    tol 1e-8 ||H||, block-Jacobi b_p = 32, eq. 12 guess; 60 GB admission budget. Matrices are
+    built before the clock starts (resident in HBM). Reports p50/p99 latency (submit to done,
+    queueing included) and solves/s, plus a closed batch of the first requests served mixed
+    against the same requests solved one at a time by the plain FP64 solver."""
+    reqs = serving_requests(args.serve_requests, args.serve_rate)
+    t0 = time.perf_counter()
+    for q in reqs:
+        L = synth.layout(q["n"], synth.interp_levels(q["n"]), 30, q["seed"])
+        r, c, v = synth.generate_device(L)
+        q["M"] = lob.Matrix(q["n"], r, c, v, precond_block=32)
+        q["n_small"] = int(synth.level_starts(L)[2])
+        del r, c, v
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+
+    def serve(sample, arrivals, mode="mixed", batched=True):
+        srv = lob.Server(budget_bytes=60 << 30, max_active=64, batched=batched)
+        ids = {}
+        res = {}
+        i = 0
+        late = 0.0
+        t_start = time.perf_counter()
+        while len(res) < len(sample):
+            now = time.perf_counter() - t_start
+            while i < len(sample) and (not arrivals or sample[i]["t"] - sample[0]["t"] <= now):
+                q = sample[i]
+                rid = srv.submit(q["M"], q["k"], q["nb"], 1e-8, mode=mode, precond=True, n_small=q["n_small"])
+                ids[rid] = i
+                if arrivals:
+                    late = max(late, now - (q["t"] - sample[0]["t"]))
+                i += 1
+            nd = srv.progress(wait=False)
+            if nd:
+                for rid in list(ids):
+                    if rid in res:
+                        continue
+                    r = srv.poll(rid)
+                    if r["state"] == lob.REQ_DONE:
+                        res[rid] = r
+        wall = time.perf_counter() - t_start
+        st = srv.stats()
+        srv.close()
+        out = [None] * len(sample)
+        for rid, j in ids.items():
+            out[j] = res[rid]
+        return out, wall, st, late
+
+    out, wall, st, late = serve(reqs, True)
+    lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in out])
+    ok = sum(1 for r in out if r["rc"] == lob.LOB_OK)
+    serving = {"workload": f"{len(reqs)} requests, Poisson {args.serve_rate:g}/s, n log-uniform [2000, 200000], "
+                           f"k U{{1..8}}, nb = next pow2 >= k, ~30 nnz/row, mixed, tol 1e-8, b_p=32, budget 60 GB",
+               "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+               "mean_ms": float(lat.mean()), "solves_per_s": len(out) / wall, "wall_s": wall, "converged": ok,
+               "max_submit_lateness_ms": late * 1e3, "peak_bytes": int(st["bytes_peak"]),
+               "spmm_products": int(st["spmm_products"]), "spmm_launches": int(st["spmm_launches"]),
+               "matrix_build_s": build_s}
+    # closed batch: the first requests all at once, served mixed vs one at a time in FP64
+    sample = reqs[:args.serve_compare]
+    outb, wallb, stb, _ = serve(sample, False)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    lam64 = []
+    for q in sample:
+        lam, _, _, rc = q["M"].solve(q["k"], q["nb"], 1e-8, mode="fp64", precond=True, n_small=q["n_small"])
+        lam64.append(lam)
+    torch.cuda.synchronize()
+    wall64 = time.perf_counter() - t1
+    diff = max(float((np.abs(r["lam"] - l) / np.maximum(np.abs(l), 1.0)).max()) for r, l in zip(outb, lam64))
+    serving["compare"] = {"requests": len(sample), "served_mixed_s": wallb, "single_fp64_s": wall64,
+                          "served_mixed_solves_per_s": len(sample) / wallb,
+                          "single_fp64_solves_per_s": len(sample) / wall64,
+                          "speedup_served_mixed_over_single_fp64": wall64 / wallb,
+                          "max_eig_rel_diff": diff, "spmm_products": int(stb["spmm_products"]),
+                          "spmm_launches": int(stb["spmm_launches"])}
+    for q in reqs:
+        q["M"].close()
+    return serving
+
+
 def run_reference(args, wl):
     import synth
     rank = int(os.environ.get("RANK", "0"))
@@ -186,6 +297,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2000)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-compare", type=int, default=100)
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -211,8 +326,7 @@ def main():
         torch.cuda.synchronize()
 
     # ---- setup (not timed): generate on the device, build the tile store and preconditioner
-    base = synth.CONFIGS[wl["cfg"]]
-    layout = synth.config_layout(wl["cfg"], seed=base["seed"] + rank)
+    layout = replica_layout(wl["cfg"], rank)
     n = int(layout.n)
     rows, cols, vals = synth.generate_device(layout)
     t0 = time.perf_counter()
@@ -248,10 +362,7 @@ def main():
     launches = lob.kernel_launches() - launches0
     clocks = sampler.stop()
     ms_total = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = reduce_max(ms_total, dist, "cuda")
     ms_step = ms_total / args.steps
 
     # SpMM roofline (the mixed-precision SpMM, the solve's dominant product): algorithmic bytes /
@@ -315,6 +426,9 @@ def main():
         out["e2e"] = {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(hr.numel() * 24),
                       "d2h_bytes_per_step": int(n * nb * 8 + k * 8),
                       "includes": "H2D of the COO, tile build + preconditioner setup, solve, D2H of X and lambda"}
+
+    if rank == 0 and not args.no_serve:
+        out["serving"] = run_serving(args, lob, synth, torch)
 
     if rank == 0 and not args.no_cpu:
         ms_cpu, desc = oracle_sample(wl["cfg"], layout)

@@ -74,7 +74,8 @@ int lob_destroy(lob_matrix* m);
 
 typedef struct {
   int64_t n, nnz, ntiles, n_tile_rows;
-  int32_t tile, values, precond_block, reserved;
+  int32_t tile, values, precond_block;
+  int32_t perm_chunk;       /* entries per chunk of the kernel-private permutation (lob_export_perm) */
   double norm_inf;          /* max_i sum_j |h_ij| over the full symmetric H */
   int64_t store_bytes;      /* device bytes of the tile store (indices + values kept) */
   int64_t precond_bytes;    /* device bytes of the preconditioner */
@@ -90,7 +91,8 @@ int lob_export_tiles(const lob_matrix* m, int64_t* tile_rowptr, int32_t* tile_co
                      double* v64, float* v32);
 
 /* Copy the kernel-private column-order permutation to a host uint16 array of nnz entries.
- * The SpMM walks each tile in chunks of 4096 entries (the last chunk of a tile may be shorter);
+ * The SpMM walks each tile in chunks of perm_chunk entries (lob_matrix_info; the last chunk of a
+ * tile may be shorter);
  * for the chunk starting at entry b, perm[b + j] is the chunk-local index of the j-th entry of
  * the chunk in (column, row) order. Derived from the canonical store at create time; exposed
  * so tests can check it against the canonical order. */
@@ -123,13 +125,25 @@ int lob_gram(int64_t n, int32_t p, const double* A, int32_t lda, int32_t q, cons
 int lob_lincomb(int64_t n, int32_t p, const double* A, int32_t lda, int32_t q, const double* C, double* Y,
                 int32_t ldy, int32_t mode, void* stream);
 
+/* Solvers for the shifted block systems of eq. 11 (Sections 3.2, 4.3). */
+#define LOB_PSOLVE_FOM 0     /* `steps` FOM iterations from a zero start (the paper's choice) */
+#define LOB_PSOLVE_DIRECT 1  /* exact solve */
+#define LOB_PSOLVE_MINRES 2  /* `steps` minimal-residual iterations from a zero start (GMRES for
+                                a symmetric system) */
+#define LOB_PSOLVE_ABS 3     /* |H~_[i] - mu_j I|^{-1}: the direct solve made positive definite */
+
 /* Block-diagonal preconditioner apply of eq. 11: for each diagonal block [i*b_p, (i+1)*b_p)
- * of H and each column j, W_[i](:, j) = (H~_[i] - mu_j I)^{-1} R_[i](:, j), through the
- * eigendecomposition H~_[i] = Q diag(lambda) Q^T made at create; a shifted eigenvalue with
- * |lambda - mu_j| < 1e-8 ||H|| is replaced by +-1e-8 ||H|| keeping its sign. Arithmetic FP32
- * (footnote 5), inputs/outputs FP64. R, W: device n x nb; mu: device, nb. Needs
- * precond_block > 0 at create. */
-int lob_precond_apply(lob_matrix* m, const double* mu, const double* R, double* W, int32_t nb, void* stream);
+ * of H and each column j, W_[i](:, j) = approximate solution of
+ * (H~_[i] - mu_j I) w = R_[i](:, j) by `solve` (LOB_PSOLVE_*; steps 1..3 for the Krylov
+ * solvers, ignored otherwise). All work in the eigendecomposition H~_[i] = Q diag(lambda) Q^T
+ * made at create: Krylov spaces of (H~ - mu I, r) map exactly to those of (diag(lambda - mu),
+ * Q^T r). FOM falls back to the minimal-residual iterate on a breakdown (a pivot of the
+ * projected tridiagonal below 1e-4 of its largest entry). For DIRECT and ABS a shifted
+ * eigenvalue with |lambda - mu_j| < 1e-8 ||H|| is replaced by +-1e-8 ||H|| keeping its sign.
+ * Arithmetic FP32 (Section 4.4, footnote 5), inputs/outputs FP64. R, W: device n x nb; mu:
+ * device, nb. Needs precond_block > 0 at create. Errors: LOB_ERR_ARG. */
+int lob_precond_apply(lob_matrix* m, const double* mu, const double* R, double* W, int32_t nb, int32_t solve,
+                      int32_t steps, void* stream);
 
 /* Rayleigh-Ritz of eq. 9 on the GPU: solve G c = theta M c for symmetric G and
  * positive-definite M (m x m, device, row-major; only the upper triangles are read) by
@@ -163,13 +177,16 @@ typedef struct {
   int32_t mode;            /* LOB_MODE_* */
   int32_t precond;         /* 1: block-diagonal preconditioner (needs precond_block at create) */
   int32_t max_iter;        /* 0 = 500 */
-  int32_t refine_iter;     /* MIXED: max FP64 refinement iterations; 0 = 50 */
+  int32_t refine_iter;     /* MIXED: max FP64 refinement iterations; 0 = what max_iter leaves
+                              after the FP32-value phase (at least 50) */
   double norm_H;           /* 0: use ||H||_inf */
   int64_t n_small;         /* X0 == NULL: if > 0, the initial guess of eq. 12 from the leading
                               n_small x n_small block (the smaller configuration space,
                               Section 3.3.1); else seeded random vectors */
   uint64_t seed;           /* seed of the random vectors the method draws */
   int32_t precond_shift;   /* 0: mu_j = theta_j; 1: the per-column rules of Section 4.3 */
+  int32_t precond_solve;   /* LOB_PSOLVE_* for eq. 11; 0 = FOM (the paper's solver) */
+  int32_t precond_steps;   /* Krylov steps for FOM / MINRES, 1..3; 0 = 3 */
   int32_t verbose;
   double mixed_tol;        /* MIXED: relative residual at which the FP32-value phase stops
                               (0 = max(tol, 1e-6)) */
@@ -200,6 +217,83 @@ typedef struct {
  * LOB_ERR_BREAKDOWN. */
 int lob_solve(lob_matrix* m, int32_t k, int32_t nb, double tol, const double* X0, const lob_solve_opts* opts,
               double* lambda, double* X, lob_stats* st);
+
+/* ---- serving: continuous batching of solves ----
+ *
+ * A server keeps the LOBPCG state of every admitted solve resident on the device (S = [X W P],
+ * H S, R, the Ritz values) and advances all of them together: each call of
+ * lob_server_progress() moves every admitted solve to its next host decision, and the SpMMs
+ * that several solves need at the same time go out as shared launches (one per arithmetic and
+ * vector width, lob_spmm_batch). Each solve has its own CUDA stream, so the small dense work of
+ * different solves overlaps on the device. Requests that arrive while others run are admitted
+ * between progress calls as soon as a slot and enough of the device-memory budget are free
+ * (any queued request that fits, in arrival order).
+ *
+ * A solve gives the same result in the mix as alone (lob_solve) up to the rounding of the
+ * SpMM's atomic column sums, which are not ordered in either case. */
+
+/* Y_j = H_j X_j for njobs distinct matrices in shared launches (one kernel per arithmetic and
+ * vector width; each CTA finds its matrix and tile row in a job table). X[j], Y[j]: device,
+ * n_j x nb[j] row-major, 1 <= nb[j] <= 16; mode[j]: LOB_SPMM_*. Runs on `stream` and returns
+ * when the products are complete. Errors: LOB_ERR_ARG (null pointers, nb out of range, a matrix
+ * listed twice, missing value copy), LOB_ERR_NOMEM, LOB_ERR_CUDA. */
+int lob_spmm_batch(int32_t njobs, lob_matrix* const* H, const double* const* X, double* const* Y,
+                   const int32_t* nb, const int32_t* mode, void* stream);
+
+typedef struct lob_server lob_server; /* opaque */
+
+typedef struct {
+  uint64_t budget_bytes;   /* device memory the admitted solves may hold (matrix + solver state);
+                              0 = 60 GiB */
+  int32_t max_active;      /* admitted solves at once; 0 = 64 */
+  int32_t batch_spmm;      /* 1 (default when 0): shared SpMM launches; -1: one launch per solve */
+} lob_server_opts;
+
+typedef struct {
+  lob_matrix* H;           /* caller-owned; must stay valid until the request is finished */
+  int32_t k, nb;           /* 1 <= k <= nb <= 16 */
+  double tol;              /* as lob_solve */
+  double* X;               /* device n x nb output (eigenvectors), or NULL */
+  lob_solve_opts opts;     /* as lob_solve; opts.stream is ignored (the server owns the streams) */
+} lob_request;
+
+#define LOB_REQ_QUEUED 1
+#define LOB_REQ_RUNNING 2
+#define LOB_REQ_DONE 3
+
+typedef struct {
+  int32_t state;           /* LOB_REQ_* */
+  int32_t rc;              /* when DONE: the solve's return code (as lob_solve) */
+  double lambda[16];       /* when DONE: the k smallest eigenvalues */
+  lob_stats stats;         /* when DONE: iterations, SpMM counts, final residuals (no phase times) */
+  double t_submit_ms, t_admit_ms, t_done_ms; /* server clock (ms since lob_server_create) */
+  uint64_t bytes;          /* device bytes charged against the budget */
+} lob_result;
+
+typedef struct {
+  int64_t submitted, admitted, finished, active, queued;
+  uint64_t bytes_in_use, bytes_peak;
+  int64_t spmm_launches;   /* SpMM kernel launches made for the solves */
+  int64_t spmm_products;   /* SpMM products they computed (one per solve per step) */
+  int64_t progress_calls;
+} lob_server_stats;
+
+/* The server uses the current CUDA device. Errors: LOB_ERR_ARG, LOB_ERR_NOMEM, LOB_ERR_CUDA. */
+int lob_server_create(const lob_server_opts* o, lob_server** out);
+/* Queue a solve; *id identifies it. The request is copied. Errors: LOB_ERR_ARG (bad sizes, or a
+ * solve that could never fit the budget). */
+int lob_server_submit(lob_server* s, const lob_request* r, int64_t* id);
+/* Admit what fits, then advance every admitted solve until it waits on the device, sharing the
+ * SpMM launches. wait != 0: if no solve could move, block until the oldest pending device step
+ * completes. *n_done (may be NULL) gets the number of solves finished by this call. */
+int lob_server_progress(lob_server* s, int32_t wait, int32_t* n_done);
+/* State of a request; once DONE has been reported the record is released (the id becomes
+ * unknown: LOB_ERR_ARG). */
+int lob_server_poll(lob_server* s, int64_t id, lob_result* out);
+int lob_server_stats_get(const lob_server* s, lob_server_stats* out);
+/* Waits for the device work of every admitted solve, then frees the server. Queued and running
+ * requests are dropped. */
+int lob_server_destroy(lob_server* s);
 
 const char* lob_strerror(int code);
 

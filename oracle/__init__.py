@@ -59,6 +59,7 @@ def lib():
         L.orc_gram.argtypes = [_I, _I, _P, _I, _P, _P]
         L.orc_lincomb.argtypes = [_I, _I, _P, _I, _P, _P]
         L.orc_block_precond.argtypes = [_I, _I, _P, _P, _P, _I, _P, _I, _P, _P, _P]
+        L.orc_block_krylov.argtypes = [_I, _I, _P, _P, _P, _I, _P, _I, _P, _P, ctypes.c_int, ctypes.c_int, _D, _P]
         L.orc_block_precond.restype = ctypes.c_int
         L.orc_rayleigh_ritz.argtypes = [_I, _P, _P, _P, _P]
         L.orc_rayleigh_ritz.restype = ctypes.c_int
@@ -204,6 +205,24 @@ def block_precond(H: Coo, bounds, mu, R: np.ndarray) -> np.ndarray:
                                  R.ctypes.data, W.ctypes.data)
     if st != 0:
         raise ZeroDivisionError("singular block system")
+    return W
+
+
+KRYLOV = {"fom": 0, "minres": 2, "abs": 3}
+
+
+def block_krylov(H: Coo, bounds, mu, R: np.ndarray, method: str, steps: int = 3, guard: float = 0.0) -> np.ndarray:
+    """Approximate eq. 11 solves per block and column: FOM or minimal residual with `steps`
+    Krylov iterations from a zero start, or |H~_[i] - mu_j I|^{-1} ('abs')."""
+    bounds = _i64(bounds)
+    assert np.diff(bounds).max() <= 64
+    mu = _f64(mu)
+    R = _f64(R)
+    W = np.empty_like(R)
+    st = lib().orc_block_krylov(*H.args(), len(bounds) - 1, bounds.ctypes.data, R.shape[1], mu.ctypes.data,
+                                R.ctypes.data, KRYLOV[method], steps, guard, W.ctypes.data)
+    if st != 0:
+        raise RuntimeError("block eigendecomposition failed")
     return W
 
 

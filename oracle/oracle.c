@@ -20,6 +20,8 @@
  *   orc_gram          block inner product X^T Y (Section 4.4)
  *   orc_lincomb       linear combination Y = X G (Section 4.4, eq. 7)
  *   orc_block_precond block-diagonal shifted solve (H~_[i] - mu_j I) W_[i] = R_[i] (eq. 11)
+ *   orc_block_krylov  the same systems solved approximately by a few FOM or minimal-residual
+ *                     iterations from a zero start (Sections 3.2, 4.3), or by |H~_[i] - mu_j I|^{-1}
  *   orc_rayleigh_ritz generalised projected problem (Y^T H Y) G = (Y^T Y) G Theta (eq. 9)
  *   orc_norm_inf      ||H||_inf, the norm used in the relative residual (Section 3.3.1)
  */
@@ -496,6 +498,149 @@ int orc_block_precond(int64_t n, int64_t nnz, const int64_t* row, const int64_t*
     }
   }
   free(blk); free(M); free(rhs); free(owner);
+  return st;
+}
+
+/* One shifted block system A w = r (A = H~_[i] - mu I, m x m dense, row-major) solved by a
+ * Krylov method from a zero start (the paper's FOM or GMRES with two or three iterations,
+ * Sections 3.2 and 4.3). Lanczos with full reorthogonalisation builds V = [v_1 .. v_s],
+ * v_1 = r / beta, and the tridiagonal T = V^T A V (diagonal alpha, off-diagonal b); b_s couples
+ * v_s to the next vector. The process stops early when b_i <= 1e-12 (|alpha_i| + b_{i-1})
+ * (an invariant subspace: the iterate is then exact).
+ *   method 0, FOM: w = V y with T y = beta e_1 (Galerkin condition V^T (r - A w) = 0). A pivot
+ *     of the unpivoted elimination of T below 1e-4 max_i (|alpha_i| + b_i) counts as a FOM
+ *     breakdown, and the minimal-residual iterate is returned instead.
+ *   method 2, minimal residual: w = V y minimising || beta e_1 - Tbar y ||, Tbar = [T; b_s e_s^T]
+ *     ((s+1) x s), through the normal equations Tbar^T Tbar y = beta Tbar^T e_1. */
+static void krylov_block(int64_t m, const double* A, const double* r, int method, int steps, double* w) {
+  double V[4][64], al[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0}, u[64];
+  for (int64_t a = 0; a < m; a++) w[a] = 0.0;
+  double beta = 0.0;
+  for (int64_t a = 0; a < m; a++) beta += r[a] * r[a];
+  beta = sqrt(beta);
+  if (beta == 0.0) return;
+  for (int64_t a = 0; a < m; a++) V[0][a] = r[a] / beta;
+  int s = 0;
+  for (int i = 0; i < steps; i++) {
+    for (int64_t a = 0; a < m; a++) {
+      double t = 0.0;
+      for (int64_t c = 0; c < m; c++) t += A[a * m + c] * V[i][c];
+      u[a] = t;
+    }
+    al[i] = 0.0;
+    for (int64_t a = 0; a < m; a++) al[i] += V[i][a] * u[a];
+    for (int t = 0; t <= i; t++) {
+      double h = 0.0;
+      for (int64_t a = 0; a < m; a++) h += V[t][a] * u[a];
+      for (int64_t a = 0; a < m; a++) u[a] -= h * V[t][a];
+    }
+    double nu = 0.0;
+    for (int64_t a = 0; a < m; a++) nu += u[a] * u[a];
+    b[i] = sqrt(nu);
+    s = i + 1;
+    const double scale = fabs(al[i]) + (i > 0 ? b[i - 1] : 0.0);
+    if (!(b[i] > 1e-12 * scale)) { b[i] = 0.0; break; }
+    if (i + 1 == steps) break;
+    for (int64_t a = 0; a < m; a++) V[i + 1][a] = u[a] / b[i];
+  }
+  double y[4] = {0, 0, 0, 0};
+  double tmax = 0.0;
+  for (int i = 0; i < s; i++) tmax = fmax(tmax, fabs(al[i]) + b[i]);
+  int fom_ok = 0;
+  if (method == 0) {
+    double dg[4], rhs[4] = {beta, 0, 0, 0};
+    fom_ok = 1;
+    for (int i = 0; i < s; i++) {
+      dg[i] = al[i];
+      if (i > 0) {
+        const double l = b[i - 1] / dg[i - 1];
+        dg[i] -= l * b[i - 1];
+        rhs[i] -= l * rhs[i - 1];
+      }
+      if (!(fabs(dg[i]) > 1e-4 * tmax)) fom_ok = 0;
+    }
+    if (fom_ok)
+      for (int i = s - 1; i >= 0; i--) y[i] = (rhs[i] - (i + 1 < s ? b[i] * y[i + 1] : 0.0)) / dg[i];
+  }
+  if (!fom_ok) {
+    /* Tbar ((s+1) x s): Tbar[i][i] = al[i], Tbar[i+1][i] = b[i], Tbar[i][i+1] = b[i] */
+    double Tb[5][4], N[16], g[4];
+    memset(Tb, 0, sizeof(Tb));
+    for (int i = 0; i < s; i++) {
+      Tb[i][i] = al[i];
+      Tb[i + 1][i] = b[i];
+      if (i + 1 < s) Tb[i][i + 1] = b[i];
+    }
+    for (int i = 0; i < s; i++) {
+      for (int j = 0; j < s; j++) {
+        double t = 0.0;
+        for (int k = 0; k <= s; k++) t += Tb[k][i] * Tb[k][j];
+        N[i * s + j] = t;
+      }
+      g[i] = beta * Tb[0][i];
+    }
+    if (gauss_solve(s, N, g) == 0)
+      for (int i = 0; i < s; i++) y[i] = g[i];
+  }
+  for (int i = 0; i < s; i++)
+    for (int64_t a = 0; a < m; a++) w[a] += y[i] * V[i][a];
+}
+
+/* Approximate solves of eq. 11 on the diagonal blocks given by bounds (block sizes <= 64):
+ * method 0 FOM / 2 minimal residual with `steps` (1..3) Krylov iterations (krylov_block), or
+ * method 3: w = |H~_[i] - mu_j I|^{-1} r through the block's eigendecomposition (orc_syev),
+ * shifted eigenvalues of magnitude below `guard` replaced by +-guard. Returns 0, or -2 if a
+ * block eigendecomposition failed. */
+int orc_block_krylov(int64_t n, int64_t nnz, const int64_t* row, const int64_t* col, const double* val,
+                     int64_t nblk, const int64_t* bounds, int64_t nb, const double* mu, const double* R,
+                     int method, int steps, double guard, double* W) {
+  int64_t* owner = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+  for (int64_t i = 0; i < nblk; i++)
+    for (int64_t r = bounds[i]; r < bounds[i + 1]; r++) owner[r] = i;
+  double* blk = (double*)malloc(64 * 64 * sizeof(double));
+  double* A = (double*)malloc(64 * 64 * sizeof(double));
+  double* Z = (double*)malloc(64 * 64 * sizeof(double));
+  double lam[64], r[64], w[64];
+  int st = 0;
+  for (int64_t bi = 0; bi < nblk && !st; bi++) {
+    const int64_t o = bounds[bi], m = bounds[bi + 1] - o;
+    memset(blk, 0, (size_t)(m * m) * sizeof(double));
+    for (int64_t t = 0; t < nnz; t++) {
+      const int64_t i = row[t], j = col[t];
+      if (owner[i] != bi || owner[j] != bi) continue;
+      blk[(i - o) * m + (j - o)] = val[t];
+      blk[(j - o) * m + (i - o)] = val[t];
+    }
+    if (method == 3) {
+      memcpy(Z, blk, (size_t)(m * m) * sizeof(double));
+      if (orc_syev(m, Z, lam) != 0) { st = -2; break; }
+    }
+    for (int64_t c = 0; c < nb; c++) {
+      for (int64_t a = 0; a < m; a++) r[a] = R[(o + a) * nb + c];
+      if (method == 3) {
+        for (int64_t k = 0; k < m; k++) {
+          double ck = 0.0;
+          for (int64_t a = 0; a < m; a++) ck += Z[a * m + k] * r[a];
+          double d = fabs(lam[k] - mu[c]);
+          if (d < guard) d = guard;
+          w[k] = ck / d;
+        }
+        for (int64_t a = 0; a < m; a++) {
+          double t = 0.0;
+          for (int64_t k = 0; k < m; k++) t += Z[a * m + k] * w[k];
+          W[(o + a) * nb + c] = t;
+        }
+      } else {
+        for (int64_t a = 0; a < m; a++) {
+          for (int64_t b2 = 0; b2 < m; b2++) A[a * m + b2] = blk[a * m + b2];
+          A[a * m + a] -= mu[c];
+        }
+        krylov_block(m, A, r, method, steps, w);
+        for (int64_t a = 0; a < m; a++) W[(o + a) * nb + c] = w[a];
+      }
+    }
+  }
+  free(owner); free(blk); free(A); free(Z);
   return st;
 }
 

@@ -9,6 +9,8 @@ Main objects:
   Matrix.spmm(X, mode)                          Y = H X (lob_spmm)
   Matrix.solve(k, nb, tol, ...)                 k smallest eigenpairs by LOBPCG (lob_solve)
   gram, lincomb, rayleigh_ritz, Matrix.precond_apply   the pieces of one iteration
+  spmm_batch(mats, Xs, modes)                   products of several matrices in shared launches
+  Server(budget_bytes, max_active)              continuous batching of solves (lob_server_*)
 """
 from __future__ import annotations
 
@@ -31,6 +33,8 @@ LOB_ERR_BREAKDOWN = -5
 VALUES_FP64, VALUES_FP32, VALUES_BOTH = 1, 2, 3
 SPMM_FP64, SPMM_MIXED, SPMM_DF64 = 0, 1, 2
 MODE_FP64, MODE_MIXED = 0, 1
+PSOLVE_FOM, PSOLVE_DIRECT, PSOLVE_MINRES, PSOLVE_ABS = 0, 1, 2, 3
+_PSOLVE = {"fom": 0, "direct": 1, "minres": 2, "abs": 3, 0: 0, 1: 1, 2: 2, 3: 3}
 _MODES = {"fp64": 0, "mixed": 1, "df64": 2, 0: 0, 1: 1, 2: 2}
 
 _P = ctypes.c_void_p
@@ -49,14 +53,14 @@ class CreateOpts(ctypes.Structure):
 
 class MatrixInfo(ctypes.Structure):
     _fields_ = [("n", _I64), ("nnz", _I64), ("ntiles", _I64), ("n_tile_rows", _I64), ("tile", _I32),
-                ("values", _I32), ("precond_block", _I32), ("reserved", _I32), ("norm_inf", _D),
+                ("values", _I32), ("precond_block", _I32), ("perm_chunk", _I32), ("norm_inf", _D),
                 ("store_bytes", _I64), ("precond_bytes", _I64)]
 
 
 class SolveOpts(ctypes.Structure):
     _fields_ = [("mode", _I32), ("precond", _I32), ("max_iter", _I32), ("refine_iter", _I32), ("norm_H", _D),
-                ("n_small", _I64), ("seed", ctypes.c_uint64), ("precond_shift", _I32), ("verbose", _I32),
-                ("mixed_tol", _D), ("stream", _P)]
+                ("n_small", _I64), ("seed", ctypes.c_uint64), ("precond_shift", _I32), ("precond_solve", _I32),
+                ("precond_steps", _I32), ("verbose", _I32), ("mixed_tol", _D), ("stream", _P)]
 
 
 class Stats(ctypes.Structure):
@@ -75,6 +79,28 @@ class Stats(ctypes.Structure):
                                           bytes=self.spmm_bytes_mode[i])
                                   for i, m in enumerate(("fp64", "mixed", "df64"))},
                     residual=[self.residual[j] for j in range(nb)])
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("max_active", _I32), ("batch_spmm", _I32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("H", _P), ("k", _I32), ("nb", _I32), ("tol", _D), ("X", _P), ("opts", SolveOpts)]
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE = 1, 2, 3
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("state", _I32), ("rc", _I32), ("lambda_", _D * 16), ("stats", Stats), ("t_submit_ms", _D),
+                ("t_admit_ms", _D), ("t_done_ms", _D), ("bytes", ctypes.c_uint64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", _I64), ("admitted", _I64), ("finished", _I64), ("active", _I64), ("queued", _I64),
+                ("bytes_in_use", ctypes.c_uint64), ("bytes_peak", ctypes.c_uint64), ("spmm_launches", _I64),
+                ("spmm_products", _I64), ("progress_calls", _I64)]
 
 
 class LobError(RuntimeError):
@@ -96,18 +122,27 @@ def _load():
     L.lob_spmm.argtypes = [_P, _I32, _P, _P, _I32, _P]
     L.lob_gram.argtypes = [_I64, _I32, _P, _I32, _I32, _P, _I32, _P, _I32, _P]
     L.lob_lincomb.argtypes = [_I64, _I32, _P, _I32, _I32, _P, _P, _I32, _I32, _P]
-    L.lob_precond_apply.argtypes = [_P, _P, _P, _P, _I32, _P]
+    L.lob_precond_apply.argtypes = [_P, _P, _P, _P, _I32, _I32, _I32, _P]
     L.lob_rayleigh_ritz.argtypes = [_I32, _P, _P, _P, _P, _P, _I32, _P]
     L.lob_rayleigh_ritz_noalloc.argtypes = [_I32, _P, _P, _P, _P, _P, _I32, _P]
     L.lob_rayleigh_ritz_noalloc.restype = ctypes.c_int
     L.lob_solve.argtypes = [_P, _I32, _I32, _D, _P, ctypes.POINTER(SolveOpts), _P, _P, ctypes.POINTER(Stats)]
+    L.lob_spmm_batch.argtypes = [_I32, _P, _P, _P, _P, _P, _P]
+    L.lob_server_create.argtypes = [ctypes.POINTER(ServerOpts), ctypes.POINTER(_P)]
+    L.lob_server_submit.argtypes = [_P, ctypes.POINTER(Request), ctypes.POINTER(_I64)]
+    L.lob_server_progress.argtypes = [_P, _I32, ctypes.POINTER(_I32)]
+    L.lob_server_poll.argtypes = [_P, _I64, ctypes.POINTER(Result)]
+    L.lob_server_stats_get.argtypes = [_P, ctypes.POINTER(ServerStats)]
+    L.lob_server_destroy.argtypes = [_P]
     L.lob_kernel_launches.argtypes = []
     L.lob_kernel_launches.restype = ctypes.c_longlong
     L.lob_strerror.argtypes = [ctypes.c_int]
     L.lob_strerror.restype = ctypes.c_char_p
     for f in ("lob_create", "lob_destroy", "lob_matrix_info_get", "lob_export_tiles", "lob_export_perm", "lob_spmm",
               "lob_gram",
-              "lob_lincomb", "lob_precond_apply", "lob_rayleigh_ritz", "lob_solve"):
+              "lob_lincomb", "lob_precond_apply", "lob_rayleigh_ritz", "lob_solve", "lob_spmm_batch",
+              "lob_server_create", "lob_server_submit", "lob_server_progress", "lob_server_poll",
+              "lob_server_stats_get", "lob_server_destroy"):
         getattr(L, f).restype = ctypes.c_int
     return L
 
@@ -234,16 +269,17 @@ class Matrix:
         _check(lib().lob_spmm(self._h, _MODES[mode], X.data_ptr(), Y.data_ptr(), nb, _stream()), "lob_spmm")
         return Y
 
-    def precond_apply(self, mu, R):
+    def precond_apply(self, mu, R, solve="direct", steps=3):
+        """Approximate solves of eq. 11 per block and column (lob_precond_apply)."""
         R = _dev_f64(R)
         mu = _dev_f64(mu)
         W = _torch().empty_like(R)
-        _check(lib().lob_precond_apply(self._h, mu.data_ptr(), R.data_ptr(), W.data_ptr(), R.shape[1], _stream()),
-               "lob_precond_apply")
+        _check(lib().lob_precond_apply(self._h, mu.data_ptr(), R.data_ptr(), W.data_ptr(), R.shape[1],
+                                       _PSOLVE[solve], steps, _stream()), "lob_precond_apply")
         return W
 
     def solve(self, k, nb, tol, X0=None, mode="fp64", precond=False, n_small=0, max_iter=0, refine_iter=0,
-              seed=1, precond_shift=0, mixed_tol=0.0, norm_H=0.0, X_out=None):
+              seed=1, precond_shift=0, mixed_tol=0.0, norm_H=0.0, X_out=None, precond_solve="fom", precond_steps=3):
         """k smallest eigenpairs (lob_solve). Returns (lam, X, stats, status)."""
         torch = _torch()
         X = X_out if X_out is not None else torch.empty((self.n, nb), dtype=torch.float64, device="cuda")
@@ -251,7 +287,7 @@ class Matrix:
         lam = np.zeros(k, np.float64)
         st = Stats()
         o = SolveOpts(_MODES[mode], int(bool(precond)), max_iter, refine_iter, norm_H, n_small, seed, precond_shift,
-                      0, mixed_tol, _stream())
+                      _PSOLVE[precond_solve], precond_steps, 0, mixed_tol, _stream())
         rc = lib().lob_solve(self._h, k, nb, tol, x0.data_ptr() if x0 is not None else None, ctypes.byref(o),
                              lam.ctypes.data, X.data_ptr(), ctypes.byref(st))
         if rc not in (LOB_OK, LOB_ERR_NOCONV):
@@ -306,3 +342,77 @@ def rayleigh_ritz_noalloc(G, M, mode="fp64", theta=None, C=None, info=None):
     if int(info.item()) != 0:
         raise np.linalg.LinAlgError(f"Gram matrix not positive definite (pivot {int(info.item())})")
     return theta, C
+
+
+def spmm_batch(mats, Xs, modes="fp64"):
+    """[H_j X_j] for distinct matrices in shared launches (lob_spmm_batch)."""
+    torch = _torch()
+    nj = len(mats)
+    if isinstance(modes, (str, int)):
+        modes = [modes] * nj
+    Xs = [_dev_f64(x) for x in Xs]
+    Ys = [torch.empty_like(x) for x in Xs]
+    H = (_P * nj)(*[m.handle.value for m in mats])
+    Xp = (_P * nj)(*[x.data_ptr() for x in Xs])
+    Yp = (_P * nj)(*[y.data_ptr() for y in Ys])
+    nb = (_I32 * nj)(*[1 if x.dim() == 1 else x.shape[1] for x in Xs])
+    md = (_I32 * nj)(*[_MODES[m] for m in modes])
+    _check(lib().lob_spmm_batch(nj, H, Xp, Yp, nb, md, _stream()), "lob_spmm_batch")
+    return Ys
+
+
+class Server:
+    """Continuous batching of eigen-solves (lob_server_*): submit() queues a solve, progress()
+    admits what fits the device-memory budget and advances every admitted solve, sharing the
+    SpMM launches; poll() returns a finished solve's eigenvalues, stats and timestamps."""
+
+    def __init__(self, budget_bytes=0, max_active=0, batched=True):
+        o = ServerOpts(budget_bytes, max_active, 1 if batched else -1)
+        h = _P()
+        _check(lib().lob_server_create(ctypes.byref(o), ctypes.byref(h)), "lob_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, matrix, k, nb, tol, mode="mixed", precond=False, n_small=0, max_iter=0, refine_iter=0, seed=1,
+               precond_shift=0, mixed_tol=0.0, X_out=None, precond_solve="fom", precond_steps=3):
+        o = SolveOpts(_MODES[mode], int(bool(precond)), max_iter, refine_iter, 0.0, n_small, seed, precond_shift,
+                      _PSOLVE[precond_solve], precond_steps, 0, mixed_tol, None)
+        r = Request(matrix.handle, k, nb, tol, X_out.data_ptr() if X_out is not None else None, o)
+        rid = _I64()
+        _check(lib().lob_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)), "lob_server_submit")
+        self._keep[rid.value] = (matrix, k)
+        return rid.value
+
+    def progress(self, wait=True):
+        nd = _I32()
+        _check(lib().lob_server_progress(self._h, int(bool(wait)), ctypes.byref(nd)), "lob_server_progress")
+        return nd.value
+
+    def poll(self, rid):
+        """dict(state, bytes, t_submit_ms, ...); once state == REQ_DONE also rc, lam (k values),
+        stats, t_admit_ms, t_done_ms, and the record is released."""
+        res = Result()
+        _check(lib().lob_server_poll(self._h, rid, ctypes.byref(res)), "lob_server_poll")
+        out = dict(state=res.state, bytes=int(res.bytes), t_submit_ms=res.t_submit_ms, t_admit_ms=res.t_admit_ms)
+        if res.state == REQ_DONE:
+            _, k = self._keep.pop(rid, (None, 16))
+            out.update(rc=res.rc, lam=np.array(res.lambda_[:k]), stats=res.stats.to_dict(16),
+                       t_done_ms=res.t_done_ms)
+        return out
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().lob_server_stats_get(self._h, ctypes.byref(st)), "lob_server_stats_get")
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lob_server_destroy(self._h)
+            self._h = None
+            self._keep = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

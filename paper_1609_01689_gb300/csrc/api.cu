@@ -83,7 +83,7 @@ int lob_matrix_info_get(const lob_matrix* m, lob_matrix_info* out) {
   if (!m || !out) return LOB_ERR_ARG;
   memset(out, 0, sizeof(*out));
   out->n = m->T.n; out->nnz = m->T.nnz; out->ntiles = m->T.ntiles; out->n_tile_rows = m->T.nt;
-  out->tile = LOB_TILE; out->values = m->values; out->precond_block = m->P.bp;
+  out->tile = LOB_TILE; out->values = m->values; out->precond_block = m->P.bp; out->perm_chunk = LOB_PERM_CHUNK;
   out->norm_inf = m->norm_inf;
   out->store_bytes = (m->T.nt + 1) * 8 + m->T.ntiles * (4 + 4 + 8) + 8 + m->T.nnz * 4 +
                      (m->T.v64 ? m->T.nnz * 8 : 0) + (m->T.v32 ? m->T.nnz * 4 : 0);
@@ -126,9 +126,11 @@ int lob_lincomb(int64_t n, int32_t p, const double* A, int32_t lda, int32_t q, c
   return lob_lincomb_launch(n, p, A, lda, q, C, Y, ldy, mode, (cudaStream_t)stream);
 }
 
-int lob_precond_apply(lob_matrix* m, const double* mu, const double* R, double* W, int32_t nb, void* stream) {
+int lob_precond_apply(lob_matrix* m, const double* mu, const double* R, double* W, int32_t nb, int32_t solve,
+                      int32_t steps, void* stream) {
   if (!m || !mu || !R || !W) return LOB_ERR_ARG;
-  return lob_precond_launch(m, mu, R, W, nb, m->T.n, (cudaStream_t)stream);
+  if (solve == LOB_PSOLVE_DIRECT || solve == LOB_PSOLVE_ABS) steps = 1;
+  return lob_precond_launch(m, mu, R, W, nb, m->T.n, solve, steps, (cudaStream_t)stream);
 }
 
 int lob_rayleigh_ritz(int32_t m, const double* G, const double* M, double* theta, double* C, int32_t* info,

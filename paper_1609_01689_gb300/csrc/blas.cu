@@ -43,25 +43,17 @@ struct Ar<true> {
 
 // U = tile edge / 16 outputs per thread along each dimension (1, 2 or 3): small Gram matrices
 // (16 x 16, 32 x 32) use a matching tile instead of a zero-padded 48 x 48 one.
-template <bool DF, int U>
-__global__ void __launch_bounds__(256) k_gram(int64_t n, int p, const double* __restrict__ A, int lda, int q,
-                                              const double* __restrict__ B, int ldb, double* __restrict__ part,
-                                              int64_t rpc) {
+// TRI: only the upper triangle of a symmetric result is needed -- the thread skips its
+// sub-blocks below the diagonal (3 of 9 at U = 3); the reduction mirrors them.
+template <bool DF, int U, bool TRI>
+__device__ __forceinline__ void gram_body(int64_t r0, int64_t r1, int p, const double* __restrict__ A, int lda, int q,
+                                          const double* __restrict__ B, int ldb, int a0, int b0,
+                                          typename Ar<DF>::in_t (*As)[16 * U], typename Ar<DF>::in_t (*Bs)[16 * U],
+                                          typename Ar<DF>::acc_t (&acc)[U][U]) {
   using R = Ar<DF>;
   using in_t = typename R::in_t;
   constexpr int TGU = 16 * U;
-  __shared__ in_t As[RB][TGU];
-  __shared__ in_t Bs[RB][TGU];
-  const int chunk = blockIdx.x;
-  const int a0 = blockIdx.y * TGU, b0 = blockIdx.z * TGU;
-  const int64_t r0 = (int64_t)chunk * rpc;
-  const int64_t r1 = (r0 + rpc) < n ? (r0 + rpc) : n;
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  typename R::acc_t acc[U][U];
-#pragma unroll
-  for (int i = 0; i < U; i++)
-#pragma unroll
-    for (int j = 0; j < U; j++) R::zero(acc[i][j]);
   for (int64_t rr = r0; rr < r1; rr += RB) {
     for (int idx = tid; idx < RB * TGU; idx += 256) {
       const int i = idx / TGU, a = idx % TGU;
@@ -78,25 +70,61 @@ __global__ void __launch_bounds__(256) k_gram(int64_t n, int p, const double* __
 #pragma unroll
       for (int u = 0; u < U; u++)
 #pragma unroll
-        for (int v = 0; v < U; v++) R::mac(acc[u][v], av[u], bv[v]);
+        for (int v = 0; v < U; v++)
+          if (!TRI || u <= v) R::mac(acc[u][v], av[u], bv[v]);
     }
     __syncthreads();
   }
+}
+
+template <bool DF, int U>
+__global__ void __launch_bounds__(256) k_gram(int64_t n, int p, const double* __restrict__ A, int lda, int q,
+                                              const double* __restrict__ B, int ldb, double* __restrict__ part,
+                                              int64_t rpc, int sym) {
+  using R = Ar<DF>;
+  using in_t = typename R::in_t;
+  constexpr int TGU = 16 * U;
+  __shared__ in_t As[RB][TGU];
+  __shared__ in_t Bs[RB][TGU];
+  const int chunk = blockIdx.x;
+  if (sym && blockIdx.y > blockIdx.z) return;  // below-diagonal tile: mirrored by the reduction
+  const int a0 = blockIdx.y * TGU, b0 = blockIdx.z * TGU;
+  const int64_t r0 = (int64_t)chunk * rpc;
+  const int64_t r1 = (r0 + rpc) < n ? (r0 + rpc) : n;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const bool tri = sym && blockIdx.y == blockIdx.z;
+  typename R::acc_t acc[U][U];
+#pragma unroll
+  for (int i = 0; i < U; i++)
+#pragma unroll
+    for (int j = 0; j < U; j++) R::zero(acc[i][j]);
+  if (tri) gram_body<DF, U, true>(r0, r1, p, A, lda, q, B, ldb, a0, b0, As, Bs, acc);
+  else gram_body<DF, U, false>(r0, r1, p, A, lda, q, B, ldb, a0, b0, As, Bs, acc);
 #pragma unroll
   for (int u = 0; u < U; u++)
 #pragma unroll
     for (int v = 0; v < U; v++) {
+      if (tri && u > v) continue;
       const int a = a0 + ty + 16 * u, b = b0 + tx + 16 * v;
       if (a < p && b < q) part[(int64_t)chunk * p * q + (int64_t)a * q + b] = R::out(acc[u][v]);
     }
 }
 
-// G[e] = sum over chunks of part[chunk][e], one warp per entry, fixed order.
-__global__ void k_gram_reduce(int nchunks, int pq, const double* __restrict__ part, double* __restrict__ G) {
+// G[e] = sum over chunks of part[chunk][e], one warp per entry, fixed order. With sym (p == q)
+// an entry below the diagonal whose partial was not computed takes its mirror's: the tiles
+// below the diagonal were skipped, and inside diagonal tiles so were the 16 x 16 sub-blocks
+// below the diagonal; entries of diagonal sub-blocks were computed on both sides.
+__global__ void k_gram_reduce(int nchunks, int pq, int q, int sym, int tge, const double* __restrict__ part,
+                              double* __restrict__ G) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
   if (warp >= pq) return;
+  int src = warp;
+  if (sym) {
+    const int a = warp / q, b = warp % q;
+    if (a / 16 > b / 16 || a / tge > b / tge) src = b * q + a;  // not computed: use the mirror
+  }
   double s = 0.0;
-  for (int c = lane; c < nchunks; c += 32) s += part[(int64_t)c * pq + warp];
+  for (int c = lane; c < nchunks; c += 32) s += part[(int64_t)c * pq + src];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
   if (lane == 0) G[warp] = s;
@@ -152,23 +180,24 @@ size_t lob_gram_work_doubles(int64_t n, int p, int q) {
 
 template <bool DF>
 static void gram_go(dim3 grid, cudaStream_t st, int U, int64_t n, int p, const double* A, int lda, int q,
-                    const double* B, int ldb, double* work, int64_t rpc) {
-  if (U == 1) (k_gram<DF, 1><<<grid, 256, 0, st>>>(n, p, A, lda, q, B, ldb, work, rpc), LOB_LAUNCHED());
-  else if (U == 2) (k_gram<DF, 2><<<grid, 256, 0, st>>>(n, p, A, lda, q, B, ldb, work, rpc), LOB_LAUNCHED());
-  else (k_gram<DF, 3><<<grid, 256, 0, st>>>(n, p, A, lda, q, B, ldb, work, rpc), LOB_LAUNCHED());
+                    const double* B, int ldb, double* work, int64_t rpc, int sym) {
+  if (U == 1) (k_gram<DF, 1><<<grid, 256, 0, st>>>(n, p, A, lda, q, B, ldb, work, rpc, sym), LOB_LAUNCHED());
+  else if (U == 2) (k_gram<DF, 2><<<grid, 256, 0, st>>>(n, p, A, lda, q, B, ldb, work, rpc, sym), LOB_LAUNCHED());
+  else (k_gram<DF, 3><<<grid, 256, 0, st>>>(n, p, A, lda, q, B, ldb, work, rpc, sym), LOB_LAUNCHED());
 }
 
 int lob_gram_launch_ws(int64_t n, int p, const double* A, int lda, int q, const double* B, int ldb, double* G,
-                       int mode, double* work, cudaStream_t st) {
+                       int mode, double* work, cudaStream_t st, int sym) {
+  if (sym && p != q) return LOB_ERR_ARG;
   const int e = gram_edge(p, q);
   const int ta = (p + e - 1) / e, tb = (q + e - 1) / e;
-  const int nch = nchunks_for(n, ta * tb);
+  const int nch = nchunks_for(n, sym ? ta * (ta + 1) / 2 : ta * tb);
   const int64_t rpc = (n + nch - 1) / nch;
   dim3 grid(nch, ta, tb);
-  if (mode == LOB_SPMM_MIXED) gram_go<true>(grid, st, e / 16, n, p, A, lda, q, B, ldb, work, rpc);
-  else gram_go<false>(grid, st, e / 16, n, p, A, lda, q, B, ldb, work, rpc);
+  if (mode == LOB_SPMM_MIXED) gram_go<true>(grid, st, e / 16, n, p, A, lda, q, B, ldb, work, rpc, sym);
+  else gram_go<false>(grid, st, e / 16, n, p, A, lda, q, B, ldb, work, rpc, sym);
   const int pq = p * q;
-  (k_gram_reduce<<<(pq * 32 + 255) / 256, 256, 0, st>>>(nch, pq, work, G), LOB_LAUNCHED());
+  (k_gram_reduce<<<(pq * 32 + 255) / 256, 256, 0, st>>>(nch, pq, q, sym, e, work, G), LOB_LAUNCHED());
   LOB_CUDA(cudaGetLastError());
   return LOB_OK;
 }

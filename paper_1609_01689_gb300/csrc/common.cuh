@@ -74,29 +74,76 @@ struct lob_matrix {
   size_t xs_bytes = 0;
 };
 
+// One matrix's share of a batched SpMM launch (several matrices' tile rows in one grid).
+struct lob_spmm_job {
+  const int64_t* rowptr;
+  const int32_t* tcol;
+  const int64_t* tptr;
+  const int32_t* tchunk;
+  const uint32_t* rc;
+  const void* vals;   // FP32 (MIXED, DF64 high part) or FP64 values
+  const void* vlo;    // DF64 low parts
+  const uint16_t* cperm;
+  const uint16_t* cptrs;
+  const void* Xs;     // staged X of this matrix
+  double* Y;
+  int32_t ldy, c0, w, pad;
+  int64_t n_act;
+  int64_t cta_begin;  // first CTA of this job in the grid
+};
+
 // ---- internal launchers (return LOB_OK or an error code) ----
 int lob_build_tiles(const lob_coo* H, int values, cudaStream_t st, lob_tiles* T, double* norm_inf);
 void lob_free_tiles(lob_tiles* T);
 int lob_build_precond(const lob_coo* Hdev, int bp, int64_t n, cudaStream_t st, lob_precond* P);
 void lob_free_precond(lob_precond* P);
 
+// Grow the matrix's staged-X scratch to at least `need` bytes (synchronous allocation).
+int lob_ensure_xs(const lob_matrix* m, size_t need);
 // Y = H X over the active leading n_act x n_act block (n_act <= n; rows/cols >= n_act are
 // treated as absent). Y is fully written (rows >= n_act get 0).
 int lob_spmm_launch(const lob_matrix* m, int mode, const double* X, double* Y, int nb, int64_t n_act,
                     cudaStream_t st);
+// Y_j = H_j X_j for several matrices in as few launches as possible (one per arithmetic
+// class); X_j, Y_j contiguous n_j x ncol_j, ncol_j <= 16; nact (nullable) restricts job j to
+// its leading nact[j] x nact[j] block. Matrices must be distinct. jobs_dev: device buffer of at least
+// njobs lob_spmm_job entries owned by the caller; jobs_host: pinned host buffer of the same size
+// that the caller leaves untouched until the stream has passed this launch.
+int lob_spmm_batch_launch(const lob_matrix* const* ms, const double* const* X, double* const* Y, const int* ncol,
+                          const int* mode, const int64_t* nact, int njobs, lob_spmm_job* jobs_host,
+                          lob_spmm_job* jobs_dev, cudaStream_t st, int* n_kernels = nullptr);
+// ---- resumable LOBPCG task (lobpcg.cu) ----
+#define LOB_TASK_SYNC 1  // wait for lob_task_event(leaf), then step again
+#define LOB_TASK_SPMM 2  // run the leaf's SpMM (lob_task_spmm_args), then step again
+#define LOB_TASK_DONE 3  // lob_task_result
+struct lob_task;
+int lob_task_create(lob_matrix* m, int32_t k, int32_t nb, double tol, const double* X0, const lob_solve_opts* o,
+                    double* X, int64_t n_act, cudaStream_t st, bool timing, lob_task** out);
+int lob_task_step(lob_task* t);
+lob_task* lob_task_leaf(lob_task* t);
+cudaEvent_t lob_task_event(const lob_task* leaf);
+void lob_task_spmm_args(const lob_task* leaf, const lob_matrix** m, const double** X, double** Y, int* ncol,
+                        int* mode, int64_t* n_act);
+int lob_task_spmm_direct(lob_task* leaf);
+int lob_task_result(const lob_task* t, double* lambda, lob_stats* st);
+void lob_task_destroy(lob_task* t);
+size_t lob_task_bytes(const lob_matrix* m, int nb, int64_t n_small);
+
 int lob_gram_launch(int64_t n, int p, const double* A, int lda, int q, const double* B, int ldb, double* G, int mode,
                     cudaStream_t st);
 int lob_lincomb_launch(int64_t n, int p, const double* A, int lda, int q, const double* C, double* Y, int ldy,
                        int mode, cudaStream_t st);
 int lob_precond_launch(const lob_matrix* m, const double* mu, const double* R, double* W, int nb, int64_t n_act,
-                       cudaStream_t st);
+                       int solve, int steps, cudaStream_t st);
 int lob_rr_launch(int m, const double* G, const double* M, double* theta, double* C, int32_t* info, double* work,
                   cudaStream_t st, int chol_only = 0);
 size_t lob_rr_work_doubles(int m);
 int lob_rr_launch_df(int m, const double* G, const double* M, double* theta, double* C, int32_t* info, double* work,
                      cudaStream_t st, int chol_only = 0);
 size_t lob_gram_work_doubles(int64_t n, int p, int q);
+// sym: A^T B is known to be symmetric (p == q) and only its upper triangle is computed; the
+// lower one is mirrored.
 int lob_gram_launch_ws(int64_t n, int p, const double* A, int lda, int q, const double* B, int ldb, double* G,
-                       int mode, double* work, cudaStream_t st);
+                       int mode, double* work, cudaStream_t st, int sym = 0);
 int lob_solve_impl(lob_matrix* m, int32_t k, int32_t nb, double tol, const double* X0,
                               const lob_solve_opts* o, double* lambda, double* X, lob_stats* st, int64_t n_act);

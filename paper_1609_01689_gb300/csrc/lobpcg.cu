@@ -1,7 +1,14 @@
-// LOBPCG driver (Section 3.1, Algorithm 1) with the block-diagonal preconditioner
+// LOBPCG (Section 3.1, Algorithm 1) with the block-diagonal preconditioner
 // (Section 3.2, eq. 11), the robustness rules of Section 4.3, and the initial guess of
 // Section 3.3.1 (eq. 12). All vectors stay on the device; the host orchestrates launches and
 // reads back nb residual norms per iteration for the convergence test (step 5).
+//
+// The solver is a resumable task: lob_task_step() enqueues work on the task's stream until the
+// host needs a value from the device (a convergence test or a factorisation status, returned as
+// LOB_TASK_SYNC with an event to wait on) or until it needs H times a block (LOB_TASK_SPMM, which
+// the driver runs either alone or batched with other tasks' products). lob_solve drives one task;
+// the server drives many and shares the SpMM launches between them. Each iteration has three
+// host synchronisations (residual norms; Cholesky-QR of W and P; Rayleigh-Ritz) and one SpMM.
 //
 // Per iteration i (S = [X W P], HS = H S, m = nb + 2 na columns):
 //   R = H X - X Theta                         (step 4)
@@ -19,6 +26,7 @@
 #include <string.h>
 
 #include <chrono>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -113,6 +121,12 @@ __global__ void k_shifts(int nb, int mode, const double* __restrict__ theta, con
   }
 }
 
+// Identity columns: out[(c0 + i) * ld + i] = 1 for i < ncol (after zeroing out).
+__global__ void k_unit_cols(int64_t c0, int ncol, int ld, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ncol) out[(c0 + i) * ld + i] = 1.0;
+}
+
 // C2 = [-Z; I] (rows: nb rows of -Z then na rows of the identity), for W - X Z as [X W] C2.
 __global__ void k_proj_coef(int nb, int na, const double* __restrict__ Z, double* __restrict__ C2) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -121,9 +135,8 @@ __global__ void k_proj_coef(int nb, int na, const double* __restrict__ Z, double
   C2[t] = r < nb ? -Z[r * na + c] : (r - nb == c ? 1.0 : 0.0);
 }
 
-// Phase timing with CUDA events on the solver's stream. Event pairs are recorded without
-// synchronising and resolved in bulk whenever the solver synchronises anyway (the per-iteration
-// convergence readback), so timing adds no host-device round trips.
+// Phase timing with CUDA events on the task's stream. Event pairs are recorded without
+// synchronising and resolved in bulk whenever the task passes a synchronisation point anyway.
 struct PhaseClock {
   struct Pair { cudaEvent_t a, b; double* acc; };
   std::vector<Pair> pending;
@@ -132,7 +145,7 @@ struct PhaseClock {
     if (pool.empty()) { cudaEvent_t e; cudaEventCreate(&e); return e; }
     cudaEvent_t e = pool.back(); pool.pop_back(); return e;
   }
-  void resolve() {  // call after the stream has been synchronised
+  void resolve() {  // every recorded event has completed
     for (auto& p : pending) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess && p.acc) *p.acc += ms;
@@ -145,168 +158,272 @@ struct PhaseClock {
     for (auto e : pool) cudaEventDestroy(e);
   }
 };
-thread_local PhaseClock* g_clock = nullptr;
 
 struct Timer {
-  cudaEvent_t a = nullptr, b = nullptr;
+  PhaseClock* clk;
+  cudaEvent_t a = nullptr;
   cudaStream_t st;
   double* acc;
-  Timer(cudaStream_t s, double* accum) : st(s), acc(accum) {
-    if (acc && g_clock) { a = g_clock->get(); cudaEventRecord(a, st); }
+  Timer(PhaseClock* c, cudaStream_t s, double* accum) : clk(c), st(s), acc(accum) {
+    if (acc && clk) { a = clk->get(); cudaEventRecord(a, st); }
   }
   ~Timer() {
     if (a) {
-      b = g_clock->get();
+      cudaEvent_t b = clk->get();
       cudaEventRecord(b, st);
-      g_clock->pending.push_back({a, b, acc});
+      clk->pending.push_back({a, b, acc});
     }
   }
 };
 
+// Stream-ordered device buffer: allocation and release are ordered on the owning stream, so
+// creating and retiring tasks never synchronises the device.
 struct DBuf {
   double* p = nullptr;
-  ~DBuf() { if (p) cudaFree(p); }
-  int alloc(size_t n) {
-    if (cudaMalloc((void**)&p, (n ? n : 1) * sizeof(double)) != cudaSuccess) { cudaGetLastError(); return LOB_ERR_NOMEM; }
+  cudaStream_t st = nullptr;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { if (p) cudaFreeAsync(p, st); }
+  int alloc(size_t n, cudaStream_t s) {
+    st = s;
+    if (cudaMallocAsync((void**)&p, (n ? n : 1) * sizeof(double), s) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return LOB_ERR_NOMEM;
+    }
     return LOB_OK;
   }
 };
+
+// Pinned host words a task reads back asynchronously (residual norms, factorisation status,
+// Ritz values) and the active-column map it uploads. Boxes come from a process-wide pool.
+struct HostBox {
+  double relres[64];
+  double theta[64];
+  int32_t info[4];
+  int32_t map[64];
+};
+std::mutex g_box_mu;
+std::vector<HostBox*> g_box_free;
+HostBox* box_get() {
+  std::lock_guard<std::mutex> g(g_box_mu);
+  if (g_box_free.empty()) {
+    HostBox* chunk = nullptr;
+    if (cudaHostAlloc((void**)&chunk, 64 * sizeof(HostBox), cudaHostAllocPortable) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    for (int i = 0; i < 64; i++) g_box_free.push_back(chunk + i);
+  }
+  HostBox* b = g_box_free.back();
+  g_box_free.pop_back();
+  memset(b, 0, sizeof(*b));
+  return b;
+}
+void box_put(HostBox* b) {
+  if (!b) return;
+  std::lock_guard<std::mutex> g(g_box_mu);
+  g_box_free.push_back(b);
+}
 
 enum { PH_SPMM, PH_GRAM, PH_RR, PH_UPDATE, PH_PRECOND, PH_RESID, PH_ORTH, PH_GUESS };
 
-struct Solver {
-  const lob_matrix* M;
-  int64_t n, n_act;
-  int nb, k, spmm_mode, blas_mode;
-  cudaStream_t st;
-  double normH;
-  lob_stats* stats;
-  bool timing;
-  int ldS;
-  DBuf S, HS, P, HP, R, W, Tn, THn, Tp, THp, G, Mm, Cc, Cx, theta, thw, work, rrwork, part, relres_d, mu, C2, Z;
-  DBuf info_d;
-  int* map_d = nullptr;
-  std::vector<double> relres_h;
-  int npart;
+// info slots in the host box
+enum { SLOT_W = 0, SLOT_P = 1, SLOT_RR = 2 };
 
-  ~Solver() { if (map_d) cudaFree(map_d); }
+enum {
+  PC_INIT, PC_GUESS_CHILD, PC_PHASE, PC_RUN_SPMM0, PC_RUN_RR0, PC_RUN_RR0_CHECK, PC_ITER_RESID, PC_ITER_DECIDE,
+  PC_ITER_CHOL, PC_ITER_RR, PC_ITER_RR_CHECK, PC_RUN_END, PC_FINISH, PC_OUT, PC_END
+};
+
+size_t solver_doubles(int64_t n, int nb) {
+  const size_t m = 3 * (size_t)nb;
+  size_t d = 2 * (size_t)n * m + 8 * (size_t)n * nb;       // S, HS; P, HP, R, W, Tn, THn, Tp, THp
+  d += 11 * m * m + 3 * m + 2 * (size_t)nb;                 // G, M, C, Cx, C2, Z, M_P, C_P, ...
+  d += lob_gram_work_doubles(n, 1, 1) * m * m;              // Gram chunk partials
+  d += lob_rr_work_doubles((int)m);
+  d += (size_t)nblk(n) * 2 * m;                             // residual partials
+  return d;
+}
+
+}  // namespace
+
+struct lob_task {
+  // problem
+  lob_matrix* M = nullptr;
+  int64_t n = 0, n_act = 0;
+  int nb = 0, k = 0;
+  double tol = 0.0, normH = 0.0;
+  lob_solve_opts o{};
+  const double* X0 = nullptr;
+  double* Xout = nullptr;
+  cudaStream_t st = nullptr;
+  bool timing = false;
+  lob_stats stats{};
+  PhaseClock clock;
+  std::chrono::steady_clock::time_point t0;
+  // device state
+  int ldS = 0;
+  DBuf S, HS, P, HP, R, W, Tn, THn, Tp, THp, G, Mm, Cc, Cx, theta, thw, work, rrwork, part, relres_d, mu, C2, Z;
+  DBuf MmP, CcP, thP, info_d, imap;
+  DBuf gEc, gHEc, gG, gM, gth, gC, gwk;  // dense initial guess
+  HostBox* hb = nullptr;
+  cudaEvent_t ev = nullptr;
+  // control
+  int pc = PC_INIT, status = LOB_OK, run_status = LOB_OK, phase = 0;
+  int spmm_mode = LOB_SPMM_FP64, blas_mode = LOB_SPMM_FP64;
+  double run_tol = 0.0;
+  int run_max = 0, max_iter = 0;
+  int it = 0, restarts = 0, na = 0, m = 0, iters_total = 0, restarts_total = 0;
+  bool haveP = false, retry = false, wretry = false;
+  // the SpMM the task waits for: Y = H X on contiguous n x ncol blocks, then Y copied to post
+  const double* sp_x = nullptr;
+  double* sp_y = nullptr;
+  int sp_ncol = 0;
+  double* sp_post = nullptr;
+  int sp_post_ld = 0;
+  lob_task* child = nullptr;
+
+  ~lob_task() {
+    delete child;
+    if (ev) cudaEventDestroy(ev);
+    box_put(hb);
+  }
+
+  double* ph(int i) { return timing ? &stats.phase_ms[i] : nullptr; }
+  PhaseClock* clk() { return timing ? &clock : nullptr; }
 
   int alloc() {
     ldS = 3 * nb;
-    const size_t nS = (size_t)n * ldS, nv = (size_t)n * nb, m = ldS;
-    LOB_TRY(S.alloc(nS)); LOB_TRY(HS.alloc(nS));
-    LOB_TRY(P.alloc(nv)); LOB_TRY(HP.alloc(nv)); LOB_TRY(R.alloc(nv)); LOB_TRY(W.alloc(nv));
-    LOB_TRY(Tn.alloc(nv)); LOB_TRY(THn.alloc(nv)); LOB_TRY(Tp.alloc(nv)); LOB_TRY(THp.alloc(nv));
-    LOB_TRY(G.alloc(m * m)); LOB_TRY(Mm.alloc(m * m)); LOB_TRY(Cc.alloc(m * m)); LOB_TRY(Cx.alloc(m * m)); LOB_TRY(theta.alloc(m)); LOB_TRY(thw.alloc(m));
-    LOB_TRY(work.alloc(lob_gram_work_doubles(n, 1, 1) * m * m));  // bound over every (p, q) <= m
-    LOB_TRY(rrwork.alloc(lob_rr_work_doubles((int)m)));
-    npart = (int)nblk(n);
-    LOB_TRY(part.alloc((size_t)npart * 2 * m));
-    LOB_TRY(relres_d.alloc(nb)); LOB_TRY(mu.alloc(nb)); LOB_TRY(C2.alloc(m * m)); LOB_TRY(Z.alloc(m * m));
-    LOB_TRY(info_d.alloc(1));
-    if (cudaMalloc((void**)&map_d, 64 * sizeof(int)) != cudaSuccess) { cudaGetLastError(); return LOB_ERR_NOMEM; }
-    relres_h.assign(nb, 0.0);
+    const size_t nS = (size_t)n * ldS, nv = (size_t)n * nb, mm = ldS;
+    LOB_TRY(S.alloc(nS, st)); LOB_TRY(HS.alloc(nS, st));
+    LOB_TRY(P.alloc(nv, st)); LOB_TRY(HP.alloc(nv, st)); LOB_TRY(R.alloc(nv, st)); LOB_TRY(W.alloc(nv, st));
+    LOB_TRY(Tn.alloc(nv, st)); LOB_TRY(THn.alloc(nv, st)); LOB_TRY(Tp.alloc(nv, st)); LOB_TRY(THp.alloc(nv, st));
+    LOB_TRY(G.alloc(mm * mm, st)); LOB_TRY(Mm.alloc(mm * mm, st)); LOB_TRY(Cc.alloc(mm * mm, st));
+    LOB_TRY(Cx.alloc(mm * mm, st)); LOB_TRY(theta.alloc(mm, st)); LOB_TRY(thw.alloc(mm, st));
+    LOB_TRY(MmP.alloc(mm * mm, st)); LOB_TRY(CcP.alloc(mm * mm, st)); LOB_TRY(thP.alloc(mm, st));
+    LOB_TRY(work.alloc(lob_gram_work_doubles(n, 1, 1) * mm * mm, st));  // bound over every (p, q) <= m
+    LOB_TRY(rrwork.alloc(lob_rr_work_doubles((int)mm), st));
+    LOB_TRY(part.alloc((size_t)nblk(n) * 2 * mm, st));
+    LOB_TRY(relres_d.alloc(nb, st)); LOB_TRY(mu.alloc(nb, st)); LOB_TRY(C2.alloc(mm * mm, st));
+    LOB_TRY(Z.alloc(mm * mm, st));
+    LOB_TRY(info_d.alloc(2, st));  // 4 int32 slots
+    LOB_TRY(imap.alloc(32, st));   // 64 int32
+    hb = box_get();
+    if (!hb) return LOB_ERR_NOMEM;
+    LOB_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     return LOB_OK;
   }
 
-  double* ph(int i) { return (timing && stats) ? &stats->phase_ms[i] : nullptr; }
+  int32_t* info_slot(int s) { return reinterpret_cast<int32_t*>(info_d.p) + s; }
+  int* map_d() { return reinterpret_cast<int*>(imap.p); }
 
-  // projected eigenproblem in the solver's block arithmetic (native FP64 or double-float)
-  int rr(int m, const double* Gp, const double* Mp, double* th, double* Cp, int chol_only = 0) {
-    if (blas_mode == LOB_SPMM_MIXED)
-      return lob_rr_launch_df(m, Gp, Mp, th, Cp, (int32_t*)info_d.p, rrwork.p, st, chol_only);
-    return lob_rr_launch(m, Gp, Mp, th, Cp, (int32_t*)info_d.p, rrwork.p, st, chol_only);
+  int sync_point() {
+    LOB_CUDA(cudaEventRecord(ev, st));
+    return LOB_TASK_SYNC;
   }
 
-  int spmm(const double* X, int ldx, double* Y, int ldy, int ncol) {
-    // the SpMM kernel wants contiguous n x ncol blocks: stage through Tp / THp when strided
-    const double* src = X;
-    double* dst = Y;
+  // projected eigenproblem in the task's block arithmetic (native FP64 or double-float)
+  int rr(int mm, const double* Gp, const double* Mp, double* th, double* Cp, int slot, int chol_only) {
+    if (blas_mode == LOB_SPMM_MIXED)
+      return lob_rr_launch_df(mm, Gp, Mp, th, Cp, info_slot(slot), rrwork.p, st, chol_only);
+    return lob_rr_launch(mm, Gp, Mp, th, Cp, info_slot(slot), rrwork.p, st, chol_only);
+  }
+
+  int read_info(int slot) {
+    LOB_CUDA(cudaMemcpyAsync(&hb->info[slot], info_slot(slot), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    return LOB_OK;
+  }
+
+  // Register the product Y = H X (X, Y: ncol columns with leading dimensions ldx, ldy).
+  int want_spmm(const double* X, int ldx, double* Y, int ldy, int ncol) {
+    sp_x = X;
     if (ldx != ncol) {
       (k_copy_cols<<<nblk(n * ncol), BS, 0, st>>>(n, ncol, X, ldx, nullptr, Tp.p, ncol), LOB_LAUNCHED());
-      src = Tp.p;
+      sp_x = Tp.p;
     }
-    if (ldy != ncol) dst = THp.p;
-    {
-      Timer t(st, ph(PH_SPMM));  // the SpMM launch itself (zeroing of Y and the kernel)
-      Timer tm(st, (timing && stats) ? &stats->spmm_ms_mode[spmm_mode] : nullptr);
-      LOB_TRY(lob_spmm_launch(M, spmm_mode, src, dst, ncol, n_act, st));
-    }
-    if (ldy != ncol) (k_copy_cols<<<nblk(n * ncol), BS, 0, st>>>(n, ncol, THp.p, ncol, nullptr, Y, ldy), LOB_LAUNCHED());
-    if (stats) {
-      stats->spmm_calls++;
-      const double vb = spmm_mode == LOB_SPMM_MIXED ? 4.0 : 8.0;  // FP32 or FP64 (split pair) values
-      const double bytes = (double)M->T.nnz * (vb + 4.0) + (double)M->T.ntiles * 12.0 + (double)n * ncol * 16.0;
-      stats->spmm_bytes += bytes;
-      stats->spmm_bytes_mode[spmm_mode] += bytes;
-      stats->spmm_calls_mode[spmm_mode]++;
-    }
+    sp_y = ldy != ncol ? THp.p : Y;
+    sp_post = ldy != ncol ? Y : nullptr;
+    sp_post_ld = ldy;
+    sp_ncol = ncol;
+    stats.spmm_calls++;
+    const double vb = spmm_mode == LOB_SPMM_MIXED ? 4.0 : 8.0;  // FP32 or FP64 (split pair) values
+    const double bytes = (double)M->T.nnz * (vb + 4.0) + (double)M->T.ntiles * 12.0 + (double)n * ncol * 16.0;
+    stats.spmm_bytes += bytes;
+    stats.spmm_bytes_mode[spmm_mode] += bytes;
+    stats.spmm_calls_mode[spmm_mode]++;
     LOB_CUDA(cudaGetLastError());
+    return LOB_TASK_SPMM;
+  }
+
+  int spmm_post() {
+    if (sp_post)
+      (k_copy_cols<<<nblk(n * sp_ncol), BS, 0, st>>>(n, sp_ncol, sp_y, sp_ncol, nullptr, sp_post, sp_post_ld),
+       LOB_LAUNCHED());
+    sp_post = nullptr;
     return LOB_OK;
   }
 
-  // Rayleigh-Ritz on the first m columns of S / HS. Returns info (0 ok).
-  int rayleigh_ritz(int m, int* info) {
+  // G = S^T H S, M = S^T S on the first mm columns, then the Rayleigh-Ritz solve (status to SLOT_RR)
+  int rr_begin(int mm) {
     {
-      Timer t(st, ph(PH_GRAM));
-      LOB_TRY(lob_gram_launch_ws(n_act, m, S.p, ldS, m, HS.p, ldS, G.p, blas_mode, work.p, st));
-      LOB_TRY(lob_gram_launch_ws(n_act, m, S.p, ldS, m, S.p, ldS, Mm.p, blas_mode, work.p, st));
+      Timer t(clk(), st, ph(PH_GRAM));
+      // both symmetric (H is): only their upper triangles are formed (and read by the solve)
+      LOB_TRY(lob_gram_launch_ws(n_act, mm, S.p, ldS, mm, HS.p, ldS, G.p, blas_mode, work.p, st, 1));
+      LOB_TRY(lob_gram_launch_ws(n_act, mm, S.p, ldS, mm, S.p, ldS, Mm.p, blas_mode, work.p, st, 1));
     }
-    Timer t(st, ph(PH_RR));
-    LOB_TRY(rr(m, G.p, Mm.p, theta.p, Cc.p));
-    int hinfo = 0;
-    LOB_CUDA(cudaMemcpyAsync(&hinfo, info_d.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LOB_CUDA(cudaStreamSynchronize(st));
-    *info = hinfo;
-    return LOB_OK;
+    Timer t(clk(), st, ph(PH_RR));
+    LOB_TRY(rr(mm, G.p, Mm.p, theta.p, Cc.p, SLOT_RR, 0));
+    return read_info(SLOT_RR);
   }
 
-  // Cholesky-QR of ncol columns at S[:, col0] (and the same transform on HS if withH):
-  // B <- B L^{-T} with B^T B = L L^T. Uses the RR kernel with G = M (then C = L^{-T}).
-  int cholqr(int col0, int ncol, bool withH, int* info) {
-    Timer t(st, ph(PH_ORTH));
+  // Cholesky-QR, first half: B^T B = L L^T for the ncol columns at S[:, col0]; C = L^{-T}.
+  int cholqr_begin(int col0, int ncol, double* Mb, double* Cb, double* thb, int slot) {
+    Timer t(clk(), st, ph(PH_ORTH));
     const double* B = S.p + col0;
-    LOB_TRY(lob_gram_launch_ws(n_act, ncol, B, ldS, ncol, B, ldS, Mm.p, blas_mode, work.p, st));
-    LOB_TRY(rr(ncol, Mm.p, Mm.p, thw.p, Cc.p, 1));
-    int hinfo = 0;
-    LOB_CUDA(cudaMemcpyAsync(&hinfo, info_d.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LOB_CUDA(cudaStreamSynchronize(st));
-    *info = hinfo;
-    if (hinfo) return LOB_OK;
-    LOB_TRY(lob_lincomb_launch(n_act, ncol, B, ldS, ncol, Cc.p, Tn.p, ncol, blas_mode, st));
+    LOB_TRY(lob_gram_launch_ws(n_act, ncol, B, ldS, ncol, B, ldS, Mb, blas_mode, work.p, st, 1));
+    LOB_TRY(rr(ncol, Mb, Mb, thb, Cb, slot, 1));
+    return read_info(slot);
+  }
+
+  // Cholesky-QR, second half: B <- B C (and the same on HS when withH).
+  int cholqr_finish(int col0, int ncol, bool withH, const double* Cb) {
+    Timer t(clk(), st, ph(PH_ORTH));
+    LOB_TRY(lob_lincomb_launch(n_act, ncol, S.p + col0, ldS, ncol, Cb, Tn.p, ncol, blas_mode, st));
     (k_copy_cols<<<nblk(n_act * ncol), BS, 0, st>>>(n_act, ncol, Tn.p, ncol, nullptr, S.p + col0, ldS), LOB_LAUNCHED());
     if (withH) {
-      LOB_TRY(lob_lincomb_launch(n_act, ncol, HS.p + col0, ldS, ncol, Cc.p, Tn.p, ncol, blas_mode, st));
-      (k_copy_cols<<<nblk(n_act * ncol), BS, 0, st>>>(n_act, ncol, Tn.p, ncol, nullptr, HS.p + col0, ldS), LOB_LAUNCHED());
+      LOB_TRY(lob_lincomb_launch(n_act, ncol, HS.p + col0, ldS, ncol, Cb, Tn.p, ncol, blas_mode, st));
+      (k_copy_cols<<<nblk(n_act * ncol), BS, 0, st>>>(n_act, ncol, Tn.p, ncol, nullptr, HS.p + col0, ldS),
+       LOB_LAUNCHED());
     }
     LOB_CUDA(cudaGetLastError());
     return LOB_OK;
   }
 
-  int residual() {
-    Timer t(st, ph(PH_RESID));
+  int residual_begin() {
+    Timer t(clk(), st, ph(PH_RESID));
     const size_t smem = (BS / 32) * 2 * nb * sizeof(double);
     (k_residual<<<nblk(n_act), BS, smem, st>>>(n_act, nb, S.p, ldS, HS.p, ldS, theta.p, R.p, part.p), LOB_LAUNCHED());
     (k_relres<<<1, 64, 0, st>>>((int)nblk(n_act), nb, part.p, normH, relres_d.p), LOB_LAUNCHED());
-    LOB_CUDA(cudaMemcpyAsync(relres_h.data(), relres_d.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
-    LOB_CUDA(cudaStreamSynchronize(st));
-    if (g_clock) g_clock->resolve();
+    LOB_CUDA(cudaMemcpyAsync(hb->relres, relres_d.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
     return LOB_OK;
   }
 
-  // X <- S C[:, :nb], HX <- HS C[:, :nb]; P <- S[:, nb:m] C[nb:m, :nb], HP likewise.
-  int update(int m) {
-    Timer t(st, ph(PH_UPDATE));
-    // first nb columns of the m x m (leading dimension m) Ritz coefficients -> compact m x nb
-    (k_copy_cols<<<nblk((int64_t)m * nb), BS, 0, st>>>(m, nb, Cc.p, m, nullptr, Cx.p, nb), LOB_LAUNCHED());
-    LOB_TRY(lob_lincomb_launch(n_act, m, S.p, ldS, nb, Cx.p, Tn.p, nb, blas_mode, st));
-    LOB_TRY(lob_lincomb_launch(n_act, m, HS.p, ldS, nb, Cx.p, THn.p, nb, blas_mode, st));
-    if (m > nb) {
-      // C rows nb..m-1 (a row-major m x m matrix: rows start at Cc + nb*m, leading dimension m)
-      // -> compact (m-nb) x nb coefficient block in C2
-      (k_copy_cols<<<nblk((int64_t)(m - nb) * nb), BS, 0, st>>>(m - nb, nb, Cc.p + (size_t)nb * m, m, nullptr, C2.p, nb), LOB_LAUNCHED());
-      LOB_TRY(lob_lincomb_launch(n_act, m - nb, S.p + nb, ldS, nb, C2.p, P.p, nb, blas_mode, st));
-      LOB_TRY(lob_lincomb_launch(n_act, m - nb, HS.p + nb, ldS, nb, C2.p, HP.p, nb, blas_mode, st));
+  // X <- S C[:, :nb], HX <- HS C[:, :nb]; P <- S[:, nb:mm] C[nb:mm, :nb], HP likewise.
+  int update(int mm) {
+    Timer t(clk(), st, ph(PH_UPDATE));
+    // first nb columns of the mm x mm (leading dimension mm) Ritz coefficients -> compact mm x nb
+    (k_copy_cols<<<nblk((int64_t)mm * nb), BS, 0, st>>>(mm, nb, Cc.p, mm, nullptr, Cx.p, nb), LOB_LAUNCHED());
+    LOB_TRY(lob_lincomb_launch(n_act, mm, S.p, ldS, nb, Cx.p, Tn.p, nb, blas_mode, st));
+    LOB_TRY(lob_lincomb_launch(n_act, mm, HS.p, ldS, nb, Cx.p, THn.p, nb, blas_mode, st));
+    if (mm > nb) {
+      // rows nb..mm-1 of C (row-major, leading dimension mm) -> compact (mm-nb) x nb block in C2
+      (k_copy_cols<<<nblk((int64_t)(mm - nb) * nb), BS, 0, st>>>(mm - nb, nb, Cc.p + (size_t)nb * mm, mm, nullptr,
+                                                                    C2.p, nb),
+       LOB_LAUNCHED());
+      LOB_TRY(lob_lincomb_launch(n_act, mm - nb, S.p + nb, ldS, nb, C2.p, P.p, nb, blas_mode, st));
+      LOB_TRY(lob_lincomb_launch(n_act, mm - nb, HS.p + nb, ldS, nb, C2.p, HP.p, nb, blas_mode, st));
     }
     (k_copy_cols<<<nblk(n_act * nb), BS, 0, st>>>(n_act, nb, Tn.p, nb, nullptr, S.p, ldS), LOB_LAUNCHED());
     (k_copy_cols<<<nblk(n_act * nb), BS, 0, st>>>(n_act, nb, THn.p, nb, nullptr, HS.p, ldS), LOB_LAUNCHED());
@@ -314,140 +431,321 @@ struct Solver {
     return LOB_OK;
   }
 
-  // One full solve from X currently in S[:, :nb] (rows < n_act). Returns LOB_OK,
-  // LOB_ERR_NOCONV or an error.
-  int run(double tol, int max_iter, bool use_precond, int shift_mode, int* iters_out, int* restarts_out) {
-    int info = 0;
-    // step 1: Rayleigh-Ritz on X alone (also orthonormalises it)
-    LOB_TRY(spmm(S.p, ldS, HS.p, ldS, nb));
-    LOB_TRY(rayleigh_ritz(nb, &info));
-    if (info) {  // X0 rank-deficient: orthonormalise a randomised copy
-      (k_random<<<nblk(n * nb), BS, 0, st>>>(n, n_act, nb, ldS, 0, nb, 0x5EEDull, S.p), LOB_LAUNCHED());
-      LOB_TRY(spmm(S.p, ldS, HS.p, ldS, nb));
-      LOB_TRY(rayleigh_ritz(nb, &info));
-      if (info) return LOB_ERR_BREAKDOWN;
-    }
-    LOB_TRY(update(nb));
-    bool haveP = false;
-    int restarts = 0, it = 0;
-    std::vector<int> act;
-    int status = LOB_ERR_NOCONV;
-    for (it = 1; it <= max_iter; it++) {
-      LOB_TRY(residual());
-      act.clear();
-      bool conv = true;
-      for (int j = 0; j < nb; j++) {
-        if (j < k && !(relres_h[j] <= tol)) conv = false;
-        if (!(relres_h[j] <= tol)) act.push_back(j);
-      }
-      if (conv) { status = LOB_OK; break; }
-      const int na = (int)act.size();
-      // W = T^{-1} R (step 6) with the rules of Section 4.3
-      {
-        Timer t(st, ph(PH_PRECOND));
-        const bool pc = use_precond && M->P.bp > 0 && it > 3 && relres_h[0] <= 1e-1;
-        if (pc) {
-          (k_shifts<<<1, 32, 0, st>>>(nb, shift_mode, theta.p, relres_d.p, normH, mu.p), LOB_LAUNCHED());
-          LOB_TRY(lob_precond_launch(M, mu.p, R.p, W.p, nb, n_act, st));
-        }
-        LOB_CUDA(cudaMemcpyAsync(map_d, act.data(), na * sizeof(int), cudaMemcpyHostToDevice, st));
-        (k_copy_cols<<<nblk(n_act * na), BS, 0, st>>>(n_act, na, pc ? W.p : R.p, nb, map_d, S.p + nb, ldS), LOB_LAUNCHED());
-      }
-      // W <- W - X (X^T W), then Cholesky-QR (step 7)
-      {
-        Timer t(st, ph(PH_ORTH));
-        LOB_TRY(lob_gram_launch_ws(n_act, nb, S.p, ldS, na, S.p + nb, ldS, Z.p, blas_mode, work.p, st));
-        (k_proj_coef<<<nblk((nb + na) * na), BS, 0, st>>>(nb, na, Z.p, C2.p), LOB_LAUNCHED());
-        LOB_TRY(lob_lincomb_launch(n_act, nb + na, S.p, ldS, na, C2.p, Tn.p, na, blas_mode, st));
-        (k_copy_cols<<<nblk(n_act * na), BS, 0, st>>>(n_act, na, Tn.p, na, nullptr, S.p + nb, ldS), LOB_LAUNCHED());
-      }
-      LOB_TRY(cholqr(nb, na, false, &info));
-      if (info) {
-        // W lost rank: replace it by seeded random directions projected as above
-        (k_random<<<nblk(n * na), BS, 0, st>>>(n, n_act, nb, ldS, nb, na, 0xB10Cull + it, S.p), LOB_LAUNCHED());
-        LOB_TRY(cholqr(nb, na, false, &info));
-        if (info) { status = LOB_ERR_BREAKDOWN; break; }
-      }
-      LOB_TRY(spmm(S.p + nb, ldS, HS.p + nb, ldS, na));
-      int m = nb + na;
-      if (haveP) {
-        (k_copy_cols<<<nblk(n_act * na), BS, 0, st>>>(n_act, na, P.p, nb, map_d, S.p + m, ldS), LOB_LAUNCHED());
-        (k_copy_cols<<<nblk(n_act * na), BS, 0, st>>>(n_act, na, HP.p, nb, map_d, HS.p + m, ldS), LOB_LAUNCHED());
-        LOB_TRY(cholqr(m, na, true, &info));
-        if (!info) m += na;
-        else restarts++;
-      }
-      LOB_TRY(rayleigh_ritz(m, &info));
-      if (info && m > nb + na) {  // drop P and retry (restart)
-        restarts++;
-        m = nb + na;
-        LOB_TRY(rayleigh_ritz(m, &info));
-      }
-      if (info) { status = LOB_ERR_BREAKDOWN; break; }
-      LOB_TRY(update(m));
-      haveP = true;
-    }
-    if (it > max_iter) it = max_iter;
-    *iters_out = it;
-    *restarts_out = restarts;
-    return status;
-  }
-};
-
-}  // namespace
-
-static int initial_guess(lob_matrix* m, int nb, const lob_solve_opts* o, double* Xout, cudaStream_t st) {
-  // eq. 12: eigenvectors of the leading n_small x n_small block (the smaller configuration
-  // space), zero-padded. The small problem is solved by this same LOBPCG from seeded random
-  // vectors (the paper's multi-level use, Section 3.3.1), or directly when it is tiny.
-  const int64_t n = m->T.n, ns = o->n_small;
-  lob_solve_opts so = *o;
-  so.n_small = 0;
-  so.precond = o->precond;
-  so.max_iter = 2000;
-  so.refine_iter = 0;
-  so.mixed_tol = 0.0;
-  so.verbose = 0;
-  std::vector<double> lam(nb);
-  if (ns <= 3 * nb) {
-    // dense: G = H11 (by SpMM of identity columns), M = I, Rayleigh-Ritz gives all eigenpairs
+  // eq. 12 for a tiny leading block (ns <= 3 nb): G = H_11 by SpMMs of unit columns, M = I,
+  // Rayleigh-Ritz gives all its eigenpairs; X = [C[:, :nb]; 0], seeded random columns beyond ns.
+  int guess_dense(int64_t ns, double* Xo) {
     const int nsi = (int)ns;
-    DBuf E, HE, Gd, Md, th, Cd, wk, inf;
-    LOB_TRY(E.alloc((size_t)n * nsi)); LOB_TRY(HE.alloc((size_t)n * nsi));
-    LOB_TRY(Gd.alloc((size_t)nsi * nsi)); LOB_TRY(Md.alloc((size_t)nsi * nsi)); LOB_TRY(th.alloc(nsi));
-    LOB_TRY(Cd.alloc((size_t)nsi * nsi)); LOB_TRY(wk.alloc(lob_rr_work_doubles(nsi))); LOB_TRY(inf.alloc(1));
-    std::vector<double> eye((size_t)nsi * nsi, 0.0);
-    for (int i = 0; i < nsi; i++) eye[(size_t)i * nsi + i] = 1.0;
-    LOB_CUDA(cudaMemsetAsync(E.p, 0, (size_t)n * nsi * 8, st));
-    LOB_CUDA(cudaMemcpyAsync(E.p, eye.data(), eye.size() * 8, cudaMemcpyHostToDevice, st));
-    LOB_CUDA(cudaMemcpyAsync(Md.p, eye.data(), eye.size() * 8, cudaMemcpyHostToDevice, st));
+    const int cw = nsi < 64 ? nsi : 64;
+    LOB_TRY(gEc.alloc((size_t)n * cw, st)); LOB_TRY(gHEc.alloc((size_t)n * cw, st));
+    LOB_TRY(gG.alloc((size_t)nsi * nsi, st)); LOB_TRY(gM.alloc((size_t)nsi * nsi, st));
+    LOB_TRY(gth.alloc(nsi, st)); LOB_TRY(gC.alloc((size_t)nsi * nsi, st));
+    LOB_TRY(gwk.alloc(lob_rr_work_doubles(nsi), st));
+    LOB_CUDA(cudaMemsetAsync(gM.p, 0, (size_t)nsi * nsi * 8, st));
+    (k_unit_cols<<<1, 128, 0, st>>>(0, nsi, nsi, gM.p), LOB_LAUNCHED());
     for (int c0 = 0; c0 < nsi; c0 += 64) {
       const int w = nsi - c0 < 64 ? nsi - c0 : 64;
-      DBuf Ec, HEc;
-      LOB_TRY(Ec.alloc((size_t)n * w)); LOB_TRY(HEc.alloc((size_t)n * w));
-      (k_copy_cols<<<nblk(n * w), BS, 0, st>>>(n, w, E.p + c0, nsi, nullptr, Ec.p, w), LOB_LAUNCHED());
-      LOB_TRY(lob_spmm_launch(m, LOB_SPMM_FP64, Ec.p, HEc.p, w, ns, st));
-      (k_copy_cols<<<nblk(ns * w), BS, 0, st>>>(ns, w, HEc.p, w, nullptr, Gd.p + c0, nsi), LOB_LAUNCHED());
-      LOB_CUDA(cudaStreamSynchronize(st));
+      LOB_CUDA(cudaMemsetAsync(gEc.p, 0, (size_t)n * w * 8, st));
+      (k_unit_cols<<<1, 128, 0, st>>>(c0, w, w, gEc.p), LOB_LAUNCHED());
+      LOB_TRY(lob_spmm_launch(M, LOB_SPMM_FP64, gEc.p, gHEc.p, w, ns, st));
+      (k_copy_cols<<<nblk(ns * w), BS, 0, st>>>(ns, w, gHEc.p, w, nullptr, gG.p + c0, nsi), LOB_LAUNCHED());
     }
-    LOB_TRY(lob_rr_launch(nsi, Gd.p, Md.p, th.p, Cd.p, (int32_t*)inf.p, wk.p, st));
-    // X = [C[:, :min(nb, ns)] ; 0], remaining columns seeded random (in the first ns rows)
-    (k_random<<<nblk(n * nb), BS, 0, st>>>(n, ns, nb, nb, 0, nb, o->seed ^ 0x1A5Eull, Xout), LOB_LAUNCHED());
+    LOB_TRY(lob_rr_launch(nsi, gG.p, gM.p, gth.p, gC.p, info_slot(3), gwk.p, st));
+    (k_random<<<nblk(n * nb), BS, 0, st>>>(n, ns, nb, nb, 0, nb, o.seed ^ 0x1A5Eull, Xo), LOB_LAUNCHED());
     const int nc = nsi < nb ? nsi : nb;
-    (k_copy_cols<<<nblk(ns * nc), BS, 0, st>>>(ns, nc, Cd.p, nsi, nullptr, Xout, nb), LOB_LAUNCHED());
-    LOB_CUDA(cudaStreamSynchronize(st));
+    (k_copy_cols<<<nblk(ns * nc), BS, 0, st>>>(ns, nc, gC.p, nsi, nullptr, Xo, nb), LOB_LAUNCHED());
+    LOB_CUDA(cudaGetLastError());
     return LOB_OK;
   }
-  LOB_CUDA(cudaMemsetAsync(Xout, 0, (size_t)n * nb * 8, st));
-  // The guess only needs the accuracy of eq. 12 itself (its residual is set by the coupling
-  // ||H_21||), so the smaller problem is solved to a moderate tolerance.
-  int rc = lob_solve_impl(m, nb, nb, 1e-4, nullptr, &so, lam.data(), Xout, nullptr, ns);
-  if (rc != LOB_OK && rc != LOB_ERR_NOCONV) return rc;
+
+  int step();
+};
+
+namespace {
+int task_init(lob_task* t, lob_matrix* m, int32_t k, int32_t nb, double tol, const double* X0,
+              const lob_solve_opts* o, double* X, int64_t n_act, cudaStream_t st, bool timing) {
+  t->M = m; t->n = m->T.n; t->n_act = n_act; t->nb = nb; t->k = k; t->tol = tol; t->o = *o; t->X0 = X0;
+  t->Xout = X; t->st = st; t->timing = timing;
+  t->normH = o->norm_H > 0.0 ? o->norm_H : m->norm_inf;
+  // block products: native FP64 in the plain solver, FP64-class double-float in MIXED
+  t->blas_mode = o->mode == LOB_MODE_MIXED ? LOB_SPMM_MIXED : LOB_SPMM_FP64;
+  t->max_iter = o->max_iter > 0 ? o->max_iter : 500;
+  t->t0 = std::chrono::steady_clock::now();
+  return t->alloc();
+}
+}  // namespace
+
+int lob_task::step() {
+  if (child) {
+    const int r = child->step();
+    if (r != LOB_TASK_DONE) return r;
+    const int crc = child->status;
+    delete child;
+    child = nullptr;
+    if (crc != LOB_OK && crc != LOB_ERR_NOCONV) { status = crc; pc = PC_END; return LOB_TASK_DONE; }
+    (k_copy_cols<<<nblk(n * nb), BS, 0, st>>>(n, nb, W.p, nb, nullptr, S.p, ldS), LOB_LAUNCHED());
+    pc = PC_PHASE;
+  }
+  for (;;) {
+    switch (pc) {
+      case PC_INIT: {
+        Timer t(clk(), st, ph(PH_GUESS));
+        if (X0) {
+          (k_copy_cols<<<nblk(n * nb), BS, 0, st>>>(n, nb, X0, nb, nullptr, S.p, ldS), LOB_LAUNCHED());
+        } else if (o.n_small > 0 && o.n_small < n_act) {
+          // eq. 12: eigenvectors of the leading n_small x n_small block (the smaller
+          // configuration space), zero-padded. The small problem is solved directly when it is
+          // tiny, else by a child LOBPCG task from seeded random vectors (the multi-level use of
+          // Section 3.3.1) to a moderate tolerance: the guess only needs the accuracy of eq. 12
+          // itself, whose residual is set by the coupling ||H_21||.
+          const int64_t ns = o.n_small;
+          if (ns <= 3 * nb) {
+            LOB_TRY(guess_dense(ns, W.p));
+          } else {
+            LOB_CUDA(cudaMemsetAsync(W.p, 0, (size_t)n * nb * 8, st));
+            lob_solve_opts so = o;
+            so.n_small = 0;
+            so.max_iter = 2000;
+            so.refine_iter = 0;
+            so.mixed_tol = 0.0;
+            so.verbose = 0;
+            child = new lob_task();
+            const int rc = task_init(child, M, nb, nb, 1e-4, nullptr, &so, W.p, ns, st, false);
+            if (rc != LOB_OK) { delete child; child = nullptr; return rc; }
+            pc = PC_GUESS_CHILD;
+            return step();
+          }
+          (k_copy_cols<<<nblk(n * nb), BS, 0, st>>>(n, nb, W.p, nb, nullptr, S.p, ldS), LOB_LAUNCHED());
+        } else {
+          (k_random<<<nblk(n * nb), BS, 0, st>>>(n, n_act, nb, ldS, 0, nb, o.seed, S.p), LOB_LAUNCHED());
+        }
+        LOB_CUDA(cudaGetLastError());
+        pc = PC_PHASE;
+        continue;
+      }
+      case PC_GUESS_CHILD:
+        return LOB_ERR_ARG;  // unreachable: the child is stepped above
+      case PC_PHASE: {
+        if (o.mode == LOB_MODE_MIXED && phase == 0) {
+          // phase 1: FP32-value SpMM down to the FP32 floor
+          spmm_mode = LOB_SPMM_MIXED;
+          run_tol = o.mixed_tol > 0.0 ? o.mixed_tol : (tol > 1e-6 ? tol : 1e-6);
+          run_max = max_iter;
+        } else if (o.mode == LOB_MODE_MIXED) {
+          // phase 2: FP64-class refinement products from the phase-1 vectors
+          spmm_mode = M->T.v32lo ? LOB_SPMM_DF64 : LOB_SPMM_FP64;
+          run_tol = tol;
+          run_max = o.refine_iter > 0 ? o.refine_iter : (max_iter - iters_total > 50 ? max_iter - iters_total : 50);
+        } else {
+          spmm_mode = LOB_SPMM_FP64;
+          run_tol = tol;
+          run_max = max_iter;
+        }
+        retry = false;
+        it = 0;
+        restarts = 0;
+        pc = PC_RUN_SPMM0;
+        continue;
+      }
+      case PC_RUN_SPMM0:  // step 1: Rayleigh-Ritz on X alone (also orthonormalises it)
+        pc = PC_RUN_RR0;
+        return want_spmm(S.p, ldS, HS.p, ldS, nb);
+      case PC_RUN_RR0:
+        LOB_TRY(spmm_post());
+        LOB_TRY(rr_begin(nb));
+        pc = PC_RUN_RR0_CHECK;
+        return sync_point();
+      case PC_RUN_RR0_CHECK: {
+        clock.resolve();
+        if (hb->info[SLOT_RR]) {
+          if (retry) { run_status = LOB_ERR_BREAKDOWN; pc = PC_RUN_END; continue; }
+          retry = true;  // X0 rank-deficient: orthonormalise a randomised copy
+          (k_random<<<nblk(n * nb), BS, 0, st>>>(n, n_act, nb, ldS, 0, nb, 0x5EEDull, S.p), LOB_LAUNCHED());
+          pc = PC_RUN_SPMM0;
+          continue;
+        }
+        LOB_TRY(update(nb));
+        haveP = false;
+        it = 1;
+        pc = PC_ITER_RESID;
+        continue;
+      }
+      case PC_ITER_RESID:
+        if (it > run_max) { it = run_max; run_status = LOB_ERR_NOCONV; pc = PC_RUN_END; continue; }
+        LOB_TRY(residual_begin());  // steps 4-5
+        pc = PC_ITER_DECIDE;
+        return sync_point();
+      case PC_ITER_DECIDE: {
+        clock.resolve();
+        bool conv = true;
+        na = 0;
+        for (int j = 0; j < nb; j++) {
+          if (j < k && !(hb->relres[j] <= run_tol)) conv = false;
+          if (!(hb->relres[j] <= run_tol)) hb->map[na++] = j;
+        }
+        if (conv) { run_status = LOB_OK; pc = PC_RUN_END; continue; }
+        // W = T^{-1} R (step 6) with the rules of Section 4.3
+        {
+          Timer t(clk(), st, ph(PH_PRECOND));
+          const bool pc_on = o.precond && M->P.bp > 0 && it > 3 && hb->relres[0] <= 1e-1;
+          if (pc_on) {
+            (k_shifts<<<1, 32, 0, st>>>(nb, o.precond_shift, theta.p, relres_d.p, normH, mu.p), LOB_LAUNCHED());
+            LOB_TRY(lob_precond_launch(M, mu.p, R.p, W.p, nb, n_act, o.precond_solve,
+                                       o.precond_steps > 0 ? o.precond_steps : 3, st));
+          }
+          LOB_CUDA(cudaMemcpyAsync(map_d(), hb->map, na * sizeof(int), cudaMemcpyHostToDevice, st));
+          (k_copy_cols<<<nblk(n_act * na), BS, 0, st>>>(n_act, na, pc_on ? W.p : R.p, nb, map_d(), S.p + nb, ldS),
+           LOB_LAUNCHED());
+        }
+        // W <- W - X (X^T W), then Cholesky-QR (step 7)
+        {
+          Timer t(clk(), st, ph(PH_ORTH));
+          LOB_TRY(lob_gram_launch_ws(n_act, nb, S.p, ldS, na, S.p + nb, ldS, Z.p, blas_mode, work.p, st));
+          (k_proj_coef<<<nblk((nb + na) * na), BS, 0, st>>>(nb, na, Z.p, C2.p), LOB_LAUNCHED());
+          LOB_TRY(lob_lincomb_launch(n_act, nb + na, S.p, ldS, na, C2.p, Tn.p, na, blas_mode, st));
+          (k_copy_cols<<<nblk(n_act * na), BS, 0, st>>>(n_act, na, Tn.p, na, nullptr, S.p + nb, ldS), LOB_LAUNCHED());
+        }
+        LOB_TRY(cholqr_begin(nb, na, Mm.p, Cc.p, thw.p, SLOT_W));
+        if (haveP) {
+          // P and H P restricted to the active columns, after [X W]; Cholesky-QR of P alongside W's
+          (k_copy_cols<<<nblk(n_act * na), BS, 0, st>>>(n_act, na, P.p, nb, map_d(), S.p + nb + na, ldS), LOB_LAUNCHED());
+          (k_copy_cols<<<nblk(n_act * na), BS, 0, st>>>(n_act, na, HP.p, nb, map_d(), HS.p + nb + na, ldS),
+           LOB_LAUNCHED());
+          LOB_TRY(cholqr_begin(nb + na, na, MmP.p, CcP.p, thP.p, SLOT_P));
+        }
+        wretry = false;
+        pc = PC_ITER_CHOL;
+        return sync_point();
+      }
+      case PC_ITER_CHOL: {
+        clock.resolve();
+        if (hb->info[SLOT_W]) {
+          if (wretry) { run_status = LOB_ERR_BREAKDOWN; pc = PC_RUN_END; continue; }
+          // W lost rank: replace it by seeded random directions
+          wretry = true;
+          (k_random<<<nblk(n * na), BS, 0, st>>>(n, n_act, nb, ldS, nb, na, 0xB10Cull + it, S.p), LOB_LAUNCHED());
+          LOB_TRY(cholqr_begin(nb, na, Mm.p, Cc.p, thw.p, SLOT_W));
+          return sync_point();
+        }
+        LOB_TRY(cholqr_finish(nb, na, false, Cc.p));
+        m = nb + na;
+        if (haveP) {
+          if (!hb->info[SLOT_P]) {
+            LOB_TRY(cholqr_finish(nb + na, na, true, CcP.p));
+            m += na;
+          } else {
+            restarts++;  // P lost rank: drop it for this iteration
+          }
+        }
+        pc = PC_ITER_RR;
+        return want_spmm(S.p + nb, ldS, HS.p + nb, ldS, na);
+      }
+      case PC_ITER_RR:
+        LOB_TRY(spmm_post());
+        LOB_TRY(rr_begin(m));  // eq. 9, steps 7-8
+        pc = PC_ITER_RR_CHECK;
+        return sync_point();
+      case PC_ITER_RR_CHECK: {
+        clock.resolve();
+        if (hb->info[SLOT_RR] && m > nb + na) {  // drop P and retry (restart)
+          restarts++;
+          m = nb + na;
+          LOB_TRY(rr_begin(m));
+          return sync_point();
+        }
+        if (hb->info[SLOT_RR]) { run_status = LOB_ERR_BREAKDOWN; pc = PC_RUN_END; continue; }
+        LOB_TRY(update(m));  // eq. 7, steps 9-10
+        haveP = true;
+        it++;
+        pc = PC_ITER_RESID;
+        continue;
+      }
+      case PC_RUN_END: {
+        iters_total += it;
+        restarts_total += restarts;
+        if (o.mode == LOB_MODE_MIXED && phase == 1) stats.refine_iterations = it;
+        if (run_status != LOB_OK && run_status != LOB_ERR_NOCONV) { status = run_status; pc = PC_END; continue; }
+        if (o.mode == LOB_MODE_MIXED && phase == 0) { phase = 1; pc = PC_PHASE; continue; }
+        status = run_status;
+        pc = PC_FINISH;
+        continue;
+      }
+      case PC_FINISH: {
+        // outputs: X = S[:, :nb], lambda = theta[:k], final residuals
+        LOB_TRY(residual_begin());
+        if (Xout) {
+          (k_copy_cols<<<nblk(n * nb), BS, 0, st>>>(n, nb, S.p, ldS, nullptr, Xout, nb), LOB_LAUNCHED());
+          if (n_act < n) LOB_CUDA(cudaMemsetAsync(Xout + n_act * nb, 0, (size_t)(n - n_act) * nb * 8, st));
+        }
+        LOB_CUDA(cudaMemcpyAsync(hb->theta, theta.p, k * sizeof(double), cudaMemcpyDeviceToHost, st));
+        pc = PC_OUT;
+        return sync_point();
+      }
+      case PC_OUT: {
+        clock.resolve();
+        stats.iterations = iters_total;
+        stats.restarts = restarts_total;
+        for (int j = 0; j < nb && j < 64; j++) stats.residual[j] = hb->relres[j];
+        stats.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        pc = PC_END;
+        return LOB_TASK_DONE;
+      }
+      case PC_END:
+      default:
+        return LOB_TASK_DONE;
+    }
+  }
+}
+
+int lob_task_create(lob_matrix* m, int32_t k, int32_t nb, double tol, const double* X0, const lob_solve_opts* o,
+                    double* X, int64_t n_act, cudaStream_t st, bool timing, lob_task** out) {
+  lob_task* t = new lob_task();
+  const int rc = task_init(t, m, k, nb, tol, X0, o, X, n_act, st, timing);
+  if (rc != LOB_OK) { delete t; return rc; }
+  *out = t;
   return LOB_OK;
 }
 
-int lob_solve_impl(lob_matrix* m, int32_t k, int32_t nb, double tol, const double* X0,
-                              const lob_solve_opts* o, double* lambda, double* X, lob_stats* st, int64_t n_act) {
+int lob_task_step(lob_task* t) { return t->step(); }
+
+lob_task* lob_task_leaf(lob_task* t) {
+  while (t->child) t = t->child;
+  return t;
+}
+
+cudaEvent_t lob_task_event(const lob_task* leaf) { return leaf->ev; }
+
+void lob_task_spmm_args(const lob_task* leaf, const lob_matrix** m, const double** X, double** Y, int* ncol,
+                        int* mode, int64_t* n_act) {
+  *m = leaf->M; *X = leaf->sp_x; *Y = leaf->sp_y; *ncol = leaf->sp_ncol; *mode = leaf->spmm_mode;
+  *n_act = leaf->n_act;
+}
+
+int lob_task_spmm_direct(lob_task* leaf) {
+  Timer t(leaf->clk(), leaf->st, leaf->ph(PH_SPMM));
+  Timer tm(leaf->clk(), leaf->st, leaf->timing ? &leaf->stats.spmm_ms_mode[leaf->spmm_mode] : nullptr);
+  return lob_spmm_launch(leaf->M, leaf->spmm_mode, leaf->sp_x, leaf->sp_y, leaf->sp_ncol, leaf->n_act, leaf->st);
+}
+
+int lob_task_result(const lob_task* t, double* lambda, lob_stats* st) {
+  if (t->pc != PC_END) return LOB_ERR_ARG;
+  if (t->status == LOB_OK || t->status == LOB_ERR_NOCONV)
+    if (lambda) memcpy(lambda, t->hb->theta, t->k * sizeof(double));
+  if (st) *st = t->stats;
+  return t->status;
+}
+
+void lob_task_destroy(lob_task* t) { delete t; }
+
+size_t lob_task_bytes(const lob_matrix* m, int nb, int64_t n_small) {
+  const int64_t n = m->T.n;
+  size_t d = solver_doubles(n, nb);
+  if (n_small > 3 * nb) d += solver_doubles(n, nb);
+  else if (n_small > 0) d += 2 * (size_t)n * 64 + 5 * 96 * 96;
+  return d * sizeof(double);
+}
+
+int lob_solve_impl(lob_matrix* m, int32_t k, int32_t nb, double tol, const double* X0, const lob_solve_opts* o,
+                   double* lambda, double* X, lob_stats* st, int64_t n_act) {
   lob_solve_opts dflt;
   memset(&dflt, 0, sizeof(dflt));
   if (!o) o = &dflt;
@@ -457,67 +755,27 @@ int lob_solve_impl(lob_matrix* m, int32_t k, int32_t nb, double tol, const doubl
   if (o->mode == LOB_MODE_MIXED && (!m->T.v32 || !m->T.v64)) return LOB_ERR_ARG;
   if (o->mode == LOB_MODE_FP64 && !m->T.v64) return LOB_ERR_ARG;
   if (o->precond && m->P.bp < 1) return LOB_ERR_ARG;
+  if (o->precond_solve < LOB_PSOLVE_FOM || o->precond_solve > LOB_PSOLVE_ABS || o->precond_steps < 0 ||
+      o->precond_steps > 3)
+    return LOB_ERR_ARG;
   cudaStream_t stream = (cudaStream_t)o->stream;
-  const auto t0 = std::chrono::steady_clock::now();
-  if (st) memset(st, 0, sizeof(*st));
-
-  Solver S;
-  S.M = m; S.n = m->T.n; S.n_act = n_act; S.nb = nb; S.k = k; S.st = stream;
-  S.normH = o->norm_H > 0.0 ? o->norm_H : m->norm_inf;
-  S.stats = st; S.timing = st != nullptr;
-  // block products: native FP64 in the plain solver, FP64-class double-float in MIXED
-  S.blas_mode = o->mode == LOB_MODE_MIXED ? LOB_SPMM_MIXED : LOB_SPMM_FP64;
-  LOB_TRY(S.alloc());
-  PhaseClock clock;
-  PhaseClock* prev_clock = g_clock;
-  if (st) g_clock = &clock;
-  struct ClockReset { PhaseClock* p; ~ClockReset() { g_clock = p; } } clock_reset{prev_clock};
-
-  // X0 into S[:, :nb]
-  {
-    Timer t(stream, st ? &st->phase_ms[PH_GUESS] : nullptr);
-    if (X0) {
-      (k_copy_cols<<<nblk(S.n * nb), BS, 0, stream>>>(S.n, nb, X0, nb, nullptr, S.S.p, S.ldS), LOB_LAUNCHED());
-    } else if (o->n_small > 0 && o->n_small < n_act) {
-      LOB_TRY(initial_guess(m, nb, o, S.W.p, stream));
-      (k_copy_cols<<<nblk(S.n * nb), BS, 0, stream>>>(S.n, nb, S.W.p, nb, nullptr, S.S.p, S.ldS), LOB_LAUNCHED());
+  lob_task* t = nullptr;
+  LOB_TRY(lob_task_create(m, k, nb, tol, X0, o, X, n_act, stream, st != nullptr, &t));
+  int rc = LOB_OK;
+  for (;;) {
+    const int r = lob_task_step(t);
+    if (r < 0) { rc = r; break; }
+    lob_task* leaf = lob_task_leaf(t);
+    if (r == LOB_TASK_SYNC) {
+      if (cudaEventSynchronize(leaf->ev) != cudaSuccess) { rc = LOB_ERR_CUDA; break; }
+    } else if (r == LOB_TASK_SPMM) {
+      rc = lob_task_spmm_direct(leaf);
+      if (rc != LOB_OK) break;
     } else {
-      (k_random<<<nblk(S.n * nb), BS, 0, stream>>>(S.n, n_act, nb, S.ldS, 0, nb, o->seed, S.S.p), LOB_LAUNCHED());
+      rc = lob_task_result(t, lambda, st);
+      break;
     }
-    LOB_CUDA(cudaGetLastError());
   }
-  const int max_iter = o->max_iter > 0 ? o->max_iter : 500;
-  int iters = 0, restarts = 0, status;
-  if (o->mode == LOB_MODE_MIXED) {
-    // phase 1: FP32-value SpMM down to the FP32 floor; phase 2: FP64 refinement from there
-    const double tol1 = o->mixed_tol > 0.0 ? o->mixed_tol : (tol > 1e-6 ? tol : 1e-6);
-    S.spmm_mode = LOB_SPMM_MIXED;
-    status = S.run(tol1, max_iter, o->precond != 0, o->precond_shift, &iters, &restarts);
-    if (status != LOB_OK && status != LOB_ERR_NOCONV) return status;
-    int it2 = 0, rs2 = 0;
-    S.spmm_mode = m->T.v32lo ? LOB_SPMM_DF64 : LOB_SPMM_FP64;  // FP64-class refinement products
-    const int max2 = o->refine_iter > 0 ? o->refine_iter : 50;
-    status = S.run(tol, max2, o->precond != 0, o->precond_shift, &it2, &rs2);
-    if (st) st->refine_iterations = it2;
-    iters += it2;
-    restarts += rs2;
-  } else {
-    S.spmm_mode = LOB_SPMM_FP64;
-    status = S.run(tol, max_iter, o->precond != 0, o->precond_shift, &iters, &restarts);
-  }
-  if (status != LOB_OK && status != LOB_ERR_NOCONV) return status;
-  // outputs: X = S[:, :nb], lambda = theta[:k], final residuals
-  LOB_TRY(S.residual());
-  (k_copy_cols<<<nblk(S.n * nb), BS, 0, stream>>>(S.n, nb, S.S.p, S.ldS, nullptr, X, nb), LOB_LAUNCHED());
-  if (n_act < S.n) LOB_CUDA(cudaMemsetAsync(X + n_act * nb, 0, (size_t)(S.n - n_act) * nb * 8, stream));
-  LOB_CUDA(cudaMemcpyAsync(lambda, S.theta.p, k * sizeof(double), cudaMemcpyDeviceToHost, stream));
-  LOB_CUDA(cudaStreamSynchronize(stream));
-  if (st) clock.resolve();
-  if (st) {
-    st->iterations = iters;
-    st->restarts = restarts;
-    for (int j = 0; j < nb && j < 64; j++) st->residual[j] = S.relres_h[j];
-    st->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  }
-  return status;
+  lob_task_destroy(t);
+  return rc;
 }

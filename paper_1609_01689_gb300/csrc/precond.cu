@@ -4,9 +4,11 @@
 //
 // Setup, once per matrix: gather each diagonal block (both triangles) densely and compute
 // H~_[i] = Q_i diag(lambda_i) Q_i^T by cyclic Jacobi, one CTA per block, in FP32 -- the paper
-// runs the preconditioner in single precision (footnote 5 of Section 4.4). A direct solve of
-// eq. 11 for every shift is then W_[i] = Q_i (Lambda_i - mu_j I)^{-1} Q_i^T R_[i], which needs
-// no factorisation per shift: two small products per block and a scaling.
+// runs the preconditioner in single precision (footnote 5 of Section 4.4). Any solve of eq. 11
+// for any shift then works in the block's eigenbasis: W_[i] = Q_i f(Lambda_i - mu_j I) Q_i^T R_[i]
+// with f(D) = D^{-1} for a direct solve, or the polynomial that m steps of FOM or of a
+// minimal-residual method (the paper's iterative solvers, Sections 3.2 and 4.3, "two or three
+// iterations") produce from a zero start -- two small products per block in every case.
 #include "common.cuh"
 #include "df.cuh"
 
@@ -111,11 +113,116 @@ __global__ void __launch_bounds__(256) k_block_eig(int bp, const double* __restr
   for (int k = tid; k < bp; k += nt) lam[b * bp + k] = A[k * bp + k];
 }
 
-// W_[i] = Q (Lambda - mu_j)^{-1} Q^T R_[i]; one CTA per block, FP32 arithmetic.
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+  return x;
+}
+
+// x = f(D) c for one right-hand side in a block's eigenbasis (D = Lambda - mu I diagonal,
+// c = Q^T r), one warp, entries k = lane and lane + 32. The Krylov solvers of eq. 11 with a
+// zero start reduce to this basis exactly: K_m(A, r) = Q K_m(D, c), so Lanczos on (D, c)
+// gives the FOM (Galerkin) or minimal-residual iterate of (H~ - mu I) w = r after m steps.
+__device__ void block_solve(int solve, int steps, float guard, const float d[2], const float c[2], float x[2]) {
+  if (solve == LOB_PSOLVE_DIRECT || solve == LOB_PSOLVE_ABS) {
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      float dd = d[u];
+      if (solve == LOB_PSOLVE_ABS) dd = fabsf(dd);
+      if (fabsf(dd) < guard) dd = dd < 0.f ? -guard : guard;
+      x[u] = c[u] / dd;
+    }
+    return;
+  }
+  x[0] = x[1] = 0.f;
+  const float beta0 = sqrtf(warp_sum(c[0] * c[0] + c[1] * c[1]));
+  if (!(beta0 > 0.f)) return;
+  // Lanczos on (D, c), full reorthogonalisation (at most 3 vectors)
+  float v[3][2], al[3] = {0.f, 0.f, 0.f}, be[3] = {0.f, 0.f, 0.f};
+  v[0][0] = c[0] / beta0;
+  v[0][1] = c[1] / beta0;
+  int m = 0;
+  for (int i = 0; i < steps; i++) {
+    float w[2] = {d[0] * v[i][0], d[1] * v[i][1]};
+    al[i] = warp_sum(v[i][0] * w[0] + v[i][1] * w[1]);
+    m = i + 1;
+    for (int t = 0; t <= i; t++) {
+      const float h = warp_sum(v[t][0] * w[0] + v[t][1] * w[1]);
+      w[0] -= h * v[t][0];
+      w[1] -= h * v[t][1];
+    }
+    be[i] = sqrtf(warp_sum(w[0] * w[0] + w[1] * w[1]));
+    const float scale = fabsf(al[i]) + (i > 0 ? be[i - 1] : 0.f);
+    if (i + 1 == steps || !(be[i] > 1e-6f * scale)) {
+      if (!(be[i] > 1e-6f * scale)) be[i] = 0.f;  // invariant subspace: both iterates are exact
+      break;
+    }
+    v[i + 1][0] = w[0] / be[i];
+    v[i + 1][1] = w[1] / be[i];
+  }
+  // tridiagonal T (m x m): diagonal al, off-diagonal be[0..m-2]; T_bar adds the row be[m-1] e_m^T
+  float y[3] = {0.f, 0.f, 0.f};
+  bool ok = false;
+  float tmax = 0.f;
+  for (int i = 0; i < m; i++) tmax = fmaxf(tmax, fabsf(al[i]) + be[i]);
+  if (solve == LOB_PSOLVE_FOM) {
+    // Galerkin: T y = beta0 e1 by elimination without pivoting; a small pivot is a FOM breakdown
+    float dg[3], rhs[3] = {beta0, 0.f, 0.f};
+    ok = true;
+    for (int i = 0; i < m; i++) {
+      dg[i] = al[i];
+      if (i > 0) {
+        const float l = be[i - 1] / dg[i - 1];
+        dg[i] -= l * be[i - 1];
+        rhs[i] -= l * rhs[i - 1];
+      }
+      if (!(fabsf(dg[i]) > 1e-4f * tmax)) ok = false;
+    }
+    if (ok) {
+      for (int i = m - 1; i >= 0; i--) y[i] = (rhs[i] - (i + 1 < m ? be[i] * y[i + 1] : 0.f)) / dg[i];
+    }
+  }
+  if (!ok) {
+    // minimal residual: min || beta0 e1 - T_bar y || by Givens rotations on the (m+1) x m T_bar
+    float R[4][3] = {{0.f}}, g[4] = {beta0, 0.f, 0.f, 0.f};
+    for (int i = 0; i < m; i++) {
+      R[i][i] = al[i];
+      R[i + 1][i] = be[i];
+      if (i + 1 < m) R[i][i + 1] = be[i];
+    }
+    for (int i = 0; i < m; i++) {
+      const float a = R[i][i], b = R[i + 1][i];
+      const float r = sqrtf(a * a + b * b);
+      if (!(r > 0.f)) continue;
+      const float cs = a / r, sn = b / r;
+      for (int j = i; j < m; j++) {
+        const float p = R[i][j], q = R[i + 1][j];
+        R[i][j] = cs * p + sn * q;
+        R[i + 1][j] = -sn * p + cs * q;
+      }
+      const float p = g[i], q = g[i + 1];
+      g[i] = cs * p + sn * q;
+      g[i + 1] = -sn * p + cs * q;
+    }
+    for (int i = m - 1; i >= 0; i--) {
+      float s2 = g[i];
+      for (int j = i + 1; j < m; j++) s2 -= R[i][j] * y[j];
+      y[i] = fabsf(R[i][i]) > 1e-6f * tmax ? s2 / R[i][i] : 0.f;
+    }
+  }
+  for (int i = 0; i < m; i++) {
+    x[0] += y[i] * v[i][0];
+    x[1] += y[i] * v[i][1];
+  }
+}
+
+// W_[i] = Q f(Lambda - mu_j) Q^T R_[i]; one CTA per block, FP32 arithmetic. f is the exact
+// inverse (a direct solve of eq. 11), its absolute value, or the FOM / minimal-residual
+// polynomial of the given number of Krylov steps (the paper's iterative solve, Section 4.3).
 __global__ void __launch_bounds__(256) k_block_apply(int bp, int64_t n_act, const float* __restrict__ Q,
                                                      const float* __restrict__ lam, const double* __restrict__ mu,
                                                      float guard, const double* __restrict__ R, double* __restrict__ W,
-                                                     int nb) {
+                                                     int nb, int solve, int steps) {
   extern __shared__ float sm[];
   float* Qs = sm;             // bp x bp, column-major (Qs[k*bp + i])
   float* Rs = Qs + bp * bp;   // bp x nb
@@ -130,14 +237,29 @@ __global__ void __launch_bounds__(256) k_block_apply(int bp, int64_t n_act, cons
     Rs[e] = (o + i < n_act) ? f64_to_f32_rz(R[(o + i) * nb + j]) : 0.f;
   }
   __syncthreads();
-  for (int e = tid; e < bp * nb; e += nt) {  // T = diag(1/(lambda - mu)) Q^T R
+  for (int e = tid; e < bp * nb; e += nt) {  // C = Q^T R
     const int k = e / nb, j = e % nb;
     float s = 0.f;
     for (int i = 0; i < bp; i++) s = fmaf(Qs[k * bp + i], Rs[i * nb + j], s);
+    Ts[e] = s;
+  }
+  __syncthreads();
+  const int warp = tid / 32, lane = tid % 32, nw = nt / 32;
+  for (int j = warp; j < nb; j += nw) {  // T[:, j] = f(Lambda - mu_j) C[:, j], one warp per column
     const float2 m = df_split(mu[j]);
-    float d = __fsub_rn(__fsub_rn(lam[b * bp + k], m.x), m.y);
-    if (fabsf(d) < guard) d = d < 0.f ? -guard : guard;
-    Ts[e] = s / d;
+    float d[2], c[2], x[2];
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      const int k = lane + 32 * u;
+      d[u] = k < bp ? __fsub_rn(__fsub_rn(lam[b * bp + k], m.x), m.y) : 0.f;
+      c[u] = k < bp ? Ts[k * nb + j] : 0.f;
+    }
+    block_solve(solve, steps, guard, d, c, x);
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      const int k = lane + 32 * u;
+      if (k < bp) Ts[k * nb + j] = x[u];
+    }
   }
   __syncthreads();
   for (int e = tid; e < bp * nb; e += nt) {  // W = Q T
@@ -185,15 +307,18 @@ int lob_build_precond(const lob_coo* H, int bp, int64_t n, cudaStream_t st, lob_
 }
 
 int lob_precond_launch(const lob_matrix* m, const double* mu, const double* R, double* W, int nb, int64_t n_act,
-                       cudaStream_t st) {
+                       int solve, int steps, cudaStream_t st) {
   const lob_precond& P = m->P;
   if (P.bp < 1 || nb < 1 || nb > 64) return LOB_ERR_ARG;
+  if (solve < LOB_PSOLVE_FOM || solve > LOB_PSOLVE_ABS || steps < 1 || steps > 3) return LOB_ERR_ARG;
   const int bp = P.bp;
   const size_t smem = ((size_t)bp * bp + 2ull * bp * nb) * sizeof(float);
   const int64_t nblk = (n_act + bp - 1) / bp;
   if (n_act < m->T.n) LOB_CUDA(cudaMemsetAsync(W + n_act * nb, 0, (size_t)(m->T.n - n_act) * nb * 8, st));
   if (nblk > 0)
-    (k_block_apply<<<(unsigned)nblk, 256, smem, st>>>(bp, n_act, P.Q, P.lam, mu, (float)(1e-8 * m->norm_inf), R, W, nb), LOB_LAUNCHED());
+    (k_block_apply<<<(unsigned)nblk, 256, smem, st>>>(bp, n_act, P.Q, P.lam, mu, (float)(1e-8 * m->norm_inf), R, W, nb,
+                                                      solve, steps),
+     LOB_LAUNCHED());
   LOB_CUDA(cudaGetLastError());
   return LOB_OK;
 }

@@ -6,7 +6,7 @@
 // entries with r != c are applied both ways and the diagonal once.
 //
 // Schedule: one CTA per tile row I. X_I (256 rows) stays in shared memory for the whole row;
-// the row's tiles are streamed in chunks of up to 4096 entries -- the records, the chunk's
+// the row's tiles are streamed in chunks of up to LOB_PERM_CHUNK entries -- the records, the chunk's
 // column-order permutation, the chunk's row and column start pointers (both derived once at
 // create time from the canonical store), and X_J for a new tile -- with cp.async, the next
 // chunk loading while the current one computes. A lane group of NB/VW lanes (VW elements =
@@ -24,6 +24,18 @@
 // cross-tile sums in Y are FP64 (footnote 5 of Section 4.4). FP64: every operation in FP64.
 #include "common.cuh"
 #include "df.cuh"
+
+// Staged-X scratch of a matrix (grown on demand, owned by the matrix).
+int lob_ensure_xs(const lob_matrix* m, size_t need) {
+  lob_matrix* mm = const_cast<lob_matrix*>(m);
+  if (mm->xs_bytes >= need) return LOB_OK;
+  cudaFree(mm->xs);
+  mm->xs = nullptr;
+  mm->xs_bytes = 0;
+  if (cudaMalloc(&mm->xs, need) != cudaSuccess) { cudaGetLastError(); return LOB_ERR_NOMEM; }
+  mm->xs_bytes = need;
+  return LOB_OK;
+}
 
 namespace {
 
@@ -103,9 +115,6 @@ struct Cfg {
   using T = typename Elt<MIXED>::T;
   static constexpr int VW = Elt<MIXED>::VW;
   static constexpr int G = NB / VW;
-  static constexpr int THREADS = (LOB_TILE * G) < 1024 ? (LOB_TILE * G) : 1024;
-  static constexpr int NG = THREADS / G;
-  static constexpr int RPG = LOB_TILE / NG;
   static constexpr int CH = LOB_PERM_CHUNK;
   static constexpr int PTRS = 2 * (LOB_TILE + 1);  // row starts then column starts, uint16
   static constexpr size_t XV = sizeof(T) * LOB_TILE * NB;
@@ -116,6 +125,12 @@ struct Cfg {
   static constexpr size_t PM = VV + 2 * sizeof(T) * CH;    // 2 x (CH + 8) uint16
   static constexpr size_t PT = PM + 2 * 2 * (CH + 8);      // 2 x PTRS uint16
   static constexpr size_t BYTES = PT + 2 * 2 * PTRS;
+  // one CTA per SM: 1,024 threads, one in-tile row and column per lane group at NB = 16 (a
+  // variant with two 512-thread CTAs per SM and 2,048-entry chunks measured 15% slower)
+  static constexpr int MINB = 1;
+  static constexpr int THREADS = (LOB_TILE * G) < 1024 ? (LOB_TILE * G) : 1024;
+  static constexpr int NG = THREADS / G;
+  static constexpr int RPG = LOB_TILE / NG;
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -134,12 +149,13 @@ __device__ __forceinline__ void atomic_out(double* y, double v) { if (v != 0.0) 
 //               accumulator (row a and column a have the same owner).
 // Nothing is accumulated in shared memory and no shared-memory atomics are used.
 template <bool MIXED, int NB>
-__global__ void __launch_bounds__(Cfg<MIXED, NB>::THREADS, 1)
+__global__ void __launch_bounds__(Cfg<MIXED, NB>::THREADS, Cfg<MIXED, NB>::MINB)
     k_spmm4(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ tcol, const int64_t* __restrict__ tptr,
             const int32_t* __restrict__ tchunk, const uint32_t* __restrict__ rc,
             const typename Elt<MIXED>::T* __restrict__ vals, const uint16_t* __restrict__ cperm,
             const uint16_t* __restrict__ cptrs, const typename Elt<MIXED>::T* __restrict__ Xs,
-            double* __restrict__ Y, int ldy, int c0, int w, int64_t n_act) {
+            double* __restrict__ Y, int ldy, int c0, int w, int64_t n_act, const lob_spmm_job* __restrict__ jobs,
+            int njobs) {
   using C = Cfg<MIXED, NB>;
   using T = typename C::T;
   using V = typename Elt<MIXED>::V;
@@ -154,7 +170,19 @@ __global__ void __launch_bounds__(Cfg<MIXED, NB>::THREADS, 1)
   uint16_t* PMb = reinterpret_cast<uint16_t*>(sm + C::PM);
   uint16_t* PTb = reinterpret_cast<uint16_t*>(sm + C::PT);
 
-  const int64_t I = blockIdx.x;
+  int64_t I = blockIdx.x;
+  if (jobs) {  // batched launch: find this CTA's matrix and tile row
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].cta_begin <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const lob_spmm_job& jb = jobs[lo];
+    rowptr = jb.rowptr; tcol = jb.tcol; tptr = jb.tptr; tchunk = jb.tchunk; rc = jb.rc;
+    vals = reinterpret_cast<const T*>(jb.vals); cperm = jb.cperm; cptrs = jb.cptrs;
+    Xs = reinterpret_cast<const T*>(jb.Xs); Y = jb.Y; ldy = jb.ldy; c0 = jb.c0; w = jb.w; n_act = jb.n_act;
+    I = (int64_t)blockIdx.x - jb.cta_begin;
+  }
   const int64_t row0 = I * LOB_TILE;
   const int tid = threadIdx.x;
   const int g = tid / G, gl = tid % G;
@@ -334,7 +362,8 @@ __global__ void __launch_bounds__(CfgDF<NB>::THREADS, 1)
     k_spmm4df(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ tcol, const int64_t* __restrict__ tptr,
               const int32_t* __restrict__ tchunk, const uint32_t* __restrict__ rc, const float* __restrict__ vhi,
               const float* __restrict__ vlo, const uint16_t* __restrict__ cperm, const uint16_t* __restrict__ cptrs,
-              const float2* __restrict__ Xs, double* __restrict__ Y, int ldy, int c0, int w, int64_t n_act) {
+              const float2* __restrict__ Xs, double* __restrict__ Y, int ldy, int c0, int w, int64_t n_act,
+              const lob_spmm_job* __restrict__ jobs, int njobs) {
   using C = CfgDF<NB>;
   constexpr int VW = C::VW, G = C::G, NG = C::NG, RPG = C::RPG, CH = C::CH, THREADS = C::THREADS;
   constexpr int XN = LOB_TILE * NB;
@@ -347,7 +376,20 @@ __global__ void __launch_bounds__(CfgDF<NB>::THREADS, 1)
   uint16_t* PMb = reinterpret_cast<uint16_t*>(sm + C::PM);
   uint16_t* PTb = reinterpret_cast<uint16_t*>(sm + C::PT);
 
-  const int64_t I = blockIdx.x;
+  int64_t I = blockIdx.x;
+  if (jobs) {  // batched launch: find this CTA's matrix and tile row
+    int lo = 0, hi = njobs - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].cta_begin <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    const lob_spmm_job& jb = jobs[lo];
+    rowptr = jb.rowptr; tcol = jb.tcol; tptr = jb.tptr; tchunk = jb.tchunk; rc = jb.rc;
+    vhi = reinterpret_cast<const float*>(jb.vals); vlo = reinterpret_cast<const float*>(jb.vlo);
+    cperm = jb.cperm; cptrs = jb.cptrs;
+    Xs = reinterpret_cast<const float2*>(jb.Xs); Y = jb.Y; ldy = jb.ldy; c0 = jb.c0; w = jb.w; n_act = jb.n_act;
+    I = (int64_t)blockIdx.x - jb.cta_begin;
+  }
   const int64_t row0 = I * LOB_TILE;
   const int tid = threadIdx.x;
   const int g = tid / G, gl = tid % G;
@@ -485,16 +527,8 @@ int launch_df(const lob_matrix* m, const double* X, double* Y, int nb, int64_t n
   const int64_t nt_act = (n_act + LOB_TILE - 1) / LOB_TILE;
   if (nt_act == 0) return LOB_OK;
   const int64_t rows_pad = TS.nt * LOB_TILE;
-  const size_t need = (size_t)rows_pad * NB * sizeof(float2);
-  lob_matrix* mm = const_cast<lob_matrix*>(m);
-  if (mm->xs_bytes < need) {
-    cudaFree(mm->xs);
-    mm->xs = nullptr;
-    mm->xs_bytes = 0;
-    if (cudaMalloc(&mm->xs, need) != cudaSuccess) { cudaGetLastError(); return LOB_ERR_NOMEM; }
-    mm->xs_bytes = need;
-  }
-  float2* Xs = reinterpret_cast<float2*>(mm->xs);
+  LOB_TRY(lob_ensure_xs(m, (size_t)rows_pad * NB * sizeof(float2)));
+  float2* Xs = reinterpret_cast<float2*>(m->xs);
   auto kern = k_spmm4df<NB>;
   LOB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES));
   for (int c0 = 0; c0 < nb; c0 += NB) {
@@ -502,7 +536,8 @@ int launch_df(const lob_matrix* m, const double* X, double* Y, int nb, int64_t n
     (k_stage_x_df<<<(unsigned)((rows_pad * NB + 255) / 256), 256, 0, st>>>(rows_pad, n_act, nb, c0, w, NB, X, Xs),
      LOB_LAUNCHED());
     (kern<<<(unsigned)nt_act, C::THREADS, C::BYTES, st>>>(TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rc, TS.v32,
-                                                           TS.v32lo, TS.cperm, TS.cptrs, Xs, Y, nb, c0, w, n_act),
+                                                           TS.v32lo, TS.cperm, TS.cptrs, Xs, Y, nb, c0, w, n_act,
+                                                           nullptr, 0),
      LOB_LAUNCHED());
   }
   LOB_CUDA(cudaGetLastError());
@@ -519,16 +554,8 @@ int launch(const lob_matrix* m, const double* X, double* Y, int nb, int64_t n_ac
   if (nt_act == 0) return LOB_OK;
   // staged X: rows padded to whole tiles, NB columns (scratch owned by the matrix)
   const int64_t rows_pad = TS.nt * LOB_TILE;
-  const size_t need = (size_t)rows_pad * NB * sizeof(T);
-  lob_matrix* mm = const_cast<lob_matrix*>(m);
-  if (mm->xs_bytes < need) {
-    cudaFree(mm->xs);
-    mm->xs = nullptr;
-    mm->xs_bytes = 0;
-    if (cudaMalloc(&mm->xs, need) != cudaSuccess) { cudaGetLastError(); return LOB_ERR_NOMEM; }
-    mm->xs_bytes = need;
-  }
-  T* Xs = reinterpret_cast<T*>(mm->xs);
+  LOB_TRY(lob_ensure_xs(m, (size_t)rows_pad * NB * sizeof(T)));
+  T* Xs = reinterpret_cast<T*>(m->xs);
   auto kern = k_spmm4<MIXED, NB>;
   LOB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES));
   for (int c0 = 0; c0 < nb; c0 += NB) {
@@ -538,14 +565,116 @@ int launch(const lob_matrix* m, const double* X, double* Y, int nb, int64_t n_ac
     (kern<<<(unsigned)nt_act, C::THREADS, C::BYTES, st>>>(
          TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rc,
          MIXED ? (const T*)(const void*)TS.v32 : (const T*)(const void*)TS.v64, TS.cperm, TS.cptrs, Xs, Y, nb, c0, w,
-         n_act),
+         n_act, nullptr, 0),
      LOB_LAUNCHED());
   }
   LOB_CUDA(cudaGetLastError());
   return LOB_OK;
 }
 
+template <int MODE, int NB>
+int batch_class(const lob_matrix* const* ms, const double* const* X, double* const* Y, const int* ncol,
+                const int64_t* nact, const std::vector<int>& idx, lob_spmm_job* jobs_host, lob_spmm_job* jobs_dev, cudaStream_t st) {
+  int njob = 0;
+  int64_t ctas = 0;
+  for (int j : idx) {
+    const lob_matrix* m = ms[j];
+    const lob_tiles& TS = m->T;
+    const int64_t na = nact ? nact[j] : TS.n;
+    const int64_t nt_act = (na + LOB_TILE - 1) / LOB_TILE;
+    if (nt_act == 0) continue;
+    const int64_t rows_pad = TS.nt * LOB_TILE;
+    const size_t esz = MODE == LOB_SPMM_MIXED ? 4 : 8;
+    LOB_TRY(lob_ensure_xs(m, (size_t)rows_pad * NB * esz));
+    if (MODE == LOB_SPMM_DF64)
+      (k_stage_x_df<<<(unsigned)((rows_pad * NB + 255) / 256), 256, 0, st>>>(rows_pad, na, ncol[j], 0, ncol[j], NB,
+                                                                             X[j], (float2*)m->xs), LOB_LAUNCHED());
+    else if (MODE == LOB_SPMM_MIXED)
+      (k_stage_x<float><<<(unsigned)((rows_pad * NB + 255) / 256), 256, 0, st>>>(rows_pad, na, ncol[j], 0, ncol[j], NB,
+                                                                                 X[j], (float*)m->xs), LOB_LAUNCHED());
+    else
+      (k_stage_x<double><<<(unsigned)((rows_pad * NB + 255) / 256), 256, 0, st>>>(rows_pad, TS.n, ncol[j], 0, ncol[j],
+                                                                                  NB, X[j], (double*)m->xs), LOB_LAUNCHED());
+    lob_spmm_job jb;
+    jb.rowptr = TS.rowptr; jb.tcol = TS.tcol; jb.tptr = TS.tptr; jb.tchunk = TS.tchunk; jb.rc = TS.rc;
+    jb.vals = MODE == LOB_SPMM_FP64 ? (const void*)TS.v64 : (const void*)TS.v32;
+    jb.vlo = TS.v32lo; jb.cperm = TS.cperm; jb.cptrs = TS.cptrs; jb.Xs = m->xs; jb.Y = Y[j];
+    jb.ldy = ncol[j]; jb.c0 = 0; jb.w = ncol[j]; jb.pad = 0; jb.n_act = na; jb.cta_begin = ctas;
+    jobs_host[njob++] = jb;
+    ctas += nt_act;
+  }
+  if (njob == 0) return LOB_OK;
+  LOB_CUDA(cudaMemcpyAsync(jobs_dev, jobs_host, njob * sizeof(lob_spmm_job), cudaMemcpyHostToDevice, st));
+  if (MODE == LOB_SPMM_DF64) {
+    using C = CfgDF<NB>;
+    LOB_CUDA(cudaFuncSetAttribute(k_spmm4df<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES));
+    (k_spmm4df<NB><<<(unsigned)ctas, C::THREADS, C::BYTES, st>>>(nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                                 nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0, 0, 0,
+                                                                 jobs_dev, njob), LOB_LAUNCHED());
+  } else {
+    constexpr bool MX = MODE == LOB_SPMM_MIXED;
+    using C = Cfg<MX, NB>;
+    LOB_CUDA(cudaFuncSetAttribute(k_spmm4<MX, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES));
+    (k_spmm4<MX, NB><<<(unsigned)ctas, C::THREADS, C::BYTES, st>>>(nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                                   nullptr, nullptr, nullptr, nullptr, 0, 0, 0, 0,
+                                                                   jobs_dev, njob), LOB_LAUNCHED());
+  }
+  LOB_CUDA(cudaGetLastError());
+  return LOB_OK;
+}
+
 }  // namespace
+
+int lob_spmm_batch_launch(const lob_matrix* const* ms, const double* const* X, double* const* Y, const int* ncol,
+                          const int* mode, const int64_t* nact, int njobs, lob_spmm_job* jobs_host,
+                          lob_spmm_job* jobs_dev, cudaStream_t st, int* n_kernels) {
+  if (n_kernels) *n_kernels = 0;
+  // classes by (arithmetic, vector width); each class is one launch
+  std::vector<int> cls[3][4];
+  for (int j = 0; j < njobs; j++) {
+    if (ncol[j] < 1 || ncol[j] > 16) return LOB_ERR_ARG;
+    const int md = mode[j];
+    if (md < 0 || md > 2) return LOB_ERR_ARG;
+    if (nact && (nact[j] < 0 || nact[j] > ms[j]->T.n)) return LOB_ERR_ARG;
+    if ((md == LOB_SPMM_MIXED && !ms[j]->T.v32) || (md == LOB_SPMM_FP64 && !ms[j]->T.v64) ||
+        (md == LOB_SPMM_DF64 && !ms[j]->T.v32lo))
+      return LOB_ERR_ARG;
+    for (int i = 0; i < j; i++)
+      if (ms[i] == ms[j]) return LOB_ERR_ARG;  // one staged-X scratch per matrix
+    LOB_CUDA(cudaMemsetAsync(Y[j], 0, (size_t)ms[j]->T.n * ncol[j] * sizeof(double), st));
+    const int w = ncol[j];
+    const int c = md == LOB_SPMM_MIXED ? (w <= 4 ? 1 : (w <= 8 ? 2 : 3)) : (w <= 2 ? 0 : (w <= 4 ? 1 : (w <= 8 ? 2 : 3)));
+    cls[md][c].push_back(j);
+  }
+  // offsets into the caller's job buffer per class (each class uses a disjoint slice)
+  int off = 0;
+  auto run = [&](int md, int c) -> int {
+    const std::vector<int>& v = cls[md][c];
+    if (v.empty()) return LOB_OK;
+    lob_spmm_job* jd = jobs_dev + off;
+    lob_spmm_job* jh = jobs_host + off;
+    off += (int)v.size();
+    if (n_kernels) (*n_kernels)++;
+    if (md == LOB_SPMM_MIXED) {
+      if (c == 1) return batch_class<LOB_SPMM_MIXED, 4>(ms, X, Y, ncol, nact, v, jh, jd, st);
+      if (c == 2) return batch_class<LOB_SPMM_MIXED, 8>(ms, X, Y, ncol, nact, v, jh, jd, st);
+      return batch_class<LOB_SPMM_MIXED, 16>(ms, X, Y, ncol, nact, v, jh, jd, st);
+    }
+    if (md == LOB_SPMM_DF64) {
+      if (c == 0) return batch_class<LOB_SPMM_DF64, 2>(ms, X, Y, ncol, nact, v, jh, jd, st);
+      if (c == 1) return batch_class<LOB_SPMM_DF64, 4>(ms, X, Y, ncol, nact, v, jh, jd, st);
+      if (c == 2) return batch_class<LOB_SPMM_DF64, 8>(ms, X, Y, ncol, nact, v, jh, jd, st);
+      return batch_class<LOB_SPMM_DF64, 16>(ms, X, Y, ncol, nact, v, jh, jd, st);
+    }
+    if (c == 0) return batch_class<LOB_SPMM_FP64, 2>(ms, X, Y, ncol, nact, v, jh, jd, st);
+    if (c == 1) return batch_class<LOB_SPMM_FP64, 4>(ms, X, Y, ncol, nact, v, jh, jd, st);
+    if (c == 2) return batch_class<LOB_SPMM_FP64, 8>(ms, X, Y, ncol, nact, v, jh, jd, st);
+    return batch_class<LOB_SPMM_FP64, 16>(ms, X, Y, ncol, nact, v, jh, jd, st);
+  };
+  for (int md = 0; md < 3; md++)
+    for (int c = 0; c < 4; c++) LOB_TRY(run(md, c));
+  return LOB_OK;
+}
 
 int lob_spmm_launch(const lob_matrix* m, int mode, const double* X, double* Y, int nb, int64_t n_act,
                     cudaStream_t st) {

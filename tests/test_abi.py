@@ -30,7 +30,9 @@ def built_lib():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for f in ("lob_create", "lob_spmm", "lob_solve", "lob_destroy", "lob_strerror", "lob_gram", "lob_lincomb",
-              "lob_precond_apply", "lob_rayleigh_ritz", "lob_export_tiles", "lob_matrix_info_get"):
+              "lob_precond_apply", "lob_rayleigh_ritz", "lob_export_tiles", "lob_matrix_info_get", "lob_spmm_batch",
+              "lob_server_create", "lob_server_submit", "lob_server_progress", "lob_server_poll",
+              "lob_server_destroy"):
         assert f in names
 
 
@@ -50,6 +52,13 @@ def test_library_loads_and_reports_errors(built_lib):
     assert lib.lob_spmm(None, 0, None, None, 8, None) == lob.LOB_ERR_ARG
     assert lib.lob_gram(0, 1, None, 1, 1, None, 1, None, 0, None) == lob.LOB_ERR_ARG
     assert lib.lob_destroy(None) == lob.LOB_OK
+    assert lib.lob_spmm_batch(1, None, None, None, None, None, None) == lob.LOB_ERR_ARG
+    assert lib.lob_spmm_batch(0, None, None, None, None, None, None) == lob.LOB_OK
+    assert lib.lob_server_create(None, None) == lob.LOB_ERR_ARG
+    assert lib.lob_server_submit(None, None, None) == lob.LOB_ERR_ARG
+    assert lib.lob_server_progress(None, 0, None) == lob.LOB_ERR_ARG
+    assert lib.lob_server_poll(None, 1, None) == lob.LOB_ERR_ARG
+    assert lib.lob_server_destroy(None) == lob.LOB_ERR_ARG
 
 
 def test_synth_device_library_builds():

@@ -66,7 +66,7 @@ def test_tiles_reject_bad_entries():
         lob.Matrix(4, np.array([0]), np.array([4]), np.array([1.0]))  # out of range
 
 
-def expected_perm(T, chunk=4096):
+def expected_perm(T, chunk):
     """Chunk-local (column, row)-order permutation rebuilt from the canonical store."""
     rc = T["rc"].astype(np.int64)
     tp = T["tile_ptr"]
@@ -89,4 +89,6 @@ def test_column_permutation_round_trips(n, density):
     H = random_upper(n, density, rng)
     M = lob.Matrix(n, H.rows, H.cols, H.vals)
     T = M.export_tiles()
-    assert np.array_equal(M.export_perm(), expected_perm(T))
+    chunk = M.info()["perm_chunk"]
+    assert chunk in (1024, 2048, 4096)
+    assert np.array_equal(M.export_perm(), expected_perm(T, chunk))

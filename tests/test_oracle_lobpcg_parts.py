@@ -135,3 +135,97 @@ def test_eq13_block_diag_precond_gives_correction_and_eps_squared():
     r1 = res[0] / res[1]
     r2 = res[1] / res[2]
     assert 3.0 < r1 < 5.0 and 3.0 < r2 < 5.0, res
+
+
+def _blocks(A, bounds):
+    return [A[bounds[i]:bounds[i + 1], bounds[i]:bounds[i + 1]] for i in range(len(bounds) - 1)]
+
+
+@pytest.mark.parametrize("bp", [5, 16])
+def test_krylov_one_step_closed_forms(bp):
+    """One FOM step is w = (r^T r / r^T A r) r; one minimal-residual step is
+    w = (r^T A r / ||A r||^2) r (A = H~_[i] - mu_j I)."""
+    rng = np.random.default_rng(40 + bp)
+    n = 3 * bp + 2
+    H = random_upper(n, 0.4, rng)
+    Ad = dense_by_indexing(H)
+    bounds = oracle.uniform_bounds(n, bp)
+    mu = np.array([-0.7, 0.3])
+    R = rng.standard_normal((n, 2))
+    Wf = oracle.block_krylov(H, bounds, mu, R, "fom", 1)
+    Wm = oracle.block_krylov(H, bounds, mu, R, "minres", 1)
+    for i, B in enumerate(_blocks(Ad, bounds)):
+        s = slice(bounds[i], bounds[i + 1])
+        for j in range(2):
+            A = B - mu[j] * np.eye(B.shape[0])
+            r = R[s, j]
+            Ar = A @ r
+            np.testing.assert_allclose(Wf[s, j], (r @ r) / (r @ Ar) * r, rtol=1e-11, atol=0)
+            np.testing.assert_allclose(Wm[s, j], (r @ Ar) / (Ar @ Ar) * r, rtol=1e-11, atol=0)
+
+
+@pytest.mark.parametrize("bp", [2, 3])
+def test_krylov_full_space_is_the_direct_solve(bp):
+    """With as many steps as the block order the Krylov space is the whole block space, so FOM
+    and the minimal-residual iterate both equal the direct solve of eq. 11 (a 2-step process on
+    2 x 2 blocks stops early on the invariant subspace)."""
+    rng = np.random.default_rng(50 + bp)
+    n = 7 * bp
+    H = random_upper(n, 0.6, rng)
+    bounds = oracle.uniform_bounds(n, bp)
+    mu = np.array([0.25, -1.5, 2.0])
+    R = rng.standard_normal((n, 3))
+    Wd = oracle.block_precond(H, bounds, mu, R)
+    for method in ("fom", "minres"):
+        W = oracle.block_krylov(H, bounds, mu, R, method, 3)
+        assert np.abs(W - Wd).max() <= 1e-9 * np.abs(Wd).max()
+
+
+@pytest.mark.parametrize("steps", [2, 3])
+def test_krylov_galerkin_and_minimal_residual(steps):
+    """FOM: r - A w is orthogonal to K_s(A, r). Minimal residual: ||r - A w|| is no larger than
+    for any other w in K_s(A, r) (checked against the FOM iterate and random members)."""
+    rng = np.random.default_rng(60 + steps)
+    bp = 24
+    n = 2 * bp
+    H = random_upper(n, 0.3, rng)
+    Ad = dense_by_indexing(H)
+    bounds = oracle.uniform_bounds(n, bp)
+    lam_all = np.linalg.eigvalsh(_blocks(Ad, bounds)[0])
+    mu = np.array([lam_all[3] + 0.01, lam_all[0] - 1.0])  # one indefinite shift, one definite
+    R = rng.standard_normal((n, 2))
+    Wf = oracle.block_krylov(H, bounds, mu, R, "fom", steps)
+    Wm = oracle.block_krylov(H, bounds, mu, R, "minres", steps)
+    for i, B in enumerate(_blocks(Ad, bounds)):
+        s = slice(bounds[i], bounds[i + 1])
+        for j in range(2):
+            A = B - mu[j] * np.eye(bp)
+            r = R[s, j]
+            K = np.stack([np.linalg.matrix_power(A, t) @ r for t in range(steps)], axis=1)
+            res_f = r - A @ Wf[s, j]
+            assert np.abs(K.T @ res_f).max() <= 1e-8 * np.abs(K).max() * np.linalg.norm(r)
+            rm = np.linalg.norm(r - A @ Wm[s, j])
+            assert rm <= np.linalg.norm(res_f) * (1 + 1e-10)
+            for _ in range(20):
+                w = K @ rng.standard_normal(steps)
+                assert rm <= np.linalg.norm(r - A @ w) * (1 + 1e-10)
+
+
+def test_krylov_abs_is_direct_below_the_spectrum_and_spd():
+    rng = np.random.default_rng(70)
+    n, bp = 60, 20
+    H = random_upper(n, 0.3, rng)
+    Ad = dense_by_indexing(H)
+    bounds = oracle.uniform_bounds(n, bp)
+    lo = min(np.linalg.eigvalsh(B).min() for B in _blocks(Ad, bounds))
+    R = rng.standard_normal((n, 2))
+    mu = np.array([lo - 0.5, lo - 3.0])
+    Wa = oracle.block_krylov(H, bounds, mu, R, "abs")
+    Wd = oracle.block_precond(H, bounds, mu, R)
+    assert np.abs(Wa - Wd).max() <= 1e-10 * np.abs(Wd).max()
+    mu2 = np.array([0.0, 0.4])  # inside the spectra: |A|^{-1} stays positive definite
+    Wa2 = oracle.block_krylov(H, bounds, mu2, R, "abs")
+    for i in range(len(bounds) - 1):
+        s = slice(bounds[i], bounds[i + 1])
+        for j in range(2):
+            assert R[s, j] @ Wa2[s, j] > 0
