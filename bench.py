@@ -235,10 +235,13 @@ def run_serving(args, lob, synth, torch):
     out, wall, st, late = serve(reqs, True)
     lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in out])
     ok = sum(1 for r in out if r["rc"] == lob.LOB_OK)
+    failed = [dict(n=q["n"], k=q["k"], nb=q["nb"], rc=int(r["rc"]), iterations=int(r["stats"]["iterations"]))
+              for q, r in zip(reqs, out) if r["rc"] != lob.LOB_OK]
     serving = {"workload": f"{len(reqs)} requests, Poisson {args.serve_rate:g}/s, n log-uniform [2000, 200000], "
                            f"k U{{1..8}}, nb = next pow2 >= k, ~30 nnz/row, mixed, tol 1e-8, b_p=32, budget 60 GB",
                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                "mean_ms": float(lat.mean()), "solves_per_s": len(out) / wall, "wall_s": wall, "converged": ok,
+               "not_converged": failed[:20],
                "max_submit_lateness_ms": late * 1e3, "peak_bytes": int(st["bytes_peak"]),
                "spmm_products": int(st["spmm_products"]), "spmm_launches": int(st["spmm_launches"]),
                "matrix_build_s": build_s}

@@ -218,6 +218,26 @@ typedef struct {
 int lob_solve(lob_matrix* m, int32_t k, int32_t nb, double tol, const double* X0, const lob_solve_opts* opts,
               double* lambda, double* X, lob_stats* st);
 
+/* ---- the Lanczos baseline ----
+ * The legacy single-vector solver LOBPCG is compared against (Section 1; Section 5.2, Table 3),
+ * on the GPU: FP64 SpMV through the tile store, full reorthogonalisation (classical Gram-Schmidt,
+ * twice) against all previous Lanczos vectors, and every `check` steps (0 = 10) the k smallest
+ * Ritz pairs of the tridiagonal (bisection + inverse iteration on the host); it stops when every
+ * Ritz residual estimate beta_j |s_{j,i}| <= tol ||H||_inf, the relative residual lob_solve's
+ * test uses. 1 <= k <= 16, max_steps > k (holds n x max_steps doubles). lambda: host, k values
+ * ascending. X: device n x k row-major Ritz vectors, or NULL. Needs FP64 values. Errors:
+ * LOB_ERR_ARG, LOB_ERR_NOMEM, LOB_ERR_CUDA, LOB_ERR_NOCONV (max_steps reached; outputs filled). */
+typedef struct {
+  int32_t steps;
+  int32_t reserved;
+  double time_ms;       /* wall time */
+  double spmv_ms;       /* device time of one SpMV (the last one timed) */
+  double device_bytes;  /* Lanczos basis bytes */
+} lob_lanczos_stats;
+
+int lob_lanczos(lob_matrix* H, int32_t k, double tol, int32_t max_steps, int32_t check, uint64_t seed,
+                double* lambda, double* X, lob_lanczos_stats* stats, void* stream);
+
 /* ---- serving: continuous batching of solves ----
  *
  * A server keeps the LOBPCG state of every admitted solve resident on the device (S = [X W P],

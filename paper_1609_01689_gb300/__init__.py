@@ -81,6 +81,10 @@ class Stats(ctypes.Structure):
                     residual=[self.residual[j] for j in range(nb)])
 
 
+class LanczosStats(ctypes.Structure):
+    _fields_ = [("steps", _I32), ("reserved", _I32), ("time_ms", _D), ("spmv_ms", _D), ("device_bytes", _D)]
+
+
 class ServerOpts(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_uint64), ("max_active", _I32), ("batch_spmm", _I32)]
 
@@ -128,6 +132,7 @@ def _load():
     L.lob_rayleigh_ritz_noalloc.restype = ctypes.c_int
     L.lob_solve.argtypes = [_P, _I32, _I32, _D, _P, ctypes.POINTER(SolveOpts), _P, _P, ctypes.POINTER(Stats)]
     L.lob_spmm_batch.argtypes = [_I32, _P, _P, _P, _P, _P, _P]
+    L.lob_lanczos.argtypes = [_P, _I32, _D, _I32, _I32, ctypes.c_uint64, _P, _P, ctypes.POINTER(LanczosStats), _P]
     L.lob_server_create.argtypes = [ctypes.POINTER(ServerOpts), ctypes.POINTER(_P)]
     L.lob_server_submit.argtypes = [_P, ctypes.POINTER(Request), ctypes.POINTER(_I64)]
     L.lob_server_progress.argtypes = [_P, _I32, ctypes.POINTER(_I32)]
@@ -140,7 +145,7 @@ def _load():
     L.lob_strerror.restype = ctypes.c_char_p
     for f in ("lob_create", "lob_destroy", "lob_matrix_info_get", "lob_export_tiles", "lob_export_perm", "lob_spmm",
               "lob_gram",
-              "lob_lincomb", "lob_precond_apply", "lob_rayleigh_ritz", "lob_solve", "lob_spmm_batch",
+              "lob_lincomb", "lob_precond_apply", "lob_rayleigh_ritz", "lob_solve", "lob_spmm_batch", "lob_lanczos",
               "lob_server_create", "lob_server_submit", "lob_server_progress", "lob_server_poll",
               "lob_server_stats_get", "lob_server_destroy"):
         getattr(L, f).restype = ctypes.c_int
@@ -279,8 +284,10 @@ class Matrix:
         return W
 
     def solve(self, k, nb, tol, X0=None, mode="fp64", precond=False, n_small=0, max_iter=0, refine_iter=0,
-              seed=1, precond_shift=0, mixed_tol=0.0, norm_H=0.0, X_out=None, precond_solve="fom", precond_steps=3):
-        """k smallest eigenpairs (lob_solve). Returns (lam, X, stats, status)."""
+              seed=1, precond_shift=0, mixed_tol=0.0, norm_H=0.0, X_out=None, precond_solve="fom", precond_steps=3,
+              stats=True):
+        """k smallest eigenpairs (lob_solve). Returns (lam, X, stats, status). stats=False passes no
+        stats struct: the solver then keeps no phase timers and replays its stages as CUDA graphs."""
         torch = _torch()
         X = X_out if X_out is not None else torch.empty((self.n, nb), dtype=torch.float64, device="cuda")
         x0 = _dev_f64(X0) if X0 is not None else None
@@ -289,10 +296,23 @@ class Matrix:
         o = SolveOpts(_MODES[mode], int(bool(precond)), max_iter, refine_iter, norm_H, n_small, seed, precond_shift,
                       _PSOLVE[precond_solve], precond_steps, 0, mixed_tol, _stream())
         rc = lib().lob_solve(self._h, k, nb, tol, x0.data_ptr() if x0 is not None else None, ctypes.byref(o),
-                             lam.ctypes.data, X.data_ptr(), ctypes.byref(st))
+                             lam.ctypes.data, X.data_ptr(), ctypes.byref(st) if stats else None)
         if rc not in (LOB_OK, LOB_ERR_NOCONV):
             raise LobError(rc, "lob_solve")
         return lam, X, st.to_dict(nb), rc
+
+
+def lanczos(matrix, k, tol, max_steps=1000, check=10, seed=7, vectors=True):
+    """k smallest eigenpairs by the GPU Lanczos baseline (lob_lanczos). Returns (lam, X, stats, rc)."""
+    torch = _torch()
+    lam = np.zeros(k, np.float64)
+    X = torch.empty((matrix.n, k), dtype=torch.float64, device="cuda") if vectors else None
+    st = LanczosStats()
+    rc = lib().lob_lanczos(matrix.handle, k, tol, max_steps, check, seed, lam.ctypes.data,
+                           X.data_ptr() if X is not None else None, ctypes.byref(st), _stream())
+    if rc not in (LOB_OK, LOB_ERR_NOCONV):
+        raise LobError(rc, "lob_lanczos")
+    return lam, X, dict(steps=st.steps, time_ms=st.time_ms, spmv_ms=st.spmv_ms, device_bytes=st.device_bytes), rc
 
 
 def gram(A, B, mode="fp64"):

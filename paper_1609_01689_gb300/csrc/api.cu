@@ -86,7 +86,7 @@ int lob_matrix_info_get(const lob_matrix* m, lob_matrix_info* out) {
   out->tile = LOB_TILE; out->values = m->values; out->precond_block = m->P.bp; out->perm_chunk = LOB_PERM_CHUNK;
   out->norm_inf = m->norm_inf;
   out->store_bytes = (m->T.nt + 1) * 8 + m->T.ntiles * (4 + 4 + 8) + 8 + m->T.nnz * 4 +
-                     (m->T.v64 ? m->T.nnz * 8 : 0) + (m->T.v32 ? m->T.nnz * 4 : 0);
+                     (m->T.v64 ? m->T.nnz * 8 : 0) + (m->T.v32 ? m->T.nnz * 4 : 0);  // canonical arrays only
   out->precond_bytes = m->P.nblk * (int64_t)m->P.bp * m->P.bp * 4 + m->P.nblk * (int64_t)m->P.bp * 4;
   return LOB_OK;
 }

@@ -27,6 +27,7 @@ struct Ar<false> {
   __device__ static in_t load(double x) { return x; }
   __device__ static in_t zero_in() { return 0.0; }
   __device__ static void zero(acc_t& a) { a.v = 0.0; }
+  __device__ static void init(acc_t& a, double x) { a.v = x; }
   __device__ static void mac(acc_t& a, in_t x, in_t y) { a.v = fma(x, y, a.v); }
   __device__ static double out(acc_t a) { return a.v; }
 };
@@ -37,6 +38,7 @@ struct Ar<true> {
   __device__ static in_t load(double x) { return df_split(x); }
   __device__ static in_t zero_in() { return make_float2(0.f, 0.f); }
   __device__ static void zero(acc_t& a) { a.hi = 0.f; a.lo = 0.f; }
+  __device__ static void init(acc_t& a, double x) { const float2 s = df_split(x); a.hi = s.x; a.lo = s.y; }
   __device__ static void mac(acc_t& a, in_t x, in_t y) { df_mac(a.hi, a.lo, x.x, x.y, y.x, y.y); }
   __device__ static double out(acc_t a) { df_renorm(a.hi, a.lo); return df_join_int(a.hi, a.lo); }
 };
@@ -130,9 +132,13 @@ __global__ void k_gram_reduce(int nchunks, int pq, int q, int sym, int tge, cons
   if (lane == 0) G[warp] = s;
 }
 
+// Y = A C (+ D): 16 rows x 16 output columns per CTA. The CTA loads its rows of A (all p
+// columns) into shared memory before writing any output, so with a single column block (q <= 16)
+// the output may be columns of A's own rows (used in place by the solver).
 template <bool DF>
 __global__ void __launch_bounds__(256) k_lincomb(int64_t n, int p, const double* __restrict__ A, int lda, int q,
-                                                 const double* __restrict__ C, double* __restrict__ Y, int ldy) {
+                                                 const double* __restrict__ C, double* __restrict__ Y, int ldy,
+                                                 const double* __restrict__ D, int ldd) {
   using R = Ar<DF>;
   using in_t = typename R::in_t;
   extern __shared__ __align__(16) unsigned char sm[];
@@ -152,9 +158,10 @@ __global__ void __launch_bounds__(256) k_lincomb(int64_t n, int p, const double*
   }
   __syncthreads();
   typename R::acc_t acc;
-  R::zero(acc);
-  for (int a = 0; a < p; a++) R::mac(acc, As[rl * p + a], Cs[a * 16 + j]);
   const int64_t r = r0 + rl;
+  R::zero(acc);
+  if (D && r < n && j0 + j < q) R::init(acc, D[r * ldd + j0 + j]);  // Y = A C + D
+  for (int a = 0; a < p; a++) R::mac(acc, As[rl * p + a], Cs[a * 16 + j]);
   if (r < n && j0 + j < q) Y[r * ldy + j0 + j] = R::out(acc);
 }
 
@@ -214,17 +221,17 @@ int lob_gram_launch(int64_t n, int p, const double* A, int lda, int q, const dou
 }
 
 int lob_lincomb_launch(int64_t n, int p, const double* A, int lda, int q, const double* C, double* Y, int ldy,
-                       int mode, cudaStream_t st) {
+                       int mode, cudaStream_t st, const double* D, int ldd) {
   if (n < 1 || p < 1 || q < 1 || p > 192 || q > 192 || lda < p || ldy < q || !A || !C || !Y) return LOB_ERR_ARG;
   if (mode != LOB_SPMM_FP64 && mode != LOB_SPMM_MIXED) return LOB_ERR_ARG;
   dim3 grid((unsigned)((n + 15) / 16), (q + 15) / 16);
   const size_t smem = 2ull * 16 * p * (mode == LOB_SPMM_MIXED ? sizeof(float2) : sizeof(double));
   if (mode == LOB_SPMM_MIXED) {
     LOB_CUDA(cudaFuncSetAttribute(k_lincomb<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    (k_lincomb<true><<<grid, 256, smem, st>>>(n, p, A, lda, q, C, Y, ldy), LOB_LAUNCHED());
+    (k_lincomb<true><<<grid, 256, smem, st>>>(n, p, A, lda, q, C, Y, ldy, D, ldd), LOB_LAUNCHED());
   } else {
     LOB_CUDA(cudaFuncSetAttribute(k_lincomb<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    (k_lincomb<false><<<grid, 256, smem, st>>>(n, p, A, lda, q, C, Y, ldy), LOB_LAUNCHED());
+    (k_lincomb<false><<<grid, 256, smem, st>>>(n, p, A, lda, q, C, Y, ldy, D, ldd), LOB_LAUNCHED());
   }
   LOB_CUDA(cudaGetLastError());
   return LOB_OK;

@@ -51,6 +51,11 @@ struct lob_tiles {
   int32_t* tchunk = nullptr;   // [ntiles+1] first chunk id of each tile
   uint16_t* cptrs = nullptr;   // [nchunks][2][257] kernel-private: start of each in-tile row in the
                                // chunk's (r, c) order, then of each in-tile column in (c, r) order
+  uint32_t* cpr = nullptr;     // [nnz] kernel-private: the chunk's (c, r) order as (r << 16) | q, q the
+                               // chunk-local index of the entry (cperm with the row attached)
+  uint2* rec = nullptr;        // [nnz] kernel-private (FP32 values): {bits of v32, rc} interleaved
+  uint8_t* cmap = nullptr;     // [ntiles][256] kernel-private: column handled by in-tile slot a in the
+                               // column pass; off-diagonal tiles pair long rows with short columns
 };
 
 // Block-diagonal preconditioner of eq. 11: per block i (rows [i*bp, i*bp + m_i)),
@@ -85,6 +90,9 @@ struct lob_spmm_job {
   const void* vlo;    // DF64 low parts
   const uint16_t* cperm;
   const uint16_t* cptrs;
+  const uint32_t* cpr;
+  const uint2* rec;
+  const uint8_t* cmap;
   const void* Xs;     // staged X of this matrix
   double* Y;
   int32_t ldy, c0, w, pad;
@@ -131,8 +139,9 @@ size_t lob_task_bytes(const lob_matrix* m, int nb, int64_t n_small);
 
 int lob_gram_launch(int64_t n, int p, const double* A, int lda, int q, const double* B, int ldb, double* G, int mode,
                     cudaStream_t st);
+// Y = A C (+ D when D is given, n x q with leading dimension ldd).
 int lob_lincomb_launch(int64_t n, int p, const double* A, int lda, int q, const double* C, double* Y, int ldy,
-                       int mode, cudaStream_t st);
+                       int mode, cudaStream_t st, const double* D = nullptr, int ldd = 0);
 int lob_precond_launch(const lob_matrix* m, const double* mu, const double* R, double* W, int nb, int64_t n_act,
                        int solve, int steps, cudaStream_t st);
 int lob_rr_launch(int m, const double* G, const double* M, double* theta, double* C, int32_t* info, double* work,

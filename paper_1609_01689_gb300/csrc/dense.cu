@@ -379,15 +379,23 @@ __global__ void __launch_bounds__(RR_THREADS) k_rayleigh_ritz_df(int m, const do
 static size_t rr_smem_bytes(int m) { return 3ull * m * m * 8; }
 static const size_t RR_SMEM_MAX = 200 * 1024;
 
+// Threads for order m: one per 2x2 block of a Jacobi round ((m+1)/2 squared), 128 to 1,024 --
+// the kernel is barrier-latency bound, and fewer warps make each barrier cheaper.
+static int rr_threads(int m) {
+  const int np = (m + 1) / 2;
+  int t = ((np * np + 31) / 32) * 32;
+  return t < 128 ? 128 : (t > RR_THREADS ? RR_THREADS : t);
+}
+
 int lob_rr_launch_df(int m, const double* G, const double* M, double* theta, double* C, int32_t* info, double* work,
                      cudaStream_t st, int chol_only) {
   if (m < 1 || m > 192) return LOB_ERR_ARG;
   const size_t sb = rr_smem_bytes(m);
   if (sb <= RR_SMEM_MAX) {
     LOB_CUDA(cudaFuncSetAttribute(k_rayleigh_ritz_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
-    (k_rayleigh_ritz_df<true><<<1, RR_THREADS, sb, st>>>(m, G, M, theta, C, info, work, chol_only), LOB_LAUNCHED());
+    (k_rayleigh_ritz_df<true><<<1, rr_threads(m), sb, st>>>(m, G, M, theta, C, info, work, chol_only), LOB_LAUNCHED());
   } else {
-    (k_rayleigh_ritz_df<false><<<1, RR_THREADS, 0, st>>>(m, G, M, theta, C, info, work, chol_only), LOB_LAUNCHED());
+    (k_rayleigh_ritz_df<false><<<1, rr_threads(m), 0, st>>>(m, G, M, theta, C, info, work, chol_only), LOB_LAUNCHED());
   }
   LOB_CUDA(cudaGetLastError());
   return LOB_OK;
@@ -401,9 +409,9 @@ int lob_rr_launch(int m, const double* G, const double* M, double* theta, double
   const size_t sb = rr_smem_bytes(m);
   if (sb <= RR_SMEM_MAX) {
     LOB_CUDA(cudaFuncSetAttribute(k_rayleigh_ritz<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
-    (k_rayleigh_ritz<true><<<1, RR_THREADS, sb, st>>>(m, G, M, theta, C, info, work, chol_only), LOB_LAUNCHED());
+    (k_rayleigh_ritz<true><<<1, rr_threads(m), sb, st>>>(m, G, M, theta, C, info, work, chol_only), LOB_LAUNCHED());
   } else {
-    (k_rayleigh_ritz<false><<<1, RR_THREADS, 0, st>>>(m, G, M, theta, C, info, work, chol_only), LOB_LAUNCHED());
+    (k_rayleigh_ritz<false><<<1, rr_threads(m), 0, st>>>(m, G, M, theta, C, info, work, chol_only), LOB_LAUNCHED());
   }
   LOB_CUDA(cudaGetLastError());
   return LOB_OK;

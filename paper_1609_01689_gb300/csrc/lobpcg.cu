@@ -94,13 +94,22 @@ __global__ void k_residual(int64_t n, int nb, const double* __restrict__ X, int 
   }
 }
 
-// relres_j = sqrt(sum r^2) / (normH sqrt(sum x^2)), fixed-order reduction over the partials.
-__global__ void k_relres(int nparts, int nb, const double* __restrict__ part, double normH, double* __restrict__ out) {
-  const int j = threadIdx.x;
-  if (j >= nb) return;
+// relres_j = sqrt(sum r^2) / (normH sqrt(sum x^2)): one CTA per column, a strided pass over the
+// partials then a fixed-order tree, so the result is deterministic.
+__global__ void __launch_bounds__(256) k_relres(int nparts, int nb, const double* __restrict__ part, double normH,
+                                                double* __restrict__ out) {
+  __shared__ double srr[256], sxx[256];
+  const int j = blockIdx.x, tid = threadIdx.x;
   double rr = 0.0, xx = 0.0;
-  for (int b = 0; b < nparts; b++) { rr += part[(int64_t)b * 2 * nb + j]; xx += part[(int64_t)b * 2 * nb + nb + j]; }
-  out[j] = sqrt(rr) / (normH * sqrt(xx > 0.0 ? xx : 1.0));
+  for (int b = tid; b < nparts; b += 256) { rr += part[(int64_t)b * 2 * nb + j]; xx += part[(int64_t)b * 2 * nb + nb + j]; }
+  srr[tid] = rr;
+  sxx[tid] = xx;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (tid < o) { srr[tid] += srr[tid + o]; sxx[tid] += sxx[tid + o]; }
+    __syncthreads();
+  }
+  if (tid == 0) out[j] = sqrt(srr[0]) / (normH * sqrt(sxx[0] > 0.0 ? sxx[0] : 1.0));
 }
 
 // Shifts mu_j for the preconditioner. mode 0: mu_j = theta_j. mode 1 (Section 4.3 rules 3-4):
@@ -239,7 +248,7 @@ enum {
 
 size_t solver_doubles(int64_t n, int nb) {
   const size_t m = 3 * (size_t)nb;
-  size_t d = 2 * (size_t)n * m + 8 * (size_t)n * nb;       // S, HS; P, HP, R, W, Tn, THn, Tp, THp
+  size_t d = 2 * (size_t)n * m + 7 * (size_t)n * nb;       // S, HS; P, HP, R, W, Tn, Tp, THp
   d += 11 * m * m + 3 * m + 2 * (size_t)nb;                 // G, M, C, Cx, C2, Z, M_P, C_P, ...
   d += lob_gram_work_doubles(n, 1, 1) * m * m;              // Gram chunk partials
   d += lob_rr_work_doubles((int)m);
@@ -265,7 +274,7 @@ struct lob_task {
   std::chrono::steady_clock::time_point t0;
   // device state
   int ldS = 0;
-  DBuf S, HS, P, HP, R, W, Tn, THn, Tp, THp, G, Mm, Cc, Cx, theta, thw, work, rrwork, part, relres_d, mu, C2, Z;
+  DBuf S, HS, P, HP, R, W, Tn, Tp, THp, G, Mm, Cc, Cx, theta, thw, work, rrwork, part, relres_d, mu, C2, Z;
   DBuf MmP, CcP, thP, info_d, imap;
   DBuf gEc, gHEc, gG, gM, gth, gC, gwk;  // dense initial guess
   HostBox* hb = nullptr;
@@ -284,11 +293,58 @@ struct lob_task {
   double* sp_post = nullptr;
   int sp_post_ld = 0;
   lob_task* child = nullptr;
+  // captured stages: one graph per stage shape (stage, active columns, P present, ...), replayed
+  // as a single launch; used when the task keeps no phase timers
+  bool graphs = false;
+  struct Staged { uint64_t key; cudaGraphExec_t exec; long long kernels; };
+  std::vector<Staged> gcache;
 
   ~lob_task() {
     delete child;
+    for (auto& g : gcache) cudaGraphExecDestroy(g.exec);
     if (ev) cudaEventDestroy(ev);
     box_put(hb);
+  }
+
+  uint64_t skey(int stage_id, int a, int b, int c) const {
+    return (uint64_t)stage_id | ((uint64_t)(a & 0xFFF) << 4) | ((uint64_t)(b & 0xFFF) << 16) |
+           ((uint64_t)(c & 0xFF) << 28) | ((uint64_t)blas_mode << 36) | ((uint64_t)spmm_mode << 40);
+  }
+
+  // Enqueue a stage: replay its graph, or capture it on first use (falling back to plain launches
+  // if capture is not possible).
+  template <class F>
+  int stage(uint64_t key, F&& enqueue) {
+    if (!graphs) return enqueue();
+    for (const Staged& g : gcache)
+      if (g.key == key) {
+        LOB_CUDA(cudaGraphLaunch(g.exec, st));
+        g_lob_launches.fetch_add(g.kernels, std::memory_order_relaxed);
+        return LOB_OK;
+      }
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      graphs = false;
+      return enqueue();
+    }
+    const long long k0 = g_lob_launches.load();
+    const int rc = enqueue();
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &g);
+    const long long nk = g_lob_launches.load() - k0;
+    g_lob_launches.fetch_sub(nk, std::memory_order_relaxed);  // captured, not yet launched
+    cudaGraphExec_t x = nullptr;
+    if (rc != LOB_OK || e != cudaSuccess || !g || cudaGraphInstantiate(&x, g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      graphs = false;
+      return rc != LOB_OK ? rc : enqueue();
+    }
+    cudaGraphDestroy(g);
+    gcache.push_back({key, x, nk});
+    LOB_CUDA(cudaGraphLaunch(x, st));
+    g_lob_launches.fetch_add(nk, std::memory_order_relaxed);
+    return LOB_OK;
   }
 
   double* ph(int i) { return timing ? &stats.phase_ms[i] : nullptr; }
@@ -299,7 +355,7 @@ struct lob_task {
     const size_t nS = (size_t)n * ldS, nv = (size_t)n * nb, mm = ldS;
     LOB_TRY(S.alloc(nS, st)); LOB_TRY(HS.alloc(nS, st));
     LOB_TRY(P.alloc(nv, st)); LOB_TRY(HP.alloc(nv, st)); LOB_TRY(R.alloc(nv, st)); LOB_TRY(W.alloc(nv, st));
-    LOB_TRY(Tn.alloc(nv, st)); LOB_TRY(THn.alloc(nv, st)); LOB_TRY(Tp.alloc(nv, st)); LOB_TRY(THp.alloc(nv, st));
+    LOB_TRY(Tn.alloc(nv, st)); LOB_TRY(Tp.alloc(nv, st)); LOB_TRY(THp.alloc(nv, st));
     LOB_TRY(G.alloc(mm * mm, st)); LOB_TRY(Mm.alloc(mm * mm, st)); LOB_TRY(Cc.alloc(mm * mm, st));
     LOB_TRY(Cx.alloc(mm * mm, st)); LOB_TRY(theta.alloc(mm, st)); LOB_TRY(thw.alloc(mm, st));
     LOB_TRY(MmP.alloc(mm * mm, st)); LOB_TRY(CcP.alloc(mm * mm, st)); LOB_TRY(thP.alloc(mm, st));
@@ -336,13 +392,18 @@ struct lob_task {
     return LOB_OK;
   }
 
-  // Register the product Y = H X (X, Y: ncol columns with leading dimensions ldx, ldy).
-  int want_spmm(const double* X, int ldx, double* Y, int ldy, int ncol) {
-    sp_x = X;
-    if (ldx != ncol) {
+  // Stage the operand of Y = H X (X, Y: ncol columns with leading dimensions ldx, ldy).
+  int spmm_stage(const double* X, int ldx, int ncol) {
+    if (ldx != ncol)
       (k_copy_cols<<<nblk(n * ncol), BS, 0, st>>>(n, ncol, X, ldx, nullptr, Tp.p, ncol), LOB_LAUNCHED());
-      sp_x = Tp.p;
-    }
+    return LOB_OK;
+  }
+
+  // Register the product Y = H X (X, Y: ncol columns with leading dimensions ldx, ldy); the
+  // operand must have been staged (spmm_stage) unless staged is false.
+  int want_spmm(const double* X, int ldx, double* Y, int ldy, int ncol, bool staged = false) {
+    if (!staged) LOB_TRY(spmm_stage(X, ldx, ncol));
+    sp_x = ldx != ncol ? Tp.p : X;
     sp_y = ldy != ncol ? THp.p : Y;
     sp_post = ldy != ncol ? Y : nullptr;
     sp_post_ld = ldy;
@@ -361,7 +422,6 @@ struct lob_task {
     if (sp_post)
       (k_copy_cols<<<nblk(n * sp_ncol), BS, 0, st>>>(n, sp_ncol, sp_y, sp_ncol, nullptr, sp_post, sp_post_ld),
        LOB_LAUNCHED());
-    sp_post = nullptr;
     return LOB_OK;
   }
 
@@ -378,6 +438,17 @@ struct lob_task {
     return read_info(SLOT_RR);
   }
 
+  // Y = A C (+ D) written to Y (leading dimension ldy), where Y may be columns of A's own rows:
+  // with q <= 16 one CTA covers all output columns of its rows and loads them before writing, so
+  // the product goes straight into place; wider products go through Tn.
+  int lincomb_into(int p, const double* A, int lda, int q, const double* C, double* Y, int ldy,
+                   const double* D = nullptr, int ldd = 0) {
+    if (q <= 16) return lob_lincomb_launch(n_act, p, A, lda, q, C, Y, ldy, blas_mode, st, D, ldd);
+    LOB_TRY(lob_lincomb_launch(n_act, p, A, lda, q, C, Tn.p, q, blas_mode, st, D, ldd));
+    (k_copy_cols<<<nblk(n_act * q), BS, 0, st>>>(n_act, q, Tn.p, q, nullptr, Y, ldy), LOB_LAUNCHED());
+    return LOB_OK;
+  }
+
   // Cholesky-QR, first half: B^T B = L L^T for the ncol columns at S[:, col0]; C = L^{-T}.
   int cholqr_begin(int col0, int ncol, double* Mb, double* Cb, double* thb, int slot) {
     Timer t(clk(), st, ph(PH_ORTH));
@@ -390,13 +461,8 @@ struct lob_task {
   // Cholesky-QR, second half: B <- B C (and the same on HS when withH).
   int cholqr_finish(int col0, int ncol, bool withH, const double* Cb) {
     Timer t(clk(), st, ph(PH_ORTH));
-    LOB_TRY(lob_lincomb_launch(n_act, ncol, S.p + col0, ldS, ncol, Cb, Tn.p, ncol, blas_mode, st));
-    (k_copy_cols<<<nblk(n_act * ncol), BS, 0, st>>>(n_act, ncol, Tn.p, ncol, nullptr, S.p + col0, ldS), LOB_LAUNCHED());
-    if (withH) {
-      LOB_TRY(lob_lincomb_launch(n_act, ncol, HS.p + col0, ldS, ncol, Cb, Tn.p, ncol, blas_mode, st));
-      (k_copy_cols<<<nblk(n_act * ncol), BS, 0, st>>>(n_act, ncol, Tn.p, ncol, nullptr, HS.p + col0, ldS),
-       LOB_LAUNCHED());
-    }
+    LOB_TRY(lincomb_into(ncol, S.p + col0, ldS, ncol, Cb, S.p + col0, ldS));
+    if (withH) LOB_TRY(lincomb_into(ncol, HS.p + col0, ldS, ncol, Cb, HS.p + col0, ldS));
     LOB_CUDA(cudaGetLastError());
     return LOB_OK;
   }
@@ -405,28 +471,31 @@ struct lob_task {
     Timer t(clk(), st, ph(PH_RESID));
     const size_t smem = (BS / 32) * 2 * nb * sizeof(double);
     (k_residual<<<nblk(n_act), BS, smem, st>>>(n_act, nb, S.p, ldS, HS.p, ldS, theta.p, R.p, part.p), LOB_LAUNCHED());
-    (k_relres<<<1, 64, 0, st>>>((int)nblk(n_act), nb, part.p, normH, relres_d.p), LOB_LAUNCHED());
+    (k_relres<<<nb, 256, 0, st>>>((int)nblk(n_act), nb, part.p, normH, relres_d.p), LOB_LAUNCHED());
     LOB_CUDA(cudaMemcpyAsync(hb->relres, relres_d.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
     return LOB_OK;
   }
 
-  // X <- S C[:, :nb], HX <- HS C[:, :nb]; P <- S[:, nb:mm] C[nb:mm, :nb], HP likewise.
+  // X <- S C[:, :nb], HX <- HS C[:, :nb]; P <- S[:, nb:mm] C[nb:mm, :nb], HP likewise. P is formed
+  // first and reused: X <- X C[:nb, :nb] + P (and H X likewise), which saves the products of the
+  // [W P] columns a second time.
   int update(int mm) {
     Timer t(clk(), st, ph(PH_UPDATE));
-    // first nb columns of the mm x mm (leading dimension mm) Ritz coefficients -> compact mm x nb
-    (k_copy_cols<<<nblk((int64_t)mm * nb), BS, 0, st>>>(mm, nb, Cc.p, mm, nullptr, Cx.p, nb), LOB_LAUNCHED());
-    LOB_TRY(lob_lincomb_launch(n_act, mm, S.p, ldS, nb, Cx.p, Tn.p, nb, blas_mode, st));
-    LOB_TRY(lob_lincomb_launch(n_act, mm, HS.p, ldS, nb, Cx.p, THn.p, nb, blas_mode, st));
-    if (mm > nb) {
-      // rows nb..mm-1 of C (row-major, leading dimension mm) -> compact (mm-nb) x nb block in C2
+    if (mm == nb) {
+      LOB_TRY(lincomb_into(nb, S.p, ldS, nb, Cc.p, S.p, ldS));
+      LOB_TRY(lincomb_into(nb, HS.p, ldS, nb, Cc.p, HS.p, ldS));
+    } else {
+      // rows nb..mm-1 of C (row-major, leading dimension mm) -> compact (mm-nb) x nb block in C2;
+      // rows 0..nb-1 -> Cx (nb x nb)
       (k_copy_cols<<<nblk((int64_t)(mm - nb) * nb), BS, 0, st>>>(mm - nb, nb, Cc.p + (size_t)nb * mm, mm, nullptr,
                                                                     C2.p, nb),
        LOB_LAUNCHED());
+      (k_copy_cols<<<nblk((int64_t)nb * nb), BS, 0, st>>>(nb, nb, Cc.p, mm, nullptr, Cx.p, nb), LOB_LAUNCHED());
       LOB_TRY(lob_lincomb_launch(n_act, mm - nb, S.p + nb, ldS, nb, C2.p, P.p, nb, blas_mode, st));
       LOB_TRY(lob_lincomb_launch(n_act, mm - nb, HS.p + nb, ldS, nb, C2.p, HP.p, nb, blas_mode, st));
+      LOB_TRY(lincomb_into(nb, S.p, ldS, nb, Cx.p, S.p, ldS, P.p, nb));
+      LOB_TRY(lincomb_into(nb, HS.p, ldS, nb, Cx.p, HS.p, ldS, HP.p, nb));
     }
-    (k_copy_cols<<<nblk(n_act * nb), BS, 0, st>>>(n_act, nb, Tn.p, nb, nullptr, S.p, ldS), LOB_LAUNCHED());
-    (k_copy_cols<<<nblk(n_act * nb), BS, 0, st>>>(n_act, nb, THn.p, nb, nullptr, HS.p, ldS), LOB_LAUNCHED());
     LOB_CUDA(cudaGetLastError());
     return LOB_OK;
   }
@@ -470,6 +539,7 @@ int task_init(lob_task* t, lob_matrix* m, int32_t k, int32_t nb, double tol, con
   t->blas_mode = o->mode == LOB_MODE_MIXED ? LOB_SPMM_MIXED : LOB_SPMM_FP64;
   t->max_iter = o->max_iter > 0 ? o->max_iter : 500;
   t->t0 = std::chrono::steady_clock::now();
+  t->graphs = !timing;
   return t->alloc();
 }
 }  // namespace
@@ -551,6 +621,7 @@ int lob_task::step() {
         return want_spmm(S.p, ldS, HS.p, ldS, nb);
       case PC_RUN_RR0:
         LOB_TRY(spmm_post());
+        sp_post = nullptr;
         LOB_TRY(rr_begin(nb));
         pc = PC_RUN_RR0_CHECK;
         return sync_point();
@@ -584,34 +655,37 @@ int lob_task::step() {
         }
         if (conv) { run_status = LOB_OK; pc = PC_RUN_END; continue; }
         // W = T^{-1} R (step 6) with the rules of Section 4.3
-        {
-          Timer t(clk(), st, ph(PH_PRECOND));
-          const bool pc_on = o.precond && M->P.bp > 0 && it > 3 && hb->relres[0] <= 1e-1;
-          if (pc_on) {
-            (k_shifts<<<1, 32, 0, st>>>(nb, o.precond_shift, theta.p, relres_d.p, normH, mu.p), LOB_LAUNCHED());
-            LOB_TRY(lob_precond_launch(M, mu.p, R.p, W.p, nb, n_act, o.precond_solve,
-                                       o.precond_steps > 0 ? o.precond_steps : 3, st));
+        const bool pc_on = o.precond && M->P.bp > 0 && it > 3 && hb->relres[0] <= 1e-1;
+        LOB_TRY(stage(skey(1, na, haveP ? 1 : 0, pc_on ? 1 : 0), [&]() -> int {
+          {
+            Timer t(clk(), st, ph(PH_PRECOND));
+            if (pc_on) {
+              (k_shifts<<<1, 32, 0, st>>>(nb, o.precond_shift, theta.p, relres_d.p, normH, mu.p), LOB_LAUNCHED());
+              LOB_TRY(lob_precond_launch(M, mu.p, R.p, W.p, nb, n_act, o.precond_solve,
+                                         o.precond_steps > 0 ? o.precond_steps : 3, st));
+            }
+            LOB_CUDA(cudaMemcpyAsync(map_d(), hb->map, na * sizeof(int), cudaMemcpyHostToDevice, st));
+            (k_copy_cols<<<nblk(n_act * na), BS, 0, st>>>(n_act, na, pc_on ? W.p : R.p, nb, map_d(), S.p + nb, ldS),
+             LOB_LAUNCHED());
           }
-          LOB_CUDA(cudaMemcpyAsync(map_d(), hb->map, na * sizeof(int), cudaMemcpyHostToDevice, st));
-          (k_copy_cols<<<nblk(n_act * na), BS, 0, st>>>(n_act, na, pc_on ? W.p : R.p, nb, map_d(), S.p + nb, ldS),
-           LOB_LAUNCHED());
-        }
-        // W <- W - X (X^T W), then Cholesky-QR (step 7)
-        {
-          Timer t(clk(), st, ph(PH_ORTH));
-          LOB_TRY(lob_gram_launch_ws(n_act, nb, S.p, ldS, na, S.p + nb, ldS, Z.p, blas_mode, work.p, st));
-          (k_proj_coef<<<nblk((nb + na) * na), BS, 0, st>>>(nb, na, Z.p, C2.p), LOB_LAUNCHED());
-          LOB_TRY(lob_lincomb_launch(n_act, nb + na, S.p, ldS, na, C2.p, Tn.p, na, blas_mode, st));
-          (k_copy_cols<<<nblk(n_act * na), BS, 0, st>>>(n_act, na, Tn.p, na, nullptr, S.p + nb, ldS), LOB_LAUNCHED());
-        }
-        LOB_TRY(cholqr_begin(nb, na, Mm.p, Cc.p, thw.p, SLOT_W));
-        if (haveP) {
-          // P and H P restricted to the active columns, after [X W]; Cholesky-QR of P alongside W's
-          (k_copy_cols<<<nblk(n_act * na), BS, 0, st>>>(n_act, na, P.p, nb, map_d(), S.p + nb + na, ldS), LOB_LAUNCHED());
-          (k_copy_cols<<<nblk(n_act * na), BS, 0, st>>>(n_act, na, HP.p, nb, map_d(), HS.p + nb + na, ldS),
-           LOB_LAUNCHED());
-          LOB_TRY(cholqr_begin(nb + na, na, MmP.p, CcP.p, thP.p, SLOT_P));
-        }
+          // W <- W - X (X^T W), then Cholesky-QR (step 7)
+          {
+            Timer t(clk(), st, ph(PH_ORTH));
+            LOB_TRY(lob_gram_launch_ws(n_act, nb, S.p, ldS, na, S.p + nb, ldS, Z.p, blas_mode, work.p, st));
+            (k_proj_coef<<<nblk((nb + na) * na), BS, 0, st>>>(nb, na, Z.p, C2.p), LOB_LAUNCHED());
+            LOB_TRY(lincomb_into(nb + na, S.p, ldS, na, C2.p, S.p + nb, ldS));
+          }
+          LOB_TRY(cholqr_begin(nb, na, Mm.p, Cc.p, thw.p, SLOT_W));
+          if (haveP) {
+            // P and H P restricted to the active columns, after [X W]; Cholesky-QR of P alongside W's
+            (k_copy_cols<<<nblk(n_act * na), BS, 0, st>>>(n_act, na, P.p, nb, map_d(), S.p + nb + na, ldS),
+             LOB_LAUNCHED());
+            (k_copy_cols<<<nblk(n_act * na), BS, 0, st>>>(n_act, na, HP.p, nb, map_d(), HS.p + nb + na, ldS),
+             LOB_LAUNCHED());
+            LOB_TRY(cholqr_begin(nb + na, na, MmP.p, CcP.p, thP.p, SLOT_P));
+          }
+          return LOB_OK;
+        }));
         wretry = false;
         pc = PC_ITER_CHOL;
         return sync_point();
@@ -626,22 +700,24 @@ int lob_task::step() {
           LOB_TRY(cholqr_begin(nb, na, Mm.p, Cc.p, thw.p, SLOT_W));
           return sync_point();
         }
-        LOB_TRY(cholqr_finish(nb, na, false, Cc.p));
         m = nb + na;
-        if (haveP) {
-          if (!hb->info[SLOT_P]) {
-            LOB_TRY(cholqr_finish(nb + na, na, true, CcP.p));
-            m += na;
-          } else {
-            restarts++;  // P lost rank: drop it for this iteration
-          }
-        }
+        const bool pok = haveP && !hb->info[SLOT_P];
+        if (haveP && !pok) restarts++;  // P lost rank: drop it for this iteration
+        if (pok) m += na;
+        LOB_TRY(stage(skey(2, na, pok ? 1 : 0, 0), [&]() -> int {
+          LOB_TRY(cholqr_finish(nb, na, false, Cc.p));
+          if (pok) LOB_TRY(cholqr_finish(nb + na, na, true, CcP.p));
+          return spmm_stage(S.p + nb, ldS, na);
+        }));
         pc = PC_ITER_RR;
-        return want_spmm(S.p + nb, ldS, HS.p + nb, ldS, na);
+        return want_spmm(S.p + nb, ldS, HS.p + nb, ldS, na, true);
       }
       case PC_ITER_RR:
-        LOB_TRY(spmm_post());
-        LOB_TRY(rr_begin(m));  // eq. 9, steps 7-8
+        LOB_TRY(stage(skey(3, m, na, 0), [&]() -> int {
+          LOB_TRY(spmm_post());
+          return rr_begin(m);  // eq. 9, steps 7-8
+        }));
+        sp_post = nullptr;
         pc = PC_ITER_RR_CHECK;
         return sync_point();
       case PC_ITER_RR_CHECK: {
@@ -653,11 +729,20 @@ int lob_task::step() {
           return sync_point();
         }
         if (hb->info[SLOT_RR]) { run_status = LOB_ERR_BREAKDOWN; pc = PC_RUN_END; continue; }
-        LOB_TRY(update(m));  // eq. 7, steps 9-10
         haveP = true;
         it++;
-        pc = PC_ITER_RESID;
-        continue;
+        if (it > run_max) {
+          LOB_TRY(update(m));
+          pc = PC_ITER_RESID;
+          continue;
+        }
+        // eq. 7, steps 9-10, then steps 4-5 of the next iteration
+        LOB_TRY(stage(skey(4, m, 0, 0), [&]() -> int {
+          LOB_TRY(update(m));
+          return residual_begin();
+        }));
+        pc = PC_ITER_DECIDE;
+        return sync_point();
       }
       case PC_RUN_END: {
         iters_total += it;

@@ -117,3 +117,33 @@ def test_solve_full_size_500k(c2_golden, mode, tol_lam):
     H = oracle.Coo(L.n, rows, cols, vals)
     res = oracle.residual_norms(H, X.cpu().numpy()[:, :8], lam) / oracle.norm_inf(H)
     assert res.max() <= 1e-8, res
+
+
+def test_solve_graph_replay_matches_plain(c1):
+    """Without a stats struct the solver captures each iteration stage once and replays it as a
+    CUDA graph; the result must match the plain launches."""
+    import paper_1609_01689_gb300 as lob
+    L, H, lam_ref, X_ref = c1
+    M = lob.Matrix(L.n, H.rows, H.cols, H.vals, precond_block=32)
+    n_small = int(synth.level_starts(L)[2])
+    for mode in ("fp64", "mixed"):
+        lam_a, _, _, rc_a = M.solve(5, 8, 1e-8, mode=mode, precond=True, n_small=n_small)
+        k0 = lob.kernel_launches()
+        lam_b, X, _, rc_b = M.solve(5, 8, 1e-8, mode=mode, precond=True, n_small=n_small, stats=False)
+        assert lob.kernel_launches() > k0  # graph replays are counted as their kernels
+        assert rc_a == rc_b == lob.LOB_OK
+        assert np.abs(lam_a - lam_b).max() <= 1e-10 * np.abs(lam_ref).max()
+        check(H, L, lam_b, X, lam_ref, X_ref, 5, 1e-9 if mode == "fp64" else 1e-8, 1e-8)
+
+
+def test_lanczos_baseline_matches_oracle(c1):
+    """The GPU Lanczos baseline (the paper's legacy solver) reaches the same eigenpairs."""
+    import paper_1609_01689_gb300 as lob
+    L, H, lam_ref, X_ref = c1
+    M = lob.Matrix(L.n, H.rows, H.cols, H.vals)
+    lam, X, st, rc = lob.lanczos(M, 5, 1e-10, max_steps=600)
+    assert rc == lob.LOB_OK
+    assert np.abs(lam - lam_ref[:5]).max() / max(np.abs(lam_ref[:5]).max(), 1.0) <= 1e-9
+    res = oracle.residual_norms(H, X.cpu().numpy(), lam)
+    assert res.max() <= 1e-8 * oracle.norm_inf(H)
+    assert st["steps"] % 10 == 0 and st["steps"] > 5
