@@ -35,6 +35,8 @@ WORKLOADS = {
                bp=32, tol=1e-8),
     "c1": dict(name="n=1536 levels 0..6, ~30 nnz/row, k=5, nb=8, b_p=32, tol 1e-8", cfg="c1", k=5, nb=8, bp=32,
                tol=1e-8),
+    "c3": dict(name="n=8000000 levels 0..14, ~300 nnz/row, k=10, nb=16, b_p=64, tol 1e-8", cfg="c3", k=10, nb=16,
+               bp=64, tol=1e-8),
 }
 
 
@@ -97,6 +99,12 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# DRAM bytes (read + write) of one FP32-value SpMM launch (k_spmm4<1, 16>) on the n = 500,000
+# workload, from an ncu capture of this bench's own command (profiles/spmm_mixed_c2_nb16.md).
+# Valid for the kernel as captured; reset to None when the kernel changes.
+SPMM_TRAFFIC = {"c2": 906987520}
 
 
 def golden_eigs(cfg):
@@ -301,6 +309,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-lanczos", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-compare", type=int, default=100)
@@ -385,7 +394,8 @@ def main():
                       "l2": "inputs larger than L2 (tile store %.2f GB)" % (info["store_bytes"] / 1e9),
                       "parallelism": f"replicas x{world}"},
            "roofline": {"bound": "hbm", "kernel": "symmetric SpMM (mixed)", "achieved": achieved, "peak": peak,
-                        "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                        "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                        "traffic": SPMM_TRAFFIC.get(wl["cfg"]),
                         "launches": spmm_calls, "avg_launch_ms": spmm_ms / max(spmm_calls, 1),
                         "bytes_per_launch": spmm_bytes / max(spmm_calls, 1)},
            "clocks": clocks, "gpu_launches": launches}
@@ -412,6 +422,22 @@ def main():
             fp["eig_err_vs_oracle"] = float((np.abs(lam64 - gold[:k]) / np.maximum(np.abs(gold[:k]), 1.0)).max())
         out["fp64_solver"] = fp
 
+    # ---- the Lanczos baseline (single vector, full reorthogonalisation, FP64) to the same residual
+    if not args.no_lanczos:
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lam_l, _, st_l, rc_l = lob.lanczos(M, k, tol, max_steps=1200, vectors=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_l = e0.elapsed_time(e1)
+        la = {"ms": t_l, "steps": st_l["steps"], "status": int(rc_l), "spmv_ms": st_l["spmv_ms"],
+              "basis_bytes": st_l["device_bytes"], "speedup_mixed_lobpcg_over_lanczos": t_l / ms_step}
+        if lam is not None:
+            la["max_eig_rel_diff_vs_lobpcg"] = float((np.abs(lam_l - lam) / np.maximum(np.abs(lam), 1.0)).max())
+        if gold is not None:
+            la["eig_err_vs_oracle"] = float((np.abs(lam_l - gold[:k]) / np.maximum(np.abs(gold[:k]), 1.0)).max())
+        out["lanczos_baseline"] = la
+
     # ---- end to end through the public API from pinned host buffers
     if not args.no_e2e:
         hr = rows.cpu().pin_memory(); hc = cols.cpu().pin_memory(); hv = vals.cpu().pin_memory()
@@ -433,7 +459,7 @@ def main():
     if rank == 0 and not args.no_serve:
         out["serving"] = run_serving(args, lob, synth, torch)
 
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and not args.no_cpu and wl["cfg"] != "c3":
         ms_cpu, desc = oracle_sample(wl["cfg"], layout)
         out["cpu_baseline"] = dict(desc, value=ms_cpu, unit="ms")
     if rank == 0:

@@ -198,6 +198,11 @@ typedef struct {
   int32_t refine_iterations;/* of which FP64 refinement iterations (MIXED) */
   int32_t spmm_calls;
   int32_t restarts;         /* times P was dropped after an indefinite Gram matrix */
+  int32_t precond_dropped;  /* iteration at which stagnation turned the preconditioner off (the
+                               worst unconverged relative residual of the first k columns had not
+                               halved in 40 iterations; it stays off for the rest of that phase);
+                               0 if it never happened */
+  int32_t reserved;
   double time_ms;           /* wall time of lob_solve */
   double phase_ms[8];       /* device time per phase: spmm, gram, rr, update, precond,
                                residual, orth, guess */

@@ -65,14 +65,15 @@ class SolveOpts(ctypes.Structure):
 
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", _I32), ("refine_iterations", _I32), ("spmm_calls", _I32), ("restarts", _I32),
-                ("time_ms", _D), ("phase_ms", _D * 8), ("spmm_bytes", _D), ("spmm_calls_mode", _I32 * 4),
+                ("precond_dropped", _I32), ("reserved", _I32), ("time_ms", _D), ("phase_ms", _D * 8), ("spmm_bytes", _D), ("spmm_calls_mode", _I32 * 4),
                 ("spmm_ms_mode", _D * 4), ("spmm_bytes_mode", _D * 4), ("residual", _D * 64)]
 
     PHASES = ("spmm", "gram", "rr", "update", "precond", "residual", "orth", "guess")
 
     def to_dict(self, nb):
         return dict(iterations=self.iterations, refine_iterations=self.refine_iterations,
-                    spmm_calls=self.spmm_calls, restarts=self.restarts, time_ms=self.time_ms,
+                    spmm_calls=self.spmm_calls, restarts=self.restarts, precond_dropped=self.precond_dropped,
+                    time_ms=self.time_ms,
                     phase_ms={p: self.phase_ms[i] for i, p in enumerate(self.PHASES)},
                     spmm_bytes=self.spmm_bytes,
                     spmm_by_mode={m: dict(calls=self.spmm_calls_mode[i], ms=self.spmm_ms_mode[i],

@@ -136,16 +136,16 @@ __global__ void k_gram_reduce(int nchunks, int pq, int q, int sym, int tge, cons
 // columns) into shared memory before writing any output, so with a single column block (q <= 16)
 // the output may be columns of A's own rows (used in place by the solver).
 template <bool DF>
-__global__ void __launch_bounds__(256) k_lincomb(int64_t n, int p, const double* __restrict__ A, int lda, int q,
-                                                 const double* __restrict__ C, double* __restrict__ Y, int ldy,
-                                                 const double* __restrict__ D, int ldd) {
+__device__ __forceinline__ void lincomb_body(int64_t n, int p, const double* __restrict__ A, int lda, int q,
+                                             const double* __restrict__ C, double* __restrict__ Y, int ldy,
+                                             const double* __restrict__ D, int ldd, int64_t rb, int cb,
+                                             unsigned char* sm) {
   using R = Ar<DF>;
   using in_t = typename R::in_t;
-  extern __shared__ __align__(16) unsigned char sm[];
   in_t* As = reinterpret_cast<in_t*>(sm);  // [16][p]
   in_t* Cs = As + 16 * p;                  // [p][16]
-  const int64_t r0 = (int64_t)blockIdx.x * 16;
-  const int j0 = blockIdx.y * 16;
+  const int64_t r0 = rb * 16;
+  const int j0 = cb * 16;
   const int tid = threadIdx.x, rl = tid / 16, j = tid % 16;
   for (int idx = tid; idx < 16 * p; idx += 256) {
     const int i = idx / p, a = idx % p;
@@ -163,6 +163,84 @@ __global__ void __launch_bounds__(256) k_lincomb(int64_t n, int p, const double*
   if (D && r < n && j0 + j < q) R::init(acc, D[r * ldd + j0 + j]);  // Y = A C + D
   for (int a = 0; a < p; a++) R::mac(acc, As[rl * p + a], Cs[a * 16 + j]);
   if (r < n && j0 + j < q) Y[r * ldy + j0 + j] = R::out(acc);
+}
+
+template <bool DF>
+__global__ void __launch_bounds__(256) k_lincomb(int64_t n, int p, const double* __restrict__ A, int lda, int q,
+                                                 const double* __restrict__ C, double* __restrict__ Y, int ldy,
+                                                 const double* __restrict__ D, int ldd) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  lincomb_body<DF>(n, p, A, lda, q, C, Y, ldy, D, ldd, blockIdx.x, blockIdx.y, sm);
+}
+
+__device__ __forceinline__ int find_job(const lob_bjob* __restrict__ jobs, int njobs, int64_t b) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].cta_begin <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Batched Y = A C (+ D), q <= 16: job fields A, lda, p, C, q, Y, ldy, D, ldd, n; ceil(n / 16) CTAs.
+template <bool DF>
+__global__ void __launch_bounds__(256) k_lincomb_batch(const lob_bjob* __restrict__ jobs, int njobs) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const lob_bjob& j = jobs[find_job(jobs, njobs, blockIdx.x)];
+  lincomb_body<DF>(j.n, j.p, j.A, j.lda, j.q, j.C, j.Y, j.ldy, j.D, j.ldd, (int64_t)blockIdx.x - j.cta_begin, 0, sm);
+}
+
+// Batched Gram products, one output tile (p, q <= 16 U): job fields A, lda, p, B, ldb, q, n,
+// W0 (chunk partials), x0 (chunks), x1 (sym); x0 CTAs.
+template <bool DF, int U>
+__global__ void __launch_bounds__(256) k_gram_batch(const lob_bjob* __restrict__ jobs, int njobs) {
+  using R = Ar<DF>;
+  using in_t = typename R::in_t;
+  constexpr int TGU = 16 * U;
+  __shared__ in_t As[RB][TGU];
+  __shared__ in_t Bs[RB][TGU];
+  const lob_bjob& j = jobs[find_job(jobs, njobs, blockIdx.x)];
+  const int chunk = (int)((int64_t)blockIdx.x - j.cta_begin);
+  const int64_t rpc = (j.n + j.x0 - 1) / j.x0;
+  const int64_t r0 = (int64_t)chunk * rpc;
+  const int64_t r1 = (r0 + rpc) < j.n ? (r0 + rpc) : j.n;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  typename R::acc_t acc[U][U];
+#pragma unroll
+  for (int a = 0; a < U; a++)
+#pragma unroll
+    for (int b = 0; b < U; b++) R::zero(acc[a][b]);
+  if (j.x1) gram_body<DF, U, true>(r0, r1, j.p, j.A, j.lda, j.q, j.B, j.ldb, 0, 0, As, Bs, acc);
+  else gram_body<DF, U, false>(r0, r1, j.p, j.A, j.lda, j.q, j.B, j.ldb, 0, 0, As, Bs, acc);
+  const int pq = j.p * j.q;
+#pragma unroll
+  for (int u = 0; u < U; u++)
+#pragma unroll
+    for (int v = 0; v < U; v++) {
+      if (j.x1 && u > v) continue;
+      const int a = ty + 16 * u, b = tx + 16 * v;
+      if (a < j.p && b < j.q) j.W0[(int64_t)chunk * pq + (int64_t)a * j.q + b] = R::out(acc[u][v]);
+    }
+}
+
+// Batched fixed-order sum of the chunk partials: job fields W0, x0 (chunks), p, q, x1 (sym), Y;
+// ceil(p q 32 / 256) CTAs.
+__global__ void k_gram_reduce_batch(const lob_bjob* __restrict__ jobs, int njobs) {
+  const lob_bjob& j = jobs[find_job(jobs, njobs, blockIdx.x)];
+  const int64_t lb = (int64_t)blockIdx.x - j.cta_begin;
+  const int e = (int)((lb * blockDim.x + threadIdx.x) / 32), lane = threadIdx.x % 32;
+  const int pq = j.p * j.q;
+  if (e >= pq) return;
+  int src = e;
+  if (j.x1) {
+    const int a = e / j.q, b = e % j.q;
+    if (a / 16 > b / 16) src = b * j.q + a;
+  }
+  double s = 0.0;
+  for (int c = lane; c < j.x0; c += 32) s += j.W0[(int64_t)c * pq + src];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+  if (lane == 0) j.Y[e] = s;
 }
 
 inline int nchunks_for(int64_t n, int tiles) {
@@ -232,6 +310,64 @@ int lob_lincomb_launch(int64_t n, int p, const double* A, int lda, int q, const 
   } else {
     LOB_CUDA(cudaFuncSetAttribute(k_lincomb<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     (k_lincomb<false><<<grid, 256, smem, st>>>(n, p, A, lda, q, C, Y, ldy, D, ldd), LOB_LAUNCHED());
+  }
+  LOB_CUDA(cudaGetLastError());
+  return LOB_OK;
+}
+
+int lob_gram_chunks(int64_t n, int p, int q) {
+  const int e = gram_edge(p, q);
+  return nchunks_for(n, ((p + e - 1) / e) * ((q + e - 1) / e));
+}
+
+int lob_gram_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pqmax, int mode,
+                          lob_bjob* red_host, lob_bjob* red_dev, cudaStream_t st) {
+  if (njobs <= 0) return LOB_OK;
+  if (pqmax > TG) return LOB_ERR_ARG;
+  int64_t ctas = 0, rctas = 0;
+  for (int i = 0; i < njobs; i++) {
+    lob_bjob& j = jobs_host[i];
+    j.cta_begin = ctas;
+    ctas += j.x0;
+    red_host[i] = j;
+    red_host[i].cta_begin = rctas;
+    rctas += ((int64_t)j.p * j.q * 32 + 255) / 256;
+  }
+  LOB_CUDA(cudaMemcpyAsync(jobs_dev, jobs_host, njobs * sizeof(lob_bjob), cudaMemcpyHostToDevice, st));
+  LOB_CUDA(cudaMemcpyAsync(red_dev, red_host, njobs * sizeof(lob_bjob), cudaMemcpyHostToDevice, st));
+  const int U = pqmax <= 16 ? 1 : (pqmax <= 32 ? 2 : 3);
+  if (mode == LOB_SPMM_MIXED) {
+    if (U == 1) (k_gram_batch<true, 1><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
+    else if (U == 2) (k_gram_batch<true, 2><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
+    else (k_gram_batch<true, 3><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
+  } else {
+    if (U == 1) (k_gram_batch<false, 1><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
+    else if (U == 2) (k_gram_batch<false, 2><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
+    else (k_gram_batch<false, 3><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
+  }
+  (k_gram_reduce_batch<<<(unsigned)rctas, 256, 0, st>>>(red_dev, njobs), LOB_LAUNCHED());
+  LOB_CUDA(cudaGetLastError());
+  return LOB_OK;
+}
+
+int lob_lincomb_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pmax, int mode,
+                             cudaStream_t st) {
+  if (njobs <= 0) return LOB_OK;
+  int64_t ctas = 0;
+  for (int i = 0; i < njobs; i++) {
+    if (jobs_host[i].q > 16) return LOB_ERR_ARG;
+    jobs_host[i].cta_begin = ctas;
+    ctas += (jobs_host[i].n + 15) / 16;
+  }
+  if (ctas == 0) return LOB_OK;
+  LOB_CUDA(cudaMemcpyAsync(jobs_dev, jobs_host, njobs * sizeof(lob_bjob), cudaMemcpyHostToDevice, st));
+  const size_t smem = 2ull * 16 * pmax * (mode == LOB_SPMM_MIXED ? sizeof(float2) : sizeof(double));
+  if (mode == LOB_SPMM_MIXED) {
+    LOB_CUDA(cudaFuncSetAttribute(k_lincomb_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    (k_lincomb_batch<true><<<(unsigned)ctas, 256, smem, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
+  } else {
+    LOB_CUDA(cudaFuncSetAttribute(k_lincomb_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    (k_lincomb_batch<false><<<(unsigned)ctas, 256, smem, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
   }
   LOB_CUDA(cudaGetLastError());
   return LOB_OK;

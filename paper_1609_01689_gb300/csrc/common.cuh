@@ -51,11 +51,6 @@ struct lob_tiles {
   int32_t* tchunk = nullptr;   // [ntiles+1] first chunk id of each tile
   uint16_t* cptrs = nullptr;   // [nchunks][2][257] kernel-private: start of each in-tile row in the
                                // chunk's (r, c) order, then of each in-tile column in (c, r) order
-  uint32_t* cpr = nullptr;     // [nnz] kernel-private: the chunk's (c, r) order as (r << 16) | q, q the
-                               // chunk-local index of the entry (cperm with the row attached)
-  uint2* rec = nullptr;        // [nnz] kernel-private (FP32 values): {bits of v32, rc} interleaved
-  uint8_t* cmap = nullptr;     // [ntiles][256] kernel-private: column handled by in-tile slot a in the
-                               // column pass; off-diagonal tiles pair long rows with short columns
 };
 
 // Block-diagonal preconditioner of eq. 11: per block i (rows [i*bp, i*bp + m_i)),
@@ -90,14 +85,30 @@ struct lob_spmm_job {
   const void* vlo;    // DF64 low parts
   const uint16_t* cperm;
   const uint16_t* cptrs;
-  const uint32_t* cpr;
-  const uint2* rec;
-  const uint8_t* cmap;
   const void* Xs;     // staged X of this matrix
   double* Y;
   int32_t ldy, c0, w, pad;
   int64_t n_act;
   int64_t cta_begin;  // first CTA of this job in the grid
+};
+
+// One job of a batched launch (lockstep engine): the fields each kernel uses are listed at the
+// kernel; cta_begin is the job's first CTA in the grid (jobs sorted by it).
+struct lob_bjob {
+  const double* A;
+  const double* B;
+  const double* C;
+  const double* D;
+  double* Y;
+  double* W0;
+  double* W1;
+  const void* P0;
+  const void* P1;
+  int32_t* I0;
+  int64_t n;
+  int32_t p, q, lda, ldb, ldy, ldd, x0, x1, x2, x3;
+  double s0;
+  int64_t cta_begin;
 };
 
 // ---- internal launchers (return LOB_OK or an error code) ----
@@ -147,6 +158,15 @@ int lob_precond_launch(const lob_matrix* m, const double* mu, const double* R, d
 int lob_rr_launch(int m, const double* G, const double* M, double* theta, double* C, int32_t* info, double* work,
                   cudaStream_t st, int chol_only = 0);
 size_t lob_rr_work_doubles(int m);
+// Batched block products for the lockstep engine. The launchers fill cta_begin and copy the
+// host job tables (pinned, left untouched until the stream passes) to the device tables.
+int lob_gram_chunks(int64_t n, int p, int q);
+int lob_gram_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pqmax, int mode,
+                          lob_bjob* red_host, lob_bjob* red_dev, cudaStream_t st);
+int lob_lincomb_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pmax, int mode,
+                             cudaStream_t st);
+// Rayleigh-Ritz / Cholesky-QR problems, one per job and CTA (fields at k_rr_batch).
+int lob_rr_batch_launch(const lob_bjob* jobs_dev, int njobs, int mmax, int df, cudaStream_t st);
 int lob_rr_launch_df(int m, const double* G, const double* M, double* theta, double* C, int32_t* info, double* work,
                      cudaStream_t st, int chol_only = 0);
 size_t lob_gram_work_doubles(int64_t n, int p, int q);

@@ -130,11 +130,10 @@ __device__ void jacobi_blocks(int m, E* A, E* V, double stop_ratio, E* cs_c, E* 
 // SMEM: the matrices live in dynamic shared memory (the address space is a compile-time
 // property, so every access is a shared-memory instruction); otherwise in the global workspace.
 template <bool SMEM>
-__global__ void __launch_bounds__(RR_THREADS) k_rayleigh_ritz(int m, const double* __restrict__ G,
-                                                              const double* __restrict__ Mi, double* __restrict__ theta,
-                                                              double* __restrict__ C, int32_t* __restrict__ info,
-                                                              double* __restrict__ work, int chol_only) {
-  extern __shared__ __align__(16) unsigned char rr_sm[];
+__device__ __forceinline__ void rr_body(int m, const double* __restrict__ G, const double* __restrict__ Mi,
+                                        double* __restrict__ theta, double* __restrict__ C,
+                                        int32_t* __restrict__ info, double* __restrict__ work, int chol_only,
+                                        unsigned char* rr_sm) {
   double* base = SMEM ? reinterpret_cast<double*>(rr_sm) : work;
   double* A = base;          // m x m
   double* L = base + m * m;  // m x m, lower Cholesky factor
@@ -245,12 +244,10 @@ __global__ void __launch_bounds__(RR_THREADS) k_rayleigh_ritz(int m, const doubl
 // reciprocals, rotation angles, convergence sums) is done in FP64. The workspace holds the
 // three m x m matrices as (hi, lo) pairs.
 template <bool SMEM>
-__global__ void __launch_bounds__(RR_THREADS) k_rayleigh_ritz_df(int m, const double* __restrict__ G,
-                                                                 const double* __restrict__ Mi,
-                                                                 double* __restrict__ theta, double* __restrict__ C,
-                                                                 int32_t* __restrict__ info, double* __restrict__ work,
-                                                                 int chol_only) {
-  extern __shared__ __align__(16) unsigned char rr_sm[];
+__device__ __forceinline__ void rr_body_df(int m, const double* __restrict__ G, const double* __restrict__ Mi,
+                                           double* __restrict__ theta, double* __restrict__ C,
+                                           int32_t* __restrict__ info, double* __restrict__ work, int chol_only,
+                                           unsigned char* rr_sm) {
   d2* A = SMEM ? reinterpret_cast<d2*>(rr_sm) : reinterpret_cast<d2*>(work);
   d2* L = A + m * m;
   d2* V = L + m * m;
@@ -372,6 +369,35 @@ __global__ void __launch_bounds__(RR_THREADS) k_rayleigh_ritz_df(int m, const do
   if (tid == 0) *info = 0;
 }
 
+template <bool SMEM>
+__global__ void __launch_bounds__(RR_THREADS) k_rayleigh_ritz(int m, const double* __restrict__ G,
+                                                              const double* __restrict__ Mi, double* __restrict__ theta,
+                                                              double* __restrict__ C, int32_t* __restrict__ info,
+                                                              double* __restrict__ work, int chol_only) {
+  extern __shared__ __align__(16) unsigned char rr_sm[];
+  rr_body<SMEM>(m, G, Mi, theta, C, info, work, chol_only, rr_sm);
+}
+
+template <bool SMEM>
+__global__ void __launch_bounds__(RR_THREADS) k_rayleigh_ritz_df(int m, const double* __restrict__ G,
+                                                                 const double* __restrict__ Mi,
+                                                                 double* __restrict__ theta, double* __restrict__ C,
+                                                                 int32_t* __restrict__ info, double* __restrict__ work,
+                                                                 int chol_only) {
+  extern __shared__ __align__(16) unsigned char rr_sm[];
+  rr_body_df<SMEM>(m, G, Mi, theta, C, info, work, chol_only, rr_sm);
+}
+
+// One Rayleigh-Ritz (or Cholesky-QR) problem per CTA: job j gives m (x0), chol_only (x1), G (A),
+// M (B), theta (Y), C (W0), info (I0) and a global workspace (W1, used when m > 64).
+template <bool DF, bool SMEM>
+__global__ void __launch_bounds__(RR_THREADS) k_rr_batch(const lob_bjob* __restrict__ jobs) {
+  extern __shared__ __align__(16) unsigned char rr_sm[];
+  const lob_bjob& j = jobs[blockIdx.x];
+  if (DF) rr_body_df<SMEM>(j.x0, j.A, j.B, j.Y, j.W0, j.I0, j.W1, j.x1, rr_sm);
+  else rr_body<SMEM>(j.x0, j.A, j.B, j.Y, j.W0, j.I0, j.W1, j.x1, rr_sm);
+}
+
 }  // namespace
 
 // The three m x m matrices live in shared memory when they fit (m <= 64), else in the
@@ -456,4 +482,25 @@ extern "C" int lob_rayleigh_ritz_noalloc(int32_t m, const double* G, const doubl
   cudaStream_t st = (cudaStream_t)stream;
   return mode == LOB_SPMM_MIXED ? lob_rr_launch_df(m, G, M, theta, C, info, work, st)
                                 : lob_rr_launch(m, G, M, theta, C, info, work, st);
+}
+
+int lob_rr_batch_launch(const lob_bjob* jobs_dev, int njobs, int mmax, int df, cudaStream_t st) {
+  if (njobs <= 0) return LOB_OK;
+  if (mmax < 1 || mmax > 192) return LOB_ERR_ARG;
+  const size_t sb = rr_smem_bytes(mmax);
+  const int nt = rr_threads(mmax);
+  if (sb <= RR_SMEM_MAX) {
+    if (df) {
+      LOB_CUDA(cudaFuncSetAttribute(k_rr_batch<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
+      (k_rr_batch<true, true><<<njobs, nt, sb, st>>>(jobs_dev), LOB_LAUNCHED());
+    } else {
+      LOB_CUDA(cudaFuncSetAttribute(k_rr_batch<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
+      (k_rr_batch<false, true><<<njobs, nt, sb, st>>>(jobs_dev), LOB_LAUNCHED());
+    }
+  } else {
+    if (df) (k_rr_batch<true, false><<<njobs, nt, 0, st>>>(jobs_dev), LOB_LAUNCHED());
+    else (k_rr_batch<false, false><<<njobs, nt, 0, st>>>(jobs_dev), LOB_LAUNCHED());
+  }
+  LOB_CUDA(cudaGetLastError());
+  return LOB_OK;
 }

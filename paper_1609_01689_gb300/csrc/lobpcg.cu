@@ -286,6 +286,11 @@ struct lob_task {
   int run_max = 0, max_iter = 0;
   int it = 0, restarts = 0, na = 0, m = 0, iters_total = 0, restarts_total = 0;
   bool haveP = false, retry = false, wretry = false;
+  // stagnation safeguard: the worst unconverged relative residual among the first k columns has
+  // not halved for PC_STALL iterations -> the rest of the run goes without the preconditioner
+  double best_res = 0.0;
+  int best_it = 0;
+  bool pc_dropped = false;
   // the SpMM the task waits for: Y = H X on contiguous n x ncol blocks, then Y copied to post
   const double* sp_x = nullptr;
   double* sp_y = nullptr;
@@ -613,6 +618,9 @@ int lob_task::step() {
         retry = false;
         it = 0;
         restarts = 0;
+        best_res = 1e300;
+        best_it = 0;
+        pc_dropped = false;
         pc = PC_RUN_SPMM0;
         continue;
       }
@@ -654,8 +662,18 @@ int lob_task::step() {
           if (!(hb->relres[j] <= run_tol)) hb->map[na++] = j;
         }
         if (conv) { run_status = LOB_OK; pc = PC_RUN_END; continue; }
+        {
+          double worst = 0.0;
+          for (int j = 0; j < k; j++)
+            if (!(hb->relres[j] <= run_tol)) worst = fmax(worst, hb->relres[j]);
+          if (worst < 0.5 * best_res) { best_res = worst; best_it = it; }
+          if (!pc_dropped && o.precond && it - best_it >= 40) {
+            pc_dropped = true;
+            if (!stats.precond_dropped) stats.precond_dropped = iters_total + it;
+          }
+        }
         // W = T^{-1} R (step 6) with the rules of Section 4.3
-        const bool pc_on = o.precond && M->P.bp > 0 && it > 3 && hb->relres[0] <= 1e-1;
+        const bool pc_on = o.precond && !pc_dropped && M->P.bp > 0 && it > 3 && hb->relres[0] <= 1e-1;
         LOB_TRY(stage(skey(1, na, haveP ? 1 : 0, pc_on ? 1 : 0), [&]() -> int {
           {
             Timer t(clk(), st, ph(PH_PRECOND));

@@ -120,13 +120,11 @@ struct Cfg {
   static constexpr size_t XV = sizeof(T) * LOB_TILE * NB;
   static constexpr size_t XI = 0;
   static constexpr size_t XJ = XI + XV;               // 2 buffers
-  // MIXED: 2 x CH records {value bits, rc}; FP64: 2 x CH rc then 2 x CH values
-  static constexpr size_t RC = XJ + 2 * XV;
-  static constexpr size_t VV = RC + 2 * 4 * CH;
-  static constexpr size_t CP = MIXED ? RC + 2 * 8 * CH : VV + 2 * sizeof(T) * CH;  // 2 x CH uint32 (r << 16) | q
-  static constexpr size_t PT = CP + 2 * 4 * CH;       // 2 x PTRS uint16
-  static constexpr size_t CM = PT + 2 * 2 * PTRS;     // 2 x 256 uint8 column map
-  static constexpr size_t BYTES = CM + 2 * LOB_TILE;
+  static constexpr size_t RC = XJ + 2 * XV;           // 2 x CH uint32
+  static constexpr size_t VV = RC + 2 * 4 * CH;       // 2 x CH values
+  static constexpr size_t PM = VV + 2 * sizeof(T) * CH;    // 2 x (CH + 8) uint16
+  static constexpr size_t PT = PM + 2 * 2 * (CH + 8);      // 2 x PTRS uint16
+  static constexpr size_t BYTES = PT + 2 * 2 * PTRS;
   // one CTA per SM: 1,024 threads, one in-tile row and column per lane group at NB = 16 (a
   // variant with two 512-thread CTAs per SM and 2,048-entry chunks measured 15% slower)
   static constexpr int MINB = 1;
@@ -154,8 +152,7 @@ template <bool MIXED, int NB>
 __global__ void __launch_bounds__(Cfg<MIXED, NB>::THREADS, Cfg<MIXED, NB>::MINB)
     k_spmm4(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ tcol, const int64_t* __restrict__ tptr,
             const int32_t* __restrict__ tchunk, const uint32_t* __restrict__ rc,
-            const typename Elt<MIXED>::T* __restrict__ vals, const uint32_t* __restrict__ cpr,
-            const uint2* __restrict__ rec, const uint8_t* __restrict__ cmap,
+            const typename Elt<MIXED>::T* __restrict__ vals, const uint16_t* __restrict__ cperm,
             const uint16_t* __restrict__ cptrs, const typename Elt<MIXED>::T* __restrict__ Xs,
             double* __restrict__ Y, int ldy, int c0, int w, int64_t n_act, const lob_spmm_job* __restrict__ jobs,
             int njobs) {
@@ -168,12 +165,10 @@ __global__ void __launch_bounds__(Cfg<MIXED, NB>::THREADS, Cfg<MIXED, NB>::MINB)
   extern __shared__ __align__(16) unsigned char sm[];
   T* XI = reinterpret_cast<T*>(sm + C::XI);
   T* XJb = reinterpret_cast<T*>(sm + C::XJ);
-  uint32_t* RCb = reinterpret_cast<uint32_t*>(sm + C::RC);  // FP64: rc
-  uint2* RECb = reinterpret_cast<uint2*>(sm + C::RC);       // MIXED: records
-  T* VVb = reinterpret_cast<T*>(sm + C::VV);                // FP64: values
-  uint32_t* CPb = reinterpret_cast<uint32_t*>(sm + C::CP);
+  uint32_t* RCb = reinterpret_cast<uint32_t*>(sm + C::RC);
+  T* VVb = reinterpret_cast<T*>(sm + C::VV);
+  uint16_t* PMb = reinterpret_cast<uint16_t*>(sm + C::PM);
   uint16_t* PTb = reinterpret_cast<uint16_t*>(sm + C::PT);
-  uint8_t* CMb = reinterpret_cast<uint8_t*>(sm + C::CM);
 
   int64_t I = blockIdx.x;
   if (jobs) {  // batched launch: find this CTA's matrix and tile row
@@ -184,7 +179,7 @@ __global__ void __launch_bounds__(Cfg<MIXED, NB>::THREADS, Cfg<MIXED, NB>::MINB)
     }
     const lob_spmm_job& jb = jobs[lo];
     rowptr = jb.rowptr; tcol = jb.tcol; tptr = jb.tptr; tchunk = jb.tchunk; rc = jb.rc;
-    vals = reinterpret_cast<const T*>(jb.vals); cpr = jb.cpr; rec = jb.rec; cmap = jb.cmap; cptrs = jb.cptrs;
+    vals = reinterpret_cast<const T*>(jb.vals); cperm = jb.cperm; cptrs = jb.cptrs;
     Xs = reinterpret_cast<const T*>(jb.Xs); Y = jb.Y; ldy = jb.ldy; c0 = jb.c0; w = jb.w; n_act = jb.n_act;
     I = (int64_t)blockIdx.x - jb.cta_begin;
   }
@@ -208,25 +203,20 @@ __global__ void __launch_bounds__(Cfg<MIXED, NB>::THREADS, Cfg<MIXED, NB>::MINB)
     const int64_t base = tptr[t] + k * CH;
     const int64_t rem = tptr[t + 1] - base;
     const int cnt = (int)(rem < CH ? rem : CH);
-    if (MIXED) {
-      uint2* RECs = RECb + buf * CH;
-      for (int i = tid; i < cnt; i += THREADS) cp_async8(&RECs[i], &rec[base + i]);
-    } else {
-      uint32_t* RCs = RCb + buf * CH;
-      T* VVs = VVb + buf * CH;
-      for (int i = tid; i < cnt; i += THREADS) {
-        cp_async4(&RCs[i], &rc[base + i]);
-        cp_async8(&VVs[i], &vals[base + i]);
-      }
+    uint32_t* RCs = RCb + buf * CH;
+    T* VVs = VVb + buf * CH;
+    for (int i = tid; i < cnt; i += THREADS) {
+      cp_async4(&RCs[i], &rc[base + i]);
+      if (MIXED) cp_async4(&VVs[i], &vals[base + i]); else cp_async8(&VVs[i], &vals[base + i]);
     }
-    uint32_t* CPs = CPb + buf * CH;
-    for (int i = tid; i < cnt; i += THREADS) cp_async4(&CPs[i], &cpr[base + i]);
+    uint32_t* PM32 = reinterpret_cast<uint32_t*>(PMb + buf * (CH + 8));
+    const int64_t wb = base & ~(int64_t)1;
+    const int nwords = (int)((base + cnt - wb + 1) / 2);
+    const uint32_t* src32 = reinterpret_cast<const uint32_t*>(cperm + wb);
+    for (int i = tid; i < nwords; i += THREADS) cp_async4(&PM32[i], &src32[i]);
     uint32_t* PT32 = reinterpret_cast<uint32_t*>(PTb + buf * C::PTRS);
     const uint32_t* srcp = reinterpret_cast<const uint32_t*>(cptrs + (int64_t)(tchunk[t] + k) * C::PTRS);
     for (int i = tid; i < C::PTRS / 2; i += THREADS) cp_async4(&PT32[i], &srcp[i]);
-    uint32_t* CM32 = reinterpret_cast<uint32_t*>(CMb + buf * LOB_TILE);
-    const uint32_t* srcm = reinterpret_cast<const uint32_t*>(cmap + t * LOB_TILE);
-    for (int i = tid; i < LOB_TILE / 4; i += THREADS) cp_async4(&CM32[i], &srcm[i]);
     cp_async_commit();
   };
 
@@ -254,12 +244,10 @@ __global__ void __launch_bounds__(Cfg<MIXED, NB>::THREADS, Cfg<MIXED, NB>::MINB)
     if (tn < t1) { issue(tn, kn, buf ^ 1, tln & 1); cp_async_wait_1(); } else { cp_async_wait_all(); }
     __syncthreads();
     const uint32_t* RCs = RCb + buf * CH;
-    const uint2* RECs = RECb + buf * CH;
     const T* VVs = VVb + buf * CH;
-    const uint32_t* CP = CPb + buf * CH;
+    const uint16_t* PM = PMb + buf * (CH + 8) + (int)((tptr[t] + k * CH) & 1);
     const uint16_t* PR = PTb + buf * C::PTRS;
     const uint16_t* PC = PR + (LOB_TILE + 1);
-    const uint8_t* CM = CMb + buf * LOB_TILE;
     const T* xj = diag ? XI : XJb + (tl & 1) * XN;
 #pragma unroll
     for (int a = 0; a < RPG; a++) {
@@ -270,35 +258,23 @@ __global__ void __launch_bounds__(Cfg<MIXED, NB>::THREADS, Cfg<MIXED, NB>::MINB)
         V acc = acc_t[a];
 #pragma unroll 4
         for (int i = s; i < e; i++) {
-          T v;
-          int c;
-          if (MIXED) {
-            const uint2 rv = RECs[i];
-            v = (T)__uint_as_float(rv.x);
-            c = (int)(rv.y & 0xFFu);
-          } else {
-            v = VVs[i];
-            c = (int)(RCs[i] & 0xFFu);
-          }
+          const int c = (int)(RCs[i] & 0xFFFFu);
           const V x = *reinterpret_cast<const V*>(&xj[c * NB + gl * VW]);
-          fma_v(acc, v, x);
+          fma_v(acc, VVs[i], x);
         }
         acc_t[a] = acc;
       }
-      // column pass over the column this slot handles on this tile
+      // column pass
       {
-        const int col = CM[idx];
-        const int s = PC[col], e = PC[col + 1];
+        const int s = PC[idx], e = PC[idx + 1];
         V acc = acc_c[a];
 #pragma unroll 4
         for (int i = s; i < e; i++) {
-          const uint32_t cp = CP[i];
-          const int q = (int)(cp & (CH - 1));  // chunk-local index (the mask keeps a stray value inside)
-          const int r = (int)((cp >> 16) & 0xFFu);
-          if (diag && r == col) continue;  // the diagonal entry is applied once (row pass)
-          const T v = MIXED ? (T)__uint_as_float(RECs[q].x) : VVs[q];
+          const int q = PM[i] & (CH - 1);  // a chunk-local index (mask keeps a stray value inside the chunk)
+          const int r = (int)(RCs[q] >> 16);
+          if (diag && r == idx) continue;  // the diagonal entry is applied once (row pass)
           const V xi = *reinterpret_cast<const V*>(&XI[r * NB + gl * VW]);
-          fma_v(acc, v, xi);
+          fma_v(acc, VVs[q], xi);
         }
         acc_c[a] = acc;
       }
@@ -307,20 +283,19 @@ __global__ void __launch_bounds__(Cfg<MIXED, NB>::THREADS, Cfg<MIXED, NB>::MINB)
 #pragma unroll
       for (int a = 0; a < RPG; a++) {
         const int idx = g + a * NG;
-        const int col = CM[idx];
         const T* ta = reinterpret_cast<const T*>(&acc_t[a]);
         const T* ca = reinterpret_cast<const T*>(&acc_c[a]);
 #pragma unroll
         for (int q = 0; q < VW; q++) {
           if (MIXED) {
             df_add(rh[a][q], rl[a][q], (float)ta[q], 0.f);
-            if (diag) df_add(rh[a][q], rl[a][q], (float)ca[q], 0.f);  // col == idx on a diagonal tile
+            if (diag) df_add(rh[a][q], rl[a][q], (float)ca[q], 0.f);
           } else {
             rd[a][q] += (double)ta[q];
             if (diag) rd[a][q] += (double)ca[q];
           }
           const int kk = gl * VW + q;
-          const int64_t gr = J * LOB_TILE + col;
+          const int64_t gr = J * LOB_TILE + idx;
           if (!diag && kk < w && gr < n_act) atomic_out(&Y[gr * ldy + c0 + kk], ca[q]);
         }
         zero_v(acc_t[a]);
@@ -589,8 +564,8 @@ int launch(const lob_matrix* m, const double* X, double* Y, int nb, int64_t n_ac
      LOB_LAUNCHED());
     (kern<<<(unsigned)nt_act, C::THREADS, C::BYTES, st>>>(
          TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rc,
-         MIXED ? (const T*)(const void*)TS.v32 : (const T*)(const void*)TS.v64, TS.cpr, TS.rec, TS.cmap, TS.cptrs, Xs,
-         Y, nb, c0, w, n_act, nullptr, 0),
+         MIXED ? (const T*)(const void*)TS.v32 : (const T*)(const void*)TS.v64, TS.cperm, TS.cptrs, Xs, Y, nb, c0, w,
+         n_act, nullptr, 0),
      LOB_LAUNCHED());
   }
   LOB_CUDA(cudaGetLastError());
@@ -624,7 +599,6 @@ int batch_class(const lob_matrix* const* ms, const double* const* X, double* con
     jb.rowptr = TS.rowptr; jb.tcol = TS.tcol; jb.tptr = TS.tptr; jb.tchunk = TS.tchunk; jb.rc = TS.rc;
     jb.vals = MODE == LOB_SPMM_FP64 ? (const void*)TS.v64 : (const void*)TS.v32;
     jb.vlo = TS.v32lo; jb.cperm = TS.cperm; jb.cptrs = TS.cptrs; jb.Xs = m->xs; jb.Y = Y[j];
-    jb.cpr = TS.cpr; jb.rec = TS.rec; jb.cmap = TS.cmap;
     jb.ldy = ncol[j]; jb.c0 = 0; jb.w = ncol[j]; jb.pad = 0; jb.n_act = na; jb.cta_begin = ctas;
     jobs_host[njob++] = jb;
     ctas += nt_act;
@@ -642,8 +616,8 @@ int batch_class(const lob_matrix* const* ms, const double* const* X, double* con
     using C = Cfg<MX, NB>;
     LOB_CUDA(cudaFuncSetAttribute(k_spmm4<MX, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES));
     (k_spmm4<MX, NB><<<(unsigned)ctas, C::THREADS, C::BYTES, st>>>(nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                                   nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                                   0, 0, 0, 0, jobs_dev, njob), LOB_LAUNCHED());
+                                                                   nullptr, nullptr, nullptr, nullptr, 0, 0, 0, 0,
+                                                                   jobs_dev, njob), LOB_LAUNCHED());
   }
   LOB_CUDA(cudaGetLastError());
   return LOB_OK;

@@ -150,58 +150,6 @@ __global__ void k_chunk_ptrs(int64_t ntiles, const int64_t* __restrict__ tptr, c
   }
 }
 
-// (r << 16) | q for position k of the sorted column-order permutation: q = perm[k] is the
-// chunk-local index of the entry, r its in-tile row.
-__global__ void k_perm_pack(int64_t nnz, const int32_t* __restrict__ flag, const int32_t* __restrict__ tid,
-                            const int64_t* __restrict__ tptr, const uint32_t* __restrict__ rc,
-                            const uint16_t* __restrict__ perm, uint32_t* __restrict__ cpr) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nnz) return;
-  const int64_t t0 = tptr[tid[k] + flag[k] - 1];
-  const int64_t base = t0 + ((k - t0) / LOB_PERM_CHUNK) * LOB_PERM_CHUNK;
-  const uint32_t q = perm[k];
-  cpr[k] = ((rc[base + q] >> 16) << 16) | q;
-}
-
-// {bits of v32, rc} per entry.
-__global__ void k_make_rec(int64_t nnz, const float* __restrict__ v32, const uint32_t* __restrict__ rc,
-                           uint2* __restrict__ rec) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nnz) return;
-  rec[k] = make_uint2(__float_as_uint(v32[k]), rc[k]);
-}
-
-// One CTA per tile: the column each in-tile slot handles in the SpMM's column pass. Slot a owns
-// row a for the whole tile row; on an off-diagonal tile it takes the column whose length ranks
-// opposite to its row's (the longest row with the shortest column), so the row-plus-column work
-// per slot is even between barriers. Diagonal tiles keep column a (its partial joins row a).
-__global__ void k_tile_cmap(int64_t ntiles, const int64_t* __restrict__ tptr, const int32_t* __restrict__ tcol,
-                            const int32_t* __restrict__ trow, const uint32_t* __restrict__ rc,
-                            uint8_t* __restrict__ cmap) {
-  __shared__ int rl[LOB_TILE], cl[LOB_TILE], col_of_rank[LOB_TILE];
-  const int64_t t = blockIdx.x;
-  const int a = threadIdx.x;  // blockDim.x == LOB_TILE
-  uint8_t* out = cmap + t * LOB_TILE;
-  if (tcol[t] == trow[t]) { out[a] = (uint8_t)a; return; }
-  rl[a] = 0;
-  cl[a] = 0;
-  __syncthreads();
-  for (int64_t k = tptr[t] + a; k < tptr[t + 1]; k += LOB_TILE) {
-    const uint32_t p = rc[k];
-    atomicAdd(&rl[p >> 16], 1);
-    atomicAdd(&cl[p & 0xFFu], 1);
-  }
-  __syncthreads();
-  int rr = 0, rcn = 0;
-  for (int u = 0; u < LOB_TILE; u++) {
-    rr += (rl[u] > rl[a]) || (rl[u] == rl[a] && u < a);   // rank of row a, longest first
-    rcn += (cl[u] < cl[a]) || (cl[u] == cl[a] && u < a);  // rank of column a, shortest first
-  }
-  col_of_rank[rcn] = a;
-  __syncthreads();
-  out[a] = (uint8_t)col_of_rank[rr];
-}
-
 // Low parts of the values: v64 - v32, rounded to FP32 (so v32 + v32lo carries ~48 bits).
 __global__ void k_value_lo(int64_t nnz, const double* __restrict__ v64, const float* __restrict__ v32,
                            float* __restrict__ lo) {
@@ -227,7 +175,6 @@ void lob_free_tiles(lob_tiles* T) {
   cudaFree(T->rowptr); cudaFree(T->tcol); cudaFree(T->trow); cudaFree(T->tptr);
   cudaFree(T->rc); cudaFree(T->v64); cudaFree(T->v32); cudaFree(T->cperm);
   cudaFree(T->tchunk); cudaFree(T->cptrs); cudaFree(T->v32lo);
-  cudaFree(T->cpr); cudaFree(T->rec); cudaFree(T->cmap);
   *T = lob_tiles();
 }
 
@@ -323,16 +270,7 @@ int lob_build_tiles(const lob_coo* H, int values, cudaStream_t st, lob_tiles* T,
     size_t tpb = tp > tb ? tp : tb;
     LOB_CUDA(cub::DeviceRadixSort::SortPairs(tpp, tpb, pk, pv, (int)nnz, 0, ebits, st));
     LOB_CUDA(cudaMemcpyAsync(R.cperm, pv.Current(), nnz * 2, cudaMemcpyDeviceToDevice, st));
-    if (cudaMalloc(&R.cpr, (nnz + 8) * 4) != cudaSuccess) { cudaGetLastError(); lob_free_tiles(&R); return LOB_ERR_NOMEM; }
-    (k_perm_pack<<<nblocks(nnz, bs), bs, 0, st>>>(nnz, (const int32_t*)flag.p, (const int32_t*)tid.p, R.tptr, R.rc,
-                                                 R.cperm, R.cpr), LOB_LAUNCHED());
     LOB_CUDA(cudaStreamSynchronize(st));
-  }
-  if (cudaMalloc(&R.cmap, (size_t)ntiles * LOB_TILE) != cudaSuccess) { cudaGetLastError(); lob_free_tiles(&R); return LOB_ERR_NOMEM; }
-  (k_tile_cmap<<<(unsigned)ntiles, LOB_TILE, 0, st>>>(ntiles, R.tptr, R.tcol, R.trow, R.rc, R.cmap), LOB_LAUNCHED());
-  if (R.v32) {
-    if (cudaMalloc(&R.rec, (nnz + 8) * 8) != cudaSuccess) { cudaGetLastError(); lob_free_tiles(&R); return LOB_ERR_NOMEM; }
-    (k_make_rec<<<nblocks(nnz, bs), bs, 0, st>>>(nnz, R.v32, R.rc, R.rec), LOB_LAUNCHED());
   }
   // per-chunk row and column start pointers (kernel-private, derived from the canonical store)
   {
