@@ -208,8 +208,8 @@ def run_serving(args, lob, synth, torch):
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
 
-    def serve(sample, arrivals, mode="mixed", batched=True):
-        srv = lob.Server(budget_bytes=60 << 30, max_active=64, batched=batched)
+    def serve(sample, arrivals, mode="mixed", engine="lockstep"):
+        srv = lob.Server(budget_bytes=60 << 30, max_active=args.serve_slots, engine=engine)
         ids = {}
         res = {}
         i = 0
@@ -276,6 +276,71 @@ def run_serving(args, lob, synth, torch):
     return serving
 
 
+def run_batched_small(args, lob, synth, torch):
+    """The batched small-instance workload: 4,096 matrices, n uniform in [256, 4,096], ~40
+    nonzeros per row, k = 4, nb = 8, FP32-value SpMM with double-float block products and
+    Rayleigh-Ritz, tol 1e-8, random start, no preconditioner -- all admitted at once to the
+    lockstep engine, one iteration of every instance per round. Also: a sample solved one at a
+    time by lob_solve (same settings, and FP64) for the speedup and the eigenvalue agreement."""
+    rng = np.random.default_rng(4096)
+    count = args.small_count
+    ns = rng.integers(256, 4097, count)
+    mats = []
+    t0 = time.perf_counter()
+    for i, n in enumerate(ns):
+        L = synth.layout(int(n), synth.interp_levels(int(n)), 40, 50000 + i)
+        r, c, v = synth.generate_device(L)
+        mats.append(lob.Matrix(int(n), r, c, v))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    srv = lob.Server(budget_bytes=60 << 30, max_active=count, engine="lockstep")
+    k0 = lob.kernel_launches()
+    t0 = time.perf_counter()
+    ids = [srv.submit(M, 4, 8, 1e-8, mode="mixed", precond=False, seed=1 + i) for i, M in enumerate(mats)]
+    res = {}
+    rounds = 0
+    while len(res) < count:
+        nd = srv.progress(wait=True)
+        rounds += 1
+        if nd:
+            for i in ids:
+                if i not in res:
+                    r = srv.poll(i)
+                    if r["state"] == lob.REQ_DONE:
+                        res[i] = r
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = lob.kernel_launches() - k0
+    st = srv.stats()
+    srv.close()
+    its = np.array([res[i]["stats"]["iterations"] for i in ids])
+    ok = sum(1 for i in ids if res[i]["rc"] == lob.LOB_OK)
+    # sample one at a time: lob_solve mixed, and FP64 for the accuracy reference
+    samp = list(range(0, count, max(1, count // args.small_sample)))[:args.small_sample]
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for i in samp:
+        mats[i].solve(4, 8, 1e-8, mode="mixed", precond=False, seed=1 + i, stats=False)
+    torch.cuda.synchronize()
+    seq = (time.perf_counter() - t1) / len(samp)
+    diff = 0.0
+    for i in samp:
+        lam64, _, _, _ = mats[i].solve(4, 8, 1e-8, mode="fp64", precond=False, seed=1 + i, stats=False)
+        lb = res[ids[i]]["lam"]
+        diff = max(diff, float((np.abs(lb - lam64) / np.maximum(np.abs(lam64), 1.0)).max()))
+    for M in mats:
+        M.close()
+    return {"workload": f"{count} matrices, n uniform [256, 4096], ~40 nnz/row, k=4, nb=8, mixed, tol 1e-8, "
+                        f"no preconditioner, lockstep engine (all admitted at once)",
+            "wall_s": wall, "instances_per_s": count / wall, "converged": ok, "rounds": rounds,
+            "iterations_mean": float(its.mean()), "iterations_max": int(its.max()),
+            "kernel_launches": int(launches), "spmm_launches": int(st["spmm_launches"]),
+            "spmm_products": int(st["spmm_products"]), "matrix_build_s": build_s,
+            "sequential_lob_solve_s_per_instance": seq,
+            "speedup_batched_over_sequential": seq * count / wall,
+            "max_eig_rel_diff_vs_fp64_single": diff, "sample": len(samp)}
+
+
 def run_reference(args, wl):
     import synth
     rank = int(os.environ.get("RANK", "0"))
@@ -313,6 +378,10 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-compare", type=int, default=100)
+    ap.add_argument("--serve-slots", type=int, default=256)
+    ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--small-count", type=int, default=4096)
+    ap.add_argument("--small-sample", type=int, default=64)
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -458,6 +527,8 @@ def main():
 
     if rank == 0 and not args.no_serve:
         out["serving"] = run_serving(args, lob, synth, torch)
+    if rank == 0 and not args.no_small:
+        out["batched_small"] = run_batched_small(args, lob, synth, torch)
 
     if rank == 0 and not args.no_cpu and wl["cfg"] != "c3":
         ms_cpu, desc = oracle_sample(wl["cfg"], layout)

@@ -246,32 +246,41 @@ int lob_lanczos(lob_matrix* H, int32_t k, double tol, int32_t max_steps, int32_t
 /* ---- serving: continuous batching of solves ----
  *
  * A server keeps the LOBPCG state of every admitted solve resident on the device (S = [X W P],
- * H S, R, the Ritz values) and advances all of them together: each call of
- * lob_server_progress() moves every admitted solve to its next host decision, and the SpMMs
- * that several solves need at the same time go out as shared launches (one per arithmetic and
- * vector width, lob_spmm_batch). Each solve has its own CUDA stream, so the small dense work of
- * different solves overlaps on the device. Requests that arrive while others run are admitted
- * between progress calls as soon as a slot and enough of the device-memory budget are free
- * (any queued request that fits, in arrival order).
+ * H S, R, the Ritz values) and advances all of them together. With the lockstep engine (the
+ * default) each call of lob_server_progress() runs one iteration of every admitted solve, every
+ * kernel of it as one launch over all solves (SpMMs: one launch per arithmetic and vector width,
+ * lob_spmm_batch). With the stream engines each solve has its own CUDA stream and each call moves
+ * every solve to its next host decision. Requests that arrive while others run are admitted
+ * between progress calls as soon as a slot and enough of the device-memory budget are free (any
+ * queued request that fits, in arrival order).
  *
  * A solve gives the same result in the mix as alone (lob_solve) up to the rounding of the
  * SpMM's atomic column sums, which are not ordered in either case. */
 
 /* Y_j = H_j X_j for njobs distinct matrices in shared launches (one kernel per arithmetic and
  * vector width; each CTA finds its matrix and tile row in a job table). X[j], Y[j]: device,
- * n_j x nb[j] row-major, 1 <= nb[j] <= 16; mode[j]: LOB_SPMM_*. Runs on `stream` and returns
- * when the products are complete. Errors: LOB_ERR_ARG (null pointers, nb out of range, a matrix
+ * n_j x nb[j] row-major, 1 <= nb[j] <= 16; mode[j]: LOB_SPMM_*. n_act (NULL: n_j) restricts job j
+ * to the leading n_act[j] x n_act[j] block of H_j: rows of X_j at or beyond n_act[j] are never read
+ * and rows of Y_j below n_act[j] get that block's product. Runs on `stream` and returns when the
+ * products are complete. Errors: LOB_ERR_ARG (null pointers, nb or n_act out of range, a matrix
  * listed twice, missing value copy), LOB_ERR_NOMEM, LOB_ERR_CUDA. */
 int lob_spmm_batch(int32_t njobs, lob_matrix* const* H, const double* const* X, double* const* Y,
-                   const int32_t* nb, const int32_t* mode, void* stream);
+                   const int32_t* nb, const int32_t* mode, const int64_t* n_act, void* stream);
 
 typedef struct lob_server lob_server; /* opaque */
+
+#define LOB_ENGINE_LOCKSTEP 0  /* every admitted solve advances one iteration per round; each kernel of
+                                  the round is one launch for all solves (job tables); three host
+                                  synchronisations per round whatever the number of solves */
+#define LOB_ENGINE_SHARED 1    /* one CUDA stream per solve, stages replayed as CUDA graphs, SpMMs of
+                                  solves that reach them together share launches */
+#define LOB_ENGINE_STREAMS 2   /* one CUDA stream per solve, one SpMM launch per solve */
 
 typedef struct {
   uint64_t budget_bytes;   /* device memory the admitted solves may hold (matrix + solver state);
                               0 = 60 GiB */
   int32_t max_active;      /* admitted solves at once; 0 = 64 */
-  int32_t batch_spmm;      /* 1 (default when 0): shared SpMM launches; -1: one launch per solve */
+  int32_t engine;          /* LOB_ENGINE_* (0 = lockstep) */
 } lob_server_opts;
 
 typedef struct {
@@ -308,9 +317,10 @@ int lob_server_create(const lob_server_opts* o, lob_server** out);
 /* Queue a solve; *id identifies it. The request is copied. Errors: LOB_ERR_ARG (bad sizes, or a
  * solve that could never fit the budget). */
 int lob_server_submit(lob_server* s, const lob_request* r, int64_t* id);
-/* Admit what fits, then advance every admitted solve until it waits on the device, sharing the
- * SpMM launches. wait != 0: if no solve could move, block until the oldest pending device step
- * completes. *n_done (may be NULL) gets the number of solves finished by this call. */
+/* Admit what fits, then advance the admitted solves: lockstep, one iteration of all of them
+ * (blocking); stream engines, each until it waits on the device (wait != 0: if no solve could
+ * move, block until the oldest pending device step completes). *n_done (may be NULL) gets the
+ * number of solves finished by this call. */
 int lob_server_progress(lob_server* s, int32_t wait, int32_t* n_done);
 /* State of a request; once DONE has been reported the record is released (the id becomes
  * unknown: LOB_ERR_ARG). */

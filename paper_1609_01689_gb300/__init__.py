@@ -87,7 +87,11 @@ class LanczosStats(ctypes.Structure):
 
 
 class ServerOpts(ctypes.Structure):
-    _fields_ = [("budget_bytes", ctypes.c_uint64), ("max_active", _I32), ("batch_spmm", _I32)]
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("max_active", _I32), ("engine", _I32)]
+
+
+ENGINE_LOCKSTEP, ENGINE_SHARED, ENGINE_STREAMS = 0, 1, 2
+_ENGINES = {"lockstep": 0, "shared": 1, "streams": 2, 0: 0, 1: 1, 2: 2}
 
 
 class Request(ctypes.Structure):
@@ -132,7 +136,7 @@ def _load():
     L.lob_rayleigh_ritz_noalloc.argtypes = [_I32, _P, _P, _P, _P, _P, _I32, _P]
     L.lob_rayleigh_ritz_noalloc.restype = ctypes.c_int
     L.lob_solve.argtypes = [_P, _I32, _I32, _D, _P, ctypes.POINTER(SolveOpts), _P, _P, ctypes.POINTER(Stats)]
-    L.lob_spmm_batch.argtypes = [_I32, _P, _P, _P, _P, _P, _P]
+    L.lob_spmm_batch.argtypes = [_I32, _P, _P, _P, _P, _P, _P, _P]
     L.lob_lanczos.argtypes = [_P, _I32, _D, _I32, _I32, ctypes.c_uint64, _P, _P, ctypes.POINTER(LanczosStats), _P]
     L.lob_server_create.argtypes = [ctypes.POINTER(ServerOpts), ctypes.POINTER(_P)]
     L.lob_server_submit.argtypes = [_P, ctypes.POINTER(Request), ctypes.POINTER(_I64)]
@@ -365,8 +369,9 @@ def rayleigh_ritz_noalloc(G, M, mode="fp64", theta=None, C=None, info=None):
     return theta, C
 
 
-def spmm_batch(mats, Xs, modes="fp64"):
-    """[H_j X_j] for distinct matrices in shared launches (lob_spmm_batch)."""
+def spmm_batch(mats, Xs, modes="fp64", n_act=None):
+    """[H_j X_j] for distinct matrices in shared launches (lob_spmm_batch); n_act restricts each
+    product to the leading n_act[j] block."""
     torch = _torch()
     nj = len(mats)
     if isinstance(modes, (str, int)):
@@ -378,7 +383,8 @@ def spmm_batch(mats, Xs, modes="fp64"):
     Yp = (_P * nj)(*[y.data_ptr() for y in Ys])
     nb = (_I32 * nj)(*[1 if x.dim() == 1 else x.shape[1] for x in Xs])
     md = (_I32 * nj)(*[_MODES[m] for m in modes])
-    _check(lib().lob_spmm_batch(nj, H, Xp, Yp, nb, md, _stream()), "lob_spmm_batch")
+    na = (_I64 * nj)(*n_act) if n_act is not None else None
+    _check(lib().lob_spmm_batch(nj, H, Xp, Yp, nb, md, na, _stream()), "lob_spmm_batch")
     return Ys
 
 
@@ -387,8 +393,8 @@ class Server:
     admits what fits the device-memory budget and advances every admitted solve, sharing the
     SpMM launches; poll() returns a finished solve's eigenvalues, stats and timestamps."""
 
-    def __init__(self, budget_bytes=0, max_active=0, batched=True):
-        o = ServerOpts(budget_bytes, max_active, 1 if batched else -1)
+    def __init__(self, budget_bytes=0, max_active=0, engine="lockstep"):
+        o = ServerOpts(budget_bytes, max_active, _ENGINES[engine])
         h = _P()
         _check(lib().lob_server_create(ctypes.byref(o), ctypes.byref(h)), "lob_server_create")
         self._h = h

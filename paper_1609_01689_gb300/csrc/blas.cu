@@ -135,25 +135,26 @@ __global__ void k_gram_reduce(int nchunks, int pq, int q, int sym, int tge, cons
 // Y = A C (+ D): 16 rows x 16 output columns per CTA. The CTA loads its rows of A (all p
 // columns) into shared memory before writing any output, so with a single column block (q <= 16)
 // the output may be columns of A's own rows (used in place by the solver).
-template <bool DF>
+template <bool DF, int QT>
 __device__ __forceinline__ void lincomb_body(int64_t n, int p, const double* __restrict__ A, int lda, int q,
                                              const double* __restrict__ C, double* __restrict__ Y, int ldy,
                                              const double* __restrict__ D, int ldd, int64_t rb, int cb,
                                              unsigned char* sm) {
   using R = Ar<DF>;
   using in_t = typename R::in_t;
-  in_t* As = reinterpret_cast<in_t*>(sm);  // [16][p]
-  in_t* Cs = As + 16 * p;                  // [p][16]
-  const int64_t r0 = rb * 16;
-  const int j0 = cb * 16;
-  const int tid = threadIdx.x, rl = tid / 16, j = tid % 16;
-  for (int idx = tid; idx < 16 * p; idx += 256) {
+  constexpr int RPC = 256 / QT;            // rows per CTA
+  in_t* As = reinterpret_cast<in_t*>(sm);  // [RPC][p]
+  in_t* Cs = As + RPC * p;                 // [p][QT]
+  const int64_t r0 = rb * RPC;
+  const int j0 = cb * QT;
+  const int tid = threadIdx.x, rl = tid / QT, j = tid % QT;
+  for (int idx = tid; idx < RPC * p; idx += 256) {
     const int i = idx / p, a = idx % p;
     const int64_t r = r0 + i;
     As[idx] = r < n ? R::load(A[r * lda + a]) : R::zero_in();
   }
-  for (int idx = tid; idx < 16 * p; idx += 256) {
-    const int a = idx / 16, jj = idx % 16;
+  for (int idx = tid; idx < QT * p; idx += 256) {
+    const int a = idx / QT, jj = idx % QT;
     Cs[idx] = (j0 + jj < q) ? R::load(C[(int64_t)a * q + j0 + jj]) : R::zero_in();
   }
   __syncthreads();
@@ -161,7 +162,7 @@ __device__ __forceinline__ void lincomb_body(int64_t n, int p, const double* __r
   const int64_t r = r0 + rl;
   R::zero(acc);
   if (D && r < n && j0 + j < q) R::init(acc, D[r * ldd + j0 + j]);  // Y = A C + D
-  for (int a = 0; a < p; a++) R::mac(acc, As[rl * p + a], Cs[a * 16 + j]);
+  for (int a = 0; a < p; a++) R::mac(acc, As[rl * p + a], Cs[a * QT + j]);
   if (r < n && j0 + j < q) Y[r * ldy + j0 + j] = R::out(acc);
 }
 
@@ -170,7 +171,7 @@ __global__ void __launch_bounds__(256) k_lincomb(int64_t n, int p, const double*
                                                  const double* __restrict__ C, double* __restrict__ Y, int ldy,
                                                  const double* __restrict__ D, int ldd) {
   extern __shared__ __align__(16) unsigned char sm[];
-  lincomb_body<DF>(n, p, A, lda, q, C, Y, ldy, D, ldd, blockIdx.x, blockIdx.y, sm);
+  lincomb_body<DF, 16>(n, p, A, lda, q, C, Y, ldy, D, ldd, blockIdx.x, blockIdx.y, sm);
 }
 
 __device__ __forceinline__ int find_job(const lob_bjob* __restrict__ jobs, int njobs, int64_t b) {
@@ -182,12 +183,14 @@ __device__ __forceinline__ int find_job(const lob_bjob* __restrict__ jobs, int n
   return lo;
 }
 
-// Batched Y = A C (+ D), q <= 16: job fields A, lda, p, C, q, Y, ldy, D, ldd, n; ceil(n / 16) CTAs.
-template <bool DF>
+// Batched Y = A C (+ D), q <= QT: job fields A, lda, p, C, q, Y, ldy, D, ldd, n; ceil(n / (256 / QT))
+// CTAs. Narrow blocks (QT = 4, 8) put more rows in a CTA instead of idle output columns.
+template <bool DF, int QT>
 __global__ void __launch_bounds__(256) k_lincomb_batch(const lob_bjob* __restrict__ jobs, int njobs) {
   extern __shared__ __align__(16) unsigned char sm[];
   const lob_bjob& j = jobs[find_job(jobs, njobs, blockIdx.x)];
-  lincomb_body<DF>(j.n, j.p, j.A, j.lda, j.q, j.C, j.Y, j.ldy, j.D, j.ldd, (int64_t)blockIdx.x - j.cta_begin, 0, sm);
+  lincomb_body<DF, QT>(j.n, j.p, j.A, j.lda, j.q, j.C, j.Y, j.ldy, j.D, j.ldd, (int64_t)blockIdx.x - j.cta_begin, 0,
+                       sm);
 }
 
 // Batched Gram products, one output tile (p, q <= 16 U): job fields A, lda, p, B, ldb, q, n,
@@ -223,8 +226,68 @@ __global__ void __launch_bounds__(256) k_gram_batch(const lob_bjob* __restrict__
     }
 }
 
-// Batched fixed-order sum of the chunk partials: job fields W0, x0 (chunks), p, q, x1 (sym), Y;
-// ceil(p q 32 / 256) CTAs.
+// Batched Gram products by output pairs, for at most 1,024 pairs (p q, or p (p + 1) / 2 when
+// symmetric: only a <= b): thread t owns pairs t, t + 256, t + 512, t + 768 and walks the chunk's
+// rows through shared memory, so no work goes to padding. Job fields as k_gram_batch.
+template <bool DF>
+__global__ void __launch_bounds__(256) k_gram_pairs_batch(const lob_bjob* __restrict__ jobs, int njobs) {
+  using R = Ar<DF>;
+  using in_t = typename R::in_t;
+  constexpr int PMAX = 48;
+  __shared__ in_t As[RB][PMAX];
+  __shared__ in_t Bs[RB][PMAX];
+  const lob_bjob& j = jobs[find_job(jobs, njobs, blockIdx.x)];
+  const int chunk = (int)((int64_t)blockIdx.x - j.cta_begin);
+  const int64_t rpc = (j.n + j.x0 - 1) / j.x0;
+  const int64_t r0 = (int64_t)chunk * rpc;
+  const int64_t r1 = (r0 + rpc) < j.n ? (r0 + rpc) : j.n;
+  const int p = j.p, q = j.q, tid = threadIdx.x;
+  const int npairs = j.x1 ? p * (p + 1) / 2 : p * q;
+  int pa[4], pb[4];
+  typename R::acc_t acc[4];
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    R::zero(acc[u]);
+    int idx = tid + 256 * u;
+    pa[u] = -1;
+    pb[u] = 0;
+    if (idx < npairs) {
+      if (j.x1) {  // idx-th pair (a, b), a <= b, row-major over the upper triangle
+        int a = 0;
+        while (idx >= p - a) { idx -= p - a; a++; }
+        pa[u] = a;
+        pb[u] = a + idx;
+      } else {
+        pa[u] = idx / q;
+        pb[u] = idx % q;
+      }
+    }
+  }
+  for (int64_t rr = r0; rr < r1; rr += RB) {
+    for (int idx = tid; idx < RB * PMAX; idx += 256) {
+      const int i = idx / PMAX, a = idx % PMAX;
+      const int64_t r = rr + i;
+      As[i][a] = (r < r1 && a < p) ? R::load(j.A[r * j.lda + a]) : R::zero_in();
+      Bs[i][a] = (r < r1 && a < q) ? R::load(j.B[r * j.ldb + a]) : R::zero_in();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      if (pa[u] < 0) continue;
+#pragma unroll 4
+      for (int i = 0; i < RB; i++) R::mac(acc[u], As[i][pa[u]], Bs[i][pb[u]]);
+    }
+    __syncthreads();
+  }
+  const int pq = p * q;
+#pragma unroll
+  for (int u = 0; u < 4; u++)
+    if (pa[u] >= 0) j.W0[(int64_t)chunk * pq + (int64_t)pa[u] * q + pb[u]] = R::out(acc[u]);
+}
+
+// Batched fixed-order sum of the chunk partials: job fields W0, x0 (chunks), p, q, x1 (sym),
+// x3 (which entries of a symmetric result were formed: 0 = the tile kernel's, entries with
+// a / 16 > b / 16 missing; 1 = the pair kernel's, a > b missing), Y; ceil(p q 32 / 256) CTAs.
 __global__ void k_gram_reduce_batch(const lob_bjob* __restrict__ jobs, int njobs) {
   const lob_bjob& j = jobs[find_job(jobs, njobs, blockIdx.x)];
   const int64_t lb = (int64_t)blockIdx.x - j.cta_begin;
@@ -234,7 +297,7 @@ __global__ void k_gram_reduce_batch(const lob_bjob* __restrict__ jobs, int njobs
   int src = e;
   if (j.x1) {
     const int a = e / j.q, b = e % j.q;
-    if (a / 16 > b / 16) src = b * j.q + a;
+    if (j.x3 ? a > b : a / 16 > b / 16) src = b * j.q + a;
   }
   double s = 0.0;
   for (int c = lane; c < j.x0; c += 32) s += j.W0[(int64_t)c * pq + src];
@@ -321,9 +384,13 @@ int lob_gram_chunks(int64_t n, int p, int q) {
 }
 
 int lob_gram_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pqmax, int mode,
-                          lob_bjob* red_host, lob_bjob* red_dev, cudaStream_t st) {
+                          lob_bjob* red_host, lob_bjob* red_dev, cudaStream_t st, int pairs) {
   if (njobs <= 0) return LOB_OK;
   if (pqmax > TG) return LOB_ERR_ARG;
+  for (int i = 0; pairs && i < njobs; i++) {
+    const lob_bjob& j = jobs_host[i];
+    if ((j.x1 ? j.p * (j.p + 1) / 2 : j.p * j.q) > 1024) return LOB_ERR_ARG;
+  }
   int64_t ctas = 0, rctas = 0;
   for (int i = 0; i < njobs; i++) {
     lob_bjob& j = jobs_host[i];
@@ -336,7 +403,12 @@ int lob_gram_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, in
   LOB_CUDA(cudaMemcpyAsync(jobs_dev, jobs_host, njobs * sizeof(lob_bjob), cudaMemcpyHostToDevice, st));
   LOB_CUDA(cudaMemcpyAsync(red_dev, red_host, njobs * sizeof(lob_bjob), cudaMemcpyHostToDevice, st));
   const int U = pqmax <= 16 ? 1 : (pqmax <= 32 ? 2 : 3);
-  if (mode == LOB_SPMM_MIXED) {
+  if (pairs) {
+    for (int i = 0; i < njobs; i++) red_host[i].x3 = 1;
+    LOB_CUDA(cudaMemcpyAsync(red_dev, red_host, njobs * sizeof(lob_bjob), cudaMemcpyHostToDevice, st));
+    if (mode == LOB_SPMM_MIXED) (k_gram_pairs_batch<true><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
+    else (k_gram_pairs_batch<false><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
+  } else if (mode == LOB_SPMM_MIXED) {
     if (U == 1) (k_gram_batch<true, 1><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
     else if (U == 2) (k_gram_batch<true, 2><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
     else (k_gram_batch<true, 3><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
@@ -350,25 +422,35 @@ int lob_gram_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, in
   return LOB_OK;
 }
 
-int lob_lincomb_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pmax, int mode,
-                             cudaStream_t st) {
-  if (njobs <= 0) return LOB_OK;
+template <bool DF, int QT>
+static int lincomb_batch_go(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pmax, cudaStream_t st) {
+  constexpr int RPC = 256 / QT;
   int64_t ctas = 0;
   for (int i = 0; i < njobs; i++) {
-    if (jobs_host[i].q > 16) return LOB_ERR_ARG;
     jobs_host[i].cta_begin = ctas;
-    ctas += (jobs_host[i].n + 15) / 16;
+    ctas += (jobs_host[i].n + RPC - 1) / RPC;
   }
   if (ctas == 0) return LOB_OK;
   LOB_CUDA(cudaMemcpyAsync(jobs_dev, jobs_host, njobs * sizeof(lob_bjob), cudaMemcpyHostToDevice, st));
-  const size_t smem = 2ull * 16 * pmax * (mode == LOB_SPMM_MIXED ? sizeof(float2) : sizeof(double));
-  if (mode == LOB_SPMM_MIXED) {
-    LOB_CUDA(cudaFuncSetAttribute(k_lincomb_batch<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    (k_lincomb_batch<true><<<(unsigned)ctas, 256, smem, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
-  } else {
-    LOB_CUDA(cudaFuncSetAttribute(k_lincomb_batch<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    (k_lincomb_batch<false><<<(unsigned)ctas, 256, smem, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
-  }
+  const size_t smem = (size_t)(RPC + QT) * pmax * (DF ? sizeof(float2) : sizeof(double));
+  LOB_CUDA(cudaFuncSetAttribute(k_lincomb_batch<DF, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  (k_lincomb_batch<DF, QT><<<(unsigned)ctas, 256, smem, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
   LOB_CUDA(cudaGetLastError());
   return LOB_OK;
+}
+
+// All jobs of one call must share the output width class (q <= 4, <= 8 or <= 16; qmax selects).
+int lob_lincomb_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pmax, int qmax, int mode,
+                             cudaStream_t st) {
+  if (njobs <= 0) return LOB_OK;
+  if (qmax > 16 || pmax > 64) return LOB_ERR_ARG;
+  const bool df = mode == LOB_SPMM_MIXED;
+  if (qmax <= 4)
+    return df ? lincomb_batch_go<true, 4>(jobs_host, jobs_dev, njobs, pmax, st)
+              : lincomb_batch_go<false, 4>(jobs_host, jobs_dev, njobs, pmax, st);
+  if (qmax <= 8)
+    return df ? lincomb_batch_go<true, 8>(jobs_host, jobs_dev, njobs, pmax, st)
+              : lincomb_batch_go<false, 8>(jobs_host, jobs_dev, njobs, pmax, st);
+  return df ? lincomb_batch_go<true, 16>(jobs_host, jobs_dev, njobs, pmax, st)
+            : lincomb_batch_go<false, 16>(jobs_host, jobs_dev, njobs, pmax, st);
 }

@@ -90,6 +90,11 @@ struct lob_spmm_job {
   int32_t ldy, c0, w, pad;
   int64_t n_act;
   int64_t cta_begin;  // first CTA of this job in the grid
+  // staging (one launch per class before the SpMM): X (n x w, leading dimension w) rounded into Xs
+  // with rows >= n_act and columns >= w zeroed, rows padded to whole tiles; Y (n x w) zeroed
+  const double* Xsrc;
+  int64_t n_rows, rows_pad;
+  int64_t stage_begin;  // first CTA of this job in the staging grid
 };
 
 // One job of a batched launch (lockstep engine): the fields each kernel uses are listed at the
@@ -131,6 +136,21 @@ int lob_spmm_launch(const lob_matrix* m, int mode, const double* X, double* Y, i
 int lob_spmm_batch_launch(const lob_matrix* const* ms, const double* const* X, double* const* Y, const int* ncol,
                           const int* mode, const int64_t* nact, int njobs, lob_spmm_job* jobs_host,
                           lob_spmm_job* jobs_dev, cudaStream_t st, int* n_kernels = nullptr);
+// ---- lockstep engine (lockstep.cu): many solves, one iteration per round for all ----
+struct lob_engine;
+struct lob_ltask;
+int lob_engine_create(int cap, cudaStream_t st, lob_engine** out);
+void lob_engine_destroy(lob_engine* E);
+size_t lob_engine_task_bytes(const lob_matrix* m, int nb, int64_t n_small);
+int lob_engine_free_slots(const lob_engine* E);
+int lob_engine_add(lob_engine* E, lob_matrix* M, int32_t k, int32_t nb, double tol, const lob_solve_opts* o,
+                   double* Xout, int64_t n_act, int64_t user, lob_ltask** out);
+int lob_engine_round(lob_engine* E, std::vector<lob_ltask*>& done);
+int lob_engine_result(lob_engine* E, lob_ltask* t, double* lambda, lob_stats* st, int64_t* user);
+long long lob_engine_spmm_launches(const lob_engine* E);
+long long lob_engine_spmm_products(const lob_engine* E);
+int lob_engine_ntasks(const lob_engine* E);
+
 // ---- resumable LOBPCG task (lobpcg.cu) ----
 #define LOB_TASK_SYNC 1  // wait for lob_task_event(leaf), then step again
 #define LOB_TASK_SPMM 2  // run the leaf's SpMM (lob_task_spmm_args), then step again
@@ -161,9 +181,13 @@ size_t lob_rr_work_doubles(int m);
 // Batched block products for the lockstep engine. The launchers fill cta_begin and copy the
 // host job tables (pinned, left untouched until the stream passes) to the device tables.
 int lob_gram_chunks(int64_t n, int p, int q);
+// pairs: use the pair-list kernel (every job with at most 1,024 output pairs); else one tile of
+// edge 16, 32 or 48 (pqmax).
 int lob_gram_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pqmax, int mode,
-                          lob_bjob* red_host, lob_bjob* red_dev, cudaStream_t st);
-int lob_lincomb_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pmax, int mode,
+                          lob_bjob* red_host, lob_bjob* red_dev, cudaStream_t st, int pairs = 0);
+int lob_lincomb_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pmax, int qmax, int mode,
+                             cudaStream_t st);
+int lob_precond_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int bpmax, int nbmax,
                              cudaStream_t st);
 // Rayleigh-Ritz / Cholesky-QR problems, one per job and CTA (fields at k_rr_batch).
 int lob_rr_batch_launch(const lob_bjob* jobs_dev, int njobs, int mmax, int df, cudaStream_t st);

@@ -219,15 +219,13 @@ __device__ void block_solve(int solve, int steps, float guard, const float d[2],
 // W_[i] = Q f(Lambda - mu_j) Q^T R_[i]; one CTA per block, FP32 arithmetic. f is the exact
 // inverse (a direct solve of eq. 11), its absolute value, or the FOM / minimal-residual
 // polynomial of the given number of Krylov steps (the paper's iterative solve, Section 4.3).
-__global__ void __launch_bounds__(256) k_block_apply(int bp, int64_t n_act, const float* __restrict__ Q,
-                                                     const float* __restrict__ lam, const double* __restrict__ mu,
-                                                     float guard, const double* __restrict__ R, double* __restrict__ W,
-                                                     int nb, int solve, int steps) {
-  extern __shared__ float sm[];
+__device__ __forceinline__ void block_apply_body(int bp, int64_t n_act, const float* __restrict__ Q,
+                                                 const float* __restrict__ lam, const double* __restrict__ mu,
+                                                 float guard, const double* __restrict__ R, double* __restrict__ W,
+                                                 int nb, int solve, int steps, int64_t b, float* sm) {
   float* Qs = sm;             // bp x bp, column-major (Qs[k*bp + i])
   float* Rs = Qs + bp * bp;   // bp x nb
   float* Ts = Rs + bp * nb;   // bp x nb
-  const int64_t b = blockIdx.x;
   const int64_t o = b * bp;
   const int tid = threadIdx.x, nt = blockDim.x;
   const float* Qb = Q + b * (int64_t)bp * bp;
@@ -269,6 +267,28 @@ __global__ void __launch_bounds__(256) k_block_apply(int bp, int64_t n_act, cons
     for (int k = 0; k < bp; k++) s = fmaf(Qs[k * bp + i], Ts[k * nb + j], s);
     W[(o + i) * nb + j] = f32_to_f64(s);
   }
+}
+
+__global__ void __launch_bounds__(256) k_block_apply(int bp, int64_t n_act, const float* __restrict__ Q,
+                                                     const float* __restrict__ lam, const double* __restrict__ mu,
+                                                     float guard, const double* __restrict__ R, double* __restrict__ W,
+                                                     int nb, int solve, int steps) {
+  extern __shared__ float sm[];
+  block_apply_body(bp, n_act, Q, lam, mu, guard, R, W, nb, solve, steps, blockIdx.x, sm);
+}
+
+// Batched apply: job fields P0 (Q), P1 (lambda), C (mu), A (R), Y (W), x0 (nb), x1 (bp), n (rows),
+// s0 (guard), x2 (solve), x3 (steps); ceil(n / bp) CTAs.
+__global__ void __launch_bounds__(256) k_block_apply_batch(const lob_bjob* __restrict__ jobs, int njobs) {
+  extern __shared__ float sm[];
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].cta_begin <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const lob_bjob& j = jobs[lo];
+  block_apply_body(j.x1, j.n, reinterpret_cast<const float*>(j.P0), reinterpret_cast<const float*>(j.P1), j.C,
+                   (float)j.s0, j.A, j.Y, j.x0, j.x2, j.x3, (int64_t)blockIdx.x - j.cta_begin, sm);
 }
 
 }  // namespace
@@ -319,6 +339,24 @@ int lob_precond_launch(const lob_matrix* m, const double* mu, const double* R, d
     (k_block_apply<<<(unsigned)nblk, 256, smem, st>>>(bp, n_act, P.Q, P.lam, mu, (float)(1e-8 * m->norm_inf), R, W, nb,
                                                       solve, steps),
      LOB_LAUNCHED());
+  LOB_CUDA(cudaGetLastError());
+  return LOB_OK;
+}
+
+int lob_precond_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int bpmax, int nbmax,
+                             cudaStream_t st) {
+  if (njobs <= 0) return LOB_OK;
+  int64_t ctas = 0;
+  for (int i = 0; i < njobs; i++) {
+    lob_bjob& j = jobs_host[i];
+    if (j.x1 < 1 || j.x1 > 64 || j.x0 < 1 || j.x0 > 64) return LOB_ERR_ARG;
+    j.cta_begin = ctas;
+    ctas += (j.n + j.x1 - 1) / j.x1;
+  }
+  if (ctas == 0) return LOB_OK;
+  LOB_CUDA(cudaMemcpyAsync(jobs_dev, jobs_host, njobs * sizeof(lob_bjob), cudaMemcpyHostToDevice, st));
+  const size_t smem = ((size_t)bpmax * bpmax + 2ull * bpmax * nbmax) * sizeof(float);
+  (k_block_apply_batch<<<(unsigned)ctas, 256, smem, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
   LOB_CUDA(cudaGetLastError());
   return LOB_OK;
 }

@@ -1,6 +1,8 @@
-// Serving: many LOBPCG solves advanced together with shared SpMM launches (continuous batching).
+// Serving: many LOBPCG solves advanced together (continuous batching).
 //
-// Every admitted solve is a resumable task (lobpcg.cu) on its own stream. One progress pass steps
+// Default: the lockstep engine (lockstep.cu) -- one iteration of every admitted solve per progress
+// call, each kernel one launch for all solves. The stream engines below run each admitted solve as
+// a resumable task (lobpcg.cu) on its own stream. One progress pass steps
 // each task until it waits on the device (an event it recorded) or asks for H times a block.
 // The products asked for in the same pass go out as one batched launch per arithmetic class on
 // the server's stream: the server stream waits on each task's "ready" event, launches, and each
@@ -38,6 +40,7 @@ struct Req {
   int64_t id = 0;
   lob_request r{};
   lob_task* t = nullptr;
+  lob_ltask* lt = nullptr;  // lockstep engine
   cudaStream_t st = nullptr;
   cudaEvent_t ready = nullptr;
   size_t bytes = 0;
@@ -65,6 +68,7 @@ struct lob_server {
   bool jev_used[RING] = {};
   int ring = 0;
   cudaEvent_t batch_done = nullptr;
+  lob_engine* E = nullptr;  // lockstep engine (engine == LOB_ENGINE_LOCKSTEP)
   lob_server_stats stats{};
 
   double now() const {
@@ -82,6 +86,12 @@ struct lob_server {
   }
 
   void retire(Req* q, int rc) {
+    if (q->lt) {
+      double lam[64];
+      rc = lob_engine_result(E, q->lt, lam, &q->res.stats, nullptr);
+      if (rc == LOB_OK || rc == LOB_ERR_NOCONV) memcpy(q->res.lambda, lam, q->r.k * sizeof(double));
+      q->lt = nullptr;
+    }
     if (q->t) {
       if (rc == LOB_OK || rc == LOB_ERR_NOCONV || rc > 0) {
         double lam[64];
@@ -106,6 +116,23 @@ struct lob_server {
       if ((int)active.size() >= o.max_active) break;
       Req* q = *it;
       if (used + q->bytes > o.budget_bytes) { ++it; continue; }
+      if (E) {
+        const bool guess = q->r.opts.n_small >= 3 * q->r.nb && q->r.opts.n_small < q->r.H->T.n;
+        if (lob_engine_free_slots(E) < (guess ? 2 : 1)) break;
+        it = queue.erase(it);
+        used += q->bytes;
+        if (used > stats.bytes_peak) stats.bytes_peak = used;
+        q->res.state = LOB_REQ_RUNNING;
+        q->res.t_admit_ms = now();
+        stats.admitted++;
+        active.push_back(q);
+        const lob_matrix* H = q->r.H;
+        int rc = lob_ensure_xs(H, (size_t)H->T.nt * LOB_TILE * 16 * 8);
+        if (rc == LOB_OK)
+          rc = lob_engine_add(E, q->r.H, q->r.k, q->r.nb, q->r.tol, &q->r.opts, q->r.X, H->T.n, q->id, &q->lt);
+        if (rc != LOB_OK) { q->lt = nullptr; retire(q, rc); }
+        continue;
+      }
       it = queue.erase(it);
       used += q->bytes;
       if (used > stats.bytes_peak) stats.bytes_peak = used;
@@ -151,7 +178,7 @@ struct lob_server {
 
   int launch(std::vector<Req*>& want) {
     const int nj = (int)want.size();
-    if (o.batch_spmm < 0) {  // one launch per solve, on the solve's own stream
+    if (o.engine == LOB_ENGINE_STREAMS) {  // one launch per solve, on the solve's own stream
       for (Req* q : want) {
         const int rc = lob_task_spmm_direct(lob_task_leaf(q->t));
         if (rc != LOB_OK) retire(q, rc);
@@ -190,9 +217,35 @@ struct lob_server {
     return LOB_OK;
   }
 
+  int progress_lockstep(int* n_done) {
+    const int64_t fin0 = stats.finished;
+    LOB_TRY(admit());
+    if (lob_engine_ntasks(E) > 0) {
+      std::vector<lob_ltask*> done;
+      LOB_TRY(lob_engine_round(E, done));
+      for (lob_ltask* t : done) {
+        // find the request of this solve (its tag is the request id)
+        int64_t id = 0;
+        for (Req* q : active)
+          if (q->lt == t) { id = q->id; retire(q, LOB_OK); break; }
+        (void)id;
+      }
+      size_t w = 0;
+      for (size_t i = 0; i < active.size(); i++)
+        if (!active[i]->finished) active[w++] = active[i];
+      active.resize(w);
+      stats.spmm_launches = lob_engine_spmm_launches(E);
+      stats.spmm_products = lob_engine_spmm_products(E);
+    }
+    if (stats.finished > fin0) LOB_TRY(admit());
+    if (n_done) *n_done = (int)(stats.finished - fin0);
+    return LOB_OK;
+  }
+
   int progress(int wait, int* n_done) {
     LOB_CUDA(cudaSetDevice(device));
     stats.progress_calls++;
+    if (E) return progress_lockstep(n_done);
     const int64_t fin0 = stats.finished;
     LOB_TRY(admit());
     int moved = 0;
@@ -228,7 +281,7 @@ struct lob_server {
 extern "C" {
 
 int lob_spmm_batch(int32_t njobs, lob_matrix* const* H, const double* const* X, double* const* Y, const int32_t* nb,
-                   const int32_t* mode, void* stream) {
+                   const int32_t* mode, const int64_t* n_act, void* stream) {
   if (njobs < 0 || (njobs > 0 && (!H || !X || !Y || !nb || !mode))) return LOB_ERR_ARG;
   if (njobs == 0) return LOB_OK;
   for (int j = 0; j < njobs; j++)
@@ -252,7 +305,7 @@ int lob_spmm_batch(int32_t njobs, lob_matrix* const* H, const double* const* X, 
     cudaFreeHost(jh);
     return LOB_ERR_NOMEM;
   }
-  int rc = lob_spmm_batch_launch(ms.data(), X, Y, ncol.data(), md.data(), nullptr, njobs, jh, jd, st);
+  int rc = lob_spmm_batch_launch(ms.data(), X, Y, ncol.data(), md.data(), n_act, njobs, jh, jd, st);
   cudaFreeAsync(jd, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && rc == LOB_OK) rc = LOB_ERR_CUDA;
   cudaFreeHost(jh);
@@ -266,7 +319,10 @@ int lob_server_create(const lob_server_opts* o, lob_server** out) {
   if (o) s->o = *o;
   if (s->o.budget_bytes == 0) s->o.budget_bytes = 60ull << 30;
   if (s->o.max_active <= 0) s->o.max_active = 64;
-  if (s->o.batch_spmm == 0) s->o.batch_spmm = 1;
+  if (s->o.engine < LOB_ENGINE_LOCKSTEP || s->o.engine > LOB_ENGINE_STREAMS) {
+    delete s;
+    return LOB_ERR_ARG;
+  }
   s->t0 = std::chrono::steady_clock::now();
   int rc = LOB_OK;
   if (cudaGetDevice(&s->device) != cudaSuccess ||
@@ -275,6 +331,7 @@ int lob_server_create(const lob_server_opts* o, lob_server** out) {
     rc = LOB_ERR_CUDA;
   for (int i = 0; rc == LOB_OK && i < RING; i++)
     if (cudaEventCreateWithFlags(&s->jev[i], cudaEventDisableTiming) != cudaSuccess) rc = LOB_ERR_CUDA;
+  if (rc == LOB_OK && s->o.engine == LOB_ENGINE_LOCKSTEP) rc = lob_engine_create(2 * s->o.max_active, s->sst, &s->E);
   const size_t jb = (size_t)RING * s->o.max_active * sizeof(lob_spmm_job);
   if (rc == LOB_OK && (cudaHostAlloc((void**)&s->jh, jb, cudaHostAllocDefault) != cudaSuccess ||
                        cudaMalloc((void**)&s->jd, jb) != cudaSuccess))
@@ -303,7 +360,7 @@ int lob_server_submit(lob_server* s, const lob_request* r, int64_t* id) {
   Req* q = new Req();
   q->id = s->next_id++;
   q->r = *r;
-  q->bytes = matrix_bytes(H) + lob_task_bytes(H, r->nb, o.n_small);
+  q->bytes = matrix_bytes(H) + (s->E ? lob_engine_task_bytes(H, r->nb, o.n_small) : lob_task_bytes(H, r->nb, o.n_small));
   if (q->bytes > s->o.budget_bytes) { delete q; return LOB_ERR_ARG; }
   q->res.state = LOB_REQ_QUEUED;
   q->res.bytes = q->bytes;
@@ -351,6 +408,7 @@ int lob_server_destroy(lob_server* s) {
   for (Req* q : s->active)
     if (q->st) cudaStreamSynchronize(q->st);
   if (s->sst) cudaStreamSynchronize(s->sst);
+  if (s->E) { lob_engine_destroy(s->E); s->E = nullptr; }
   for (Req* q : s->active) {
     if (q->t) lob_task_destroy(q->t);
     if (q->st) cudaStreamSynchronize(q->st), cudaStreamDestroy(q->st);

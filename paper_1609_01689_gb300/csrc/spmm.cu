@@ -357,6 +357,30 @@ __global__ void k_stage_x_df(int64_t rows, int64_t n_act, int nb, int c0, int w,
   Xs[t] = df_split(v);
 }
 
+__device__ __forceinline__ void stage_put(float* p, double v) { *p = f64_to_f32_rn(v); }
+__device__ __forceinline__ void stage_put(double* p, double v) { *p = v; }
+__device__ __forceinline__ void stage_put(float2* p, double v) { *p = df_split(v); }
+
+// Staging for a batched class: every job's X into its matrix's staged copy (NB columns, rows
+// padded to whole tiles, zero beyond n_act and w) and its Y zeroed, in one launch.
+template <typename T, int NB>
+__global__ void k_stage_batch(const lob_spmm_job* __restrict__ jobs, int njobs) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].stage_begin <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const lob_spmm_job& j = jobs[lo];
+  const int64_t t = ((int64_t)blockIdx.x - j.stage_begin) * blockDim.x + threadIdx.x;
+  if (t < j.rows_pad * NB) {
+    const int64_t i = t / NB;
+    const int c = (int)(t % NB);
+    const double v = (c < j.w && i < j.n_act) ? j.Xsrc[i * j.w + c] : 0.0;
+    stage_put(reinterpret_cast<T*>(const_cast<void*>(j.Xs)) + t, v);
+  }
+  if (t < j.n_rows * j.w) j.Y[t] = 0.0;
+}
+
 template <int NB>
 __global__ void __launch_bounds__(CfgDF<NB>::THREADS, 1)
     k_spmm4df(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ tcol, const int64_t* __restrict__ tptr,
@@ -576,7 +600,7 @@ template <int MODE, int NB>
 int batch_class(const lob_matrix* const* ms, const double* const* X, double* const* Y, const int* ncol,
                 const int64_t* nact, const std::vector<int>& idx, lob_spmm_job* jobs_host, lob_spmm_job* jobs_dev, cudaStream_t st) {
   int njob = 0;
-  int64_t ctas = 0;
+  int64_t ctas = 0, sctas = 0;
   for (int j : idx) {
     const lob_matrix* m = ms[j];
     const lob_tiles& TS = m->T;
@@ -586,25 +610,22 @@ int batch_class(const lob_matrix* const* ms, const double* const* X, double* con
     const int64_t rows_pad = TS.nt * LOB_TILE;
     const size_t esz = MODE == LOB_SPMM_MIXED ? 4 : 8;
     LOB_TRY(lob_ensure_xs(m, (size_t)rows_pad * NB * esz));
-    if (MODE == LOB_SPMM_DF64)
-      (k_stage_x_df<<<(unsigned)((rows_pad * NB + 255) / 256), 256, 0, st>>>(rows_pad, na, ncol[j], 0, ncol[j], NB,
-                                                                             X[j], (float2*)m->xs), LOB_LAUNCHED());
-    else if (MODE == LOB_SPMM_MIXED)
-      (k_stage_x<float><<<(unsigned)((rows_pad * NB + 255) / 256), 256, 0, st>>>(rows_pad, na, ncol[j], 0, ncol[j], NB,
-                                                                                 X[j], (float*)m->xs), LOB_LAUNCHED());
-    else
-      (k_stage_x<double><<<(unsigned)((rows_pad * NB + 255) / 256), 256, 0, st>>>(rows_pad, TS.n, ncol[j], 0, ncol[j],
-                                                                                  NB, X[j], (double*)m->xs), LOB_LAUNCHED());
     lob_spmm_job jb;
     jb.rowptr = TS.rowptr; jb.tcol = TS.tcol; jb.tptr = TS.tptr; jb.tchunk = TS.tchunk; jb.rc = TS.rc;
     jb.vals = MODE == LOB_SPMM_FP64 ? (const void*)TS.v64 : (const void*)TS.v32;
     jb.vlo = TS.v32lo; jb.cperm = TS.cperm; jb.cptrs = TS.cptrs; jb.Xs = m->xs; jb.Y = Y[j];
     jb.ldy = ncol[j]; jb.c0 = 0; jb.w = ncol[j]; jb.pad = 0; jb.n_act = na; jb.cta_begin = ctas;
+    jb.Xsrc = X[j]; jb.n_rows = TS.n; jb.rows_pad = rows_pad; jb.stage_begin = sctas;
     jobs_host[njob++] = jb;
     ctas += nt_act;
+    const int64_t work = std::max<int64_t>(rows_pad * NB, TS.n * ncol[j]);
+    sctas += (work + 255) / 256;
   }
   if (njob == 0) return LOB_OK;
   LOB_CUDA(cudaMemcpyAsync(jobs_dev, jobs_host, njob * sizeof(lob_spmm_job), cudaMemcpyHostToDevice, st));
+  if (MODE == LOB_SPMM_DF64) (k_stage_batch<float2, NB><<<(unsigned)sctas, 256, 0, st>>>(jobs_dev, njob), LOB_LAUNCHED());
+  else if (MODE == LOB_SPMM_MIXED) (k_stage_batch<float, NB><<<(unsigned)sctas, 256, 0, st>>>(jobs_dev, njob), LOB_LAUNCHED());
+  else (k_stage_batch<double, NB><<<(unsigned)sctas, 256, 0, st>>>(jobs_dev, njob), LOB_LAUNCHED());
   if (MODE == LOB_SPMM_DF64) {
     using C = CfgDF<NB>;
     LOB_CUDA(cudaFuncSetAttribute(k_spmm4df<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES));
@@ -641,7 +662,6 @@ int lob_spmm_batch_launch(const lob_matrix* const* ms, const double* const* X, d
       return LOB_ERR_ARG;
     for (int i = 0; i < j; i++)
       if (ms[i] == ms[j]) return LOB_ERR_ARG;  // one staged-X scratch per matrix
-    LOB_CUDA(cudaMemsetAsync(Y[j], 0, (size_t)ms[j]->T.n * ncol[j] * sizeof(double), st));
     const int w = ncol[j];
     const int c = md == LOB_SPMM_MIXED ? (w <= 4 ? 1 : (w <= 8 ? 2 : 3)) : (w <= 2 ? 0 : (w <= 4 ? 1 : (w <= 8 ? 2 : 3)));
     cls[md][c].push_back(j);

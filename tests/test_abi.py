@@ -52,8 +52,8 @@ def test_library_loads_and_reports_errors(built_lib):
     assert lib.lob_spmm(None, 0, None, None, 8, None) == lob.LOB_ERR_ARG
     assert lib.lob_gram(0, 1, None, 1, 1, None, 1, None, 0, None) == lob.LOB_ERR_ARG
     assert lib.lob_destroy(None) == lob.LOB_OK
-    assert lib.lob_spmm_batch(1, None, None, None, None, None, None) == lob.LOB_ERR_ARG
-    assert lib.lob_spmm_batch(0, None, None, None, None, None, None) == lob.LOB_OK
+    assert lib.lob_spmm_batch(1, None, None, None, None, None, None, None) == lob.LOB_ERR_ARG
+    assert lib.lob_spmm_batch(0, None, None, None, None, None, None, None) == lob.LOB_OK
     assert lib.lob_server_create(None, None) == lob.LOB_ERR_ARG
     assert lib.lob_server_submit(None, None, None) == lob.LOB_ERR_ARG
     assert lib.lob_server_progress(None, 0, None) == lob.LOB_ERR_ARG

@@ -35,6 +35,32 @@ def test_spmm_batch_integer_exact():
         np.testing.assert_array_equal(Y.cpu().numpy(), oracle.spmm(H, X))
 
 
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "df64"])
+def test_spmm_batch_leading_block_never_reads_beyond(mode):
+    """With n_act the product is the leading block's: rows of X at or beyond n_act are not read
+    (NaN there must not reach Y), and rows below n_act equal the oracle product of the leading
+    block (integer data: exact in every arithmetic)."""
+    import torch
+    import paper_1609_01689_gb300 as lob
+    rng = np.random.default_rng(11)
+    sizes, nacts = [900, 1300, 520], [47, 700, 300]
+    Hs, mats, Xs = [], [], []
+    for n in sizes:
+        H = random_upper(n, 30.0 / n, rng, integer=True)
+        Hs.append(H)
+        mats.append(lob.Matrix(n, H.rows, H.cols, H.vals))
+    for n, na in zip(sizes, nacts):
+        X = rng.integers(-8, 9, (n, 4)).astype(np.float64)
+        X[na:] = np.nan
+        Xs.append(X)
+    Ys = lob.spmm_batch(mats, Xs, mode, n_act=nacts)
+    torch.cuda.synchronize()
+    for H, X, Y, na in zip(Hs, Xs, Ys, nacts):
+        keep = (H.rows < na) & (H.cols < na)
+        Hl = oracle.Coo(na, H.rows[keep], H.cols[keep], H.vals[keep])
+        np.testing.assert_array_equal(Y.cpu().numpy()[:na], oracle.spmm(Hl, X[:na]))
+
+
 def test_spmm_batch_rejects_repeated_matrix():
     import paper_1609_01689_gb300 as lob
     rng = np.random.default_rng(3)
@@ -73,7 +99,8 @@ def _rel(a, b):
     return np.abs(a - b) / np.maximum(np.abs(b), 1.0)
 
 
-def test_server_results_match_alone_and_oracle(mix):
+@pytest.mark.parametrize("engine", ["lockstep", "shared"])
+def test_server_results_match_alone_and_oracle(mix, engine):
     import torch
     import paper_1609_01689_gb300 as lob
     alone = []
@@ -81,7 +108,7 @@ def test_server_results_match_alone_and_oracle(mix):
         lam, X, st, rc = p["M"].solve(p["k"], p["nb"], 1e-8, mode=p["mode"], precond=True, n_small=p["n_small"])
         assert rc == lob.LOB_OK
         alone.append(lam)
-    srv = lob.Server(budget_bytes=8 << 30, max_active=16)
+    srv = lob.Server(budget_bytes=8 << 30, max_active=16, engine=engine)
     Xs, ids = [], []
     for p in mix:
         X = torch.empty((p["M"].n, p["nb"]), dtype=torch.float64, device="cuda")
@@ -170,7 +197,7 @@ def test_server_admits_by_memory_while_others_run(mix):
 
 def test_server_unbatched_mode_same_results(mix):
     import paper_1609_01689_gb300 as lob
-    srv = lob.Server(batched=False)
+    srv = lob.Server(engine="streams")
     ids = [srv.submit(p["M"], p["k"], p["nb"], 1e-8, mode=p["mode"], precond=True, n_small=p["n_small"])
            for p in mix[:3]]
     res = {}
