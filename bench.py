@@ -252,6 +252,7 @@ def run_serving(args, lob, synth, torch):
                "not_converged": failed[:20],
                "max_submit_lateness_ms": late * 1e3, "peak_bytes": int(st["bytes_peak"]),
                "spmm_products": int(st["spmm_products"]), "spmm_launches": int(st["spmm_launches"]),
+               "rounds": int(st["rounds"]), "host_ms": st["host_ms"], "device_wait_ms": st["wait_ms"],
                "matrix_build_s": build_s}
     # closed batch: the first requests all at once, served mixed vs one at a time in FP64
     sample = reqs[:args.serve_compare]
@@ -335,10 +336,60 @@ def run_batched_small(args, lob, synth, torch):
             "wall_s": wall, "instances_per_s": count / wall, "converged": ok, "rounds": rounds,
             "iterations_mean": float(its.mean()), "iterations_max": int(its.max()),
             "kernel_launches": int(launches), "spmm_launches": int(st["spmm_launches"]),
+            "host_ms": st["host_ms"], "device_wait_ms": st["wait_ms"],
             "spmm_products": int(st["spmm_products"]), "matrix_build_s": build_s,
             "sequential_lob_solve_s_per_instance": seq,
             "speedup_batched_over_sequential": seq * count / wall,
             "max_eig_rel_diff_vs_fp64_single": diff, "sample": len(samp)}
+
+
+def run_kernels(args, lob, M, info, torch):
+    """Each hot-path kernel alone at the workload's sizes (CUDA events, L2 flushed between
+    repetitions): the symmetric SpMM in its three arithmetics, the 48 x 48 double-float Gram,
+    the n x 48 by 48 x 16 double-float linear combination and the 48 x 48 Rayleigh-Ritz solve.
+    Prints one JSON line; a clean target for profiler captures of one launch of each kernel."""
+    n, nb = M.n, 16
+    g = torch.Generator(device="cuda").manual_seed(5)
+    X = torch.randn((n, nb), dtype=torch.float64, device="cuda", generator=g)
+    S = torch.randn((n, 48), dtype=torch.float64, device="cuda", generator=g)
+    T = torch.randn((n, 48), dtype=torch.float64, device="cuda", generator=g)
+    Cm = torch.randn((48, 16), dtype=torch.float64, device="cuda", generator=g)
+    Gd = S[:4096].T @ T[:4096]
+    Gs = (Gd + Gd.T) / 2
+    Ms = S[:4096].T @ S[:4096]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    out = {}
+
+    def timeit(name, fn, reps=10, **extra):
+        for _ in range(2):
+            fn()
+        ms = []
+        for _ in range(reps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        out[name] = dict(ms=float(np.median(ms)), **extra)
+
+    nnz, ntiles, nt = int(info["nnz"]), int(info["ntiles"]), (n + 255) // 256
+    for mode, sv in (("mixed", 4), ("df64", 8), ("fp64", 8)):
+        byts = nnz * (sv + 4) + ntiles * 12 + (nt + 1) * 8 + n * nb * (8 + 8)
+        timeit("spmm_" + mode, lambda mode=mode: M.spmm(X, mode), algorithmic_bytes=byts)
+    timeit("gram_df_48x48", lambda: lob.gram(S, T, "mixed"), df_macs=n * 48 * 48, algorithmic_bytes=n * 96 * 8)
+    timeit("lincomb_df_48x16", lambda: lob.lincomb(S, Cm, "mixed"), df_macs=n * 48 * 16,
+           algorithmic_bytes=n * (48 + 16) * 8)
+    timeit("rayleigh_ritz_df_48", lambda: lob.rayleigh_ritz(Gs, Ms, "mixed"), reps=20)
+    for v in out.values():
+        if "algorithmic_bytes" in v:
+            v["gbs"] = v["algorithmic_bytes"] / (v["ms"] * 1e-3) / 1e9
+        if "df_macs" in v:  # 12 FP32 instructions per double-float multiply-add
+            v["fp32_tinst_s"] = 12 * v["df_macs"] / (v["ms"] * 1e-3) / 1e12
+    print(json.dumps({"kernels": out, "n": n, "nnz_stored": nnz}))
 
 
 def run_reference(args, wl):
@@ -382,6 +433,7 @@ def main():
     ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--small-count", type=int, default=4096)
     ap.add_argument("--small-sample", type=int, default=64)
+    ap.add_argument("--kernels", action="store_true", help="time each hot-path kernel alone and exit")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -415,6 +467,8 @@ def main():
     torch.cuda.synchronize()
     create_ms = (time.perf_counter() - t0) * 1e3
     info = M.info()
+    if args.kernels:
+        return run_kernels(args, lob, M, info, torch)
     n_small = int(synth.level_starts(layout)[2])
     k, nb, tol = wl["k"], wl["nb"], wl["tol"]
     X = torch.empty((n, nb), dtype=torch.float64, device="cuda")

@@ -310,6 +310,9 @@ typedef struct {
   int64_t spmm_launches;   /* SpMM kernel launches made for the solves */
   int64_t spmm_products;   /* SpMM products they computed (one per solve per step) */
   int64_t progress_calls;
+  int64_t rounds;          /* lockstep rounds */
+  double host_ms;          /* lockstep: host time in rounds outside device waits */
+  double wait_ms;          /* lockstep: time waiting for the device */
 } lob_server_stats;
 
 /* The server uses the current CUDA device. Errors: LOB_ERR_ARG, LOB_ERR_NOMEM, LOB_ERR_CUDA. */

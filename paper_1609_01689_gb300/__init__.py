@@ -109,7 +109,8 @@ class Result(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", _I64), ("admitted", _I64), ("finished", _I64), ("active", _I64), ("queued", _I64),
                 ("bytes_in_use", ctypes.c_uint64), ("bytes_peak", ctypes.c_uint64), ("spmm_launches", _I64),
-                ("spmm_products", _I64), ("progress_calls", _I64)]
+                ("spmm_products", _I64), ("progress_calls", _I64), ("rounds", _I64), ("host_ms", _D),
+                ("wait_ms", _D)]
 
 
 class LobError(RuntimeError):

@@ -132,17 +132,20 @@ __global__ void k_gram_reduce(int nchunks, int pq, int q, int sym, int tge, cons
   if (lane == 0) G[warp] = s;
 }
 
-// Y = A C (+ D): 16 rows x 16 output columns per CTA. The CTA loads its rows of A (all p
-// columns) into shared memory before writing any output, so with a single column block (q <= 16)
-// the output may be columns of A's own rows (used in place by the solver).
-template <bool DF, int QT>
+// Y = A C (+ D): RM 256/QT rows x QT output columns per CTA; thread (rl, j) computes rows
+// rl, rl + 256/QT, ... (RM of them) of output column j, so each staged value of C feeds RM
+// independent accumulators. The CTA loads its rows of A (all p columns) into shared memory
+// before writing any output, so with a single column block (q <= QT) the output may be columns
+// of A's own rows (used in place by the solver).
+template <bool DF, int QT, int RM>
 __device__ __forceinline__ void lincomb_body(int64_t n, int p, const double* __restrict__ A, int lda, int q,
                                              const double* __restrict__ C, double* __restrict__ Y, int ldy,
                                              const double* __restrict__ D, int ldd, int64_t rb, int cb,
                                              unsigned char* sm) {
   using R = Ar<DF>;
   using in_t = typename R::in_t;
-  constexpr int RPC = 256 / QT;            // rows per CTA
+  constexpr int RT = 256 / QT;             // rows per pass of the CTA's threads
+  constexpr int RPC = RT * RM;             // rows per CTA
   in_t* As = reinterpret_cast<in_t*>(sm);  // [RPC][p]
   in_t* Cs = As + RPC * p;                 // [p][QT]
   const int64_t r0 = rb * RPC;
@@ -158,20 +161,32 @@ __device__ __forceinline__ void lincomb_body(int64_t n, int p, const double* __r
     Cs[idx] = (j0 + jj < q) ? R::load(C[(int64_t)a * q + j0 + jj]) : R::zero_in();
   }
   __syncthreads();
-  typename R::acc_t acc;
-  const int64_t r = r0 + rl;
-  R::zero(acc);
-  if (D && r < n && j0 + j < q) R::init(acc, D[r * ldd + j0 + j]);  // Y = A C + D
-  for (int a = 0; a < p; a++) R::mac(acc, As[rl * p + a], Cs[a * QT + j]);
-  if (r < n && j0 + j < q) Y[r * ldy + j0 + j] = R::out(acc);
+  typename R::acc_t acc[RM];
+#pragma unroll
+  for (int u = 0; u < RM; u++) {
+    R::zero(acc[u]);
+    const int64_t r = r0 + rl + RT * u;
+    if (D && r < n && j0 + j < q) R::init(acc[u], D[r * ldd + j0 + j]);  // Y = A C + D
+  }
+#pragma unroll 2
+  for (int a = 0; a < p; a++) {
+    const in_t c = Cs[a * QT + j];
+#pragma unroll
+    for (int u = 0; u < RM; u++) R::mac(acc[u], As[(rl + RT * u) * p + a], c);
+  }
+#pragma unroll
+  for (int u = 0; u < RM; u++) {
+    const int64_t r = r0 + rl + RT * u;
+    if (r < n && j0 + j < q) Y[r * ldy + j0 + j] = R::out(acc[u]);
+  }
 }
 
-template <bool DF>
+template <bool DF, int RM>
 __global__ void __launch_bounds__(256) k_lincomb(int64_t n, int p, const double* __restrict__ A, int lda, int q,
                                                  const double* __restrict__ C, double* __restrict__ Y, int ldy,
                                                  const double* __restrict__ D, int ldd) {
   extern __shared__ __align__(16) unsigned char sm[];
-  lincomb_body<DF, 16>(n, p, A, lda, q, C, Y, ldy, D, ldd, blockIdx.x, blockIdx.y, sm);
+  lincomb_body<DF, 16, RM>(n, p, A, lda, q, C, Y, ldy, D, ldd, blockIdx.x, blockIdx.y, sm);
 }
 
 __device__ __forceinline__ int find_job(const lob_bjob* __restrict__ jobs, int njobs, int64_t b) {
@@ -183,14 +198,15 @@ __device__ __forceinline__ int find_job(const lob_bjob* __restrict__ jobs, int n
   return lo;
 }
 
-// Batched Y = A C (+ D), q <= QT: job fields A, lda, p, C, q, Y, ldy, D, ldd, n; ceil(n / (256 / QT))
-// CTAs. Narrow blocks (QT = 4, 8) put more rows in a CTA instead of idle output columns.
+// Batched Y = A C (+ D), q <= QT: job fields A, lda, p, C, q, Y, ldy, D, ldd, n; ceil(n / (LB_RM 256 /
+// QT)) CTAs. Narrow blocks (QT = 4, 8) put more rows in a CTA instead of idle output columns.
+constexpr int LB_RM = 4;
 template <bool DF, int QT>
 __global__ void __launch_bounds__(256) k_lincomb_batch(const lob_bjob* __restrict__ jobs, int njobs) {
   extern __shared__ __align__(16) unsigned char sm[];
   const lob_bjob& j = jobs[find_job(jobs, njobs, blockIdx.x)];
-  lincomb_body<DF, QT>(j.n, j.p, j.A, j.lda, j.q, j.C, j.Y, j.ldy, j.D, j.ldd, (int64_t)blockIdx.x - j.cta_begin, 0,
-                       sm);
+  lincomb_body<DF, QT, LB_RM>(j.n, j.p, j.A, j.lda, j.q, j.C, j.Y, j.ldy, j.D, j.ldd,
+                              (int64_t)blockIdx.x - j.cta_begin, 0, sm);
 }
 
 // Batched Gram products, one output tile (p, q <= 16 U): job fields A, lda, p, B, ldb, q, n,
@@ -226,63 +242,111 @@ __global__ void __launch_bounds__(256) k_gram_batch(const lob_bjob* __restrict__
     }
 }
 
-// Batched Gram products by output pairs, for at most 1,024 pairs (p q, or p (p + 1) / 2 when
-// symmetric: only a <= b): thread t owns pairs t, t + 256, t + 512, t + 768 and walks the chunk's
-// rows through shared memory, so no work goes to padding. Job fields as k_gram_batch.
+// Batched Gram products by 2 x 2 output blocks, for at most 1,024 blocks (ceil(p/2) ceil(q/2), or
+// the upper triangle of blocks when symmetric), so little work goes to padding and each
+// multiply-add costs one shared-memory load. With many blocks thread t owns blocks t, t + 256,
+// t + 512, t + 768 over all rows of the chunk; with P <= 128 blocks the 256 threads form
+// G = floor(256 / P) groups of P that split the rows, and the groups' sums are added in a fixed
+// order at the end. Job fields as k_gram_batch.
 template <bool DF>
 __global__ void __launch_bounds__(256) k_gram_pairs_batch(const lob_bjob* __restrict__ jobs, int njobs) {
   using R = Ar<DF>;
   using in_t = typename R::in_t;
+  using acc_t = typename R::acc_t;
   constexpr int PMAX = 48;
-  __shared__ in_t As[RB][PMAX];
-  __shared__ in_t Bs[RB][PMAX];
+  __shared__ in_t As[RB * PMAX];
+  __shared__ in_t Bs[RB * PMAX];
+  __shared__ double gsum[4][256];
   const lob_bjob& j = jobs[find_job(jobs, njobs, blockIdx.x)];
   const int chunk = (int)((int64_t)blockIdx.x - j.cta_begin);
   const int64_t rpc = (j.n + j.x0 - 1) / j.x0;
   const int64_t r0 = (int64_t)chunk * rpc;
   const int64_t r1 = (r0 + rpc) < j.n ? (r0 + rpc) : j.n;
   const int p = j.p, q = j.q, tid = threadIdx.x;
-  const int npairs = j.x1 ? p * (p + 1) / 2 : p * q;
-  int pa[4], pb[4];
-  typename R::acc_t acc[4];
+  const int bp = (p + 1) / 2, bq = (q + 1) / 2, pe = 2 * bp, qe = 2 * bq;
+  const int nblocks = j.x1 ? bp * (bp + 1) / 2 : bp * bq;
+  const int P = nblocks;                           // threads of a row group
+  const int G = nblocks <= 128 ? 256 / P : 1;      // row groups (threads past G P idle)
+  const int slot = G > 1 ? tid % P : tid, grp = G > 1 ? tid / P : 0;
+  const int per = G > 1 ? 1 : 4;
+  int ba[4], bb[4];
+  acc_t acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; u++) {
-    R::zero(acc[u]);
-    int idx = tid + 256 * u;
-    pa[u] = -1;
-    pb[u] = 0;
-    if (idx < npairs) {
-      if (j.x1) {  // idx-th pair (a, b), a <= b, row-major over the upper triangle
+#pragma unroll
+    for (int e = 0; e < 4; e++) R::zero(acc[u][e]);
+    int idx = slot + 256 * u;
+    ba[u] = -1;
+    bb[u] = 0;
+    if (u < per && idx < nblocks && grp < G) {
+      if (j.x1) {  // idx-th block (A, B), A <= B, row-major over the upper triangle of blocks
         int a = 0;
-        while (idx >= p - a) { idx -= p - a; a++; }
-        pa[u] = a;
-        pb[u] = a + idx;
+        while (idx >= bp - a) { idx -= bp - a; a++; }
+        ba[u] = 2 * a;
+        bb[u] = 2 * (a + idx);
       } else {
-        pa[u] = idx / q;
-        pb[u] = idx % q;
+        ba[u] = 2 * (idx / bq);
+        bb[u] = 2 * (idx % bq);
       }
     }
   }
-  for (int64_t rr = r0; rr < r1; rr += RB) {
-    for (int idx = tid; idx < RB * PMAX; idx += 256) {
-      const int i = idx / PMAX, a = idx % PMAX;
+  // rows staged per step: the shared arrays hold RB rows of 48 columns, so narrow blocks stage
+  // proportionally more rows (each row group then has several rows per barrier)
+  const int RS = (RB * PMAX) / (pe > qe ? pe : qe);
+  for (int64_t rr = r0; rr < r1; rr += RS) {
+    for (int idx = tid; idx < RS * pe; idx += 256) {
+      const int i = idx / pe, a = idx % pe;
       const int64_t r = rr + i;
-      As[i][a] = (r < r1 && a < p) ? R::load(j.A[r * j.lda + a]) : R::zero_in();
-      Bs[i][a] = (r < r1 && a < q) ? R::load(j.B[r * j.ldb + a]) : R::zero_in();
+      As[idx] = (r < r1 && a < p) ? R::load(j.A[r * j.lda + a]) : R::zero_in();
+    }
+    for (int idx = tid; idx < RS * qe; idx += 256) {
+      const int i = idx / qe, a = idx % qe;
+      const int64_t r = rr + i;
+      Bs[idx] = (r < r1 && a < q) ? R::load(j.B[r * j.ldb + a]) : R::zero_in();
     }
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < 4; u++) {
-      if (pa[u] < 0) continue;
-#pragma unroll 4
-      for (int i = 0; i < RB; i++) R::mac(acc[u], As[i][pa[u]], Bs[i][pb[u]]);
+      if (ba[u] < 0) continue;
+      for (int i = grp; i < RS; i += G) {
+        const in_t* ar = As + i * pe;
+        const in_t* br = Bs + i * qe;
+        const in_t a0 = ar[ba[u]], a1 = ar[ba[u] + 1], b0 = br[bb[u]], b1 = br[bb[u] + 1];
+        R::mac(acc[u][0], a0, b0);
+        R::mac(acc[u][1], a0, b1);
+        R::mac(acc[u][2], a1, b0);
+        R::mac(acc[u][3], a1, b1);
+      }
     }
     __syncthreads();
   }
   const int pq = p * q;
+  if (G > 1) {
+    // fixed-order sum over the row groups (FP64 values of each group's partials)
 #pragma unroll
-  for (int u = 0; u < 4; u++)
-    if (pa[u] >= 0) j.W0[(int64_t)chunk * pq + (int64_t)pa[u] * q + pb[u]] = R::out(acc[u]);
+    for (int e = 0; e < 4; e++) gsum[e][tid] = ba[0] >= 0 ? R::out(acc[0][e]) : 0.0;
+    __syncthreads();
+    if (grp == 0 && ba[0] >= 0) {
+#pragma unroll
+      for (int e = 0; e < 4; e++) {
+        const int a = ba[0] + e / 2, b = bb[0] + e % 2;
+        if (a >= p || b >= q) continue;
+        double sum = 0.0;
+        for (int g = 0; g < G; g++) sum += gsum[e][g * P + slot];
+        j.W0[(int64_t)chunk * pq + (int64_t)a * q + b] = sum;
+      }
+    }
+    return;
+  }
+#pragma unroll
+  for (int u = 0; u < 4; u++) {
+    if (ba[u] < 0) continue;
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+      const int a = ba[u] + e / 2, b = bb[u] + e % 2;
+      if (a < p && b < q) j.W0[(int64_t)chunk * pq + (int64_t)a * q + b] = R::out(acc[u][e]);
+    }
+  }
 }
 
 // Batched fixed-order sum of the chunk partials: job fields W0, x0 (chunks), p, q, x1 (sym),
@@ -306,8 +370,11 @@ __global__ void k_gram_reduce_batch(const lob_bjob* __restrict__ jobs, int njobs
   if (lane == 0) j.Y[e] = s;
 }
 
-inline int nchunks_for(int64_t n, int tiles) {
-  int64_t c = (4 * 152 + tiles - 1) / tiles;
+// Row chunks of one Gram product: one full wave of CTAs over all output tiles -- 8 CTAs per SM
+// for 16 x 16 tiles (32 registers a thread), 4 for the larger ones (register-limited) -- with at
+// least 64 rows each.
+inline int nchunks_for(int64_t n, int tiles, int edge) {
+  int64_t c = ((edge == 16 ? 8 : 4) * 152 + tiles - 1) / tiles;
   int64_t maxc = (n + 63) / 64;
   if (c > maxc) c = maxc;
   return (int)(c < 1 ? 1 : c);
@@ -323,7 +390,7 @@ static int gram_edge(int p, int q) {
 size_t lob_gram_work_doubles(int64_t n, int p, int q) {
   const int e = gram_edge(p, q);
   const int tiles = ((p + e - 1) / e) * ((q + e - 1) / e);
-  return (size_t)nchunks_for(n, tiles) * p * q;
+  return (size_t)nchunks_for(n, tiles, e) * p * q;
 }
 
 template <bool DF>
@@ -339,7 +406,7 @@ int lob_gram_launch_ws(int64_t n, int p, const double* A, int lda, int q, const 
   if (sym && p != q) return LOB_ERR_ARG;
   const int e = gram_edge(p, q);
   const int ta = (p + e - 1) / e, tb = (q + e - 1) / e;
-  const int nch = nchunks_for(n, sym ? ta * (ta + 1) / 2 : ta * tb);
+  const int nch = nchunks_for(n, sym ? ta * (ta + 1) / 2 : ta * tb, e);
   const int64_t rpc = (n + nch - 1) / nch;
   dim3 grid(nch, ta, tb);
   if (mode == LOB_SPMM_MIXED) gram_go<true>(grid, st, e / 16, n, p, A, lda, q, B, ldb, work, rpc, sym);
@@ -365,22 +432,23 @@ int lob_lincomb_launch(int64_t n, int p, const double* A, int lda, int q, const 
                        int mode, cudaStream_t st, const double* D, int ldd) {
   if (n < 1 || p < 1 || q < 1 || p > 192 || q > 192 || lda < p || ldy < q || !A || !C || !Y) return LOB_ERR_ARG;
   if (mode != LOB_SPMM_FP64 && mode != LOB_SPMM_MIXED) return LOB_ERR_ARG;
-  dim3 grid((unsigned)((n + 15) / 16), (q + 15) / 16);
-  const size_t smem = 2ull * 16 * p * (mode == LOB_SPMM_MIXED ? sizeof(float2) : sizeof(double));
-  if (mode == LOB_SPMM_MIXED) {
-    LOB_CUDA(cudaFuncSetAttribute(k_lincomb<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    (k_lincomb<true><<<grid, 256, smem, st>>>(n, p, A, lda, q, C, Y, ldy, D, ldd), LOB_LAUNCHED());
-  } else {
-    LOB_CUDA(cudaFuncSetAttribute(k_lincomb<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    (k_lincomb<false><<<grid, 256, smem, st>>>(n, p, A, lda, q, C, Y, ldy, D, ldd), LOB_LAUNCHED());
-  }
-  LOB_CUDA(cudaGetLastError());
-  return LOB_OK;
+  // four rows a thread when the CTA's rows of A fit comfortably in shared memory, else one
+  const int RM = p <= 64 ? 4 : 1;
+  dim3 grid((unsigned)((n + 16 * RM - 1) / (16 * RM)), (q + 15) / 16);
+  const size_t smem = (16ull * RM + 16) * p * (mode == LOB_SPMM_MIXED ? sizeof(float2) : sizeof(double));
+  auto go = [&](auto kern) -> int {
+    LOB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    (kern<<<grid, 256, smem, st>>>(n, p, A, lda, q, C, Y, ldy, D, ldd), LOB_LAUNCHED());
+    LOB_CUDA(cudaGetLastError());
+    return LOB_OK;
+  };
+  if (mode == LOB_SPMM_MIXED) return RM == 4 ? go(k_lincomb<true, 4>) : go(k_lincomb<true, 1>);
+  return RM == 4 ? go(k_lincomb<false, 4>) : go(k_lincomb<false, 1>);
 }
 
 int lob_gram_chunks(int64_t n, int p, int q) {
   const int e = gram_edge(p, q);
-  return nchunks_for(n, ((p + e - 1) / e) * ((q + e - 1) / e));
+  return nchunks_for(n, ((p + e - 1) / e) * ((q + e - 1) / e), e);
 }
 
 int lob_gram_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pqmax, int mode,
@@ -389,7 +457,8 @@ int lob_gram_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, in
   if (pqmax > TG) return LOB_ERR_ARG;
   for (int i = 0; pairs && i < njobs; i++) {
     const lob_bjob& j = jobs_host[i];
-    if ((j.x1 ? j.p * (j.p + 1) / 2 : j.p * j.q) > 1024) return LOB_ERR_ARG;
+    const int bp = (j.p + 1) / 2, bq = (j.q + 1) / 2;
+    if ((j.x1 ? bp * (bp + 1) / 2 : bp * bq) > 1024 || j.p > 48 || j.q > 48) return LOB_ERR_ARG;
   }
   int64_t ctas = 0, rctas = 0;
   for (int i = 0; i < njobs; i++) {
@@ -424,7 +493,7 @@ int lob_gram_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, in
 
 template <bool DF, int QT>
 static int lincomb_batch_go(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pmax, cudaStream_t st) {
-  constexpr int RPC = 256 / QT;
+  constexpr int RPC = LB_RM * 256 / QT;
   int64_t ctas = 0;
   for (int i = 0; i < njobs; i++) {
     jobs_host[i].cta_begin = ctas;

@@ -150,6 +150,7 @@ int lob_engine_result(lob_engine* E, lob_ltask* t, double* lambda, lob_stats* st
 long long lob_engine_spmm_launches(const lob_engine* E);
 long long lob_engine_spmm_products(const lob_engine* E);
 int lob_engine_ntasks(const lob_engine* E);
+void lob_engine_times(const lob_engine* E, double* host_ms, double* wait_ms, long long* rounds);
 
 // ---- resumable LOBPCG task (lobpcg.cu) ----
 #define LOB_TASK_SYNC 1  // wait for lob_task_event(leaf), then step again
@@ -181,7 +182,7 @@ size_t lob_rr_work_doubles(int m);
 // Batched block products for the lockstep engine. The launchers fill cta_begin and copy the
 // host job tables (pinned, left untouched until the stream passes) to the device tables.
 int lob_gram_chunks(int64_t n, int p, int q);
-// pairs: use the pair-list kernel (every job with at most 1,024 output pairs); else one tile of
+// pairs: use the 2 x 2-block kernel (every job with at most 1,024 blocks); else one tile of
 // edge 16, 32 or 48 (pqmax).
 int lob_gram_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pqmax, int mode,
                           lob_bjob* red_host, lob_bjob* red_dev, cudaStream_t st, int pairs = 0);

@@ -16,19 +16,19 @@ namespace {
 
 constexpr int RR_THREADS = 1024;
 
-__device__ __forceinline__ int rr_player(int pos, int round, int mp) {
-  // circle method: position 0 holds player 0; the others rotate by one each round
-  return pos == 0 ? 0 : 1 + (pos - 1 + round) % (mp - 1);
-}
-
 
 // ---- cyclic Jacobi with 2x2-block updates (both kernels) ----
 // Round r of the round-robin order pairs the indices as (p_k, q_k), k < m/2, all disjoint.
 // A <- J^T A J with J the product of the round's rotations; for the 2x2 block of rows {p1, q1}
 // and columns {p2, q2} the new values depend only on that block, so one thread updates a whole
 // block (left rotation k1, then right rotation k2) and the round needs no barrier between its
-// row and column halves: angles (one thread per pair) | barrier | blocks of A and pairs of
-// columns of V | barrier.
+// row and column halves. V <- V J touches no value the angles depend on, so V's rotations of
+// round r run in the next round's first phase, beside the angle computation:
+//   phase 1: warp 0 computes round r's angles | the other warps rotate V by round r-1's
+//   barrier
+//   phase 2: all threads update the 2x2 blocks of A by round r's rotations
+//   barrier
+// Angles and pairs are double-buffered by round parity.
 __device__ __forceinline__ void rot2(double& x, double& y, double c, double s) {
   const double u = c * x - s * y, v = s * x + c * y;
   x = u;
@@ -68,12 +68,45 @@ __device__ __forceinline__ void jac_angle(d2 app, d2 aqq, d2 apq, d2& c, d2& s) 
   s = d2_mul(tt, c);
 }
 
+// b-th pair (k1 <= k2) of an np x np array, row by row over its upper triangle
+__device__ __forceinline__ void tri_index(int b, int np, int& k1, int& k2) {
+  const float t = (float)(2 * np + 1);
+  int r = (int)floorf(0.5f * (t - sqrtf(fmaxf(t * t - 8.f * (float)b, 0.f))));
+  auto first = [np](int x) { return x * np - x * (x - 1) / 2; };  // index of (x, x)
+  if (r < 0) r = 0;
+  if (r > np - 1) r = np - 1;
+  while (r > 0 && first(r) > b) r--;
+  while (r < np - 1 && first(r + 1) <= b) r++;
+  k1 = r;
+  k2 = r + (b - first(r));
+}
+
+// position -> index in round r (circle method: position 0 fixed, the others rotate by one)
+__device__ __forceinline__ int rr_index(int pos, int round, int mp) {
+  if (pos == 0) return 0;
+  int x = pos - 1 + round;  // < 2 (mp - 1)
+  if (x >= mp - 1) x -= mp - 1;
+  return 1 + x;
+}
+
+// Cyclic Jacobi on A (m x m, symmetric), accumulating the rotations into V. cs_c, cs_s, pr_p,
+// pr_q hold two rounds of 96 pairs each.
 template <typename E>
 __device__ void jacobi_blocks(int m, E* A, E* V, double stop_ratio, E* cs_c, E* cs_s, int* pr_p, int* pr_q,
                               double* red, double* s_off, double* s_fro) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int mm = m * m;
   const int mp = m + (m & 1), np = mp / 2;
+  int pend = -1;  // buffer of the round whose V rotations are still to be applied
+  auto rotate_v = [&](int b, int t0, int ts) {
+    for (int e = t0; e < np * m; e += ts) {
+      const int k = e / m, row = e % m;
+      const int q = pr_q[b * 96 + k];
+      if (q >= m || !nonzero(cs_s[b * 96 + k])) continue;
+      rot2(V[row * m + pr_p[b * 96 + k]], V[row * m + q], cs_c[b * 96 + k], cs_s[b * 96 + k]);
+    }
+  };
+  int rcount = 0;
   for (int sweep = 0; sweep < 40; sweep++) {
     double off = 0.0, fro = 0.0;
     for (int e = tid; e < mm; e += nt) {
@@ -91,39 +124,55 @@ __device__ void jacobi_blocks(int m, E* A, E* V, double stop_ratio, E* cs_c, E* 
     }
     __syncthreads();
     if (*s_off <= stop_ratio * *s_fro || *s_off == 0.0) break;
-    for (int round = 0; round < mp - 1; round++) {
-      for (int k = tid; k < np; k += nt) {
-        int p = rr_player(k, round, mp), q = rr_player(mp - 1 - k, round, mp);
-        if (p > q) { const int t = p; p = q; q = t; }
-        E c = ident_one(E{}), sn = ident_zero(E{});
-        if (q < m) jac_angle(A[p * m + p], A[q * m + q], A[p * m + q], c, sn);
-        pr_p[k] = p; pr_q[k] = q; cs_c[k] = c; cs_s[k] = sn;
+    for (int round = 0; round < mp - 1; round++, rcount++) {
+      const int b = rcount & 1;
+      E* cc = cs_c + b * 96;
+      E* ss = cs_s + b * 96;
+      int* pp = pr_p + b * 96;
+      int* qq = pr_q + b * 96;
+      if (tid < 32) {
+        for (int k = tid; k < np; k += 32) {
+          int p = rr_index(k, round, mp), q = rr_index(mp - 1 - k, round, mp);
+          if (p > q) { const int t = p; p = q; q = t; }
+          E c = ident_one(E{}), sn = ident_zero(E{});
+          if (q < m) jac_angle(A[p * m + p], A[q * m + q], A[p * m + q], c, sn);
+          pp[k] = p; qq[k] = q; cc[k] = c; ss[k] = sn;
+        }
+      } else if (pend >= 0) {
+        rotate_v(pend, tid - 32, nt - 32);
       }
       __syncthreads();
-      // 2x2 blocks of A: block (k1, k2) = rows {p1, q1} x columns {p2, q2}
-      for (int b = tid; b < np * np; b += nt) {
-        const int k1 = b / np, k2 = b % np;
-        const int p1 = pr_p[k1], q1 = pr_q[k1], p2 = pr_p[k2], q2 = pr_q[k2];
+      // 2x2 blocks of A: block (k1, k2) = rows {p1, q1} x columns {p2, q2}, k1 <= k2; the block
+      // (k2, k1) is its transpose and is written by the same thread, so A stays exactly symmetric
+      for (int bb = tid; bb < np * (np + 1) / 2; bb += nt) {
+        int k1, k2;
+        tri_index(bb, np, k1, k2);
+        const int p1 = pp[k1], q1 = qq[k1], p2 = pp[k2], q2 = qq[k2];
         const bool r1 = q1 < m, r2 = q2 < m;  // second index valid (not the dummy)
         E a11 = A[p1 * m + p2];
         E a12 = r2 ? A[p1 * m + q2] : ident_zero(E{});
         E a21 = r1 ? A[q1 * m + p2] : ident_zero(E{});
         E a22 = (r1 && r2) ? A[q1 * m + q2] : ident_zero(E{});
-        if (r1 && nonzero(cs_s[k1])) { rot2(a11, a21, cs_c[k1], cs_s[k1]); rot2(a12, a22, cs_c[k1], cs_s[k1]); }
-        if (r2 && nonzero(cs_s[k2])) { rot2(a11, a12, cs_c[k2], cs_s[k2]); rot2(a21, a22, cs_c[k2], cs_s[k2]); }
+        if (r1 && nonzero(ss[k1])) { rot2(a11, a21, cc[k1], ss[k1]); rot2(a12, a22, cc[k1], ss[k1]); }
+        if (r2 && nonzero(ss[k2])) { rot2(a11, a12, cc[k2], ss[k2]); rot2(a21, a22, cc[k2], ss[k2]); }
         A[p1 * m + p2] = a11;
         if (r2) A[p1 * m + q2] = a12;
         if (r1) A[q1 * m + p2] = a21;
         if (r1 && r2) A[q1 * m + q2] = a22;
-      }
-      // columns p, q of V
-      for (int e = tid; e < np * m; e += nt) {
-        const int k = e / m, row = e % m;
-        if (pr_q[k] >= m || !nonzero(cs_s[k])) continue;
-        rot2(V[row * m + pr_p[k]], V[row * m + pr_q[k]], cs_c[k], cs_s[k]);
+        if (k1 != k2) {
+          A[p2 * m + p1] = a11;
+          if (r2) A[q2 * m + p1] = a12;
+          if (r1) A[p2 * m + q1] = a21;
+          if (r1 && r2) A[q2 * m + q1] = a22;
+        }
       }
       __syncthreads();
+      pend = b;
     }
+  }
+  if (pend >= 0) {
+    rotate_v(pend, tid, nt);
+    __syncthreads();
   }
 }
 
@@ -138,8 +187,8 @@ __device__ __forceinline__ void rr_body(int m, const double* __restrict__ G, con
   double* A = base;          // m x m
   double* L = base + m * m;  // m x m, lower Cholesky factor
   double* V = L + m * m;     // m x m, eigenvectors
-  __shared__ double cs_c[96], cs_s[96];
-  __shared__ int pr_p[96], pr_q[96];
+  __shared__ double cs_c[192], cs_s[192];
+  __shared__ int pr_p[192], pr_q[192];
   __shared__ double red[64];
   __shared__ int s_fail;
   __shared__ double s_off, s_fro;
@@ -251,8 +300,8 @@ __device__ __forceinline__ void rr_body_df(int m, const double* __restrict__ G, 
   d2* A = SMEM ? reinterpret_cast<d2*>(rr_sm) : reinterpret_cast<d2*>(work);
   d2* L = A + m * m;
   d2* V = L + m * m;
-  __shared__ d2 cs_c[96], cs_s[96];
-  __shared__ int pr_p[96], pr_q[96];
+  __shared__ d2 cs_c[192], cs_s[192];
+  __shared__ int pr_p[192], pr_q[192];
   __shared__ d2 inv[192];
   __shared__ double red[64];
   __shared__ int s_fail;
@@ -405,11 +454,11 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_batch(const lob_bjob* __restr
 static size_t rr_smem_bytes(int m) { return 3ull * m * m * 8; }
 static const size_t RR_SMEM_MAX = 200 * 1024;
 
-// Threads for order m: one per 2x2 block of a Jacobi round ((m+1)/2 squared), 128 to 1,024 --
+// Threads for order m: one per 2x2 block of the upper triangle of a Jacobi round, 128 to 1,024 --
 // the kernel is barrier-latency bound, and fewer warps make each barrier cheaper.
 static int rr_threads(int m) {
   const int np = (m + 1) / 2;
-  int t = ((np * np + 31) / 32) * 32;
+  int t = ((np * (np + 1) / 2 + 31) / 32) * 32;
   return t < 128 ? 128 : (t > RR_THREADS ? RR_THREADS : t);
 }
 

@@ -146,8 +146,10 @@ __global__ void k_proj_coef(int nb, int na, const double* __restrict__ Z, double
 
 // Phase timing with CUDA events on the task's stream. Event pairs are recorded without
 // synchronising and resolved in bulk whenever the task passes a synchronisation point anyway.
+// Pairs recorded while a stage is captured belong to the stage's graph: the graph records them on
+// every replay, and they are queued again (owned) after each launch.
 struct PhaseClock {
-  struct Pair { cudaEvent_t a, b; double* acc; };
+  struct Pair { cudaEvent_t a, b; double* acc; bool owned; };
   std::vector<Pair> pending;
   std::vector<cudaEvent_t> pool;
   cudaEvent_t get() {
@@ -158,12 +160,14 @@ struct PhaseClock {
     for (auto& p : pending) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess && p.acc) *p.acc += ms;
-      pool.push_back(p.a); pool.push_back(p.b);
+      else cudaGetLastError();
+      if (!p.owned) { pool.push_back(p.a); pool.push_back(p.b); }
     }
     pending.clear();
   }
   ~PhaseClock() {
-    for (auto& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto& p : pending)
+      if (!p.owned) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : pool) cudaEventDestroy(e);
   }
 };
@@ -180,7 +184,7 @@ struct Timer {
     if (a) {
       cudaEvent_t b = clk->get();
       cudaEventRecord(b, st);
-      clk->pending.push_back({a, b, acc});
+      clk->pending.push_back({a, b, acc, false});
     }
   }
 };
@@ -299,14 +303,17 @@ struct lob_task {
   int sp_post_ld = 0;
   lob_task* child = nullptr;
   // captured stages: one graph per stage shape (stage, active columns, P present, ...), replayed
-  // as a single launch; used when the task keeps no phase timers
+  // as a single launch (phase timers inside a stage become event nodes of its graph)
   bool graphs = false;
-  struct Staged { uint64_t key; cudaGraphExec_t exec; long long kernels; };
+  struct Staged { uint64_t key; cudaGraphExec_t exec; long long kernels; std::vector<PhaseClock::Pair> timers; };
   std::vector<Staged> gcache;
 
   ~lob_task() {
     delete child;
-    for (auto& g : gcache) cudaGraphExecDestroy(g.exec);
+    for (auto& g : gcache) {
+      cudaGraphExecDestroy(g.exec);
+      for (auto& p : g.timers) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    }
     if (ev) cudaEventDestroy(ev);
     box_put(hb);
   }
@@ -325,8 +332,10 @@ struct lob_task {
       if (g.key == key) {
         LOB_CUDA(cudaGraphLaunch(g.exec, st));
         g_lob_launches.fetch_add(g.kernels, std::memory_order_relaxed);
+        for (const auto& p : g.timers) clock.pending.push_back(p);
         return LOB_OK;
       }
+    const size_t p0 = clock.pending.size();
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       cudaGetLastError();
       graphs = false;
@@ -342,13 +351,23 @@ struct lob_task {
     if (rc != LOB_OK || e != cudaSuccess || !g || cudaGraphInstantiate(&x, g, 0) != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
       cudaGetLastError();
+      for (size_t i = p0; i < clock.pending.size(); i++) {  // recorded only in the abandoned capture
+        clock.pool.push_back(clock.pending[i].a);
+        clock.pool.push_back(clock.pending[i].b);
+      }
+      clock.pending.resize(p0);
       graphs = false;
       return rc != LOB_OK ? rc : enqueue();
     }
     cudaGraphDestroy(g);
-    gcache.push_back({key, x, nk});
+    // timer pairs recorded during the capture now belong to the graph
+    std::vector<PhaseClock::Pair> timers(clock.pending.begin() + p0, clock.pending.end());
+    clock.pending.resize(p0);
+    for (auto& p : timers) p.owned = true;
+    gcache.push_back({key, x, nk, timers});
     LOB_CUDA(cudaGraphLaunch(x, st));
     g_lob_launches.fetch_add(nk, std::memory_order_relaxed);
+    for (const auto& p : gcache.back().timers) clock.pending.push_back(p);
     return LOB_OK;
   }
 
@@ -544,7 +563,7 @@ int task_init(lob_task* t, lob_matrix* m, int32_t k, int32_t nb, double tol, con
   t->blas_mode = o->mode == LOB_MODE_MIXED ? LOB_SPMM_MIXED : LOB_SPMM_FP64;
   t->max_iter = o->max_iter > 0 ? o->max_iter : 500;
   t->t0 = std::chrono::steady_clock::now();
-  t->graphs = !timing;
+  t->graphs = true;
   return t->alloc();
 }
 }  // namespace

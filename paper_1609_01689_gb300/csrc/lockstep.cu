@@ -172,6 +172,7 @@ struct lob_ltask {
       *part, *gw, *rrw;
   int* map;
   int nparts = 0;
+  size_t gw_half = 0;  // doubles in each half of the Gram partial buffer
   // control
   int blas = LOB_SPMM_FP64;
   int phase = 0;        // MIXED: 0 = FP32-value products, 1 = FP64-class refinement
@@ -200,7 +201,7 @@ namespace {
 
 size_t task_doubles(int64_t n, int nb, int* nch) {
   const int mm = 3 * nb;
-  *nch = lob_gram_chunks(n, 48, 48) > 0 ? (int)std::min<int64_t>(608, (n + 63) / 64) : 1;
+  *nch = lob_gram_chunks(n, 16, 16);  // the most chunks any Gram of this solve uses (one 16 x 16 tile)
   size_t d = 2 * (size_t)n * mm + 6 * (size_t)n * nb;
   d += 8 * (size_t)mm * mm + 5 * (size_t)mm + 64;
   d += (size_t)nblk(n) * 2 * nb + 2 * (size_t)(*nch) * mm * mm + lob_rr_work_doubles(mm);
@@ -223,6 +224,7 @@ struct lob_engine {
   int scap = 0;
   std::vector<lob_ltask*> tasks;  // admitted (active, waiting, or starting)
   long long rounds = 0, spmm_launches = 0, spmm_products = 0;
+  double host_ms = 0.0, wait_ms = 0.0;  // time in rounds outside / inside stream synchronisation
 
   lob_bjob* take(size_t k, lob_bjob** dev) {
     if (joff + k > jcap) return nullptr;
@@ -284,16 +286,21 @@ lob_bjob gram_job(const lob_ltask* t, const double* A, int p, const double* B, i
   lob_bjob j{};
   j.x2 = t->blas;
   j.A = A; j.lda = t->ldS; j.p = p; j.B = B; j.ldb = t->ldS; j.q = q; j.n = t->n_act; j.W0 = partials;
-  j.x0 = lob_gram_chunks(t->n_act, p, q); j.x1 = sym; j.Y = out;
+  // in a batch the solves fill the GPU together: about 1,024 rows per chunk (at most the
+  // single-solve chunk count, which sizes the partial buffers)
+  j.x0 = (int)std::max<int64_t>(1, std::min<int64_t>(lob_gram_chunks(t->n_act, p, q), (t->n_act + 1023) / 1024));
+  j.x1 = sym; j.Y = out;
   return j;
 }
 
 // The block products of a batch run in each solve's own arithmetic (x2: LOB_SPMM_FP64 or
 // LOB_SPMM_MIXED, i.e. double-float): one launch per arithmetic present.
-// Gram jobs also split by size: products with at most 1,024 output pairs (counting only a <= b when
-// symmetric) use the pair-list kernel (class 0); larger ones a tile of edge 16, 32 or 48.
+// Gram jobs also split by size: products with at most 1,024 2 x 2 output blocks (counting only the
+// upper triangle when symmetric) use the block kernel (class 0); larger ones a tile of edge 16,
+// 32 or 48.
 inline int tile_class(const lob_bjob& j) {
-  if ((j.x1 ? j.p * (j.p + 1) / 2 : j.p * j.q) <= 1024) return 0;
+  const int bp = (j.p + 1) / 2, bq = (j.q + 1) / 2;
+  if ((j.x1 ? bp * (bp + 1) / 2 : bp * bq) <= 1024) return 0;
   const int e = std::max(j.p, j.q);
   return e <= 16 ? 1 : (e <= 32 ? 2 : 3);
 }
@@ -368,7 +375,9 @@ lob_bjob rr_job(const lob_ltask* t, int m, const double* G, const double* Mm, do
 }
 
 int sync(lob_engine* E) {
+  const auto a = std::chrono::steady_clock::now();
   LOB_CUDA(cudaStreamSynchronize(E->st));
+  E->wait_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
   return LOB_OK;
 }
 
@@ -451,6 +460,7 @@ int task_alloc(lob_engine* E, lob_ltask* t) {
   t->nparts = (int)nblk(t->n_act);
   t->part = take((size_t)nblk(n) * 2 * nb);
   t->gw = take(2 * (size_t)nch * mm * mm);
+  t->gw_half = (size_t)nch * mm * mm;
   t->rrw = take(lob_rr_work_doubles(mm));
   return LOB_OK;
 }
@@ -535,7 +545,24 @@ int lob_engine_add(lob_engine* E, lob_matrix* M, int32_t k, int32_t nb, double t
 }
 
 // One round for every admitted solve. Finished solves (top-level ones) are appended to done.
+static int engine_round(lob_engine* E, std::vector<lob_ltask*>& done);
+
 int lob_engine_round(lob_engine* E, std::vector<lob_ltask*>& done) {
+  const auto a = std::chrono::steady_clock::now();
+  const double w0 = E->wait_ms;
+  const int rc = engine_round(E, done);
+  E->host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count() -
+                (E->wait_ms - w0);
+  return rc;
+}
+
+void lob_engine_times(const lob_engine* E, double* host_ms, double* wait_ms, long long* rounds) {
+  *host_ms = E->host_ms;
+  *wait_ms = E->wait_ms;
+  *rounds = E->rounds;
+}
+
+static int engine_round(lob_engine* E, std::vector<lob_ltask*>& done) {
   E->joff = 0;
   E->rounds++;
   std::vector<lob_ltask*> iter, start;  // iterating this round; (re)starting with H X
@@ -645,9 +672,8 @@ int lob_engine_round(lob_engine* E, std::vector<lob_ltask*>& done) {
   std::vector<lob_bjob> j_pcholg;
   for (lob_ltask* t : iter) {
     if (!t->haveP) continue;
-    const int nch = lob_gram_chunks(t->n_act, t->na, t->na);
     j_pcholg.push_back(gram_job(t, t->S + t->nb + t->na, t->na, t->S + t->nb + t->na, t->na, t->MmP,
-                                t->gw + (size_t)nch * t->ldS * t->ldS, 1));
+                                t->gw + t->gw_half, 1));
     lob_bjob r = rr_job(t, t->na, t->MmP, t->MmP, t->thP, t->CcP, 1);
     r.I0 = info_dev(E, t, 1);
     j_rr1.push_back(r);
@@ -704,9 +730,8 @@ int lob_engine_round(lob_engine* E, std::vector<lob_ltask*>& done) {
   }
   LOB_TRY(copy_batch(E, j_post));
   for (lob_ltask* t : rr_tasks) {
-    const int nch = lob_gram_chunks(t->n_act, t->m, t->m);
     j_g.push_back(gram_job(t, t->S, t->m, t->HS, t->m, t->G, t->gw, 1));
-    j_g.push_back(gram_job(t, t->S, t->m, t->S, t->m, t->Mm, t->gw + (size_t)nch * t->ldS * t->ldS, 1));
+    j_g.push_back(gram_job(t, t->S, t->m, t->S, t->m, t->Mm, t->gw + t->gw_half, 1));
     lob_bjob r = rr_job(t, t->m, t->G, t->Mm, t->theta, t->Cc, 0);
     r.I0 = info_dev(E, t, 2);
     j_rr.push_back(r);
@@ -734,9 +759,8 @@ int lob_engine_round(lob_engine* E, std::vector<lob_ltask*>& done) {
         t->restarts++;
         t->pok = false;
         t->m = t->nb + t->na;
-        const int nch = lob_gram_chunks(t->n_act, t->m, t->m);
         j_g2.push_back(gram_job(t, t->S, t->m, t->HS, t->m, t->G, t->gw, 1));
-        j_g2.push_back(gram_job(t, t->S, t->m, t->S, t->m, t->Mm, t->gw + (size_t)nch * t->ldS * t->ldS, 1));
+        j_g2.push_back(gram_job(t, t->S, t->m, t->S, t->m, t->Mm, t->gw + t->gw_half, 1));
         lob_bjob r = rr_job(t, t->m, t->G, t->Mm, t->theta, t->Cc, 0);
         r.I0 = info_dev(E, t, 2);
         j_rr2.push_back(r);

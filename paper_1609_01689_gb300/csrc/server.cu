@@ -399,6 +399,11 @@ int lob_server_stats_get(const lob_server* s, lob_server_stats* out) {
   out->active = (int64_t)s->active.size();
   out->queued = (int64_t)s->queue.size();
   out->bytes_in_use = s->used;
+  if (s->E) {
+    long long r = 0;
+    lob_engine_times(s->E, &out->host_ms, &out->wait_ms, &r);
+    out->rounds = r;
+  }
   return LOB_OK;
 }
 

@@ -33,6 +33,19 @@ def test_spmm_integer_exact(nb, mode):
     assert np.array_equal(run(M, X, mode), oracle.spmm(H, X))
 
 
+@pytest.mark.parametrize("n,density,nb", [(600, 0.9, 16), (520, 0.45, 17), (1100, 0.12, 16)])
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_spmm_dense_tiles_integer_exact(n, density, nb, mode):
+    """Dense tiles: a tile spans several chunks of the column permutation, and one row or column
+    runs across many lane groups' segments of a chunk (carried partials)."""
+    import paper_1609_01689_gb300 as lob
+    rng = np.random.default_rng(n + nb)
+    H = random_upper(n, density, rng, integer=True)
+    X = rng.integers(-4, 5, (n, nb)).astype(np.float64)
+    M = lob.Matrix(H.n, H.rows, H.cols, H.vals)
+    assert np.array_equal(run(M, X, mode), oracle.spmm(H, X))
+
+
 @pytest.mark.parametrize("n,nb", [(1, 1), (255, 4), (256, 8), (257, 16), (3000, 16), (5000, 2)])
 @pytest.mark.parametrize("mode", ["fp64", "mixed"])
 def test_spmm_random_within_bound(n, nb, mode):
