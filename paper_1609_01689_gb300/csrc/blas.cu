@@ -43,25 +43,55 @@ struct Ar<true> {
   __device__ static double out(acc_t a) { df_renorm(a.hi, a.lo); return df_join_int(a.hi, a.lo); }
 };
 
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
 // U = tile edge / 16 outputs per thread along each dimension (1, 2 or 3): small Gram matrices
 // (16 x 16, 32 x 32) use a matching tile instead of a zero-padded 48 x 48 one.
 // TRI: only the upper triangle of a symmetric result is needed -- the thread skips its
 // sub-blocks below the diagonal (3 of 9 at U = 3); the reduction mirrors them.
+// Rows arrive by cp.async into a double-buffered raw FP64 stage (Ra, Rb): the next RB rows load
+// while the current ones are converted (to double-float for DF) and multiplied.
 template <bool DF, int U, bool TRI>
 __device__ __forceinline__ void gram_body(int64_t r0, int64_t r1, int p, const double* __restrict__ A, int lda, int q,
                                           const double* __restrict__ B, int ldb, int a0, int b0,
                                           typename Ar<DF>::in_t (*As)[16 * U], typename Ar<DF>::in_t (*Bs)[16 * U],
+                                          double (*Ra)[RB][16 * U], double (*Rb)[RB][16 * U],
                                           typename Ar<DF>::acc_t (&acc)[U][U]) {
   using R = Ar<DF>;
   using in_t = typename R::in_t;
   constexpr int TGU = 16 * U;
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  for (int64_t rr = r0; rr < r1; rr += RB) {
+  auto fetch = [&](int64_t rr, int buf) {
     for (int idx = tid; idx < RB * TGU; idx += 256) {
       const int i = idx / TGU, a = idx % TGU;
       const int64_t r = rr + i;
-      As[i][a] = (r < r1 && a0 + a < p) ? R::load(A[r * lda + a0 + a]) : R::zero_in();
-      Bs[i][a] = (r < r1 && b0 + a < q) ? R::load(B[r * ldb + b0 + a]) : R::zero_in();
+      if (r < r1 && a0 + a < p) cp_async8(&Ra[buf][i][a], &A[r * lda + a0 + a]);
+      else Ra[buf][i][a] = 0.0;
+      if (r < r1 && b0 + a < q) cp_async8(&Rb[buf][i][a], &B[r * ldb + b0 + a]);
+      else Rb[buf][i][a] = 0.0;
+    }
+    cp_async_commit();
+  };
+  if (r0 < r1) fetch(r0, 0);
+  int buf = 0;
+  for (int64_t rr = r0; rr < r1; rr += RB, buf ^= 1) {
+    if (rr + RB < r1) {
+      fetch(rr + RB, buf ^ 1);
+      cp_async_wait_1();
+    } else {
+      cp_async_wait_all();
+    }
+    __syncthreads();  // this step's rows have landed; the previous step's products are done
+    for (int idx = tid; idx < RB * TGU; idx += 256) {
+      const int i = idx / TGU, a = idx % TGU;
+      As[i][a] = R::load(Ra[buf][i][a]);
+      Bs[i][a] = R::load(Rb[buf][i][a]);
     }
     __syncthreads();
 #pragma unroll 4
@@ -75,7 +105,6 @@ __device__ __forceinline__ void gram_body(int64_t r0, int64_t r1, int p, const d
         for (int v = 0; v < U; v++)
           if (!TRI || u <= v) R::mac(acc[u][v], av[u], bv[v]);
     }
-    __syncthreads();
   }
 }
 
@@ -88,6 +117,8 @@ __global__ void __launch_bounds__(256) k_gram(int64_t n, int p, const double* __
   constexpr int TGU = 16 * U;
   __shared__ in_t As[RB][TGU];
   __shared__ in_t Bs[RB][TGU];
+  __shared__ __align__(16) double Ra[2][RB][TGU];
+  __shared__ __align__(16) double Rb[2][RB][TGU];
   const int chunk = blockIdx.x;
   if (sym && blockIdx.y > blockIdx.z) return;  // below-diagonal tile: mirrored by the reduction
   const int a0 = blockIdx.y * TGU, b0 = blockIdx.z * TGU;
@@ -100,8 +131,8 @@ __global__ void __launch_bounds__(256) k_gram(int64_t n, int p, const double* __
   for (int i = 0; i < U; i++)
 #pragma unroll
     for (int j = 0; j < U; j++) R::zero(acc[i][j]);
-  if (tri) gram_body<DF, U, true>(r0, r1, p, A, lda, q, B, ldb, a0, b0, As, Bs, acc);
-  else gram_body<DF, U, false>(r0, r1, p, A, lda, q, B, ldb, a0, b0, As, Bs, acc);
+  if (tri) gram_body<DF, U, true>(r0, r1, p, A, lda, q, B, ldb, a0, b0, As, Bs, Ra, Rb, acc);
+  else gram_body<DF, U, false>(r0, r1, p, A, lda, q, B, ldb, a0, b0, As, Bs, Ra, Rb, acc);
 #pragma unroll
   for (int u = 0; u < U; u++)
 #pragma unroll
@@ -146,15 +177,16 @@ __device__ __forceinline__ void lincomb_body(int64_t n, int p, const double* __r
   using in_t = typename R::in_t;
   constexpr int RT = 256 / QT;             // rows per pass of the CTA's threads
   constexpr int RPC = RT * RM;             // rows per CTA
-  in_t* As = reinterpret_cast<in_t*>(sm);  // [RPC][p]
-  in_t* Cs = As + RPC * p;                 // [p][QT]
+  const int lp = p | 1;                    // odd row stride: the warp's rows fall in different banks
+  in_t* As = reinterpret_cast<in_t*>(sm);  // [RPC][lp]
+  in_t* Cs = As + RPC * lp;                // [p][QT]
   const int64_t r0 = rb * RPC;
   const int j0 = cb * QT;
   const int tid = threadIdx.x, rl = tid / QT, j = tid % QT;
   for (int idx = tid; idx < RPC * p; idx += 256) {
     const int i = idx / p, a = idx % p;
     const int64_t r = r0 + i;
-    As[idx] = r < n ? R::load(A[r * lda + a]) : R::zero_in();
+    As[i * lp + a] = r < n ? R::load(A[r * lda + a]) : R::zero_in();
   }
   for (int idx = tid; idx < QT * p; idx += 256) {
     const int a = idx / QT, jj = idx % QT;
@@ -172,7 +204,7 @@ __device__ __forceinline__ void lincomb_body(int64_t n, int p, const double* __r
   for (int a = 0; a < p; a++) {
     const in_t c = Cs[a * QT + j];
 #pragma unroll
-    for (int u = 0; u < RM; u++) R::mac(acc[u], As[(rl + RT * u) * p + a], c);
+    for (int u = 0; u < RM; u++) R::mac(acc[u], As[(rl + RT * u) * lp + a], c);
   }
 #pragma unroll
   for (int u = 0; u < RM; u++) {
@@ -218,6 +250,8 @@ __global__ void __launch_bounds__(256) k_gram_batch(const lob_bjob* __restrict__
   constexpr int TGU = 16 * U;
   __shared__ in_t As[RB][TGU];
   __shared__ in_t Bs[RB][TGU];
+  __shared__ __align__(16) double Ra[2][RB][TGU];
+  __shared__ __align__(16) double Rb[2][RB][TGU];
   const lob_bjob& j = jobs[find_job(jobs, njobs, blockIdx.x)];
   const int chunk = (int)((int64_t)blockIdx.x - j.cta_begin);
   const int64_t rpc = (j.n + j.x0 - 1) / j.x0;
@@ -229,8 +263,8 @@ __global__ void __launch_bounds__(256) k_gram_batch(const lob_bjob* __restrict__
   for (int a = 0; a < U; a++)
 #pragma unroll
     for (int b = 0; b < U; b++) R::zero(acc[a][b]);
-  if (j.x1) gram_body<DF, U, true>(r0, r1, j.p, j.A, j.lda, j.q, j.B, j.ldb, 0, 0, As, Bs, acc);
-  else gram_body<DF, U, false>(r0, r1, j.p, j.A, j.lda, j.q, j.B, j.ldb, 0, 0, As, Bs, acc);
+  if (j.x1) gram_body<DF, U, true>(r0, r1, j.p, j.A, j.lda, j.q, j.B, j.ldb, 0, 0, As, Bs, Ra, Rb, acc);
+  else gram_body<DF, U, false>(r0, r1, j.p, j.A, j.lda, j.q, j.B, j.ldb, 0, 0, As, Bs, Ra, Rb, acc);
   const int pq = j.p * j.q;
 #pragma unroll
   for (int u = 0; u < U; u++)
@@ -370,11 +404,11 @@ __global__ void k_gram_reduce_batch(const lob_bjob* __restrict__ jobs, int njobs
   if (lane == 0) j.Y[e] = s;
 }
 
-// Row chunks of one Gram product: one full wave of CTAs over all output tiles -- 8 CTAs per SM
-// for 16 x 16 tiles (32 registers a thread), 4 for the larger ones (register-limited) -- with at
-// least 64 rows each.
+// Row chunks of one Gram product: one full wave of CTAs over all output tiles -- as many CTAs as
+// fit on an SM by registers (8 for 16 x 16 tiles, 6 for 32 x 32, 5 for 48 x 48) -- with at least
+// 64 rows each.
 inline int nchunks_for(int64_t n, int tiles, int edge) {
-  int64_t c = ((edge == 16 ? 8 : 4) * 152 + tiles - 1) / tiles;
+  int64_t c = ((edge == 16 ? 8 : (edge == 32 ? 6 : 5)) * 152 + tiles - 1) / tiles;
   int64_t maxc = (n + 63) / 64;
   if (c > maxc) c = maxc;
   return (int)(c < 1 ? 1 : c);
@@ -435,7 +469,7 @@ int lob_lincomb_launch(int64_t n, int p, const double* A, int lda, int q, const 
   // four rows a thread when the CTA's rows of A fit comfortably in shared memory, else one
   const int RM = p <= 64 ? 4 : 1;
   dim3 grid((unsigned)((n + 16 * RM - 1) / (16 * RM)), (q + 15) / 16);
-  const size_t smem = (16ull * RM + 16) * p * (mode == LOB_SPMM_MIXED ? sizeof(float2) : sizeof(double));
+  const size_t smem = (16ull * RM * (p | 1) + 16ull * p) * (mode == LOB_SPMM_MIXED ? sizeof(float2) : sizeof(double));
   auto go = [&](auto kern) -> int {
     LOB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     (kern<<<grid, 256, smem, st>>>(n, p, A, lda, q, C, Y, ldy, D, ldd), LOB_LAUNCHED());
@@ -501,7 +535,7 @@ static int lincomb_batch_go(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, 
   }
   if (ctas == 0) return LOB_OK;
   LOB_CUDA(cudaMemcpyAsync(jobs_dev, jobs_host, njobs * sizeof(lob_bjob), cudaMemcpyHostToDevice, st));
-  const size_t smem = (size_t)(RPC + QT) * pmax * (DF ? sizeof(float2) : sizeof(double));
+  const size_t smem = ((size_t)RPC * (pmax | 1) + (size_t)QT * pmax) * (DF ? sizeof(float2) : sizeof(double));
   LOB_CUDA(cudaFuncSetAttribute(k_lincomb_batch<DF, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   (k_lincomb_batch<DF, QT><<<(unsigned)ctas, 256, smem, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
   LOB_CUDA(cudaGetLastError());

@@ -92,7 +92,7 @@ __device__ __forceinline__ int rr_index(int pos, int round, int mp) {
 // Cyclic Jacobi on A (m x m, symmetric), accumulating the rotations into V. cs_c, cs_s, pr_p,
 // pr_q hold two rounds of 96 pairs each.
 template <typename E>
-__device__ void jacobi_blocks(int m, E* A, E* V, double stop_ratio, E* cs_c, E* cs_s, int* pr_p, int* pr_q,
+__device__ void jacobi_blocks(int m, int ld, E* A, E* V, double stop_ratio, E* cs_c, E* cs_s, int* pr_p, int* pr_q,
                               double* red, double* s_off, double* s_fro) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int mm = m * m;
@@ -100,19 +100,20 @@ __device__ void jacobi_blocks(int m, E* A, E* V, double stop_ratio, E* cs_c, E* 
   int pend = -1;  // buffer of the round whose V rotations are still to be applied
   auto rotate_v = [&](int b, int t0, int ts) {
     for (int e = t0; e < np * m; e += ts) {
-      const int k = e / m, row = e % m;
+      const int row = e / np, k = e % np;  // neighbouring threads: one row, neighbouring pairs
       const int q = pr_q[b * 96 + k];
       if (q >= m || !nonzero(cs_s[b * 96 + k])) continue;
-      rot2(V[row * m + pr_p[b * 96 + k]], V[row * m + q], cs_c[b * 96 + k], cs_s[b * 96 + k]);
+      rot2(V[row * ld + pr_p[b * 96 + k]], V[row * ld + q], cs_c[b * 96 + k], cs_s[b * 96 + k]);
     }
   };
   int rcount = 0;
   for (int sweep = 0; sweep < 40; sweep++) {
     double off = 0.0, fro = 0.0;
     for (int e = tid; e < mm; e += nt) {
-      const double x = hi64(A[e]);
+      const int i = e / m, j = e % m;
+      const double x = hi64(A[i * ld + j]);
       fro += x * x;
-      if (e / m != e % m) off += x * x;
+      if (i != j) off += x * x;
     }
     for (int o = 16; o > 0; o >>= 1) { off += __shfl_down_sync(0xFFFFFFFFu, off, o); fro += __shfl_down_sync(0xFFFFFFFFu, fro, o); }
     if (tid % 32 == 0) { red[tid / 32] = off; red[32 + tid / 32] = fro; }
@@ -135,7 +136,7 @@ __device__ void jacobi_blocks(int m, E* A, E* V, double stop_ratio, E* cs_c, E* 
           int p = rr_index(k, round, mp), q = rr_index(mp - 1 - k, round, mp);
           if (p > q) { const int t = p; p = q; q = t; }
           E c = ident_one(E{}), sn = ident_zero(E{});
-          if (q < m) jac_angle(A[p * m + p], A[q * m + q], A[p * m + q], c, sn);
+          if (q < m) jac_angle(A[p * ld + p], A[q * ld + q], A[p * ld + q], c, sn);
           pp[k] = p; qq[k] = q; cc[k] = c; ss[k] = sn;
         }
       } else if (pend >= 0) {
@@ -149,21 +150,21 @@ __device__ void jacobi_blocks(int m, E* A, E* V, double stop_ratio, E* cs_c, E* 
         tri_index(bb, np, k1, k2);
         const int p1 = pp[k1], q1 = qq[k1], p2 = pp[k2], q2 = qq[k2];
         const bool r1 = q1 < m, r2 = q2 < m;  // second index valid (not the dummy)
-        E a11 = A[p1 * m + p2];
-        E a12 = r2 ? A[p1 * m + q2] : ident_zero(E{});
-        E a21 = r1 ? A[q1 * m + p2] : ident_zero(E{});
-        E a22 = (r1 && r2) ? A[q1 * m + q2] : ident_zero(E{});
+        E a11 = A[p1 * ld + p2];
+        E a12 = r2 ? A[p1 * ld + q2] : ident_zero(E{});
+        E a21 = r1 ? A[q1 * ld + p2] : ident_zero(E{});
+        E a22 = (r1 && r2) ? A[q1 * ld + q2] : ident_zero(E{});
         if (r1 && nonzero(ss[k1])) { rot2(a11, a21, cc[k1], ss[k1]); rot2(a12, a22, cc[k1], ss[k1]); }
         if (r2 && nonzero(ss[k2])) { rot2(a11, a12, cc[k2], ss[k2]); rot2(a21, a22, cc[k2], ss[k2]); }
-        A[p1 * m + p2] = a11;
-        if (r2) A[p1 * m + q2] = a12;
-        if (r1) A[q1 * m + p2] = a21;
-        if (r1 && r2) A[q1 * m + q2] = a22;
+        A[p1 * ld + p2] = a11;
+        if (r2) A[p1 * ld + q2] = a12;
+        if (r1) A[q1 * ld + p2] = a21;
+        if (r1 && r2) A[q1 * ld + q2] = a22;
         if (k1 != k2) {
-          A[p2 * m + p1] = a11;
-          if (r2) A[q2 * m + p1] = a12;
-          if (r1) A[p2 * m + q1] = a21;
-          if (r1 && r2) A[q2 * m + q1] = a22;
+          A[p2 * ld + p1] = a11;
+          if (r2) A[q2 * ld + p1] = a12;
+          if (r1) A[p2 * ld + q1] = a21;
+          if (r1 && r2) A[q2 * ld + q1] = a22;
         }
       }
       __syncthreads();
@@ -183,10 +184,11 @@ __device__ __forceinline__ void rr_body(int m, const double* __restrict__ G, con
                                         double* __restrict__ theta, double* __restrict__ C,
                                         int32_t* __restrict__ info, double* __restrict__ work, int chol_only,
                                         unsigned char* rr_sm) {
+  const int ld = SMEM ? m + 1 : m;  // padded rows in shared memory: column walks hit distinct banks
   double* base = SMEM ? reinterpret_cast<double*>(rr_sm) : work;
   double* A = base;          // m x m
-  double* L = base + m * m;  // m x m, lower Cholesky factor
-  double* V = L + m * m;     // m x m, eigenvectors
+  double* L = base + m * ld;  // m x m, lower Cholesky factor
+  double* V = L + m * ld;    // m x m, eigenvectors
   __shared__ double cs_c[192], cs_s[192];
   __shared__ int pr_p[192], pr_q[192];
   __shared__ double red[64];
@@ -199,9 +201,9 @@ __device__ __forceinline__ void rr_body(int m, const double* __restrict__ G, con
   for (int e = tid; e < mm; e += nt) {
     const int i = e / m, j = e % m;
     const int a = i < j ? i : j, b = i < j ? j : i;
-    A[e] = G[a * m + b];
-    L[e] = Mi[a * m + b];
-    V[e] = (i == j) ? 1.0 : 0.0;
+    A[i * ld + j] = G[a * m + b];
+    L[i * ld + j] = Mi[a * m + b];
+    V[i * ld + j] = (i == j) ? 1.0 : 0.0;
   }
   if (tid == 0) s_fail = 0;
   __syncthreads();
@@ -209,19 +211,19 @@ __device__ __forceinline__ void rr_body(int m, const double* __restrict__ G, con
   // 1. right-looking Cholesky in place on L (lower part)
   for (int j = 0; j < m; j++) {
     if (tid == 0) {
-      const double d = L[j * m + j];
+      const double d = L[j * ld + j];
       if (!(d > 0.0)) s_fail = j + 1;
-      else L[j * m + j] = sqrt(d);
+      else L[j * ld + j] = sqrt(d);
     }
     __syncthreads();
     if (s_fail) break;
-    const double ljj = L[j * m + j];
-    for (int i = j + 1 + tid; i < m; i += nt) L[i * m + j] /= ljj;
+    const double ljj = L[j * ld + j];
+    for (int i = j + 1 + tid; i < m; i += nt) L[i * ld + j] /= ljj;
     __syncthreads();
     const int rem = m - j - 1;
     for (int e = tid; e < rem * rem; e += nt) {
       const int i = j + 1 + e / rem, k = j + 1 + e % rem;
-      if (k <= i) L[i * m + k] -= L[i * m + j] * L[k * m + j];
+      if (k <= i) L[i * ld + k] -= L[i * ld + j] * L[k * ld + j];
     }
     __syncthreads();
   }
@@ -234,8 +236,8 @@ __device__ __forceinline__ void rr_body(int m, const double* __restrict__ G, con
       theta[j] = 1.0;
       for (int i = m - 1; i >= 0; i--) {
         double s = (i == j) ? 1.0 : 0.0;
-        for (int t = i + 1; t < m; t++) s -= L[t * m + i] * C[t * m + j];
-        C[i * m + j] = s / L[i * m + i];
+        for (int t = i + 1; t < m; t++) s -= L[t * ld + i] * C[t * m + j];
+        C[i * m + j] = s / L[i * ld + i];
       }
     }
     if (tid == 0) *info = 0;
@@ -244,44 +246,44 @@ __device__ __forceinline__ void rr_body(int m, const double* __restrict__ G, con
   // 2a. A <- L^{-1} A: forward substitution, one column per thread
   for (int c = tid; c < m; c += nt)
     for (int i = 0; i < m; i++) {
-      double s = A[i * m + c];
-      for (int t = 0; t < i; t++) s -= L[i * m + t] * A[t * m + c];
-      A[i * m + c] = s / L[i * m + i];
+      double s = A[i * ld + c];
+      for (int t = 0; t < i; t++) s -= L[i * ld + t] * A[t * ld + c];
+      A[i * ld + c] = s / L[i * ld + i];
     }
   __syncthreads();
   // 2b. A <- A L^{-T}: forward substitution on each row
   for (int r = tid; r < m; r += nt)
     for (int i = 0; i < m; i++) {
-      double s = A[r * m + i];
-      for (int t = 0; t < i; t++) s -= L[i * m + t] * A[r * m + t];
-      A[r * m + i] = s / L[i * m + i];
+      double s = A[r * ld + i];
+      for (int t = 0; t < i; t++) s -= L[i * ld + t] * A[r * ld + t];
+      A[r * ld + i] = s / L[i * ld + i];
     }
   __syncthreads();
   for (int e = tid; e < mm; e += nt) {
     const int i = e / m, j = e % m;
     if (i < j) {
-      const double s = 0.5 * (A[i * m + j] + A[j * m + i]);
-      A[i * m + j] = s;
-      A[j * m + i] = s;
+      const double s = 0.5 * (A[i * ld + j] + A[j * ld + i]);
+      A[i * ld + j] = s;
+      A[j * ld + i] = s;
     }
   }
   __syncthreads();
 
   // 3. cyclic Jacobi (round-robin order, 2x2-block updates)
-  jacobi_blocks<double>(m, A, V, 1e-30, cs_c, cs_s, pr_p, pr_q, red, &s_off, &s_fro);
+  jacobi_blocks<double>(m, ld, A, V, 1e-30, cs_c, cs_s, pr_p, pr_q, red, &s_off, &s_fro);
   // 4. rank sort (ties by index), C = L^{-T} V in the sorted order
   for (int j = tid; j < m; j += nt) {
-    const double wj = A[j * m + j];
+    const double wj = A[j * ld + j];
     int rank = 0;
     for (int i = 0; i < m; i++) {
-      const double wi = A[i * m + i];
+      const double wi = A[i * ld + i];
       rank += (wi < wj) || (wi == wj && i < j);
     }
     theta[rank] = wj;
     for (int i = m - 1; i >= 0; i--) {
-      double s = V[i * m + j];
-      for (int t = i + 1; t < m; t++) s -= L[t * m + i] * C[t * m + rank];
-      C[i * m + rank] = s / L[i * m + i];
+      double s = V[i * ld + j];
+      for (int t = i + 1; t < m; t++) s -= L[t * ld + i] * C[t * m + rank];
+      C[i * m + rank] = s / L[i * ld + i];
     }
   }
   if (tid == 0) *info = 0;
@@ -297,9 +299,10 @@ __device__ __forceinline__ void rr_body_df(int m, const double* __restrict__ G, 
                                            double* __restrict__ theta, double* __restrict__ C,
                                            int32_t* __restrict__ info, double* __restrict__ work, int chol_only,
                                            unsigned char* rr_sm) {
+  const int ld = SMEM ? m + 1 : m;  // padded rows in shared memory: column walks hit distinct banks
   d2* A = SMEM ? reinterpret_cast<d2*>(rr_sm) : reinterpret_cast<d2*>(work);
-  d2* L = A + m * m;
-  d2* V = L + m * m;
+  d2* L = A + m * ld;
+  d2* V = L + m * ld;
   __shared__ d2 cs_c[192], cs_s[192];
   __shared__ int pr_p[192], pr_q[192];
   __shared__ d2 inv[192];
@@ -311,36 +314,36 @@ __device__ __forceinline__ void rr_body_df(int m, const double* __restrict__ G, 
   for (int e = tid; e < mm; e += nt) {
     const int i = e / m, j = e % m;
     const int a = i < j ? i : j, b = i < j ? j : i;
-    A[e] = d2_from(G[a * m + b]);
-    L[e] = d2_from(Mi[a * m + b]);
-    V[e] = d2{(i == j) ? 1.f : 0.f, 0.f};
+    A[i * ld + j] = d2_from(G[a * m + b]);
+    L[i * ld + j] = d2_from(Mi[a * m + b]);
+    V[i * ld + j] = d2{(i == j) ? 1.f : 0.f, 0.f};
   }
   if (tid == 0) s_fail = 0;
   __syncthreads();
   // 1. Cholesky (right-looking); inv[j] = 1 / L_jj
   for (int j = 0; j < m; j++) {
     if (tid == 0) {
-      const d2 d = d2_norm(L[j * m + j]);
+      const d2 d = d2_norm(L[j * ld + j]);
       if (!(d.hi > 0.f)) s_fail = j + 1;
       else {
         const d2 ri = d2_rsqrt(d);  // 1 / sqrt(d)
-        L[j * m + j] = d2_mul(d, ri);
+        L[j * ld + j] = d2_mul(d, ri);
         inv[j] = ri;
       }
     }
     __syncthreads();
     if (s_fail) break;
     const d2 ij = inv[j];
-    for (int i = j + 1 + tid; i < m; i += nt) L[i * m + j] = d2_mul(L[i * m + j], ij);
+    for (int i = j + 1 + tid; i < m; i += nt) L[i * ld + j] = d2_mul(L[i * ld + j], ij);
     __syncthreads();
     const int rem = m - j - 1;
     for (int e = tid; e < rem * rem; e += nt) {
       const int i = j + 1 + e / rem, k = j + 1 + e % rem;
       if (k <= i) {
-        d2 x = L[i * m + k];
-        const d2 a = L[i * m + j], b = L[k * m + j];
+        d2 x = L[i * ld + k];
+        const d2 a = L[i * ld + j], b = L[k * ld + j];
         df_mac(x.hi, x.lo, -a.hi, -a.lo, b.hi, b.lo);
-        L[i * m + k] = d2_norm(x);
+        L[i * ld + k] = d2_norm(x);
       }
     }
     __syncthreads();
@@ -355,12 +358,12 @@ __device__ __forceinline__ void rr_body_df(int m, const double* __restrict__ G, 
       for (int i = m - 1; i >= 0; i--) {
         d2 s{(i == j) ? 1.f : 0.f, 0.f};
         for (int t = i + 1; t < m; t++) {
-          const d2 l = L[t * m + i], x = V[t * m + j];
+          const d2 l = L[t * ld + i], x = V[t * ld + j];
           df_mac(s.hi, s.lo, -l.hi, -l.lo, x.hi, x.lo);
         }
-        V[i * m + j] = d2_mul(d2_norm(s), inv[i]);
+        V[i * ld + j] = d2_mul(d2_norm(s), inv[i]);
       }
-      for (int i = 0; i < m; i++) C[i * m + j] = d2_to(V[i * m + j]);
+      for (int i = 0; i < m; i++) C[i * m + j] = d2_to(V[i * ld + j]);
     }
     if (tid == 0) *info = 0;
     return;
@@ -368,25 +371,25 @@ __device__ __forceinline__ void rr_body_df(int m, const double* __restrict__ G, 
   // 2a. A <- L^{-1} A (columns), 2b. A <- A L^{-T} (rows)
   for (int c = tid; c < m; c += nt)
     for (int i = 0; i < m; i++) {
-      d2 s = A[i * m + c];
-      for (int t = 0; t < i; t++) { const d2 l = L[i * m + t], a = A[t * m + c]; df_mac(s.hi, s.lo, -l.hi, -l.lo, a.hi, a.lo); }
-      A[i * m + c] = d2_mul(d2_norm(s), inv[i]);
+      d2 s = A[i * ld + c];
+      for (int t = 0; t < i; t++) { const d2 l = L[i * ld + t], a = A[t * ld + c]; df_mac(s.hi, s.lo, -l.hi, -l.lo, a.hi, a.lo); }
+      A[i * ld + c] = d2_mul(d2_norm(s), inv[i]);
     }
   __syncthreads();
   for (int r = tid; r < m; r += nt)
     for (int i = 0; i < m; i++) {
-      d2 s = A[r * m + i];
-      for (int t = 0; t < i; t++) { const d2 l = L[i * m + t], a = A[r * m + t]; df_mac(s.hi, s.lo, -l.hi, -l.lo, a.hi, a.lo); }
-      A[r * m + i] = d2_mul(d2_norm(s), inv[i]);
+      d2 s = A[r * ld + i];
+      for (int t = 0; t < i; t++) { const d2 l = L[i * ld + t], a = A[r * ld + t]; df_mac(s.hi, s.lo, -l.hi, -l.lo, a.hi, a.lo); }
+      A[r * ld + i] = d2_mul(d2_norm(s), inv[i]);
     }
   __syncthreads();
   for (int e = tid; e < mm; e += nt) {
     const int i = e / m, j = e % m;
     if (i < j) {
-      d2 s = d2_add(A[i * m + j], A[j * m + i]);
+      d2 s = d2_add(A[i * ld + j], A[j * ld + i]);
       s.hi *= 0.5f; s.lo *= 0.5f;  // exact
-      A[i * m + j] = s;
-      A[j * m + i] = s;
+      A[i * ld + j] = s;
+      A[j * ld + i] = s;
     }
   }
   __syncthreads();
@@ -394,26 +397,26 @@ __device__ __forceinline__ void rr_body_df(int m, const double* __restrict__ G, 
   // ~48 significant bits, so the off-diagonal part cannot fall much below 2^-46 of the whole;
   // stop at ||off|| <= 1e-10 ||A|| (quadratic convergence: the Ritz values then carry errors of
   // order ||off||^2 / gap, far below the FP64 target).
-  jacobi_blocks<d2>(m, A, V, 1e-20, cs_c, cs_s, pr_p, pr_q, red, &s_off, &s_fro);
+  jacobi_blocks<d2>(m, ld, A, V, 1e-20, cs_c, cs_s, pr_p, pr_q, red, &s_off, &s_fro);
   // 4. rank sort, C = L^{-T} V
   for (int j = tid; j < m; j += nt) {
-    const double wj = d2_to(A[j * m + j]);
+    const double wj = d2_to(A[j * ld + j]);
     int rank = 0;
     for (int i = 0; i < m; i++) {
-      const double wi = d2_to(A[i * m + i]);
+      const double wi = d2_to(A[i * ld + i]);
       rank += (wi < wj) || (wi == wj && i < j);
     }
     theta[rank] = wj;
     // back substitution in double-float; column `rank` of C kept in V's column j
     for (int i = m - 1; i >= 0; i--) {
-      d2 s = V[i * m + j];
+      d2 s = V[i * ld + j];
       for (int t = i + 1; t < m; t++) {
-        const d2 l = L[t * m + i], x = V[t * m + j];
+        const d2 l = L[t * ld + i], x = V[t * ld + j];
         df_mac(s.hi, s.lo, -l.hi, -l.lo, x.hi, x.lo);
       }
-      V[i * m + j] = d2_mul(d2_norm(s), inv[i]);
+      V[i * ld + j] = d2_mul(d2_norm(s), inv[i]);
     }
-    for (int i = 0; i < m; i++) C[i * m + rank] = d2_to(V[i * m + j]);
+    for (int i = 0; i < m; i++) C[i * m + rank] = d2_to(V[i * ld + j]);
   }
   if (tid == 0) *info = 0;
 }
@@ -451,7 +454,7 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_batch(const lob_bjob* __restr
 
 // The three m x m matrices live in shared memory when they fit (m <= 64), else in the
 // caller's global workspace (L1-cached).
-static size_t rr_smem_bytes(int m) { return 3ull * m * m * 8; }
+static size_t rr_smem_bytes(int m) { return 3ull * m * (m + 1) * 8; }  // rows padded to m + 1
 static const size_t RR_SMEM_MAX = 200 * 1024;
 
 // Threads for order m: one per 2x2 block of the upper triangle of a Jacobi round, 128 to 1,024 --

@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(Cfg<MIXED, NB>::THREADS, Cfg<MIXED, NB>::MINB)
 // group g owns in-tile rows/columns g, g + NG, ...; each lane holds VW = 2 vector columns.
 template <int NB>
 struct CfgDF {
-  static constexpr int VW = 2;
+  static constexpr int VW = 2;  // vector columns per lane (four measured slower: register-limited at 1,024 threads)
   static constexpr int G = NB / VW;
   static constexpr int THREADS = (LOB_TILE * G) < 1024 ? (LOB_TILE * G) : 1024;
   static constexpr int NG = THREADS / G;
@@ -483,10 +483,13 @@ __global__ void __launch_bounds__(CfgDF<NB>::THREADS, 1)
         const int s = PR[idx], e = PR[idx + 1];
         for (int i = s; i < e; i++) {
           const int c = (int)(RCs[i] & 0xFFFFu);
-          const float4 x = *reinterpret_cast<const float4*>(&xj[c * NB + gl * VW]);  // (h0, l0, h1, l1)
           const float vh = VH[i], vl = VL[i];
-          df_mac(th[a][0], tlo[a][0], vh, vl, x.x, x.y);
-          df_mac(th[a][1], tlo[a][1], vh, vl, x.z, x.w);
+#pragma unroll
+          for (int h = 0; h < VW; h += 2) {
+            const float4 x = *reinterpret_cast<const float4*>(&xj[c * NB + gl * VW + h]);  // (h0, l0, h1, l1)
+            df_mac(th[a][h], tlo[a][h], vh, vl, x.x, x.y);
+            df_mac(th[a][h + 1], tlo[a][h + 1], vh, vl, x.z, x.w);
+          }
         }
       }
       {
@@ -495,10 +498,13 @@ __global__ void __launch_bounds__(CfgDF<NB>::THREADS, 1)
           const int q = PM[i] & (CH - 1);
           const int r = (int)(RCs[q] >> 16);
           if (diag && r == idx) continue;
-          const float4 x = *reinterpret_cast<const float4*>(&XI[r * NB + gl * VW]);
           const float vh = VH[q], vl = VL[q];
-          df_mac(chh[a][0], clo[a][0], vh, vl, x.x, x.y);
-          df_mac(chh[a][1], clo[a][1], vh, vl, x.z, x.w);
+#pragma unroll
+          for (int h = 0; h < VW; h += 2) {
+            const float4 x = *reinterpret_cast<const float4*>(&XI[r * NB + gl * VW + h]);
+            df_mac(chh[a][h], clo[a][h], vh, vl, x.x, x.y);
+            df_mac(chh[a][h + 1], clo[a][h + 1], vh, vl, x.z, x.w);
+          }
         }
       }
     }
