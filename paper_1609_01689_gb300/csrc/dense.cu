@@ -35,6 +35,15 @@ __device__ __forceinline__ void rot2(double& x, double& y, double c, double s) {
   y = v;
 }
 __device__ __forceinline__ void rot2(d2& x, d2& y, d2 c, d2 s) { d2_rot(x, y, c, s); }
+__device__ __forceinline__ void rot2(float& x, float& y, float c, float s) {
+  const float u = fmaf(c, x, -s * y), v = fmaf(s, x, c * y);
+  x = u;
+  y = v;
+}
+__device__ __forceinline__ double hi64(float x) { return (double)x; }
+__device__ __forceinline__ bool nonzero(float x) { return x != 0.f; }
+__device__ __forceinline__ float ident_one(float) { return 1.f; }
+__device__ __forceinline__ float ident_zero(float) { return 0.f; }
 __device__ __forceinline__ double hi64(double x) { return x; }
 __device__ __forceinline__ double hi64(d2 x) { return d2_hi64(x); }
 __device__ __forceinline__ bool nonzero(double x) { return x != 0.0; }
@@ -53,6 +62,14 @@ __device__ __forceinline__ void jac_angle(double app, double aqq, double apq, do
   const double tau = (aqq - app) / (2.0 * apq);
   const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
   c = 1.0 / sqrt(1.0 + t * t);
+  s = t * c;
+}
+__device__ __forceinline__ void jac_angle(float app, float aqq, float apq, float& c, float& s) {
+  c = 1.f; s = 0.f;
+  if (apq == 0.f) return;
+  const float tau = (aqq - app) / (2.f * apq);
+  const float t = (tau >= 0.f ? 1.f : -1.f) / (fabsf(tau) + sqrtf(1.f + tau * tau));
+  c = rsqrtf(1.f + t * t);
   s = t * c;
 }
 __device__ __forceinline__ void jac_angle(d2 app, d2 aqq, d2 apq, d2& c, d2& s) {
@@ -303,14 +320,92 @@ __device__ __forceinline__ void rr_body_df(int m, const double* __restrict__ G, 
   d2* A = SMEM ? reinterpret_cast<d2*>(rr_sm) : reinterpret_cast<d2*>(work);
   d2* L = A + m * ld;
   d2* V = L + m * ld;
+  // shared-memory path only: a temporary, the Cholesky factor of V32^T V32, and V32 (FP32)
+  d2* T = V + m * ld;
+  d2* Lb = T + m * ld;
+  float* VF = reinterpret_cast<float*>(Lb + m * ld);
   __shared__ d2 cs_c[192], cs_s[192];
   __shared__ int pr_p[192], pr_q[192];
-  __shared__ d2 inv[192];
+  __shared__ d2 inv[192], inv2[192];
   __shared__ double red[64];
   __shared__ int s_fail;
   __shared__ double s_off, s_fro;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int mm = m * m;
+
+  // Cholesky (right-looking) of the symmetric Lm in place: lower factor, iv[j] = 1 / L_jj.
+  // Returns 0, or j + 1 for a non-positive pivot j.
+  auto cholesky = [&](d2* Lm, d2* iv) -> int {
+    if (tid == 0) s_fail = 0;
+    __syncthreads();
+    for (int j = 0; j < m; j++) {
+      if (tid == 0) {
+        const d2 d = d2_norm(Lm[j * ld + j]);
+        if (!(d.hi > 0.f)) s_fail = j + 1;
+        else {
+          const d2 ri = d2_rsqrt(d);  // 1 / sqrt(d)
+          Lm[j * ld + j] = d2_mul(d, ri);
+          iv[j] = ri;
+        }
+      }
+      __syncthreads();
+      if (s_fail) break;
+      const d2 ij = iv[j];
+      for (int i = j + 1 + tid; i < m; i += nt) Lm[i * ld + j] = d2_mul(Lm[i * ld + j], ij);
+      __syncthreads();
+      const int rem = m - j - 1;
+      for (int e = tid; e < rem * rem; e += nt) {
+        const int i = j + 1 + e / rem, k = j + 1 + e % rem;
+        if (k <= i) {
+          d2 x = Lm[i * ld + k];
+          const d2 a = Lm[i * ld + j], b = Lm[k * ld + j];
+          df_mac(x.hi, x.lo, -a.hi, -a.lo, b.hi, b.lo);
+          Lm[i * ld + k] = d2_norm(x);
+        }
+      }
+      __syncthreads();
+    }
+    return s_fail;
+  };
+  // Am <- Lm^{-1} Am Lm^{-T}, made exactly symmetric
+  auto congruence = [&](d2* Am, const d2* Lm, const d2* iv) {
+    for (int c = tid; c < m; c += nt)
+      for (int i = 0; i < m; i++) {
+        d2 sum = Am[i * ld + c];
+        for (int t = 0; t < i; t++) { const d2 l = Lm[i * ld + t], a = Am[t * ld + c]; df_mac(sum.hi, sum.lo, -l.hi, -l.lo, a.hi, a.lo); }
+        Am[i * ld + c] = d2_mul(d2_norm(sum), iv[i]);
+      }
+    __syncthreads();
+    for (int r = tid; r < m; r += nt)
+      for (int i = 0; i < m; i++) {
+        d2 sum = Am[r * ld + i];
+        for (int t = 0; t < i; t++) { const d2 l = Lm[i * ld + t], a = Am[r * ld + t]; df_mac(sum.hi, sum.lo, -l.hi, -l.lo, a.hi, a.lo); }
+        Am[r * ld + i] = d2_mul(d2_norm(sum), iv[i]);
+      }
+    __syncthreads();
+    for (int e = tid; e < mm; e += nt) {
+      const int i = e / m, j = e % m;
+      if (i < j) {
+        d2 sum = d2_add(Am[i * ld + j], Am[j * ld + i]);
+        sum.hi *= 0.5f; sum.lo *= 0.5f;  // exact
+        Am[i * ld + j] = sum;
+        Am[j * ld + i] = sum;
+      }
+    }
+    __syncthreads();
+  };
+  // column j of Lm^{-T} Src written to Dst (Dst may be Src)
+  auto back_sub = [&](const d2* Lm, const d2* iv, const d2* Src, d2* Dst, int j) {
+    for (int i = m - 1; i >= 0; i--) {
+      d2 sum = Src[i * ld + j];
+      for (int t = i + 1; t < m; t++) {
+        const d2 l = Lm[t * ld + i], x = Dst[t * ld + j];
+        df_mac(sum.hi, sum.lo, -l.hi, -l.lo, x.hi, x.lo);
+      }
+      Dst[i * ld + j] = d2_mul(d2_norm(sum), iv[i]);
+    }
+  };
+
   for (int e = tid; e < mm; e += nt) {
     const int i = e / m, j = e % m;
     const int a = i < j ? i : j, b = i < j ? j : i;
@@ -318,86 +413,95 @@ __device__ __forceinline__ void rr_body_df(int m, const double* __restrict__ G, 
     L[i * ld + j] = d2_from(Mi[a * m + b]);
     V[i * ld + j] = d2{(i == j) ? 1.f : 0.f, 0.f};
   }
-  if (tid == 0) s_fail = 0;
   __syncthreads();
-  // 1. Cholesky (right-looking); inv[j] = 1 / L_jj
-  for (int j = 0; j < m; j++) {
-    if (tid == 0) {
-      const d2 d = d2_norm(L[j * ld + j]);
-      if (!(d.hi > 0.f)) s_fail = j + 1;
-      else {
-        const d2 ri = d2_rsqrt(d);  // 1 / sqrt(d)
-        L[j * ld + j] = d2_mul(d, ri);
-        inv[j] = ri;
-      }
-    }
-    __syncthreads();
-    if (s_fail) break;
-    const d2 ij = inv[j];
-    for (int i = j + 1 + tid; i < m; i += nt) L[i * ld + j] = d2_mul(L[i * ld + j], ij);
-    __syncthreads();
-    const int rem = m - j - 1;
-    for (int e = tid; e < rem * rem; e += nt) {
-      const int i = j + 1 + e / rem, k = j + 1 + e % rem;
-      if (k <= i) {
-        d2 x = L[i * ld + k];
-        const d2 a = L[i * ld + j], b = L[k * ld + j];
-        df_mac(x.hi, x.lo, -a.hi, -a.lo, b.hi, b.lo);
-        L[i * ld + k] = d2_norm(x);
-      }
-    }
-    __syncthreads();
-  }
-  if (s_fail) {
-    if (tid == 0) *info = s_fail;
+  // 1. M = L L^T
+  const int fail = cholesky(L, inv);
+  if (fail) {
+    if (tid == 0) *info = fail;
     return;
   }
   if (chol_only) {  // Cholesky-QR: C = L^{-T}
     for (int j = tid; j < m; j += nt) {
       theta[j] = 1.0;
-      for (int i = m - 1; i >= 0; i--) {
-        d2 s{(i == j) ? 1.f : 0.f, 0.f};
-        for (int t = i + 1; t < m; t++) {
-          const d2 l = L[t * ld + i], x = V[t * ld + j];
-          df_mac(s.hi, s.lo, -l.hi, -l.lo, x.hi, x.lo);
-        }
-        V[i * ld + j] = d2_mul(d2_norm(s), inv[i]);
-      }
+      back_sub(L, inv, V, V, j);
       for (int i = 0; i < m; i++) C[i * m + j] = d2_to(V[i * ld + j]);
     }
     if (tid == 0) *info = 0;
     return;
   }
-  // 2a. A <- L^{-1} A (columns), 2b. A <- A L^{-T} (rows)
-  for (int c = tid; c < m; c += nt)
-    for (int i = 0; i < m; i++) {
-      d2 s = A[i * ld + c];
-      for (int t = 0; t < i; t++) { const d2 l = L[i * ld + t], a = A[t * ld + c]; df_mac(s.hi, s.lo, -l.hi, -l.lo, a.hi, a.lo); }
-      A[i * ld + c] = d2_mul(d2_norm(s), inv[i]);
+  // 2. A <- L^{-1} G L^{-T}
+  congruence(A, L, inv);
+  // 3. A = V diag(theta) V^T. Double-float carries ~48 significant bits, so the off-diagonal part
+  // cannot fall much below 2^-46 of the whole; the Jacobi sweeps stop at ||off|| <= 1e-10 ||A||
+  // (quadratic convergence: the Ritz values then carry errors of order ||off||^2 / gap).
+  if (!SMEM) {
+    jacobi_blocks<d2>(m, ld, A, V, 1e-20, cs_c, cs_s, pr_p, pr_q, red, &s_off, &s_fro);
+  } else {
+    // Two stages. (a) Cyclic Jacobi on an FP32 copy of A, to ||off|| <= 1e-5 ||A||, gives V32 with
+    // V32^T A V32 nearly diagonal -- most sweeps run at FP32 cost. (b) In double-float, with
+    // V32^T V32 = Lb Lb^T: A <- Lb^{-1} V32^T A V32 Lb^{-T}, an exact congruence by
+    // Q = V32 Lb^{-T} (Q^T Q = I), finished by Jacobi sweeps from V = I (one or two, as A starts
+    // nearly diagonal); the eigenvectors of the step-2 matrix are Q V.
+    float* F = reinterpret_cast<float*>(T);  // FP32 copy of A, in T's space until (b)
+    for (int e = tid; e < mm; e += nt) {
+      const int i = e / m, j = e % m;
+      F[i * ld + j] = __fadd_rn(A[i * ld + j].hi, A[i * ld + j].lo);
+      VF[i * ld + j] = (i == j) ? 1.f : 0.f;
     }
-  __syncthreads();
-  for (int r = tid; r < m; r += nt)
-    for (int i = 0; i < m; i++) {
-      d2 s = A[r * ld + i];
-      for (int t = 0; t < i; t++) { const d2 l = L[i * ld + t], a = A[r * ld + t]; df_mac(s.hi, s.lo, -l.hi, -l.lo, a.hi, a.lo); }
-      A[r * ld + i] = d2_mul(d2_norm(s), inv[i]);
+    __syncthreads();
+    jacobi_blocks<float>(m, ld, F, VF, 1e-10, reinterpret_cast<float*>(cs_c), reinterpret_cast<float*>(cs_s), pr_p,
+                         pr_q, red, &s_off, &s_fro);
+    // T = A V32 (double-float times FP32)
+    for (int e = tid; e < mm; e += nt) {
+      const int i = e / m, j = e % m;
+      float h = 0.f, l = 0.f;
+      for (int k = 0; k < m; k++) {
+        const d2 a = A[i * ld + k];
+        df_mac(h, l, a.hi, a.lo, VF[k * ld + j], 0.f);
+      }
+      T[i * ld + j] = d2_norm(d2{h, l});
     }
-  __syncthreads();
-  for (int e = tid; e < mm; e += nt) {
-    const int i = e / m, j = e % m;
-    if (i < j) {
-      d2 s = d2_add(A[i * ld + j], A[j * ld + i]);
-      s.hi *= 0.5f; s.lo *= 0.5f;  // exact
-      A[i * ld + j] = s;
-      A[j * ld + i] = s;
+    __syncthreads();
+    // upper triangles of A <- V32^T T and Lb <- V32^T V32, mirrored
+    for (int e = tid; e < mm; e += nt) {
+      const int i = e / m, j = e % m;
+      if (i > j) continue;
+      float h = 0.f, l = 0.f, bh = 0.f, bl = 0.f;
+      for (int k = 0; k < m; k++) {
+        const float vki = VF[k * ld + i];
+        const d2 t = T[k * ld + j];
+        df_mac(h, l, vki, 0.f, t.hi, t.lo);
+        df_mac(bh, bl, vki, 0.f, VF[k * ld + j], 0.f);
+      }
+      const d2 av = d2_norm(d2{h, l}), bv = d2_norm(d2{bh, bl});
+      A[i * ld + j] = av;
+      A[j * ld + i] = av;
+      Lb[i * ld + j] = bv;
+      Lb[j * ld + i] = bv;
+      V[i * ld + j] = d2{(i == j) ? 1.f : 0.f, 0.f};
+      V[j * ld + i] = d2{(i == j) ? 1.f : 0.f, 0.f};
     }
+    __syncthreads();
+    if (cholesky(Lb, inv2)) {  // V32 lost rank: cannot happen for a finite A
+      if (tid == 0) *info = m + 1;
+      return;
+    }
+    congruence(A, Lb, inv2);
+    jacobi_blocks<d2>(m, ld, A, V, 1e-20, cs_c, cs_s, pr_p, pr_q, red, &s_off, &s_fro);
+    // V <- V32 Lb^{-T} V
+    for (int j = tid; j < m; j += nt) back_sub(Lb, inv2, V, T, j);
+    __syncthreads();
+    for (int e = tid; e < mm; e += nt) {
+      const int i = e / m, j = e % m;
+      float h = 0.f, l = 0.f;
+      for (int k = 0; k < m; k++) {
+        const d2 t = T[k * ld + j];
+        df_mac(h, l, VF[i * ld + k], 0.f, t.hi, t.lo);
+      }
+      V[i * ld + j] = d2_norm(d2{h, l});
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  // 3. cyclic Jacobi (round-robin order, 2x2-block updates) in double-float. Double-float carries
-  // ~48 significant bits, so the off-diagonal part cannot fall much below 2^-46 of the whole;
-  // stop at ||off|| <= 1e-10 ||A|| (quadratic convergence: the Ritz values then carry errors of
-  // order ||off||^2 / gap, far below the FP64 target).
-  jacobi_blocks<d2>(m, ld, A, V, 1e-20, cs_c, cs_s, pr_p, pr_q, red, &s_off, &s_fro);
   // 4. rank sort, C = L^{-T} V
   for (int j = tid; j < m; j += nt) {
     const double wj = d2_to(A[j * ld + j]);
@@ -407,15 +511,7 @@ __device__ __forceinline__ void rr_body_df(int m, const double* __restrict__ G, 
       rank += (wi < wj) || (wi == wj && i < j);
     }
     theta[rank] = wj;
-    // back substitution in double-float; column `rank` of C kept in V's column j
-    for (int i = m - 1; i >= 0; i--) {
-      d2 s = V[i * ld + j];
-      for (int t = i + 1; t < m; t++) {
-        const d2 l = L[t * ld + i], x = V[t * ld + j];
-        df_mac(s.hi, s.lo, -l.hi, -l.lo, x.hi, x.lo);
-      }
-      V[i * ld + j] = d2_mul(d2_norm(s), inv[i]);
-    }
+    back_sub(L, inv, V, V, j);  // column `rank` of C kept in V's column j
     for (int i = 0; i < m; i++) C[i * m + rank] = d2_to(V[i * ld + j]);
   }
   if (tid == 0) *info = 0;
@@ -454,7 +550,10 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_batch(const lob_bjob* __restr
 
 // The three m x m matrices live in shared memory when they fit (m <= 64), else in the
 // caller's global workspace (L1-cached).
-static size_t rr_smem_bytes(int m) { return 3ull * m * (m + 1) * 8; }  // rows padded to m + 1
+// rows padded to m + 1; the double-float solve keeps five double-float matrices and one FP32 one
+static size_t rr_smem_bytes(int m, bool df = false) {
+  return (df ? 5ull * 8 + 4 : 3ull * 8) * m * (m + 1);
+}
 static const size_t RR_SMEM_MAX = 200 * 1024;
 
 // Threads for order m: one per 2x2 block of the upper triangle of a Jacobi round, 128 to 1,024 --
@@ -468,7 +567,7 @@ static int rr_threads(int m) {
 int lob_rr_launch_df(int m, const double* G, const double* M, double* theta, double* C, int32_t* info, double* work,
                      cudaStream_t st, int chol_only) {
   if (m < 1 || m > 192) return LOB_ERR_ARG;
-  const size_t sb = rr_smem_bytes(m);
+  const size_t sb = rr_smem_bytes(m, true);
   if (sb <= RR_SMEM_MAX) {
     LOB_CUDA(cudaFuncSetAttribute(k_rayleigh_ritz_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
     (k_rayleigh_ritz_df<true><<<1, rr_threads(m), sb, st>>>(m, G, M, theta, C, info, work, chol_only), LOB_LAUNCHED());
@@ -539,7 +638,7 @@ extern "C" int lob_rayleigh_ritz_noalloc(int32_t m, const double* G, const doubl
 int lob_rr_batch_launch(const lob_bjob* jobs_dev, int njobs, int mmax, int df, cudaStream_t st) {
   if (njobs <= 0) return LOB_OK;
   if (mmax < 1 || mmax > 192) return LOB_ERR_ARG;
-  const size_t sb = rr_smem_bytes(mmax);
+  const size_t sb = rr_smem_bytes(mmax, df != 0);
   const int nt = rr_threads(mmax);
   if (sb <= RR_SMEM_MAX) {
     if (df) {
