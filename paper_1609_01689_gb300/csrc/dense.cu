@@ -14,7 +14,7 @@
 
 namespace {
 
-constexpr int RR_THREADS = 1024;
+constexpr int RR_THREADS = 512;  // at most; rounds with more blocks loop
 
 
 // ---- cyclic Jacobi with 2x2-block updates (both kernels) ----
@@ -123,6 +123,32 @@ __device__ void jacobi_blocks(int m, int ld, E* A, E* V, double stop_ratio, E* c
       rot2(V[row * ld + pr_p[b * 96 + k]], V[row * ld + q], cs_c[b * 96 + k], cs_s[b * 96 + k]);
     }
   };
+  // This thread's work items are the same in every round: its block (k1, k2) of the upper
+  // triangle and up to VMAX (row, pair) rotations of V; found once, when they fit.
+  constexpr int VMAX = 4;
+  const int nA = np * (np + 1) / 2, nV = np * m;
+  const bool afix = nA <= nt;
+  const bool vfix = nt > 32 && nV <= VMAX * (nt - 32);
+  int ak1 = -1, ak2 = 0;
+  if (afix && tid < nA) tri_index(tid, np, ak1, ak2);
+  int vrow[VMAX], vk[VMAX];
+#pragma unroll
+  for (int u = 0; u < VMAX; u++) {
+    const int e = (tid - 32) + u * (nt - 32);
+    const bool ok = vfix && tid >= 32 && e < nV;
+    vrow[u] = ok ? (e / np) * ld : -1;
+    vk[u] = ok ? e % np : 0;
+  }
+  auto rotate_v_fixed = [&](int b) {
+#pragma unroll
+    for (int u = 0; u < VMAX; u++) {
+      if (vrow[u] < 0) continue;
+      const int k = vk[u];
+      const int q = pr_q[b * 96 + k];
+      if (q >= m || !nonzero(cs_s[b * 96 + k])) continue;
+      rot2(V[vrow[u] + pr_p[b * 96 + k]], V[vrow[u] + q], cs_c[b * 96 + k], cs_s[b * 96 + k]);
+    }
+  };
   int rcount = 0;
   for (int sweep = 0; sweep < 40; sweep++) {
     double off = 0.0, fro = 0.0;
@@ -157,14 +183,13 @@ __device__ void jacobi_blocks(int m, int ld, E* A, E* V, double stop_ratio, E* c
           pp[k] = p; qq[k] = q; cc[k] = c; ss[k] = sn;
         }
       } else if (pend >= 0) {
-        rotate_v(pend, tid - 32, nt - 32);
+        if (vfix) rotate_v_fixed(pend);
+        else rotate_v(pend, tid - 32, nt - 32);
       }
       __syncthreads();
       // 2x2 blocks of A: block (k1, k2) = rows {p1, q1} x columns {p2, q2}, k1 <= k2; the block
       // (k2, k1) is its transpose and is written by the same thread, so A stays exactly symmetric
-      for (int bb = tid; bb < np * (np + 1) / 2; bb += nt) {
-        int k1, k2;
-        tri_index(bb, np, k1, k2);
+      auto block = [&](int k1, int k2) {
         const int p1 = pp[k1], q1 = qq[k1], p2 = pp[k2], q2 = qq[k2];
         const bool r1 = q1 < m, r2 = q2 < m;  // second index valid (not the dummy)
         E a11 = A[p1 * ld + p2];
@@ -182,6 +207,15 @@ __device__ void jacobi_blocks(int m, int ld, E* A, E* V, double stop_ratio, E* c
           if (r2) A[q2 * ld + p1] = a12;
           if (r1) A[p2 * ld + q1] = a21;
           if (r1 && r2) A[q2 * ld + q1] = a22;
+        }
+      };
+      if (afix) {
+        if (ak1 >= 0) block(ak1, ak2);
+      } else {
+        for (int bb = tid; bb < nA; bb += nt) {
+          int k1, k2;
+          tri_index(bb, np, k1, k2);
+          block(k1, k2);
         }
       }
       __syncthreads();
@@ -327,11 +361,16 @@ __device__ __forceinline__ void rr_body_df(int m, const double* __restrict__ G, 
   __shared__ d2 cs_c[192], cs_s[192];
   __shared__ int pr_p[192], pr_q[192];
   __shared__ d2 inv[192], inv2[192];
+  __shared__ int rk[192];
   __shared__ double red[64];
   __shared__ int s_fail;
   __shared__ double s_off, s_fro;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int mm = m * m;
+  // element (r, c) updates of the right-looking loops: thread = (R0, C0), RS rows at a time
+  // (the launch gives nt >= m threads)
+  const int RS = nt / m, R0 = tid / m, C0 = tid % m;
+  const bool upd = tid < RS * m;
 
   // Cholesky (right-looking) of the symmetric Lm in place: lower factor, iv[j] = 1 / L_jj.
   // Returns 0, or j + 1 for a non-positive pivot j.
@@ -353,36 +392,45 @@ __device__ __forceinline__ void rr_body_df(int m, const double* __restrict__ G, 
       const d2 ij = iv[j];
       for (int i = j + 1 + tid; i < m; i += nt) Lm[i * ld + j] = d2_mul(Lm[i * ld + j], ij);
       __syncthreads();
-      const int rem = m - j - 1;
-      for (int e = tid; e < rem * rem; e += nt) {
-        const int i = j + 1 + e / rem, k = j + 1 + e % rem;
-        if (k <= i) {
-          d2 x = Lm[i * ld + k];
-          const d2 a = Lm[i * ld + j], b = Lm[k * ld + j];
+      if (upd && C0 > j)
+        for (int i = j + 1 + R0; i < m; i += RS) {
+          if (C0 > i) continue;
+          d2 x = Lm[i * ld + C0];
+          const d2 a = Lm[i * ld + j], b = Lm[C0 * ld + j];
           df_mac(x.hi, x.lo, -a.hi, -a.lo, b.hi, b.lo);
-          Lm[i * ld + k] = d2_norm(x);
+          Lm[i * ld + C0] = d2_norm(x);
         }
-      }
       __syncthreads();
     }
     return s_fail;
   };
-  // Am <- Lm^{-1} Am Lm^{-T}, made exactly symmetric
+  // Am <- Lm^{-1} Am Lm^{-T} (right-looking: row i, then column i, is final once the earlier
+  // ones have been subtracted), made exactly symmetric
   auto congruence = [&](d2* Am, const d2* Lm, const d2* iv) {
-    for (int c = tid; c < m; c += nt)
-      for (int i = 0; i < m; i++) {
-        d2 sum = Am[i * ld + c];
-        for (int t = 0; t < i; t++) { const d2 l = Lm[i * ld + t], a = Am[t * ld + c]; df_mac(sum.hi, sum.lo, -l.hi, -l.lo, a.hi, a.lo); }
-        Am[i * ld + c] = d2_mul(d2_norm(sum), iv[i]);
-      }
-    __syncthreads();
-    for (int r = tid; r < m; r += nt)
-      for (int i = 0; i < m; i++) {
-        d2 sum = Am[r * ld + i];
-        for (int t = 0; t < i; t++) { const d2 l = Lm[i * ld + t], a = Am[r * ld + t]; df_mac(sum.hi, sum.lo, -l.hi, -l.lo, a.hi, a.lo); }
-        Am[r * ld + i] = d2_mul(d2_norm(sum), iv[i]);
-      }
-    __syncthreads();
+    for (int i = 0; i < m; i++) {
+      if (tid < m) Am[i * ld + tid] = d2_mul(d2_norm(Am[i * ld + tid]), iv[i]);
+      __syncthreads();
+      if (upd)
+        for (int r = i + 1 + R0; r < m; r += RS) {
+          d2 x = Am[r * ld + C0];
+          const d2 l = Lm[r * ld + i], a = Am[i * ld + C0];
+          df_mac(x.hi, x.lo, -l.hi, -l.lo, a.hi, a.lo);
+          Am[r * ld + C0] = d2_norm(x);
+        }
+      __syncthreads();
+    }
+    for (int i = 0; i < m; i++) {
+      if (tid < m) Am[tid * ld + i] = d2_mul(d2_norm(Am[tid * ld + i]), iv[i]);
+      __syncthreads();
+      if (upd)
+        for (int c = i + 1 + R0; c < m; c += RS) {
+          d2 x = Am[C0 * ld + c];
+          const d2 a = Am[C0 * ld + i], l = Lm[c * ld + i];
+          df_mac(x.hi, x.lo, -a.hi, -a.lo, l.hi, l.lo);
+          Am[C0 * ld + c] = d2_norm(x);
+        }
+      __syncthreads();
+    }
     for (int e = tid; e < mm; e += nt) {
       const int i = e / m, j = e % m;
       if (i < j) {
@@ -394,15 +442,19 @@ __device__ __forceinline__ void rr_body_df(int m, const double* __restrict__ G, 
     }
     __syncthreads();
   };
-  // column j of Lm^{-T} Src written to Dst (Dst may be Src)
-  auto back_sub = [&](const d2* Lm, const d2* iv, const d2* Src, d2* Dst, int j) {
+  // Xm <- Lm^{-T} Xm for all columns (right-looking back substitution)
+  auto back_sub = [&](const d2* Lm, const d2* iv, d2* Xm) {
     for (int i = m - 1; i >= 0; i--) {
-      d2 sum = Src[i * ld + j];
-      for (int t = i + 1; t < m; t++) {
-        const d2 l = Lm[t * ld + i], x = Dst[t * ld + j];
-        df_mac(sum.hi, sum.lo, -l.hi, -l.lo, x.hi, x.lo);
-      }
-      Dst[i * ld + j] = d2_mul(d2_norm(sum), iv[i]);
+      if (tid < m) Xm[i * ld + tid] = d2_mul(d2_norm(Xm[i * ld + tid]), iv[i]);
+      __syncthreads();
+      if (upd)
+        for (int r = R0; r < i; r += RS) {
+          d2 x = Xm[r * ld + C0];
+          const d2 l = Lm[i * ld + r], a = Xm[i * ld + C0];
+          df_mac(x.hi, x.lo, -l.hi, -l.lo, a.hi, a.lo);
+          Xm[r * ld + C0] = d2_norm(x);
+        }
+      __syncthreads();
     }
   };
 
@@ -421,19 +473,21 @@ __device__ __forceinline__ void rr_body_df(int m, const double* __restrict__ G, 
     return;
   }
   if (chol_only) {  // Cholesky-QR: C = L^{-T}
-    for (int j = tid; j < m; j += nt) {
-      theta[j] = 1.0;
-      back_sub(L, inv, V, V, j);
-      for (int i = 0; i < m; i++) C[i * m + j] = d2_to(V[i * ld + j]);
+    back_sub(L, inv, V);
+    for (int e = tid; e < mm; e += nt) {
+      const int i = e / m, j = e % m;
+      C[i * m + j] = d2_to(V[i * ld + j]);
     }
+    for (int j = tid; j < m; j += nt) theta[j] = 1.0;
     if (tid == 0) *info = 0;
     return;
   }
   // 2. A <- L^{-1} G L^{-T}
   congruence(A, L, inv);
-  // 3. A = V diag(theta) V^T. Double-float carries ~48 significant bits, so the off-diagonal part
+  // 3. A = W diag(theta) W^T. Double-float carries ~48 significant bits, so the off-diagonal part
   // cannot fall much below 2^-46 of the whole; the Jacobi sweeps stop at ||off|| <= 1e-10 ||A||
   // (quadratic convergence: the Ritz values then carry errors of order ||off||^2 / gap).
+  d2* W = V;  // eigenvectors of the step-2 matrix
   if (!SMEM) {
     jacobi_blocks<d2>(m, ld, A, V, 1e-20, cs_c, cs_s, pr_p, pr_q, red, &s_off, &s_fro);
   } else {
@@ -441,7 +495,7 @@ __device__ __forceinline__ void rr_body_df(int m, const double* __restrict__ G, 
     // V32^T A V32 nearly diagonal -- most sweeps run at FP32 cost. (b) In double-float, with
     // V32^T V32 = Lb Lb^T: A <- Lb^{-1} V32^T A V32 Lb^{-T}, an exact congruence by
     // Q = V32 Lb^{-T} (Q^T Q = I), finished by Jacobi sweeps from V = I (one or two, as A starts
-    // nearly diagonal); the eigenvectors of the step-2 matrix are Q V.
+    // nearly diagonal); the eigenvectors of the step-2 matrix are W = Q V.
     float* F = reinterpret_cast<float*>(T);  // FP32 copy of A, in T's space until (b)
     for (int e = tid; e < mm; e += nt) {
       const int i = e / m, j = e % m;
@@ -488,21 +542,20 @@ __device__ __forceinline__ void rr_body_df(int m, const double* __restrict__ G, 
     }
     congruence(A, Lb, inv2);
     jacobi_blocks<d2>(m, ld, A, V, 1e-20, cs_c, cs_s, pr_p, pr_q, red, &s_off, &s_fro);
-    // V <- V32 Lb^{-T} V
-    for (int j = tid; j < m; j += nt) back_sub(Lb, inv2, V, T, j);
-    __syncthreads();
-    for (int e = tid; e < mm; e += nt) {
+    back_sub(Lb, inv2, V);  // V <- Lb^{-T} V
+    for (int e = tid; e < mm; e += nt) {  // W = V32 V
       const int i = e / m, j = e % m;
       float h = 0.f, l = 0.f;
       for (int k = 0; k < m; k++) {
-        const d2 t = T[k * ld + j];
+        const d2 t = V[k * ld + j];
         df_mac(h, l, VF[i * ld + k], 0.f, t.hi, t.lo);
       }
-      V[i * ld + j] = d2_norm(d2{h, l});
+      T[i * ld + j] = d2_norm(d2{h, l});
     }
+    W = T;
     __syncthreads();
   }
-  // 4. rank sort, C = L^{-T} V
+  // 4. rank sort of the Ritz values (ties by index), C = L^{-T} W in that order
   for (int j = tid; j < m; j += nt) {
     const double wj = d2_to(A[j * ld + j]);
     int rank = 0;
@@ -511,8 +564,12 @@ __device__ __forceinline__ void rr_body_df(int m, const double* __restrict__ G, 
       rank += (wi < wj) || (wi == wj && i < j);
     }
     theta[rank] = wj;
-    back_sub(L, inv, V, V, j);  // column `rank` of C kept in V's column j
-    for (int i = 0; i < m; i++) C[i * m + rank] = d2_to(V[i * ld + j]);
+    rk[j] = rank;
+  }
+  back_sub(L, inv, W);  // (its first barrier orders the ranks before their use below)
+  for (int e = tid; e < mm; e += nt) {
+    const int i = e / m, j = e % m;
+    C[i * m + rk[j]] = d2_to(W[i * ld + j]);
   }
   if (tid == 0) *info = 0;
 }
@@ -556,7 +613,7 @@ static size_t rr_smem_bytes(int m, bool df = false) {
 }
 static const size_t RR_SMEM_MAX = 200 * 1024;
 
-// Threads for order m: one per 2x2 block of the upper triangle of a Jacobi round, 128 to 1,024 --
+// Threads for order m: one per 2x2 block of the upper triangle of a Jacobi round, 128 to 512 --
 // the kernel is barrier-latency bound, and fewer warps make each barrier cheaper.
 static int rr_threads(int m) {
   const int np = (m + 1) / 2;
