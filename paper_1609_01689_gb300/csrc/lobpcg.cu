@@ -691,8 +691,10 @@ int lob_task::step() {
             if (!stats.precond_dropped) stats.precond_dropped = iters_total + it;
           }
         }
-        // W = T^{-1} R (step 6) with the rules of Section 4.3
-        const bool pc_on = o.precond && !pc_dropped && M->P.bp > 0 && it > 3 && hb->relres[0] <= 1e-1;
+        // W = T^{-1} R (step 6) with the rules of Section 4.3: no preconditioner in the first three
+        // iterations of the solve (counted across its phases: the refinement phase continues the
+        // same eigenpairs) nor while the first residual is above 1e-1
+        const bool pc_on = o.precond && !pc_dropped && M->P.bp > 0 && iters_total + it > 3 && hb->relres[0] <= 1e-1;
         LOB_TRY(stage(skey(1, na, haveP ? 1 : 0, pc_on ? 1 : 0), [&]() -> int {
           {
             Timer t(clk(), st, ph(PH_PRECOND));

@@ -604,7 +604,10 @@ static int engine_round(lob_engine* E, std::vector<lob_ltask*>& done) {
       t->pc_dropped = true;
       if (!t->precond_dropped) t->precond_dropped = t->iters_total + t->it;
     }
-    t->pc_on = t->o.precond && !t->pc_dropped && t->M->P.bp > 0 && t->it > 3 && relres_host(E, t, 0) <= 1e-1;
+    // Section 4.3: not in the first three iterations of the solve (across its phases), nor while the
+    // first residual is above 1e-1
+    t->pc_on = t->o.precond && !t->pc_dropped && t->M->P.bp > 0 && t->iters_total + t->it > 3 &&
+               relres_host(E, t, 0) <= 1e-1;
     iter.push_back(t);
   }
   // finished solves: outputs
