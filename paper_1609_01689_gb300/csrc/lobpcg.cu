@@ -686,6 +686,14 @@ int lob_task::step() {
           for (int j = 0; j < k; j++)
             if (!(hb->relres[j] <= run_tol)) worst = fmax(worst, hb->relres[j]);
           if (worst < 0.5 * best_res) { best_res = worst; best_it = it; }
+          // MIXED, FP32-value phase: no halving of the worst residual in 40 iterations means the
+          // FP32 products limit it (a near-degenerate pair at the edge of the block, say); the
+          // FP64-class phase takes over from here
+          if (o.mode == LOB_MODE_MIXED && phase == 0 && it - best_it >= 40) {
+            run_status = LOB_ERR_NOCONV;
+            pc = PC_RUN_END;
+            continue;
+          }
           if (!pc_dropped && o.precond && it - best_it >= 40) {
             pc_dropped = true;
             if (!stats.precond_dropped) stats.precond_dropped = iters_total + it;

@@ -581,6 +581,15 @@ static int engine_round(lob_engine* E, std::vector<lob_ltask*>& done) {
       if (!(r <= t->run_tol)) t->hmap[t->na++] = j;
     }
     if (!conv && t->it >= t->run_max) { t->status = LOB_ERR_NOCONV; conv = true; }
+    double worst = 0.0;
+    for (int j = 0; j < t->k; j++) {
+      const double r = relres_host(E, t, j);
+      if (!(r <= t->run_tol)) worst = fmax(worst, r);
+    }
+    if (worst < 0.5 * t->best_res) { t->best_res = worst; t->best_it = t->it; }
+    // MIXED, FP32-value phase: no halving of the worst residual in 40 iterations -> the FP64-class
+    // phase takes over from here
+    if (!conv && t->o.mode == LOB_MODE_MIXED && t->phase == 0 && t->it - t->best_it >= 40) conv = true;
     if (conv) {
       t->iters_total += t->it;
       if (t->o.mode == LOB_MODE_MIXED && t->phase == 1) t->refine_its = t->it;
@@ -594,12 +603,6 @@ static int engine_round(lob_engine* E, std::vector<lob_ltask*>& done) {
       finishing.push_back(t);
       continue;
     }
-    double worst = 0.0;
-    for (int j = 0; j < t->k; j++) {
-      const double r = relres_host(E, t, j);
-      if (!(r <= t->run_tol)) worst = fmax(worst, r);
-    }
-    if (worst < 0.5 * t->best_res) { t->best_res = worst; t->best_it = t->it; }
     if (!t->pc_dropped && t->o.precond && t->it - t->best_it >= 40) {
       t->pc_dropped = true;
       if (!t->precond_dropped) t->precond_dropped = t->iters_total + t->it;
