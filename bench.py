@@ -384,6 +384,11 @@ def run_kernels(args, lob, M, info, torch):
     timeit("lincomb_df_48x16", lambda: lob.lincomb(S, Cm, "mixed"), df_macs=n * 48 * 16,
            algorithmic_bytes=n * (48 + 16) * 8)
     timeit("rayleigh_ritz_df_48", lambda: lob.rayleigh_ritz(Gs, Ms, "mixed"), reps=20)
+    if info.get("precond_block", 0) > 0:
+        bp = int(info["precond_block"])
+        mu = torch.linspace(-5.0, -4.0, nb, dtype=torch.float64, device="cuda")
+        timeit("precond_fom3", lambda: M.precond_apply(mu, X, solve="fom", steps=3),
+               algorithmic_bytes=((n + bp - 1) // bp) * bp * bp * 4 + 2 * n * nb * 8)
     for v in out.values():
         if "algorithmic_bytes" in v:
             v["gbs"] = v["algorithmic_bytes"] / (v["ms"] * 1e-3) / 1e9

@@ -11,6 +11,10 @@
 
 #define LOB_TILE 256
 #define LOB_TILE_LOG 8
+// Relative residual to which the eq. 12 guess (the leading n_small block's eigenvectors) is solved.
+// The guess cannot be better than eq. 12 itself: on the n = 500,000 workload 1e-3 gives the
+// main solve the same iteration count as 1e-4 (21) at a lower cost, and 1e-2 costs 6 more.
+#define LOB_GUESS_TOL 1e-3
 #define LOB_PERM_CHUNK 4096  // entries per SpMM chunk (column-order permutation granularity)
 
 // Report a failed CUDA call and return LOB_ERR_CUDA from the enclosing function.

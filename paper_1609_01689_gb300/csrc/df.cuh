@@ -176,3 +176,55 @@ __device__ __forceinline__ d2 d2_rsqrt(d2 x) {
   const d2 corr = d2_mul(d2{0.5f * y0, 0.f}, r);
   return d2_add(d2{y0, 0.f}, corr);
 }
+
+// One CTA of 256 threads, rows [256 blk, 256 blk + 256) of the residual R = HX - X diag(theta)
+// (Algorithm 1, step 4): R written (FP64), and the CTA's column sums of (r / ||H||)^2 and x^2
+// (step 5) into part[blk][0 .. 2 nb). Thread t takes column t mod NBP (NBP = nb rounded up to a
+// power of two) and every (256 / NBP)-th row, so a warp reads whole 8-byte-column rows
+// (coalesced). Squares are summed in FP32 -- the norms decide convergence at relative accuracy
+// ~1e-6, which is plenty -- in a fixed order (registers, lanes, warps), and each CTA's sum is
+// stored as FP64. sred: 8 x 64 floats. nb <= 32.
+__device__ __forceinline__ void lob_residual_rows(int64_t n, int nb, const double* __restrict__ X, int ldx,
+                                                  const double* __restrict__ HX, int ldh,
+                                                  const double* __restrict__ theta, double inv_norm,
+                                                  double* __restrict__ R, double* __restrict__ part, int64_t blk,
+                                                  float* sred) {
+  const int tid = threadIdx.x;
+  int NBP = 1;
+  while (NBP < nb) NBP <<= 1;
+  const int c = tid % NBP, r0 = tid / NBP, rstep = 256 / NBP;
+  const float sc = (float)inv_norm;
+  float rr = 0.f, xx = 0.f;
+  if (c < nb) {
+    const double th = theta[c];
+    for (int i = r0; i < 256; i += rstep) {
+      const int64_t r = blk * 256 + i;
+      if (r >= n) break;
+      const double x = X[r * ldx + c];
+      const double v = HX[r * ldh + c] - x * th;
+      R[r * nb + c] = v;
+      const float vs = f64_to_f32_rz(v) * sc, xf = f64_to_f32_rz(x);
+      rr = fmaf(vs, vs, rr);
+      xx = fmaf(xf, xf, xx);
+    }
+  }
+  for (int o = NBP; o < 32; o <<= 1) {
+    rr += __shfl_xor_sync(0xFFFFFFFFu, rr, o);
+    xx += __shfl_xor_sync(0xFFFFFFFFu, xx, o);
+  }
+  const int warp = tid / 32, lane = tid % 32;
+  if (lane < NBP) {
+    sred[warp * 64 + lane] = rr;
+    sred[warp * 64 + 32 + lane] = xx;
+  }
+  __syncthreads();
+  if (tid < nb) {
+    double s = 0.0, t = 0.0;
+    for (int w = 0; w < 8; w++) {
+      s += (double)sred[w * 64 + tid];
+      t += (double)sred[w * 64 + 32 + tid];
+    }
+    part[blk * 2 * nb + tid] = s;
+    part[blk * 2 * nb + nb + tid] = t;
+  }
+}

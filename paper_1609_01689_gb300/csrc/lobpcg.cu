@@ -68,34 +68,17 @@ __global__ void k_copy_cols(int64_t n, int ncol, const double* __restrict__ src,
 }
 
 // R = HX - X diag(theta); per-CTA partial column sums of r^2 and x^2 into part[blk][2*nb].
-__global__ void k_residual(int64_t n, int nb, const double* __restrict__ X, int ldx, const double* __restrict__ HX,
-                           int ldh, const double* __restrict__ theta, double* __restrict__ R, double* __restrict__ part) {
-  extern __shared__ double sred[];  // [BS/32][2*nb]
-  const int tid = threadIdx.x;
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + tid;
-  const int lane = tid % 32, warp = tid / 32;
-  for (int j = 0; j < nb; j++) {
-    double rr = 0.0, xx = 0.0;
-    if (r < n) {
-      const double x = X[r * ldx + j];
-      const double v = HX[r * ldh + j] - x * theta[j];
-      R[r * nb + j] = v;
-      rr = v * v;
-      xx = x * x;
-    }
-    for (int o = 16; o > 0; o >>= 1) { rr += __shfl_down_sync(0xFFFFFFFFu, rr, o); xx += __shfl_down_sync(0xFFFFFFFFu, xx, o); }
-    if (lane == 0) { sred[warp * 2 * nb + j] = rr; sred[warp * 2 * nb + nb + j] = xx; }
-  }
-  __syncthreads();
-  for (int j = tid; j < 2 * nb; j += blockDim.x) {
-    double s = 0.0;
-    for (int w = 0; w < (int)blockDim.x / 32; w++) s += sred[w * 2 * nb + j];
-    part[(int64_t)blockIdx.x * 2 * nb + j] = s;
-  }
+__global__ void __launch_bounds__(256) k_residual(int64_t n, int nb, const double* __restrict__ X, int ldx,
+                                                  const double* __restrict__ HX, int ldh,
+                                                  const double* __restrict__ theta, double inv_norm,
+                                                  double* __restrict__ R, double* __restrict__ part) {
+  __shared__ float sred[8 * 64];
+  lob_residual_rows(n, nb, X, ldx, HX, ldh, theta, inv_norm, R, part, blockIdx.x, sred);
 }
 
 // relres_j = sqrt(sum r^2) / (normH sqrt(sum x^2)): one CTA per column, a strided pass over the
-// partials then a fixed-order tree, so the result is deterministic.
+// partials then a fixed-order tree, so the result is deterministic. (The residual kernel's
+// partials are already scaled by 1 / normH; it is then called with normH = 1.)
 __global__ void __launch_bounds__(256) k_relres(int nparts, int nb, const double* __restrict__ part, double normH,
                                                 double* __restrict__ out) {
   __shared__ double srr[256], sxx[256];
@@ -493,9 +476,9 @@ struct lob_task {
 
   int residual_begin() {
     Timer t(clk(), st, ph(PH_RESID));
-    const size_t smem = (BS / 32) * 2 * nb * sizeof(double);
-    (k_residual<<<nblk(n_act), BS, smem, st>>>(n_act, nb, S.p, ldS, HS.p, ldS, theta.p, R.p, part.p), LOB_LAUNCHED());
-    (k_relres<<<nb, 256, 0, st>>>((int)nblk(n_act), nb, part.p, normH, relres_d.p), LOB_LAUNCHED());
+    (k_residual<<<nblk(n_act), BS, 0, st>>>(n_act, nb, S.p, ldS, HS.p, ldS, theta.p, 1.0 / normH, R.p, part.p),
+     LOB_LAUNCHED());
+    (k_relres<<<nb, 256, 0, st>>>((int)nblk(n_act), nb, part.p, 1.0, relres_d.p), LOB_LAUNCHED());
     LOB_CUDA(cudaMemcpyAsync(hb->relres, relres_d.p, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
     return LOB_OK;
   }
@@ -603,7 +586,7 @@ int lob_task::step() {
             so.mixed_tol = 0.0;
             so.verbose = 0;
             child = new lob_task();
-            const int rc = task_init(child, M, nb, nb, 1e-4, nullptr, &so, W.p, ns, st, false);
+            const int rc = task_init(child, M, nb, nb, LOB_GUESS_TOL, nullptr, &so, W.p, ns, st, false);
             if (rc != LOB_OK) { delete child; child = nullptr; return rc; }
             pc = PC_GUESS_CHILD;
             return step();
@@ -796,7 +779,12 @@ int lob_task::step() {
         restarts_total += restarts;
         if (o.mode == LOB_MODE_MIXED && phase == 1) stats.refine_iterations = it;
         if (run_status != LOB_OK && run_status != LOB_ERR_NOCONV) { status = run_status; pc = PC_END; continue; }
-        if (o.mode == LOB_MODE_MIXED && phase == 0) { phase = 1; pc = PC_PHASE; continue; }
+        // the FP64-class phase, unless the FP32-value phase already met the final tol (tol >= 1e-6)
+        if (o.mode == LOB_MODE_MIXED && phase == 0 && !(run_status == LOB_OK && run_tol <= tol)) {
+          phase = 1;
+          pc = PC_PHASE;
+          continue;
+        }
         status = run_status;
         pc = PC_FINISH;
         continue;

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "df.cuh"
 
 namespace {
 
@@ -64,39 +65,14 @@ __global__ void k_proj_batch(const lob_bjob* __restrict__ jobs) {
 
 // R = HX - X diag(theta) and per-CTA column sums of r^2 and x^2: X = A (lda), HX = B (ldb),
 // theta = C, R = Y (x0 columns), partials W0; ceil(n / 256) CTAs.
+// job fields: A = X (lda), B = H X (ldb), C = theta, Y = R, W0 = partials, n, x0 = nb, s0 = 1 / normH
 __global__ void __launch_bounds__(BS) k_resid_batch(const lob_bjob* __restrict__ jobs, int njobs) {
-  __shared__ double sred[BS / 32][2 * NBMAX];
+  __shared__ float sred[8 * 64];
   const lob_bjob& j = jobs[find_job(jobs, njobs, blockIdx.x)];
-  const int64_t lb = (int64_t)blockIdx.x - j.cta_begin;
-  const int tid = threadIdx.x, lane = tid % 32, warp = tid / 32;
-  const int64_t r = lb * BS + tid;
-  const int nb = j.x0;
-  for (int c = 0; c < nb; c++) {
-    double rr = 0.0, xx = 0.0;
-    if (r < j.n) {
-      const double x = j.A[r * j.lda + c];
-      const double v = j.B[r * j.ldb + c] - x * j.C[c];
-      j.Y[r * nb + c] = v;
-      rr = v * v;
-      xx = x * x;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      rr += __shfl_down_sync(0xFFFFFFFFu, rr, o);
-      xx += __shfl_down_sync(0xFFFFFFFFu, xx, o);
-    }
-    if (lane == 0) { sred[warp][c] = rr; sred[warp][NBMAX + c] = xx; }
-  }
-  __syncthreads();
-  for (int c = tid; c < 2 * nb; c += BS) {
-    const int col = c < nb ? c : NBMAX + (c - nb);
-    double s = 0.0;
-    for (int w = 0; w < BS / 32; w++) s += sred[w][col];
-    j.W0[lb * 2 * nb + c] = s;
-  }
+  lob_residual_rows(j.n, j.x0, j.A, j.lda, j.B, j.ldb, j.C, j.s0, j.Y, j.W0, (int64_t)blockIdx.x - j.cta_begin, sred);
 }
 
-// relres_c = sqrt(sum r^2) / (normH sqrt(sum x^2)) over x1 partials (fixed order): W0, x0 (nb),
-// s0 (normH), Y; one CTA per job.
+// Column norms from the residual partials (already scaled by 1 / normH, so s0 = 1 here)
 __global__ void __launch_bounds__(BS) k_relres_batch(const lob_bjob* __restrict__ jobs) {
   __shared__ double sr[BS], sx[BS];
   const lob_bjob& j = jobs[blockIdx.x];
@@ -525,14 +501,14 @@ int lob_engine_add(lob_engine* E, lob_matrix* M, int32_t k, int32_t nb, double t
   if (rc != LOB_OK) { task_release(E, t); delete t; return rc; }
   E->tasks.push_back(t);
   if (o->n_small >= 3 * nb && o->n_small < n_act) {
-    // eq. 12: the leading n_small block solved first (to 1e-4), its vectors (zero-padded) become X0
+    // eq. 12: the leading n_small block solved first (to LOB_GUESS_TOL), its vectors (zero-padded) become X0
     lob_solve_opts so = *o;
     so.n_small = 0;
     so.max_iter = 2000;
     so.refine_iter = 0;
     so.mixed_tol = 0.0;
     lob_ltask* c = nullptr;
-    rc = lob_engine_add(E, M, nb, nb, 1e-4, &so, t->W, o->n_small, -1, &c);
+    rc = lob_engine_add(E, M, nb, nb, LOB_GUESS_TOL, &so, t->W, o->n_small, -1, &c);
     if (rc == LOB_OK) {
       c->parent = t;
       t->child = c;
@@ -589,11 +565,15 @@ static int engine_round(lob_engine* E, std::vector<lob_ltask*>& done) {
     if (worst < 0.5 * t->best_res) { t->best_res = worst; t->best_it = t->it; }
     // MIXED, FP32-value phase: no halving of the worst residual in 40 iterations -> the FP64-class
     // phase takes over from here
-    if (!conv && t->o.mode == LOB_MODE_MIXED && t->phase == 0 && t->it - t->best_it >= 40) conv = true;
+    if (!conv && t->o.mode == LOB_MODE_MIXED && t->phase == 0 && t->it - t->best_it >= 40) {
+      t->status = LOB_ERR_NOCONV;
+      conv = true;
+    }
     if (conv) {
       t->iters_total += t->it;
       if (t->o.mode == LOB_MODE_MIXED && t->phase == 1) t->refine_its = t->it;
-      if (t->o.mode == LOB_MODE_MIXED && t->phase == 0) {
+      // the FP64-class phase, unless the FP32-value phase already met the final tol (tol >= 1e-6)
+      if (t->o.mode == LOB_MODE_MIXED && t->phase == 0 && !(t->status == LOB_OK && t->run_tol <= t->tol)) {
         t->phase = 1;
         t->status = LOB_OK;
         set_phase(t);
@@ -807,10 +787,10 @@ static int engine_round(lob_engine* E, std::vector<lob_ltask*>& done) {
     }
     lob_bjob rj{};
     rj.A = t->S; rj.lda = t->ldS; rj.B = t->HS; rj.ldb = t->ldS; rj.C = t->theta; rj.Y = t->R; rj.W0 = t->part;
-    rj.n = t->n_act; rj.x0 = nb;
+    rj.n = t->n_act; rj.x0 = nb; rj.s0 = 1.0 / t->normH;
     j_res.push_back(rj);
     lob_bjob rl{};
-    rl.W0 = t->part; rl.x1 = (int32_t)nblk(t->n_act); rl.x0 = nb; rl.s0 = t->normH; rl.Y = relres_dev(E, t);
+    rl.W0 = t->part; rl.x1 = (int32_t)nblk(t->n_act); rl.x0 = nb; rl.s0 = 1.0; rl.Y = relres_dev(E, t);
     j_rel.push_back(rl);
     if (t->start) {
       t->start = false;

@@ -134,68 +134,105 @@ __device__ void block_solve(int solve, int steps, float guard, const float d[2],
     }
     return;
   }
+  // All loops below run to the fixed bound KM = 3 (the most Krylov steps) and test the runtime
+  // count inside, so every small array is indexed by constants and stays in registers.
+  constexpr int KM = 3;
   x[0] = x[1] = 0.f;
   const float beta0 = sqrtf(warp_sum(c[0] * c[0] + c[1] * c[1]));
   if (!(beta0 > 0.f)) return;
   // Lanczos on (D, c), full reorthogonalisation (at most 3 vectors)
-  float v[3][2], al[3] = {0.f, 0.f, 0.f}, be[3] = {0.f, 0.f, 0.f};
+  float v[KM][2], al[KM], be[KM];
+#pragma unroll
+  for (int i = 0; i < KM; i++) { v[i][0] = v[i][1] = 0.f; al[i] = be[i] = 0.f; }
   v[0][0] = c[0] / beta0;
   v[0][1] = c[1] / beta0;
   int m = 0;
-  for (int i = 0; i < steps; i++) {
+  bool done = false;  // warp-uniform: it depends on warp sums only
+#pragma unroll
+  for (int i = 0; i < KM; i++) {
+    if (done || i >= steps) continue;
     float w[2] = {d[0] * v[i][0], d[1] * v[i][1]};
     al[i] = warp_sum(v[i][0] * w[0] + v[i][1] * w[1]);
     m = i + 1;
-    for (int t = 0; t <= i; t++) {
+#pragma unroll
+    for (int t = 0; t < KM; t++) {
+      if (t > i) continue;
       const float h = warp_sum(v[t][0] * w[0] + v[t][1] * w[1]);
       w[0] -= h * v[t][0];
       w[1] -= h * v[t][1];
     }
     be[i] = sqrtf(warp_sum(w[0] * w[0] + w[1] * w[1]));
-    const float scale = fabsf(al[i]) + (i > 0 ? be[i - 1] : 0.f);
+    const float scale = fabsf(al[i]) + (i > 0 ? be[i > 0 ? i - 1 : 0] : 0.f);
     if (i + 1 == steps || !(be[i] > 1e-6f * scale)) {
       if (!(be[i] > 1e-6f * scale)) be[i] = 0.f;  // invariant subspace: both iterates are exact
-      break;
+      done = true;
+    } else if (i + 1 < KM) {
+      v[i + 1 < KM ? i + 1 : i][0] = w[0] / be[i];
+      v[i + 1 < KM ? i + 1 : i][1] = w[1] / be[i];
     }
-    v[i + 1][0] = w[0] / be[i];
-    v[i + 1][1] = w[1] / be[i];
   }
   // tridiagonal T (m x m): diagonal al, off-diagonal be[0..m-2]; T_bar adds the row be[m-1] e_m^T
-  float y[3] = {0.f, 0.f, 0.f};
+  float y[KM];
+#pragma unroll
+  for (int i = 0; i < KM; i++) y[i] = 0.f;
   bool ok = false;
   float tmax = 0.f;
-  for (int i = 0; i < m; i++) tmax = fmaxf(tmax, fabsf(al[i]) + be[i]);
+#pragma unroll
+  for (int i = 0; i < KM; i++)
+    if (i < m) tmax = fmaxf(tmax, fabsf(al[i]) + be[i]);
   if (solve == LOB_PSOLVE_FOM) {
     // Galerkin: T y = beta0 e1 by elimination without pivoting; a small pivot is a FOM breakdown
-    float dg[3], rhs[3] = {beta0, 0.f, 0.f};
+    float dg[KM], rhs[KM];
+#pragma unroll
+    for (int i = 0; i < KM; i++) { dg[i] = 1.f; rhs[i] = i == 0 ? beta0 : 0.f; }
     ok = true;
-    for (int i = 0; i < m; i++) {
+#pragma unroll
+    for (int i = 0; i < KM; i++) {
+      if (i >= m) continue;
       dg[i] = al[i];
       if (i > 0) {
-        const float l = be[i - 1] / dg[i - 1];
-        dg[i] -= l * be[i - 1];
-        rhs[i] -= l * rhs[i - 1];
+        const int ip = i > 0 ? i - 1 : 0;
+        const float l = be[ip] / dg[ip];
+        dg[i] -= l * be[ip];
+        rhs[i] -= l * rhs[ip];
       }
       if (!(fabsf(dg[i]) > 1e-4f * tmax)) ok = false;
     }
     if (ok) {
-      for (int i = m - 1; i >= 0; i--) y[i] = (rhs[i] - (i + 1 < m ? be[i] * y[i + 1] : 0.f)) / dg[i];
+#pragma unroll
+      for (int i = KM - 1; i >= 0; i--) {
+        if (i >= m) continue;
+        const int in = i + 1 < KM ? i + 1 : i;
+        y[i] = (rhs[i] - (i + 1 < m ? be[i] * y[in] : 0.f)) / dg[i];
+      }
     }
   }
   if (!ok) {
     // minimal residual: min || beta0 e1 - T_bar y || by Givens rotations on the (m+1) x m T_bar
-    float R[4][3] = {{0.f}}, g[4] = {beta0, 0.f, 0.f, 0.f};
-    for (int i = 0; i < m; i++) {
+    float R[KM + 1][KM], g[KM + 1];
+#pragma unroll
+    for (int i = 0; i <= KM; i++) {
+      g[i] = i == 0 ? beta0 : 0.f;
+#pragma unroll
+      for (int j = 0; j < KM; j++) R[i][j] = 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < KM; i++) {
+      if (i >= m) continue;
       R[i][i] = al[i];
       R[i + 1][i] = be[i];
-      if (i + 1 < m) R[i][i + 1] = be[i];
+      if (i + 1 < m) R[i][i + 1 < KM ? i + 1 : i] = be[i];
     }
-    for (int i = 0; i < m; i++) {
+#pragma unroll
+    for (int i = 0; i < KM; i++) {
+      if (i >= m) continue;
       const float a = R[i][i], b = R[i + 1][i];
       const float r = sqrtf(a * a + b * b);
       if (!(r > 0.f)) continue;
       const float cs = a / r, sn = b / r;
-      for (int j = i; j < m; j++) {
+#pragma unroll
+      for (int j = 0; j < KM; j++) {
+        if (j < i || j >= m) continue;
         const float p = R[i][j], q = R[i + 1][j];
         R[i][j] = cs * p + sn * q;
         R[i + 1][j] = -sn * p + cs * q;
@@ -204,13 +241,19 @@ __device__ void block_solve(int solve, int steps, float guard, const float d[2],
       g[i] = cs * p + sn * q;
       g[i + 1] = -sn * p + cs * q;
     }
-    for (int i = m - 1; i >= 0; i--) {
+#pragma unroll
+    for (int i = KM - 1; i >= 0; i--) {
+      if (i >= m) continue;
       float s2 = g[i];
-      for (int j = i + 1; j < m; j++) s2 -= R[i][j] * y[j];
+#pragma unroll
+      for (int j = 0; j < KM; j++)
+        if (j > i && j < m) s2 -= R[i][j] * y[j];
       y[i] = fabsf(R[i][i]) > 1e-6f * tmax ? s2 / R[i][i] : 0.f;
     }
   }
-  for (int i = 0; i < m; i++) {
+#pragma unroll
+  for (int i = 0; i < KM; i++) {
+    if (i >= m) continue;
     x[0] += y[i] * v[i][0];
     x[1] += y[i] * v[i][1];
   }
