@@ -240,7 +240,9 @@ def run_serving(args, lob, synth, torch):
             out[j] = res[rid]
         return out, wall, st, late
 
+    torch.cuda.nvtx.range_push("serve")  # marks the timed serving run for profilers
     out, wall, st, late = serve(reqs, True)
+    torch.cuda.nvtx.range_pop()
     lat = np.array([r["t_done_ms"] - r["t_submit_ms"] for r in out])
     ok = sum(1 for r in out if r["rc"] == lob.LOB_OK)
     failed = [dict(n=q["n"], k=q["k"], nb=q["nb"], rc=int(r["rc"]), iterations=int(r["stats"]["iterations"]))

@@ -230,15 +230,17 @@ __device__ __forceinline__ int find_job(const lob_bjob* __restrict__ jobs, int n
   return lo;
 }
 
-// Batched Y = A C (+ D), q <= QT: job fields A, lda, p, C, q, Y, ldy, D, ldd, n; ceil(n / (LB_RM 256 /
-// QT)) CTAs. Narrow blocks (QT = 4, 8) put more rows in a CTA instead of idle output columns.
-constexpr int LB_RM = 4;
+// Batched Y = A C (+ D), q <= QT: job fields A, lda, p, C, q, Y, ldy, D, ldd, n; ceil(n / (lb_rm 256 /
+// QT)) CTAs. Narrow blocks (QT = 1, 2, 4, 8) put more rows in a CTA instead of idle output columns.
+// rows a thread: 4 (1 or 2 for the one- and two-column classes, whose CTAs already span 256
+// or 128 rows a pass)
+__host__ __device__ constexpr int lb_rm(int QT) { return QT >= 4 ? 4 : QT; }
 template <bool DF, int QT>
 __global__ void __launch_bounds__(256) k_lincomb_batch(const lob_bjob* __restrict__ jobs, int njobs) {
   extern __shared__ __align__(16) unsigned char sm[];
   const lob_bjob& j = jobs[find_job(jobs, njobs, blockIdx.x)];
-  lincomb_body<DF, QT, LB_RM>(j.n, j.p, j.A, j.lda, j.q, j.C, j.Y, j.ldy, j.D, j.ldd,
-                              (int64_t)blockIdx.x - j.cta_begin, 0, sm);
+  lincomb_body<DF, QT, lb_rm(QT)>(j.n, j.p, j.A, j.lda, j.q, j.C, j.Y, j.ldy, j.D, j.ldd,
+                                  (int64_t)blockIdx.x - j.cta_begin, 0, sm);
 }
 
 // Batched Gram products, one output tile (p, q <= 16 U): job fields A, lda, p, B, ldb, q, n,
@@ -527,7 +529,7 @@ int lob_gram_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, in
 
 template <bool DF, int QT>
 static int lincomb_batch_go(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pmax, cudaStream_t st) {
-  constexpr int RPC = LB_RM * 256 / QT;
+  constexpr int RPC = lb_rm(QT) * 256 / QT;
   int64_t ctas = 0;
   for (int i = 0; i < njobs; i++) {
     jobs_host[i].cta_begin = ctas;
@@ -542,12 +544,18 @@ static int lincomb_batch_go(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, 
   return LOB_OK;
 }
 
-// All jobs of one call must share the output width class (q <= 4, <= 8 or <= 16; qmax selects).
+// All jobs of one call must share the output width class (q <= 1, 2, 4, 8 or 16; qmax selects).
 int lob_lincomb_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pmax, int qmax, int mode,
                              cudaStream_t st) {
   if (njobs <= 0) return LOB_OK;
   if (qmax > 16 || pmax > 64) return LOB_ERR_ARG;
   const bool df = mode == LOB_SPMM_MIXED;
+  if (qmax <= 1)
+    return df ? lincomb_batch_go<true, 1>(jobs_host, jobs_dev, njobs, pmax, st)
+              : lincomb_batch_go<false, 1>(jobs_host, jobs_dev, njobs, pmax, st);
+  if (qmax <= 2)
+    return df ? lincomb_batch_go<true, 2>(jobs_host, jobs_dev, njobs, pmax, st)
+              : lincomb_batch_go<false, 2>(jobs_host, jobs_dev, njobs, pmax, st);
   if (qmax <= 4)
     return df ? lincomb_batch_go<true, 4>(jobs_host, jobs_dev, njobs, pmax, st)
               : lincomb_batch_go<false, 4>(jobs_host, jobs_dev, njobs, pmax, st);

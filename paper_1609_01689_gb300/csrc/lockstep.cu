@@ -299,11 +299,11 @@ int gram_batch(lob_engine* E, std::vector<lob_bjob>& v, int) {
   return LOB_OK;
 }
 
-inline int width_class(const lob_bjob& j) { return j.q <= 4 ? 4 : (j.q <= 8 ? 8 : 16); }
+inline int width_class(const lob_bjob& j) { return j.q <= 1 ? 1 : (j.q <= 2 ? 2 : (j.q <= 4 ? 4 : (j.q <= 8 ? 8 : 16))); }
 
 int lincomb_batch(lob_engine* E, std::vector<lob_bjob>& v, int) {
   for (int blas : {LOB_SPMM_FP64, LOB_SPMM_MIXED})
-    for (int w : {4, 8, 16}) {
+    for (int w : {1, 2, 4, 8, 16}) {
       size_t cnt = 0;
       for (const lob_bjob& j : v) cnt += j.x2 == blas && width_class(j) == w;
       if (!cnt) continue;

@@ -259,57 +259,63 @@ __device__ void block_solve(int solve, int steps, float guard, const float d[2],
   }
 }
 
-// W_[i] = Q f(Lambda - mu_j) Q^T R_[i]; one CTA per block, FP32 arithmetic. f is the exact
-// inverse (a direct solve of eq. 11), its absolute value, or the FOM / minimal-residual
-// polynomial of the given number of Krylov steps (the paper's iterative solve, Section 4.3).
+// W_[i] = Q f(Lambda - mu_j) Q^T R_[i], FP32 arithmetic. f is the exact inverse (a direct solve
+// of eq. 11), its absolute value, or the FOM / minimal-residual polynomial of the given number of
+// Krylov steps (the paper's iterative solve, Section 4.3). The block is handled by nt threads
+// (tid = 0 .. nt-1, whole warps) of the CTA; valid = false makes them pass the barriers only.
 __device__ __forceinline__ void block_apply_body(int bp, int64_t n_act, const float* __restrict__ Q,
                                                  const float* __restrict__ lam, const double* __restrict__ mu,
                                                  float guard, const double* __restrict__ R, double* __restrict__ W,
-                                                 int nb, int solve, int steps, int64_t b, float* sm) {
+                                                 int nb, int solve, int steps, int64_t b, float* sm, int tid, int nt,
+                                                 bool valid) {
   float* Qs = sm;             // bp x bp, column-major (Qs[k*bp + i])
   float* Rs = Qs + bp * bp;   // bp x nb
   float* Ts = Rs + bp * nb;   // bp x nb
   const int64_t o = b * bp;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const float* Qb = Q + b * (int64_t)bp * bp;
-  for (int e = tid; e < bp * bp; e += nt) Qs[e] = Qb[e];
-  for (int e = tid; e < bp * nb; e += nt) {
-    const int i = e / nb, j = e % nb;
-    Rs[e] = (o + i < n_act) ? f64_to_f32_rz(R[(o + i) * nb + j]) : 0.f;
+  if (valid) {
+    const float* Qb = Q + b * (int64_t)bp * bp;
+    for (int e = tid; e < bp * bp; e += nt) Qs[e] = Qb[e];
+    for (int e = tid; e < bp * nb; e += nt) {
+      const int i = e / nb, j = e % nb;
+      Rs[e] = (o + i < n_act) ? f64_to_f32_rz(R[(o + i) * nb + j]) : 0.f;
+    }
   }
   __syncthreads();
-  for (int e = tid; e < bp * nb; e += nt) {  // C = Q^T R
-    const int k = e / nb, j = e % nb;
-    float s = 0.f;
-    for (int i = 0; i < bp; i++) s = fmaf(Qs[k * bp + i], Rs[i * nb + j], s);
-    Ts[e] = s;
-  }
+  if (valid)
+    for (int e = tid; e < bp * nb; e += nt) {  // C = Q^T R
+      const int k = e / nb, j = e % nb;
+      float sum = 0.f;
+      for (int i = 0; i < bp; i++) sum = fmaf(Qs[k * bp + i], Rs[i * nb + j], sum);
+      Ts[e] = sum;
+    }
   __syncthreads();
   const int warp = tid / 32, lane = tid % 32, nw = nt / 32;
-  for (int j = warp; j < nb; j += nw) {  // T[:, j] = f(Lambda - mu_j) C[:, j], one warp per column
-    const float2 m = df_split(mu[j]);
-    float d[2], c[2], x[2];
+  if (valid)
+    for (int j = warp; j < nb; j += nw) {  // T[:, j] = f(Lambda - mu_j) C[:, j], one warp per column
+      const float2 m = df_split(mu[j]);
+      float d[2], c[2], x[2];
 #pragma unroll
-    for (int u = 0; u < 2; u++) {
-      const int k = lane + 32 * u;
-      d[u] = k < bp ? __fsub_rn(__fsub_rn(lam[b * bp + k], m.x), m.y) : 0.f;
-      c[u] = k < bp ? Ts[k * nb + j] : 0.f;
-    }
-    block_solve(solve, steps, guard, d, c, x);
+      for (int u = 0; u < 2; u++) {
+        const int k = lane + 32 * u;
+        d[u] = k < bp ? __fsub_rn(__fsub_rn(lam[b * bp + k], m.x), m.y) : 0.f;
+        c[u] = k < bp ? Ts[k * nb + j] : 0.f;
+      }
+      block_solve(solve, steps, guard, d, c, x);
 #pragma unroll
-    for (int u = 0; u < 2; u++) {
-      const int k = lane + 32 * u;
-      if (k < bp) Ts[k * nb + j] = x[u];
+      for (int u = 0; u < 2; u++) {
+        const int k = lane + 32 * u;
+        if (k < bp) Ts[k * nb + j] = x[u];
+      }
     }
-  }
   __syncthreads();
-  for (int e = tid; e < bp * nb; e += nt) {  // W = Q T
-    const int i = e / nb, j = e % nb;
-    if (o + i >= n_act) continue;
-    float s = 0.f;
-    for (int k = 0; k < bp; k++) s = fmaf(Qs[k * bp + i], Ts[k * nb + j], s);
-    W[(o + i) * nb + j] = f32_to_f64(s);
-  }
+  if (valid)
+    for (int e = tid; e < bp * nb; e += nt) {  // W = Q T
+      const int i = e / nb, j = e % nb;
+      if (o + i >= n_act) continue;
+      float sum = 0.f;
+      for (int k = 0; k < bp; k++) sum = fmaf(Qs[k * bp + i], Ts[k * nb + j], sum);
+      W[(o + i) * nb + j] = f32_to_f64(sum);
+    }
 }
 
 __global__ void __launch_bounds__(256) k_block_apply(int bp, int64_t n_act, const float* __restrict__ Q,
@@ -317,7 +323,19 @@ __global__ void __launch_bounds__(256) k_block_apply(int bp, int64_t n_act, cons
                                                      float guard, const double* __restrict__ R, double* __restrict__ W,
                                                      int nb, int solve, int steps) {
   extern __shared__ float sm[];
-  block_apply_body(bp, n_act, Q, lam, mu, guard, R, W, nb, solve, steps, blockIdx.x, sm);
+  block_apply_body(bp, n_act, Q, lam, mu, guard, R, W, nb, solve, steps, blockIdx.x, sm, threadIdx.x, blockDim.x,
+                   true);
+}
+
+// Blocks per CTA of the batched apply: with nb <= 8 a block takes 32 nb threads (one warp per
+// column in the Krylov solve, one thread per element in the products), and 8 / nb blocks share a
+// 256-thread CTA, as many as fit in 48 KB of shared memory.
+__host__ __device__ inline int blocks_per_cta(int bp, int nb) {
+  if (nb > 8) return 1;
+  int k = 8 / nb;
+  const int per = (bp * bp + 2 * bp * nb) * 4;
+  while (k > 1 && k * per > 48 * 1024) k--;
+  return k;
 }
 
 // Batched apply: job fields P0 (Q), P1 (lambda), C (mu), A (R), Y (W), x0 (nb), x1 (bp), n (rows),
@@ -330,8 +348,15 @@ __global__ void __launch_bounds__(256) k_block_apply_batch(const lob_bjob* __res
     if (jobs[mid].cta_begin <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
   }
   const lob_bjob& j = jobs[lo];
-  block_apply_body(j.x1, j.n, reinterpret_cast<const float*>(j.P0), reinterpret_cast<const float*>(j.P1), j.C,
-                   (float)j.s0, j.A, j.Y, j.x0, j.x2, j.x3, (int64_t)blockIdx.x - j.cta_begin, sm);
+  const int bp = j.x1, nb = j.x0;
+  const int bpc = blocks_per_cta(bp, nb);
+  const int tpb = nb > 8 ? 256 : 32 * nb;  // threads of one block
+  const int sub = threadIdx.x / tpb;
+  const int64_t b = ((int64_t)blockIdx.x - j.cta_begin) * bpc + sub;
+  const bool valid = sub < bpc && b * bp < j.n;
+  block_apply_body(bp, j.n, reinterpret_cast<const float*>(j.P0), reinterpret_cast<const float*>(j.P1), j.C,
+                   (float)j.s0, j.A, j.Y, nb, j.x2, j.x3, b, sm + (sub < bpc ? sub : 0) * (bp * bp + 2 * bp * nb),
+                   threadIdx.x % tpb, tpb, valid);
 }
 
 }  // namespace
@@ -390,15 +415,20 @@ int lob_precond_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs,
                              cudaStream_t st) {
   if (njobs <= 0) return LOB_OK;
   int64_t ctas = 0;
+  size_t smem = 0;
   for (int i = 0; i < njobs; i++) {
     lob_bjob& j = jobs_host[i];
     if (j.x1 < 1 || j.x1 > 64 || j.x0 < 1 || j.x0 > 64) return LOB_ERR_ARG;
+    const int bpc = blocks_per_cta(j.x1, j.x0);
     j.cta_begin = ctas;
-    ctas += (j.n + j.x1 - 1) / j.x1;
+    ctas += ((j.n + j.x1 - 1) / j.x1 + bpc - 1) / bpc;
+    const size_t need = (size_t)bpc * ((size_t)j.x1 * j.x1 + 2ull * j.x1 * j.x0) * sizeof(float);
+    if (need > smem) smem = need;
   }
   if (ctas == 0) return LOB_OK;
+  (void)bpmax;
+  (void)nbmax;
   LOB_CUDA(cudaMemcpyAsync(jobs_dev, jobs_host, njobs * sizeof(lob_bjob), cudaMemcpyHostToDevice, st));
-  const size_t smem = ((size_t)bpmax * bpmax + 2ull * bpmax * nbmax) * sizeof(float);
   (k_block_apply_batch<<<(unsigned)ctas, 256, smem, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
   LOB_CUDA(cudaGetLastError());
   return LOB_OK;
