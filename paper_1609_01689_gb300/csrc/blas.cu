@@ -284,12 +284,16 @@ __global__ void __launch_bounds__(256) k_gram_batch(const lob_bjob* __restrict__
 // t + 512, t + 768 over all rows of the chunk; with P <= 128 blocks the 256 threads form
 // G = floor(256 / P) groups of P that split the rows, and the groups' sums are added in a fixed
 // order at the end. Job fields as k_gram_batch.
-template <bool DF>
+// FUSED: G = A^T B and M = A^T A of a symmetric pair in one pass (p == q, sym, at most 128
+// blocks): the staged rows of A serve as M's second operand, so M costs no staging of its own.
+// M's partials go to W1.
+template <bool DF, bool FUSED>
 __global__ void __launch_bounds__(256) k_gram_pairs_batch(const lob_bjob* __restrict__ jobs, int njobs) {
   using R = Ar<DF>;
   using in_t = typename R::in_t;
   using acc_t = typename R::acc_t;
   constexpr int PMAX = 48;
+  constexpr int PER = FUSED ? 1 : 4;  // blocks a thread at most
   __shared__ in_t As[RB * PMAX];
   __shared__ in_t Bs[RB * PMAX];
   __shared__ double gsum[4][256];
@@ -304,13 +308,13 @@ __global__ void __launch_bounds__(256) k_gram_pairs_batch(const lob_bjob* __rest
   const int P = nblocks;                           // threads of a row group
   const int G = nblocks <= 128 ? 256 / P : 1;      // row groups (threads past G P idle)
   const int slot = G > 1 ? tid % P : tid, grp = G > 1 ? tid / P : 0;
-  const int per = G > 1 ? 1 : 4;
-  int ba[4], bb[4];
-  acc_t acc[4][4];
+  const int per = G > 1 ? 1 : PER;
+  int ba[PER], bb[PER];
+  acc_t acc[PER][4], acm[PER][4];
 #pragma unroll
-  for (int u = 0; u < 4; u++) {
+  for (int u = 0; u < PER; u++) {
 #pragma unroll
-    for (int e = 0; e < 4; e++) R::zero(acc[u][e]);
+    for (int e = 0; e < 4; e++) { R::zero(acc[u][e]); R::zero(acm[u][e]); }
     int idx = slot + 256 * u;
     ba[u] = -1;
     bb[u] = 0;
@@ -342,7 +346,7 @@ __global__ void __launch_bounds__(256) k_gram_pairs_batch(const lob_bjob* __rest
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < 4; u++) {
+    for (int u = 0; u < PER; u++) {
       if (ba[u] < 0) continue;
       for (int i = grp; i < RS; i += G) {
         const in_t* ar = As + i * pe;
@@ -352,6 +356,13 @@ __global__ void __launch_bounds__(256) k_gram_pairs_batch(const lob_bjob* __rest
         R::mac(acc[u][1], a0, b1);
         R::mac(acc[u][2], a1, b0);
         R::mac(acc[u][3], a1, b1);
+        if (FUSED) {
+          const in_t c0 = ar[bb[u]], c1 = ar[bb[u] + 1];
+          R::mac(acm[u][0], a0, c0);
+          R::mac(acm[u][1], a0, c1);
+          R::mac(acm[u][2], a1, c0);
+          R::mac(acm[u][3], a1, c1);
+        }
       }
     }
     __syncthreads();
@@ -359,28 +370,36 @@ __global__ void __launch_bounds__(256) k_gram_pairs_batch(const lob_bjob* __rest
   const int pq = p * q;
   if (G > 1) {
     // fixed-order sum over the row groups (FP64 values of each group's partials)
+    for (int out = 0; out < (FUSED ? 2 : 1); out++) {
+      acc_t* ac = out == 0 ? acc[0] : acm[0];
+      double* W = out == 0 ? j.W0 : j.W1;
+      if (out) __syncthreads();  // the first product's sums have been read
 #pragma unroll
-    for (int e = 0; e < 4; e++) gsum[e][tid] = ba[0] >= 0 ? R::out(acc[0][e]) : 0.0;
-    __syncthreads();
-    if (grp == 0 && ba[0] >= 0) {
+      for (int e = 0; e < 4; e++) gsum[e][tid] = ba[0] >= 0 ? R::out(ac[e]) : 0.0;
+      __syncthreads();
+      if (grp == 0 && ba[0] >= 0) {
 #pragma unroll
-      for (int e = 0; e < 4; e++) {
-        const int a = ba[0] + e / 2, b = bb[0] + e % 2;
-        if (a >= p || b >= q) continue;
-        double sum = 0.0;
-        for (int g = 0; g < G; g++) sum += gsum[e][g * P + slot];
-        j.W0[(int64_t)chunk * pq + (int64_t)a * q + b] = sum;
+        for (int e = 0; e < 4; e++) {
+          const int a = ba[0] + e / 2, b = bb[0] + e % 2;
+          if (a >= p || b >= q) continue;
+          double sum = 0.0;
+          for (int g = 0; g < G; g++) sum += gsum[e][g * P + slot];
+          W[(int64_t)chunk * pq + (int64_t)a * q + b] = sum;
+        }
       }
     }
     return;
   }
 #pragma unroll
-  for (int u = 0; u < 4; u++) {
+  for (int u = 0; u < PER; u++) {
     if (ba[u] < 0) continue;
 #pragma unroll
     for (int e = 0; e < 4; e++) {
       const int a = ba[u] + e / 2, b = bb[u] + e % 2;
-      if (a < p && b < q) j.W0[(int64_t)chunk * pq + (int64_t)a * q + b] = R::out(acc[u][e]);
+      if (a < p && b < q) {
+        j.W0[(int64_t)chunk * pq + (int64_t)a * q + b] = R::out(acc[u][e]);
+        if (FUSED) j.W1[(int64_t)chunk * pq + (int64_t)a * q + b] = R::out(acm[u][e]);
+      }
     }
   }
 }
@@ -488,31 +507,44 @@ int lob_gram_chunks(int64_t n, int p, int q) {
 }
 
 int lob_gram_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pqmax, int mode,
-                          lob_bjob* red_host, lob_bjob* red_dev, cudaStream_t st, int pairs) {
+                          lob_bjob* red_host, lob_bjob* red_dev, cudaStream_t st, int pairs, int fused) {
   if (njobs <= 0) return LOB_OK;
   if (pqmax > TG) return LOB_ERR_ARG;
   for (int i = 0; pairs && i < njobs; i++) {
     const lob_bjob& j = jobs_host[i];
     const int bp = (j.p + 1) / 2, bq = (j.q + 1) / 2;
-    if ((j.x1 ? bp * (bp + 1) / 2 : bp * bq) > 1024 || j.p > 48 || j.q > 48) return LOB_ERR_ARG;
+    const int nbl = j.x1 ? bp * (bp + 1) / 2 : bp * bq;
+    if (nbl > 1024 || j.p > 48 || j.q > 48) return LOB_ERR_ARG;
+    if (fused && (nbl > 128 || j.p != j.q || !j.x1 || !j.W1 || !j.D)) return LOB_ERR_ARG;
   }
+  if (fused && !pairs) return LOB_ERR_ARG;
+  // reductions: one per product (two per fused job: G from W0 into Y, M from W1 into D)
   int64_t ctas = 0, rctas = 0;
+  int nred = 0;
   for (int i = 0; i < njobs; i++) {
     lob_bjob& j = jobs_host[i];
     j.cta_begin = ctas;
     ctas += j.x0;
-    red_host[i] = j;
-    red_host[i].cta_begin = rctas;
-    rctas += ((int64_t)j.p * j.q * 32 + 255) / 256;
+    for (int o = 0; o < (fused ? 2 : 1); o++) {
+      lob_bjob rj = j;
+      if (o == 1) { rj.W0 = j.W1; rj.Y = const_cast<double*>(j.D); }  // a fused job carries M's output in D
+      rj.cta_begin = rctas;
+      rj.x3 = pairs ? 1 : 0;  // which entries of a symmetric result were formed
+      red_host[nred++] = rj;
+      rctas += ((int64_t)j.p * j.q * 32 + 255) / 256;
+    }
   }
   LOB_CUDA(cudaMemcpyAsync(jobs_dev, jobs_host, njobs * sizeof(lob_bjob), cudaMemcpyHostToDevice, st));
-  LOB_CUDA(cudaMemcpyAsync(red_dev, red_host, njobs * sizeof(lob_bjob), cudaMemcpyHostToDevice, st));
+  LOB_CUDA(cudaMemcpyAsync(red_dev, red_host, nred * sizeof(lob_bjob), cudaMemcpyHostToDevice, st));
   const int U = pqmax <= 16 ? 1 : (pqmax <= 32 ? 2 : 3);
   if (pairs) {
-    for (int i = 0; i < njobs; i++) red_host[i].x3 = 1;
-    LOB_CUDA(cudaMemcpyAsync(red_dev, red_host, njobs * sizeof(lob_bjob), cudaMemcpyHostToDevice, st));
-    if (mode == LOB_SPMM_MIXED) (k_gram_pairs_batch<true><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
-    else (k_gram_pairs_batch<false><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
+    if (mode == LOB_SPMM_MIXED) {
+      if (fused) (k_gram_pairs_batch<true, true><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
+      else (k_gram_pairs_batch<true, false><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
+    } else {
+      if (fused) (k_gram_pairs_batch<false, true><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
+      else (k_gram_pairs_batch<false, false><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
+    }
   } else if (mode == LOB_SPMM_MIXED) {
     if (U == 1) (k_gram_batch<true, 1><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
     else if (U == 2) (k_gram_batch<true, 2><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
@@ -522,7 +554,7 @@ int lob_gram_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, in
     else if (U == 2) (k_gram_batch<false, 2><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
     else (k_gram_batch<false, 3><<<(unsigned)ctas, 256, 0, st>>>(jobs_dev, njobs), LOB_LAUNCHED());
   }
-  (k_gram_reduce_batch<<<(unsigned)rctas, 256, 0, st>>>(red_dev, njobs), LOB_LAUNCHED());
+  (k_gram_reduce_batch<<<(unsigned)rctas, 256, 0, st>>>(red_dev, nred), LOB_LAUNCHED());
   LOB_CUDA(cudaGetLastError());
   return LOB_OK;
 }

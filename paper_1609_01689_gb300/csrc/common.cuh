@@ -187,9 +187,11 @@ size_t lob_rr_work_doubles(int m);
 // host job tables (pinned, left untouched until the stream passes) to the device tables.
 int lob_gram_chunks(int64_t n, int p, int q);
 // pairs: use the 2 x 2-block kernel (every job with at most 1,024 blocks); else one tile of
-// edge 16, 32 or 48 (pqmax).
+// edge 16, 32 or 48 (pqmax). fused (pairs only): every job computes G = A^T B into Y and
+// M = A^T A into D (partials W0 and W1; symmetric, p == q, at most 128 blocks); red_host must
+// hold 2 njobs entries.
 int lob_gram_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pqmax, int mode,
-                          lob_bjob* red_host, lob_bjob* red_dev, cudaStream_t st, int pairs = 0);
+                          lob_bjob* red_host, lob_bjob* red_dev, cudaStream_t st, int pairs = 0, int fused = 0);
 int lob_lincomb_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int pmax, int qmax, int mode,
                              cudaStream_t st);
 int lob_precond_batch_launch(lob_bjob* jobs_host, lob_bjob* jobs_dev, int njobs, int bpmax, int nbmax,

@@ -281,22 +281,42 @@ inline int tile_class(const lob_bjob& j) {
   return e <= 16 ? 1 : (e <= 32 ? 2 : 3);
 }
 
+// Classes: (arithmetic, tile class, fused); fused jobs (x3 == 2: G and M of one solve in one pass)
+// are all of tile class 0.
 int gram_batch(lob_engine* E, std::vector<lob_bjob>& v, int) {
   for (int blas : {LOB_SPMM_FP64, LOB_SPMM_MIXED})
-    for (int u = 0; u <= 3; u++) {
-      size_t cnt = 0;
-      for (const lob_bjob& j : v) cnt += j.x2 == blas && tile_class(j) == u;
-      if (!cnt) continue;
-      lob_bjob *d1 = nullptr, *d2 = nullptr;
-      lob_bjob* h1 = E->take(cnt, &d1);
-      lob_bjob* h2 = E->take(cnt, &d2);
-      if (!h1 || !h2) return LOB_ERR_NOMEM;
-      int i = 0;
-      for (const lob_bjob& j : v)
-        if (j.x2 == blas && tile_class(j) == u) h1[i++] = j;
-      LOB_TRY(lob_gram_batch_launch(h1, d1, (int)cnt, u == 0 ? 48 : 16 * u, blas, h2, d2, E->st, u == 0));
-    }
+    for (int u = 0; u <= 3; u++)
+      for (int fused = 0; fused <= (u == 0 ? 1 : 0); fused++) {
+        auto in_class = [&](const lob_bjob& j) { return j.x2 == blas && tile_class(j) == u && (j.x3 == 2) == (fused == 1); };
+        size_t cnt = 0;
+        for (const lob_bjob& j : v) cnt += in_class(j);
+        if (!cnt) continue;
+        lob_bjob *d1 = nullptr, *d2 = nullptr;
+        lob_bjob* h1 = E->take(cnt, &d1);
+        lob_bjob* h2 = E->take(fused ? 2 * cnt : cnt, &d2);
+        if (!h1 || !h2) return LOB_ERR_NOMEM;
+        int i = 0;
+        for (const lob_bjob& j : v)
+          if (in_class(j)) h1[i++] = j;
+        LOB_TRY(lob_gram_batch_launch(h1, d1, (int)cnt, u == 0 ? 48 : 16 * u, blas, h2, d2, E->st, u == 0, fused));
+      }
   return LOB_OK;
+}
+
+// G = S^T H S into G and M = S^T S into M: one fused job when the solve's 2 x 2 blocks fit one
+// row-group pass (m <= 30), else two jobs
+void push_gm(std::vector<lob_bjob>& v, const lob_ltask* t) {
+  const int bp = (t->m + 1) / 2;
+  if (bp * (bp + 1) / 2 <= 128) {
+    lob_bjob j = gram_job(t, t->S, t->m, t->HS, t->m, t->G, t->gw, 1);
+    j.W1 = t->gw + t->gw_half;
+    j.D = t->Mm;
+    j.x3 = 2;
+    v.push_back(j);
+  } else {
+    v.push_back(gram_job(t, t->S, t->m, t->HS, t->m, t->G, t->gw, 1));
+    v.push_back(gram_job(t, t->S, t->m, t->S, t->m, t->Mm, t->gw + t->gw_half, 1));
+  }
 }
 
 inline int width_class(const lob_bjob& j) { return j.q <= 1 ? 1 : (j.q <= 2 ? 2 : (j.q <= 4 ? 4 : (j.q <= 8 ? 8 : 16))); }
@@ -716,8 +736,7 @@ static int engine_round(lob_engine* E, std::vector<lob_ltask*>& done) {
   }
   LOB_TRY(copy_batch(E, j_post));
   for (lob_ltask* t : rr_tasks) {
-    j_g.push_back(gram_job(t, t->S, t->m, t->HS, t->m, t->G, t->gw, 1));
-    j_g.push_back(gram_job(t, t->S, t->m, t->S, t->m, t->Mm, t->gw + t->gw_half, 1));
+    push_gm(j_g, t);
     lob_bjob r = rr_job(t, t->m, t->G, t->Mm, t->theta, t->Cc, 0);
     r.I0 = info_dev(E, t, 2);
     j_rr.push_back(r);
@@ -745,8 +764,7 @@ static int engine_round(lob_engine* E, std::vector<lob_ltask*>& done) {
         t->restarts++;
         t->pok = false;
         t->m = t->nb + t->na;
-        j_g2.push_back(gram_job(t, t->S, t->m, t->HS, t->m, t->G, t->gw, 1));
-        j_g2.push_back(gram_job(t, t->S, t->m, t->S, t->m, t->Mm, t->gw + t->gw_half, 1));
+        push_gm(j_g2, t);
         lob_bjob r = rr_job(t, t->m, t->G, t->Mm, t->theta, t->Cc, 0);
         r.I0 = info_dev(E, t, 2);
         j_rr2.push_back(r);
