@@ -189,7 +189,8 @@ typedef struct {
   int32_t precond_steps;   /* Krylov steps for FOM / MINRES, 1..3; 0 = 3 */
   int32_t verbose;
   double mixed_tol;        /* MIXED: relative residual at which the FP32-value phase stops
-                              (0 = max(tol, 1e-6)) */
+                              (0 = max(tol, 1e-7); a phase that stalls near its FP32
+                              floor hands over to the FP64-class phase earlier) */
   void* stream;
 } lob_solve_opts;
 

@@ -15,6 +15,13 @@
 // The guess cannot be better than eq. 12 itself: on the n = 500,000 workload 1e-3 gives the
 // main solve the same iteration count as 1e-4 (21) at a lower cost, and 1e-2 costs 6 more.
 #define LOB_GUESS_TOL 1e-3
+// Mixed solver, FP32-value phase: default target (relative residual) and the number of
+// iterations without the worst residual halving after which it hands over to the FP64-class
+// phase. The target sits near the floor of the FP32-value product (values and X rounded to FP32,
+// FP32 products and in-tile sums: ~1e-7 of |H||X|); a solve that cannot reach it stalls and hands
+// over after LOB_MIXED_STALL iterations instead.
+#define LOB_MIXED_TOL 1e-7
+#define LOB_MIXED_STALL 12
 #define LOB_PERM_CHUNK 4096  // entries per SpMM chunk (column-order permutation granularity)
 
 // Report a failed CUDA call and return LOB_ERR_CUDA from the enclosing function.

@@ -605,7 +605,7 @@ int lob_task::step() {
         if (o.mode == LOB_MODE_MIXED && phase == 0) {
           // phase 1: FP32-value SpMM down to the FP32 floor
           spmm_mode = LOB_SPMM_MIXED;
-          run_tol = o.mixed_tol > 0.0 ? o.mixed_tol : (tol > 1e-6 ? tol : 1e-6);
+          run_tol = o.mixed_tol > 0.0 ? o.mixed_tol : (tol > LOB_MIXED_TOL ? tol : LOB_MIXED_TOL);
           run_max = max_iter;
         } else if (o.mode == LOB_MODE_MIXED) {
           // phase 2: FP64-class refinement products from the phase-1 vectors
@@ -669,10 +669,10 @@ int lob_task::step() {
           for (int j = 0; j < k; j++)
             if (!(hb->relres[j] <= run_tol)) worst = fmax(worst, hb->relres[j]);
           if (worst < 0.5 * best_res) { best_res = worst; best_it = it; }
-          // MIXED, FP32-value phase: no halving of the worst residual in 40 iterations means the
+          // MIXED, FP32-value phase: no halving of the worst residual in LOB_MIXED_STALL iterations means the
           // FP32 products limit it (a near-degenerate pair at the edge of the block, say); the
           // FP64-class phase takes over from here
-          if (o.mode == LOB_MODE_MIXED && phase == 0 && it - best_it >= 40) {
+          if (o.mode == LOB_MODE_MIXED && phase == 0 && it - best_it >= LOB_MIXED_STALL) {
             run_status = LOB_ERR_NOCONV;
             pc = PC_RUN_END;
             continue;
@@ -779,7 +779,7 @@ int lob_task::step() {
         restarts_total += restarts;
         if (o.mode == LOB_MODE_MIXED && phase == 1) stats.refine_iterations = it;
         if (run_status != LOB_OK && run_status != LOB_ERR_NOCONV) { status = run_status; pc = PC_END; continue; }
-        // the FP64-class phase, unless the FP32-value phase already met the final tol (tol >= 1e-6)
+        // the FP64-class phase, unless the FP32-value phase already met the final tol
         if (o.mode == LOB_MODE_MIXED && phase == 0 && !(run_status == LOB_OK && run_tol <= tol)) {
           phase = 1;
           pc = PC_PHASE;

@@ -474,7 +474,7 @@ double relres_host(lob_engine* E, lob_ltask* t, int j) { return E->h_relres[(siz
 
 void set_phase(lob_ltask* t) {
   if (t->o.mode == LOB_MODE_MIXED && t->phase == 0) {
-    t->run_tol = t->o.mixed_tol > 0.0 ? t->o.mixed_tol : (t->tol > 1e-6 ? t->tol : 1e-6);
+    t->run_tol = t->o.mixed_tol > 0.0 ? t->o.mixed_tol : (t->tol > LOB_MIXED_TOL ? t->tol : LOB_MIXED_TOL);
     t->run_max = t->max_iter;
   } else {
     t->run_tol = t->tol;
@@ -583,16 +583,16 @@ static int engine_round(lob_engine* E, std::vector<lob_ltask*>& done) {
       if (!(r <= t->run_tol)) worst = fmax(worst, r);
     }
     if (worst < 0.5 * t->best_res) { t->best_res = worst; t->best_it = t->it; }
-    // MIXED, FP32-value phase: no halving of the worst residual in 40 iterations -> the FP64-class
+    // MIXED, FP32-value phase: no halving of the worst residual in LOB_MIXED_STALL iterations -> the FP64-class
     // phase takes over from here
-    if (!conv && t->o.mode == LOB_MODE_MIXED && t->phase == 0 && t->it - t->best_it >= 40) {
+    if (!conv && t->o.mode == LOB_MODE_MIXED && t->phase == 0 && t->it - t->best_it >= LOB_MIXED_STALL) {
       t->status = LOB_ERR_NOCONV;
       conv = true;
     }
     if (conv) {
       t->iters_total += t->it;
       if (t->o.mode == LOB_MODE_MIXED && t->phase == 1) t->refine_its = t->it;
-      // the FP64-class phase, unless the FP32-value phase already met the final tol (tol >= 1e-6)
+      // the FP64-class phase, unless the FP32-value phase already met the final tol
       if (t->o.mode == LOB_MODE_MIXED && t->phase == 0 && !(t->status == LOB_OK && t->run_tol <= t->tol)) {
         t->phase = 1;
         t->status = LOB_OK;
