@@ -23,6 +23,10 @@
 #define LOB_MIXED_TOL 1e-7
 #define LOB_MIXED_STALL 12
 #define LOB_PERM_CHUNK 4096  // entries per SpMM chunk (column-order permutation granularity)
+// Slack entries after every per-entry array of the tile store (and 16 bytes per slack entry
+// after the chunk pointers): the SpMM copies 16-byte aligned windows around a chunk and may
+// read up to 15 bytes past the last entry.
+#define LOB_STORE_PAD 8
 
 // Report a failed CUDA call and return LOB_ERR_CUDA from the enclosing function.
 #define LOB_CUDA(call)                                                                          \
@@ -137,6 +141,8 @@ void lob_free_precond(lob_precond* P);
 int lob_ensure_xs(const lob_matrix* m, size_t need);
 // Y = H X over the active leading n_act x n_act block (n_act <= n; rows/cols >= n_act are
 // treated as absent). Y is fully written (rows >= n_act get 0).
+// Nonzero once an SpMM wait ran out of time since the last call (then cleared); synchronises.
+int lob_spmm_fault_take();
 int lob_spmm_launch(const lob_matrix* m, int mode, const double* X, double* Y, int nb, int64_t n_act,
                     cudaStream_t st);
 // Y_j = H_j X_j for several matrices in as few launches as possible (one per arithmetic

@@ -897,5 +897,9 @@ int lob_solve_impl(lob_matrix* m, int32_t k, int32_t nb, double tol, const doubl
     }
   }
   lob_task_destroy(t);
+  if ((rc == LOB_OK || rc == LOB_ERR_NOCONV) && lob_spmm_fault_take() != 0) {
+    fprintf(stderr, "lob: an SpMM wait ran out of time; the result is not valid\n");
+    rc = LOB_ERR_CUDA;
+  }
   return rc;
 }

@@ -323,6 +323,325 @@ __global__ void __launch_bounds__(Cfg<MIXED, NB>::THREADS, Cfg<MIXED, NB>::MINB)
   }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Ring-pipelined variant of the FP32-value product (MIXED, NB = 16): same ownership and
+// arithmetic as k_spmm4, without its two CTA-wide barriers per chunk.
+//
+// Each CTA is persistent and takes a contiguous range of tile rows holding about 1/grid of the
+// stored entries. The chunks of that range pass through a ring of D shared-memory stages. A
+// stage is filled by bulk async copies (records, values, permutation, chunk pointers and X_J)
+// that complete on the stage's mbarrier; a warp waits on that barrier, works the chunk, and
+// counts itself out of the stage with a shared-memory counter. The warp that counts out last
+// refills the stage with the chunk D places further on. So warps drift apart by up to D chunks
+// instead of meeting at every chunk: the work of a lane group differs from chunk to chunk (the
+// row and column counts of a tile are uneven) and the slack absorbs most of it. X_I has two
+// slots, refilled the same way by the last warp to finish a tile row.
+//
+// Every wait is bounded (about 2^32 SM clocks); a wait that runs out records it in
+// lob_spmm_fault and the warp leaves the kernel. Copies are only issued for chunks that all
+// warps go on to wait for, so none is in flight when the CTA ends.
+// ---------------------------------------------------------------------------------------------
+__device__ int lob_spmm_fault = 0;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// Bulk global -> shared copy completing on bar; addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// Wait, with the whole warp, for the completion of the phase with the given parity. Every
+// lane waits (each acquires the copied data); the outcome is warp-uniform. False if the wait
+// ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (__all_sync(0xffffffffu, done != 0)) return true;
+    if (__any_sync(0xffffffffu, clock64() - t0 > (1ll << 32))) {
+      if ((threadIdx.x & 31) == 0) atomicExch(&lob_spmm_fault, 1);
+      return false;
+    }
+  }
+}
+
+// The chunk walk of one CTA: tile rows [I, Ie), in each the tiles left after trimming to the
+// active rows, in each tile its chunks.
+struct RingCur {
+  int64_t I, Ie, t, t1;
+  int32_t k, nk;
+};
+
+template <int NB>
+struct CfgR {
+  static constexpr int VW = 4;  // FP32 vector columns per lane (one 16-byte slice)
+  static constexpr int G = NB / VW;
+  static constexpr int THREADS = LOB_TILE * G;  // one lane group per in-tile row and column
+  static constexpr int NW = THREADS / 32;
+  static constexpr int D = 3;  // ring stages
+  static constexpr int CH = LOB_PERM_CHUNK;
+  static constexpr int PTRS = 2 * (LOB_TILE + 1);
+  static constexpr size_t XV = sizeof(float) * LOB_TILE * NB;
+  // one stage: records and values (16-byte aligned window around the chunk), permutation,
+  // chunk pointers, X_J
+  static constexpr size_t S_RC = 0;
+  static constexpr size_t S_VV = S_RC + 4 * (CH + 8);
+  static constexpr size_t S_PM = S_VV + 4 * (CH + 8);
+  static constexpr size_t S_PT = S_PM + 2 * (CH + 16);
+  static constexpr size_t S_XJ = (S_PT + 2 * PTRS + 32 + 15) / 16 * 16;
+  static constexpr size_t STAGE = S_XJ + XV;
+  static constexpr size_t XI = 0;              // two X_I slots
+  static constexpr size_t ST = XI + 2 * XV;    // D stages
+  static constexpr size_t BAR = ST + D * STAGE;  // full[D], xfull[2] (8 B each)
+  static constexpr size_t RNG = BAR + 8 * (D + 2);  // this CTA's tile rows [Ib, Ie)
+  static constexpr size_t CUR = RNG + 16;           // the refill cursor
+  static constexpr size_t CNT = CUR + 48;           // stage and X_I counters
+  static constexpr size_t BYTES = CNT + 4 * (D + 2);
+  static_assert(VW * G == NB && THREADS <= 1024 && THREADS % 32 == 0, "launch shape");
+  static_assert(sizeof(RingCur) <= 48, "cursor slot");
+  static_assert(S_VV % 16 == 0 && S_PM % 16 == 0 && S_PT % 16 == 0 && STAGE % 16 == 0 && ST % 16 == 0,
+                "bulk copy destinations must be 16-byte aligned");
+};
+
+__device__ __forceinline__ int64_t ring_trim(const int64_t* rowptr, const int32_t* tcol, int64_t n_act, int64_t I,
+                                             int64_t* t0) {
+  *t0 = rowptr[I];
+  int64_t t1 = rowptr[I + 1];
+  while (t1 > *t0 && (int64_t)tcol[t1 - 1] * LOB_TILE >= n_act) t1--;
+  return t1;
+}
+
+// Move c to the first chunk at or after its position (k == nk means "past this tile").
+// Returns false at the end of the range.
+__device__ __forceinline__ bool ring_settle(RingCur& c, const int64_t* rowptr, const int32_t* tcol,
+                                           const int32_t* tchunk, int64_t n_act) {
+  while (c.k >= c.nk) {
+    c.t++;
+    c.k = 0;
+    while (c.t >= c.t1) {
+      c.I++;
+      if (c.I >= c.Ie) return false;
+      int64_t t0;
+      c.t1 = ring_trim(rowptr, tcol, n_act, c.I, &t0);
+      c.t = t0;
+    }
+    c.nk = tchunk[c.t + 1] - tchunk[c.t];
+  }
+  return true;
+}
+
+// Issue the copies of chunk (t, k) of tile row I into a stage.
+template <int NB>
+__device__ __forceinline__ void ring_issue(unsigned char* stage, uint64_t* bar, int64_t I, int64_t t, int k,
+                                           const int32_t* tcol, const int64_t* tptr, const int32_t* tchunk,
+                                           const uint32_t* rc, const float* vals, const uint16_t* cperm,
+                                           const uint16_t* cptrs, const float* Xs) {
+  using C = CfgR<NB>;
+  const int64_t J = tcol[t];
+  const int64_t base = tptr[t] + (int64_t)k * C::CH;
+  const int64_t rem = tptr[t + 1] - base;
+  const int64_t cnt = rem < C::CH ? rem : C::CH;
+  const int64_t a0 = base & ~(int64_t)3, e1 = (base + cnt + 3) & ~(int64_t)3;      // 4-byte arrays
+  const int64_t p0 = base & ~(int64_t)7, p1 = (base + cnt + 7) & ~(int64_t)7;      // 2-byte array
+  const int64_t bo = (int64_t)(tchunk[t] + k) * (C::PTRS * 2);                     // chunk pointers, bytes
+  const int64_t q0 = bo & ~(int64_t)15, q1 = (bo + C::PTRS * 2 + 15) & ~(int64_t)15;
+  const uint32_t brc = (uint32_t)((e1 - a0) * 4), bpm = (uint32_t)((p1 - p0) * 2), bpt = (uint32_t)(q1 - q0);
+  const uint32_t bxj = (J != I) ? (uint32_t)C::XV : 0u;
+  mbar_expect_tx(bar, 2 * brc + bpm + bpt + bxj);
+  bulk_g2s(stage + C::S_RC, rc + a0, brc, bar);
+  bulk_g2s(stage + C::S_VV, vals + a0, brc, bar);
+  bulk_g2s(stage + C::S_PM, cperm + p0, bpm, bar);
+  bulk_g2s(stage + C::S_PT, reinterpret_cast<const unsigned char*>(cptrs) + q0, bpt, bar);
+  if (bxj) bulk_g2s(stage + C::S_XJ, Xs + J * LOB_TILE * NB, bxj, bar);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(CfgR<NB>::THREADS, 1)
+    k_spmm_ring(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ tcol,
+                const int64_t* __restrict__ tptr, const int32_t* __restrict__ tchunk,
+                const uint32_t* __restrict__ rc, const float* __restrict__ vals,
+                const uint16_t* __restrict__ cperm, const uint16_t* __restrict__ cptrs,
+                const float* __restrict__ Xs, double* __restrict__ Y, int ldy, int c0, int w, int64_t n_act,
+                int64_t ntr) {
+  using C = CfgR<NB>;
+  constexpr int VW = C::VW, G = C::G, NW = C::NW, D = C::D, CH = C::CH;
+  constexpr int XN = LOB_TILE * NB;
+  extern __shared__ __align__(16) unsigned char sm[];
+  float* XIb = reinterpret_cast<float*>(sm + C::XI);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + C::BAR);
+  uint64_t* xfull = full + D;
+  int* cnt = reinterpret_cast<int*>(sm + C::CNT);
+  int* xcnt = cnt + D;
+  int64_t* range = reinterpret_cast<int64_t*>(sm + C::RNG);
+  RingCur* cur = reinterpret_cast<RingCur*>(sm + C::CUR);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int g = tid / G, gl = tid % G;
+
+  if (tid == 0) {
+    // this CTA's tile rows: entries before row I are tptr[rowptr[I]]; split them evenly
+    const int64_t E = tptr[rowptr[ntr]];
+    auto first_row = [&](int64_t b) -> int64_t {
+      if (b >= (int64_t)gridDim.x) return ntr;
+      const int64_t target = E * b / (int64_t)gridDim.x;
+      int64_t lo = 0, hi = ntr;  // first I with tptr[rowptr[I]] >= target
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (tptr[rowptr[mid]] >= target) hi = mid; else lo = mid + 1;
+      }
+      return lo;
+    };
+    range[0] = first_row(blockIdx.x);
+    range[1] = first_row((int64_t)blockIdx.x + 1);
+    for (int s = 0; s < D; s++) { mbar_init(&full[s], 1); cnt[s] = 0; }
+    for (int s = 0; s < 2; s++) { mbar_init(&xfull[s], 1); xcnt[s] = 0; }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  const int64_t Ib = range[0], Ie = range[1];
+  if (tid == 0 && Ib < Ie) {
+    for (int s = 0; s < 2 && Ib + s < Ie; s++) {
+      mbar_expect_tx(&xfull[s], (uint32_t)C::XV);
+      bulk_g2s(XIb + s * XN, Xs + (Ib + s) * LOB_TILE * NB, (uint32_t)C::XV, &xfull[s]);
+    }
+    RingCur c;
+    c.I = Ib; c.Ie = Ie;
+    int64_t t0;
+    c.t1 = ring_trim(rowptr, tcol, n_act, Ib, &t0);
+    c.t = t0 - 1; c.k = 0; c.nk = 0;  // settle moves to the first chunk
+    bool more = ring_settle(c, rowptr, tcol, tchunk, n_act);
+    for (int s = 0; s < D && more; s++) {
+      ring_issue<NB>(sm + C::ST + s * C::STAGE, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rc, vals, cperm, cptrs,
+                     Xs);
+      c.k++;
+      more = ring_settle(c, rowptr, tcol, tchunk, n_act);
+    }
+    if (!more) c.I = Ie;
+    *cur = c;
+  }
+  __syncthreads();
+
+  int64_t ch = 0;  // chunks this CTA has worked so far
+  for (int64_t I = Ib; I < Ie; I++) {
+    const int64_t ri = I - Ib;
+    const int xs = (int)(ri & 1);
+    if (!mbar_wait(&xfull[xs], (uint32_t)((ri >> 1) & 1))) return;
+    const float* XI = XIb + xs * XN;
+    int64_t t0;
+    const int64_t t1 = ring_trim(rowptr, tcol, n_act, I, &t0);
+    float rh[VW], rl[VW];
+#pragma unroll
+    for (int q = 0; q < VW; q++) { rh[q] = 0.f; rl[q] = 0.f; }
+    for (int64_t t = t0; t < t1; t++) {
+      const int64_t J = tcol[t];
+      const bool diag = (J == I);
+      const int nk = tchunk[t + 1] - tchunk[t];
+      float4 acc_t = make_float4(0.f, 0.f, 0.f, 0.f), acc_c = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int k = 0; k < nk; k++) {
+        const int s = (int)(ch % D);
+        if (!mbar_wait(&full[s], (uint32_t)((ch / D) & 1))) return;
+        unsigned char* stage = sm + C::ST + s * C::STAGE;
+        const int64_t base = tptr[t] + (int64_t)k * CH;
+        const uint32_t* RCs = reinterpret_cast<const uint32_t*>(stage + C::S_RC) + (base & 3);
+        const float* VVs = reinterpret_cast<const float*>(stage + C::S_VV) + (base & 3);
+        const uint16_t* PM = reinterpret_cast<const uint16_t*>(stage + C::S_PM) + (base & 7);
+        const int64_t bo = (int64_t)(tchunk[t] + k) * (C::PTRS * 2);
+        const uint16_t* PR = reinterpret_cast<const uint16_t*>(stage + C::S_PT + (bo & 15));
+        const uint16_t* PC = PR + (LOB_TILE + 1);
+        const float* xj = diag ? XI : reinterpret_cast<const float*>(stage + C::S_XJ);
+        {  // row pass
+          const int s0 = PR[g], e0 = PR[g + 1];
+          float4 acc = acc_t;
+#pragma unroll 4
+          for (int i = s0; i < e0; i++) {
+            const int c = (int)(RCs[i] & 0xFFFFu);
+            const float4 x = *reinterpret_cast<const float4*>(&xj[c * NB + gl * VW]);
+            fma_v(acc, VVs[i], x);
+          }
+          acc_t = acc;
+        }
+        {  // column pass
+          const int s0 = PC[g], e0 = PC[g + 1];
+          float4 acc = acc_c;
+#pragma unroll 4
+          for (int i = s0; i < e0; i++) {
+            const int q = PM[i] & (CH - 1);
+            const int r = (int)(RCs[q] >> 16);
+            if (diag && r == g) continue;  // the diagonal entry is applied once (row pass)
+            const float4 xi = *reinterpret_cast<const float4*>(&XI[r * NB + gl * VW]);
+            fma_v(acc, VVs[q], xi);
+          }
+          acc_c = acc;
+        }
+        // count this warp out of the stage; the last one refills it with the chunk D places on
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence_block();
+          const int old = atomicAdd(&cnt[s], 1);
+          if (old == NW * (int)(ch / D + 1) - 1) {
+            __threadfence_block();
+            RingCur c = *cur;
+            if (c.I < c.Ie) {
+              asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+              ring_issue<NB>(stage, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rc, vals, cperm, cptrs, Xs);
+              c.k++;
+              if (!ring_settle(c, rowptr, tcol, tchunk, n_act)) c.I = c.Ie;
+              *cur = c;
+            }
+            __threadfence_block();
+          }
+        }
+        ch++;
+      }
+      // tile end: column partials to Y_J (FP64 atomics), row partials into the row accumulator
+      const float* ta = reinterpret_cast<const float*>(&acc_t);
+      const float* ca = reinterpret_cast<const float*>(&acc_c);
+#pragma unroll
+      for (int q = 0; q < VW; q++) {
+        df_add(rh[q], rl[q], ta[q], 0.f);
+        if (diag) df_add(rh[q], rl[q], ca[q], 0.f);
+        const int kk = gl * VW + q;
+        const int64_t gr = J * LOB_TILE + g;
+        if (!diag && kk < w && gr < n_act) atomic_out(&Y[gr * ldy + c0 + kk], ca[q]);
+      }
+    }
+    // tile row end: row sums to Y_I
+    const int64_t gr = I * LOB_TILE + g;
+#pragma unroll
+    for (int q = 0; q < VW; q++) {
+      const int kk = gl * VW + q;
+      if (kk >= w || gr >= n_act) continue;
+      if (rh[q] != 0.f) atomicAdd(&Y[gr * ldy + c0 + kk], f32_to_f64(rh[q]));
+      if (rl[q] != 0.f) atomicAdd(&Y[gr * ldy + c0 + kk], f32_to_f64(rl[q]));
+    }
+    // count this warp out of the X_I slot; the last one loads the row two places on into it
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      const int old = atomicAdd(&xcnt[xs], 1);
+      if (old == NW * (int)((ri >> 1) + 1) - 1 && I + 2 < Ie) {
+        __threadfence_block();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_expect_tx(&xfull[xs], (uint32_t)C::XV);
+        bulk_g2s(XIb + xs * XN, Xs + (I + 2) * LOB_TILE * NB, (uint32_t)C::XV, &xfull[xs]);
+      }
+    }
+  }
+}
+
 // FP64-class variant (LOB_SPMM_DF64): values as (hi, lo) FP32 pairs (hi = the FP32 value,
 // lo = the rounded remainder, ~48 significant bits together), X staged as (hi, lo) pairs, every
 // product and sum in double-float (df.cuh) on the FP32 pipes. Same schedule as k_spmm4: lane
@@ -602,6 +921,39 @@ int launch(const lob_matrix* m, const double* X, double* Y, int nb, int64_t n_ac
   return LOB_OK;
 }
 
+// FP32-value product at NB = 16 through the ring kernel: one persistent CTA per SM (fewer when
+// the matrix has fewer tile rows).
+int launch_ring16(const lob_matrix* m, const double* X, double* Y, int nb, int64_t n_act, cudaStream_t st) {
+  constexpr int NB = 16;
+  using C = CfgR<NB>;
+  static_assert(C::BYTES <= 227 * 1024, "shared memory budget");
+  const lob_tiles& TS = m->T;
+  const int64_t nt_act = (n_act + LOB_TILE - 1) / LOB_TILE;
+  if (nt_act == 0) return LOB_OK;
+  const int64_t rows_pad = TS.nt * LOB_TILE;
+  LOB_TRY(lob_ensure_xs(m, (size_t)rows_pad * NB * sizeof(float)));
+  float* Xs = reinterpret_cast<float*>(m->xs);
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    LOB_CUDA(cudaGetDevice(&dev));
+    LOB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int64_t grid = nt_act < sms ? nt_act : sms;
+  LOB_CUDA(cudaFuncSetAttribute(k_spmm_ring<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES));
+  for (int c0 = 0; c0 < nb; c0 += NB) {
+    const int w = (nb - c0) < NB ? (nb - c0) : NB;
+    (k_stage_x<float><<<(unsigned)((rows_pad * NB + 255) / 256), 256, 0, st>>>(rows_pad, n_act, nb, c0, w, NB, X, Xs),
+     LOB_LAUNCHED());
+    (k_spmm_ring<NB><<<(unsigned)grid, C::THREADS, C::BYTES, st>>>(TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rc,
+                                                                  TS.v32, TS.cperm, TS.cptrs, Xs, Y, nb, c0, w,
+                                                                  n_act, nt_act),
+     LOB_LAUNCHED());
+  }
+  LOB_CUDA(cudaGetLastError());
+  return LOB_OK;
+}
+
 template <int MODE, int NB>
 int batch_class(const lob_matrix* const* ms, const double* const* X, double* const* Y, const int* ncol,
                 const int64_t* nact, const std::vector<int>& idx, lob_spmm_job* jobs_host, lob_spmm_job* jobs_dev, cudaStream_t st) {
@@ -702,6 +1054,16 @@ int lob_spmm_batch_launch(const lob_matrix* const* ms, const double* const* X, d
   return LOB_OK;
 }
 
+int lob_spmm_fault_take() {
+  int h = 0;
+  if (cudaMemcpyFromSymbol(&h, lob_spmm_fault, sizeof(int)) != cudaSuccess) return -1;
+  if (h) {
+    const int z = 0;
+    cudaMemcpyToSymbol(lob_spmm_fault, &z, sizeof(int));
+  }
+  return h;
+}
+
 int lob_spmm_launch(const lob_matrix* m, int mode, const double* X, double* Y, int nb, int64_t n_act,
                     cudaStream_t st) {
   if (nb < 1 || nb > 64 || n_act < 0 || n_act > m->T.n) return LOB_ERR_ARG;
@@ -719,7 +1081,7 @@ int lob_spmm_launch(const lob_matrix* m, int mode, const double* X, double* Y, i
   if (mode == LOB_SPMM_MIXED) {
     if (nb <= 4) return launch<true, 4>(m, X, Y, nb, n_act, st);
     if (nb <= 8) return launch<true, 8>(m, X, Y, nb, n_act, st);
-    return launch<true, 16>(m, X, Y, nb, n_act, st);
+    return launch_ring16(m, X, Y, nb, n_act, st);
   }
   if (nb <= 2) return launch<false, 2>(m, X, Y, nb, n_act, st);
   if (nb <= 4) return launch<false, 4>(m, X, Y, nb, n_act, st);

@@ -238,17 +238,16 @@ int lob_build_tiles(const lob_coo* H, int values, cudaStream_t st, lob_tiles* T,
   R.n = n; R.nnz = nnz; R.ntiles = ntiles; R.nt = nt;
   bool ok = cudaMalloc(&R.rowptr, (nt + 1) * 8) == cudaSuccess && cudaMalloc(&R.tcol, ntiles * 4) == cudaSuccess &&
             cudaMalloc(&R.trow, ntiles * 4) == cudaSuccess && cudaMalloc(&R.tptr, (ntiles + 1) * 8) == cudaSuccess &&
-            cudaMalloc(&R.rc, nnz * 4) == cudaSuccess;
-  if (ok && (values & LOB_VALUES_FP64)) ok = cudaMalloc(&R.v64, nnz * 8) == cudaSuccess;
-  if (ok && (values & LOB_VALUES_FP32)) ok = cudaMalloc(&R.v32, nnz * 4) == cudaSuccess;
+            cudaMalloc(&R.rc, (nnz + LOB_STORE_PAD) * 4) == cudaSuccess;
+  if (ok && (values & LOB_VALUES_FP64)) ok = cudaMalloc(&R.v64, (nnz + LOB_STORE_PAD) * 8) == cudaSuccess;
+  if (ok && (values & LOB_VALUES_FP32)) ok = cudaMalloc(&R.v32, (nnz + LOB_STORE_PAD) * 4) == cudaSuccess;
   if (!ok) { cudaGetLastError(); lob_free_tiles(&R); return LOB_ERR_NOMEM; }
   (k_fill<<<nblocks(nnz, bs), bs, 0, st>>>(nnz, skeys, sidx, (const int32_t*)flag.p, (const int32_t*)tid.p, val,
                                           bits_t, R.rc, R.v64, R.v32, R.tptr, R.tcol, R.trow), LOB_LAUNCHED());
   (k_rowptr<<<nblocks(nt + 1, bs), bs, 0, st>>>(nt, ntiles, R.trow, R.rowptr, R.tptr, nnz), LOB_LAUNCHED());
 
   // kernel-private column-order permutation of every chunk (derived from the canonical store)
-  // (+8 entries: the SpMM stages the permutation in 4-byte words and may read one past the end)
-  if (cudaMalloc(&R.cperm, (nnz + 8) * 2) != cudaSuccess) { cudaGetLastError(); lob_free_tiles(&R); return LOB_ERR_NOMEM; }
+  if (cudaMalloc(&R.cperm, (nnz + LOB_STORE_PAD) * 2) != cudaSuccess) { cudaGetLastError(); lob_free_tiles(&R); return LOB_ERR_NOMEM; }
   {
     // reuse the sort buffers: keys0/keys1 (uint64) and idx0/idx1 (32-bit slots, used as uint16)
     uint64_t* pk0 = (uint64_t*)keys0.p;
@@ -291,7 +290,7 @@ int lob_build_tiles(const lob_coo* H, int values, cudaStream_t st, lob_tiles* T,
     const int32_t total_chunks = lastc + lastt;
     R.nchunks = total_chunks;
     LOB_CUDA(cudaMemcpyAsync(R.tchunk + ntiles, &total_chunks, 4, cudaMemcpyHostToDevice, st));
-    if (cudaMalloc(&R.cptrs, (size_t)R.nchunks * 2 * (LOB_TILE + 1) * 2) != cudaSuccess) {
+    if (cudaMalloc(&R.cptrs, (size_t)R.nchunks * 2 * (LOB_TILE + 1) * 2 + 16 * LOB_STORE_PAD) != cudaSuccess) {
       cudaGetLastError(); lob_free_tiles(&R); return LOB_ERR_NOMEM;
     }
     (k_chunk_ptrs<<<(unsigned)R.nchunks, 256, 0, st>>>(ntiles, R.tptr, R.tchunk, R.rc, R.cptrs), LOB_LAUNCHED());
@@ -299,7 +298,7 @@ int lob_build_tiles(const lob_coo* H, int values, cudaStream_t st, lob_tiles* T,
   }
 
   if (R.v64 && R.v32) {
-    if (cudaMalloc(&R.v32lo, nnz * 4) != cudaSuccess) { cudaGetLastError(); lob_free_tiles(&R); return LOB_ERR_NOMEM; }
+    if (cudaMalloc(&R.v32lo, (nnz + LOB_STORE_PAD) * 4) != cudaSuccess) { cudaGetLastError(); lob_free_tiles(&R); return LOB_ERR_NOMEM; }
     (k_value_lo<<<nblocks(nnz, bs), bs, 0, st>>>(nnz, R.v64, R.v32, R.v32lo), LOB_LAUNCHED());
   }
 
