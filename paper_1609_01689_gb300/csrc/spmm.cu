@@ -868,6 +868,273 @@ __global__ void __launch_bounds__(CfgDF<NB>::THREADS, 1)
   }
 }
 
+// Ring-pipelined FP64-class (double-float) product at NB = 16: the schedule of k_spmm_ring with
+// the ownership and arithmetic of k_spmm4df (lane group of NB/2 lanes, two vector columns a
+// lane, two owned rows and columns a group). Its X tiles are (hi, lo) pairs, twice the FP32
+// size, so the ring has two stages and X_I one slot: the warps meet once per tile row, when
+// the last of them loads the next X_I.
+template <int NB>
+struct CfgRD {
+  static constexpr int VW = 2;
+  static constexpr int G = NB / VW;
+  static constexpr int THREADS = 1024;
+  static constexpr int NG = THREADS / G;
+  static constexpr int RPG = LOB_TILE / NG;
+  static constexpr int NW = THREADS / 32;
+  static constexpr int D = 2;
+  static constexpr int CH = LOB_PERM_CHUNK;
+  static constexpr int PTRS = 2 * (LOB_TILE + 1);
+  static constexpr size_t XV = sizeof(float2) * LOB_TILE * NB;
+  static constexpr size_t S_RC = 0;
+  static constexpr size_t S_VH = S_RC + 4 * (CH + 8);
+  static constexpr size_t S_VL = S_VH + 4 * (CH + 8);
+  static constexpr size_t S_PM = S_VL + 4 * (CH + 8);
+  static constexpr size_t S_PT = S_PM + 2 * (CH + 16);
+  static constexpr size_t S_XJ = (S_PT + 2 * PTRS + 32 + 15) / 16 * 16;
+  static constexpr size_t STAGE = S_XJ + XV;
+  static constexpr size_t XI = 0;  // one X_I slot
+  static constexpr size_t ST = XI + XV;
+  static constexpr size_t BAR = ST + D * STAGE;  // full[D], xfull
+  static constexpr size_t RNG = BAR + 8 * (D + 1);
+  static constexpr size_t CUR = RNG + 16;
+  static constexpr size_t CNT = CUR + 48;
+  static constexpr size_t BYTES = CNT + 4 * (D + 1);
+  static_assert(VW * G == NB && NG * RPG == LOB_TILE && THREADS % G == 0, "launch shape");
+  static_assert(sizeof(RingCur) <= 48, "cursor slot");
+  static_assert(S_VH % 16 == 0 && S_VL % 16 == 0 && S_PM % 16 == 0 && S_PT % 16 == 0 && STAGE % 16 == 0 &&
+                    ST % 16 == 0,
+                "bulk copy destinations must be 16-byte aligned");
+};
+
+template <int NB>
+__device__ __forceinline__ void ring_issue_df(unsigned char* stage, uint64_t* bar, int64_t I, int64_t t, int k,
+                                              const int32_t* tcol, const int64_t* tptr, const int32_t* tchunk,
+                                              const uint32_t* rc, const float* vhi, const float* vlo,
+                                              const uint16_t* cperm, const uint16_t* cptrs, const float2* Xs) {
+  using C = CfgRD<NB>;
+  const int64_t J = tcol[t];
+  const int64_t base = tptr[t] + (int64_t)k * C::CH;
+  const int64_t rem = tptr[t + 1] - base;
+  const int64_t cnt = rem < C::CH ? rem : C::CH;
+  const int64_t a0 = base & ~(int64_t)3, e1 = (base + cnt + 3) & ~(int64_t)3;
+  const int64_t p0 = base & ~(int64_t)7, p1 = (base + cnt + 7) & ~(int64_t)7;
+  const int64_t bo = (int64_t)(tchunk[t] + k) * (C::PTRS * 2);
+  const int64_t q0 = bo & ~(int64_t)15, q1 = (bo + C::PTRS * 2 + 15) & ~(int64_t)15;
+  const uint32_t brc = (uint32_t)((e1 - a0) * 4), bpm = (uint32_t)((p1 - p0) * 2), bpt = (uint32_t)(q1 - q0);
+  const uint32_t bxj = (J != I) ? (uint32_t)C::XV : 0u;
+  mbar_expect_tx(bar, 3 * brc + bpm + bpt + bxj);
+  bulk_g2s(stage + C::S_RC, rc + a0, brc, bar);
+  bulk_g2s(stage + C::S_VH, vhi + a0, brc, bar);
+  bulk_g2s(stage + C::S_VL, vlo + a0, brc, bar);
+  bulk_g2s(stage + C::S_PM, cperm + p0, bpm, bar);
+  bulk_g2s(stage + C::S_PT, reinterpret_cast<const unsigned char*>(cptrs) + q0, bpt, bar);
+  if (bxj) bulk_g2s(stage + C::S_XJ, Xs + J * LOB_TILE * NB, bxj, bar);
+}
+
+template <int NB>
+__global__ void __launch_bounds__(CfgRD<NB>::THREADS, 1)
+    k_spmm_ring_df(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ tcol,
+                   const int64_t* __restrict__ tptr, const int32_t* __restrict__ tchunk,
+                   const uint32_t* __restrict__ rc, const float* __restrict__ vhi, const float* __restrict__ vlo,
+                   const uint16_t* __restrict__ cperm, const uint16_t* __restrict__ cptrs,
+                   const float2* __restrict__ Xs, double* __restrict__ Y, int ldy, int c0, int w, int64_t n_act,
+                   int64_t ntr) {
+  using C = CfgRD<NB>;
+  constexpr int VW = C::VW, G = C::G, NG = C::NG, RPG = C::RPG, NW = C::NW, D = C::D, CH = C::CH;
+  extern __shared__ __align__(16) unsigned char sm[];
+  float2* XI = reinterpret_cast<float2*>(sm + C::XI);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + C::BAR);
+  uint64_t* xfull = full + D;
+  int* cnt = reinterpret_cast<int*>(sm + C::CNT);
+  int* xcnt = cnt + D;
+  int64_t* range = reinterpret_cast<int64_t*>(sm + C::RNG);
+  RingCur* cur = reinterpret_cast<RingCur*>(sm + C::CUR);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int g = tid / G, gl = tid % G;
+
+  if (tid == 0) {
+    const int64_t E = tptr[rowptr[ntr]];
+    auto first_row = [&](int64_t b) -> int64_t {
+      if (b >= (int64_t)gridDim.x) return ntr;
+      const int64_t target = E * b / (int64_t)gridDim.x;
+      int64_t lo = 0, hi = ntr;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (tptr[rowptr[mid]] >= target) hi = mid; else lo = mid + 1;
+      }
+      return lo;
+    };
+    range[0] = first_row(blockIdx.x);
+    range[1] = first_row((int64_t)blockIdx.x + 1);
+    for (int s = 0; s < D; s++) { mbar_init(&full[s], 1); cnt[s] = 0; }
+    mbar_init(xfull, 1);
+    *xcnt = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  const int64_t Ib = range[0], Ie = range[1];
+  if (tid == 0 && Ib < Ie) {
+    mbar_expect_tx(xfull, (uint32_t)C::XV);
+    bulk_g2s(XI, Xs + Ib * LOB_TILE * NB, (uint32_t)C::XV, xfull);
+    RingCur c;
+    c.I = Ib; c.Ie = Ie;
+    int64_t t0;
+    c.t1 = ring_trim(rowptr, tcol, n_act, Ib, &t0);
+    c.t = t0 - 1; c.k = 0; c.nk = 0;
+    bool more = ring_settle(c, rowptr, tcol, tchunk, n_act);
+    for (int s = 0; s < D && more; s++) {
+      ring_issue_df<NB>(sm + C::ST + s * C::STAGE, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rc, vhi, vlo, cperm,
+                        cptrs, Xs);
+      c.k++;
+      more = ring_settle(c, rowptr, tcol, tchunk, n_act);
+    }
+    if (!more) c.I = Ie;
+    *cur = c;
+  }
+  __syncthreads();
+
+  int64_t ch = 0;
+  for (int64_t I = Ib; I < Ie; I++) {
+    const int64_t ri = I - Ib;
+    if (!mbar_wait(xfull, (uint32_t)(ri & 1))) return;
+    int64_t t0;
+    const int64_t t1 = ring_trim(rowptr, tcol, n_act, I, &t0);
+    float rh[RPG][VW], rl[RPG][VW];
+#pragma unroll
+    for (int a = 0; a < RPG; a++)
+#pragma unroll
+      for (int q = 0; q < VW; q++) { rh[a][q] = 0.f; rl[a][q] = 0.f; }
+    for (int64_t t = t0; t < t1; t++) {
+      const int64_t J = tcol[t];
+      const bool diag = (J == I);
+      const int nk = tchunk[t + 1] - tchunk[t];
+      float th[RPG][VW], tlo[RPG][VW], chh[RPG][VW], clo[RPG][VW];
+#pragma unroll
+      for (int a = 0; a < RPG; a++)
+#pragma unroll
+        for (int q = 0; q < VW; q++) { th[a][q] = tlo[a][q] = chh[a][q] = clo[a][q] = 0.f; }
+      for (int k = 0; k < nk; k++) {
+        const int s = (int)(ch % D);
+        if (!mbar_wait(&full[s], (uint32_t)((ch / D) & 1))) return;
+        unsigned char* stage = sm + C::ST + s * C::STAGE;
+        const int64_t base = tptr[t] + (int64_t)k * CH;
+        const uint32_t* RCs = reinterpret_cast<const uint32_t*>(stage + C::S_RC) + (base & 3);
+        const float* VH = reinterpret_cast<const float*>(stage + C::S_VH) + (base & 3);
+        const float* VL = reinterpret_cast<const float*>(stage + C::S_VL) + (base & 3);
+        const uint16_t* PM = reinterpret_cast<const uint16_t*>(stage + C::S_PM) + (base & 7);
+        const int64_t bo = (int64_t)(tchunk[t] + k) * (C::PTRS * 2);
+        const uint16_t* PR = reinterpret_cast<const uint16_t*>(stage + C::S_PT + (bo & 15));
+        const uint16_t* PC = PR + (LOB_TILE + 1);
+        const float2* xj = diag ? XI : reinterpret_cast<const float2*>(stage + C::S_XJ);
+#pragma unroll
+        for (int a = 0; a < RPG; a++) {
+          const int idx = g + a * NG;
+          {
+            const int s0 = PR[idx], e0 = PR[idx + 1];
+            for (int i = s0; i < e0; i++) {
+              const int c = (int)(RCs[i] & 0xFFFFu);
+              const float vh = VH[i], vl = VL[i];
+#pragma unroll
+              for (int h = 0; h < VW; h += 2) {
+                const float4 x = *reinterpret_cast<const float4*>(&xj[c * NB + gl * VW + h]);  // (h0, l0, h1, l1)
+                df_mac(th[a][h], tlo[a][h], vh, vl, x.x, x.y);
+                df_mac(th[a][h + 1], tlo[a][h + 1], vh, vl, x.z, x.w);
+              }
+            }
+          }
+          {
+            const int s0 = PC[idx], e0 = PC[idx + 1];
+            for (int i = s0; i < e0; i++) {
+              const int q = PM[i] & (CH - 1);
+              const int r = (int)(RCs[q] >> 16);
+              if (diag && r == idx) continue;
+              const float vh = VH[q], vl = VL[q];
+#pragma unroll
+              for (int h = 0; h < VW; h += 2) {
+                const float4 x = *reinterpret_cast<const float4*>(&XI[r * NB + gl * VW + h]);
+                df_mac(chh[a][h], clo[a][h], vh, vl, x.x, x.y);
+                df_mac(chh[a][h + 1], clo[a][h + 1], vh, vl, x.z, x.w);
+              }
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence_block();
+          const int old = atomicAdd(&cnt[s], 1);
+          if (old == NW * (int)(ch / D + 1) - 1) {
+            __threadfence_block();
+            RingCur c = *cur;
+            if (c.I < c.Ie) {
+              asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+              ring_issue_df<NB>(stage, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rc, vhi, vlo, cperm, cptrs, Xs);
+              c.k++;
+              if (!ring_settle(c, rowptr, tcol, tchunk, n_act)) c.I = c.Ie;
+              *cur = c;
+            }
+            __threadfence_block();
+          }
+        }
+        ch++;
+      }
+#pragma unroll
+      for (int a = 0; a < RPG; a++) {
+        const int idx = g + a * NG;
+#pragma unroll
+        for (int q = 0; q < VW; q++) {
+          df_renorm(th[a][q], tlo[a][q]);
+          df_renorm(chh[a][q], clo[a][q]);
+          df_add(rh[a][q], rl[a][q], th[a][q], tlo[a][q]);
+          if (diag) {
+            df_add(rh[a][q], rl[a][q], chh[a][q], clo[a][q]);
+          } else {
+            const int kk = gl * VW + q;
+            const int64_t gr = J * LOB_TILE + idx;
+            if (kk < w && gr < n_act) {
+              atomic_out(&Y[gr * ldy + c0 + kk], chh[a][q]);
+              atomic_out(&Y[gr * ldy + c0 + kk], clo[a][q]);
+            }
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < RPG; a++) {
+      const int64_t gr = I * LOB_TILE + g + a * NG;
+#pragma unroll
+      for (int q = 0; q < VW; q++) {
+        const int kk = gl * VW + q;
+        if (kk >= w || gr >= n_act) continue;
+        df_renorm(rh[a][q], rl[a][q]);
+        atomic_out(&Y[gr * ldy + c0 + kk], rh[a][q]);
+        atomic_out(&Y[gr * ldy + c0 + kk], rl[a][q]);
+      }
+    }
+    // count this warp out of X_I; the last one loads the next row's
+    __syncwarp();
+    if (lane == 0) {
+      __threadfence_block();
+      const int old = atomicAdd(xcnt, 1);
+      if (old == NW * (int)(ri + 1) - 1 && I + 1 < Ie) {
+        __threadfence_block();
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        mbar_expect_tx(xfull, (uint32_t)C::XV);
+        bulk_g2s(XI, Xs + (I + 1) * LOB_TILE * NB, (uint32_t)C::XV, xfull);
+      }
+    }
+  }
+}
+
+// SMs of the current device (-1 if the query fails).
+int lob_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return sms;
+}
+
 template <int NB>
 int launch_df(const lob_matrix* m, const double* X, double* Y, int nb, int64_t n_act, cudaStream_t st) {
   using C = CfgDF<NB>;
@@ -879,15 +1146,32 @@ int launch_df(const lob_matrix* m, const double* X, double* Y, int nb, int64_t n
   LOB_TRY(lob_ensure_xs(m, (size_t)rows_pad * NB * sizeof(float2)));
   float2* Xs = reinterpret_cast<float2*>(m->xs);
   auto kern = k_spmm4df<NB>;
-  LOB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES));
+  int64_t grid = nt_act;
+  if constexpr (NB == 16) {
+    static_assert(CfgRD<NB>::BYTES <= 227 * 1024, "shared memory budget");
+    const int sms = lob_sm_count();
+    if (sms < 0) return LOB_ERR_CUDA;
+    grid = nt_act < sms ? nt_act : sms;
+    LOB_CUDA(cudaFuncSetAttribute(k_spmm_ring_df<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)CfgRD<NB>::BYTES));
+  } else {
+    LOB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES));
+  }
   for (int c0 = 0; c0 < nb; c0 += NB) {
     const int w = (nb - c0) < NB ? (nb - c0) : NB;
     (k_stage_x_df<<<(unsigned)((rows_pad * NB + 255) / 256), 256, 0, st>>>(rows_pad, n_act, nb, c0, w, NB, X, Xs),
      LOB_LAUNCHED());
-    (kern<<<(unsigned)nt_act, C::THREADS, C::BYTES, st>>>(TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rc, TS.v32,
-                                                           TS.v32lo, TS.cperm, TS.cptrs, Xs, Y, nb, c0, w, n_act,
-                                                           nullptr, 0),
-     LOB_LAUNCHED());
+    if constexpr (NB == 16) {
+      (k_spmm_ring_df<NB><<<(unsigned)grid, CfgRD<NB>::THREADS, CfgRD<NB>::BYTES, st>>>(TS.rowptr, TS.tcol, TS.tptr, TS.tchunk,
+                                                                          TS.rc, TS.v32, TS.v32lo, TS.cperm,
+                                                                          TS.cptrs, Xs, Y, nb, c0, w, n_act, nt_act),
+       LOB_LAUNCHED());
+    } else {
+      (kern<<<(unsigned)nt_act, C::THREADS, C::BYTES, st>>>(TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rc, TS.v32,
+                                                             TS.v32lo, TS.cperm, TS.cptrs, Xs, Y, nb, c0, w, n_act,
+                                                             nullptr, 0),
+       LOB_LAUNCHED());
+    }
   }
   LOB_CUDA(cudaGetLastError());
   return LOB_OK;
@@ -933,12 +1217,8 @@ int launch_ring16(const lob_matrix* m, const double* X, double* Y, int nb, int64
   const int64_t rows_pad = TS.nt * LOB_TILE;
   LOB_TRY(lob_ensure_xs(m, (size_t)rows_pad * NB * sizeof(float)));
   float* Xs = reinterpret_cast<float*>(m->xs);
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
-    LOB_CUDA(cudaGetDevice(&dev));
-    LOB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  }
+  const int sms = lob_sm_count();
+  if (sms < 0) return LOB_ERR_CUDA;
   const int64_t grid = nt_act < sms ? nt_act : sms;
   LOB_CUDA(cudaFuncSetAttribute(k_spmm_ring<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES));
   for (int c0 = 0; c0 < nb; c0 += NB) {
