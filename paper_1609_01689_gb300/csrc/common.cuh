@@ -60,6 +60,8 @@ struct lob_tiles {
   double* v64 = nullptr;       // [nnz] FP64 values (may be null)
   float* v32 = nullptr;        // [nnz] FP32 values (may be null)
   float* v32lo = nullptr;      // [nnz] kernel-private: v64 - v32 rounded to FP32 (with both copies)
+  uint2* rv = nullptr;         // [nnz] kernel-private: (rc, bits of v32) pairs (with FP32 values), so
+                               // the SpMM reads an entry's position and value in one 8-byte load
   uint16_t* cperm = nullptr;   // [nnz] kernel-private: per chunk of LOB_PERM_CHUNK entries of a tile,
                                // the chunk-local indices of its entries in (c, r) order
   int64_t nchunks = 0;

@@ -28,6 +28,7 @@ size_t matrix_bytes(const lob_matrix* m) {
   if (T.v64) b += (size_t)T.nnz * 8;
   if (T.v32) b += (size_t)T.nnz * 4;
   if (T.v32lo) b += (size_t)T.nnz * 4;
+  if (T.rv) b += (size_t)T.nnz * 8;
   if (T.cperm) b += (size_t)(T.nnz + 8) * 2;
   b += (size_t)(T.nt + 1) * 8 + (size_t)T.ntiles * 8 + (size_t)(T.ntiles + 1) * 12;
   b += (size_t)T.nchunks * 2 * (LOB_TILE + 1) * 2;

@@ -396,11 +396,10 @@ struct CfgR {
   static constexpr int CH = LOB_PERM_CHUNK;
   static constexpr int PTRS = 2 * (LOB_TILE + 1);
   static constexpr size_t XV = sizeof(float) * LOB_TILE * NB;
-  // one stage: records and values (16-byte aligned window around the chunk), permutation,
+  // one stage: (record, value) pairs (16-byte aligned window around the chunk), permutation,
   // chunk pointers, X_J
-  static constexpr size_t S_RC = 0;
-  static constexpr size_t S_VV = S_RC + 4 * (CH + 8);
-  static constexpr size_t S_PM = S_VV + 4 * (CH + 8);
+  static constexpr size_t S_RV = 0;
+  static constexpr size_t S_PM = S_RV + 8 * (CH + 8);
   static constexpr size_t S_PT = S_PM + 2 * (CH + 16);
   static constexpr size_t S_XJ = (S_PT + 2 * PTRS + 32 + 15) / 16 * 16;
   static constexpr size_t STAGE = S_XJ + XV;
@@ -413,7 +412,7 @@ struct CfgR {
   static constexpr size_t BYTES = CNT + 4 * (D + 2);
   static_assert(VW * G == NB && THREADS <= 1024 && THREADS % 32 == 0, "launch shape");
   static_assert(sizeof(RingCur) <= 48, "cursor slot");
-  static_assert(S_VV % 16 == 0 && S_PM % 16 == 0 && S_PT % 16 == 0 && STAGE % 16 == 0 && ST % 16 == 0,
+  static_assert(S_PM % 16 == 0 && S_PT % 16 == 0 && STAGE % 16 == 0 && ST % 16 == 0,
                 "bulk copy destinations must be 16-byte aligned");
 };
 
@@ -448,22 +447,21 @@ __device__ __forceinline__ bool ring_settle(RingCur& c, const int64_t* rowptr, c
 template <int NB>
 __device__ __forceinline__ void ring_issue(unsigned char* stage, uint64_t* bar, int64_t I, int64_t t, int k,
                                            const int32_t* tcol, const int64_t* tptr, const int32_t* tchunk,
-                                           const uint32_t* rc, const float* vals, const uint16_t* cperm,
-                                           const uint16_t* cptrs, const float* Xs) {
+                                           const uint2* rv, const uint16_t* cperm, const uint16_t* cptrs,
+                                           const float* Xs) {
   using C = CfgR<NB>;
   const int64_t J = tcol[t];
   const int64_t base = tptr[t] + (int64_t)k * C::CH;
   const int64_t rem = tptr[t + 1] - base;
   const int64_t cnt = rem < C::CH ? rem : C::CH;
-  const int64_t a0 = base & ~(int64_t)3, e1 = (base + cnt + 3) & ~(int64_t)3;      // 4-byte arrays
+  const int64_t a0 = base & ~(int64_t)1, e1 = (base + cnt + 1) & ~(int64_t)1;      // 8-byte pairs
   const int64_t p0 = base & ~(int64_t)7, p1 = (base + cnt + 7) & ~(int64_t)7;      // 2-byte array
   const int64_t bo = (int64_t)(tchunk[t] + k) * (C::PTRS * 2);                     // chunk pointers, bytes
   const int64_t q0 = bo & ~(int64_t)15, q1 = (bo + C::PTRS * 2 + 15) & ~(int64_t)15;
-  const uint32_t brc = (uint32_t)((e1 - a0) * 4), bpm = (uint32_t)((p1 - p0) * 2), bpt = (uint32_t)(q1 - q0);
+  const uint32_t brv = (uint32_t)((e1 - a0) * 8), bpm = (uint32_t)((p1 - p0) * 2), bpt = (uint32_t)(q1 - q0);
   const uint32_t bxj = (J != I) ? (uint32_t)C::XV : 0u;
-  mbar_expect_tx(bar, 2 * brc + bpm + bpt + bxj);
-  bulk_g2s(stage + C::S_RC, rc + a0, brc, bar);
-  bulk_g2s(stage + C::S_VV, vals + a0, brc, bar);
+  mbar_expect_tx(bar, brv + bpm + bpt + bxj);
+  bulk_g2s(stage + C::S_RV, rv + a0, brv, bar);
   bulk_g2s(stage + C::S_PM, cperm + p0, bpm, bar);
   bulk_g2s(stage + C::S_PT, reinterpret_cast<const unsigned char*>(cptrs) + q0, bpt, bar);
   if (bxj) bulk_g2s(stage + C::S_XJ, Xs + J * LOB_TILE * NB, bxj, bar);
@@ -473,10 +471,9 @@ template <int NB>
 __global__ void __launch_bounds__(CfgR<NB>::THREADS, 1)
     k_spmm_ring(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ tcol,
                 const int64_t* __restrict__ tptr, const int32_t* __restrict__ tchunk,
-                const uint32_t* __restrict__ rc, const float* __restrict__ vals,
-                const uint16_t* __restrict__ cperm, const uint16_t* __restrict__ cptrs,
-                const float* __restrict__ Xs, double* __restrict__ Y, int ldy, int c0, int w, int64_t n_act,
-                int64_t ntr) {
+                const uint2* __restrict__ rv, const uint16_t* __restrict__ cperm,
+                const uint16_t* __restrict__ cptrs, const float* __restrict__ Xs, double* __restrict__ Y, int ldy,
+                int c0, int w, int64_t n_act, int64_t ntr) {
   using C = CfgR<NB>;
   constexpr int VW = C::VW, G = C::G, NW = C::NW, D = C::D, CH = C::CH;
   constexpr int XN = LOB_TILE * NB;
@@ -524,8 +521,7 @@ __global__ void __launch_bounds__(CfgR<NB>::THREADS, 1)
     c.t = t0 - 1; c.k = 0; c.nk = 0;  // settle moves to the first chunk
     bool more = ring_settle(c, rowptr, tcol, tchunk, n_act);
     for (int s = 0; s < D && more; s++) {
-      ring_issue<NB>(sm + C::ST + s * C::STAGE, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rc, vals, cperm, cptrs,
-                     Xs);
+      ring_issue<NB>(sm + C::ST + s * C::STAGE, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rv, cperm, cptrs, Xs);
       c.k++;
       more = ring_settle(c, rowptr, tcol, tchunk, n_act);
     }
@@ -555,8 +551,7 @@ __global__ void __launch_bounds__(CfgR<NB>::THREADS, 1)
         if (!mbar_wait(&full[s], (uint32_t)((ch / D) & 1))) return;
         unsigned char* stage = sm + C::ST + s * C::STAGE;
         const int64_t base = tptr[t] + (int64_t)k * CH;
-        const uint32_t* RCs = reinterpret_cast<const uint32_t*>(stage + C::S_RC) + (base & 3);
-        const float* VVs = reinterpret_cast<const float*>(stage + C::S_VV) + (base & 3);
+        const uint2* RV = reinterpret_cast<const uint2*>(stage + C::S_RV) + (base & 1);
         const uint16_t* PM = reinterpret_cast<const uint16_t*>(stage + C::S_PM) + (base & 7);
         const int64_t bo = (int64_t)(tchunk[t] + k) * (C::PTRS * 2);
         const uint16_t* PR = reinterpret_cast<const uint16_t*>(stage + C::S_PT + (bo & 15));
@@ -565,11 +560,12 @@ __global__ void __launch_bounds__(CfgR<NB>::THREADS, 1)
         {  // row pass
           const int s0 = PR[g], e0 = PR[g + 1];
           float4 acc = acc_t;
-#pragma unroll 4
+#pragma unroll 3  // 4 spills at the 64-register limit of 1,024 threads
           for (int i = s0; i < e0; i++) {
-            const int c = (int)(RCs[i] & 0xFFFFu);
+            const uint2 e = RV[i];
+            const int c = (int)(e.x & 0xFFFFu);
             const float4 x = *reinterpret_cast<const float4*>(&xj[c * NB + gl * VW]);
-            fma_v(acc, VVs[i], x);
+            fma_v(acc, __uint_as_float(e.y), x);
           }
           acc_t = acc;
         }
@@ -578,11 +574,11 @@ __global__ void __launch_bounds__(CfgR<NB>::THREADS, 1)
           float4 acc = acc_c;
 #pragma unroll 4
           for (int i = s0; i < e0; i++) {
-            const int q = PM[i] & (CH - 1);
-            const int r = (int)(RCs[q] >> 16);
+            const uint2 e = RV[PM[i] & (CH - 1)];
+            const int r = (int)(e.x >> 16);
             if (diag && r == g) continue;  // the diagonal entry is applied once (row pass)
             const float4 xi = *reinterpret_cast<const float4*>(&XI[r * NB + gl * VW]);
-            fma_v(acc, VVs[q], xi);
+            fma_v(acc, __uint_as_float(e.y), xi);
           }
           acc_c = acc;
         }
@@ -596,7 +592,7 @@ __global__ void __launch_bounds__(CfgR<NB>::THREADS, 1)
             RingCur c = *cur;
             if (c.I < c.Ie) {
               asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-              ring_issue<NB>(stage, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rc, vals, cperm, cptrs, Xs);
+              ring_issue<NB>(stage, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rv, cperm, cptrs, Xs);
               c.k++;
               if (!ring_settle(c, rowptr, tcol, tchunk, n_act)) c.I = c.Ie;
               *cur = c;
@@ -885,9 +881,8 @@ struct CfgRD {
   static constexpr int CH = LOB_PERM_CHUNK;
   static constexpr int PTRS = 2 * (LOB_TILE + 1);
   static constexpr size_t XV = sizeof(float2) * LOB_TILE * NB;
-  static constexpr size_t S_RC = 0;
-  static constexpr size_t S_VH = S_RC + 4 * (CH + 8);
-  static constexpr size_t S_VL = S_VH + 4 * (CH + 8);
+  static constexpr size_t S_RV = 0;  // (record, high part) pairs
+  static constexpr size_t S_VL = S_RV + 8 * (CH + 8);
   static constexpr size_t S_PM = S_VL + 4 * (CH + 8);
   static constexpr size_t S_PT = S_PM + 2 * (CH + 16);
   static constexpr size_t S_XJ = (S_PT + 2 * PTRS + 32 + 15) / 16 * 16;
@@ -901,7 +896,7 @@ struct CfgRD {
   static constexpr size_t BYTES = CNT + 4 * (D + 1);
   static_assert(VW * G == NB && NG * RPG == LOB_TILE && THREADS % G == 0, "launch shape");
   static_assert(sizeof(RingCur) <= 48, "cursor slot");
-  static_assert(S_VH % 16 == 0 && S_VL % 16 == 0 && S_PM % 16 == 0 && S_PT % 16 == 0 && STAGE % 16 == 0 &&
+  static_assert(S_VL % 16 == 0 && S_PM % 16 == 0 && S_PT % 16 == 0 && STAGE % 16 == 0 &&
                     ST % 16 == 0,
                 "bulk copy destinations must be 16-byte aligned");
 };
@@ -909,23 +904,24 @@ struct CfgRD {
 template <int NB>
 __device__ __forceinline__ void ring_issue_df(unsigned char* stage, uint64_t* bar, int64_t I, int64_t t, int k,
                                               const int32_t* tcol, const int64_t* tptr, const int32_t* tchunk,
-                                              const uint32_t* rc, const float* vhi, const float* vlo,
-                                              const uint16_t* cperm, const uint16_t* cptrs, const float2* Xs) {
+                                              const uint2* rv, const float* vlo, const uint16_t* cperm,
+                                              const uint16_t* cptrs, const float2* Xs) {
   using C = CfgRD<NB>;
   const int64_t J = tcol[t];
   const int64_t base = tptr[t] + (int64_t)k * C::CH;
   const int64_t rem = tptr[t + 1] - base;
   const int64_t cnt = rem < C::CH ? rem : C::CH;
-  const int64_t a0 = base & ~(int64_t)3, e1 = (base + cnt + 3) & ~(int64_t)3;
+  const int64_t r0 = base & ~(int64_t)1, r1 = (base + cnt + 1) & ~(int64_t)1;      // 8-byte pairs
+  const int64_t a0 = base & ~(int64_t)3, e1 = (base + cnt + 3) & ~(int64_t)3;      // 4-byte low parts
   const int64_t p0 = base & ~(int64_t)7, p1 = (base + cnt + 7) & ~(int64_t)7;
   const int64_t bo = (int64_t)(tchunk[t] + k) * (C::PTRS * 2);
   const int64_t q0 = bo & ~(int64_t)15, q1 = (bo + C::PTRS * 2 + 15) & ~(int64_t)15;
-  const uint32_t brc = (uint32_t)((e1 - a0) * 4), bpm = (uint32_t)((p1 - p0) * 2), bpt = (uint32_t)(q1 - q0);
+  const uint32_t brv = (uint32_t)((r1 - r0) * 8), bvl = (uint32_t)((e1 - a0) * 4);
+  const uint32_t bpm = (uint32_t)((p1 - p0) * 2), bpt = (uint32_t)(q1 - q0);
   const uint32_t bxj = (J != I) ? (uint32_t)C::XV : 0u;
-  mbar_expect_tx(bar, 3 * brc + bpm + bpt + bxj);
-  bulk_g2s(stage + C::S_RC, rc + a0, brc, bar);
-  bulk_g2s(stage + C::S_VH, vhi + a0, brc, bar);
-  bulk_g2s(stage + C::S_VL, vlo + a0, brc, bar);
+  mbar_expect_tx(bar, brv + bvl + bpm + bpt + bxj);
+  bulk_g2s(stage + C::S_RV, rv + r0, brv, bar);
+  bulk_g2s(stage + C::S_VL, vlo + a0, bvl, bar);
   bulk_g2s(stage + C::S_PM, cperm + p0, bpm, bar);
   bulk_g2s(stage + C::S_PT, reinterpret_cast<const unsigned char*>(cptrs) + q0, bpt, bar);
   if (bxj) bulk_g2s(stage + C::S_XJ, Xs + J * LOB_TILE * NB, bxj, bar);
@@ -935,7 +931,7 @@ template <int NB>
 __global__ void __launch_bounds__(CfgRD<NB>::THREADS, 1)
     k_spmm_ring_df(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ tcol,
                    const int64_t* __restrict__ tptr, const int32_t* __restrict__ tchunk,
-                   const uint32_t* __restrict__ rc, const float* __restrict__ vhi, const float* __restrict__ vlo,
+                   const uint2* __restrict__ rv, const float* __restrict__ vlo,
                    const uint16_t* __restrict__ cperm, const uint16_t* __restrict__ cptrs,
                    const float2* __restrict__ Xs, double* __restrict__ Y, int ldy, int c0, int w, int64_t n_act,
                    int64_t ntr) {
@@ -983,7 +979,7 @@ __global__ void __launch_bounds__(CfgRD<NB>::THREADS, 1)
     c.t = t0 - 1; c.k = 0; c.nk = 0;
     bool more = ring_settle(c, rowptr, tcol, tchunk, n_act);
     for (int s = 0; s < D && more; s++) {
-      ring_issue_df<NB>(sm + C::ST + s * C::STAGE, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rc, vhi, vlo, cperm,
+      ring_issue_df<NB>(sm + C::ST + s * C::STAGE, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rv, vlo, cperm,
                         cptrs, Xs);
       c.k++;
       more = ring_settle(c, rowptr, tcol, tchunk, n_act);
@@ -1018,8 +1014,7 @@ __global__ void __launch_bounds__(CfgRD<NB>::THREADS, 1)
         if (!mbar_wait(&full[s], (uint32_t)((ch / D) & 1))) return;
         unsigned char* stage = sm + C::ST + s * C::STAGE;
         const int64_t base = tptr[t] + (int64_t)k * CH;
-        const uint32_t* RCs = reinterpret_cast<const uint32_t*>(stage + C::S_RC) + (base & 3);
-        const float* VH = reinterpret_cast<const float*>(stage + C::S_VH) + (base & 3);
+        const uint2* RV = reinterpret_cast<const uint2*>(stage + C::S_RV) + (base & 1);
         const float* VL = reinterpret_cast<const float*>(stage + C::S_VL) + (base & 3);
         const uint16_t* PM = reinterpret_cast<const uint16_t*>(stage + C::S_PM) + (base & 7);
         const int64_t bo = (int64_t)(tchunk[t] + k) * (C::PTRS * 2);
@@ -1032,8 +1027,9 @@ __global__ void __launch_bounds__(CfgRD<NB>::THREADS, 1)
           {
             const int s0 = PR[idx], e0 = PR[idx + 1];
             for (int i = s0; i < e0; i++) {
-              const int c = (int)(RCs[i] & 0xFFFFu);
-              const float vh = VH[i], vl = VL[i];
+              const uint2 e = RV[i];
+              const int c = (int)(e.x & 0xFFFFu);
+              const float vh = __uint_as_float(e.y), vl = VL[i];
 #pragma unroll
               for (int h = 0; h < VW; h += 2) {
                 const float4 x = *reinterpret_cast<const float4*>(&xj[c * NB + gl * VW + h]);  // (h0, l0, h1, l1)
@@ -1046,9 +1042,10 @@ __global__ void __launch_bounds__(CfgRD<NB>::THREADS, 1)
             const int s0 = PC[idx], e0 = PC[idx + 1];
             for (int i = s0; i < e0; i++) {
               const int q = PM[i] & (CH - 1);
-              const int r = (int)(RCs[q] >> 16);
+              const uint2 e = RV[q];
+              const int r = (int)(e.x >> 16);
               if (diag && r == idx) continue;
-              const float vh = VH[q], vl = VL[q];
+              const float vh = __uint_as_float(e.y), vl = VL[q];
 #pragma unroll
               for (int h = 0; h < VW; h += 2) {
                 const float4 x = *reinterpret_cast<const float4*>(&XI[r * NB + gl * VW + h]);
@@ -1067,7 +1064,7 @@ __global__ void __launch_bounds__(CfgRD<NB>::THREADS, 1)
             RingCur c = *cur;
             if (c.I < c.Ie) {
               asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-              ring_issue_df<NB>(stage, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rc, vhi, vlo, cperm, cptrs, Xs);
+              ring_issue_df<NB>(stage, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rv, vlo, cperm, cptrs, Xs);
               c.k++;
               if (!ring_settle(c, rowptr, tcol, tchunk, n_act)) c.I = c.Ie;
               *cur = c;
@@ -1148,6 +1145,7 @@ int launch_df(const lob_matrix* m, const double* X, double* Y, int nb, int64_t n
   auto kern = k_spmm4df<NB>;
   int64_t grid = nt_act;
   if constexpr (NB == 16) {
+    if (!TS.rv) return LOB_ERR_ARG;
     static_assert(CfgRD<NB>::BYTES <= 227 * 1024, "shared memory budget");
     const int sms = lob_sm_count();
     if (sms < 0) return LOB_ERR_CUDA;
@@ -1162,9 +1160,9 @@ int launch_df(const lob_matrix* m, const double* X, double* Y, int nb, int64_t n
     (k_stage_x_df<<<(unsigned)((rows_pad * NB + 255) / 256), 256, 0, st>>>(rows_pad, n_act, nb, c0, w, NB, X, Xs),
      LOB_LAUNCHED());
     if constexpr (NB == 16) {
-      (k_spmm_ring_df<NB><<<(unsigned)grid, CfgRD<NB>::THREADS, CfgRD<NB>::BYTES, st>>>(TS.rowptr, TS.tcol, TS.tptr, TS.tchunk,
-                                                                          TS.rc, TS.v32, TS.v32lo, TS.cperm,
-                                                                          TS.cptrs, Xs, Y, nb, c0, w, n_act, nt_act),
+      (k_spmm_ring_df<NB><<<(unsigned)grid, CfgRD<NB>::THREADS, CfgRD<NB>::BYTES, st>>>(
+           TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rv, TS.v32lo, TS.cperm, TS.cptrs, Xs, Y, nb, c0, w, n_act,
+           nt_act),
        LOB_LAUNCHED());
     } else {
       (kern<<<(unsigned)nt_act, C::THREADS, C::BYTES, st>>>(TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rc, TS.v32,
@@ -1212,6 +1210,7 @@ int launch_ring16(const lob_matrix* m, const double* X, double* Y, int nb, int64
   using C = CfgR<NB>;
   static_assert(C::BYTES <= 227 * 1024, "shared memory budget");
   const lob_tiles& TS = m->T;
+  if (!TS.rv) return LOB_ERR_ARG;
   const int64_t nt_act = (n_act + LOB_TILE - 1) / LOB_TILE;
   if (nt_act == 0) return LOB_OK;
   const int64_t rows_pad = TS.nt * LOB_TILE;
@@ -1225,9 +1224,9 @@ int launch_ring16(const lob_matrix* m, const double* X, double* Y, int nb, int64
     const int w = (nb - c0) < NB ? (nb - c0) : NB;
     (k_stage_x<float><<<(unsigned)((rows_pad * NB + 255) / 256), 256, 0, st>>>(rows_pad, n_act, nb, c0, w, NB, X, Xs),
      LOB_LAUNCHED());
-    (k_spmm_ring<NB><<<(unsigned)grid, C::THREADS, C::BYTES, st>>>(TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rc,
-                                                                  TS.v32, TS.cperm, TS.cptrs, Xs, Y, nb, c0, w,
-                                                                  n_act, nt_act),
+    (k_spmm_ring<NB><<<(unsigned)grid, C::THREADS, C::BYTES, st>>>(TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rv,
+                                                                  TS.cperm, TS.cptrs, Xs, Y, nb, c0, w, n_act,
+                                                                  nt_act),
      LOB_LAUNCHED());
   }
   LOB_CUDA(cudaGetLastError());

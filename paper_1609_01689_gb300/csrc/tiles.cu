@@ -158,6 +158,13 @@ __global__ void k_value_lo(int64_t nnz, const double* __restrict__ v64, const fl
   lo[k] = __double2float_rn(v64[k] - (double)v32[k]);
 }
 
+__global__ void k_pack_rv(int64_t nnz, const uint32_t* __restrict__ rc, const float* __restrict__ v32,
+                          uint2* __restrict__ rv) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nnz) return;
+  rv[k] = make_uint2(rc[k], __float_as_uint(v32[k]));
+}
+
 __global__ void k_absrow(int64_t nnz, const int64_t* __restrict__ row, const int64_t* __restrict__ col,
                          const double* __restrict__ val, double* __restrict__ s) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -174,7 +181,7 @@ inline unsigned nblocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs
 void lob_free_tiles(lob_tiles* T) {
   cudaFree(T->rowptr); cudaFree(T->tcol); cudaFree(T->trow); cudaFree(T->tptr);
   cudaFree(T->rc); cudaFree(T->v64); cudaFree(T->v32); cudaFree(T->cperm);
-  cudaFree(T->tchunk); cudaFree(T->cptrs); cudaFree(T->v32lo);
+  cudaFree(T->tchunk); cudaFree(T->cptrs); cudaFree(T->v32lo); cudaFree(T->rv);
   *T = lob_tiles();
 }
 
@@ -297,6 +304,10 @@ int lob_build_tiles(const lob_coo* H, int values, cudaStream_t st, lob_tiles* T,
     LOB_CUDA(cudaStreamSynchronize(st));
   }
 
+  if (R.v32) {
+    if (cudaMalloc(&R.rv, (nnz + LOB_STORE_PAD) * 8) != cudaSuccess) { cudaGetLastError(); lob_free_tiles(&R); return LOB_ERR_NOMEM; }
+    (k_pack_rv<<<nblocks(nnz, bs), bs, 0, st>>>(nnz, R.rc, R.v32, R.rv), LOB_LAUNCHED());
+  }
   if (R.v64 && R.v32) {
     if (cudaMalloc(&R.v32lo, (nnz + LOB_STORE_PAD) * 4) != cudaSuccess) { cudaGetLastError(); lob_free_tiles(&R); return LOB_ERR_NOMEM; }
     (k_value_lo<<<nblocks(nnz, bs), bs, 0, st>>>(nnz, R.v64, R.v32, R.v32lo), LOB_LAUNCHED());
