@@ -126,6 +126,17 @@ def golden_eigs(cfg):
 
 
 _ORACLE_H = {}
+_HOST_COO = {}
+
+
+def host_coo(cfg, layout):
+    """The workload's upper-triangle COO on the host (generated once per configuration and seed)."""
+    import synth
+
+    key = (cfg, int(layout.seed))
+    if key not in _HOST_COO:
+        _HOST_COO[key] = synth.generate(layout)
+    return _HOST_COO[key]
 
 
 def oracle_sample(cfg, layout):
@@ -134,11 +145,10 @@ def oracle_sample(cfg, layout):
     a + b j (SpMV plus reorthogonalisation against j vectors); the time to the converged step
     count N of the full oracle run (stored with the reference eigenvalues) is N a + N^2 b / 2."""
     import oracle
-    import synth
 
     key = (cfg, int(layout.seed))
     if key not in _ORACLE_H:
-        r, c, v = synth.generate(layout)
+        r, c, v = host_coo(cfg, layout)
         H = oracle.Coo(layout.n, r, c, v)
         _ORACLE_H[key] = (H, oracle.norm_inf(H))
     H, nH = _ORACLE_H[key]
@@ -160,6 +170,33 @@ def oracle_sample(cfg, layout):
         f"oracle Lanczos (FP64, full reorthogonalisation, 1 thread) on the same matrix: {s1} and {s2} steps timed "
         f"({t[0]:.2f} s, {t[1]:.2f} s), per-step cost a + b j fitted, extrapolated to the {N} steps the full oracle "
         f"run needs to reach Ritz residual 1e-12 ||H||"))
+
+
+def csb_sample(cfg, layout, nb, bytes_per_call, gpu_ms):
+    """The paper's CPU organisation of the SpMM (threaded CSB: tile rows then tile columns, OpenMP
+    dynamic scheduling, FP32 values; Section 4.4) on all host cores, on the bench's matrix at the
+    same block width. Median of 10 calls after 2 warm-ups; algorithmic bytes as for the GPU kernel."""
+    import baseline
+    import synth
+
+    r, c, v = host_coo(cfg, layout)
+    M = baseline.CsbMatrix(layout.n, r, c, v)
+    X = np.random.default_rng(3).standard_normal((layout.n, nb))
+    Y = np.empty_like(X)
+    for _ in range(2):
+        M.spmm(X, Y)
+    t = []
+    for _ in range(10):
+        t0 = time.perf_counter()
+        M.spmm(X, Y)
+        t.append(time.perf_counter() - t0)
+    M.close()
+    ms = float(np.median(t)) * 1e3
+    threads = baseline.max_threads()
+    return {"kind": "threaded CPU CSB SpMM (row pass over tile rows, column pass over tile columns, "
+                    "OpenMP dynamic schedule, FP32 values)", "threads": threads, "nb": nb,
+            "ms": ms, "gbs": bytes_per_call / (ms * 1e-3) / 1e9, "gpu_ms": gpu_ms,
+            "gpu_speedup": ms / gpu_ms if gpu_ms > 0 else None}
 
 
 def replica_layout(cfg, rank):
@@ -430,6 +467,7 @@ def main():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-csb", action="store_true", help="skip the threaded CPU CSB SpMM baseline")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-lanczos", action="store_true")
@@ -594,6 +632,8 @@ def main():
     if rank == 0 and not args.no_cpu and wl["cfg"] != "c3":
         ms_cpu, desc = oracle_sample(wl["cfg"], layout)
         out["cpu_baseline"] = dict(desc, value=ms_cpu, unit="ms")
+    if rank == 0 and not args.no_csb and wl["cfg"] != "c3" and spmm_calls > 0:
+        out["cpu_csb_spmm"] = csb_sample(wl["cfg"], layout, nb, spmm_bytes / spmm_calls, spmm_ms / spmm_calls)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist is not None:
