@@ -41,7 +41,8 @@ def test_gram_random_bound(mode, rel):
 
 
 @pytest.mark.parametrize("mode", ["fp64", "mixed"])
-@pytest.mark.parametrize("n,p,q", [(1, 1, 1), (5000, 48, 16), (4097, 32, 16), (300, 96, 40)])
+@pytest.mark.parametrize("n,p,q", [(1, 1, 1), (5000, 48, 16), (4097, 32, 16), (1000, 7, 5), (129, 64, 16),
+                                   (257, 65, 16), (300, 96, 40)])
 def test_lincomb_exact_and_bound(mode, n, p, q):
     import paper_1609_01689_gb300 as lob
     rng = np.random.default_rng(n * 3 + p)
