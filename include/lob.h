@@ -192,6 +192,15 @@ typedef struct {
                               (0 = max(tol, 1e-7); a phase that stalls near its FP32
                               floor hands over to the FP64-class phase earlier) */
   void* stream;
+  int64_t n_small_inner;   /* multi-level guess (Section 3.3.1): if 0 < n_small_inner < n_small, the
+                              solve on the leading n_small block that makes the eq. 12 guess
+                              takes its own guess from the leading n_small_inner block (three
+                              LOBPCG runs on nested configuration spaces); 0 = random start.
+                              lob_solve only: the server's engine keeps the one-level guess */
+  double guess_tol;        /* relative residual to which the leading-block solves of the guess
+                              run, in [0, 1); 0 = 1e-3. A nested guess whose coupling
+                              ||H_21|| / ||H|| is small pays off only with a tighter value.
+                              lob_solve only */
 } lob_solve_opts;
 
 typedef struct {
@@ -335,6 +344,10 @@ int lob_server_stats_get(const lob_server* s, lob_server_stats* out);
 int lob_server_destroy(lob_server* s);
 
 const char* lob_strerror(int code);
+
+/* Size in bytes of the ABI struct with the given type name ("lob_solve_opts", "lob_stats",
+ * ...), so that a binding can check its own layout; 0 for an unknown name or NULL. Host only. */
+int64_t lob_struct_size(const char* name);
 
 /* Number of CUDA kernels this library has launched in this process so far (all devices,
  * all threads). Diagnostic: a benchmark reads it before and after a timed region. */

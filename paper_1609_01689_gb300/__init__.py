@@ -60,7 +60,8 @@ class MatrixInfo(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("mode", _I32), ("precond", _I32), ("max_iter", _I32), ("refine_iter", _I32), ("norm_H", _D),
                 ("n_small", _I64), ("seed", ctypes.c_uint64), ("precond_shift", _I32), ("precond_solve", _I32),
-                ("precond_steps", _I32), ("verbose", _I32), ("mixed_tol", _D), ("stream", _P)]
+                ("precond_steps", _I32), ("verbose", _I32), ("mixed_tol", _D), ("stream", _P),
+                ("n_small_inner", _I64), ("guess_tol", _D)]
 
 
 class Stats(ctypes.Structure):
@@ -291,7 +292,7 @@ class Matrix:
 
     def solve(self, k, nb, tol, X0=None, mode="fp64", precond=False, n_small=0, max_iter=0, refine_iter=0,
               seed=1, precond_shift=0, mixed_tol=0.0, norm_H=0.0, X_out=None, precond_solve="fom", precond_steps=3,
-              stats=True):
+              stats=True, n_small_inner=0, guess_tol=0.0):
         """k smallest eigenpairs (lob_solve). Returns (lam, X, stats, status). stats=False passes no
         stats struct: the solver then keeps no phase timers and replays its stages as CUDA graphs."""
         torch = _torch()
@@ -300,7 +301,7 @@ class Matrix:
         lam = np.zeros(k, np.float64)
         st = Stats()
         o = SolveOpts(_MODES[mode], int(bool(precond)), max_iter, refine_iter, norm_H, n_small, seed, precond_shift,
-                      _PSOLVE[precond_solve], precond_steps, 0, mixed_tol, _stream())
+                      _PSOLVE[precond_solve], precond_steps, 0, mixed_tol, _stream(), n_small_inner, guess_tol)
         rc = lib().lob_solve(self._h, k, nb, tol, x0.data_ptr() if x0 is not None else None, ctypes.byref(o),
                              lam.ctypes.data, X.data_ptr(), ctypes.byref(st) if stats else None)
         if rc not in (LOB_OK, LOB_ERR_NOCONV):

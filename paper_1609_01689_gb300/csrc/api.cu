@@ -9,6 +9,26 @@ extern "C" {
 
 long long lob_kernel_launches(void) { return g_lob_launches.load(); }
 
+int64_t lob_struct_size(const char* name) {
+  if (!name) return 0;
+  struct E { const char* n; int64_t s; };
+  static const E table[] = {
+      {"lob_coo", sizeof(lob_coo)},
+      {"lob_create_opts", sizeof(lob_create_opts)},
+      {"lob_matrix_info", sizeof(lob_matrix_info)},
+      {"lob_solve_opts", sizeof(lob_solve_opts)},
+      {"lob_stats", sizeof(lob_stats)},
+      {"lob_lanczos_stats", sizeof(lob_lanczos_stats)},
+      {"lob_server_opts", sizeof(lob_server_opts)},
+      {"lob_request", sizeof(lob_request)},
+      {"lob_result", sizeof(lob_result)},
+      {"lob_server_stats", sizeof(lob_server_stats)},
+  };
+  for (const E& e : table)
+    if (strcmp(e.n, name) == 0) return e.s;
+  return 0;
+}
+
 const char* lob_strerror(int code) {
   switch (code) {
     case LOB_OK: return "ok";

@@ -580,13 +580,16 @@ int lob_task::step() {
           } else {
             LOB_CUDA(cudaMemsetAsync(W.p, 0, (size_t)n * nb * 8, st));
             lob_solve_opts so = o;
-            so.n_small = 0;
+            // multi-level: the leading-block solve takes its own eq. 12 guess from the inner block
+            so.n_small = (o.n_small_inner > 0 && o.n_small_inner < ns) ? o.n_small_inner : 0;
+            so.n_small_inner = 0;
             so.max_iter = 2000;
             so.refine_iter = 0;
             so.mixed_tol = 0.0;
             so.verbose = 0;
+            const double gtol = o.guess_tol > 0.0 ? o.guess_tol : LOB_GUESS_TOL;
             child = new lob_task();
-            const int rc = task_init(child, M, nb, nb, LOB_GUESS_TOL, nullptr, &so, W.p, ns, st, false);
+            const int rc = task_init(child, M, nb, nb, gtol, nullptr, &so, W.p, ns, st, false);
             if (rc != LOB_OK) { delete child; child = nullptr; return rc; }
             pc = PC_GUESS_CHILD;
             return step();
@@ -875,6 +878,7 @@ int lob_solve_impl(lob_matrix* m, int32_t k, int32_t nb, double tol, const doubl
   if (o->mode == LOB_MODE_MIXED && (!m->T.v32 || !m->T.v64)) return LOB_ERR_ARG;
   if (o->mode == LOB_MODE_FP64 && !m->T.v64) return LOB_ERR_ARG;
   if (o->precond && m->P.bp < 1) return LOB_ERR_ARG;
+  if (o->n_small_inner < 0 || !(o->guess_tol >= 0.0 && o->guess_tol < 1.0)) return LOB_ERR_ARG;
   if (o->precond_solve < LOB_PSOLVE_FOM || o->precond_solve > LOB_PSOLVE_ABS || o->precond_steps < 0 ||
       o->precond_steps > 3)
     return LOB_ERR_ARG;

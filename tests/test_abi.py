@@ -64,3 +64,21 @@ def test_library_loads_and_reports_errors(built_lib):
 def test_synth_device_library_builds():
     import synth
     assert os.path.exists(synth.build_device())
+
+
+def test_binding_struct_layouts_match_the_header(built_lib):
+    """Every ctypes mirror of an ABI struct has the size the C compiler gives the header's struct."""
+    import ctypes
+
+    import paper_1609_01689_gb300 as lob
+    lib = lob.build()
+    lib.lob_struct_size.restype = ctypes.c_int64
+    lib.lob_struct_size.argtypes = [ctypes.c_char_p]
+    pairs = {"lob_coo": lob.Coo, "lob_create_opts": lob.CreateOpts, "lob_matrix_info": lob.MatrixInfo,
+             "lob_solve_opts": lob.SolveOpts, "lob_stats": lob.Stats, "lob_lanczos_stats": lob.LanczosStats,
+             "lob_server_opts": lob.ServerOpts, "lob_request": lob.Request, "lob_result": lob.Result,
+             "lob_server_stats": lob.ServerStats}
+    for name, cls in pairs.items():
+        assert lib.lob_struct_size(name.encode()) == ctypes.sizeof(cls), name
+    assert lib.lob_struct_size(b"no_such_struct") == 0
+    assert lib.lob_struct_size(None) == 0

@@ -147,3 +147,27 @@ def test_lanczos_baseline_matches_oracle(c1):
     res = oracle.residual_norms(H, X.cpu().numpy(), lam)
     assert res.max() <= 1e-8 * oracle.norm_inf(H)
     assert st["steps"] % 10 == 0 and st["steps"] > 5
+
+
+def test_solve_multilevel_guess_500k(c2_golden):
+    """The multi-level guess of Section 3.3.1 on the n = 500,000 workload: LOBPCG on levels <= 8
+    (itself started from the eq. 12 guess of levels {0, 1}) gives the guess of the full solve.
+    Same eigenvalues as the oracle; fewer iterations of the full solve than the one-level guess."""
+    import paper_1609_01689_gb300 as lob
+    L = synth.config_layout("c2")
+    r, c, v = synth.generate_device(L)
+    M = lob.Matrix(L.n, r, c, v, precond_block=32)
+    lv = synth.level_starts(L)
+    lam1, _, st1, rc1 = M.solve(8, 16, 1e-8, mode="mixed", precond=True, n_small=int(lv[2]))
+    lam, X, st, rc = M.solve(8, 16, 1e-8, mode="mixed", precond=True, n_small=int(lv[9]), n_small_inner=int(lv[2]),
+                             guess_tol=1e-6)
+    assert rc == lob.LOB_OK and rc1 == lob.LOB_OK
+    rel = np.abs(lam - c2_golden[:8]) / np.maximum(np.abs(c2_golden[:8]), 1.0)
+    assert rel.max() <= 1e-8, rel
+    assert st["iterations"] < st1["iterations"], (st["iterations"], st1["iterations"])
+    rows, cols, vals = synth.generate(L)
+    H = oracle.Coo(L.n, rows, cols, vals)
+    res = oracle.residual_norms(H, X.cpu().numpy()[:, :8], lam) / oracle.norm_inf(H)
+    assert res.max() <= 1e-8, res
+    with pytest.raises(lob.LobError):
+        M.solve(8, 16, 1e-8, mode="mixed", precond=True, n_small=int(lv[9]), guess_tol=1.5)
