@@ -34,10 +34,10 @@ def test_spmm_integer_exact(nb, mode):
 
 
 @pytest.mark.parametrize("n,density,nb", [(600, 0.9, 16), (520, 0.45, 17), (1100, 0.12, 16)])
-@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "df64"])
 def test_spmm_dense_tiles_integer_exact(n, density, nb, mode):
-    """Dense tiles: a tile spans several chunks of the column permutation, and one row or column
-    runs across many lane groups' segments of a chunk (carried partials)."""
+    """Dense tiles: a tile spans several chunks of the column permutation, so the ring kernels'
+    stages hold consecutive chunks of one tile and X_J is staged once per chunk."""
     import paper_1609_01689_gb300 as lob
     rng = np.random.default_rng(n + nb)
     H = random_upper(n, density, rng, integer=True)
@@ -96,9 +96,10 @@ def c2():
     return L, oracle.Coo(L.n, r, c, v)
 
 
-@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "df64"])
 def test_spmm_full_size_500k(c2, mode):
-    """The n = 500,000, nb = 16 workload in the launch configuration the benchmark times."""
+    """The n = 500,000, nb = 16 workload in the launch configuration the benchmark times (the ring
+    kernels for the FP32-value and double-float products)."""
     import paper_1609_01689_gb300 as lob
     L, H = c2
     M = lob.Matrix(H.n, H.rows, H.cols, H.vals)
@@ -108,8 +109,8 @@ def test_spmm_full_size_500k(c2, mode):
     Yref = oracle.spmm(H, X)
     bound_base = oracle.spmm(abs_coo(H), np.abs(X))
     m = row_counts(H)[:, None]
-    bound = (2 * (m + 2) * U64 if mode == "fp64" else 2 * (m + 4) * U32) * bound_base
-    assert np.all(np.abs(Y - Yref) <= bound)
+    unit = {"fp64": 2 * (m + 2) * U64, "mixed": 2 * (m + 4) * U32, "df64": 2 * (m + 2) * 2.0 ** -46}[mode]
+    assert np.all(np.abs(Y - Yref) <= unit * bound_base)
 
 
 @pytest.mark.parametrize("nb", [1, 2, 5, 8, 16, 24])
