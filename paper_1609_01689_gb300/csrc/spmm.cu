@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(Cfg<MIXED, NB>::THREADS, Cfg<MIXED, NB>::MINB)
 //
 // Each CTA is persistent and takes a contiguous range of tile rows holding about 1/grid of the
 // stored entries. The chunks of that range pass through a ring of D shared-memory stages. A
-// stage is filled by bulk async copies (records, values, permutation, chunk pointers and X_J)
+// stage is filled by bulk async copies ((record, value) pairs, permutation, chunk pointers, X_J)
 // that complete on the stage's mbarrier; a warp waits on that barrier, works the chunk, and
 // counts itself out of the stage with a shared-memory counter. The warp that counts out last
 // refills the stage with the chunk D places further on. So warps drift apart by up to D chunks
