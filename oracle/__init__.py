@@ -215,7 +215,7 @@ def block_krylov(H: Coo, bounds, mu, R: np.ndarray, method: str, steps: int = 3,
     """Approximate eq. 11 solves per block and column: FOM or minimal residual with `steps`
     Krylov iterations from a zero start, or |H~_[i] - mu_j I|^{-1} ('abs')."""
     bounds = _i64(bounds)
-    assert np.diff(bounds).max() <= 64
+    assert np.diff(bounds).max() <= 256
     mu = _f64(mu)
     R = _f64(R)
     W = np.empty_like(R)

@@ -513,12 +513,15 @@ int orc_block_precond(int64_t n, int64_t nnz, const int64_t* row, const int64_t*
  *   method 2, minimal residual: w = V y minimising || beta e_1 - Tbar y ||, Tbar = [T; b_s e_s^T]
  *     ((s+1) x s), through the normal equations Tbar^T Tbar y = beta Tbar^T e_1. */
 static void krylov_block(int64_t m, const double* A, const double* r, int method, int steps, double* w) {
-  double V[4][64], al[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0}, u[64];
+  double* Vbuf = (double*)malloc((size_t)(4 * m + m) * sizeof(double));
+  double* V[4] = {Vbuf, Vbuf + m, Vbuf + 2 * m, Vbuf + 3 * m};
+  double* u = Vbuf + 4 * m;
+  double al[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
   for (int64_t a = 0; a < m; a++) w[a] = 0.0;
   double beta = 0.0;
   for (int64_t a = 0; a < m; a++) beta += r[a] * r[a];
   beta = sqrt(beta);
-  if (beta == 0.0) return;
+  if (beta == 0.0) { free(Vbuf); return; }
   for (int64_t a = 0; a < m; a++) V[0][a] = r[a] / beta;
   int s = 0;
   for (int i = 0; i < steps; i++) {
@@ -584,9 +587,11 @@ static void krylov_block(int64_t m, const double* A, const double* r, int method
   }
   for (int i = 0; i < s; i++)
     for (int64_t a = 0; a < m; a++) w[a] += y[i] * V[i][a];
+  free(Vbuf);
 }
 
-/* Approximate solves of eq. 11 on the diagonal blocks given by bounds (block sizes <= 64):
+/* Approximate solves of eq. 11 on the diagonal blocks given by bounds (block sizes <= 256, so the
+ * blocks may be whole diagonal tiles, as in Section 4.3):
  * method 0 FOM / 2 minimal residual with `steps` (1..3) Krylov iterations (krylov_block), or
  * method 3: w = |H~_[i] - mu_j I|^{-1} r through the block's eigendecomposition (orc_syev),
  * shifted eigenvalues of magnitude below `guard` replaced by +-guard. Returns 0, or -2 if a
@@ -597,10 +602,15 @@ int orc_block_krylov(int64_t n, int64_t nnz, const int64_t* row, const int64_t* 
   int64_t* owner = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
   for (int64_t i = 0; i < nblk; i++)
     for (int64_t r = bounds[i]; r < bounds[i + 1]; r++) owner[r] = i;
-  double* blk = (double*)malloc(64 * 64 * sizeof(double));
-  double* A = (double*)malloc(64 * 64 * sizeof(double));
-  double* Z = (double*)malloc(64 * 64 * sizeof(double));
-  double lam[64], r[64], w[64];
+  int64_t mmax = 1;
+  for (int64_t i = 0; i < nblk; i++)
+    if (bounds[i + 1] - bounds[i] > mmax) mmax = bounds[i + 1] - bounds[i];
+  double* blk = (double*)malloc((size_t)(mmax * mmax) * sizeof(double));
+  double* A = (double*)malloc((size_t)(mmax * mmax) * sizeof(double));
+  double* Z = (double*)malloc((size_t)(mmax * mmax) * sizeof(double));
+  double* lam = (double*)malloc((size_t)mmax * sizeof(double));
+  double* r = (double*)malloc((size_t)mmax * sizeof(double));
+  double* w = (double*)malloc((size_t)mmax * sizeof(double));
   int st = 0;
   for (int64_t bi = 0; bi < nblk && !st; bi++) {
     const int64_t o = bounds[bi], m = bounds[bi + 1] - o;
@@ -640,7 +650,7 @@ int orc_block_krylov(int64_t n, int64_t nnz, const int64_t* row, const int64_t* 
       }
     }
   }
-  free(owner); free(blk); free(A); free(Z);
+  free(owner); free(blk); free(A); free(Z); free(lam); free(r); free(w);
   return st;
 }
 

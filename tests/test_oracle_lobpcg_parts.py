@@ -141,7 +141,7 @@ def _blocks(A, bounds):
     return [A[bounds[i]:bounds[i + 1], bounds[i]:bounds[i + 1]] for i in range(len(bounds) - 1)]
 
 
-@pytest.mark.parametrize("bp", [5, 16])
+@pytest.mark.parametrize("bp", [5, 16, 256])
 def test_krylov_one_step_closed_forms(bp):
     """One FOM step is w = (r^T r / r^T A r) r; one minimal-residual step is
     w = (r^T A r / ||A r||^2) r (A = H~_[i] - mu_j I)."""
@@ -182,11 +182,12 @@ def test_krylov_full_space_is_the_direct_solve(bp):
 
 
 @pytest.mark.parametrize("steps", [2, 3])
-def test_krylov_galerkin_and_minimal_residual(steps):
+@pytest.mark.parametrize("bp", [24, 256])
+def test_krylov_galerkin_and_minimal_residual(steps, bp):
     """FOM: r - A w is orthogonal to K_s(A, r). Minimal residual: ||r - A w|| is no larger than
-    for any other w in K_s(A, r) (checked against the FOM iterate and random members)."""
-    rng = np.random.default_rng(60 + steps)
-    bp = 24
+    for any other w in K_s(A, r) (checked against the FOM iterate and random members). Blocks of
+    256 rows are whole diagonal tiles, the blocks of Section 4.3's preconditioner."""
+    rng = np.random.default_rng(60 + steps + bp)
     n = 2 * bp
     H = random_upper(n, 0.3, rng)
     Ad = dense_by_indexing(H)
