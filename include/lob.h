@@ -56,7 +56,11 @@ typedef struct {
 typedef struct {
   int32_t tile;          /* CSB tile size b; 0 = 256. Must be 256 in this version. */
   int32_t values;        /* LOB_VALUES_*; 0 = BOTH */
-  int32_t precond_block; /* b_p of the block-diagonal preconditioner (eq. 11), 1..64; 0 = none */
+  int32_t precond_block; /* b_p of the block-diagonal preconditioner (eq. 11), 1..64, dense
+                            blocks eigendecomposed at create; 256: the diagonal tiles themselves,
+                            solved by FOM or minimal-residual steps on the tile store at each
+                            apply (Section 4.3; needs FP32 values; lob_solve only, not the
+                            server); 0 = none */
   int32_t reserved;
   void* stream;          /* cudaStream_t for the build */
 } lob_create_opts;
@@ -66,7 +70,8 @@ typedef struct {
  * ||H||_inf, and, if precond_block > 0, the block-diagonal preconditioner of eq. 11 (the
  * diagonal b_p x b_p blocks of H, each eigendecomposed once). Synchronous. *out receives the
  * handle. Errors: LOB_ERR_ARG (n < 1, nnz < 1, bad entry, duplicate, tile != 256,
- * precond_block outside [0, 64]), LOB_ERR_NOMEM, LOB_ERR_CUDA. */
+ * precond_block outside [0, 64] and not 256, or 256 without FP32 values), LOB_ERR_NOMEM,
+ * LOB_ERR_CUDA. */
 int lob_create(const lob_coo* H, const lob_create_opts* opts, lob_matrix** out);
 
 /* Free everything lob_create allocated. NULL is accepted. */

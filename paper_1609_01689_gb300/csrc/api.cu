@@ -49,7 +49,8 @@ int lob_create(const lob_coo* H, const lob_create_opts* opts, lob_matrix** out) 
   if (o.tile != 0 && o.tile != LOB_TILE) return LOB_ERR_ARG;
   const int values = o.values ? o.values : LOB_VALUES_BOTH;
   if (values < 1 || values > 3) return LOB_ERR_ARG;
-  if (o.precond_block < 0 || o.precond_block > 64) return LOB_ERR_ARG;
+  if (o.precond_block < 0 || (o.precond_block > 64 && o.precond_block != LOB_TILE)) return LOB_ERR_ARG;
+  if (o.precond_block == LOB_TILE && !(values & LOB_VALUES_FP32)) return LOB_ERR_ARG;  // tile mode runs on FP32 values
   cudaStream_t st = (cudaStream_t)o.stream;
   *out = nullptr;
 
@@ -107,7 +108,7 @@ int lob_matrix_info_get(const lob_matrix* m, lob_matrix_info* out) {
   out->norm_inf = m->norm_inf;
   out->store_bytes = (m->T.nt + 1) * 8 + m->T.ntiles * (4 + 4 + 8) + 8 + m->T.nnz * 4 +
                      (m->T.v64 ? m->T.nnz * 8 : 0) + (m->T.v32 ? m->T.nnz * 4 : 0);  // canonical arrays only
-  out->precond_bytes = m->P.nblk * (int64_t)m->P.bp * m->P.bp * 4 + m->P.nblk * (int64_t)m->P.bp * 4;
+  out->precond_bytes = m->P.Q ? m->P.nblk * (int64_t)m->P.bp * m->P.bp * 4 + m->P.nblk * (int64_t)m->P.bp * 4 : 0;
   return LOB_OK;
 }
 

@@ -73,7 +73,8 @@ struct lob_tiles {
 // Block-diagonal preconditioner of eq. 11: per block i (rows [i*bp, i*bp + m_i)),
 // H~_[i] = Q_i diag(lam_i) Q_i^T; Q stored FP32, column-major per block (bp x bp slots).
 struct lob_precond {
-  int32_t bp = 0;
+  int32_t bp = 0;          // block order; LOB_TILE: the diagonal tiles themselves, by Krylov steps
+                           // on the tile store (no Q, lam)
   int64_t nblk = 0;
   float* Q = nullptr;      // [nblk * bp * bp]
   float* lam = nullptr;    // [nblk * bp]

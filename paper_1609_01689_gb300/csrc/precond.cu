@@ -119,60 +119,14 @@ __device__ __forceinline__ float warp_sum(float x) {
   return x;
 }
 
-// x = f(D) c for one right-hand side in a block's eigenbasis (D = Lambda - mu I diagonal,
-// c = Q^T r), one warp, entries k = lane and lane + 32. The Krylov solvers of eq. 11 with a
-// zero start reduce to this basis exactly: K_m(A, r) = Q K_m(D, c), so Lanczos on (D, c)
-// gives the FOM (Galerkin) or minimal-residual iterate of (H~ - mu I) w = r after m steps.
-__device__ void block_solve(int solve, int steps, float guard, const float d[2], const float c[2], float x[2]) {
-  if (solve == LOB_PSOLVE_DIRECT || solve == LOB_PSOLVE_ABS) {
-#pragma unroll
-    for (int u = 0; u < 2; u++) {
-      float dd = d[u];
-      if (solve == LOB_PSOLVE_ABS) dd = fabsf(dd);
-      if (fabsf(dd) < guard) dd = dd < 0.f ? -guard : guard;
-      x[u] = c[u] / dd;
-    }
-    return;
-  }
-  // All loops below run to the fixed bound KM = 3 (the most Krylov steps) and test the runtime
-  // count inside, so every small array is indexed by constants and stays in registers.
+// Coefficients y of the Krylov iterate w = V y after m Lanczos steps (T = tridiag(al, be),
+// be[m-1] coupling to the next vector): FOM solves T y = beta0 e1 by elimination without
+// pivoting, and a pivot below 1e-4 max_i(|al_i| + be_i) counts as a FOM breakdown; then, and for
+// the minimal-residual solve, y minimises || beta0 e1 - T_bar y || (Givens rotations on the
+// (m+1) x m T_bar).
+__device__ __forceinline__ void krylov_coeffs(int solve, int m, const float al[3], const float be[3], float beta0, float y[3]) {
   constexpr int KM = 3;
-  x[0] = x[1] = 0.f;
-  const float beta0 = sqrtf(warp_sum(c[0] * c[0] + c[1] * c[1]));
-  if (!(beta0 > 0.f)) return;
-  // Lanczos on (D, c), full reorthogonalisation (at most 3 vectors)
-  float v[KM][2], al[KM], be[KM];
-#pragma unroll
-  for (int i = 0; i < KM; i++) { v[i][0] = v[i][1] = 0.f; al[i] = be[i] = 0.f; }
-  v[0][0] = c[0] / beta0;
-  v[0][1] = c[1] / beta0;
-  int m = 0;
-  bool done = false;  // warp-uniform: it depends on warp sums only
-#pragma unroll
-  for (int i = 0; i < KM; i++) {
-    if (done || i >= steps) continue;
-    float w[2] = {d[0] * v[i][0], d[1] * v[i][1]};
-    al[i] = warp_sum(v[i][0] * w[0] + v[i][1] * w[1]);
-    m = i + 1;
-#pragma unroll
-    for (int t = 0; t < KM; t++) {
-      if (t > i) continue;
-      const float h = warp_sum(v[t][0] * w[0] + v[t][1] * w[1]);
-      w[0] -= h * v[t][0];
-      w[1] -= h * v[t][1];
-    }
-    be[i] = sqrtf(warp_sum(w[0] * w[0] + w[1] * w[1]));
-    const float scale = fabsf(al[i]) + (i > 0 ? be[i > 0 ? i - 1 : 0] : 0.f);
-    if (i + 1 == steps || !(be[i] > 1e-6f * scale)) {
-      if (!(be[i] > 1e-6f * scale)) be[i] = 0.f;  // invariant subspace: both iterates are exact
-      done = true;
-    } else if (i + 1 < KM) {
-      v[i + 1 < KM ? i + 1 : i][0] = w[0] / be[i];
-      v[i + 1 < KM ? i + 1 : i][1] = w[1] / be[i];
-    }
-  }
   // tridiagonal T (m x m): diagonal al, off-diagonal be[0..m-2]; T_bar adds the row be[m-1] e_m^T
-  float y[KM];
 #pragma unroll
   for (int i = 0; i < KM; i++) y[i] = 0.f;
   bool ok = false;
@@ -251,6 +205,62 @@ __device__ void block_solve(int solve, int steps, float guard, const float d[2],
       y[i] = fabsf(R[i][i]) > 1e-6f * tmax ? s2 / R[i][i] : 0.f;
     }
   }
+}
+
+// x = f(D) c for one right-hand side in a block's eigenbasis (D = Lambda - mu I diagonal,
+// c = Q^T r), one warp, entries k = lane and lane + 32. The Krylov solvers of eq. 11 with a
+// zero start reduce to this basis exactly: K_m(A, r) = Q K_m(D, c), so Lanczos on (D, c)
+// gives the FOM (Galerkin) or minimal-residual iterate of (H~ - mu I) w = r after m steps.
+__device__ void block_solve(int solve, int steps, float guard, const float d[2], const float c[2], float x[2]) {
+  if (solve == LOB_PSOLVE_DIRECT || solve == LOB_PSOLVE_ABS) {
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+      float dd = d[u];
+      if (solve == LOB_PSOLVE_ABS) dd = fabsf(dd);
+      if (fabsf(dd) < guard) dd = dd < 0.f ? -guard : guard;
+      x[u] = c[u] / dd;
+    }
+    return;
+  }
+  // All loops below run to the fixed bound KM = 3 (the most Krylov steps) and test the runtime
+  // count inside, so every small array is indexed by constants and stays in registers.
+  constexpr int KM = 3;
+  x[0] = x[1] = 0.f;
+  const float beta0 = sqrtf(warp_sum(c[0] * c[0] + c[1] * c[1]));
+  if (!(beta0 > 0.f)) return;
+  // Lanczos on (D, c), full reorthogonalisation (at most 3 vectors)
+  float v[KM][2], al[KM], be[KM];
+#pragma unroll
+  for (int i = 0; i < KM; i++) { v[i][0] = v[i][1] = 0.f; al[i] = be[i] = 0.f; }
+  v[0][0] = c[0] / beta0;
+  v[0][1] = c[1] / beta0;
+  int m = 0;
+  bool done = false;  // warp-uniform: it depends on warp sums only
+#pragma unroll
+  for (int i = 0; i < KM; i++) {
+    if (done || i >= steps) continue;
+    float w[2] = {d[0] * v[i][0], d[1] * v[i][1]};
+    al[i] = warp_sum(v[i][0] * w[0] + v[i][1] * w[1]);
+    m = i + 1;
+#pragma unroll
+    for (int t = 0; t < KM; t++) {
+      if (t > i) continue;
+      const float h = warp_sum(v[t][0] * w[0] + v[t][1] * w[1]);
+      w[0] -= h * v[t][0];
+      w[1] -= h * v[t][1];
+    }
+    be[i] = sqrtf(warp_sum(w[0] * w[0] + w[1] * w[1]));
+    const float scale = fabsf(al[i]) + (i > 0 ? be[i > 0 ? i - 1 : 0] : 0.f);
+    if (i + 1 == steps || !(be[i] > 1e-6f * scale)) {
+      if (!(be[i] > 1e-6f * scale)) be[i] = 0.f;  // invariant subspace: both iterates are exact
+      done = true;
+    } else if (i + 1 < KM) {
+      v[i + 1 < KM ? i + 1 : i][0] = w[0] / be[i];
+      v[i + 1 < KM ? i + 1 : i][1] = w[1] / be[i];
+    }
+  }
+  float y[KM];
+  krylov_coeffs(solve, m, al, be, beta0, y);
 #pragma unroll
   for (int i = 0; i < KM; i++) {
     if (i >= m) continue;
@@ -359,6 +369,206 @@ __global__ void __launch_bounds__(256) k_block_apply_batch(const lob_bjob* __res
                    threadIdx.x % tpb, tpb, valid);
 }
 
+// Eq. 11 on the diagonal CSB tiles (Section 4.3: the block-diagonal preconditioner built from the
+// diagonal tiles of H, each shifted system solved by two or three FOM iterations from a zero
+// start). One CTA per diagonal tile I, 1,024 threads: the lane group g of four lanes owns in-tile
+// row g, each lane four of the NB = 16 columns of one pass. A product with the tile uses the tile
+// store's own layout -- the row pass over the chunk's row pointers and the column pass through
+// its column-order permutation, the stored diagonal applied once -- in FP32 (footnote 5), with
+// the pass's Lanczos vectors in shared memory. Per column j: Lanczos on (H~_I - mu_j I, r_j) with
+// full reorthogonalisation (classical Gram-Schmidt against the at most three vectors), the
+// invariant-subspace test and the projected solve of the eigenbasis path (krylov_coeffs), then
+// w_j = V y. Rows at or beyond n_act are outside the operator: their r is zero and every product
+// is cut to the active rows.
+template <int NB>
+struct CfgTF {
+  static constexpr int VW = 4, G = NB / VW, THREADS = LOB_TILE * G, NW = THREADS / 32, KM = 3;
+  static constexpr size_t V = 0;                                      // [KM][TILE][NB] Lanczos vectors
+  static constexpr size_t PART = V + sizeof(float) * KM * LOB_TILE * NB;  // [NW][KM][NB] warp partial sums
+  static constexpr size_t RES = PART + sizeof(float) * NW * KM * NB;      // [KM][NB] CTA sums
+  static constexpr size_t AL = RES + sizeof(float) * KM * NB;             // [KM][NB]
+  static constexpr size_t BE = AL + sizeof(float) * KM * NB;              // [KM][NB]
+  static constexpr size_t Y = BE + sizeof(float) * KM * NB;               // [KM][NB]
+  static constexpr size_t B0 = Y + sizeof(float) * KM * NB;               // [NB]
+  static constexpr size_t MC = B0 + sizeof(float) * NB;                   // [NB] steps taken per column
+  static constexpr size_t BYTES = MC + sizeof(int) * NB;
+  static_assert(VW * G == NB && THREADS <= 1024, "launch shape");
+};
+
+// Sums over the CTA's rows, per column, of KV values a thread holds for its four columns:
+// xor-shuffles over the eight groups of a warp, then a fixed-order sum over the warps.
+template <int NB, int KV>
+__device__ __forceinline__ void tile_col_sums(float (&x)[KV][4], float* part, float* res) {
+  using C = CfgTF<NB>;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int k = 0; k < KV; k++)
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      float v = x[k][q];
+      v += __shfl_xor_sync(0xFFFFFFFFu, v, 4);
+      v += __shfl_xor_sync(0xFFFFFFFFu, v, 8);
+      v += __shfl_xor_sync(0xFFFFFFFFu, v, 16);
+      if (lane < C::G) part[(warp * C::KM + k) * NB + lane * 4 + q] = v;
+    }
+  __syncthreads();
+  if (tid < KV * NB) {
+    const int k = tid / NB, j = tid % NB;
+    float sum = 0.f;
+    for (int w2 = 0; w2 < C::NW; w2++) sum += part[(w2 * C::KM + k) * NB + j];
+    res[k * NB + j] = sum;
+  }
+  __syncthreads();
+}
+
+template <int NB>
+__global__ void __launch_bounds__(CfgTF<NB>::THREADS, 1)
+    k_tile_fom(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ tcol,
+               const int64_t* __restrict__ tptr, const int32_t* __restrict__ tchunk,
+               const uint2* __restrict__ rv, const uint16_t* __restrict__ cperm,
+               const uint16_t* __restrict__ cptrs, const double* __restrict__ mu, const double* __restrict__ R,
+               double* __restrict__ W, int nb, int c0, int w, int64_t n_act, int solve, int steps) {
+  using C = CfgTF<NB>;
+  constexpr int KM = C::KM, CH = LOB_PERM_CHUNK, PTRS = 2 * (LOB_TILE + 1);
+  extern __shared__ __align__(16) unsigned char smt[];
+  float* V = reinterpret_cast<float*>(smt + C::V);
+  float* part = reinterpret_cast<float*>(smt + C::PART);
+  float* res = reinterpret_cast<float*>(smt + C::RES);
+  float* al = reinterpret_cast<float*>(smt + C::AL);
+  float* be = reinterpret_cast<float*>(smt + C::BE);
+  float* ys = reinterpret_cast<float*>(smt + C::Y);
+  float* b0 = reinterpret_cast<float*>(smt + C::B0);
+  int* mc = reinterpret_cast<int*>(smt + C::MC);
+  const int tid = threadIdx.x, g = tid / C::G, gl = tid % C::G;
+  const int64_t I = blockIdx.x, o = I * LOB_TILE;
+  const int m_act = (int)((n_act - o) < LOB_TILE ? (n_act - o) : LOB_TILE);
+  const bool live = g < m_act;
+  const int64_t t0 = rowptr[I];
+  const bool has_diag = t0 < rowptr[I + 1] && tcol[t0] == (int32_t)I;
+  const int nk = has_diag ? tchunk[t0 + 1] - tchunk[t0] : 0;
+
+  float r[4], muf[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const int j = gl * 4 + q;
+    r[q] = (live && j < w) ? (float)R[(o + g) * nb + c0 + j] : 0.f;
+    muf[q] = j < w ? (float)mu[c0 + j] : 0.f;
+  }
+  {  // beta0 = ||r_j|| over the tile's rows
+    float x[1][4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) x[0][q] = r[q] * r[q];
+    tile_col_sums<NB, 1>(x, part, res);
+  }
+  if (tid < NB) {
+    b0[tid] = sqrtf(res[tid]);
+    mc[tid] = 0;
+  }
+  if (tid < KM * NB) al[tid] = be[tid] = 0.f;
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const float bb = b0[gl * 4 + q];
+    V[g * NB + gl * 4 + q] = bb > 0.f ? r[q] / bb : 0.f;
+  }
+  __syncthreads();
+
+  for (int i = 0; i < steps; i++) {
+    const float* Vi = V + (size_t)i * LOB_TILE * NB;
+    // u = (H~_I - mu I) v_i on this group's row
+    float u[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < nk; k++) {
+      const int64_t base = tptr[t0] + (int64_t)k * CH;
+      const uint16_t* PR = cptrs + (int64_t)(tchunk[t0] + k) * PTRS;
+      const uint16_t* PC = PR + (LOB_TILE + 1);
+      const int rs = __ldg(&PR[g]), re = __ldg(&PR[g + 1]);
+      for (int e = rs; e < re; e++) {
+        const uint2 ent = __ldg(&rv[base + e]);
+        const float val = __uint_as_float(ent.y);
+        const float4 x = *reinterpret_cast<const float4*>(&Vi[(int)(ent.x & 0xFFFFu) * NB + gl * 4]);
+        u[0] = fmaf(val, x.x, u[0]); u[1] = fmaf(val, x.y, u[1]); u[2] = fmaf(val, x.z, u[2]); u[3] = fmaf(val, x.w, u[3]);
+      }
+      const int cs = __ldg(&PC[g]), ce = __ldg(&PC[g + 1]);
+      for (int e = cs; e < ce; e++) {
+        const uint2 ent = __ldg(&rv[base + (__ldg(&cperm[base + e]) & (CH - 1))]);
+        const int rr = (int)(ent.x >> 16);
+        if (rr == g) continue;  // the diagonal entry is applied once (row pass)
+        const float val = __uint_as_float(ent.y);
+        const float4 x = *reinterpret_cast<const float4*>(&Vi[rr * NB + gl * 4]);
+        u[0] = fmaf(val, x.x, u[0]); u[1] = fmaf(val, x.y, u[1]); u[2] = fmaf(val, x.z, u[2]); u[3] = fmaf(val, x.w, u[3]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) u[q] = live ? fmaf(-muf[q], Vi[g * NB + gl * 4 + q], u[q]) : 0.f;
+    // h_t = v_t . u for t <= i (classical Gram-Schmidt); alpha_i = h_i
+    {
+      float x[KM][4];
+#pragma unroll
+      for (int t = 0; t < KM; t++)
+#pragma unroll
+        for (int q = 0; q < 4; q++) x[t][q] = t <= i ? V[((size_t)t * LOB_TILE + g) * NB + gl * 4 + q] * u[q] : 0.f;
+      tile_col_sums<NB, KM>(x, part, res);
+    }
+#pragma unroll
+    for (int t = 0; t < KM; t++) {
+      if (t > i) continue;
+#pragma unroll
+      for (int q = 0; q < 4; q++) u[q] = fmaf(-res[t * NB + gl * 4 + q], V[((size_t)t * LOB_TILE + g) * NB + gl * 4 + q], u[q]);
+    }
+    if (tid < NB) al[i * NB + tid] = res[i * NB + tid];
+    {
+      float x[1][4];
+#pragma unroll
+      for (int q = 0; q < 4; q++) x[0][q] = u[q] * u[q];
+      tile_col_sums<NB, 1>(x, part, res);  // its first barrier also orders the al writes above
+    }
+    if (tid < NB && mc[tid] == 0 && b0[tid] > 0.f) {
+      float bi = sqrtf(res[tid]);
+      const float scale = fabsf(al[i * NB + tid]) + (i > 0 ? be[(i - 1) * NB + tid] : 0.f);
+      const bool brk = !(bi > 1e-6f * scale);
+      if (brk) bi = 0.f;  // invariant subspace: the iterate is exact
+      be[i * NB + tid] = bi;
+      if (brk || i + 1 == steps) mc[tid] = i + 1;
+    }
+    __syncthreads();
+    if (i + 1 < steps) {
+      float* Vn = V + (size_t)(i + 1) * LOB_TILE * NB;
+#pragma unroll
+      for (int q = 0; q < 4; q++) {
+        const int j = gl * 4 + q;
+        const bool stop = mc[j] != 0 || !(b0[j] > 0.f);
+        Vn[g * NB + j] = stop ? 0.f : u[q] / be[i * NB + j];
+      }
+      __syncthreads();
+    }
+  }
+  if (tid < NB) {
+    float a3[KM], b3[KM], y3[KM];
+#pragma unroll
+    for (int t = 0; t < KM; t++) { a3[t] = al[t * NB + tid]; b3[t] = be[t * NB + tid]; }
+    const int m = mc[tid];
+    if (m > 0) {
+      krylov_coeffs(solve, m, a3, b3, b0[tid], y3);
+    } else {
+#pragma unroll
+      for (int t = 0; t < KM; t++) y3[t] = 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < KM; t++) ys[t * NB + tid] = t < m ? y3[t] : 0.f;
+  }
+  __syncthreads();
+  if (!live) return;
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    const int j = gl * 4 + q;
+    if (j >= w) continue;
+    float x = 0.f;
+#pragma unroll
+    for (int t = 0; t < KM; t++) x = fmaf(ys[t * NB + j], V[((size_t)t * LOB_TILE + g) * NB + j], x);
+    W[(o + g) * nb + c0 + j] = (double)x;
+  }
+}
+
 }  // namespace
 
 void lob_free_precond(lob_precond* P) {
@@ -367,6 +577,13 @@ void lob_free_precond(lob_precond* P) {
 }
 
 int lob_build_precond(const lob_coo* H, int bp, int64_t n, cudaStream_t st, lob_precond* P) {
+  if (bp == LOB_TILE) {  // the diagonal tiles of the tile store are the blocks: nothing to build
+    lob_precond R;
+    R.bp = LOB_TILE;
+    R.nblk = (n + LOB_TILE - 1) / LOB_TILE;
+    *P = R;
+    return LOB_OK;
+  }
   if (bp < 1 || bp > 64 || !H->on_device) return LOB_ERR_ARG;
   lob_precond R;
   R.bp = bp;
@@ -399,6 +616,25 @@ int lob_precond_launch(const lob_matrix* m, const double* mu, const double* R, d
   const lob_precond& P = m->P;
   if (P.bp < 1 || nb < 1 || nb > 64) return LOB_ERR_ARG;
   if (solve < LOB_PSOLVE_FOM || solve > LOB_PSOLVE_ABS || steps < 1 || steps > 3) return LOB_ERR_ARG;
+  if (P.bp == LOB_TILE) {  // FOM / minimal residual on the diagonal tiles
+    if ((solve != LOB_PSOLVE_FOM && solve != LOB_PSOLVE_MINRES) || !m->T.rv) return LOB_ERR_ARG;
+    constexpr int NB = 16;
+    using C = CfgTF<NB>;
+    const int64_t nt_act = (n_act + LOB_TILE - 1) / LOB_TILE;
+    if (n_act < m->T.n) LOB_CUDA(cudaMemsetAsync(W + n_act * nb, 0, (size_t)(m->T.n - n_act) * nb * 8, st));
+    if (nt_act == 0) return LOB_OK;
+    LOB_CUDA(cudaFuncSetAttribute(k_tile_fom<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::BYTES));
+    const lob_tiles& T = m->T;
+    for (int c0 = 0; c0 < nb; c0 += NB) {
+      const int w = (nb - c0) < NB ? (nb - c0) : NB;
+      (k_tile_fom<NB><<<(unsigned)nt_act, C::THREADS, C::BYTES, st>>>(T.rowptr, T.tcol, T.tptr, T.tchunk, T.rv,
+                                                                      T.cperm, T.cptrs, mu, R, W, nb, c0, w, n_act,
+                                                                      solve, steps),
+       LOB_LAUNCHED());
+    }
+    LOB_CUDA(cudaGetLastError());
+    return LOB_OK;
+  }
   const int bp = P.bp;
   const size_t smem = ((size_t)bp * bp + 2ull * bp * nb) * sizeof(float);
   const int64_t nblk = (n_act + bp - 1) / bp;

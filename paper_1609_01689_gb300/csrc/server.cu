@@ -32,7 +32,7 @@ size_t matrix_bytes(const lob_matrix* m) {
   if (T.cperm) b += (size_t)(T.nnz + 8) * 2;
   b += (size_t)(T.nt + 1) * 8 + (size_t)T.ntiles * 8 + (size_t)(T.ntiles + 1) * 12;
   b += (size_t)T.nchunks * 2 * (LOB_TILE + 1) * 2;
-  b += (size_t)m->P.nblk * m->P.bp * m->P.bp * 4 + (size_t)m->P.nblk * m->P.bp * 4;
+  if (m->P.Q) b += (size_t)m->P.nblk * m->P.bp * m->P.bp * 4 + (size_t)m->P.nblk * m->P.bp * 4;
   b += (size_t)T.nt * LOB_TILE * 16 * 8;  // staged X at the widest batched class
   return b;
 }
@@ -354,7 +354,7 @@ int lob_server_submit(lob_server* s, const lob_request* r, int64_t* id) {
   if (o.mode != LOB_MODE_FP64 && o.mode != LOB_MODE_MIXED) return LOB_ERR_ARG;
   if (o.mode == LOB_MODE_MIXED && (!H->T.v32 || !H->T.v64)) return LOB_ERR_ARG;
   if (o.mode == LOB_MODE_FP64 && !H->T.v64) return LOB_ERR_ARG;
-  if (o.precond && H->P.bp < 1) return LOB_ERR_ARG;
+  if (o.precond && (H->P.bp < 1 || H->P.bp > 64)) return LOB_ERR_ARG;  // the engine applies dense blocks only
   if (o.precond_solve < LOB_PSOLVE_FOM || o.precond_solve > LOB_PSOLVE_ABS || o.precond_steps < 0 ||
       o.precond_steps > 3)
     return LOB_ERR_ARG;

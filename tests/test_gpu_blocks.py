@@ -157,3 +157,52 @@ def test_rayleigh_ritz_reports_indefinite(mode):
     Mm = np.array([[1.0, 1.0], [1.0, 1.0]])
     with pytest.raises(np.linalg.LinAlgError):
         lob.rayleigh_ritz(t(np.eye(2)), t(Mm), mode)
+
+
+@pytest.mark.parametrize("solve,steps", [("fom", 1), ("fom", 2), ("fom", 3), ("minres", 2), ("minres", 3)])
+@pytest.mark.parametrize("ncol", [4, 20])
+def test_precond_tiles_match_oracle(solve, steps, ncol):
+    """Eq. 11 on the diagonal tiles (Section 4.3), the blocks being whole 256-row tiles: Krylov
+    steps on the sparse tile in FP32 on the GPU, dense Lanczos in FP64 in the oracle. The last
+    tile is partial (n = 2,500), and 20 columns take two passes of the kernel. Shifts below every
+    tile's spectrum (definite systems). Bound as for the dense blocks: 16 b u32 kappa_j with
+    b = 256 and kappa_j = ||H~|| / min |lambda - mu_j| over the tiles."""
+    import paper_1609_01689_gb300 as lob
+    L = synth.layout(2500, 7, 40, 5)
+    r, c, v = synth.generate(L)
+    H = oracle.Coo(L.n, r, c, v)
+    M = lob.Matrix(L.n, r, c, v, precond_block=256)
+    bounds = oracle.uniform_bounds(L.n, 256)
+    A = oracle.dense(H)
+    blocks = [np.linalg.eigvalsh(A[bounds[i]:bounds[i + 1], bounds[i]:bounds[i + 1]]) for i in range(len(bounds) - 1)]
+    lo = min(b.min() for b in blocks)
+    mu = lo - np.array([0.5, 2.0, 7.0, 20.0] * 5)[:ncol]
+    rng = np.random.default_rng(ncol + steps)
+    R = rng.standard_normal((L.n, ncol))
+    W = M.precond_apply(t(mu), t(R), solve=solve, steps=steps).cpu().numpy()
+    ref = oracle.block_krylov(H, bounds, mu, R, solve, steps)
+    err = np.abs(W - ref).max(axis=0) / np.abs(ref).max(axis=0)
+    kappa = np.ones(ncol)
+    for lam_b in blocks:
+        d = np.abs(lam_b[:, None] - mu[None, :])
+        kappa = np.maximum(kappa, np.abs(lam_b).max() / d.min(axis=0))
+    assert np.all(err <= 16 * 256 * 2.0 ** -24 * kappa), (err, kappa)
+
+
+def test_precond_tiles_rejects_what_it_cannot_do():
+    """Tile mode needs FP32 values, takes only the Krylov solves, and is not served by the engine."""
+    import paper_1609_01689_gb300 as lob
+    L = synth.layout(1000, 6, 30, 2)
+    r, c, v = synth.generate(L)
+    with pytest.raises(lob.LobError):
+        lob.Matrix(L.n, r, c, v, precond_block=256, values=lob.VALUES_FP64)
+    with pytest.raises(lob.LobError):
+        lob.Matrix(L.n, r, c, v, precond_block=100)
+    M = lob.Matrix(L.n, r, c, v, precond_block=256)
+    R = np.random.default_rng(1).standard_normal((L.n, 4))
+    with pytest.raises(lob.LobError):
+        M.precond_apply(t(np.zeros(4) - 9.0), t(R), solve="direct")
+    srv = lob.Server(budget_bytes=1 << 30)
+    with pytest.raises(lob.LobError):
+        srv.submit(M, 2, 4, 1e-8, precond=True)
+    srv.close()

@@ -171,3 +171,32 @@ def test_solve_multilevel_guess_500k(c2_golden):
     assert res.max() <= 1e-8, res
     with pytest.raises(lob.LobError):
         M.solve(8, 16, 1e-8, mode="mixed", precond=True, n_small=int(lv[9]), guess_tol=1.5)
+
+
+@pytest.mark.parametrize("mode,tol_lam", [("fp64", 1e-9), ("mixed", 1e-8)])
+def test_solve_tile_preconditioner_c1(c1, mode, tol_lam):
+    """Section 4.3's preconditioner: FOM steps on the diagonal tiles (precond_block = 256)."""
+    import paper_1609_01689_gb300 as lob
+    L, H, lam_ref, X_ref = c1
+    M = lob.Matrix(L.n, H.rows, H.cols, H.vals, precond_block=256)
+    n_small = int(synth.level_starts(L)[2])
+    lam, X, st, rc = M.solve(5, 8, 1e-8, mode=mode, precond=True, n_small=n_small)
+    assert rc == lob.LOB_OK
+    check(H, L, lam, X, lam_ref, X_ref, 5, tol_lam, 1e-8)
+
+
+def test_solve_tile_preconditioner_500k(c2_golden):
+    """The n = 500,000 workload with the diagonal-tile preconditioner, mixed precision: the
+    oracle's eigenvalues and residuals, as with the dense 32 x 32 blocks."""
+    import paper_1609_01689_gb300 as lob
+    L = synth.config_layout("c2")
+    r, c, v = synth.generate_device(L)
+    M = lob.Matrix(L.n, r, c, v, precond_block=256)
+    lam, X, st, rc = M.solve(8, 16, 1e-8, mode="mixed", precond=True, n_small=int(synth.level_starts(L)[2]))
+    assert rc == lob.LOB_OK
+    rel = np.abs(lam - c2_golden[:8]) / np.maximum(np.abs(c2_golden[:8]), 1.0)
+    assert rel.max() <= 1e-8, rel
+    rows, cols, vals = synth.generate(L)
+    H = oracle.Coo(L.n, rows, cols, vals)
+    res = oracle.residual_norms(H, X.cpu().numpy()[:, :8], lam) / oracle.norm_inf(H)
+    assert res.max() <= 1e-8, res
