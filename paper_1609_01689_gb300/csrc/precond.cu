@@ -562,9 +562,11 @@ __global__ void __launch_bounds__(CfgTF<NB>::THREADS, 1)
   for (int q = 0; q < 4; q++) {
     const int j = gl * 4 + q;
     if (j >= w) continue;
+    const int m = mc[j];  // Lanczos vectors past the column's last step were never written
     float x = 0.f;
 #pragma unroll
-    for (int t = 0; t < KM; t++) x = fmaf(ys[t * NB + j], V[((size_t)t * LOB_TILE + g) * NB + j], x);
+    for (int t = 0; t < KM; t++)
+      if (t < m) x = fmaf(ys[t * NB + j], V[((size_t)t * LOB_TILE + g) * NB + j], x);
     W[(o + g) * nb + c0 + j] = (double)x;
   }
 }
