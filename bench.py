@@ -31,8 +31,8 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 WORKLOADS = {
-    "c2": dict(name="n=500000 levels 0..10, ~200 nnz/row, k=8, nb=16, b_p=32, tol 1e-8", cfg="c2", k=8, nb=16,
-               bp=32, tol=1e-8),
+    "c2": dict(name="n=500000 levels 0..10, ~200 nnz/row, k=8, nb=16, preconditioner on the diagonal 256x256 "
+                    "tiles (FOM 3), tol 1e-8", cfg="c2", k=8, nb=16, bp=256, tol=1e-8),
     "c1": dict(name="n=1536 levels 0..6, ~30 nnz/row, k=5, nb=8, b_p=32, tol 1e-8", cfg="c1", k=5, nb=8, bp=32,
                tol=1e-8),
     "c3": dict(name="n=8000000 levels 0..14, ~300 nnz/row, k=10, nb=16, b_p=64, tol 1e-8", cfg="c3", k=10, nb=16,
@@ -249,13 +249,14 @@ def guess_ablation(M, k, nb, tol, X, layout, stream, args, torch, wl, ms_one, st
 
 
 def precond_ablation(lob, synth, layout, k, nb, tol, n_small, stream, args, torch, wl, ms_one, st_one):
-    """Preconditioner ablation: the headline's dense b_p x b_p blocks (eigendecomposed at create,
-    FOM in each block's eigenbasis) against Section 4.3's own choice, the diagonal 256 x 256 tiles
-    with FOM steps on the tile store (precond_block = 256). Same matrix, guess and tolerance; each
-    solve timed end to end with CUDA events."""
+    """Preconditioner ablation: Section 4.3's own choice, the diagonal 256 x 256 tiles with FOM
+    steps on the tile store (precond_block = 256), against dense 32 x 32 blocks eigendecomposed
+    at create with FOM in each block's eigenbasis -- whichever of the two the headline does not
+    use. Same matrix, guess and tolerance; each solve timed end to end with CUDA events."""
+    alt = 32 if wl["bp"] == 256 else 256
     r, c, v = synth.generate_device(layout)
     t0 = time.perf_counter()
-    M = lob.Matrix(layout.n, r, c, v, precond_block=256)
+    M = lob.Matrix(layout.n, r, c, v, precond_block=alt)
     torch.cuda.synchronize()
     create_ms = (time.perf_counter() - t0) * 1e3
     del r, c, v
@@ -274,17 +275,17 @@ def precond_ablation(lob, synth, layout, k, nb, tol, n_small, stream, args, torc
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     lam, _, st, rc = res[-1]
-    out = {"dense_blocks": {"b_p": wl["bp"], "ms": ms_one, "iterations": st_one["iterations"],
-                            "refine_iterations": st_one["refine_iterations"],
-                            "precond_ms": st_one["phase_ms"]["precond"]},
-           "diagonal_tiles": {"b_p": 256, "ms": ms, "iterations": st["iterations"],
-                              "refine_iterations": st["refine_iterations"], "precond_ms": st["phase_ms"]["precond"],
-                              "create_ms": create_ms, "status": int(rc), "max_relres": max(st["residual"][:k])},
-           "speedup": ms_one / ms if ms > 0 else None}
+    head = {"b_p": wl["bp"], "ms": ms_one, "iterations": st_one["iterations"],
+            "refine_iterations": st_one["refine_iterations"], "precond_ms": st_one["phase_ms"]["precond"]}
+    other = {"b_p": alt, "ms": ms, "iterations": st["iterations"], "refine_iterations": st["refine_iterations"],
+             "precond_ms": st["phase_ms"]["precond"], "create_ms": create_ms, "status": int(rc),
+             "max_relres": max(st["residual"][:k])}
     gold, _ = golden_eigs(wl["cfg"])
     if gold is not None:
-        out["diagonal_tiles"]["eig_err_vs_oracle"] = float(
-            (np.abs(lam - gold[:k]) / np.maximum(np.abs(gold[:k]), 1.0)).max())
+        other["eig_err_vs_oracle"] = float((np.abs(lam - gold[:k]) / np.maximum(np.abs(gold[:k]), 1.0)).max())
+    tiles, dense = (head, other) if wl["bp"] == 256 else (other, head)
+    out = {"diagonal_tiles": tiles, "dense_blocks": dense, "headline": "diagonal_tiles" if wl["bp"] == 256 else
+           "dense_blocks", "tiles_speedup_over_dense": dense["ms"] / tiles["ms"] if tiles["ms"] > 0 else None}
     M.close()
     return out
 
@@ -472,10 +473,11 @@ def run_batched_small(args, lob, synth, torch):
             "max_eig_rel_diff_vs_fp64_single": diff, "sample": len(samp)}
 
 
-def run_kernels(args, lob, M, info, torch):
+def run_kernels(args, lob, M, info, torch, make_matrix):
     """Each hot-path kernel alone at the workload's sizes (CUDA events, L2 flushed between
     repetitions): the symmetric SpMM in its three arithmetics, the 48 x 48 double-float Gram,
-    the n x 48 by 48 x 16 double-float linear combination and the 48 x 48 Rayleigh-Ritz solve.
+    the n x 48 by 48 x 16 double-float linear combination, the 48 x 48 Rayleigh-Ritz solve and the
+    preconditioner on dense 32 x 32 blocks and on the diagonal tiles.
     Prints one JSON line; a clean target for profiler captures of one launch of each kernel."""
     n, nb = M.n, 16
     g = torch.Generator(device="cuda").manual_seed(5)
@@ -513,11 +515,18 @@ def run_kernels(args, lob, M, info, torch):
     timeit("lincomb_df_48x16", lambda: lob.lincomb(S, Cm, "mixed"), df_macs=n * 48 * 16,
            algorithmic_bytes=n * (48 + 16) * 8)
     timeit("rayleigh_ritz_df_48", lambda: lob.rayleigh_ritz(Gs, Ms, "mixed"), reps=20)
-    if info.get("precond_block", 0) > 0:
-        bp = int(info["precond_block"])
-        mu = torch.linspace(-5.0, -4.0, nb, dtype=torch.float64, device="cuda")
-        timeit("precond_fom3", lambda: M.precond_apply(mu, X, solve="fom", steps=3),
-               algorithmic_bytes=((n + bp - 1) // bp) * bp * bp * 4 + 2 * n * nb * 8)
+    mu = torch.linspace(-5.0, -4.0, nb, dtype=torch.float64, device="cuda")
+    # the preconditioner both ways: dense 32 x 32 blocks (eigenbasis FOM) and the diagonal tiles
+    for bp in (32, 256):
+        Mp = M if int(info.get("precond_block", 0)) == bp else make_matrix(bp)
+        if bp == 256:  # R and W; the diagonal tiles come from the tile store (counted with the SpMM)
+            timeit("precond_tiles_fom3", lambda Mp=Mp: Mp.precond_apply(mu, X, solve="fom", steps=3),
+                   algorithmic_bytes=2 * n * nb * 8)
+        else:
+            timeit("precond_fom3", lambda Mp=Mp: Mp.precond_apply(mu, X, solve="fom", steps=3),
+                   algorithmic_bytes=((n + bp - 1) // bp) * bp * bp * 4 + 2 * n * nb * 8)
+        if Mp is not M:
+            Mp.close()
     for v in out.values():
         if "algorithmic_bytes" in v:
             v["gbs"] = v["algorithmic_bytes"] / (v["ms"] * 1e-3) / 1e9
@@ -604,7 +613,8 @@ def main():
     create_ms = (time.perf_counter() - t0) * 1e3
     info = M.info()
     if args.kernels:
-        return run_kernels(args, lob, M, info, torch)
+        return run_kernels(args, lob, M, info, torch,
+                           lambda bp: lob.Matrix(n, rows, cols, vals, precond_block=bp))
     n_small = int(synth.level_starts(layout)[2])
     k, nb, tol = wl["k"], wl["nb"], wl["tol"]
     X = torch.empty((n, nb), dtype=torch.float64, device="cuda")
