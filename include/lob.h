@@ -145,6 +145,9 @@ int lob_lincomb(int64_t n, int32_t p, const double* A, int32_t lda, int32_t q, c
  * Q^T r). FOM falls back to the minimal-residual iterate on a breakdown (a pivot of the
  * projected tridiagonal below 1e-4 of its largest entry). For DIRECT and ABS a shifted
  * eigenvalue with |lambda - mu_j| < 1e-8 ||H|| is replaced by +-1e-8 ||H|| keeping its sign.
+ * With precond_block = 256 the blocks are the diagonal 256 x 256 tiles and nothing was
+ * factorised: FOM and minimal residual run Lanczos (full reorthogonalisation) with products
+ * taken from the tile store, then the same projected solve; DIRECT and ABS are LOB_ERR_ARG.
  * Arithmetic FP32 (Section 4.4, footnote 5), inputs/outputs FP64. R, W: device n x nb; mu:
  * device, nb. Needs precond_block > 0 at create. Errors: LOB_ERR_ARG. */
 int lob_precond_apply(lob_matrix* m, const double* mu, const double* R, double* W, int32_t nb, int32_t solve,
