@@ -46,9 +46,11 @@ def test_spmm_dense_tiles_integer_exact(n, density, nb, mode):
     assert np.array_equal(run(M, X, mode), oracle.spmm(H, X))
 
 
-@pytest.mark.parametrize("n,nb", [(1, 1), (255, 4), (256, 8), (257, 16), (3000, 16), (5000, 2)])
-@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("n,nb", [(1, 1), (1, 16), (200, 16), (255, 4), (256, 8), (257, 16), (3000, 16), (5000, 2)])
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "df64"])
 def test_spmm_random_within_bound(n, nb, mode):
+    """Random data within the rounding bound of each arithmetic, from one entry to several tile rows (nb = 16 runs
+    the ring kernels with one persistent CTA per tile-row range)."""
     import paper_1609_01689_gb300 as lob
     rng = np.random.default_rng(n * 7 + nb)
     H = random_upper(n, min(0.05, 40.0 / n), rng)
@@ -58,8 +60,8 @@ def test_spmm_random_within_bound(n, nb, mode):
     Yref = oracle.spmm(H, X)
     bound_base = oracle.spmm(abs_coo(H), np.abs(X))
     m = row_counts(H)[:, None]
-    bound = (2 * (m + 2) * U64 if mode == "fp64" else 2 * (m + 4) * U32) * bound_base + 1e-300
-    assert np.all(np.abs(Y - Yref) <= bound)
+    unit = {"fp64": 2 * (m + 2) * U64, "mixed": 2 * (m + 4) * U32, "df64": 2 * (m + 2) * 2.0 ** -46}[mode]
+    assert np.all(np.abs(Y - Yref) <= unit * bound_base + 1e-300)
 
 
 def test_spmm_unit_vectors_and_symmetry():
