@@ -369,9 +369,9 @@ __global__ void __launch_bounds__(256) k_block_apply_batch(const lob_bjob* __res
                    threadIdx.x % tpb, tpb, valid);
 }
 
-// Eq. 11 on the diagonal CSB tiles (Section 4.3: the block-diagonal preconditioner built from the
-// diagonal tiles of H, each shifted system solved by two or three FOM iterations from a zero
-// start). One CTA per diagonal tile I, 1,024 threads: the lane group g of four lanes owns in-tile
+// Eq. 11 on the diagonal CSB tiles (Sections 3.2 and 4.3: the block-diagonal preconditioner built
+// from the diagonal tiles of H, each shifted system solved by two or three FOM iterations from a
+// zero start, the iterations of all right-hand sides fused into one tile product each). One CTA per diagonal tile I, 1,024 threads: the lane group g of four lanes owns in-tile
 // row g, each lane four of the NB = 16 columns of one pass. A product with the tile uses the tile
 // store's own layout -- the row pass over the chunk's row pointers and the column pass through
 // its column-order permutation, the stored diagonal applied once -- in FP32 (footnote 5), with
