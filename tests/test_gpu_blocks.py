@@ -206,3 +206,66 @@ def test_precond_tiles_rejects_what_it_cannot_do():
     with pytest.raises(lob.LobError):
         srv.submit(M, 2, 4, 1e-8, precond=True)
     srv.close()
+
+
+def _breakdown_matrix(bp, nblk, mu, dense, seed):
+    """Block-diagonal H whose even blocks make two-step FOM break down for column 0 and whose
+    odd blocks make one-step FOM break down for column 1 (constructions and closed forms in
+    test_oracle_lobpcg_parts); columns 2-3 are random. Every block's spectrum sits at mu - 1 and
+    above, so the random columns are ordinary indefinite systems."""
+    from test_oracle_lobpcg_parts import BREAK1_A, BREAK1_X, BREAK2_A, BREAK2_X, fom_breakdown_block
+    rng = np.random.default_rng(seed)
+    n = bp * nblk
+    Hd = np.zeros((n, n))
+    R = rng.standard_normal((n, 4))
+    c2 = [1, bp // 2, bp - 2]
+    c1 = [3, bp - 1]
+    for b in range(nblk):
+        s = slice(b * bp, (b + 1) * bp)
+        B2, r2 = fom_breakdown_block(bp, mu, rng, c2, BREAK2_A, BREAK2_X, dense)
+        B1, r1 = fom_breakdown_block(bp, mu, rng, c1, BREAK1_A, BREAK1_X, dense)
+        Hd[s, s] = B2 if b % 2 == 0 else B1
+        R[s, 0] = r2 if b % 2 == 0 else rng.standard_normal(bp)
+        R[s, 1] = r1 if b % 2 == 1 else rng.standard_normal(bp)
+    # a few couplings between blocks: the preconditioner must ignore them
+    for _ in range(3 * nblk):
+        i, j = sorted(rng.integers(0, n, 2))
+        if i // bp != j // bp:
+            Hd[i, j] = Hd[j, i] = 0.25
+    iu = np.triu_indices(n)
+    keep = Hd[iu] != 0.0
+    H = oracle.Coo(n, iu[0][keep].astype(np.int64), iu[1][keep].astype(np.int64), Hd[iu][keep])
+    return H, Hd, R
+
+
+@pytest.mark.parametrize("steps", [1, 2, 3])
+@pytest.mark.parametrize("bp,dense", [(12, True), (32, False), (256, False)])
+def test_precond_fom_breakdown_matches_oracle(bp, dense, steps):
+    """The FOM breakdown path of eq. 11's Krylov solve (Sections 3.2, 4.3) on the GPU: dense
+    blocks (FOM in each block's FP32 eigenbasis) and the diagonal 256 x 256 tiles (Lanczos on the
+    sparse tile in FP32). The even blocks give column 0 an exactly singular 2 x 2 projected
+    matrix and the odd blocks give column 1 r^T A r = 0, so the FP32 pivots are rounding noise,
+    far below the 1e-4 threshold, and both sides must take the minimal-residual fallback. The
+    oracle's results there are pinned to closed forms on the CPU. Error bound: FP32 work on the
+    block, relative to the largest entry of the reference column, 8 b u32 kappa (kappa =
+    ||H~|| / min |lambda - mu|, here <= (max diagonal) / 1), plus an absolute FP32 floor of
+    b u32 ||r|| kappa for the one-step column whose exact iterate is zero."""
+    import paper_1609_01689_gb300 as lob
+    mu = 5.0
+    H, Hd, R = _breakdown_matrix(bp, 2, mu, dense, 7 * bp + steps)
+    M = lob.Matrix(H.n, H.rows, H.cols, H.vals, precond_block=bp)
+    muv = np.full(4, mu)
+    W = M.precond_apply(t(muv), t(R), solve="fom", steps=steps).cpu().numpy()
+    bounds = oracle.uniform_bounds(H.n, bp)
+    ref = oracle.block_krylov(H, bounds, muv, R, "fom", steps)
+    assert np.all(np.isfinite(W))
+    u32 = 2.0 ** -24
+    for i in range(len(bounds) - 1):
+        s = slice(bounds[i], bounds[i + 1])
+        lam = np.linalg.eigvalsh(Hd[s, s])
+        kappa = np.abs(lam).max() / np.abs(lam - mu).min()
+        for j in range(4):
+            scale = np.abs(ref[s, j]).max()
+            err = np.abs(W[s, j] - ref[s, j]).max()
+            floor = bp * u32 * kappa * np.linalg.norm(R[s, j])
+            assert err <= 8 * bp * u32 * kappa * scale + floor, (i, j, err, scale, kappa)

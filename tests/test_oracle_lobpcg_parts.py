@@ -230,3 +230,89 @@ def test_krylov_abs_is_direct_below_the_spectrum_and_spd():
         s = slice(bounds[i], bounds[i + 1])
         for j in range(2):
             assert R[s, j] @ Wa2[s, j] > 0
+
+
+# Eigenvalue offsets (from the shift) and start-vector weights in the eigenbasis for which the
+# projected 2 x 2 tridiagonal of two Lanczos steps on (A, r) is exactly singular: with
+# m_k = r^T A^k r = sum_i x_i^2 a_i^k, det T is proportional to m_1 m_3 - m_2^2, and
+# a = (-1, 1, 2), x^2 = (1/11, 1, 1) give m_1 m_3 - m_2^2 = (32/11)(96/11) - (56/11)^2 = 0 while
+# m_1 = 32/11 != 0 (the first pivot is fine).
+BREAK2_A = np.array([-1.0, 1.0, 2.0])
+BREAK2_X = np.array([1.0 / np.sqrt(11.0), 1.0, 1.0])
+# Two eigen-directions with x^2 = (1/2, 1/2) and a = (-1, 1): r^T A r = 0, the one-step pivot.
+BREAK1_A = np.array([-1.0, 1.0])
+BREAK1_X = np.array([1.0, 1.0]) / np.sqrt(2.0)
+
+
+def fom_breakdown_block(bp, mu, rng, coords, a, x, dense=False):
+    """A bp x bp symmetric block B and a vector r such that A = B - mu I restricted to the
+    Krylov space of r has the spectrum mu + a on the eigen-directions that r touches, with r's
+    weights x. The other eigenvalues are mu + 3 + 0.5 i (well away). With dense=False only the
+    rows in `coords` are coupled (a small rotation), so the block is sparse; with dense=True
+    the whole block is rotated by a random orthogonal matrix."""
+    k = len(coords)
+    d = mu + 3.0 + 0.5 * np.arange(bp)
+    d[coords] = mu + a
+    if dense:
+        Q = np.linalg.qr(rng.standard_normal((bp, bp)))[0]
+        B = (Q * d) @ Q.T
+        r = Q[:, coords] @ x
+    else:
+        Qk = np.linalg.qr(rng.standard_normal((k, k)))[0]
+        B = np.diag(d)
+        B[np.ix_(coords, coords)] = (Qk * (mu + a)) @ Qk.T
+        r = np.zeros(bp)
+        r[coords] = Qk @ x
+    return (B + B.T) / 2, r
+
+
+@pytest.mark.parametrize("dense", [False, True])
+def test_krylov_fom_breakdown_falls_back_to_minimal_residual(dense):
+    """The FOM breakdown rule of the oracle (a pivot of the projected tridiagonal below 1e-4 of
+    its largest entry, Sections 3.2 and 4.3 leave the case open) made to fire, with results fixed
+    by the mathematics and not by the oracle's own algorithm:
+      - two steps on a vector whose 2 x 2 projected matrix is singular: FOM's iterate does not
+        exist, and minimal residual stagnates (its residual cannot fall where FOM is undefined,
+        for a symmetric A), so the fallback must return the one-step minimal-residual iterate
+        (r^T A r / ||A r||^2) r -- the same vector that the 2 x 2 least-squares closed form over
+        span{r, A r} gives;
+      - three steps on the same vector: r lies in a 3-dimensional invariant subspace, so the
+        minimal-residual iterate is the exact solve A^{-1} r, although the unpivoted elimination
+        of the 3 x 3 tridiagonal meets the zero second pivot;
+      - one step on it: the pivot r^T A r / r^T r is fine, and FOM gives (r^T r / r^T A r) r;
+      - one step on a vector with r^T A r = 0: the fallback's iterate is 0."""
+    rng = np.random.default_rng(90 + dense)
+    bp, mu = 12, 5.0
+    B, r2 = fom_breakdown_block(bp, mu, rng, [1, 4, 9], BREAK2_A, BREAK2_X, dense)
+    B1, r1 = fom_breakdown_block(bp, mu, rng, [2, 7], BREAK1_A, BREAK1_X, dense)
+    n = 2 * bp
+    Hd = np.zeros((n, n))
+    Hd[:bp, :bp] = B
+    Hd[bp:, bp:] = B1
+    iu = np.triu_indices(n)
+    keep = Hd[iu] != 0.0
+    H = oracle.Coo(n, iu[0][keep].astype(np.int64), iu[1][keep].astype(np.int64), Hd[iu][keep])
+    R = np.zeros((n, 1))
+    R[:bp, 0] = r2
+    R[bp:, 0] = r1
+    bounds = oracle.uniform_bounds(n, bp)
+    A = B - mu * np.eye(bp)
+    A1 = B1 - mu * np.eye(bp)
+    Ar = A @ r2
+    m = [r2 @ np.linalg.matrix_power(A, k) @ r2 for k in range(5)]
+    assert abs(m[1] * m[3] - m[2] ** 2) <= 1e-12 * m[2] ** 2 and m[1] > 1.0
+    c = np.linalg.solve(np.array([[m[2], m[3]], [m[3], m[4]]]), np.array([m[1], m[2]]))
+    ls2 = c[0] * r2 + c[1] * Ar
+    mr1 = (r2 @ Ar) / (Ar @ Ar) * r2
+    np.testing.assert_allclose(ls2, mr1, rtol=1e-10, atol=1e-12)
+    tol = 1e-10 * np.linalg.norm(r2)
+    for method in ("fom", "minres"):
+        W2 = oracle.block_krylov(H, bounds, [mu], R, method, 2)[:, 0]
+        assert np.all(np.isfinite(W2))
+        assert np.abs(W2[:bp] - mr1).max() <= tol
+        W3 = oracle.block_krylov(H, bounds, [mu], R, method, 3)[:, 0]
+        assert np.abs(W3[:bp] - np.linalg.solve(A, r2)).max() <= tol
+    W1 = oracle.block_krylov(H, bounds, [mu], R, "fom", 1)[:, 0]
+    np.testing.assert_allclose(W1[:bp], (r2 @ r2) / (r2 @ Ar) * r2, rtol=1e-11, atol=0)
+    assert abs(r1 @ A1 @ r1) <= 1e-14
+    assert np.abs(W1[bp:]).max() <= 1e-12 * np.linalg.norm(r1)
