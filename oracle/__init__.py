@@ -43,6 +43,9 @@ def lib():
     if _lib is None:
         L = ctypes.CDLL(build())
         L.orc_spmm.argtypes = [_I, _I, _P, _P, _P, _I, _P, _P]
+        L.orc_spmm_csr.argtypes = [_I, _P, _P, _P, _I, _P, _P]
+        L.orc_lanczos_csr.argtypes = [_I, _P, _P, _P, _I, _D, _D, _I, ctypes.c_uint64, _P, _P, _P]
+        L.orc_lanczos_csr.restype = ctypes.c_int
         L.orc_dense.argtypes = [_I, _I, _P, _P, _P, _P]
         L.orc_norm_inf.argtypes = [_I, _I, _P, _P, _P]
         L.orc_norm_inf.restype = _D
@@ -150,6 +153,49 @@ def lanczos(H: Coo, k: int, tol: float, normH: float | None = None, max_steps: i
     steps = ctypes.c_int64(0)
     st = lib().orc_lanczos(*H.args(), k, tol, normH, max_steps, seed, lam.ctypes.data, X.ctypes.data,
                            ctypes.byref(steps))
+    if st < 0:
+        raise RuntimeError(f"Lanczos failed ({st})")
+    return lam, X, int(steps.value), st == 0
+
+
+class Csr:
+    """Upper triangle (row <= col) incl. diagonal in CSR form: rowptr (n+1, int64), col (int32),
+    val (float64), rows in order and columns in order within each row."""
+
+    def __init__(self, n, rowptr, col, val):
+        self.n = int(n)
+        self.rowptr = _i64(rowptr)
+        self.col = np.ascontiguousarray(col, dtype=np.int32)
+        self.val = _f64(val)
+        assert self.rowptr.shape == (self.n + 1,) and len(self.col) == len(self.val) == int(self.rowptr[-1])
+
+    @staticmethod
+    def from_sorted_coo(n, rows, cols, vals):
+        """From a COO sorted by (row, col) (the generator's order)."""
+        rowptr = np.zeros(n + 1, dtype=np.int64)
+        np.cumsum(np.bincount(rows, minlength=n), out=rowptr[1:])
+        return Csr(n, rowptr, cols.astype(np.int32), vals)
+
+    def args(self):
+        return (self.n, self.rowptr.ctypes.data, self.col.ctypes.data, self.val.ctypes.data)
+
+
+def spmm_csr(H: Csr, X: np.ndarray) -> np.ndarray:
+    """spmm on the CSR form (orc_spmm_csr)."""
+    X = _f64(X)
+    nb = 1 if X.ndim == 1 else X.shape[1]
+    Y = np.empty_like(X)
+    lib().orc_spmm_csr(*H.args(), nb, X.ctypes.data, Y.ctypes.data)
+    return Y
+
+
+def lanczos_csr(H: Csr, k: int, tol: float, normH: float, max_steps: int = 2000, seed: int = 7):
+    """lanczos on the CSR form (orc_lanczos_csr). Returns (lam, X, steps, converged)."""
+    lam = np.zeros(k, dtype=np.float64)
+    X = np.zeros((H.n, k), dtype=np.float64)
+    steps = ctypes.c_int64(0)
+    st = lib().orc_lanczos_csr(*H.args(), k, tol, normH, max_steps, seed, lam.ctypes.data, X.ctypes.data,
+                               ctypes.byref(steps))
     if st < 0:
         raise RuntimeError(f"Lanczos failed ({st})")
     return lam, X, int(steps.value), st == 0

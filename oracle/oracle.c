@@ -10,9 +10,14 @@
  * directly, by two independent dense methods and a Lanczos method for large n:
  *   orc_spmm          Y = H X from the stored triangle (Section 4.1: U_i = H_ij W_j, U_j = H_ij^T W_i)
  *   orc_dense         dense expansion of the stored triangle
- *   orc_syev          Householder tridiagonalisation + implicit-shift QL (textbook, all eigenpairs)
+ *   orc_syev          Householder tridiagonalisation + implicit-shift QL (the QL algorithm of
+ *                     Bowdler, Martin, Reinsch and Wilkinson, 1968; all eigenpairs)
  *   orc_tridiag_eig   the QL part alone, for a symmetric tridiagonal matrix
- *   orc_jacobi        cyclic Jacobi rotations (a second, independent dense method)
+ *   orc_jacobi        the cyclic-by-row Jacobi method (Jacobi 1846; Forsythe and Henrici 1960),
+ *                     a second, independent dense method
+ *   orc_spmm_csr, orc_lanczos_csr  the same on the triangle in CSR form with 32-bit columns
+ *                     (for matrices of ~1e9 entries, whose 64-bit COO would not fit beside the
+ *                     Lanczos basis in host memory)
  *   orc_lanczos       Lanczos with full reorthogonalisation (the legacy solver, Section 3 and
  *                     the footnote to Table 3), Ritz-residual stopping test every 10 steps
  *   orc_tiles         CSB-style tile store: tiles by (tile row, tile col), COO inside each tile
@@ -45,6 +50,23 @@ void orc_spmm(int64_t n, int64_t nnz, const int64_t* row, const int64_t* col, co
     if (i != j)
       for (int64_t c = 0; c < nb; c++) Y[j * nb + c] += v * X[i * nb + c];
   }
+}
+
+/* The same product with the stored triangle in CSR form (rows in order, each row's columns in
+ * order, 32-bit column indices): rowptr[n+1], col[rowptr[n]], val[rowptr[n]]. Visits the entries
+ * in the order of a COO sorted by (row, col), so it matches orc_spmm on such a COO exactly. It
+ * exists for matrices whose 64-bit COO would not fit beside the Lanczos basis in host memory. */
+void orc_spmm_csr(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, int64_t nb,
+                  const double* X, double* Y) {
+  memset(Y, 0, (size_t)(n * nb) * sizeof(double));
+  for (int64_t i = 0; i < n; i++)
+    for (int64_t t = rowptr[i]; t < rowptr[i + 1]; t++) {
+      const int64_t j = col[t];
+      const double v = val[t];
+      for (int64_t c = 0; c < nb; c++) Y[i * nb + c] += v * X[j * nb + c];
+      if (i != j)
+        for (int64_t c = 0; c < nb; c++) Y[j * nb + c] += v * X[i * nb + c];
+    }
 }
 
 /* Dense n x n (row-major) expansion of the stored triangle. */
@@ -86,8 +108,9 @@ static void sort_eig(int64_t n, double* w, double* Z, int64_t ldz, int64_t nrows
   }
 }
 
-/* Implicit-shift QL on the symmetric tridiagonal matrix with diagonal d[0..m-1] and
- * off-diagonal e[0..m-2]. Each sweep chases a bulge from the bottom of the unreduced block
+/* Implicit-shift QL (Bowdler, Martin, Reinsch and Wilkinson, "The QR and QL algorithms for
+ * symmetric matrices", Numer. Math. 11, 1968) on the symmetric tridiagonal matrix with diagonal
+ * d[0..m-1] and off-diagonal e[0..m-2]. Each sweep chases a bulge from the bottom of the unreduced block
  * upward with Givens rotations, shifted by the eigenvalue of the leading 2x2 closer to d[l].
  * The rotations are applied to the ROWS of Zt (m rows of length nrows, leading dimension ldz):
  * start from the identity to get T's eigenvectors, or from Q^T (Householder basis) to get those
@@ -226,7 +249,7 @@ int orc_syev(int64_t n, double* A, double* w) {
   return st;
 }
 
-/* Cyclic-by-row Jacobi: rotations J(p,q,theta) zero a_pq one pair at a time, A <- J^T A J, until
+/* The cyclic-by-row Jacobi method (Forsythe and Henrici, Trans. AMS 94, 1960): rotations J(p,q,theta) zero a_pq one pair at a time, A <- J^T A J, until
  * the off-diagonal Frobenius norm is below 1e-15 of the whole (or max_sweeps). A (row-major) is
  * destroyed; w gets the eigenvalues ascending and V (n x n) the eigenvectors as columns.
  * Returns the number of sweeps used, or -1 if not converged. */
@@ -286,8 +309,38 @@ static double orc_unif(uint64_t seed, uint64_t i) {
  * most tol * normH for the k smallest Ritz values. lam gets those Ritz values and X (n x k,
  * row-major) the Ritz vectors. Returns 0 when converged, 1 if max_steps was reached,
  * -1 on QL failure, -2 on allocation failure. *steps gets the number of Lanczos steps. */
+/* The matrix a Lanczos run multiplies by: the stored triangle as COO or as CSR. */
+typedef struct {
+  int64_t n, nnz;
+  const int64_t *row, *col, *rowptr;
+  const int32_t* col32;
+  const double* val;
+} orc_op;
+
+static void op_apply(const orc_op* A, const double* x, double* y) {
+  if (A->rowptr) orc_spmm_csr(A->n, A->rowptr, A->col32, A->val, 1, x, y);
+  else orc_spmm(A->n, A->nnz, A->row, A->col, A->val, 1, x, y);
+}
+
+static int lanczos_run(const orc_op* A, int64_t k, double tol, double normH, int64_t max_steps, uint64_t seed,
+                       double* lam, double* X, int64_t* steps);
+
 int orc_lanczos(int64_t n, int64_t nnz, const int64_t* row, const int64_t* col, const double* val, int64_t k,
                 double tol, double normH, int64_t max_steps, uint64_t seed, double* lam, double* X, int64_t* steps) {
+  const orc_op A = {n, nnz, row, col, NULL, NULL, val};
+  return lanczos_run(&A, k, tol, normH, max_steps, seed, lam, X, steps);
+}
+
+/* orc_lanczos on the CSR form of the stored triangle (see orc_spmm_csr). */
+int orc_lanczos_csr(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val, int64_t k, double tol,
+                    double normH, int64_t max_steps, uint64_t seed, double* lam, double* X, int64_t* steps) {
+  const orc_op A = {n, rowptr[n], NULL, NULL, rowptr, col, val};
+  return lanczos_run(&A, k, tol, normH, max_steps, seed, lam, X, steps);
+}
+
+static int lanczos_run(const orc_op* A, int64_t k, double tol, double normH, int64_t max_steps, uint64_t seed,
+                       double* lam, double* X, int64_t* steps) {
+  const int64_t n = A->n;
   if (max_steps > n) max_steps = n;
   double* Qv = (double*)malloc((size_t)(n * max_steps) * sizeof(double)); /* vector j at Qv + j*n */
   double* w = (double*)malloc((size_t)n * sizeof(double));
@@ -308,7 +361,7 @@ int orc_lanczos(int64_t n, int64_t nnz, const int64_t* row, const int64_t* col, 
   int64_t m = 0;
   for (int64_t j = 0; j < max_steps; j++) {
     double* qj = Qv + j * n;
-    orc_spmm(n, nnz, row, col, val, 1, qj, w);
+    op_apply(A, qj, w);
     double a = 0.0;
     for (int64_t i = 0; i < n; i++) a += qj[i] * w[i];
     alpha[j] = a;

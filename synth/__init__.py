@@ -31,6 +31,8 @@ class Layout(ctypes.Structure):
         ("nu", ctypes.c_int32),
         ("w_min", ctypes.c_int32),
         ("w_div", ctypes.c_int32),
+        ("draw_pct", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
         ("seed", ctypes.c_uint64),
         ("start", ctypes.c_int64 * (MAX_LEVELS + 1)),
     ]
@@ -106,11 +108,13 @@ def interp_levels(n: int) -> int:
     return int(min(14, max(6, round(q))))
 
 
-def layout(n: int, Q: int, nu: int, seed: int, w_min: int = 64, w_div: int = 0) -> Layout:
+def layout(n: int, Q: int, nu: int, seed: int, w_min: int = 64, w_div: int = 0, draw_pct: int = 0) -> Layout:
+    """draw_pct: draws per row in percent of nu (0 = 60)."""
     L = Layout()
     rc = _host_lib().syn_layout_init(ctypes.byref(L), n, Q, nu, w_min, w_div, seed)
-    if rc != 0:
+    if rc != 0 or draw_pct < 0:
         raise ValueError(f"bad generator parameters n={n} Q={Q} nu={nu} w_min={w_min} w_div={w_div}")
+    L.draw_pct = draw_pct
     return L
 
 
@@ -122,8 +126,10 @@ def candidate_cap(L: Layout) -> int:
     return int(_host_lib().syn_candidate_cap(ctypes.byref(L)))
 
 
-def generate(L: Layout):
-    """Host COO (rows, cols, vals) of the upper triangle incl. diagonal, sorted by (row, col)."""
+def generate(L: Layout, copy: bool = True):
+    """Host COO (rows, cols, vals) of the upper triangle incl. diagonal, sorted by (row, col).
+    copy=False returns views into the generator's candidate-sized buffers (no second copy of a
+    large matrix; the buffers' unused tails stay allocated)."""
     cap = candidate_cap(L)
     rows = np.empty(cap, dtype=np.int64)
     cols = np.empty(cap, dtype=np.int64)
@@ -131,6 +137,8 @@ def generate(L: Layout):
     nnz = _host_lib().syn_generate_host(ctypes.byref(L), rows.ctypes.data, cols.ctypes.data, vals.ctypes.data, cap)
     if nnz < 0:
         raise MemoryError(f"host generator failed ({nnz})")
+    if not copy:
+        return rows[:nnz], cols[:nnz], vals[:nnz]
     return rows[:nnz].copy(), cols[:nnz].copy(), vals[:nnz].copy()
 
 
@@ -155,11 +163,13 @@ def generate_device(L: Layout, device: str = "cuda", stream: int = 0):
 CONFIGS = {
     "c1": dict(n=1536, Q=6, nu=30, k=5, nb=8, bp=32, seed=1),
     "c2": dict(n=500_000, Q=10, nu=200, k=8, nb=16, bp=32, seed=1),
-    "c3": dict(n=8_000_000, Q=14, nu=300, k=10, nb=16, bp=64, seed=1),
+    # 0.7 nu draws per row: at nu = 300 more draws coincide inside the +-64 bands, and 0.6 nu would
+    # leave 269 entries per full row (1.08e9 stored) instead of ~300 (1.20e9)
+    "c3": dict(n=8_000_000, Q=14, nu=300, k=10, nb=16, bp=64, seed=1, draw_pct=70),
 }
 
 
 def config_layout(name: str, seed: int | None = None, **over) -> Layout:
     c = dict(CONFIGS[name])
     c.update(over)
-    return layout(c["n"], c["Q"], c["nu"], c["seed"] if seed is None else seed)
+    return layout(c["n"], c["Q"], c["nu"], c["seed"] if seed is None else seed, draw_pct=c.get("draw_pct", 0))

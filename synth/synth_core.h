@@ -11,8 +11,9 @@
  * truncation levels. The paper's matrices themselves are not available. The recipe:
  *   levels q = 0..Q, level sizes proportional to 2.2^q (largest-remainder rounding);
  *   diagonal  h_ii = 10*q_i + U(-1,1);
- *   each row draws m = ceil(0.6*nu) partners in levels q-2..q+2, centred on the row's
- *   relative position inside its level, within a half-width w (band);
+ *   each row draws m = ceil(f*nu) partners in levels q-2..q+2, centred on the row's
+ *   relative position inside its level, within a half-width w (band); f = 0.6 unless the
+ *   layout sets it (draw_pct), chosen so the symmetric union holds about nu per full row;
  *   off-diagonal value 0.3*(sum of 12 uniforms - 6)  (Irwin-Hall, mean 0, var 0.09),
  *   a function of the unordered pair so that the symmetric union is consistent.
  * All arithmetic that decides a structure is integer. The values use exact integer
@@ -54,6 +55,8 @@ typedef struct {
   int32_t nu;         /* target nonzeros per full row (both triangles) */
   int32_t w_min;      /* band half-width floor */
   int32_t w_div;      /* if > 0, half-width = max(w_min, ceil(c_q / w_div)) */
+  int32_t draw_pct;   /* draws per row in percent of nu; 0 = 60 */
+  int32_t reserved;
   uint64_t seed;
   int64_t start[SYN_MAX_LEVELS + 1]; /* level q occupies rows [start[q], start[q+1]) */
 } syn_layout;
@@ -74,9 +77,14 @@ SYN_HD int64_t syn_halfwidth(const syn_layout* L, int q) {
   return w;
 }
 
-/* ceil(0.6*nu) draws per row: the symmetric union with duplicates merged then holds about nu
- * entries per full row (half as many draws would leave it ~15% short). */
-SYN_HD int64_t syn_draws(const syn_layout* L) { return (6 * (int64_t)L->nu + 9) / 10; }
+/* ceil(f*nu) draws per row, f = draw_pct / 100 (default 0.6): the symmetric union with
+ * duplicates merged then holds about nu entries per full row. Half as many draws would leave it
+ * ~15% short at nu = 200; with more draws per band slot (larger nu) more of them coincide, and the
+ * layout raises f to keep the row count at nu. */
+SYN_HD int64_t syn_draws(const syn_layout* L) {
+  const int64_t pct = L->draw_pct > 0 ? L->draw_pct : 60;
+  return (pct * (int64_t)L->nu + 99) / 100;
+}
 
 /* floor(v / 2^32) for signed v, without relying on arithmetic right shift. */
 SYN_HD int64_t syn_floor_div_2p32(int64_t v) {

@@ -55,9 +55,10 @@ static void radix_sort_u64(uint64_t* a, uint64_t* tmp, int64_t m, int bits) {
 int64_t syn_generate_host(const syn_layout* L, int64_t* rows, int64_t* cols, double* vals, int64_t cap) {
   int64_t n = L->n, m = syn_draws_per_row(L);
   if (cap < syn_candidate_cap(L)) return -1;
-  uint64_t* keys = (uint64_t*)malloc((size_t)cap * sizeof(uint64_t));
-  uint64_t* tmp = (uint64_t*)malloc((size_t)cap * sizeof(uint64_t));
-  if (!keys || !tmp) { free(keys); free(tmp); return -2; }
+  /* The candidate keys and the sort's scratch live in the caller's rows and cols arrays (both
+   * cap entries of 8 bytes), so a large matrix needs no second copy of its size. */
+  uint64_t* keys = (uint64_t*)rows;
+  uint64_t* tmp = (uint64_t*)cols;
   int64_t k = 0;
   for (int64_t i = 0; i < n; i++) {
     keys[k++] = ((uint64_t)i << 32) | (uint64_t)i;
@@ -71,14 +72,17 @@ int64_t syn_generate_host(const syn_layout* L, int64_t* rows, int64_t* cols, dou
   int bits = 0;
   while (bits < 64 && ((((uint64_t)(n - 1) << 32) | (uint64_t)(n - 1)) >> bits) != 0) bits += 8;
   radix_sort_u64(keys, tmp, k, bits);
+  /* unique keys -> (row, col, value); entry nnz is written after key t >= nnz has been read */
   int64_t nnz = 0;
+  uint64_t prev = 0;
   for (int64_t t = 0; t < k; t++) {
-    if (t > 0 && keys[t] == keys[t - 1]) continue;
-    int64_t i = (int64_t)(keys[t] >> 32), j = (int64_t)(keys[t] & 0xFFFFFFFFull);
+    const uint64_t key = keys[t];
+    if (t > 0 && key == prev) continue;
+    prev = key;
+    int64_t i = (int64_t)(key >> 32), j = (int64_t)(key & 0xFFFFFFFFull);
     rows[nnz] = i; cols[nnz] = j;
     vals[nnz] = (i == j) ? syn_diag(L, i) : syn_offdiag(L->seed, i, j);
     nnz++;
   }
-  free(keys); free(tmp);
   return nnz;
 }
