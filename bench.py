@@ -102,8 +102,8 @@ class ClockSampler:
 
 
 # DRAM bytes (read + write) of one FP32-value SpMM launch (k_spmm_ring<16>) on the n = 500,000
-# workload, from an ncu capture of this bench's own kernel mode (profiles/spmm_mixed_c2_nb16.md).
-# Valid for the kernel as captured; reset to None when the kernel changes.
+# workload, from an ncu capture of this bench's own kernel mode (the profile summary of that kernel
+# and workload). Valid for the kernel as captured; reset to None when the kernel changes.
 SPMM_TRAFFIC = {"c2": 762782464 + 147569408}
 
 

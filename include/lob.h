@@ -61,7 +61,11 @@ typedef struct {
                             solved by FOM or minimal-residual steps on the tile store at each
                             apply (Section 4.3; needs FP32 values; lob_solve only, not the
                             server); 0 = none */
-  int32_t reserved;
+  int32_t wait_log2;     /* log2 of the SM clocks that any wait inside the persistent SpMM kernels
+                            may take before the kernel gives up (1..40; 0 = 32, about 2 s). A
+                            product that gives up leaves Y invalid and is reported by lob_check,
+                            lob_solve or the server (LOB_ERR_CUDA); the context stays usable.
+                            Small values exist to test that path. */
   void* stream;          /* cudaStream_t for the build */
 } lob_create_opts;
 
@@ -113,8 +117,16 @@ int lob_export_perm(const lob_matrix* m, uint16_t* perm);
 
 /* Y = H X (Section 4.1: U_i = H_ij W_j and U_j = H_ij^T W_i for every stored tile, here in one
  * pass over the tiles). X, Y: device, n x nb, row-major FP64, must not overlap. 1 <= nb <= 64.
- * The requested value copy must have been kept at create. Errors: LOB_ERR_ARG, LOB_ERR_CUDA. */
+ * The requested value copy must have been kept at create. Asynchronous: a kernel that gives up on
+ * a bounded wait (lob_create_opts.wait_log2) cannot be seen here; lob_check reports it. Errors:
+ * LOB_ERR_ARG, LOB_ERR_CUDA (a launch failed). */
 int lob_spmm(lob_matrix* m, int32_t mode, const double* X, double* Y, int32_t nb, void* stream);
+
+/* Synchronise `stream` and report whether any SpMM kernel on m gave up on a bounded wait since
+ * the last check (LOB_ERR_CUDA; the products it took part in are not valid; the flag is then
+ * cleared) or not (LOB_OK). The flag belongs to the matrix: products of one matrix running on
+ * several streams share it. lob_solve checks it itself. Errors: LOB_ERR_ARG, LOB_ERR_CUDA. */
+int lob_check(lob_matrix* m, void* stream);
 
 /* ---- the pieces of one LOBPCG iteration, each exposed for testing and reuse ---- */
 
@@ -170,16 +182,26 @@ int lob_rayleigh_ritz(int32_t m, const double* G, const double* M, double* theta
  * file-scope device array sized for m <= 192 (three 192 x 192 FP64 matrices, 884,736 bytes),
  * held by every GPU that loads the library until the process exits; m outside [1, 192]
  * returns LOB_ERR_ARG. The first call on each device looks up the array's device address
- * (with that device current); make that first call before any stream capture. All calls share
- * the array: each call overwrites it completely before reading it, and calls that overlap on
- * the GPU (other streams or host threads using the same device) race on it. */
+ * (with that device current) and keeps it for the rest of the process; make that first call
+ * before any stream capture. The kept addresses cover device ordinals 0..63 (a larger ordinal
+ * returns LOB_ERR_ARG), and a cudaDeviceReset on a device leaves its kept address stale: do not
+ * call this entry point on a device after resetting it. All calls share the array: each call
+ * overwrites it completely before reading it, and calls that overlap on the GPU (other streams
+ * or host threads using the same device) race on it. */
 int lob_rayleigh_ritz_noalloc(int32_t m, const double* G, const double* M, double* theta, double* C,
                               int32_t* info, int32_t mode, void* stream);
 
 /* ---- the solver (Algorithm 1) ---- */
 
 #define LOB_MODE_FP64 0  /* every product in FP64 (the plain solver) */
-#define LOB_MODE_MIXED 1 /* FP32-value SpMM, FP64-class block products, then FP64 refinement */
+#define LOB_MODE_MIXED 1 /* FP32-value SpMM with FP64 sums, FP64-class block products, FP64
+                            Cholesky-QR factors and Rayleigh-Ritz solves, then refinement
+                            iterations with the FP64-value SpMM (Section 4.4, footnote 5) */
+
+/* Arithmetic choices inside LOB_MODE_MIXED (lob_solve_opts.rr_arith / refine_arith). */
+#define LOB_ARITH_FP64 0 /* native FP64 (the default) */
+#define LOB_ARITH_DF 1   /* double-float on the FP32 pipes (~48-bit significands): faster on this
+                            GPU, whose FP64 rate is a small fraction of its FP32 rate */
 
 typedef struct {
   int32_t mode;            /* LOB_MODE_* */
@@ -209,6 +231,10 @@ typedef struct {
                               run, in [0, 1); 0 = 1e-3. A nested guess whose coupling
                               ||H_21|| / ||H|| is small pays off only with a tighter value.
                               lob_solve only */
+  int32_t rr_arith;        /* MIXED: LOB_ARITH_* of the small dense solves -- the Cholesky factor of
+                              Cholesky-QR and the 3nb x 3nb Rayleigh-Ritz eigenproblem (eq. 9) */
+  int32_t refine_arith;    /* MIXED: LOB_ARITH_* of the refinement phase's SpMM (FP64 values, or
+                              double-float values and products, LOB_SPMM_DF64) */
 } lob_solve_opts;
 
 typedef struct {

@@ -36,6 +36,7 @@ MODE_FP64, MODE_MIXED = 0, 1
 PSOLVE_FOM, PSOLVE_DIRECT, PSOLVE_MINRES, PSOLVE_ABS = 0, 1, 2, 3
 _PSOLVE = {"fom": 0, "direct": 1, "minres": 2, "abs": 3, 0: 0, 1: 1, 2: 2, 3: 3}
 _MODES = {"fp64": 0, "mixed": 1, "df64": 2, 0: 0, 1: 1, 2: 2}
+_ARITH = {"fp64": 0, "df": 1, 0: 0, 1: 1}
 
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -48,7 +49,7 @@ class Coo(ctypes.Structure):
 
 
 class CreateOpts(ctypes.Structure):
-    _fields_ = [("tile", _I32), ("values", _I32), ("precond_block", _I32), ("reserved", _I32), ("stream", _P)]
+    _fields_ = [("tile", _I32), ("values", _I32), ("precond_block", _I32), ("wait_log2", _I32), ("stream", _P)]
 
 
 class MatrixInfo(ctypes.Structure):
@@ -61,7 +62,7 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("mode", _I32), ("precond", _I32), ("max_iter", _I32), ("refine_iter", _I32), ("norm_H", _D),
                 ("n_small", _I64), ("seed", ctypes.c_uint64), ("precond_shift", _I32), ("precond_solve", _I32),
                 ("precond_steps", _I32), ("verbose", _I32), ("mixed_tol", _D), ("stream", _P),
-                ("n_small_inner", _I64), ("guess_tol", _D)]
+                ("n_small_inner", _I64), ("guess_tol", _D), ("rr_arith", _I32), ("refine_arith", _I32)]
 
 
 class Stats(ctypes.Structure):
@@ -131,6 +132,7 @@ def _load():
     L.lob_export_tiles.argtypes = [_P, _P, _P, _P, _P, _P, _P]
     L.lob_export_perm.argtypes = [_P, _P]
     L.lob_spmm.argtypes = [_P, _I32, _P, _P, _I32, _P]
+    L.lob_check.argtypes = [_P, _P]
     L.lob_gram.argtypes = [_I64, _I32, _P, _I32, _I32, _P, _I32, _P, _I32, _P]
     L.lob_lincomb.argtypes = [_I64, _I32, _P, _I32, _I32, _P, _P, _I32, _I32, _P]
     L.lob_precond_apply.argtypes = [_P, _P, _P, _P, _I32, _I32, _I32, _P]
@@ -151,7 +153,7 @@ def _load():
     L.lob_strerror.argtypes = [ctypes.c_int]
     L.lob_strerror.restype = ctypes.c_char_p
     for f in ("lob_create", "lob_destroy", "lob_matrix_info_get", "lob_export_tiles", "lob_export_perm", "lob_spmm",
-              "lob_gram",
+              "lob_check", "lob_gram",
               "lob_lincomb", "lob_precond_apply", "lob_rayleigh_ritz", "lob_solve", "lob_spmm_batch", "lob_lanczos",
               "lob_server_create", "lob_server_submit", "lob_server_progress", "lob_server_poll",
               "lob_server_stats_get", "lob_server_destroy"):
@@ -212,7 +214,7 @@ def _dev_f64(x):
 class Matrix:
     """Device tile store of a symmetric H given by its upper triangle (lob_create)."""
 
-    def __init__(self, n, rows, cols, vals, precond_block=0, values=VALUES_BOTH):
+    def __init__(self, n, rows, cols, vals, precond_block=0, values=VALUES_BOTH, wait_log2=0):
         torch = _torch()
         self._keep = []
         if isinstance(rows, np.ndarray):
@@ -227,7 +229,7 @@ class Matrix:
             v = vals.to(device="cuda", dtype=torch.float64).contiguous()
             coo = Coo(n, r.numel(), r.data_ptr(), c.data_ptr(), v.data_ptr(), 1)
             self._keep += [r, c, v]
-        opts = CreateOpts(0, values, precond_block, 0, _stream())
+        opts = CreateOpts(0, values, precond_block, wait_log2, _stream())
         h = _P()
         _check(lib().lob_create(ctypes.byref(coo), ctypes.byref(opts), ctypes.byref(h)), "lob_create")
         self._h = h
@@ -281,6 +283,10 @@ class Matrix:
         _check(lib().lob_spmm(self._h, _MODES[mode], X.data_ptr(), Y.data_ptr(), nb, _stream()), "lob_spmm")
         return Y
 
+    def check(self):
+        """Raise LobError if an SpMM kernel on this matrix gave up on a bounded wait (lob_check)."""
+        _check(lib().lob_check(self._h, _stream()), "lob_check")
+
     def precond_apply(self, mu, R, solve="direct", steps=3):
         """Approximate solves of eq. 11 per block and column (lob_precond_apply)."""
         R = _dev_f64(R)
@@ -292,7 +298,7 @@ class Matrix:
 
     def solve(self, k, nb, tol, X0=None, mode="fp64", precond=False, n_small=0, max_iter=0, refine_iter=0,
               seed=1, precond_shift=0, mixed_tol=0.0, norm_H=0.0, X_out=None, precond_solve="fom", precond_steps=3,
-              stats=True, n_small_inner=0, guess_tol=0.0):
+              stats=True, n_small_inner=0, guess_tol=0.0, rr_arith="fp64", refine_arith="fp64"):
         """k smallest eigenpairs (lob_solve). Returns (lam, X, stats, status). stats=False passes no
         stats struct: the solver then keeps no phase timers and replays its stages as CUDA graphs."""
         torch = _torch()
@@ -301,7 +307,8 @@ class Matrix:
         lam = np.zeros(k, np.float64)
         st = Stats()
         o = SolveOpts(_MODES[mode], int(bool(precond)), max_iter, refine_iter, norm_H, n_small, seed, precond_shift,
-                      _PSOLVE[precond_solve], precond_steps, 0, mixed_tol, _stream(), n_small_inner, guess_tol)
+                      _PSOLVE[precond_solve], precond_steps, 0, mixed_tol, _stream(), n_small_inner, guess_tol,
+                      _ARITH[rr_arith], _ARITH[refine_arith])
         rc = lib().lob_solve(self._h, k, nb, tol, x0.data_ptr() if x0 is not None else None, ctypes.byref(o),
                              lam.ctypes.data, X.data_ptr(), ctypes.byref(st) if stats else None)
         if rc not in (LOB_OK, LOB_ERR_NOCONV):
@@ -355,15 +362,28 @@ def rayleigh_ritz(G, M, mode="fp64"):
     return theta, C
 
 
+def _need(x, name, shape, dtype):
+    """Reject (never copy) a tensor the no-allocation entry point cannot take as it is."""
+    if not (hasattr(x, "is_cuda") and x.is_cuda and x.dtype == dtype and tuple(x.shape) == shape
+            and x.is_contiguous()):
+        raise ValueError(f"{name}: need a contiguous {dtype} CUDA tensor of shape {shape}")
+
+
 def rayleigh_ritz_noalloc(G, M, mode="fp64", theta=None, C=None, info=None):
     """rayleigh_ritz through lob_rayleigh_ritz_noalloc: the library allocates no device memory
     (its workspace is a fixed array for m <= 192). The caller may pass preallocated output
-    tensors; G and M must already be contiguous FP64 device tensors."""
+    tensors; G and M must already be square, contiguous FP64 device tensors. Inputs that do not
+    fit are rejected with ValueError rather than copied, so the call itself allocates nothing."""
     torch = _torch()
     m = G.shape[0]
+    _need(G, "G", (m, m), torch.float64)
+    _need(M, "M", (m, m), torch.float64)
     theta = theta if theta is not None else torch.empty(m, dtype=torch.float64, device="cuda")
     C = C if C is not None else torch.empty((m, m), dtype=torch.float64, device="cuda")
     info = info if info is not None else torch.zeros(1, dtype=torch.int32, device="cuda")
+    _need(theta, "theta", (m,), torch.float64)
+    _need(C, "C", (m, m), torch.float64)
+    _need(info, "info", (1,), torch.int32)
     _check(lib().lob_rayleigh_ritz_noalloc(m, G.data_ptr(), M.data_ptr(), theta.data_ptr(), C.data_ptr(),
                                            info.data_ptr(), _MODES[mode], _stream()), "lob_rayleigh_ritz_noalloc")
     if int(info.item()) != 0:
@@ -403,9 +423,11 @@ class Server:
         self._keep = {}
 
     def submit(self, matrix, k, nb, tol, mode="mixed", precond=False, n_small=0, max_iter=0, refine_iter=0, seed=1,
-               precond_shift=0, mixed_tol=0.0, X_out=None, precond_solve="fom", precond_steps=3):
+               precond_shift=0, mixed_tol=0.0, X_out=None, precond_solve="fom", precond_steps=3, rr_arith="fp64",
+               refine_arith="fp64"):
         o = SolveOpts(_MODES[mode], int(bool(precond)), max_iter, refine_iter, 0.0, n_small, seed, precond_shift,
-                      _PSOLVE[precond_solve], precond_steps, 0, mixed_tol, None)
+                      _PSOLVE[precond_solve], precond_steps, 0, mixed_tol, None, 0, 0.0, _ARITH[rr_arith],
+                      _ARITH[refine_arith])
         r = Request(matrix.handle, k, nb, tol, X_out.data_ptr() if X_out is not None else None, o)
         rid = _I64()
         _check(lib().lob_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)), "lob_server_submit")

@@ -51,6 +51,7 @@ int lob_create(const lob_coo* H, const lob_create_opts* opts, lob_matrix** out) 
   if (values < 1 || values > 3) return LOB_ERR_ARG;
   if (o.precond_block < 0 || (o.precond_block > 64 && o.precond_block != LOB_TILE)) return LOB_ERR_ARG;
   if (o.precond_block == LOB_TILE && !(values & LOB_VALUES_FP32)) return LOB_ERR_ARG;  // tile mode runs on FP32 values
+  if (o.wait_log2 < 0 || o.wait_log2 > 40) return LOB_ERR_ARG;
   cudaStream_t st = (cudaStream_t)o.stream;
   *out = nullptr;
 
@@ -73,7 +74,13 @@ int lob_create(const lob_coo* H, const lob_create_opts* opts, lob_matrix** out) 
   lob_matrix* m = new lob_matrix();
   cudaGetDevice(&m->device);
   m->values = values;
-  int rc = lob_build_tiles(&D, values, st, &m->T, &m->norm_inf);
+  m->wait_limit = 1ll << (o.wait_log2 ? o.wait_log2 : 32);
+  int rc = LOB_OK;
+  if (cudaMalloc((void**)&m->status, sizeof(int)) != cudaSuccess || cudaMemset(m->status, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    rc = LOB_ERR_NOMEM;
+  }
+  if (rc == LOB_OK) rc = lob_build_tiles(&D, values, st, &m->T, &m->norm_inf);
   if (rc == LOB_OK) {
     m->h_rowptr.resize(m->T.nt + 1);
     if (cudaMemcpy(m->h_rowptr.data(), m->T.rowptr, (m->T.nt + 1) * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -84,6 +91,7 @@ int lob_create(const lob_coo* H, const lob_create_opts* opts, lob_matrix** out) 
   if (rc != LOB_OK) {
     lob_free_tiles(&m->T);
     lob_free_precond(&m->P);
+    cudaFree(m->status);
     delete m;
     return rc;
   }
@@ -94,6 +102,7 @@ int lob_create(const lob_coo* H, const lob_create_opts* opts, lob_matrix** out) 
 int lob_destroy(lob_matrix* m) {
   if (!m) return LOB_OK;
   cudaFree(m->xs);
+  cudaFree(m->status);
   lob_free_tiles(&m->T);
   lob_free_precond(&m->P);
   delete m;
@@ -135,6 +144,17 @@ int lob_export_perm(const lob_matrix* m, uint16_t* perm) {
 int lob_spmm(lob_matrix* m, int32_t mode, const double* X, double* Y, int32_t nb, void* stream) {
   if (!m || !X || !Y) return LOB_ERR_ARG;
   return lob_spmm_launch(m, mode, X, Y, nb, m->T.n, (cudaStream_t)stream);
+}
+
+int lob_check(lob_matrix* m, void* stream) {
+  if (!m) return LOB_ERR_ARG;
+  const int f = lob_matrix_fault_take(m, (cudaStream_t)stream);
+  if (f < 0) return LOB_ERR_CUDA;
+  if (f) {
+    fprintf(stderr, "lob: an SpMM kernel gave up on a bounded wait; its product is not valid\n");
+    return LOB_ERR_CUDA;
+  }
+  return LOB_OK;
 }
 
 int lob_gram(int64_t n, int32_t p, const double* A, int32_t lda, int32_t q, const double* B, int32_t ldb, double* G,

@@ -90,6 +90,8 @@ struct lob_matrix {
   int device = 0;
   void* xs = nullptr;      // SpMM scratch: X rounded/staged per call (rows padded to whole tiles)
   size_t xs_bytes = 0;
+  int* status = nullptr;   // device word: bit 0 set by an SpMM kernel that gave up on a bounded wait
+  long long wait_limit = 1ll << 32;  // SM clocks any wait inside an SpMM kernel may take
 };
 
 // One matrix's share of a batched SpMM launch (several matrices' tile rows in one grid).
@@ -144,8 +146,9 @@ void lob_free_precond(lob_precond* P);
 int lob_ensure_xs(const lob_matrix* m, size_t need);
 // Y = H X over the active leading n_act x n_act block (n_act <= n; rows/cols >= n_act are
 // treated as absent). Y is fully written (rows >= n_act get 0).
-// Nonzero once an SpMM wait ran out of time since the last call (then cleared); synchronises.
-int lob_spmm_fault_take();
+// Nonzero if an SpMM kernel on m gave up on a bounded wait since the last call (the word is then
+// cleared), -1 if the read failed; synchronises st.
+int lob_matrix_fault_take(const lob_matrix* m, cudaStream_t st);
 int lob_spmm_launch(const lob_matrix* m, int mode, const double* X, double* Y, int nb, int64_t n_act,
                     cudaStream_t st);
 // Y_j = H_j X_j for several matrices in as few launches as possible (one per arithmetic

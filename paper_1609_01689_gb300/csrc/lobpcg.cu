@@ -268,7 +268,7 @@ struct lob_task {
   cudaEvent_t ev = nullptr;
   // control
   int pc = PC_INIT, status = LOB_OK, run_status = LOB_OK, phase = 0;
-  int spmm_mode = LOB_SPMM_FP64, blas_mode = LOB_SPMM_FP64;
+  int spmm_mode = LOB_SPMM_FP64, blas_mode = LOB_SPMM_FP64, rr_mode = LOB_SPMM_FP64;
   double run_tol = 0.0;
   int run_max = 0, max_iter = 0;
   int it = 0, restarts = 0, na = 0, m = 0, iters_total = 0, restarts_total = 0;
@@ -387,9 +387,10 @@ struct lob_task {
     return LOB_TASK_SYNC;
   }
 
-  // projected eigenproblem in the task's block arithmetic (native FP64 or double-float)
+  // projected eigenproblem and Cholesky-QR factors in the task's small-solve arithmetic (native
+  // FP64, or double-float when the options ask for it)
   int rr(int mm, const double* Gp, const double* Mp, double* th, double* Cp, int slot, int chol_only) {
-    if (blas_mode == LOB_SPMM_MIXED)
+    if (rr_mode == LOB_SPMM_MIXED)
       return lob_rr_launch_df(mm, Gp, Mp, th, Cp, info_slot(slot), rrwork.p, st, chol_only);
     return lob_rr_launch(mm, Gp, Mp, th, Cp, info_slot(slot), rrwork.p, st, chol_only);
   }
@@ -544,6 +545,7 @@ int task_init(lob_task* t, lob_matrix* m, int32_t k, int32_t nb, double tol, con
   t->normH = o->norm_H > 0.0 ? o->norm_H : m->norm_inf;
   // block products: native FP64 in the plain solver, FP64-class double-float in MIXED
   t->blas_mode = o->mode == LOB_MODE_MIXED ? LOB_SPMM_MIXED : LOB_SPMM_FP64;
+  t->rr_mode = (o->mode == LOB_MODE_MIXED && o->rr_arith == LOB_ARITH_DF) ? LOB_SPMM_MIXED : LOB_SPMM_FP64;
   t->max_iter = o->max_iter > 0 ? o->max_iter : 500;
   t->t0 = std::chrono::steady_clock::now();
   t->graphs = true;
@@ -611,8 +613,9 @@ int lob_task::step() {
           run_tol = o.mixed_tol > 0.0 ? o.mixed_tol : (tol > LOB_MIXED_TOL ? tol : LOB_MIXED_TOL);
           run_max = max_iter;
         } else if (o.mode == LOB_MODE_MIXED) {
-          // phase 2: FP64-class refinement products from the phase-1 vectors
-          spmm_mode = M->T.v32lo ? LOB_SPMM_DF64 : LOB_SPMM_FP64;
+          // phase 2: refinement products from the phase-1 vectors, FP64 values (or double-float
+          // values and products when the options ask for it)
+          spmm_mode = (o.refine_arith == LOB_ARITH_DF && M->T.v32lo) ? LOB_SPMM_DF64 : LOB_SPMM_FP64;
           run_tol = tol;
           run_max = o.refine_iter > 0 ? o.refine_iter : (max_iter - iters_total > 50 ? max_iter - iters_total : 50);
         } else {
@@ -876,6 +879,9 @@ int lob_solve_impl(lob_matrix* m, int32_t k, int32_t nb, double tol, const doubl
   if (n_act < 3 * nb) return LOB_ERR_ARG;
   if (o->mode != LOB_MODE_FP64 && o->mode != LOB_MODE_MIXED) return LOB_ERR_ARG;
   if (o->mode == LOB_MODE_MIXED && (!m->T.v32 || !m->T.v64)) return LOB_ERR_ARG;
+  if (o->rr_arith < LOB_ARITH_FP64 || o->rr_arith > LOB_ARITH_DF || o->refine_arith < LOB_ARITH_FP64 ||
+      o->refine_arith > LOB_ARITH_DF)
+    return LOB_ERR_ARG;
   if (o->mode == LOB_MODE_FP64 && !m->T.v64) return LOB_ERR_ARG;
   if (o->precond && m->P.bp < 1) return LOB_ERR_ARG;
   if (o->n_small_inner < 0 || !(o->guess_tol >= 0.0 && o->guess_tol < 1.0)) return LOB_ERR_ARG;
@@ -901,8 +907,10 @@ int lob_solve_impl(lob_matrix* m, int32_t k, int32_t nb, double tol, const doubl
     }
   }
   lob_task_destroy(t);
-  if ((rc == LOB_OK || rc == LOB_ERR_NOCONV) && lob_spmm_fault_take() != 0) {
-    fprintf(stderr, "lob: an SpMM wait ran out of time; the result is not valid\n");
+  // a product that gave up on a bounded wait voids whatever the iteration made of it
+  const int fault = lob_matrix_fault_take(m, stream);
+  if (fault != 0) {
+    fprintf(stderr, "lob: an SpMM kernel gave up on a bounded wait; the result is not valid\n");
     rc = LOB_ERR_CUDA;
   }
   return rc;

@@ -151,6 +151,7 @@ struct lob_ltask {
   size_t gw_half = 0;  // doubles in each half of the Gram partial buffer
   // control
   int blas = LOB_SPMM_FP64;
+  int rrb = LOB_SPMM_FP64;  // arithmetic of the small dense solves (Cholesky-QR factors, Rayleigh-Ritz)
   int phase = 0;        // MIXED: 0 = FP32-value products, 1 = FP64-class refinement
   bool start = true;    // the next round computes H X and the Rayleigh-Ritz step on X alone
   bool active = false;  // iterating (has residual norms)
@@ -365,7 +366,7 @@ int rr_batch(lob_engine* E, std::vector<lob_bjob>& v, int) {
 
 lob_bjob rr_job(const lob_ltask* t, int m, const double* G, const double* Mm, double* theta, double* C, int chol) {
   lob_bjob j{};
-  j.x2 = t->blas;
+  j.x2 = t->rrb;
   j.x0 = m; j.x1 = chol; j.A = G; j.B = Mm; j.Y = theta; j.W0 = C; j.W1 = t->rrw;
   return j;
 }
@@ -495,7 +496,7 @@ void set_phase(lob_ltask* t) {
 int spmm_mode_of(const lob_ltask* t) {
   if (t->o.mode != LOB_MODE_MIXED) return LOB_SPMM_FP64;
   if (t->phase == 0) return LOB_SPMM_MIXED;
-  return t->M->T.v32lo ? LOB_SPMM_DF64 : LOB_SPMM_FP64;
+  return (t->o.refine_arith == LOB_ARITH_DF && t->M->T.v32lo) ? LOB_SPMM_DF64 : LOB_SPMM_FP64;
 }
 
 }  // namespace
@@ -508,6 +509,7 @@ int lob_engine_add(lob_engine* E, lob_matrix* M, int32_t k, int32_t nb, double t
   t->user = user;
   t->normH = o->norm_H > 0.0 ? o->norm_H : M->norm_inf;
   t->blas = o->mode == LOB_MODE_MIXED ? LOB_SPMM_MIXED : LOB_SPMM_FP64;
+  t->rrb = (o->mode == LOB_MODE_MIXED && o->rr_arith == LOB_ARITH_DF) ? LOB_SPMM_MIXED : LOB_SPMM_FP64;
   t->max_iter = o->max_iter > 0 ? o->max_iter : 500;
   t->t0 = std::chrono::steady_clock::now();
   int rc = task_alloc(E, t);

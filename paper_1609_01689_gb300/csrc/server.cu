@@ -97,6 +97,8 @@ struct lob_server {
       if (rc == LOB_OK || rc == LOB_ERR_NOCONV || rc > 0) {
         double lam[64];
         rc = lob_task_result(q->t, lam, &q->res.stats);
+        // a persistent SpMM kernel of this solve that gave up on a bounded wait voids the result
+        if (lob_matrix_fault_take(q->r.H, q->st) != 0) rc = LOB_ERR_CUDA;
         if (rc == LOB_OK || rc == LOB_ERR_NOCONV) memcpy(q->res.lambda, lam, q->r.k * sizeof(double));
       }
       lob_task_destroy(q->t);  // stream-ordered release of the solver state
@@ -357,6 +359,9 @@ int lob_server_submit(lob_server* s, const lob_request* r, int64_t* id) {
   if (o.precond && (H->P.bp < 1 || H->P.bp > 64)) return LOB_ERR_ARG;  // the engine applies dense blocks only
   if (o.precond_solve < LOB_PSOLVE_FOM || o.precond_solve > LOB_PSOLVE_ABS || o.precond_steps < 0 ||
       o.precond_steps > 3)
+    return LOB_ERR_ARG;
+  if (o.rr_arith < LOB_ARITH_FP64 || o.rr_arith > LOB_ARITH_DF || o.refine_arith < LOB_ARITH_FP64 ||
+      o.refine_arith > LOB_ARITH_DF)
     return LOB_ERR_ARG;
   Req* q = new Req();
   q->id = s->next_id++;

@@ -337,12 +337,14 @@ __global__ void __launch_bounds__(Cfg<MIXED, NB>::THREADS, Cfg<MIXED, NB>::MINB)
 // row and column counts of a tile are uneven) and the slack absorbs most of it. X_I has two
 // slots, refilled the same way by the last warp to finish a tile row.
 //
-// Every wait is bounded (about 2^32 SM clocks); a wait that runs out records it in
-// lob_spmm_fault and the warp leaves the kernel. Copies are only issued for chunks that all
-// warps go on to wait for, so none is in flight when the CTA ends.
+// Every wait is bounded by the launch's `limit` (SM clocks; about 2^32 by default, settable per
+// matrix at create). A wait that runs out sets bit 0 of the matrix's status word and the CTA's
+// abort flag; every warp then leaves at its next wait (or right away if it is waiting), no new copy
+// is issued, and the last warp of the CTA to leave waits -- with its own bound -- for every copy
+// the CTA issued to land before the CTA ends, so no bulk copy is still writing shared memory that
+// the next CTA on the SM may own. The same last-warp drain runs on the normal exit, where every
+// issued copy has already been consumed.
 // ---------------------------------------------------------------------------------------------
-__device__ int lob_spmm_fault = 0;
-
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -358,24 +360,60 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
-// Wait, with the whole warp, for the completion of the phase with the given parity. Every
-// lane waits (each acquires the copied data); the outcome is warp-uniform. False if the wait
-// ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Shared-memory control words of a ring kernel's abort protocol.
+struct RingCtl {
+  int abort;        // set once any warp of the CTA gave up on a wait
+  int left;         // warps that have left the main loop
+  int issued[8];    // fills issued per ring stage (at most 6 stages) and X_I slot (2)
+};
+
+// Wait, with the whole warp, for the completion of the phase with the given parity. Every lane
+// waits (each acquires the copied data); the outcome is warp-uniform. False if the wait ran out
+// (the status word and the CTA's abort flag are then set) or another warp already gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit, RingCtl* ctl,
+                                          int* status) {
   const uint32_t a = smem_u32(bar);
   const long long t0 = clock64();
   for (;;) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (__all_sync(0xffffffffu, done != 0)) return true;
-    if (__any_sync(0xffffffffu, clock64() - t0 > (1ll << 32))) {
-      if ((threadIdx.x & 31) == 0) atomicExch(&lob_spmm_fault, 1);
+    if (__all_sync(0xffffffffu, mbar_test(a, parity))) return true;
+    const bool give_up = clock64() - t0 > limit || *(volatile int*)&ctl->abort != 0;
+    if (__any_sync(0xffffffffu, give_up)) {
+      if ((threadIdx.x & 31) == 0 && atomicExch(&ctl->abort, 1) == 0) atomicOr(status, 1);
       return false;
     }
+  }
+}
+
+// Leave the ring: the last warp of the CTA waits (bounded; the copies were issued and complete in
+// microseconds unless the memory system failed) for the latest fill of every stage and slot it
+// ever issued. nslots = ring stages + X_I slots, bars[i] their mbarriers (stages first).
+__device__ __forceinline__ void ring_leave(RingCtl* ctl, uint64_t* bars, int nslots, int nwarps) {
+  __syncwarp();
+  int last = 0;
+  if ((threadIdx.x & 31) == 0) {
+    __threadfence_block();
+    last = atomicAdd(&ctl->left, 1) == nwarps - 1;
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return;
+  __threadfence_block();
+  for (int i = 0; i < nslots; i++) {
+    const int k = *(volatile int*)&ctl->issued[i];
+    if (k == 0) continue;
+    const uint32_t a = smem_u32(&bars[i]);
+    const long long t0 = clock64();
+    while (!__all_sync(0xffffffffu, mbar_test(a, (uint32_t)((k - 1) & 1))))
+      if (__any_sync(0xffffffffu, clock64() - t0 > (1ll << 31))) break;
   }
 }
 
@@ -409,7 +447,8 @@ struct CfgR {
   static constexpr size_t RNG = BAR + 8 * (D + 2);  // this CTA's tile rows [Ib, Ie)
   static constexpr size_t CUR = RNG + 16;           // the refill cursor
   static constexpr size_t CNT = CUR + 48;           // stage and X_I counters
-  static constexpr size_t BYTES = CNT + 4 * (D + 2);
+  static constexpr size_t CTL = (CNT + 4 * (D + 2) + 7) / 8 * 8;  // abort protocol (RingCtl)
+  static constexpr size_t BYTES = CTL + sizeof(RingCtl);
   static_assert(VW * G == NB && THREADS <= 1024 && THREADS % 32 == 0, "launch shape");
   static_assert(sizeof(RingCur) <= 48, "cursor slot");
   static_assert(S_PM % 16 == 0 && S_PT % 16 == 0 && STAGE % 16 == 0 && ST % 16 == 0,
@@ -473,7 +512,7 @@ __global__ void __launch_bounds__(CfgR<NB>::THREADS, 1)
                 const int64_t* __restrict__ tptr, const int32_t* __restrict__ tchunk,
                 const uint2* __restrict__ rv, const uint16_t* __restrict__ cperm,
                 const uint16_t* __restrict__ cptrs, const float* __restrict__ Xs, double* __restrict__ Y, int ldy,
-                int c0, int w, int64_t n_act, int64_t ntr) {
+                int c0, int w, int64_t n_act, int64_t ntr, int* __restrict__ status, long long limit) {
   using C = CfgR<NB>;
   constexpr int VW = C::VW, G = C::G, NW = C::NW, D = C::D, CH = C::CH;
   constexpr int XN = LOB_TILE * NB;
@@ -485,10 +524,15 @@ __global__ void __launch_bounds__(CfgR<NB>::THREADS, 1)
   int* xcnt = cnt + D;
   int64_t* range = reinterpret_cast<int64_t*>(sm + C::RNG);
   RingCur* cur = reinterpret_cast<RingCur*>(sm + C::CUR);
+  RingCtl* ctl = reinterpret_cast<RingCtl*>(sm + C::CTL);
   const int tid = threadIdx.x, lane = tid & 31;
   const int g = tid / G, gl = tid % G;
+  static_assert(D + 2 <= 8, "RingCtl slots");
 
   if (tid == 0) {
+    ctl->abort = 0;
+    ctl->left = 0;
+    for (int i = 0; i < 8; i++) ctl->issued[i] = 0;
     // this CTA's tile rows: entries before row I are tptr[rowptr[I]]; split them evenly
     const int64_t E = tptr[rowptr[ntr]];
     auto first_row = [&](int64_t b) -> int64_t {
@@ -511,6 +555,7 @@ __global__ void __launch_bounds__(CfgR<NB>::THREADS, 1)
   const int64_t Ib = range[0], Ie = range[1];
   if (tid == 0 && Ib < Ie) {
     for (int s = 0; s < 2 && Ib + s < Ie; s++) {
+      ctl->issued[D + s]++;
       mbar_expect_tx(&xfull[s], (uint32_t)C::XV);
       bulk_g2s(XIb + s * XN, Xs + (Ib + s) * LOB_TILE * NB, (uint32_t)C::XV, &xfull[s]);
     }
@@ -521,6 +566,7 @@ __global__ void __launch_bounds__(CfgR<NB>::THREADS, 1)
     c.t = t0 - 1; c.k = 0; c.nk = 0;  // settle moves to the first chunk
     bool more = ring_settle(c, rowptr, tcol, tchunk, n_act);
     for (int s = 0; s < D && more; s++) {
+      ctl->issued[s]++;
       ring_issue<NB>(sm + C::ST + s * C::STAGE, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rv, cperm, cptrs, Xs);
       c.k++;
       more = ring_settle(c, rowptr, tcol, tchunk, n_act);
@@ -534,7 +580,7 @@ __global__ void __launch_bounds__(CfgR<NB>::THREADS, 1)
   for (int64_t I = Ib; I < Ie; I++) {
     const int64_t ri = I - Ib;
     const int xs = (int)(ri & 1);
-    if (!mbar_wait(&xfull[xs], (uint32_t)((ri >> 1) & 1))) return;
+    if (!mbar_wait(&xfull[xs], (uint32_t)((ri >> 1) & 1), limit, ctl, status)) goto leave;
     const float* XI = XIb + xs * XN;
     int64_t t0;
     const int64_t t1 = ring_trim(rowptr, tcol, n_act, I, &t0);
@@ -548,7 +594,7 @@ __global__ void __launch_bounds__(CfgR<NB>::THREADS, 1)
       float4 acc_t = make_float4(0.f, 0.f, 0.f, 0.f), acc_c = make_float4(0.f, 0.f, 0.f, 0.f);
       for (int k = 0; k < nk; k++) {
         const int s = (int)(ch % D);
-        if (!mbar_wait(&full[s], (uint32_t)((ch / D) & 1))) return;
+        if (!mbar_wait(&full[s], (uint32_t)((ch / D) & 1), limit, ctl, status)) goto leave;
         unsigned char* stage = sm + C::ST + s * C::STAGE;
         const int64_t base = tptr[t] + (int64_t)k * CH;
         const uint2* RV = reinterpret_cast<const uint2*>(stage + C::S_RV) + (base & 1);
@@ -590,8 +636,9 @@ __global__ void __launch_bounds__(CfgR<NB>::THREADS, 1)
           if (old == NW * (int)(ch / D + 1) - 1) {
             __threadfence_block();
             RingCur c = *cur;
-            if (c.I < c.Ie) {
+            if (c.I < c.Ie && *(volatile int*)&ctl->abort == 0) {
               asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+              ctl->issued[s]++;
               ring_issue<NB>(stage, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rv, cperm, cptrs, Xs);
               c.k++;
               if (!ring_settle(c, rowptr, tcol, tchunk, n_act)) c.I = c.Ie;
@@ -628,14 +675,17 @@ __global__ void __launch_bounds__(CfgR<NB>::THREADS, 1)
     if (lane == 0) {
       __threadfence_block();
       const int old = atomicAdd(&xcnt[xs], 1);
-      if (old == NW * (int)((ri >> 1) + 1) - 1 && I + 2 < Ie) {
+      if (old == NW * (int)((ri >> 1) + 1) - 1 && I + 2 < Ie && *(volatile int*)&ctl->abort == 0) {
         __threadfence_block();
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        ctl->issued[D + xs]++;
         mbar_expect_tx(&xfull[xs], (uint32_t)C::XV);
         bulk_g2s(XIb + xs * XN, Xs + (I + 2) * LOB_TILE * NB, (uint32_t)C::XV, &xfull[xs]);
       }
     }
   }
+leave:
+  ring_leave(ctl, full, D + 2, NW);
 }
 
 // FP64-class variant (LOB_SPMM_DF64): values as (hi, lo) FP32 pairs (hi = the FP32 value,
@@ -893,7 +943,8 @@ struct CfgRD {
   static constexpr size_t RNG = BAR + 8 * (D + 1);
   static constexpr size_t CUR = RNG + 16;
   static constexpr size_t CNT = CUR + 48;
-  static constexpr size_t BYTES = CNT + 4 * (D + 1);
+  static constexpr size_t CTL = (CNT + 4 * (D + 1) + 7) / 8 * 8;  // abort protocol (RingCtl)
+  static constexpr size_t BYTES = CTL + sizeof(RingCtl);
   static_assert(VW * G == NB && NG * RPG == LOB_TILE && THREADS % G == 0, "launch shape");
   static_assert(sizeof(RingCur) <= 48, "cursor slot");
   static_assert(S_VL % 16 == 0 && S_PM % 16 == 0 && S_PT % 16 == 0 && STAGE % 16 == 0 &&
@@ -934,7 +985,7 @@ __global__ void __launch_bounds__(CfgRD<NB>::THREADS, 1)
                    const uint2* __restrict__ rv, const float* __restrict__ vlo,
                    const uint16_t* __restrict__ cperm, const uint16_t* __restrict__ cptrs,
                    const float2* __restrict__ Xs, double* __restrict__ Y, int ldy, int c0, int w, int64_t n_act,
-                   int64_t ntr) {
+                   int64_t ntr, int* __restrict__ status, long long limit) {
   using C = CfgRD<NB>;
   constexpr int VW = C::VW, G = C::G, NG = C::NG, RPG = C::RPG, NW = C::NW, D = C::D, CH = C::CH;
   extern __shared__ __align__(16) unsigned char sm[];
@@ -945,10 +996,15 @@ __global__ void __launch_bounds__(CfgRD<NB>::THREADS, 1)
   int* xcnt = cnt + D;
   int64_t* range = reinterpret_cast<int64_t*>(sm + C::RNG);
   RingCur* cur = reinterpret_cast<RingCur*>(sm + C::CUR);
+  RingCtl* ctl = reinterpret_cast<RingCtl*>(sm + C::CTL);
   const int tid = threadIdx.x, lane = tid & 31;
   const int g = tid / G, gl = tid % G;
+  static_assert(D + 1 <= 8, "RingCtl slots");
 
   if (tid == 0) {
+    ctl->abort = 0;
+    ctl->left = 0;
+    for (int i = 0; i < 8; i++) ctl->issued[i] = 0;
     const int64_t E = tptr[rowptr[ntr]];
     auto first_row = [&](int64_t b) -> int64_t {
       if (b >= (int64_t)gridDim.x) return ntr;
@@ -970,6 +1026,7 @@ __global__ void __launch_bounds__(CfgRD<NB>::THREADS, 1)
   __syncthreads();
   const int64_t Ib = range[0], Ie = range[1];
   if (tid == 0 && Ib < Ie) {
+    ctl->issued[D]++;
     mbar_expect_tx(xfull, (uint32_t)C::XV);
     bulk_g2s(XI, Xs + Ib * LOB_TILE * NB, (uint32_t)C::XV, xfull);
     RingCur c;
@@ -979,6 +1036,7 @@ __global__ void __launch_bounds__(CfgRD<NB>::THREADS, 1)
     c.t = t0 - 1; c.k = 0; c.nk = 0;
     bool more = ring_settle(c, rowptr, tcol, tchunk, n_act);
     for (int s = 0; s < D && more; s++) {
+      ctl->issued[s]++;
       ring_issue_df<NB>(sm + C::ST + s * C::STAGE, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rv, vlo, cperm,
                         cptrs, Xs);
       c.k++;
@@ -992,7 +1050,7 @@ __global__ void __launch_bounds__(CfgRD<NB>::THREADS, 1)
   int64_t ch = 0;
   for (int64_t I = Ib; I < Ie; I++) {
     const int64_t ri = I - Ib;
-    if (!mbar_wait(xfull, (uint32_t)(ri & 1))) return;
+    if (!mbar_wait(xfull, (uint32_t)(ri & 1), limit, ctl, status)) goto leave;
     int64_t t0;
     const int64_t t1 = ring_trim(rowptr, tcol, n_act, I, &t0);
     float rh[RPG][VW], rl[RPG][VW];
@@ -1011,7 +1069,7 @@ __global__ void __launch_bounds__(CfgRD<NB>::THREADS, 1)
         for (int q = 0; q < VW; q++) { th[a][q] = tlo[a][q] = chh[a][q] = clo[a][q] = 0.f; }
       for (int k = 0; k < nk; k++) {
         const int s = (int)(ch % D);
-        if (!mbar_wait(&full[s], (uint32_t)((ch / D) & 1))) return;
+        if (!mbar_wait(&full[s], (uint32_t)((ch / D) & 1), limit, ctl, status)) goto leave;
         unsigned char* stage = sm + C::ST + s * C::STAGE;
         const int64_t base = tptr[t] + (int64_t)k * CH;
         const uint2* RV = reinterpret_cast<const uint2*>(stage + C::S_RV) + (base & 1);
@@ -1062,8 +1120,9 @@ __global__ void __launch_bounds__(CfgRD<NB>::THREADS, 1)
           if (old == NW * (int)(ch / D + 1) - 1) {
             __threadfence_block();
             RingCur c = *cur;
-            if (c.I < c.Ie) {
+            if (c.I < c.Ie && *(volatile int*)&ctl->abort == 0) {
               asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+              ctl->issued[s]++;
               ring_issue_df<NB>(stage, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rv, vlo, cperm, cptrs, Xs);
               c.k++;
               if (!ring_settle(c, rowptr, tcol, tchunk, n_act)) c.I = c.Ie;
@@ -1112,14 +1171,17 @@ __global__ void __launch_bounds__(CfgRD<NB>::THREADS, 1)
     if (lane == 0) {
       __threadfence_block();
       const int old = atomicAdd(xcnt, 1);
-      if (old == NW * (int)(ri + 1) - 1 && I + 1 < Ie) {
+      if (old == NW * (int)(ri + 1) - 1 && I + 1 < Ie && *(volatile int*)&ctl->abort == 0) {
         __threadfence_block();
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        ctl->issued[D]++;
         mbar_expect_tx(xfull, (uint32_t)C::XV);
         bulk_g2s(XI, Xs + (I + 1) * LOB_TILE * NB, (uint32_t)C::XV, xfull);
       }
     }
   }
+leave:
+  ring_leave(ctl, full, D + 1, NW);
 }
 
 // SMs of the current device (-1 if the query fails).
@@ -1162,7 +1224,7 @@ int launch_df(const lob_matrix* m, const double* X, double* Y, int nb, int64_t n
     if constexpr (NB == 16) {
       (k_spmm_ring_df<NB><<<(unsigned)grid, CfgRD<NB>::THREADS, CfgRD<NB>::BYTES, st>>>(
            TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rv, TS.v32lo, TS.cperm, TS.cptrs, Xs, Y, nb, c0, w, n_act,
-           nt_act),
+           nt_act, m->status, m->wait_limit),
        LOB_LAUNCHED());
     } else {
       (kern<<<(unsigned)nt_act, C::THREADS, C::BYTES, st>>>(TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rc, TS.v32,
@@ -1226,7 +1288,7 @@ int launch_ring16(const lob_matrix* m, const double* X, double* Y, int nb, int64
      LOB_LAUNCHED());
     (k_spmm_ring<NB><<<(unsigned)grid, C::THREADS, C::BYTES, st>>>(TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rv,
                                                                   TS.cperm, TS.cptrs, Xs, Y, nb, c0, w, n_act,
-                                                                  nt_act),
+                                                                  nt_act, m->status, m->wait_limit),
      LOB_LAUNCHED());
   }
   LOB_CUDA(cudaGetLastError());
@@ -1333,13 +1395,12 @@ int lob_spmm_batch_launch(const lob_matrix* const* ms, const double* const* X, d
   return LOB_OK;
 }
 
-int lob_spmm_fault_take() {
+int lob_matrix_fault_take(const lob_matrix* m, cudaStream_t st) {
   int h = 0;
-  if (cudaMemcpyFromSymbol(&h, lob_spmm_fault, sizeof(int)) != cudaSuccess) return -1;
-  if (h) {
-    const int z = 0;
-    cudaMemcpyToSymbol(lob_spmm_fault, &z, sizeof(int));
-  }
+  if (cudaMemcpyAsync(&h, m->status, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return -1;
+  if (h && cudaMemsetAsync(m->status, 0, sizeof(int), st) != cudaSuccess) return -1;
   return h;
 }
 

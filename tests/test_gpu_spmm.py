@@ -131,3 +131,30 @@ def test_spmm_df64_integer_exact_and_fp64_class(nb):
     Y = run(M, X, "df64")
     bound = 2 * (row_counts(H)[:, None] + 2) * 2.0 ** -46 * oracle.spmm(abs_coo(H), np.abs(X))
     assert np.all(np.abs(Y - oracle.spmm(H, X)) <= bound)
+
+
+@pytest.mark.parametrize("mode", ["mixed", "df64"])
+def test_spmm_bounded_wait_reports_and_context_survives(mode):
+    """Failure detection without a GPU fault: a matrix created with a wait limit of 2 SM clocks
+    makes every wait of the persistent SpMM kernels (nb = 16) run out before its copy lands. The
+    kernel must then stop issuing copies, let the copies already in flight land, leave, and set
+    the matrix's status word: lob_check reports LOB_ERR_CUDA once (then the word is clear), a
+    solve on that matrix returns LOB_ERR_CUDA, and a product on a normally created matrix right
+    after is exact (the context stays usable)."""
+    import paper_1609_01689_gb300 as lob
+    rng = np.random.default_rng(77)
+    H = random_upper(3000, 0.01, rng, integer=True)
+    X = rng.integers(-8, 9, (3000, 16)).astype(np.float64)
+    Mbad = lob.Matrix(H.n, H.rows, H.cols, H.vals, wait_log2=1)
+    run(Mbad, X, mode)
+    with pytest.raises(lob.LobError) as e:
+        Mbad.check()
+    assert e.value.code == lob.LOB_ERR_CUDA
+    Mbad.check()  # cleared
+    if mode == "mixed":
+        with pytest.raises(lob.LobError) as e:
+            Mbad.solve(4, 16, 1e-8, mode="mixed", max_iter=5)
+        assert e.value.code == lob.LOB_ERR_CUDA
+    Mok = lob.Matrix(H.n, H.rows, H.cols, H.vals)
+    assert np.array_equal(run(Mok, X, mode), oracle.spmm(H, X))
+    Mok.check()
