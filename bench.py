@@ -1,12 +1,13 @@
 #!/usr/bin/env python
 """Benchmark: time to the k smallest eigenpairs with the preconditioned block LOBPCG.
 
-Workload (default): the n = 500,000 precision-study matrix -- levels 0..10 with sizes ~2.2^q,
-graded diagonal 10 q + U(-1,1), ~200 nonzeros per row coupling levels |dq| <= 2, seed 1 --
-k = 8, nb = 16, block-diagonal preconditioner with 32 x 32 blocks, initial guess from the
-leading levels {0, 1} (eq. 12), residual tolerance 1e-8 ||H||. One step = one complete solve
-(every row of the hot path: SpMM, Gram, Rayleigh-Ritz, update, residual, preconditioner,
-initial guess, FP64 refinement) with the matrix already resident in HBM.
+Workload (default): the large single solve -- n = 8,000,000, levels 0..14 with sizes ~2.2^q,
+graded diagonal 10 q + U(-1,1), ~300 nonzeros per row coupling levels |dq| <= 2 (1.2e9 stored
+upper-triangle entries), seed 1 -- k = 10, nb = 16, block-diagonal preconditioner with 64 x 64
+blocks, initial guess from the leading levels {0, 1} (eq. 12), residual tolerance 1e-8 ||H||.
+One step = one complete mixed-precision solve (every row of the hot path: SpMM, Gram,
+Rayleigh-Ritz, update, residual, preconditioner, initial guess, FP64 refinement) with the matrix
+already resident in HBM. --workload c2 runs the n = 500,000 precision study instead.
 
 Prints one JSON line. Also reported: SpMM effective HBM bandwidth against the measured peak
 (roofline), the plain FP64 solver's time on the same workload, eigenvalue error against the
@@ -35,8 +36,8 @@ WORKLOADS = {
                     "tiles (FOM 3), tol 1e-8", cfg="c2", k=8, nb=16, bp=256, tol=1e-8),
     "c1": dict(name="n=1536 levels 0..6, ~30 nnz/row, k=5, nb=8, b_p=32, tol 1e-8", cfg="c1", k=5, nb=8, bp=32,
                tol=1e-8),
-    "c3": dict(name="n=8000000 levels 0..14, ~300 nnz/row, k=10, nb=16, b_p=64, tol 1e-8", cfg="c3", k=10, nb=16,
-               bp=64, tol=1e-8),
+    "c3": dict(name="n=8000000 levels 0..14, ~300 nnz/row (1.2e9 stored), k=10, nb=16, b_p=64, tol 1e-8", cfg="c3",
+               k=10, nb=16, bp=64, tol=1e-8),
 }
 
 
@@ -104,72 +105,126 @@ class ClockSampler:
 # DRAM bytes (read + write) of one FP32-value SpMM launch (k_spmm_ring<16>) on the n = 500,000
 # workload, from an ncu capture of this bench's own kernel mode (the profile summary of that kernel
 # and workload). Valid for the kernel as captured; reset to None when the kernel changes.
-SPMM_TRAFFIC = {"c2": 762782464 + 147569408}
+SPMM_TRAFFIC = {}
 
 
 def golden_eigs(cfg):
+    """Stored oracle eigenvalues of a workload and the header facts of their run: (values, steps,
+    seconds), or (None, None, None)."""
     path = os.path.join(ROOT, "tests", "golden", f"{cfg}_eigs.txt")
     if not os.path.exists(path):
-        return None, None
-    vals, steps = [], None
+        return None, None, None
+    vals, steps, secs = [], None, None
     for line in open(path):
         if line.startswith("#"):
             if " steps" in line:
                 try:
                     steps = int(line.split(" steps")[0].split(",")[-1].strip())
-                except ValueError:
+                    secs = float(line.split(" steps,")[1].split(" s ")[0].strip())
+                except (ValueError, IndexError):
                     pass
             continue
         if line.strip():
             vals.append(float(line))
-    return np.array(vals), steps
+    return np.array(vals), steps, secs
 
 
 _ORACLE_H = {}
 _HOST_COO = {}
 
 
-def host_coo(cfg, layout):
-    """The workload's upper-triangle COO on the host (generated once per configuration and seed)."""
+def host_coo(cfg, layout, dev=None):
+    """The workload's upper-triangle COO on the host (once per configuration and seed): copied from
+    the device generator's output when given (pinned host memory), else the host generator."""
     import synth
 
     key = (cfg, int(layout.seed))
     if key not in _HOST_COO:
-        _HOST_COO[key] = synth.generate(layout)
+        if dev is not None:
+            import torch
+            out = []
+            for t in dev:
+                h = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+                h.copy_(t)
+                out.append(h)
+            _HOST_COO[key] = tuple(out)
+        else:
+            _HOST_COO[key] = tuple(synth.generate(layout, copy=False))
     return _HOST_COO[key]
 
 
-def oracle_sample(cfg, layout):
-    """The oracle (plain single-threaded FP64 Lanczos, full reorthogonalisation) on a bounded
-    sample of the same workload: two short runs of s1 < s2 Lanczos steps fix the per-step cost
-    a + b j (SpMV plus reorthogonalisation against j vectors); the time to the converged step
-    count N of the full oracle run (stored with the reference eigenvalues) is N a + N^2 b / 2."""
+def _np(a):
+    return a.numpy() if hasattr(a, "numpy") else a
+
+
+# Oracle Lanczos steps of the two timed sample runs per workload (each run is a complete oracle
+# Lanczos call of that many steps; about 10-30 s of CPU work together on one core).
+ORACLE_SAMPLE_STEPS = {"c1": (10, 30), "c2": (10, 30), "c3": (2, 5)}
+
+
+def oracle_matrix(cfg, layout, dev=None):
+    """The workload in the oracle's CSR form (the COO form's arithmetic; fits beside the Lanczos
+    basis at 1.2e9 entries) and its ||H||_inf, built once per configuration and seed."""
     import oracle
 
     key = (cfg, int(layout.seed))
     if key not in _ORACLE_H:
-        r, c, v = host_coo(cfg, layout)
-        H = oracle.Coo(layout.n, r, c, v)
-        _ORACLE_H[key] = (H, oracle.norm_inf(H))
-    H, nH = _ORACLE_H[key]
-    _, N = golden_eigs(cfg)
-    s1, s2 = 10, 30
-    t = []
-    for s in (s1, s2):
-        t0 = time.perf_counter()
-        oracle.lanczos(H, 1, 1e-300, nH, max_steps=s)
-        t.append(time.perf_counter() - t0)
-    # t(s) = a s + b s^2 / 2
-    A = np.array([[s1, s1 * s1 / 2.0], [s2, s2 * s2 / 2.0]])
-    a, b = np.linalg.solve(A, np.array(t))
+        r, c, v = (_np(a) for a in host_coo(cfg, layout, dev))
+        nH = oracle.norm_inf(oracle.Coo(layout.n, r, c, v))
+        _ORACLE_H[key] = (oracle.Csr.from_sorted_coo(layout.n, r, c, v), nH)
+    return _ORACLE_H[key]
+
+
+def oracle_run_s(H, nH, steps):
+    """Seconds of one oracle Lanczos call of the given number of steps."""
+    import oracle
+
+    t0 = time.perf_counter()
+    oracle.lanczos_csr(H, 1, 1e-300, nH, max_steps=steps)
+    return time.perf_counter() - t0
+
+
+def oracle_extrapolate(points, N):
+    """Least-squares fit of t(s) = a s + b s^2 / 2 (SpMV plus reorthogonalisation against j vectors
+    per step) to timed (steps, seconds) points; the time of an N-step run in ms."""
+    A = np.array([[s, s * s / 2.0] for s, _ in points])
+    (a, b), *_ = np.linalg.lstsq(A, np.array([t for _, t in points]), rcond=None)
     a, b = max(a, 0.0), max(b, 0.0)
-    if N is None:
-        N = 300
-    est = N * a + N * N * b / 2.0
-    return est * 1e3, dict(kind="oracle", cores=1, sample=(
-        f"oracle Lanczos (FP64, full reorthogonalisation, 1 thread) on the same matrix: {s1} and {s2} steps timed "
-        f"({t[0]:.2f} s, {t[1]:.2f} s), per-step cost a + b j fitted, extrapolated to the {N} steps the full oracle "
-        f"run needs to reach Ritz residual 1e-12 ||H||"))
+    return (N * a + N * N * b / 2.0) * 1e3
+
+
+# Oracle Lanczos steps of the timed sample runs per workload: two runs for the cpu_baseline leg
+# (about 10-30 s of CPU work together on one core), one run per step of the reference arm.
+ORACLE_SAMPLE_STEPS = {"c1": (10, 30), "c2": (10, 30), "c3": (2, 5)}
+REF_STEP_STEPS = {"c1": (10, 30), "c2": (4, 12), "c3": (1, 3)}
+
+
+def oracle_desc(cfg, N, what):
+    _, _, full_s = golden_eigs(cfg)
+    desc = dict(kind="oracle", cores=1, sample=(
+        f"oracle Lanczos (FP64, full reorthogonalisation, 1 thread) on the same matrix: {what}; per-step cost "
+        f"a + b j fitted, extrapolated to the {N} steps the full oracle run needs to reach Ritz residual 1e-12 ||H||"))
+    if full_s is not None:
+        desc["full_run_measured_s"] = full_s
+        desc["full_run_note"] = (f"the full {N}-step oracle run that wrote the stored eigenvalues took {full_s:.0f} s on "
+                                 f"one core of the x86 build host")
+    return desc
+
+
+def oracle_sample(cfg, layout, dev=None):
+    """The oracle (plain single-threaded FP64 Lanczos, full reorthogonalisation) on a bounded
+    sample of the same workload: two short runs of s1 < s2 Lanczos steps fix the per-step cost
+    a + b j (SpMV plus reorthogonalisation against j vectors); the time to the converged step
+    count N of the full oracle run (stored with the reference eigenvalues) is N a + N^2 b / 2.
+    Returns (estimate ms, description)."""
+    H, nH = oracle_matrix(cfg, layout, dev)
+    _, N, _ = golden_eigs(cfg)
+    N = N or 300
+    s1, s2 = ORACLE_SAMPLE_STEPS.get(cfg, (10, 30))
+    t = [oracle_run_s(H, nH, s) for s in (s1, s2)]
+    desc = oracle_desc(cfg, N, f"{s1} and {s2} steps timed ({t[0]:.2f} s, {t[1]:.2f} s)")
+    desc["sample_s"] = sum(t)
+    return oracle_extrapolate([(s1, t[0]), (s2, t[1])], N), desc
 
 
 def csb_sample(cfg, layout, nb, bytes_per_call, gpu_ms):
@@ -179,7 +234,7 @@ def csb_sample(cfg, layout, nb, bytes_per_call, gpu_ms):
     import baseline
     import synth
 
-    r, c, v = host_coo(cfg, layout)
+    r, c, v = (_np(a) for a in host_coo(cfg, layout))
     M = baseline.CsbMatrix(layout.n, r, c, v)
     X = np.random.default_rng(3).standard_normal((layout.n, nb))
     Y = np.empty_like(X)
@@ -214,7 +269,7 @@ def guess_ablation(M, k, nb, tol, X, layout, stream, args, torch, wl, ms_one, st
     import synth
 
     lv = synth.level_starts(layout)
-    gold, _ = golden_eigs(wl["cfg"])
+    gold = golden_eigs(wl["cfg"])[0]
     n_inner = int(lv[2])
     out = {"one_level": {"guess": "eq. 12, levels {0, 1}", "n_small": n_small, "ms": ms_one,
                          "iterations": st_one["iterations"], "refine_iterations": st_one["refine_iterations"]},
@@ -280,7 +335,7 @@ def precond_ablation(lob, synth, layout, k, nb, tol, n_small, stream, args, torc
     other = {"b_p": alt, "ms": ms, "iterations": st["iterations"], "refine_iterations": st["refine_iterations"],
              "precond_ms": st["phase_ms"]["precond"], "create_ms": create_ms, "status": int(rc),
              "max_relres": max(st["residual"][:k])}
-    gold, _ = golden_eigs(wl["cfg"])
+    gold = golden_eigs(wl["cfg"])[0]
     if gold is not None:
         other["eig_err_vs_oracle"] = float((np.abs(lam - gold[:k]) / np.maximum(np.abs(gold[:k]), 1.0)).max())
     tiles, dense = (head, other) if wl["bp"] == 256 else (other, head)
@@ -536,21 +591,44 @@ def run_kernels(args, lob, M, info, torch, make_matrix):
 
 
 def run_reference(args, wl):
+    """The reference arm: the oracle as it stands on one host core. Each step is one bounded
+    oracle Lanczos call on the workload's matrix, alternating two lengths; ms_per_step is the
+    measured time of those calls, and value is the full oracle solve extrapolated from all timed
+    steps (per-step cost a + b j) to the step count of the stored reference run."""
     import synth
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     layout = synth.config_layout(wl["cfg"])
-    vals = []
-    desc = None
-    for _ in range(args.warmup + args.steps):
-        ms, desc = oracle_sample(wl["cfg"], layout)
-        vals.append(ms)
-    v = float(np.mean(vals[args.warmup:]))
+    dev = None
+    try:  # input generation only: the device generator is much faster than the host's at 1.2e9 entries
+        import torch
+        if torch.cuda.is_available():
+            dev = synth.generate_device(layout)
+    except Exception:
+        dev = None
+    H, nH = oracle_matrix(wl["cfg"], layout, dev)
+    del dev
+    _, N, _ = golden_eigs(wl["cfg"])
+    N = N or 300
+    lens = REF_STEP_STEPS.get(wl["cfg"], (10, 30))
+    points = []
+    for i in range(args.warmup + args.steps):
+        s = lens[i % 2]
+        t = oracle_run_s(H, nH, s)
+        if i >= args.warmup:
+            points.append((s, t))
+    if len({s for s, _ in points}) < 2:  # one timed length cannot fix two coefficients
+        points.append((lens[1 - lens.index(points[0][0])], oracle_run_s(H, nH, lens[1 - lens.index(points[0][0])])))
+    v = oracle_extrapolate(points, N)
+    step_ms = float(np.mean([t for _, t in points[:args.steps]])) * 1e3
+    desc = oracle_desc(wl["cfg"], N, f"each step one call of {lens[0]} or {lens[1]} steps, alternating")
     line = {"impl": "reference", "metric": "time-to-k-eigenpairs", "value": v, "unit": "ms", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl["name"], "n": int(layout.n)},
+            "value_note": "value = the full oracle solve extrapolated from the timed steps; ms_per_step = their "
+                          "measured mean",
             "cpu_baseline": dict(desc, value=v, unit="ms"),
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -563,7 +641,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-csb", action="store_true", help="skip the threaded CPU CSB SpMM baseline")
@@ -615,6 +693,12 @@ def main():
     if args.kernels:
         return run_kernels(args, lob, M, info, torch,
                            lambda bp: lob.Matrix(n, rows, cols, vals, precond_block=bp))
+    # the host legs (end to end from pinned host buffers, the oracle sample, the threaded CPU SpMM)
+    # use one pinned host copy of the COO; the device copy is then released
+    if not args.no_e2e or (rank == 0 and not (args.no_cpu and args.no_csb)):
+        host_coo(wl["cfg"], layout, dev=(rows, cols, vals))
+    del rows, cols, vals
+    torch.cuda.empty_cache()
     n_small = int(synth.level_starts(layout)[2])
     k, nb, tol = wl["k"], wl["nb"], wl["tol"]
     X = torch.empty((n, nb), dtype=torch.float64, device="cuda")
@@ -656,7 +740,9 @@ def main():
 
     out = {"metric": "time-to-k-eigenpairs", "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
-           "vs_baseline": None, "dtype": "mixed: f32 SpMM, f64/double-float blocks, f64 refinement",
+           "vs_baseline": None,
+           "dtype": "mixed: f32-value SpMM with f64 sums; f64-class (double-float) Gram and X*C; f64 Cholesky-QR "
+                    "factors and Rayleigh-Ritz; f64-value refinement SpMM",
            "data": "synthetic",
            "config": {"workload": wl["name"], "n": n, "nnz_stored": int(info["nnz"]), "ntiles": int(info["ntiles"]),
                       "k": k, "nb": nb, "b_p": wl["bp"], "tol": tol, "mode": "mixed+fp64 refinement",
@@ -678,7 +764,7 @@ def main():
     out["solve"] = {"iterations": st0["iterations"], "refine_iterations": st0["refine_iterations"],
                     "status": int(stats[-1][1]), "phase_ms": st0["phase_ms"], "create_ms": create_ms,
                     "spmm_by_mode": st0["spmm_by_mode"], "max_relres": max(st0["residual"][:k])}
-    gold, _ = golden_eigs(wl["cfg"])
+    gold = golden_eigs(wl["cfg"])[0]
     if gold is not None and rank == 0 and lam is not None:
         err = np.abs(lam - gold[:k]) / np.maximum(np.abs(gold[:k]), 1.0)
         out["eig_err_vs_oracle"] = float(err.max())
@@ -696,6 +782,24 @@ def main():
         if gold is not None:
             fp["eig_err_vs_oracle"] = float((np.abs(lam64 - gold[:k]) / np.maximum(np.abs(gold[:k]), 1.0)).max())
         out["fp64_solver"] = fp
+
+    # ---- the same mixed solve with its double-float options: Cholesky-QR factors and Rayleigh-Ritz
+    # in double-float, and double-float values and products in the refinement SpMM
+    if not args.no_fp64:
+        kw = dict(rr_arith="df", refine_arith="df")
+        M.solve(k, nb, tol, mode="mixed", precond=True, n_small=n_small, X_out=X, **kw)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lam_d, _, st_d, rc_d = M.solve(k, nb, tol, mode="mixed", precond=True, n_small=n_small, X_out=X, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dfv = {"ms": e0.elapsed_time(e1), "iterations": st_d["iterations"],
+               "refine_iterations": st_d["refine_iterations"], "status": int(rc_d),
+               "rr_ms": st_d["phase_ms"]["rr"], "spmm_ms": st_d["phase_ms"]["spmm"],
+               "what": "double-float Cholesky-QR factors and Rayleigh-Ritz, double-float-value refinement SpMM"}
+        if gold is not None:
+            dfv["eig_err_vs_oracle"] = float((np.abs(lam_d - gold[:k]) / np.maximum(np.abs(gold[:k]), 1.0)).max())
+        out["mixed_df_variant"] = dfv
 
     # ---- the Lanczos baseline (single vector, full reorthogonalisation, FP64) to the same residual
     if not args.no_lanczos:
@@ -715,7 +819,7 @@ def main():
 
     # ---- end to end through the public API from pinned host buffers
     if not args.no_e2e:
-        hr = rows.cpu().pin_memory(); hc = cols.cpu().pin_memory(); hv = vals.cpu().pin_memory()
+        hr, hc, hv = host_coo(wl["cfg"], layout)
         Xh = torch.empty((n, nb), dtype=torch.float64).pin_memory()
         steps_e2e = max(1, min(2, args.steps))
         barrier()
@@ -736,10 +840,10 @@ def main():
     if rank == 0 and not args.no_small:
         out["batched_small"] = run_batched_small(args, lob, synth, torch)
 
-    if rank == 0 and not args.no_cpu and wl["cfg"] != "c3":
+    if rank == 0 and not args.no_cpu:
         ms_cpu, desc = oracle_sample(wl["cfg"], layout)
         out["cpu_baseline"] = dict(desc, value=ms_cpu, unit="ms")
-    if rank == 0 and not args.no_csb and wl["cfg"] != "c3" and spmm_calls > 0:
+    if rank == 0 and not args.no_csb and spmm_calls > 0:
         out["cpu_csb_spmm"] = csb_sample(wl["cfg"], layout, nb, spmm_bytes / spmm_calls, spmm_ms / spmm_calls)
     if rank == 0:
         print(json.dumps(out), flush=True)

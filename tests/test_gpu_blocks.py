@@ -57,11 +57,15 @@ def test_lincomb_exact_and_bound(mode, n, p, q):
 
 @pytest.mark.parametrize("bp", [1, 32, 64])
 def test_precond_matches_block_solve(bp):
-    """FP32 arithmetic (footnote 5): the FP32 eigendecomposition is backward stable, H~ + E with
-    ||E|| ~ b_p u32 ||H~||, and (H~ + E - mu)^{-1} - (H~ - mu)^{-1} ~ (H~ - mu)^{-1} E (H~ - mu)^{-1},
-    so the relative error is bounded by ~ b_p u32 kappa_j with kappa_j = ||H~|| / min|lambda - mu_j|
-    over the blocks (at least 1; the FP32 Jacobi's orthogonality error adds a constant);
-    bound 16 b_p u32 kappa_j."""
+    """FP32 arithmetic (footnote 5). The bound, derived to first order:
+      - the S sweeps of FP32 cyclic Jacobi give H~ + E = Q diag(lambda) Q^T with Q orthogonal to
+        ||Q^T Q - I|| <= c_J b_p u32 and ||E|| <= c_J b_p u32 ||H~||, c_J about the sweep count
+        (each sweep touches every entry with b_p - 1 rotations of relative error ~u32);
+      - (H~ + E - mu)^{-1} - (H~ - mu)^{-1} ~ -(H~ - mu)^{-1} E (H~ - mu)^{-1}, so E costs
+        c_J b_p u32 kappa_j relative, kappa_j = ||H~|| / min |lambda - mu_j| over the blocks;
+      - the apply w = Q f(lambda - mu) Q^T r adds two length-b_p FP32 products, 2 b_p u32 kappa_j.
+    With c_J <= 14 (this matrix family converges in 6-10 sweeps): 16 b_p u32 kappa_j. Measured on
+    the GPU, max err / (b_p u32 kappa_j) = 1.9 (b_p = 1), 6.0 (32), 7.7 (64)."""
     import paper_1609_01689_gb300 as lob
     L = synth.layout(3000, 7, 40, 4)
     r, c, v = synth.generate(L)
@@ -90,10 +94,11 @@ def test_precond_krylov_matches_oracle(solve, steps, bp):
     """The Krylov solves of eq. 11 run in each block's FP32 eigenbasis on the GPU and by dense
     Lanczos in FP64 in the oracle (independent algorithms for the same iterate). Shifts below
     every block's spectrum (definite systems) for FOM / minimal residual, inside it for the
-    absolute-value solve. The FP32 eigendecomposition is backward stable (error ~ b_p u32 ||H~||)
-    and the iterate is a fixed low-degree rational function of the projected quantities, so the
-    relative error is bounded like the direct solve's: 16 b_p u32 kappa_j, kappa_j =
-    ||H~|| / min|lambda - mu_j|."""
+    absolute-value solve. The FP32 eigendecomposition carries the same error as for the direct
+    solve (c_J b_p u32 kappa_j with c_J <= 14, see test_precond_matches_block_solve), and the
+    iterate is a fixed low-degree rational function of the projected quantities, formed with two
+    length-b_p FP32 products, so the same bound holds: 16 b_p u32 kappa_j, kappa_j =
+    ||H~|| / min|lambda - mu_j|. Measured on the GPU, max err / (b_p u32 kappa_j) <= 3.4."""
     import paper_1609_01689_gb300 as lob
     L = synth.layout(2500, 7, 40, 5)
     r, c, v = synth.generate(L)
@@ -165,8 +170,12 @@ def test_precond_tiles_match_oracle(solve, steps, ncol):
     """Eq. 11 on the diagonal tiles (Section 4.3), the blocks being whole 256-row tiles: Krylov
     steps on the sparse tile in FP32 on the GPU, dense Lanczos in FP64 in the oracle. The last
     tile is partial (n = 2,500), and 20 columns take two passes of the kernel. Shifts below every
-    tile's spectrum (definite systems). Bound as for the dense blocks: 16 b u32 kappa_j with
-    b = 256 and kappa_j = ||H~|| / min |lambda - mu_j| over the tiles."""
+    tile's spectrum (definite systems). No eigendecomposition is involved: each Lanczos quantity
+    (a tile-row product of at most b terms, a dot product of b terms) carries a relative error of
+    at most gamma_b ~ b u32, and the s-step projected solve passes a perturbation of its
+    coefficients on with a factor of at most kappa_j = ||H~|| / min |lambda - mu_j| over the tiles,
+    so to first order the error is at most (s + 1) b u32 kappa_j <= 4 b u32 kappa_j (b = 256).
+    Measured on the GPU, max err / (b u32 kappa_j) <= 0.009."""
     import paper_1609_01689_gb300 as lob
     L = synth.layout(2500, 7, 40, 5)
     r, c, v = synth.generate(L)
@@ -186,7 +195,7 @@ def test_precond_tiles_match_oracle(solve, steps, ncol):
     for lam_b in blocks:
         d = np.abs(lam_b[:, None] - mu[None, :])
         kappa = np.maximum(kappa, np.abs(lam_b).max() / d.min(axis=0))
-    assert np.all(err <= 16 * 256 * 2.0 ** -24 * kappa), (err, kappa)
+    assert np.all(err <= 4 * 256 * 2.0 ** -24 * kappa), (err, kappa)
 
 
 def test_precond_tiles_rejects_what_it_cannot_do():
@@ -211,8 +220,8 @@ def test_precond_tiles_rejects_what_it_cannot_do():
 def _breakdown_matrix(bp, nblk, mu, dense, seed):
     """Block-diagonal H whose even blocks make two-step FOM break down for column 0 and whose
     odd blocks make one-step FOM break down for column 1 (constructions and closed forms in
-    test_oracle_lobpcg_parts); columns 2-3 are random. Every block's spectrum sits at mu - 1 and
-    above, so the random columns are ordinary indefinite systems."""
+    test_oracle_lobpcg_parts); those columns are zero in the other blocks, and columns 2-3 are
+    random. Every block's spectrum sits at mu - 1 and above."""
     from test_oracle_lobpcg_parts import BREAK1_A, BREAK1_X, BREAK2_A, BREAK2_X, fom_breakdown_block
     rng = np.random.default_rng(seed)
     n = bp * nblk
@@ -225,8 +234,8 @@ def _breakdown_matrix(bp, nblk, mu, dense, seed):
         B2, r2 = fom_breakdown_block(bp, mu, rng, c2, BREAK2_A, BREAK2_X, dense)
         B1, r1 = fom_breakdown_block(bp, mu, rng, c1, BREAK1_A, BREAK1_X, dense)
         Hd[s, s] = B2 if b % 2 == 0 else B1
-        R[s, 0] = r2 if b % 2 == 0 else rng.standard_normal(bp)
-        R[s, 1] = r1 if b % 2 == 1 else rng.standard_normal(bp)
+        R[s, 0] = r2 if b % 2 == 0 else 0.0
+        R[s, 1] = r1 if b % 2 == 1 else 0.0
     # a few couplings between blocks: the preconditioner must ignore them
     for _ in range(3 * nblk):
         i, j = sorted(rng.integers(0, n, 2))
@@ -246,15 +255,17 @@ def test_precond_fom_breakdown_matches_oracle(bp, dense, steps):
     sparse tile in FP32). The even blocks give column 0 an exactly singular 2 x 2 projected
     matrix and the odd blocks give column 1 r^T A r = 0, so the FP32 pivots are rounding noise,
     far below the 1e-4 threshold, and both sides must take the minimal-residual fallback. The
-    oracle's results there are pinned to closed forms on the CPU. Error bound: FP32 work on the
-    block, relative to the largest entry of the reference column, 8 b u32 kappa (kappa =
-    ||H~|| / min |lambda - mu|, here <= (max diagonal) / 1), plus an absolute FP32 floor of
+    oracle's results there are pinned to closed forms on the CPU. The random columns 2-3 take a
+    shift below every block's spectrum (definite systems): with an indefinite shift a random
+    right-hand side can put a pivot near the threshold, where FP32 and FP64 may take different
+    branches. Error bound: FP32 work on the block, relative to the largest entry of the reference
+    column, 8 b u32 kappa (kappa = ||H~|| / min |lambda - mu|), plus an absolute FP32 floor of
     b u32 ||r|| kappa for the one-step column whose exact iterate is zero."""
     import paper_1609_01689_gb300 as lob
     mu = 5.0
     H, Hd, R = _breakdown_matrix(bp, 2, mu, dense, 7 * bp + steps)
     M = lob.Matrix(H.n, H.rows, H.cols, H.vals, precond_block=bp)
-    muv = np.full(4, mu)
+    muv = np.array([mu, mu, mu - 5.0, mu - 9.0])
     W = M.precond_apply(t(muv), t(R), solve="fom", steps=steps).cpu().numpy()
     bounds = oracle.uniform_bounds(H.n, bp)
     ref = oracle.block_krylov(H, bounds, muv, R, "fom", steps)
@@ -263,8 +274,8 @@ def test_precond_fom_breakdown_matches_oracle(bp, dense, steps):
     for i in range(len(bounds) - 1):
         s = slice(bounds[i], bounds[i + 1])
         lam = np.linalg.eigvalsh(Hd[s, s])
-        kappa = np.abs(lam).max() / np.abs(lam - mu).min()
         for j in range(4):
+            kappa = np.abs(lam).max() / np.abs(lam - muv[j]).min()
             scale = np.abs(ref[s, j]).max()
             err = np.abs(W[s, j] - ref[s, j]).max()
             floor = bp * u32 * kappa * np.linalg.norm(R[s, j])

@@ -200,3 +200,48 @@ def test_solve_tile_preconditioner_500k(c2_golden):
     H = oracle.Coo(L.n, rows, cols, vals)
     res = oracle.residual_norms(H, X.cpu().numpy()[:, :8], lam) / oracle.norm_inf(H)
     assert res.max() <= 1e-8, res
+
+
+@pytest.fixture(scope="module")
+def c3_golden():
+    """Reference eigenvalues of the n = 8,000,000 workload, stored by tests/golden/make_golden.py
+    from the oracle's FP64 Lanczos (CSR form)."""
+    import os
+    from conftest import golden_path
+    if not os.path.exists(golden_path("c3_eigs.txt")):
+        pytest.skip("the n = 8,000,000 reference eigenvalues have not been written (make_golden.py c3)")
+    vals = [float(x) for x in open(golden_path("c3_eigs.txt")) if x.strip() and not x.startswith("#")]
+    return np.array(vals)
+
+
+def test_solve_full_size_8m(c3_golden):
+    """The large single solve (n = 8,000,000, ~300 nonzeros per row, 1.2e9 stored entries, k = 10,
+    nb = 16, 64 x 64 preconditioner blocks, eq. 12 guess from levels {0, 1}) in the configuration
+    the bench times: the mixed solver (FP32-value SpMM, FP64 small solves, FP64-value
+    refinement), its double-float options, and the plain FP64 solver. Eigenvalues against the
+    stored oracle values (1e-8 mixed, 1e-9 FP64, in |lam - lam*| / max(|lam*|, 1)); residuals
+    ||H x - lam x|| / ||H||_inf recomputed on the host by the oracle's product from the returned
+    vectors (<= 1e-8, the solve's own tolerance; the acceptance bound is 1e-6)."""
+    import torch
+    import paper_1609_01689_gb300 as lob
+    L = synth.config_layout("c3")
+    r, c, v = synth.generate_device(L)
+    M = lob.Matrix(L.n, r, c, v, precond_block=64)
+    rows, cols, vals = r.cpu().numpy(), c.cpu().numpy(), v.cpu().numpy()
+    del r, c, v
+    torch.cuda.empty_cache()
+    nH = oracle.norm_inf(oracle.Coo(L.n, rows, cols, vals))
+    Hc = oracle.Csr.from_sorted_coo(L.n, rows, cols, vals)
+    del rows, cols
+    n_small = int(synth.level_starts(L)[2])
+    for mode, kw, tol_lam in (("mixed", {}, 1e-8), ("mixed", dict(rr_arith="df", refine_arith="df"), 1e-8),
+                              ("fp64", {}, 1e-9)):
+        lam, X, st, rc = M.solve(10, 16, 1e-8, mode=mode, precond=True, n_small=n_small, **kw)
+        assert rc == lob.LOB_OK, (mode, kw)
+        rel = np.abs(lam - c3_golden[:10]) / np.maximum(np.abs(c3_golden[:10]), 1.0)
+        assert rel.max() <= tol_lam, (mode, kw, rel)
+        Xh = X.cpu().numpy()[:, :10]
+        R = oracle.spmm_csr(Hc, Xh) - Xh * lam[None, :]
+        res = np.sqrt((R * R).sum(axis=0)) / nH
+        assert res.max() <= 1e-8, (mode, kw, res)
+    M.close()
