@@ -566,9 +566,13 @@ def run_kernels(args, lob, M, info, torch, make_matrix):
     for mode, sv in (("mixed", 4), ("df64", 8), ("fp64", 8)):
         byts = nnz * (sv + 4) + ntiles * 12 + (nt + 1) * 8 + n * nb * (8 + 8)
         timeit("spmm_" + mode, lambda mode=mode: M.spmm(X, mode), algorithmic_bytes=byts)
-    timeit("gram_df_48x48", lambda: lob.gram(S, T, "mixed"), df_macs=n * 48 * 48, algorithmic_bytes=n * 96 * 8)
-    timeit("lincomb_df_48x16", lambda: lob.lincomb(S, Cm, "mixed"), df_macs=n * 48 * 16,
+    timeit("gram_df_48x48", lambda: lob.gram(S, T, "df64"), df_macs=n * 48 * 48, algorithmic_bytes=n * 96 * 8)
+    timeit("gram_tc_48x48", lambda: lob.gram(S, T, "mixed"), algorithmic_bytes=n * 96 * 8)
+    timeit("lincomb_df_48x16", lambda: lob.lincomb(S, Cm, "df64"), df_macs=n * 48 * 16,
            algorithmic_bytes=n * (48 + 16) * 8)
+    timeit("lincomb_tc_48x16", lambda: lob.lincomb(S, Cm, "mixed"), algorithmic_bytes=n * (48 + 16) * 8)
+    C48 = torch.randn((48, 48), dtype=torch.float64, device="cuda", generator=g)
+    timeit("lincomb_tc_48x48", lambda: lob.lincomb(S, C48, "mixed"), algorithmic_bytes=n * (48 + 48) * 8)
     timeit("rayleigh_ritz_df_48", lambda: lob.rayleigh_ritz(Gs, Ms, "mixed"), reps=20)
     mu = torch.linspace(-5.0, -4.0, nb, dtype=torch.float64, device="cuda")
     # the preconditioner both ways: dense 32 x 32 blocks (eigenbasis FOM) and the diagonal tiles

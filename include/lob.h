@@ -125,20 +125,28 @@ int lob_spmm(lob_matrix* m, int32_t mode, const double* X, double* Y, int32_t nb
 /* Synchronise `stream` and report whether any SpMM kernel on m gave up on a bounded wait since
  * the last check (LOB_ERR_CUDA; the products it took part in are not valid; the flag is then
  * cleared) or not (LOB_OK). The flag belongs to the matrix: products of one matrix running on
- * several streams share it. lob_solve checks it itself. Errors: LOB_ERR_ARG, LOB_ERR_CUDA. */
+ * several streams share it. The tensor-core block products (lob_gram, lob_lincomb) have one such
+ * flag per device, checked here too; m may be NULL to check only that one. lob_solve checks both
+ * itself. Errors: LOB_ERR_CUDA. */
 int lob_check(lob_matrix* m, void* stream);
 
 /* ---- the pieces of one LOBPCG iteration, each exposed for testing and reuse ---- */
 
 /* Block inner product G = A^T B (Section 4.4, the tall-skinny X^T Y): A is n x p (leading
  * dimension lda), B is n x q (ldb), G is p x q row-major. All device. p, q <= 192.
- * mode: LOB_SPMM_FP64 for native FP64, LOB_SPMM_MIXED for FP64-class double-float
- * arithmetic on the FP32 pipes (about 2^-44 relative). */
+ * mode: LOB_SPMM_FP64 for native FP64 fused multiply-adds; LOB_SPMM_MIXED for FP64-class
+ * arithmetic (about 2^-44 relative to |A|^T |B|): on the tensor cores when p, q <= 64 (each
+ * operand split exactly into seven bf16 digits per scaling group, the digit products summed
+ * exactly in FP32 tensor memory, the levels combined in double-float; Ozaki et al.'s error-free
+ * splitting), otherwise double-float on the FP32 pipes; LOB_SPMM_DF64 for that double-float
+ * kernel always. The tensor-core path treats entries below 2^-126 of the scale of their group's
+ * products as zero. */
 int lob_gram(int64_t n, int32_t p, const double* A, int32_t lda, int32_t q, const double* B, int32_t ldb, double* G,
              int32_t mode, void* stream);
 
 /* Linear combination Y = A C (Section 4.4, eq. 7): A n x p (lda), C p x q row-major, Y n x q
- * (ldy). Device. p, q <= 192. Y must not overlap A. mode as lob_gram. */
+ * (ldy). Device. p, q <= 192. Y must not overlap A. mode as lob_gram (LOB_SPMM_MIXED: tensor
+ * cores for p, q <= 64, the scaling groups being the rows of A and the columns of C). */
 int lob_lincomb(int64_t n, int32_t p, const double* A, int32_t lda, int32_t q, const double* C, double* Y,
                 int32_t ldy, int32_t mode, void* stream);
 

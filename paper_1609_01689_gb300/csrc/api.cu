@@ -147,11 +147,12 @@ int lob_spmm(lob_matrix* m, int32_t mode, const double* X, double* Y, int32_t nb
 }
 
 int lob_check(lob_matrix* m, void* stream) {
-  if (!m) return LOB_ERR_ARG;
-  const int f = lob_matrix_fault_take(m, (cudaStream_t)stream);
-  if (f < 0) return LOB_ERR_CUDA;
-  if (f) {
-    fprintf(stderr, "lob: an SpMM kernel gave up on a bounded wait; its product is not valid\n");
+  const int fm = m ? lob_matrix_fault_take(m, (cudaStream_t)stream) : 0;
+  const int fo = lob_oz_fault_take((cudaStream_t)stream);
+  if (fm < 0 || fo < 0) return LOB_ERR_CUDA;
+  if (fm || fo) {
+    fprintf(stderr, "lob: a %s kernel gave up on a bounded wait; its product is not valid\n",
+            fm ? "SpMM" : "tensor-core block");
     return LOB_ERR_CUDA;
   }
   return LOB_OK;

@@ -459,12 +459,16 @@ static void gram_go(dim3 grid, cudaStream_t st, int U, int64_t n, int p, const d
 int lob_gram_launch_ws(int64_t n, int p, const double* A, int lda, int q, const double* B, int ldb, double* G,
                        int mode, double* work, cudaStream_t st, int sym) {
   if (sym && p != q) return LOB_ERR_ARG;
+  // FP64-class products go to the tensor cores (ozaki.cu) when they fit; LOB_SPMM_DF64 keeps the
+  // double-float CUDA-core kernel
+  if (mode == LOB_SPMM_MIXED && lob_oz_fits(p, q))
+    return lob_gram_oz_launch(n, p, A, lda, nullptr, 0, q, B, ldb, G, nullptr, work, st);
   const int e = gram_edge(p, q);
   const int ta = (p + e - 1) / e, tb = (q + e - 1) / e;
   const int nch = nchunks_for(n, sym ? ta * (ta + 1) / 2 : ta * tb, e);
   const int64_t rpc = (n + nch - 1) / nch;
   dim3 grid(nch, ta, tb);
-  if (mode == LOB_SPMM_MIXED) gram_go<true>(grid, st, e / 16, n, p, A, lda, q, B, ldb, work, rpc, sym);
+  if (mode != LOB_SPMM_FP64) gram_go<true>(grid, st, e / 16, n, p, A, lda, q, B, ldb, work, rpc, sym);
   else gram_go<false>(grid, st, e / 16, n, p, A, lda, q, B, ldb, work, rpc, sym);
   const int pq = p * q;
   (k_gram_reduce<<<(pq * 32 + 255) / 256, 256, 0, st>>>(nch, pq, q, sym, e, work, G), LOB_LAUNCHED());
@@ -475,9 +479,10 @@ int lob_gram_launch_ws(int64_t n, int p, const double* A, int lda, int q, const 
 int lob_gram_launch(int64_t n, int p, const double* A, int lda, int q, const double* B, int ldb, double* G, int mode,
                     cudaStream_t st) {
   if (n < 1 || p < 1 || q < 1 || p > 192 || q > 192 || lda < p || ldb < q || !A || !B || !G) return LOB_ERR_ARG;
-  if (mode != LOB_SPMM_FP64 && mode != LOB_SPMM_MIXED) return LOB_ERR_ARG;
+  if (mode != LOB_SPMM_FP64 && mode != LOB_SPMM_MIXED && mode != LOB_SPMM_DF64) return LOB_ERR_ARG;
   double* work = nullptr;
-  LOB_CUDA(cudaMallocAsync((void**)&work, lob_gram_work_doubles(n, p, q) * sizeof(double), st));
+  const size_t wd = lob_gram_work_doubles(n, p, q), wo = lob_gram_oz_work_doubles();
+  LOB_CUDA(cudaMallocAsync((void**)&work, (wd > wo ? wd : wo) * sizeof(double), st));
   int rc = lob_gram_launch_ws(n, p, A, lda, q, B, ldb, G, mode, work, st);
   cudaFreeAsync(work, st);
   return rc;
@@ -486,18 +491,19 @@ int lob_gram_launch(int64_t n, int p, const double* A, int lda, int q, const dou
 int lob_lincomb_launch(int64_t n, int p, const double* A, int lda, int q, const double* C, double* Y, int ldy,
                        int mode, cudaStream_t st, const double* D, int ldd) {
   if (n < 1 || p < 1 || q < 1 || p > 192 || q > 192 || lda < p || ldy < q || !A || !C || !Y) return LOB_ERR_ARG;
-  if (mode != LOB_SPMM_FP64 && mode != LOB_SPMM_MIXED) return LOB_ERR_ARG;
+  if (mode != LOB_SPMM_FP64 && mode != LOB_SPMM_MIXED && mode != LOB_SPMM_DF64) return LOB_ERR_ARG;
+  if (mode == LOB_SPMM_MIXED && lob_oz_fits(p, q)) return lob_lincomb_oz_launch(n, p, A, lda, q, C, Y, ldy, st, D, ldd);
   // four rows a thread when the CTA's rows of A fit comfortably in shared memory, else one
   const int RM = p <= 64 ? 4 : 1;
   dim3 grid((unsigned)((n + 16 * RM - 1) / (16 * RM)), (q + 15) / 16);
-  const size_t smem = (16ull * RM * (p | 1) + 16ull * p) * (mode == LOB_SPMM_MIXED ? sizeof(float2) : sizeof(double));
+  const size_t smem = (16ull * RM * (p | 1) + 16ull * p) * (mode != LOB_SPMM_FP64 ? sizeof(float2) : sizeof(double));
   auto go = [&](auto kern) -> int {
     LOB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     (kern<<<grid, 256, smem, st>>>(n, p, A, lda, q, C, Y, ldy, D, ldd), LOB_LAUNCHED());
     LOB_CUDA(cudaGetLastError());
     return LOB_OK;
   };
-  if (mode == LOB_SPMM_MIXED) return RM == 4 ? go(k_lincomb<true, 4>) : go(k_lincomb<true, 1>);
+  if (mode != LOB_SPMM_FP64) return RM == 4 ? go(k_lincomb<true, 4>) : go(k_lincomb<true, 1>);
   return RM == 4 ? go(k_lincomb<false, 4>) : go(k_lincomb<false, 1>);
 }
 

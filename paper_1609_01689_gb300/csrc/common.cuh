@@ -142,6 +142,17 @@ void lob_free_tiles(lob_tiles* T);
 int lob_build_precond(const lob_coo* Hdev, int bp, int64_t n, cudaStream_t st, lob_precond* P);
 void lob_free_precond(lob_precond* P);
 
+// SMs of the current device (-1 if the query fails).
+int lob_sm_count();
+// Tensor-core FP64-class block products (ozaki.cu): p, q <= 64.
+bool lob_oz_fits(int p, int q);
+size_t lob_gram_oz_work_doubles();
+int lob_gram_oz_launch(int64_t n, int p, const double* L0, int ld0, const double* L1, int ld1, int q,
+                       const double* R, int ldr, double* G0, double* G1, double* work, cudaStream_t st);
+int lob_lincomb_oz_launch(int64_t n, int p, const double* A, int lda, int q, const double* C, double* Y, int ldy,
+                          cudaStream_t st, const double* D = nullptr, int ldd = 0);
+int lob_oz_fault_take(cudaStream_t st);
+
 // Grow the matrix's staged-X scratch to at least `need` bytes (synchronous allocation).
 int lob_ensure_xs(const lob_matrix* m, size_t need);
 // Y = H X over the active leading n_act x n_act block (n_act <= n; rows/cols >= n_act are

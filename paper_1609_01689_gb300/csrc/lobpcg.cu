@@ -25,6 +25,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <mutex>
 #include <vector>
@@ -366,7 +367,8 @@ struct lob_task {
     LOB_TRY(G.alloc(mm * mm, st)); LOB_TRY(Mm.alloc(mm * mm, st)); LOB_TRY(Cc.alloc(mm * mm, st));
     LOB_TRY(Cx.alloc(mm * mm, st)); LOB_TRY(theta.alloc(mm, st)); LOB_TRY(thw.alloc(mm, st));
     LOB_TRY(MmP.alloc(mm * mm, st)); LOB_TRY(CcP.alloc(mm * mm, st)); LOB_TRY(thP.alloc(mm, st));
-    LOB_TRY(work.alloc(lob_gram_work_doubles(n, 1, 1) * mm * mm, st));  // bound over every (p, q) <= m
+    // bound over every (p, q) <= m, and the tensor-core Gram's partial sums
+    LOB_TRY(work.alloc(std::max(lob_gram_work_doubles(n, 1, 1) * mm * mm, lob_gram_oz_work_doubles()), st));
     LOB_TRY(rrwork.alloc(lob_rr_work_doubles((int)mm), st));
     LOB_TRY(part.alloc((size_t)nblk(n) * 2 * mm, st));
     LOB_TRY(relres_d.alloc(nb, st)); LOB_TRY(mu.alloc(nb, st)); LOB_TRY(C2.alloc(mm * mm, st));
@@ -389,6 +391,10 @@ struct lob_task {
 
   // projected eigenproblem and Cholesky-QR factors in the task's small-solve arithmetic (native
   // FP64, or double-float when the options ask for it)
+  // Arithmetic of the block products other than the fused Rayleigh-Ritz Grams: native FP64, or
+  // double-float on the CUDA cores in MIXED (the tensor-core kernels serve the fused pair)
+  int bmode() const { return blas_mode == LOB_SPMM_MIXED ? LOB_SPMM_DF64 : blas_mode; }
+
   int rr(int mm, const double* Gp, const double* Mp, double* th, double* Cp, int slot, int chol_only) {
     if (rr_mode == LOB_SPMM_MIXED)
       return lob_rr_launch_df(mm, Gp, Mp, th, Cp, info_slot(slot), rrwork.p, st, chol_only);
@@ -437,9 +443,15 @@ struct lob_task {
   int rr_begin(int mm) {
     {
       Timer t(clk(), st, ph(PH_GRAM));
-      // both symmetric (H is): only their upper triangles are formed (and read by the solve)
-      LOB_TRY(lob_gram_launch_ws(n_act, mm, S.p, ldS, mm, HS.p, ldS, G.p, blas_mode, work.p, st, 1));
-      LOB_TRY(lob_gram_launch_ws(n_act, mm, S.p, ldS, mm, S.p, ldS, Mm.p, blas_mode, work.p, st, 1));
+      if (blas_mode == LOB_SPMM_MIXED && lob_oz_fits(mm, mm)) {
+        // one tensor-core pass for both: M = S^T S and (H S)^T S, the transpose of G (equal to G for
+        // the symmetric H; the solve reads the upper triangles)
+        LOB_TRY(lob_gram_oz_launch(n_act, mm, S.p, ldS, HS.p, ldS, mm, S.p, ldS, Mm.p, G.p, work.p, st));
+      } else {
+        // both symmetric (H is): only their upper triangles are formed (and read by the solve)
+        LOB_TRY(lob_gram_launch_ws(n_act, mm, S.p, ldS, mm, HS.p, ldS, G.p, bmode(), work.p, st, 1));
+        LOB_TRY(lob_gram_launch_ws(n_act, mm, S.p, ldS, mm, S.p, ldS, Mm.p, bmode(), work.p, st, 1));
+      }
     }
     Timer t(clk(), st, ph(PH_RR));
     LOB_TRY(rr(mm, G.p, Mm.p, theta.p, Cc.p, SLOT_RR, 0));
@@ -451,8 +463,8 @@ struct lob_task {
   // the product goes straight into place; wider products go through Tn.
   int lincomb_into(int p, const double* A, int lda, int q, const double* C, double* Y, int ldy,
                    const double* D = nullptr, int ldd = 0) {
-    if (q <= 16) return lob_lincomb_launch(n_act, p, A, lda, q, C, Y, ldy, blas_mode, st, D, ldd);
-    LOB_TRY(lob_lincomb_launch(n_act, p, A, lda, q, C, Tn.p, q, blas_mode, st, D, ldd));
+    if (q <= 16) return lob_lincomb_launch(n_act, p, A, lda, q, C, Y, ldy, bmode(), st, D, ldd);
+    LOB_TRY(lob_lincomb_launch(n_act, p, A, lda, q, C, Tn.p, q, bmode(), st, D, ldd));
     (k_copy_cols<<<nblk(n_act * q), BS, 0, st>>>(n_act, q, Tn.p, q, nullptr, Y, ldy), LOB_LAUNCHED());
     return LOB_OK;
   }
@@ -461,7 +473,7 @@ struct lob_task {
   int cholqr_begin(int col0, int ncol, double* Mb, double* Cb, double* thb, int slot) {
     Timer t(clk(), st, ph(PH_ORTH));
     const double* B = S.p + col0;
-    LOB_TRY(lob_gram_launch_ws(n_act, ncol, B, ldS, ncol, B, ldS, Mb, blas_mode, work.p, st, 1));
+    LOB_TRY(lob_gram_launch_ws(n_act, ncol, B, ldS, ncol, B, ldS, Mb, bmode(), work.p, st, 1));
     LOB_TRY(rr(ncol, Mb, Mb, thb, Cb, slot, 1));
     return read_info(slot);
   }
@@ -499,8 +511,8 @@ struct lob_task {
                                                                     C2.p, nb),
        LOB_LAUNCHED());
       (k_copy_cols<<<nblk((int64_t)nb * nb), BS, 0, st>>>(nb, nb, Cc.p, mm, nullptr, Cx.p, nb), LOB_LAUNCHED());
-      LOB_TRY(lob_lincomb_launch(n_act, mm - nb, S.p + nb, ldS, nb, C2.p, P.p, nb, blas_mode, st));
-      LOB_TRY(lob_lincomb_launch(n_act, mm - nb, HS.p + nb, ldS, nb, C2.p, HP.p, nb, blas_mode, st));
+      LOB_TRY(lob_lincomb_launch(n_act, mm - nb, S.p + nb, ldS, nb, C2.p, P.p, nb, bmode(), st));
+      LOB_TRY(lob_lincomb_launch(n_act, mm - nb, HS.p + nb, ldS, nb, C2.p, HP.p, nb, bmode(), st));
       LOB_TRY(lincomb_into(nb, S.p, ldS, nb, Cx.p, S.p, ldS, P.p, nb));
       LOB_TRY(lincomb_into(nb, HS.p, ldS, nb, Cx.p, HS.p, ldS, HP.p, nb));
     }
@@ -707,7 +719,7 @@ int lob_task::step() {
           // W <- W - X (X^T W), then Cholesky-QR (step 7)
           {
             Timer t(clk(), st, ph(PH_ORTH));
-            LOB_TRY(lob_gram_launch_ws(n_act, nb, S.p, ldS, na, S.p + nb, ldS, Z.p, blas_mode, work.p, st));
+            LOB_TRY(lob_gram_launch_ws(n_act, nb, S.p, ldS, na, S.p + nb, ldS, Z.p, bmode(), work.p, st));
             (k_proj_coef<<<nblk((nb + na) * na), BS, 0, st>>>(nb, na, Z.p, C2.p), LOB_LAUNCHED());
             LOB_TRY(lincomb_into(nb + na, S.p, ldS, na, C2.p, S.p + nb, ldS));
           }
@@ -908,7 +920,7 @@ int lob_solve_impl(lob_matrix* m, int32_t k, int32_t nb, double tol, const doubl
   }
   lob_task_destroy(t);
   // a product that gave up on a bounded wait voids whatever the iteration made of it
-  const int fault = lob_matrix_fault_take(m, stream);
+  const int fault = lob_matrix_fault_take(m, stream) | lob_oz_fault_take(stream);
   if (fault != 0) {
     fprintf(stderr, "lob: an SpMM kernel gave up on a bounded wait; the result is not valid\n");
     rc = LOB_ERR_CUDA;

@@ -1184,15 +1184,6 @@ leave:
   ring_leave(ctl, full, D + 1, NW);
 }
 
-// SMs of the current device (-1 if the query fails).
-int lob_sm_count() {
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-    cudaGetLastError();
-    return -1;
-  }
-  return sms;
-}
 
 template <int NB>
 int launch_df(const lob_matrix* m, const double* X, double* Y, int nb, int64_t n_act, cudaStream_t st) {
@@ -1344,6 +1335,16 @@ int batch_class(const lob_matrix* const* ms, const double* const* X, double* con
 }
 
 }  // namespace
+
+// SMs of the current device (-1 if the query fails).
+int lob_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return sms;
+}
 
 int lob_spmm_batch_launch(const lob_matrix* const* ms, const double* const* X, double* const* Y, const int* ncol,
                           const int* mode, const int64_t* nact, int njobs, lob_spmm_job* jobs_host,

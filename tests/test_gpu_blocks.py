@@ -259,8 +259,10 @@ def test_precond_fom_breakdown_matches_oracle(bp, dense, steps):
     shift below every block's spectrum (definite systems): with an indefinite shift a random
     right-hand side can put a pivot near the threshold, where FP32 and FP64 may take different
     branches. Error bound: FP32 work on the block, relative to the largest entry of the reference
-    column, 8 b u32 kappa (kappa = ||H~|| / min |lambda - mu|), plus an absolute FP32 floor of
-    b u32 ||r|| kappa for the one-step column whose exact iterate is zero."""
+    column, 8 b u32 kappa (kappa = ||H~|| / min |lambda - mu|), plus an absolute floor for the
+    one-step column whose exact iterate is zero: there the FP32 pivot r^T A r carries the block
+    eigendecomposition's error c_J b u32 ||A|| ||r||^2 (c_J <= 14, as in
+    test_precond_matches_block_solve), so the fallback iterate is at most 16 b u32 kappa ||r||."""
     import paper_1609_01689_gb300 as lob
     mu = 5.0
     H, Hd, R = _breakdown_matrix(bp, 2, mu, dense, 7 * bp + steps)
@@ -278,5 +280,64 @@ def test_precond_fom_breakdown_matches_oracle(bp, dense, steps):
             kappa = np.abs(lam).max() / np.abs(lam - muv[j]).min()
             scale = np.abs(ref[s, j]).max()
             err = np.abs(W[s, j] - ref[s, j]).max()
-            floor = bp * u32 * kappa * np.linalg.norm(R[s, j])
+            floor = 16 * bp * u32 * kappa * np.linalg.norm(R[s, j])
             assert err <= 8 * bp * u32 * kappa * scale + floor, (i, j, err, scale, kappa)
+
+
+def _scaled(rng, n, p, spread):
+    """Normal entries with per-column and per-row-block scales 2^e, e uniform in [-spread, spread]
+    (the digit split's scaling groups are columns of 128-row chunks for the Gram and rows for the
+    linear combination), plus one all-zero column."""
+    X = rng.standard_normal((n, p))
+    X *= 2.0 ** rng.integers(-spread, spread + 1, p)[None, :]
+    X *= 2.0 ** rng.integers(-spread, spread + 1, (n + 127) // 128).repeat(128)[:n, None]
+    X[:, p // 2] = 0.0
+    return X
+
+
+@pytest.mark.parametrize("n,p,q", [(1, 1, 1), (127, 16, 16), (128, 48, 48), (129, 33, 17), (1000, 64, 64),
+                                   (100_000, 48, 48), (70_000, 1, 64), (5000, 64, 1)])
+@pytest.mark.parametrize("spread", [0, 20])
+def test_gram_tensor_cores(n, p, q, spread):
+    """The FP64-class Gram on the tensor cores (p, q <= 64; Ozaki et al.'s error-free digit split).
+    Bound, from the split: each operand is truncated at 2^-49 of its scaling group's largest entry
+    and every digit product is exact, so per term |err| <= 2^-48 max_group|a| |b| + 2^-48 |a|
+    max_group|b|, plus double-float sums (~2^-47 per term). Against the oracle, in the form
+    |G - G*| <= 2^-44 (|A|^T |B| + colmax-weighted sums), checked against the double-float kernel
+    too. Ragged chunks (n = 127, 129), single rows and columns, column and row-block scales
+    spanning 2^40, and a zero column."""
+    import paper_1609_01689_gb300 as lob
+    rng = np.random.default_rng(n + 7 * p + q + spread)
+    A = _scaled(rng, n, p, spread)
+    B = _scaled(rng, n, q, spread)
+    G = lob.gram(t(A), t(B), "mixed").cpu().numpy()
+    ref = oracle.gram(A, B)
+    # group maxima over 128-row chunks, per column
+    nc = (n + 127) // 128
+    pad = nc * 128 - n
+    Am = np.abs(np.vstack([A, np.zeros((pad, p))])).reshape(nc, 128, p).max(axis=1).repeat(128, axis=0)[:n]
+    Bm = np.abs(np.vstack([B, np.zeros((pad, q))])).reshape(nc, 128, q).max(axis=1).repeat(128, axis=0)[:n]
+    bound = 2.0 ** -44 * (np.abs(A).T @ np.abs(B) + Am.T @ np.abs(B) + np.abs(A).T @ Bm)
+    assert np.all(np.abs(G - ref) <= bound), np.max(np.abs(G - ref) / np.maximum(bound, 1e-300))
+    Gd = lob.gram(t(A), t(B), "df64").cpu().numpy()
+    assert np.all(np.abs(G - Gd) <= 2 * bound)
+
+
+@pytest.mark.parametrize("n,p,q", [(1, 1, 1), (127, 48, 16), (4097, 48, 48), (1000, 64, 64), (300, 17, 3)])
+@pytest.mark.parametrize("spread", [0, 20])
+def test_lincomb_tensor_cores(n, p, q, spread):
+    """Y = A C on the tensor cores; scaling groups are the rows of A and the columns of C, so the
+    bound carries 2^-44 (|A| |C| + rowmax|A| |C| + |A| colmax|C|)."""
+    import paper_1609_01689_gb300 as lob
+    rng = np.random.default_rng(n + p + 11 * q + spread)
+    A = rng.standard_normal((n, p)) * 2.0 ** rng.integers(-spread, spread + 1, n)[:, None]
+    C = rng.standard_normal((p, q)) * 2.0 ** rng.integers(-spread, spread + 1, q)[None, :]
+    if p > 2:
+        A[:, 1] = 0.0
+    Y = lob.lincomb(t(A), t(C), "mixed").cpu().numpy()
+    ref = oracle.lincomb(A, C)
+    ra = np.abs(A).max(axis=1, keepdims=True)
+    cc = np.abs(C).max(axis=0, keepdims=True)
+    bound = 2.0 ** -44 * (np.abs(A) @ np.abs(C) + ra * np.abs(C).sum(axis=0, keepdims=True) + np.abs(A).sum(
+        axis=1, keepdims=True) * cc)
+    assert np.all(np.abs(Y - ref) <= bound), np.max(np.abs(Y - ref) / np.maximum(bound, 1e-300))
