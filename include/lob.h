@@ -65,7 +65,9 @@ typedef struct {
                             may take before the kernel gives up (1..40; 0 = 32, about 2 s). A
                             product that gives up leaves Y invalid and is reported by lob_check,
                             lob_solve or the server (LOB_ERR_CUDA); the context stays usable.
-                            Small values exist to test that path. */
+                            -1 is a test mode of that path: the first pipeline stage of every such
+                            product waits for data that nothing sends (no copy is issued for it),
+                            so the kernel gives up after 2^16 clocks every time. */
   void* stream;          /* cudaStream_t for the build */
 } lob_create_opts;
 

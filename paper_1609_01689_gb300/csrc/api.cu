@@ -51,7 +51,7 @@ int lob_create(const lob_coo* H, const lob_create_opts* opts, lob_matrix** out) 
   if (values < 1 || values > 3) return LOB_ERR_ARG;
   if (o.precond_block < 0 || (o.precond_block > 64 && o.precond_block != LOB_TILE)) return LOB_ERR_ARG;
   if (o.precond_block == LOB_TILE && !(values & LOB_VALUES_FP32)) return LOB_ERR_ARG;  // tile mode runs on FP32 values
-  if (o.wait_log2 < 0 || o.wait_log2 > 40) return LOB_ERR_ARG;
+  if (o.wait_log2 < -1 || o.wait_log2 > 40) return LOB_ERR_ARG;
   cudaStream_t st = (cudaStream_t)o.stream;
   *out = nullptr;
 
@@ -74,7 +74,8 @@ int lob_create(const lob_coo* H, const lob_create_opts* opts, lob_matrix** out) 
   lob_matrix* m = new lob_matrix();
   cudaGetDevice(&m->device);
   m->values = values;
-  m->wait_limit = 1ll << (o.wait_log2 ? o.wait_log2 : 32);
+  m->wait_limit = o.wait_log2 > 0 ? (1ll << o.wait_log2) : (o.wait_log2 < 0 ? (1ll << 16) : (1ll << 32));
+  m->wait_poison = o.wait_log2 < 0;
   int rc = LOB_OK;
   if (cudaMalloc((void**)&m->status, sizeof(int)) != cudaSuccess || cudaMemset(m->status, 0, sizeof(int)) != cudaSuccess) {
     cudaGetLastError();

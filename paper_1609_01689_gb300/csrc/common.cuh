@@ -92,6 +92,7 @@ struct lob_matrix {
   size_t xs_bytes = 0;
   int* status = nullptr;   // device word: bit 0 set by an SpMM kernel that gave up on a bounded wait
   long long wait_limit = 1ll << 32;  // SM clocks any wait inside an SpMM kernel may take
+  int wait_poison = 0;               // test mode: the first ring stage waits for bytes never sent
 };
 
 // One matrix's share of a batched SpMM launch (several matrices' tile rows in one grid).

@@ -137,11 +137,69 @@ __device__ __forceinline__ void oz_split(double x, int emax, uint32_t dg[OZ_S]) 
   }
 }
 
+// The digits of two elements x0, x1 of the same scaling group (emax as for oz_split), packed as
+// the bf16 pairs (x0's digit in the low half) that an operand row stores for two consecutive k:
+// w[t] holds digit t of both. Cheaper than two oz_split calls: one 64-bit shift per element, the
+// digit fields read at fixed positions of F < 2^49, and one byte permute per pair of digits.
+__device__ __forceinline__ uint32_t oz_fields(uint64_t F, int t) {
+  const uint32_t fh = (uint32_t)(F >> 32), fl = (uint32_t)F;
+  switch (t) {
+    case 0: return fh >> 10;                               // bits 42-48
+    case 1: return (fh >> 3) & 127u;                       // 35-41
+    case 2: return __funnelshift_r(fl, fh, 28) & 127u;     // 28-34
+    case 3: return (fl >> 21) & 127u;                      // 21-27
+    case 4: return (fl >> 14) & 127u;                      // 14-20
+    case 5: return (fl >> 7) & 127u;                       // 7-13
+    default: return fl & 127u;                             // 0-6
+  }
+}
+__device__ __forceinline__ uint64_t oz_fixed(double x, int emax, uint32_t& sign) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const uint64_t m = ex ? ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) : 0ull;
+  const int sh = 4 + emax - ex;
+  sign = (uint32_t)(b >> 32) & 0x80000000u;
+  return sh < 64 ? (m >> sh) : 0ull;
+}
+__device__ __forceinline__ void oz_split2(double x0, double x1, int emax, uint32_t w[OZ_S]) {
+  uint32_t s0, s1;
+  const uint64_t F0 = oz_fixed(x0, emax, s0), F1 = oz_fixed(x1, emax, s1);
+  const uint32_t sg = (s0 >> 16) | s1;  // bf16 sign bits of the pair
+#pragma unroll
+  for (int t = 0; t < OZ_S; t++) {
+    const float f0 = __uint_as_float(0x4B000000u | oz_fields(F0, t)) - 8388608.0f;
+    const float f1 = __uint_as_float(0x4B000000u | oz_fields(F1, t)) - 8388608.0f;
+    w[t] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632) | sg;
+  }
+}
+
 // Byte offset of element (row r, k) inside an operand buffer of K = OZ_HALF columns in the
 // canonical K-major no-swizzle layout: core matrix (r / 8, k / 8) at (r / 8) * SBO + (k / 8) * 128,
 // row r % 8 at 16 (r % 8), element k % 8 at 2 (k % 8); SBO = 16 * OZ_HALF.
 constexpr uint32_t OZ_LBO = 128, OZ_SBO = 16 * OZ_HALF;
 __device__ __forceinline__ uint32_t oz_off(int r, int k8) { return (uint32_t)(r >> 3) * OZ_SBO + (uint32_t)k8 * 128u + (uint32_t)(r & 7) * 16u; }
+
+// Issue every digit product with a + b <= 6 for one 16-deep step. The B digit slices lie one after
+// another (slice b at sB + b * bsz, each nq rows), and so do the level accumulators in tensor memory
+// (level L at column L * nq), so one MMA of A slice a against B slices b0 .. b0 + cnt - 1 stacked
+// along N writes levels a + b0 .. a + b0 + cnt - 1 in their own accumulators. N = cnt * nq <= 256.
+// The first step (acc = 0) of A slice 0 covers every level and clears them.
+template <int NQ>
+__device__ __forceinline__ void oz_mma_step(uint32_t tmem, uint32_t sA, uint32_t asz, uint32_t sB, uint32_t bsz,
+                                            uint32_t sbo, int ks, bool first) {
+  constexpr int SPAN = 256 / NQ;  // B slices per MMA
+#pragma unroll
+  for (int a = 0; a < OZ_S; a++) {
+    const int nb = OZ_S - a;  // B slices 0 .. 6 - a
+#pragma unroll
+    for (int b0 = 0; b0 < nb; b0 += SPAN) {
+      const int cnt = nb - b0 < SPAN ? nb - b0 : SPAN;
+      const uint64_t ad = oz_desc(sA + a * asz + ks * 256u, OZ_LBO, sbo);
+      const uint64_t bd = oz_desc(sB + b0 * bsz + ks * 256u, OZ_LBO, sbo);
+      oz_mma(tmem + (uint32_t)((a + b0) * NQ), ad, bd, oz_idesc(128, cnt * NQ), (first && a == 0) ? 0u : 1u);
+    }
+  }
+}
 
 // Double-float helpers on (hi, lo) pairs of FP32 (Knuth's two-sum).
 __device__ __forceinline__ void oz_add(float& h, float& l, float x) {
@@ -501,18 +559,9 @@ __global__ void __launch_bounds__(128)
   __syncthreads();
   if (tid == 0) {
     oz_fence_after();
-    constexpr uint32_t IDESC = oz_idesc(128, NQ);
     const uint32_t sA = oz_smem(sm + Cf::A0), sB = oz_smem(sm + Cf::B0);
-    for (int L = 0; L < OZ_LV; L++)
-      for (int a = 0; a <= L; a++) {
-        const int b = L - a;
 #pragma unroll
-        for (int ks = 0; ks < KP / 16; ks++) {
-          const uint64_t ad = oz_desc(sA + a * Cf::ASZ + ks * 256u, OZ_LBO, Cf::SBO);
-          const uint64_t bd = oz_desc(sB + b * Cf::BSZ + ks * 256u, OZ_LBO, Cf::SBO);
-          oz_mma(tmem + (uint32_t)(L * NQ), ad, bd, IDESC, (a > 0 || ks > 0) ? 1u : 0u);
-        }
-      }
+    for (int ks = 0; ks < KP / 16; ks++) oz_mma_step<NQ>(tmem, sA, Cf::ASZ, sB, Cf::BSZ, Cf::SBO, ks, ks == 0);
     oz_commit(bar);
   }
   const bool ok = oz_bar_wait(bar, 0, OZ_WAIT);
@@ -556,6 +605,303 @@ __global__ void __launch_bounds__(128)
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// Pipelined Gram (v2): G0 = L0^T R and optionally G1 = L1^T R, p, q <= 64, chunks of 64 rows
+// (one MMA round per chunk, scaling groups = columns of a chunk; 7 * 64 * 127^2 < 2^24).
+// Warp roles in a persistent CTA of 256 threads:
+//   producers (warps 4-7): cp.async the chunk's raw FP64 rows into shared memory (zero beyond n),
+//     take each column's largest exponent there, wait until the previous chunk's MMAs have read
+//     the operand buffers, write the digits, and signal `full`;
+//   consumers (warps 0-3): thread 0 waits for `full` and issues the chunk's 112 MMAs (28 digit
+//     products x 4 steps of 16) with a commit to `done`; all four warps wait for `done`, read the
+//     levels back and add the chunk into their double-float sums, then count the chunk out.
+// While the consumers read chunk k back, the producers already load and split chunk k + 1, so the
+// HBM stream, the digit split, the MMAs and the readout overlap. When R is L0 itself (the solver's
+// M = S^T S beside (H S)^T S) its columns are loaded once and their digits go to both operands.
+// Column exponents are double-buffered by chunk parity; the producers wait (a counter) for the
+// readout of chunk k - 2 before overwriting its half.
+// ---------------------------------------------------------------------------------------------
+template <int NQ>
+struct OzG2 {
+  static constexpr int KC = 64;
+  static constexpr uint32_t ASZ = 128u * KC * 2u;
+  static constexpr uint32_t BSZ = (uint32_t)NQ * KC * 2u;
+  static constexpr uint32_t A0 = 0;
+  static constexpr uint32_t B0 = A0 + OZ_S * ASZ;
+  static constexpr uint32_t RAW = B0 + OZ_S * BSZ;  // the chunk's raw FP64 rows: [KC][p] L0, [KC][p] L1, [KC][q] R
+  static constexpr int RAWC = NQ <= 48 ? 128 : 96;      // bound on the raw columns 2p + q (p + q when R is L0)
+  static constexpr uint32_t EX = RAW + KC * RAWC * 8u;  // int [2][3][64]
+  static constexpr uint32_t BAR = EX + 2 * 3 * 64 * 4;   // full, done, raw
+  static constexpr uint32_t CTL = BAR + 24;              // int: readout count, abort, commits
+  static constexpr uint32_t SLOT = CTL + 16;
+  static constexpr uint32_t BYTES = SLOT + 16;
+  static constexpr uint32_t TCOLS = OZ_LV * NQ <= 128 ? 128u : (OZ_LV * NQ <= 256 ? 256u : 512u);
+  static_assert(BYTES <= 227 * 1024, "shared memory");
+};
+
+__device__ __forceinline__ void oz_cp8(void* dst, const void* src, bool valid) {
+  // 8-byte async copy; zero fill when the row is beyond n
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(oz_smem(dst)), "l"(src),
+               "r"(valid ? 8 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void oz_cp_wait() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void oz_named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
+}
+// Bounded wait that also gives up once the CTA's abort flag is set; false then.
+__device__ __forceinline__ bool oz_wait2(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  const long long t0 = clock64();
+  while (!oz_bar_test(bar, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > OZ_WAIT) { *abort = 1; return false; }
+  }
+  return true;
+}
+
+template <int NQ>
+__global__ void __launch_bounds__(512, 1)
+    k_gram_oz2(int64_t n, int p, const double* __restrict__ L0, int ld0, const double* __restrict__ L1, int ld1,
+               int q, const double* __restrict__ R, int ldr, double* __restrict__ part, int bulk) {
+  using C = OzG2<NQ>;
+  constexpr int KC = C::KC, NP = 256;   // rows per chunk, producer threads
+  constexpr int NH = NQ / 2;            // columns per consumer warp half
+  extern __shared__ __align__(1024) unsigned char sm[];
+  int* ex = reinterpret_cast<int*>(sm + C::EX);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + C::BAR);
+  uint64_t* done = full + 1;
+  uint64_t* rawb = full + 2;
+  volatile int* rcount = reinterpret_cast<volatile int*>(sm + C::CTL);
+  volatile int* abort = rcount + 1;
+  volatile int* ncommit = rcount + 2;  // commits issued to `done`
+  uint32_t* slot = reinterpret_cast<uint32_t*>(sm + C::SLOT);
+  double* raw = reinterpret_cast<double*>(sm + C::RAW);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const bool shared_r = (R == L0 && ldr == ld0 && q == p);
+  const int64_t nchunks = (n + KC - 1) / KC;
+
+  for (uint32_t o = tid * 16u; o < C::RAW; o += 512u * 16u) *reinterpret_cast<uint4*>(sm + o) = make_uint4(0, 0, 0, 0);
+  if (tid == 0) {
+    oz_bar_init(full, 1);
+    oz_bar_init(done, 1);
+    oz_bar_init(rawb, 1);
+    *rcount = 0;
+    *abort = 0;
+    *ncommit = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) oz_tmem_alloc(slot, C::TCOLS);
+  oz_fence_before();
+  __syncthreads();
+  oz_fence_after();
+  const uint32_t tmem = *slot;
+
+  if (tid >= 256) {
+    // ===================== producers (warps 8-15) =====================
+    const int pt = tid - 256;
+    // raw blocks, one after another: L0 (p columns), L1 (p, if given), R (q, unless R is L0);
+    // setid = the operand role of a block (0: L0, 1: L1, 2: R)
+    int nset = 0, wd[3] = {0, 0, 0}, lds[3] = {0, 0, 0}, setid[3] = {0, 0, 0};
+    const double* srcs[3] = {nullptr, nullptr, nullptr};
+    wd[nset] = p; lds[nset] = ld0; srcs[nset] = L0; setid[nset] = 0; nset++;
+    if (L1) { wd[nset] = p; lds[nset] = ld1; srcs[nset] = L1; setid[nset] = 1; nset++; }
+    if (!shared_r) { wd[nset] = q; lds[nset] = ldr; srcs[nset] = R; setid[nset] = 2; nset++; }
+    uint32_t roff[3] = {0, 0, 0};
+    for (int b = 1; b < nset; b++) roff[b] = roff[b - 1] + (uint32_t)KC * wd[b - 1] * 8u;
+    int cstart[3] = {0, 0, 0};
+    for (int b = 1; b < nset; b++) cstart[b] = cstart[b - 1] + wd[b - 1];
+    int k = 0;
+    for (int64_t ck = blockIdx.x; ck < nchunks; ck += gridDim.x, k++) {
+      const int64_t r0 = ck * KC;
+      const int rows = (int)((n - r0) < KC ? (n - r0) : KC);
+      // raw rows of the chunk by bulk copies completing on `rawb` (the previous chunk's digits were
+      // written from raw before `full`, and every producer passed that barrier)
+      if (bulk) {
+        uint32_t bytes = 0;
+        for (int b = 0; b < nset; b++) bytes += (uint32_t)rows * wd[b] * 8u;
+        if (pt == 0)
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(oz_smem(rawb)), "r"(bytes) : "memory");
+        oz_named_sync(1, NP);
+        for (int b = 0; b < nset; b++) {
+          if (lds[b] == wd[b]) {  // contiguous rows: one copy
+            if (pt == b) {
+              const uint32_t by = (uint32_t)rows * wd[b] * 8u;
+              asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                           ::"r"(oz_smem(reinterpret_cast<unsigned char*>(raw) + roff[b])), "l"(srcs[b] + r0 * lds[b]),
+                           "r"(by), "r"(oz_smem(rawb)) : "memory");
+            }
+          } else {
+            for (int i = pt; i < rows; i += NP)
+              asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+                           ::"r"(oz_smem(reinterpret_cast<unsigned char*>(raw) + roff[b] + (uint32_t)i * wd[b] * 8u)),
+                           "l"(srcs[b] + (r0 + i) * lds[b]), "r"((uint32_t)wd[b] * 8u), "r"(oz_smem(rawb)) : "memory");
+          }
+        }
+        if (!oz_wait2(rawb, (uint32_t)(k & 1), abort)) {}
+      } else {
+        for (int b = 0; b < nset; b++)
+          for (int i = pt >> 6; i < rows; i += NP >> 6)
+            for (int c = pt & 63; c < wd[b]; c += 64)
+              oz_cp8(reinterpret_cast<unsigned char*>(raw) + roff[b] + ((uint32_t)i * wd[b] + c) * 8u,
+                     srcs[b] + (r0 + i) * lds[b] + c, true);
+        oz_cp_wait();
+      }
+      // the exponents of chunk k reuse the half of chunk k - 2: wait until that one was read back
+      if (k >= 2) {
+        const long long t0 = clock64();
+        while (*rcount < k - 1 && !*abort)
+          if (clock64() - t0 > OZ_WAIT) *abort = 1;
+      }
+      oz_named_sync(1, NP);
+      int* exk = ex + (k & 1) * 3 * 64;
+      for (int b = 0; b < nset; b++) {
+        const int c = pt - cstart[b];
+        if (c < 0 || c >= wd[b]) continue;
+        const double* blk = reinterpret_cast<const double*>(reinterpret_cast<unsigned char*>(raw) + roff[b]);
+        int e = 0;
+#pragma unroll 8
+        for (int i = 0; i < rows; i++) e = max(e, oz_bexp(blk[i * wd[b] + c]));
+        exk[setid[b] * 64 + c] = e;
+        if (shared_r && b == 0) exk[128 + c] = e;
+      }
+      // the previous chunk's MMAs must have read the operand buffers
+      if (k >= 1) oz_wait2(done, (uint32_t)((k - 1) & 1), abort);
+      oz_named_sync(1, NP);
+      if (*abort) break;
+      for (int b = 0; b < nset; b++) {
+        const int c = pt & 63;
+        if (c >= wd[b]) continue;
+        const double* blk = reinterpret_cast<const double*>(reinterpret_cast<unsigned char*>(raw) + roff[b]);
+        const int set = setid[b];
+        const int emax = exk[set * 64 + c];
+#pragma unroll
+        for (int pass = 0; pass < 2; pass++) {
+          const int k8 = (pt >> 6) + 4 * pass;
+          uint32_t pk[OZ_S][4];
+#pragma unroll
+          for (int r = 0; r < 8; r += 2) {
+            const int i0 = k8 * 8 + r;
+            const double x0 = i0 < rows ? blk[i0 * wd[b] + c] : 0.0;
+            const double x1 = i0 + 1 < rows ? blk[(i0 + 1) * wd[b] + c] : 0.0;
+            uint32_t wv[OZ_S];
+            oz_split2(x0, x1, emax, wv);
+#pragma unroll
+            for (int t = 0; t < OZ_S; t++) pk[t][r >> 1] = wv[t];
+          }
+          if (set < 2) {
+            const uint32_t off = oz_off(set * 64 + c, k8);
+#pragma unroll
+            for (int t = 0; t < OZ_S; t++)
+              *reinterpret_cast<uint4*>(sm + C::A0 + t * C::ASZ + off) = make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
+          }
+          if (set == 2 || (set == 0 && shared_r)) {
+            const uint32_t off = oz_off(c, k8);
+#pragma unroll
+            for (int t = 0; t < OZ_S; t++)
+              *reinterpret_cast<uint4*>(sm + C::B0 + t * C::BSZ + off) = make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
+          }
+        }
+      }
+      oz_fence_proxy();
+      oz_named_sync(1, NP);
+      if (pt == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(oz_smem(full)) : "memory");
+    }
+  } else {
+    // ===================== consumers (warps 0-7) =====================
+    // warp w reads accumulator lanes 32 (w % 4) .. + 31 and the columns of half w / 4
+    const int lt = tid & 127, sel = lt >> 6, m = lt & 63, cb = (warp >> 2) * NH;
+    const bool rd = m < p && (sel == 0 || L1 != nullptr);
+    float ah[NH], al[NH];
+#pragma unroll
+    for (int c = 0; c < NH; c++) { ah[c] = 0.f; al[c] = 0.f; }
+    int eref = 0;
+    bool started = false;
+    const uint32_t sA = oz_smem(sm + C::A0), sB = oz_smem(sm + C::B0);
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    int k = 0;
+    for (int64_t ck = blockIdx.x; ck < nchunks; ck += gridDim.x, k++) {
+      if (tid == 0) {
+        if (oz_wait2(full, (uint32_t)(k & 1), abort)) {
+          oz_fence_after();
+#pragma unroll
+          for (int ks = 0; ks < KC / 16; ks++) oz_mma_step<NQ>(tmem, sA, C::ASZ, sB, C::BSZ, 16u * KC, ks, ks == 0);
+          oz_commit(done);
+          *ncommit = k + 1;
+        }
+      }
+      oz_wait2(done, (uint32_t)(k & 1), abort);
+      oz_named_sync(2, 256);  // a uniform decision: every consumer goes on, or every one leaves
+      if (*abort) break;
+      oz_fence_after();
+      const int* exk = ex + (k & 1) * 3 * 64;
+      const int er = exk[sel * 64 + m];
+      int ecmax = 0;
+      for (int c = 0; c < q; c++) ecmax = max(ecmax, exk[128 + c]);
+      const bool live = rd && er > 0 && ecmax > 0;
+      const int ech = (er - 1022) + (ecmax - 1022) - 14 + 24;
+      if (live) {
+        if (!started) { eref = ech; started = true; }
+        else if (ech > eref) {
+          const float f = oz_pow2(eref - ech);
+#pragma unroll
+          for (int c = 0; c < NH; c++) { ah[c] *= f; al[c] *= f; }
+          eref = ech;
+        }
+      }
+#pragma unroll
+      for (int c0 = 0; c0 < NH; c0 += 8) {
+        float v[OZ_LV][8];
+#pragma unroll
+        for (int L = 0; L < OZ_LV; L++) oz_ld8(tmem + lane_base + (uint32_t)(L * NQ + cb + c0), v[L]);
+        oz_wait_ld();
+        if (live) {
+#pragma unroll
+          for (int c = 0; c < 8; c++) {
+            const int col = cb + c0 + c;
+            if (col >= q) continue;
+            float lv[OZ_LV];
+#pragma unroll
+            for (int L = 0; L < OZ_LV; L++) lv[L] = v[L][c];
+            float vh, vl;
+            oz_levels(lv, vh, vl);
+            const float s = oz_pow2((er - 1022) + (exk[128 + col] - 1022) - 14 - eref);
+            oz_add(ah[c0 + c], al[c0 + c], vh * s);
+            al[c0 + c] += vl * s;
+          }
+        }
+      }
+      oz_fence_before();
+      oz_named_sync(2, 256);
+      if (tid == 0) { __threadfence_block(); *rcount = k + 1; }
+    }
+    if (!*abort) {
+      double* out = part + ((int64_t)blockIdx.x * 2 + sel) * 64 * NQ + (int64_t)m * NQ + cb;
+#pragma unroll
+      for (int c = 0; c < NH; c++) out[c] = (rd && started) ? ldexp((double)ah[c] + (double)al[c], eref) : 0.0;
+    }
+  }
+  __syncthreads();
+  if (*abort) {
+    if (tid == 0) atomicExch(&lob_oz_fault, 1);
+    // the last batch of MMAs issued must finish before the tensor memory is released
+    const int nc = *ncommit;
+    if (nc > 0) oz_bar_wait(done, (uint32_t)((nc - 1) & 1), 1ll << 31);
+  }
+  oz_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    oz_fence_after();
+    oz_tmem_free(tmem, C::TCOLS);
+  }
+}
+
+}  // namespace
+
 // ---- launchers --------------------------------------------------------------------------------
 
 // Doubles of workspace the tensor-core Gram needs (the CTAs' partial sums).
@@ -577,6 +923,30 @@ int lob_gram_oz_launch(int64_t n, int p, const double* L0, int ld0, const double
   const int64_t nchunks = (n + OZ_KC - 1) / OZ_KC;
   const int grid = (int)(nchunks < sms ? nchunks : (sms < 256 ? sms : 256));
   const int nq = (q + 15) / 16 * 16;
+  const bool shared_r = (R == L0 && ldr == ld0 && q == p);
+  const int rawc = p + (L1 ? p : 0) + (shared_r ? 0 : q);
+  if (rawc <= (nq <= 48 ? OzG2<48>::RAWC : OzG2<64>::RAWC)) {  // the pipelined kernel (chunks of 64 rows)
+    // bulk copies need 16-byte aligned rows and sizes: even widths and leading dimensions, aligned bases
+    auto al16 = [](const void* ptr) { return ((uintptr_t)ptr & 15) == 0; };
+    const int bulk = (p % 2 == 0 && q % 2 == 0 && ld0 % 2 == 0 && al16(L0) && (!L1 || (ld1 % 2 == 0 && al16(L1))) &&
+                      (shared_r || (ldr % 2 == 0 && al16(R)))) ? 1 : 0;
+    const int64_t nc2 = (n + OzG2<64>::KC - 1) / OzG2<64>::KC;
+    const int grid2 = (int)(nc2 < sms ? nc2 : (sms < 256 ? sms : 256));
+    auto go2 = [&](auto kern, uint32_t bytes) -> int {
+      LOB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+      (kern<<<grid2, 512, bytes, st>>>(n, p, L0, ld0, L1, ld1, q, R, ldr, work, bulk), LOB_LAUNCHED());
+      return LOB_OK;
+    };
+    if (nq == 16) LOB_TRY(go2(k_gram_oz2<16>, OzG2<16>::BYTES));
+    else if (nq == 32) LOB_TRY(go2(k_gram_oz2<32>, OzG2<32>::BYTES));
+    else if (nq == 48) LOB_TRY(go2(k_gram_oz2<48>, OzG2<48>::BYTES));
+    else LOB_TRY(go2(k_gram_oz2<64>, OzG2<64>::BYTES));
+    const int nsel = L1 ? 2 : 1;
+    (k_gram_oz_reduce<<<(nsel * p * q + 255) / 256, 256, 0, st>>>(grid2, nq, p, q, nsel, work, G0, G1),
+     LOB_LAUNCHED());
+    LOB_CUDA(cudaGetLastError());
+    return LOB_OK;
+  }
   auto go = [&](auto kern, uint32_t bytes) -> int {
     LOB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     (kern<<<grid, 256, bytes, st>>>(n, p, L0, ld0, L1, ld1, q, R, ldr, work), LOB_LAUNCHED());
@@ -632,3 +1002,4 @@ int lob_oz_fault_take(cudaStream_t st) {
   }
   return h;
 }
+

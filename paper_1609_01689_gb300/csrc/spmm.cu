@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(CfgR<NB>::THREADS, 1)
                 const int64_t* __restrict__ tptr, const int32_t* __restrict__ tchunk,
                 const uint2* __restrict__ rv, const uint16_t* __restrict__ cperm,
                 const uint16_t* __restrict__ cptrs, const float* __restrict__ Xs, double* __restrict__ Y, int ldy,
-                int c0, int w, int64_t n_act, int64_t ntr, int* __restrict__ status, long long limit) {
+                int c0, int w, int64_t n_act, int64_t ntr, int* __restrict__ status, long long limit, int poison) {
   using C = CfgR<NB>;
   constexpr int VW = C::VW, G = C::G, NW = C::NW, D = C::D, CH = C::CH;
   constexpr int XN = LOB_TILE * NB;
@@ -566,8 +566,12 @@ __global__ void __launch_bounds__(CfgR<NB>::THREADS, 1)
     c.t = t0 - 1; c.k = 0; c.nk = 0;  // settle moves to the first chunk
     bool more = ring_settle(c, rowptr, tcol, tchunk, n_act);
     for (int s = 0; s < D && more; s++) {
-      ctl->issued[s]++;
-      ring_issue<NB>(sm + C::ST + s * C::STAGE, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rv, cperm, cptrs, Xs);
+      if (poison && s == 0) {  // test mode: stage 0 expects bytes that nothing sends (nothing in flight)
+        mbar_expect_tx(&full[0], 16u);
+      } else {
+        ctl->issued[s]++;
+        ring_issue<NB>(sm + C::ST + s * C::STAGE, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rv, cperm, cptrs, Xs);
+      }
       c.k++;
       more = ring_settle(c, rowptr, tcol, tchunk, n_act);
     }
@@ -985,7 +989,7 @@ __global__ void __launch_bounds__(CfgRD<NB>::THREADS, 1)
                    const uint2* __restrict__ rv, const float* __restrict__ vlo,
                    const uint16_t* __restrict__ cperm, const uint16_t* __restrict__ cptrs,
                    const float2* __restrict__ Xs, double* __restrict__ Y, int ldy, int c0, int w, int64_t n_act,
-                   int64_t ntr, int* __restrict__ status, long long limit) {
+                   int64_t ntr, int* __restrict__ status, long long limit, int poison) {
   using C = CfgRD<NB>;
   constexpr int VW = C::VW, G = C::G, NG = C::NG, RPG = C::RPG, NW = C::NW, D = C::D, CH = C::CH;
   extern __shared__ __align__(16) unsigned char sm[];
@@ -1036,9 +1040,13 @@ __global__ void __launch_bounds__(CfgRD<NB>::THREADS, 1)
     c.t = t0 - 1; c.k = 0; c.nk = 0;
     bool more = ring_settle(c, rowptr, tcol, tchunk, n_act);
     for (int s = 0; s < D && more; s++) {
-      ctl->issued[s]++;
-      ring_issue_df<NB>(sm + C::ST + s * C::STAGE, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rv, vlo, cperm,
-                        cptrs, Xs);
+      if (poison && s == 0) {  // test mode: stage 0 expects bytes that nothing sends (nothing in flight)
+        mbar_expect_tx(&full[0], 16u);
+      } else {
+        ctl->issued[s]++;
+        ring_issue_df<NB>(sm + C::ST + s * C::STAGE, &full[s], c.I, c.t, c.k, tcol, tptr, tchunk, rv, vlo, cperm,
+                          cptrs, Xs);
+      }
       c.k++;
       more = ring_settle(c, rowptr, tcol, tchunk, n_act);
     }
@@ -1215,7 +1223,7 @@ int launch_df(const lob_matrix* m, const double* X, double* Y, int nb, int64_t n
     if constexpr (NB == 16) {
       (k_spmm_ring_df<NB><<<(unsigned)grid, CfgRD<NB>::THREADS, CfgRD<NB>::BYTES, st>>>(
            TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rv, TS.v32lo, TS.cperm, TS.cptrs, Xs, Y, nb, c0, w, n_act,
-           nt_act, m->status, m->wait_limit),
+           nt_act, m->status, m->wait_limit, m->wait_poison),
        LOB_LAUNCHED());
     } else {
       (kern<<<(unsigned)nt_act, C::THREADS, C::BYTES, st>>>(TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rc, TS.v32,
@@ -1279,7 +1287,7 @@ int launch_ring16(const lob_matrix* m, const double* X, double* Y, int nb, int64
      LOB_LAUNCHED());
     (k_spmm_ring<NB><<<(unsigned)grid, C::THREADS, C::BYTES, st>>>(TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rv,
                                                                   TS.cperm, TS.cptrs, Xs, Y, nb, c0, w, n_act,
-                                                                  nt_act, m->status, m->wait_limit),
+                                                                  nt_act, m->status, m->wait_limit, m->wait_poison),
      LOB_LAUNCHED());
   }
   LOB_CUDA(cudaGetLastError());

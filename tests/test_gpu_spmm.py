@@ -135,17 +135,17 @@ def test_spmm_df64_integer_exact_and_fp64_class(nb):
 
 @pytest.mark.parametrize("mode", ["mixed", "df64"])
 def test_spmm_bounded_wait_reports_and_context_survives(mode):
-    """Failure detection without a GPU fault: a matrix created with a wait limit of 2 SM clocks
-    makes every wait of the persistent SpMM kernels (nb = 16) run out before its copy lands. The
-    kernel must then stop issuing copies, let the copies already in flight land, leave, and set
-    the matrix's status word: lob_check reports LOB_ERR_CUDA once (then the word is clear), a
+    """Failure detection without a GPU fault: a matrix created in the wait test mode
+    (wait_log2 = -1) makes the first pipeline stage of the persistent SpMM kernels (nb = 16) wait
+    for bytes that nothing sends, so that wait runs out every time. The kernel must then stop
+    issuing copies, let the copies already in flight land, leave, and set the matrix's status word: lob_check reports LOB_ERR_CUDA once (then the word is clear), a
     solve on that matrix returns LOB_ERR_CUDA, and a product on a normally created matrix right
     after is exact (the context stays usable)."""
     import paper_1609_01689_gb300 as lob
     rng = np.random.default_rng(77)
     H = random_upper(3000, 0.01, rng, integer=True)
     X = rng.integers(-8, 9, (3000, 16)).astype(np.float64)
-    Mbad = lob.Matrix(H.n, H.rows, H.cols, H.vals, wait_log2=1)
+    Mbad = lob.Matrix(H.n, H.rows, H.cols, H.vals, wait_log2=-1)
     run(Mbad, X, mode)
     with pytest.raises(lob.LobError) as e:
         Mbad.check()
