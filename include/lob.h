@@ -137,18 +137,22 @@ int lob_check(lob_matrix* m, void* stream);
 /* Block inner product G = A^T B (Section 4.4, the tall-skinny X^T Y): A is n x p (leading
  * dimension lda), B is n x q (ldb), G is p x q row-major. All device. p, q <= 192.
  * mode: LOB_SPMM_FP64 for native FP64 fused multiply-adds; LOB_SPMM_MIXED for FP64-class
- * arithmetic (about 2^-44 relative to |A|^T |B|): on the tensor cores when p, q <= 64 (each
+ * arithmetic (about 2^-44 relative to |A|^T |B|): on the tensor cores when p, q <= 64 and
+ * p q >= 512 (below that the double-float kernel is faster; each
  * operand split exactly into seven bf16 digits per scaling group, the digit products summed
  * exactly in FP32 tensor memory, the levels combined in double-float; Ozaki et al.'s error-free
  * splitting), otherwise double-float on the FP32 pipes; LOB_SPMM_DF64 for that double-float
- * kernel always. The tensor-core path treats entries below 2^-126 of the scale of their group's
+ * kernel always; LOB_BLAS_TC for the tensor-core kernel whenever p, q <= 64 (LOB_ERR_ARG beyond). The tensor-core path treats entries below 2^-126 of the scale of their group's
  * products as zero. */
 int lob_gram(int64_t n, int32_t p, const double* A, int32_t lda, int32_t q, const double* B, int32_t ldb, double* G,
              int32_t mode, void* stream);
 
+#define LOB_BLAS_TC 3 /* lob_gram / lob_lincomb only: the FP64-class tensor-core kernel */
+
 /* Linear combination Y = A C (Section 4.4, eq. 7): A n x p (lda), C p x q row-major, Y n x q
  * (ldy). Device. p, q <= 192. Y must not overlap A. mode as lob_gram (LOB_SPMM_MIXED: tensor
- * cores for p, q <= 64, the scaling groups being the rows of A and the columns of C). */
+ * cores for p, q <= 64 and p q >= 512, the scaling groups being the rows of A and the columns of
+ * C). */
 int lob_lincomb(int64_t n, int32_t p, const double* A, int32_t lda, int32_t q, const double* C, double* Y,
                 int32_t ldy, int32_t mode, void* stream);
 

@@ -35,7 +35,7 @@ SPMM_FP64, SPMM_MIXED, SPMM_DF64 = 0, 1, 2
 MODE_FP64, MODE_MIXED = 0, 1
 PSOLVE_FOM, PSOLVE_DIRECT, PSOLVE_MINRES, PSOLVE_ABS = 0, 1, 2, 3
 _PSOLVE = {"fom": 0, "direct": 1, "minres": 2, "abs": 3, 0: 0, 1: 1, 2: 2, 3: 3}
-_MODES = {"fp64": 0, "mixed": 1, "df64": 2, 0: 0, 1: 1, 2: 2}
+_MODES = {"fp64": 0, "mixed": 1, "df64": 2, "tc": 3, 0: 0, 1: 1, 2: 2, 3: 3}
 _ARITH = {"fp64": 0, "df": 1, 0: 0, 1: 1}
 
 _P = ctypes.c_void_p

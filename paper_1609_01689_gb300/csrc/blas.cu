@@ -461,7 +461,7 @@ int lob_gram_launch_ws(int64_t n, int p, const double* A, int lda, int q, const 
   if (sym && p != q) return LOB_ERR_ARG;
   // FP64-class products go to the tensor cores (ozaki.cu) when they fit; LOB_SPMM_DF64 keeps the
   // double-float CUDA-core kernel
-  if (mode == LOB_SPMM_MIXED && lob_oz_fits(p, q))
+  if ((mode == LOB_SPMM_MIXED && lob_oz_pays(p, q)) || mode == LOB_BLAS_TC)
     return lob_gram_oz_launch(n, p, A, lda, nullptr, 0, q, B, ldb, G, nullptr, work, st);
   const int e = gram_edge(p, q);
   const int ta = (p + e - 1) / e, tb = (q + e - 1) / e;
@@ -479,7 +479,9 @@ int lob_gram_launch_ws(int64_t n, int p, const double* A, int lda, int q, const 
 int lob_gram_launch(int64_t n, int p, const double* A, int lda, int q, const double* B, int ldb, double* G, int mode,
                     cudaStream_t st) {
   if (n < 1 || p < 1 || q < 1 || p > 192 || q > 192 || lda < p || ldb < q || !A || !B || !G) return LOB_ERR_ARG;
-  if (mode != LOB_SPMM_FP64 && mode != LOB_SPMM_MIXED && mode != LOB_SPMM_DF64) return LOB_ERR_ARG;
+  if (mode != LOB_SPMM_FP64 && mode != LOB_SPMM_MIXED && mode != LOB_SPMM_DF64 && mode != LOB_BLAS_TC)
+    return LOB_ERR_ARG;
+  if (mode == LOB_BLAS_TC && !lob_oz_fits(p, q)) return LOB_ERR_ARG;
   double* work = nullptr;
   const size_t wd = lob_gram_work_doubles(n, p, q), wo = lob_gram_oz_work_doubles();
   LOB_CUDA(cudaMallocAsync((void**)&work, (wd > wo ? wd : wo) * sizeof(double), st));
@@ -491,8 +493,11 @@ int lob_gram_launch(int64_t n, int p, const double* A, int lda, int q, const dou
 int lob_lincomb_launch(int64_t n, int p, const double* A, int lda, int q, const double* C, double* Y, int ldy,
                        int mode, cudaStream_t st, const double* D, int ldd) {
   if (n < 1 || p < 1 || q < 1 || p > 192 || q > 192 || lda < p || ldy < q || !A || !C || !Y) return LOB_ERR_ARG;
-  if (mode != LOB_SPMM_FP64 && mode != LOB_SPMM_MIXED && mode != LOB_SPMM_DF64) return LOB_ERR_ARG;
-  if (mode == LOB_SPMM_MIXED && lob_oz_fits(p, q)) return lob_lincomb_oz_launch(n, p, A, lda, q, C, Y, ldy, st, D, ldd);
+  if (mode != LOB_SPMM_FP64 && mode != LOB_SPMM_MIXED && mode != LOB_SPMM_DF64 && mode != LOB_BLAS_TC)
+    return LOB_ERR_ARG;
+  if (mode == LOB_BLAS_TC && !lob_oz_fits(p, q)) return LOB_ERR_ARG;
+  if ((mode == LOB_SPMM_MIXED && lob_oz_pays(p, q)) || mode == LOB_BLAS_TC)
+    return lob_lincomb_oz_launch(n, p, A, lda, q, C, Y, ldy, st, D, ldd);
   // four rows a thread when the CTA's rows of A fit comfortably in shared memory, else one
   const int RM = p <= 64 ? 4 : 1;
   dim3 grid((unsigned)((n + 16 * RM - 1) / (16 * RM)), (q + 15) / 16);

@@ -147,6 +147,7 @@ void lob_free_precond(lob_precond* P);
 int lob_sm_count();
 // Tensor-core FP64-class block products (ozaki.cu): p, q <= 64.
 bool lob_oz_fits(int p, int q);
+bool lob_oz_pays(int p, int q);
 size_t lob_gram_oz_work_doubles();
 int lob_gram_oz_launch(int64_t n, int p, const double* L0, int ld0, const double* L1, int ld1, int q,
                        const double* R, int ldr, double* G0, double* G1, double* work, cudaStream_t st);

@@ -391,9 +391,9 @@ struct lob_task {
 
   // projected eigenproblem and Cholesky-QR factors in the task's small-solve arithmetic (native
   // FP64, or double-float when the options ask for it)
-  // Arithmetic of the block products other than the fused Rayleigh-Ritz Grams: native FP64, or
-  // double-float on the CUDA cores in MIXED (the tensor-core kernels serve the fused pair)
-  int bmode() const { return blas_mode == LOB_SPMM_MIXED ? LOB_SPMM_DF64 : blas_mode; }
+  // Arithmetic of the block products: native FP64, or in MIXED the FP64-class tensor-core kernels
+  // (lob_gram_launch_ws / lob_lincomb_launch fall back to double-float beyond their shapes)
+  int bmode() const { return blas_mode; }
 
   int rr(int mm, const double* Gp, const double* Mp, double* th, double* Cp, int slot, int chol_only) {
     if (rr_mode == LOB_SPMM_MIXED)
@@ -443,7 +443,7 @@ struct lob_task {
   int rr_begin(int mm) {
     {
       Timer t(clk(), st, ph(PH_GRAM));
-      if (blas_mode == LOB_SPMM_MIXED && lob_oz_fits(mm, mm)) {
+      if (blas_mode == LOB_SPMM_MIXED && lob_oz_pays(mm, mm)) {
         // one tensor-core pass for both: M = S^T S and (H S)^T S, the transpose of G (equal to G for
         // the symmetric H; the solve reads the upper triangles)
         LOB_TRY(lob_gram_oz_launch(n_act, mm, S.p, ldS, HS.p, ldS, mm, S.p, ldS, Mm.p, G.p, work.p, st));
@@ -463,7 +463,10 @@ struct lob_task {
   // the product goes straight into place; wider products go through Tn.
   int lincomb_into(int p, const double* A, int lda, int q, const double* C, double* Y, int ldy,
                    const double* D = nullptr, int ldd = 0) {
-    if (q <= 16) return lob_lincomb_launch(n_act, p, A, lda, q, C, Y, ldy, bmode(), st, D, ldd);
+    // one pass straight into place: one CTA covers all output columns of its rows (the tensor-core
+    // kernel up to 64, the CUDA-core kernels up to 16)
+    if (q <= 16 || (blas_mode == LOB_SPMM_MIXED && lob_oz_pays(p, q)))
+      return lob_lincomb_launch(n_act, p, A, lda, q, C, Y, ldy, bmode(), st, D, ldd);
     LOB_TRY(lob_lincomb_launch(n_act, p, A, lda, q, C, Tn.p, q, bmode(), st, D, ldd));
     (k_copy_cols<<<nblk(n_act * q), BS, 0, st>>>(n_act, q, Tn.p, q, nullptr, Y, ldy), LOB_LAUNCHED());
     return LOB_OK;

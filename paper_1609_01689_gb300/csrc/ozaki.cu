@@ -902,12 +902,253 @@ __global__ void __launch_bounds__(512, 1)
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------------------------------------
+// Pipelined linear combination (v2): Y = A C (+ D), p, q <= 64, tiles of 128 rows. Persistent CTAs
+// of 16 warps:
+//   producers (warps 8-15): the digits of C once (B operand: 7 x NQ x KP, scaling groups the
+//     columns of C); per tile, bulk-copy the 128 rows of A into shared memory, take each row's
+//     largest exponent, wait until the previous tile's MMAs have read the A operand, write the
+//     digits (scaling groups the rows), signal `full`;
+//   consumers (warps 0-7): thread 0 issues the tile's digit products (B slices stacked along N) and
+//     commits them; all wait, read the levels of their row (thread = tile row, warp half = column
+//     half), combine and scale them, add D and store Y.
+// The tile's rows of A are all read before any of its rows of Y is written and a CTA owns its
+// tiles, so Y may be the same rows of A (an in-place update).
+// ---------------------------------------------------------------------------------------------
+template <int NQ, int KP>
+struct OzL2 {
+  static constexpr uint32_t SBO = 16u * KP;
+  static constexpr uint32_t ASZ = 128u * KP * 2u;
+  static constexpr uint32_t BSZ = (uint32_t)NQ * KP * 2u;
+  static constexpr uint32_t A0 = 0;
+  static constexpr uint32_t B0 = A0 + OZ_S * ASZ;
+  static constexpr uint32_t RAW = B0 + OZ_S * BSZ;        // [128][p | 1] FP64 rows of the tile
+  static constexpr uint32_t ER = RAW + 128u * (KP + 1) * 8u;  // int [2][128]: row exponents by tile parity
+  static constexpr uint32_t EC = ER + 2 * 128 * 4;         // int [64]: column exponents of C
+  static constexpr uint32_t BAR = EC + 64 * 4;             // full, done, raw
+  static constexpr uint32_t CTL = BAR + 24;                // readout count, abort, commits
+  static constexpr uint32_t SLOT = CTL + 16;
+  static constexpr uint32_t BYTES = SLOT + 16;
+  static constexpr uint32_t TCOLS = OZ_LV * NQ <= 128 ? 128u : (OZ_LV * NQ <= 256 ? 256u : 512u);
+  static_assert(BYTES <= 227 * 1024, "shared memory");
+};
+
+// FP64 value of the double-float (h, l) times 2^e: the two parts converted by their bit fields (no
+// FP64 conversion instructions), one FP64 addition, and the scaling as an exponent-field add.
+// Requires h, l normal or zero and the result in the normal FP64 range.
+__device__ __forceinline__ double oz_f32_to_f64(float f) {
+  const uint32_t u = __float_as_uint(f);
+  if ((u & 0x7F800000u) == 0) return 0.0;  // zero; a subnormal low part is far below the result's ulp
+  const uint32_t s = u & 0x80000000u, e = (u >> 23) & 0xFF, mt = u & 0x7FFFFFu;
+  const uint32_t hi = s | ((e - 127 + 1023) << 20) | (mt >> 3), lo = mt << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double oz_df_to_f64(float h, float l, int e) {
+  const double v = oz_f32_to_f64(h) + oz_f32_to_f64(l);
+  if (v == 0.0) return 0.0;
+  const int hv = __double2hiint(v);
+  const int ef = ((hv >> 20) & 0x7FF) + e;
+  if (ef <= 0 || ef >= 2047) return ldexp(v, e);  // outside the normal range: the library scaling
+  return __hiloint2double(hv + (e << 20), __double2loint(v));
+}
+
+template <int NQ, int KP>
+__global__ void __launch_bounds__(512, 1)
+    k_lincomb_oz2(int64_t n, int p, const double* A, int lda, int q, const double* __restrict__ Cm, double* Y,
+                  int ldy, const double* D, int ldd) {
+  using Cf = OzL2<NQ, KP>;
+  constexpr int NP = 256, NH = NQ / 2;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  int* er = reinterpret_cast<int*>(sm + Cf::ER);
+  int* ec = reinterpret_cast<int*>(sm + Cf::EC);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + Cf::BAR);
+  uint64_t* done = full + 1;
+  uint64_t* rawb = full + 2;
+  volatile int* rcount = reinterpret_cast<volatile int*>(sm + Cf::CTL);
+  volatile int* abort = rcount + 1;
+  volatile int* ncommit = rcount + 2;
+  uint32_t* slot = reinterpret_cast<uint32_t*>(sm + Cf::SLOT);
+  double* raw = reinterpret_cast<double*>(sm + Cf::RAW);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int64_t ntiles = (n + 127) / 128;
+  const int rs = p | 1;
+
+  for (uint32_t o = tid * 16u; o < Cf::RAW; o += 512u * 16u) *reinterpret_cast<uint4*>(sm + o) = make_uint4(0, 0, 0, 0);
+  if (tid == 0) {
+    oz_bar_init(full, 1);
+    oz_bar_init(done, 1);
+    oz_bar_init(rawb, 1);
+    *rcount = 0;
+    *abort = 0;
+    *ncommit = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) oz_tmem_alloc(slot, Cf::TCOLS);
+  oz_fence_before();
+  __syncthreads();
+  oz_fence_after();
+  const uint32_t tmem = *slot;
+
+  if (tid >= 256) {
+    // ===================== producers =====================
+    const int pt = tid - 256;
+    // C once: column exponents, then the digits (B operand row l = output column l, K = rows of C)
+    if (pt < q) {
+      int e = 0;
+      for (int k = 0; k < p; k++) e = max(e, oz_bexp(Cm[k * q + pt]));
+      ec[pt] = e;
+    }
+    oz_named_sync(1, NP);
+    for (int w = pt; w < NQ * (KP / 8); w += NP) {
+      const int l = w % NQ, k8 = w / NQ;
+      const int emax = l < q ? ec[l] : 0;
+      uint32_t pk[OZ_S][4];
+#pragma unroll
+      for (int r = 0; r < 8; r += 2) {
+        const int k = k8 * 8 + r;
+        const double x0 = (l < q && k < p) ? Cm[k * q + l] : 0.0;
+        const double x1 = (l < q && k + 1 < p) ? Cm[(k + 1) * q + l] : 0.0;
+        uint32_t wv[OZ_S];
+        oz_split2(x0, x1, emax, wv);
+#pragma unroll
+        for (int t = 0; t < OZ_S; t++) pk[t][r >> 1] = wv[t];
+      }
+      const uint32_t off = (uint32_t)(l >> 3) * Cf::SBO + (uint32_t)k8 * 128u + (uint32_t)(l & 7) * 16u;
+#pragma unroll
+      for (int t = 0; t < OZ_S; t++)
+        *reinterpret_cast<uint4*>(sm + Cf::B0 + t * Cf::BSZ + off) = make_uint4(pk[t][0], pk[t][1], pk[t][2], pk[t][3]);
+    }
+    int k = 0;
+    for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x, k++) {
+      const int64_t i0 = tl * 128;
+      const int rows = (int)((n - i0) < 128 ? (n - i0) : 128);
+      // the tile's rows of A into raw, row stride rs = p | 1 (odd, so that consecutive rows fall in
+      // different banks for the row-wise scans below); the previous tile's digits were written from
+      // raw before `full`
+      for (int i = pt >> 6; i < rows; i += NP >> 6)
+        for (int c = pt & 63; c < p; c += 64) oz_cp8(raw + i * rs + c, A + (i0 + i) * lda + c, true);
+      oz_cp_wait();
+      // row exponents of tile k use the half of tile k - 2: wait until that one was read back
+      if (k >= 2) {
+        const long long t0 = clock64();
+        while (*rcount < k - 1 && !*abort)
+          if (clock64() - t0 > OZ_WAIT) *abort = 1;
+      }
+      oz_named_sync(1, NP);
+      int* erk = er + (k & 1) * 128;
+      if (pt < 128) {
+        int e = 0;
+        if (pt < rows)
+          for (int c = 0; c < p; c++) e = max(e, oz_bexp(raw[pt * rs + c]));
+        erk[pt] = e;
+      }
+      if (k >= 1) oz_wait2(done, (uint32_t)((k - 1) & 1), abort);  // previous MMAs read the A operand
+      oz_named_sync(1, NP);
+      if (*abort) break;
+      // digits: item = (row t, octet k8); rows beyond the tile are zero
+      for (int w = pt; w < 128 * (KP / 8); w += NP) {
+        const int t = w & 127, k8 = w >> 7;
+        const int emax = erk[t];
+        uint32_t pk[OZ_S][4];
+#pragma unroll
+        for (int r = 0; r < 8; r += 2) {
+          const int c = k8 * 8 + r;
+          const double x0 = (t < rows && c < p) ? raw[t * rs + c] : 0.0;
+          const double x1 = (t < rows && c + 1 < p) ? raw[t * rs + c + 1] : 0.0;
+          uint32_t wv[OZ_S];
+          oz_split2(x0, x1, emax, wv);
+#pragma unroll
+          for (int s = 0; s < OZ_S; s++) pk[s][r >> 1] = wv[s];
+        }
+        const uint32_t off = (uint32_t)(t >> 3) * Cf::SBO + (uint32_t)k8 * 128u + (uint32_t)(t & 7) * 16u;
+#pragma unroll
+        for (int s = 0; s < OZ_S; s++)
+          *reinterpret_cast<uint4*>(sm + Cf::A0 + s * Cf::ASZ + off) = make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
+      }
+      oz_fence_proxy();
+      oz_named_sync(1, NP);
+      if (pt == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(oz_smem(full)) : "memory");
+    }
+  } else {
+    // ===================== consumers =====================
+    const int t = tid & 127, cb = (warp >> 2) * NH;
+    const uint32_t sA = oz_smem(sm + Cf::A0), sB = oz_smem(sm + Cf::B0);
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    int k = 0;
+    for (int64_t tl = blockIdx.x; tl < ntiles; tl += gridDim.x, k++) {
+      if (tid == 0) {
+        if (oz_wait2(full, (uint32_t)(k & 1), abort)) {
+          oz_fence_after();
+#pragma unroll
+          for (int ks = 0; ks < KP / 16; ks++) oz_mma_step<NQ>(tmem, sA, Cf::ASZ, sB, Cf::BSZ, Cf::SBO, ks, ks == 0);
+          oz_commit(done);
+          *ncommit = k + 1;
+        }
+      }
+      oz_wait2(done, (uint32_t)(k & 1), abort);
+      oz_named_sync(2, 256);
+      if (*abort) break;
+      oz_fence_after();
+      const int64_t row = tl * 128 + t;
+      const int erow = er[(k & 1) * 128 + t];
+#pragma unroll
+      for (int c0 = 0; c0 < NH; c0 += 8) {
+        float v[OZ_LV][8];
+#pragma unroll
+        for (int L = 0; L < OZ_LV; L++) oz_ld8(tmem + lane_base + (uint32_t)(L * NQ + cb + c0), v[L]);
+        oz_wait_ld();
+        if (row < n) {
+#pragma unroll
+          for (int c = 0; c < 8; c++) {
+            const int col = cb + c0 + c;
+            if (col >= q) continue;
+            float lv[OZ_LV];
+#pragma unroll
+            for (int L = 0; L < OZ_LV; L++) lv[L] = v[L][c];
+            float vh, vl;
+            oz_levels(lv, vh, vl);
+            double y = (erow == 0 || ec[col] == 0) ? 0.0
+                                                  : oz_df_to_f64(vh, vl, (erow - 1022) + (ec[col] - 1022) - 14);
+            if (D) y += D[row * ldd + col];
+            Y[row * ldy + col] = y;
+          }
+        }
+      }
+      oz_fence_before();
+      oz_named_sync(2, 256);
+      if (tid == 0) { __threadfence_block(); *rcount = k + 1; }
+    }
+  }
+  __syncthreads();
+  if (*abort) {
+    if (tid == 0) atomicExch(&lob_oz_fault, 1);
+    const int nc = *ncommit;
+    if (nc > 0) oz_bar_wait(done, (uint32_t)((nc - 1) & 1), 1ll << 31);
+  }
+  oz_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    oz_fence_after();
+    oz_tmem_free(tmem, Cf::TCOLS);
+  }
+}
+
+}  // namespace
+
 // ---- launchers --------------------------------------------------------------------------------
 
 // Doubles of workspace the tensor-core Gram needs (the CTAs' partial sums).
 size_t lob_gram_oz_work_doubles() { return (size_t)256 * 2 * 64 * 64; }
 
 bool lob_oz_fits(int p, int q) { return p >= 1 && p <= 64 && q >= 1 && q <= 64; }
+
+// Whether the tensor-core kernels beat the double-float ones for this shape. Their cost is mostly
+// a fixed pipeline cost per 64- or 128-row block, the double-float kernels' grows with p q; measured
+// at n = 8,000,000 (ms, tensor cores / double-float): Gram 16 x 16 4.9 / 2.2, 16 x 32 5.2 / 5.7,
+// 48 x 48 5.6 / 11.3; X C 16 -> 16 2.4 / 1.7, 32 -> 16 2.7 / 2.9, 48 -> 48 3.9 / 12.1.
+bool lob_oz_pays(int p, int q) { return lob_oz_fits(p, q) && p * q >= 512; }
 
 // G0 = L0^T R and, with L1, G1 = L1^T R (p x q each, row-major), FP64-class on the tensor cores.
 int lob_gram_oz_launch(int64_t n, int p, const double* L0, int ld0, const double* L1, int ld1, int q,
@@ -968,6 +1209,25 @@ int lob_lincomb_oz_launch(int64_t n, int p, const double* A, int lda, int q, con
   if (!lob_oz_fits(p, q) || n < 0) return LOB_ERR_ARG;
   if (n == 0) return LOB_OK;
   const int nq = (q + 15) / 16 * 16, kp = (p + 15) / 16 * 16;
+  {  // the pipelined kernel: persistent CTAs over tiles of 128 rows
+    const int sms = lob_sm_count();
+    if (sms < 0) return LOB_ERR_CUDA;
+    const int64_t nt = (n + 127) / 128;
+    const unsigned grid2 = (unsigned)(nt < sms ? nt : sms);
+    auto go2 = [&](auto kern, uint32_t bytes) -> int {
+      LOB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+      (kern<<<grid2, 512, bytes, st>>>(n, p, A, lda, q, C, Y, ldy, D, ldd), LOB_LAUNCHED());
+      LOB_CUDA(cudaGetLastError());
+      return LOB_OK;
+    };
+#define LOB_OZ_L2(NQ_, KP_) \
+    if (nq == NQ_ && kp == KP_) return go2(k_lincomb_oz2<NQ_, KP_>, OzL2<NQ_, KP_>::BYTES)
+    LOB_OZ_L2(16, 16); LOB_OZ_L2(16, 32); LOB_OZ_L2(16, 48); LOB_OZ_L2(16, 64);
+    LOB_OZ_L2(32, 16); LOB_OZ_L2(32, 32); LOB_OZ_L2(32, 48); LOB_OZ_L2(32, 64);
+    LOB_OZ_L2(48, 16); LOB_OZ_L2(48, 32); LOB_OZ_L2(48, 48);
+    LOB_OZ_L2(64, 16); LOB_OZ_L2(64, 32);
+#undef LOB_OZ_L2
+  }
   const unsigned grid = (unsigned)((n + 127) / 128);
   // Shared memory is requested so that no more CTAs share an SM than its 512 tensor-memory columns
   // can hold at once (a CTA whose allocation would not fit waits in tcgen05.alloc otherwise).
@@ -1002,4 +1262,5 @@ int lob_oz_fault_take(cudaStream_t st) {
   }
   return h;
 }
+
 

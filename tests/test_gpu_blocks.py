@@ -16,9 +16,11 @@ def t(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "tc"])
 @pytest.mark.parametrize("n,p,q", [(1, 1, 1), (1000, 16, 16), (4097, 48, 48), (3000, 8, 100), (20000, 49, 17)])
 def test_gram_integer_exact(mode, n, p, q):
+    if mode == "tc" and q > 64:
+        pytest.skip("the tensor-core kernel takes p, q <= 64")
     import paper_1609_01689_gb300 as lob
     rng = np.random.default_rng(n + p + q)
     A = rng.integers(-8, 9, (n, p)).astype(np.float64)
@@ -40,10 +42,12 @@ def test_gram_random_bound(mode, rel):
     assert np.all(np.abs(G - ref) <= bound)
 
 
-@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "tc"])
 @pytest.mark.parametrize("n,p,q", [(1, 1, 1), (5000, 48, 16), (4097, 32, 16), (1000, 7, 5), (129, 64, 16),
                                    (257, 65, 16), (300, 96, 40)])
 def test_lincomb_exact_and_bound(mode, n, p, q):
+    if mode == "tc" and p > 64:
+        pytest.skip("the tensor-core kernel takes p, q <= 64")
     import paper_1609_01689_gb300 as lob
     rng = np.random.default_rng(n * 3 + p)
     A = rng.integers(-8, 9, (n, p)).astype(np.float64)
@@ -52,6 +56,13 @@ def test_lincomb_exact_and_bound(mode, n, p, q):
     A = rng.standard_normal((n, p)); C = rng.standard_normal((p, q))
     Y = lob.lincomb(t(A), t(C), mode).cpu().numpy()
     rel = 2 * p * 2.0 ** -53 if mode == "fp64" else 2.0 ** -44 * p
+    if mode == "tc":  # scaling groups: rows of A, columns of C (see test_lincomb_tensor_cores)
+        ra = np.abs(A).max(axis=1, keepdims=True)
+        cc = np.abs(C).max(axis=0, keepdims=True)
+        bnd = 2.0 ** -44 * (np.abs(A) @ np.abs(C) + ra * np.abs(C).sum(axis=0, keepdims=True)
+                            + np.abs(A).sum(axis=1, keepdims=True) * cc)
+        assert np.all(np.abs(Y - oracle.lincomb(A, C)) <= bnd + 1e-300)
+        return
     assert np.all(np.abs(Y - oracle.lincomb(A, C)) <= rel * (np.abs(A) @ np.abs(C)) + 1e-300)
 
 
@@ -310,7 +321,7 @@ def test_gram_tensor_cores(n, p, q, spread):
     rng = np.random.default_rng(n + 7 * p + q + spread)
     A = _scaled(rng, n, p, spread)
     B = _scaled(rng, n, q, spread)
-    G = lob.gram(t(A), t(B), "mixed").cpu().numpy()
+    G = lob.gram(t(A), t(B), "tc").cpu().numpy()
     ref = oracle.gram(A, B)
     # group maxima over 128-row chunks, per column
     nc = (n + 127) // 128
@@ -334,7 +345,7 @@ def test_lincomb_tensor_cores(n, p, q, spread):
     C = rng.standard_normal((p, q)) * 2.0 ** rng.integers(-spread, spread + 1, q)[None, :]
     if p > 2:
         A[:, 1] = 0.0
-    Y = lob.lincomb(t(A), t(C), "mixed").cpu().numpy()
+    Y = lob.lincomb(t(A), t(C), "tc").cpu().numpy()
     ref = oracle.lincomb(A, C)
     ra = np.abs(A).max(axis=1, keepdims=True)
     cc = np.abs(C).max(axis=0, keepdims=True)
