@@ -193,7 +193,7 @@ int lob_rayleigh_ritz(int32_t m, const double* G, const double* M, double* theta
  * memory (a framework's caching allocator, a fixed memory budget), or a latency-critical loop
  * where an allocation's implicit device synchronisation is not acceptable. The caller still
  * passes every input and output (same meaning as lob_rayleigh_ritz). The workspace is a
- * file-scope device array sized for m <= 192 (three 192 x 192 FP64 matrices, 884,736 bytes),
+ * file-scope device array sized for m <= 192 (five 192 x 192 FP64 matrices, 1,474,560 bytes),
  * held by every GPU that loads the library until the process exits; m outside [1, 192]
  * returns LOB_ERR_ARG. The first call on each device looks up the array's device address
  * (with that device current) and keeps it for the rest of the process; make that first call

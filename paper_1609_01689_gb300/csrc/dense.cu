@@ -14,10 +14,10 @@
 
 namespace {
 
-constexpr int RR_THREADS = 512;  // at most; rounds with more blocks loop
+constexpr int RR_THREADS = 544;  // at most (every 2x2 block of a round has its thread up to m = 64)
 
 
-// ---- cyclic Jacobi with 2x2-block updates (both kernels) ----
+// ---- cyclic Jacobi with 2x2-block updates (double-float and FP32 eigensolvers) ----
 // Round r of the round-robin order pairs the indices as (p_k, q_k), k < m/2, all disjoint.
 // A <- J^T A J with J the product of the round's rotations; for the 2x2 block of rows {p1, q1}
 // and columns {p2, q2} the new values depend only on that block, so one thread updates a whole
@@ -29,11 +29,6 @@ constexpr int RR_THREADS = 512;  // at most; rounds with more blocks loop
 //   phase 2: all threads update the 2x2 blocks of A by round r's rotations
 //   barrier
 // Angles and pairs are double-buffered by round parity.
-__device__ __forceinline__ void rot2(double& x, double& y, double c, double s) {
-  const double u = c * x - s * y, v = s * x + c * y;
-  x = u;
-  y = v;
-}
 __device__ __forceinline__ void rot2(d2& x, d2& y, d2 c, d2 s) { d2_rot(x, y, c, s); }
 __device__ __forceinline__ void rot2(float& x, float& y, float c, float s) {
   const float u = fmaf(c, x, -s * y), v = fmaf(s, x, c * y);
@@ -44,26 +39,14 @@ __device__ __forceinline__ double hi64(float x) { return (double)x; }
 __device__ __forceinline__ bool nonzero(float x) { return x != 0.f; }
 __device__ __forceinline__ float ident_one(float) { return 1.f; }
 __device__ __forceinline__ float ident_zero(float) { return 0.f; }
-__device__ __forceinline__ double hi64(double x) { return x; }
 __device__ __forceinline__ double hi64(d2 x) { return d2_hi64(x); }
-__device__ __forceinline__ bool nonzero(double x) { return x != 0.0; }
 __device__ __forceinline__ bool nonzero(d2 x) { return x.hi != 0.f; }
-__device__ __forceinline__ double ident_one(double) { return 1.0; }
 __device__ __forceinline__ d2 ident_one(d2) { return d2{1.f, 0.f}; }
-__device__ __forceinline__ double ident_zero(double) { return 0.0; }
 __device__ __forceinline__ d2 ident_zero(d2) { return d2{0.f, 0.f}; }
 
 // rotation (c, s) that zeros a_pq (GVL 8.5: tau = (a_qq - a_pp) / (2 a_pq), t = sign(tau) /
-// (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c). FP64: all in FP64. Double-float:
+// (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c). FP32: all in FP32. Double-float:
 // the angle in FP32 from a double-float difference, then c, s in double-float from that exact t.
-__device__ __forceinline__ void jac_angle(double app, double aqq, double apq, double& c, double& s) {
-  c = 1.0; s = 0.0;
-  if (apq == 0.0) return;
-  const double tau = (aqq - app) / (2.0 * apq);
-  const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-  c = 1.0 / sqrt(1.0 + t * t);
-  s = t * c;
-}
 __device__ __forceinline__ void jac_angle(float app, float aqq, float apq, float& c, float& s) {
   c = 1.f; s = 0.f;
   if (apq == 0.f) return;
@@ -150,6 +133,7 @@ __device__ void jacobi_blocks(int m, int ld, E* A, E* V, double stop_ratio, E* c
     }
   };
   int rcount = 0;
+  double prev = 0.0;
   for (int sweep = 0; sweep < 40; sweep++) {
     double off = 0.0, fro = 0.0;
     for (int e = tid; e < mm; e += nt) {
@@ -168,6 +152,9 @@ __device__ void jacobi_blocks(int m, int ld, E* A, E* V, double stop_ratio, E* c
     }
     __syncthreads();
     if (*s_off <= stop_ratio * *s_fro || *s_off == 0.0) break;
+    // near the arithmetic's floor a sweep that no longer reduces ||off||^2 fourfold ends it
+    if (sweep > 0 && *s_off <= 1e-8 * *s_fro && *s_off > 0.25 * prev) break;
+    prev = *s_off;
     for (int round = 0; round < mp - 1; round++, rcount++) {
       const int b = rcount & 1;
       E* cc = cs_c + b * 96;
@@ -228,8 +215,28 @@ __device__ void jacobi_blocks(int m, int ld, E* A, E* V, double stop_ratio, E* c
   }
 }
 
-// SMEM: the matrices live in dynamic shared memory (the address space is a compile-time
-// property, so every access is a shared-memory instruction); otherwise in the global workspace.
+// ---- FP64 Rayleigh-Ritz (eq. 9): G c = theta M c for one CTA ----
+// GB300's FP64 pipe retires about 1.6 multiply-adds per clock per SM, so a dependent chain of FP64
+// scalar operations (a QL recurrence, a Jacobi angle per rotation) stalls for tens of clocks at every
+// step. The solve therefore keeps its FP64 work in parallel products and does the iterative part in
+// FP32:
+//   1. M = L L^T and A = L^{-1} G L^{-T} in FP64 (right-looking, every thread at every step);
+//   2. cyclic Jacobi on fl32(A) gives an approximate eigenbasis X (FP32 accuracy);
+//   3. iterative refinement of X in FP64 (Ogita and Aishima, "Iterative refinement for symmetric
+//      eigenvalue decomposition", Japan J. Indust. Appl. Math. 35, 2018): with R = I - X^T X and
+//      S = X^T A X, the Ritz values are l_i = s_ii / (1 - r_ii), and X <- X + X E with
+//      e_ij = (s_ij + l_j r_ij) / (l_j - l_i) for |l_i - l_j| > d, e_ij = r_ij / 2 otherwise
+//      (e_ii = r_ii / 2), d = 2 (||S - diag(l)|| + ||A|| ||R||) (Frobenius norms). The error
+//      squares at every step, so two steps take FP32 accuracy to FP64's. Two safeguards keep the
+//      iteration from oscillating on pairs that FP32 could not separate: d never falls below an
+//      earlier step's, and a pair whose first-order correction exceeds 1e-3 is treated as close;
+//   4. close pairs are not separated by step 3: where S (of the final X) still couples two
+//      columns, FP64 Jacobi rotations on S and X separate them (skipped when S is diagonal to
+//      rounding);
+//   5. C = L^{-T} X, columns in ascending order of the Ritz values.
+// The FP64 multiply-adds are about m^3 (1 + 2 per refinement step); X E runs in FP32, as E is
+// small (its rounding error is below the next step's or the final accuracy).
+// Storage: A, L, X, T and SR (m x m each, row stride ld); SR holds S above its diagonal and R below.
 template <bool SMEM>
 __device__ __forceinline__ void rr_body(int m, const double* __restrict__ G, const double* __restrict__ Mi,
                                         double* __restrict__ theta, double* __restrict__ C,
@@ -237,16 +244,66 @@ __device__ __forceinline__ void rr_body(int m, const double* __restrict__ G, con
                                         unsigned char* rr_sm) {
   const int ld = SMEM ? m + 1 : m;  // padded rows in shared memory: column walks hit distinct banks
   double* base = SMEM ? reinterpret_cast<double*>(rr_sm) : work;
-  double* A = base;          // m x m
-  double* L = base + m * ld;  // m x m, lower Cholesky factor
-  double* V = L + m * ld;    // m x m, eigenvectors
-  __shared__ double cs_c[192], cs_s[192];
+  double* A = base;
+  double* L = A + m * ld;
+  double* X = L + m * ld;
+  double* T = X + m * ld;
+  double* SR = T + m * ld;
+  __shared__ float cs_c[192], cs_s[192];
   __shared__ int pr_p[192], pr_q[192];
   __shared__ double red[64];
+  __shared__ double inv[192], lam[192], rdg[192];
+  __shared__ int rk[192];
+  __shared__ unsigned pmask[192 * 192 / 32];
   __shared__ int s_fail;
-  __shared__ double s_off, s_fro;
+  __shared__ double s_off, s_fro, s_sc[4];
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int mm = m * m;
+  const int mm = m * m, ntri = m * (m + 1) / 2;
+  // element (r, c) updates of the right-looking loops: thread = (R0, C0), RS rows at a time
+  // (the launch gives nt >= m threads)
+  const int RS = nt / m, R0 = tid / m, C0 = tid % m;
+  const bool upd = tid < RS * m;
+  // sums over the CTA of one or two per-thread values (every thread gets the result)
+  auto sum2 = [&](double a, double b, double& ra, double& rb) {
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_down_sync(0xFFFFFFFFu, a, o);
+      b += __shfl_down_sync(0xFFFFFFFFu, b, o);
+    }
+    if ((tid & 31) == 0) { red[tid >> 5] = a; red[32 + (tid >> 5)] = b; }
+    __syncthreads();
+    if (tid == 0) {
+      double x = 0.0, y = 0.0;
+      for (int w = 0; w < (nt + 31) / 32; w++) { x += red[w]; y += red[32 + w]; }
+      s_sc[0] = x; s_sc[1] = y;
+    }
+    __syncthreads();
+    ra = s_sc[0]; rb = s_sc[1];
+    __syncthreads();
+  };
+  auto max1 = [&](double a) -> double {
+    for (int o = 16; o > 0; o >>= 1) a = fmax(a, __shfl_down_sync(0xFFFFFFFFu, a, o));
+    if ((tid & 31) == 0) red[tid >> 5] = a;
+    __syncthreads();
+    if (tid == 0) {
+      double x = 0.0;
+      for (int w = 0; w < (nt + 31) / 32; w++) x = fmax(x, red[w]);
+      s_sc[2] = x;
+    }
+    __syncthreads();
+    const double r = s_sc[2];
+    __syncthreads();
+    return r;
+  };
+  // Xm <- L^{-T} Xm for all columns (right-looking back substitution)
+  auto back_sub = [&](double* Xm) {
+    for (int i = m - 1; i >= 0; i--) {
+      if (tid < m) Xm[i * ld + tid] *= inv[i];
+      __syncthreads();
+      if (upd)
+        for (int r = R0; r < i; r += RS) Xm[r * ld + C0] -= L[i * ld + r] * Xm[i * ld + C0];
+      __syncthreads();
+    }
+  };
 
   // symmetric copies from the upper triangles
   for (int e = tid; e < mm; e += nt) {
@@ -254,62 +311,60 @@ __device__ __forceinline__ void rr_body(int m, const double* __restrict__ G, con
     const int a = i < j ? i : j, b = i < j ? j : i;
     A[i * ld + j] = G[a * m + b];
     L[i * ld + j] = Mi[a * m + b];
-    V[i * ld + j] = (i == j) ? 1.0 : 0.0;
+    X[i * ld + j] = (i == j) ? 1.0 : 0.0;
   }
   if (tid == 0) s_fail = 0;
   __syncthreads();
 
-  // 1. right-looking Cholesky in place on L (lower part)
+  // 1. right-looking Cholesky in place on L (lower part), inv[j] = 1 / L_jj
   for (int j = 0; j < m; j++) {
     if (tid == 0) {
       const double d = L[j * ld + j];
-      if (!(d > 0.0)) s_fail = j + 1;
-      else L[j * ld + j] = sqrt(d);
+      if (!(d > 0.0)) {
+        s_fail = j + 1;
+      } else {
+        const double r = sqrt(d);
+        L[j * ld + j] = r;
+        inv[j] = 1.0 / r;
+      }
     }
     __syncthreads();
     if (s_fail) break;
-    const double ljj = L[j * ld + j];
-    for (int i = j + 1 + tid; i < m; i += nt) L[i * ld + j] /= ljj;
+    const double ij = inv[j];
+    for (int i = j + 1 + tid; i < m; i += nt) L[i * ld + j] *= ij;
     __syncthreads();
-    const int rem = m - j - 1;
-    for (int e = tid; e < rem * rem; e += nt) {
-      const int i = j + 1 + e / rem, k = j + 1 + e % rem;
-      if (k <= i) L[i * ld + k] -= L[i * ld + j] * L[k * ld + j];
-    }
+    if (upd && C0 > j)
+      for (int i = j + 1 + R0; i < m; i += RS)
+        if (C0 <= i) L[i * ld + C0] -= L[i * ld + j] * L[C0 * ld + j];
     __syncthreads();
   }
   if (s_fail) {
     if (tid == 0) *info = s_fail;
     return;
   }
-  if (chol_only) {  // Cholesky-QR: C = L^{-T} (columns of the identity through the back substitution)
-    for (int j = tid; j < m; j += nt) {
-      theta[j] = 1.0;
-      for (int i = m - 1; i >= 0; i--) {
-        double s = (i == j) ? 1.0 : 0.0;
-        for (int t = i + 1; t < m; t++) s -= L[t * ld + i] * C[t * m + j];
-        C[i * m + j] = s / L[i * ld + i];
-      }
-    }
+  if (chol_only) {  // Cholesky-QR: C = L^{-T}
+    back_sub(X);
+    for (int e = tid; e < mm; e += nt) C[e] = X[(e / m) * ld + e % m];
+    for (int j = tid; j < m; j += nt) theta[j] = 1.0;
     if (tid == 0) *info = 0;
     return;
   }
-  // 2a. A <- L^{-1} A: forward substitution, one column per thread
-  for (int c = tid; c < m; c += nt)
-    for (int i = 0; i < m; i++) {
-      double s = A[i * ld + c];
-      for (int t = 0; t < i; t++) s -= L[i * ld + t] * A[t * ld + c];
-      A[i * ld + c] = s / L[i * ld + i];
-    }
-  __syncthreads();
-  // 2b. A <- A L^{-T}: forward substitution on each row
-  for (int r = tid; r < m; r += nt)
-    for (int i = 0; i < m; i++) {
-      double s = A[r * ld + i];
-      for (int t = 0; t < i; t++) s -= L[i * ld + t] * A[r * ld + t];
-      A[r * ld + i] = s / L[i * ld + i];
-    }
-  __syncthreads();
+  // 2. A <- L^{-1} A L^{-T} (right-looking: row i, then column i, is final once the earlier ones
+  // have been subtracted), made exactly symmetric
+  for (int i = 0; i < m; i++) {
+    if (tid < m) A[i * ld + tid] *= inv[i];
+    __syncthreads();
+    if (upd)
+      for (int r = i + 1 + R0; r < m; r += RS) A[r * ld + C0] -= L[r * ld + i] * A[i * ld + C0];
+    __syncthreads();
+  }
+  for (int i = 0; i < m; i++) {
+    if (tid < m) A[tid * ld + i] *= inv[i];
+    __syncthreads();
+    if (upd)
+      for (int c = i + 1 + R0; c < m; c += RS) A[C0 * ld + c] -= A[C0 * ld + i] * L[c * ld + i];
+    __syncthreads();
+  }
   for (int e = tid; e < mm; e += nt) {
     const int i = e / m, j = e % m;
     if (i < j) {
@@ -319,23 +374,210 @@ __device__ __forceinline__ void rr_body(int m, const double* __restrict__ G, con
     }
   }
   __syncthreads();
-
-  // 3. cyclic Jacobi (round-robin order, 2x2-block updates)
-  jacobi_blocks<double>(m, ld, A, V, 1e-30, cs_c, cs_s, pr_p, pr_q, red, &s_off, &s_fro);
-  // 4. rank sort (ties by index), C = L^{-T} V in the sorted order
+  // 3. approximate eigenbasis: cyclic Jacobi on fl32(A) to ||off|| <= 3e-7 ||A|| or FP32's floor
+  // (F and VF in T's space)
+  {
+    float* F = reinterpret_cast<float*>(T);
+    float* VF = F + m * ld;
+    for (int e = tid; e < mm; e += nt) {
+      const int i = e / m, j = e % m;
+      F[i * ld + j] = (float)A[i * ld + j];
+      VF[i * ld + j] = (i == j) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    jacobi_blocks<float>(m, ld, F, VF, 1e-13, cs_c, cs_s, pr_p, pr_q, red, &s_off, &s_fro);
+    for (int e = tid; e < mm; e += nt) {
+      const int i = e / m, j = e % m;
+      X[i * ld + j] = (double)VF[i * ld + j];
+    }
+  }
+  double nA;
+  {
+    double a2 = 0.0, z = 0.0;
+    for (int e = tid; e < mm; e += nt) {
+      const double x = A[(e / m) * ld + e % m];
+      a2 += x * x;
+    }
+    sum2(a2, 0.0, a2, z);  // (its barriers also order X's writes above)
+    nA = sqrt(a2);
+  }
+  // 4. refinement: R = I - X^T X, S = X^T A X, then X <- X + X E
+  double* X32s = T;  // FP32 copies of X and E for the correction product (T's space, free by then)
+  double dl = 0.0, cmax = 0.0;
+  for (int it = 0; it < 6; it++) {
+    for (int e = tid; e < mm; e += nt) {  // T = A X
+      const int i = e / m, j = e % m;
+      double s = 0.0;
+      for (int k = 0; k < m; k++) s = fma(A[i * ld + k], X[k * ld + j], s);
+      T[i * ld + j] = s;
+    }
+    __syncthreads();
+    for (int b = tid; b < ntri; b += nt) {  // S (upper), R (lower; its diagonal in rdg)
+      int i, j;
+      tri_index(b, m, i, j);
+      double s = 0.0, r = 0.0;
+      for (int k = 0; k < m; k++) {
+        const double xi = X[k * ld + i];
+        s = fma(xi, T[k * ld + j], s);
+        r = fma(xi, X[k * ld + j], r);
+      }
+      SR[i * ld + j] = s;
+      if (i < j) SR[j * ld + i] = -r;
+      else rdg[i] = 1.0 - r;
+    }
+    __syncthreads();
+    for (int i = tid; i < m; i += nt) lam[i] = SR[i * ld + i] / (1.0 - rdg[i]);
+    __syncthreads();
+    double so = 0.0, sr = 0.0;
+    for (int e = tid; e < mm; e += nt) {
+      const int i = e / m, j = e % m;
+      if (i < j) {
+        const double s = SR[i * ld + j], r = SR[j * ld + i];
+        so += 2.0 * s * s;
+        sr += 2.0 * r * r;
+      } else if (i == j) {
+        const double s = SR[i * ld + i] - lam[i];
+        so += s * s;
+        sr += rdg[i] * rdg[i];
+      }
+    }
+    sum2(so, sr, so, sr);
+    dl = fmax(dl, 2.0 * (sqrt(so) + nA * sqrt(sr)));  // never below an earlier step's
+    // E, written as FP32 into the second half of T's space, X as FP32 into the first half
+    float* X32 = reinterpret_cast<float*>(X32s);
+    float* E32 = X32 + m * ld;
+    double emax = 0.0, cmx = 0.0;  // largest correction; largest coupling between close pairs
+    for (int e = tid; e < mm; e += nt) {
+      const int i = e / m, j = e % m;
+      X32[i * ld + j] = (float)X[i * ld + j];
+      if (i > j) continue;
+      if (i == j) {
+        const double d = 0.5 * rdg[i];
+        E32[i * ld + i] = (float)d;
+        emax = fmax(emax, fabs(d));
+        continue;
+      }
+      const double s = SR[i * ld + j], r = SR[j * ld + i];
+      double eij = 0.0, eji = 0.0;
+      bool sep = fabs(lam[i] - lam[j]) > dl;
+      if (sep) {
+        eij = (s + lam[j] * r) / (lam[j] - lam[i]);
+        eji = (s + lam[i] * r) / (lam[i] - lam[j]);
+        sep = fmax(fabs(eij), fabs(eji)) <= 1e-3;  // a larger first-order step would not converge
+      }
+      if (!sep) {
+        eij = 0.5 * r;
+        eji = eij;
+        cmx = fmax(cmx, fabs(s));
+      }
+      E32[i * ld + j] = (float)eij;
+      E32[j * ld + i] = (float)eji;
+      emax = fmax(emax, fmax(fabs(eij), fabs(eji)));
+    }
+    emax = max1(emax);  // (its barriers also order the FP32 copies)
+    cmax = max1(cmx);
+    for (int e = tid; e < mm; e += nt) {  // X + X E into SR's space
+      const int i = e / m, j = e % m;
+      float s = 0.f;
+      for (int k = 0; k < m; k++) s = fmaf(X32[i * ld + k], E32[k * ld + j], s);
+      SR[i * ld + j] = X[i * ld + j] + (double)s;
+    }
+    __syncthreads();
+    double* t = X; X = SR; SR = t;
+    if (emax <= 1e-9) break;  // the update just made leaves an error of order emax^2
+  }
+  // 5. close pairs still coupled: FP64 Jacobi rotations on S = X^T A X (of the final X) and on X,
+  // pair by pair, wherever |s_pq| exceeds the rounding level of S
+  const double thr = 32.0 * 1.1102230246251565e-16 * nA;
+  if (cmax > thr) {
+    for (int e = tid; e < mm; e += nt) {  // T = A X
+      const int i = e / m, j = e % m;
+      double s = 0.0;
+      for (int k = 0; k < m; k++) s = fma(A[i * ld + k], X[k * ld + j], s);
+      T[i * ld + j] = s;
+    }
+    __syncthreads();
+    for (int b = tid; b < ntri; b += nt) {  // S, both triangles
+      int i, j;
+      tri_index(b, m, i, j);
+      double s = 0.0;
+      for (int k = 0; k < m; k++) s = fma(X[k * ld + i], T[k * ld + j], s);
+      SR[i * ld + j] = s;
+      SR[j * ld + i] = s;
+    }
+    __syncthreads();
+    // each sweep: flag the coupled pairs (bit p m + q of pmask, p < q) in parallel, then rotate
+    // them in row-major order, skipping a pair that earlier rotations of the sweep decoupled
+    const int nw = (mm + 31) / 32;
+    for (int sweep = 0; sweep < 10; sweep++) {
+      for (int w = tid; w < nw; w += nt) {
+        unsigned bits = 0u;
+        for (int b = 0; b < 32; b++) {
+          const int e = w * 32 + b;
+          if (e >= mm) break;
+          const int p = e / m, q = e % m;
+          if (p < q && fabs(SR[p * ld + q]) > thr) bits |= 1u << b;
+        }
+        pmask[w] = bits;
+      }
+      __syncthreads();
+      bool any = false;  // uniform: every thread reads the same values after the same barriers
+      for (int w = 0; w < nw; w++) {
+        unsigned bits = pmask[w];
+        while (bits) {
+          const int e = w * 32 + __ffs(bits) - 1;
+          bits &= bits - 1u;
+          const int p = e / m, q = e % m;
+          const double spq = SR[p * ld + q];
+          if (!(fabs(spq) > thr)) continue;
+          any = true;
+          const double spp = SR[p * ld + p], sqq = SR[q * ld + q];
+          const double tau = (sqq - spp) / (2.0 * spq);
+          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          const double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+          __syncthreads();  // every thread has read S before any writes
+          for (int k = tid; k < m; k += nt) {
+            if (k == p) {
+              SR[p * ld + p] = spp - t * spq;
+              SR[q * ld + q] = sqq + t * spq;
+              SR[p * ld + q] = 0.0;
+              SR[q * ld + p] = 0.0;
+            } else if (k != q) {
+              const double a = SR[k * ld + p], b = SR[k * ld + q];
+              const double na = c * a - sn * b, nb = sn * a + c * b;
+              SR[k * ld + p] = na;
+              SR[p * ld + k] = na;
+              SR[k * ld + q] = nb;
+              SR[q * ld + k] = nb;
+            }
+            const double xa = X[k * ld + p], xb = X[k * ld + q];
+            X[k * ld + p] = c * xa - sn * xb;
+            X[k * ld + q] = sn * xa + c * xb;
+          }
+          __syncthreads();
+        }
+      }
+      __syncthreads();  // pmask is rewritten by the next sweep
+      if (!any) break;
+    }
+    for (int i = tid; i < m; i += nt) lam[i] = SR[i * ld + i];
+    __syncthreads();
+  }
+  // 6. rank sort of the Ritz values (ties by index), C = L^{-T} X in that order
   for (int j = tid; j < m; j += nt) {
-    const double wj = A[j * ld + j];
+    const double wj = lam[j];
     int rank = 0;
     for (int i = 0; i < m; i++) {
-      const double wi = A[i * ld + i];
+      const double wi = lam[i];
       rank += (wi < wj) || (wi == wj && i < j);
     }
     theta[rank] = wj;
-    for (int i = m - 1; i >= 0; i--) {
-      double s = V[i * ld + j];
-      for (int t = i + 1; t < m; t++) s -= L[t * ld + i] * C[t * m + rank];
-      C[i * m + rank] = s / L[i * ld + i];
-    }
+    rk[j] = rank;
+  }
+  back_sub(X);  // (its first barrier orders the ranks before their use below)
+  for (int e = tid; e < mm; e += nt) {
+    const int i = e / m, j = e % m;
+    C[i * m + rk[j]] = X[i * ld + j];
   }
   if (tid == 0) *info = 0;
 }
@@ -605,11 +847,11 @@ __global__ void __launch_bounds__(RR_THREADS) k_rr_batch(const lob_bjob* __restr
 
 }  // namespace
 
-// The three m x m matrices live in shared memory when they fit (m <= 64), else in the
-// caller's global workspace (L1-cached).
-// rows padded to m + 1; the double-float solve keeps five double-float matrices and one FP32 one
+// The m x m matrices live in shared memory when they fit (m <= 64), else in the caller's global
+// workspace (L1-cached). Rows padded to m + 1; the FP64 solve keeps five FP64 matrices, the
+// double-float one five double-float matrices and one FP32 one.
 static size_t rr_smem_bytes(int m, bool df = false) {
-  return (df ? 5ull * 8 + 4 : 3ull * 8) * m * (m + 1);
+  return (df ? 5ull * 8 + 4 : 5ull * 8) * m * (m + 1);
 }
 static const size_t RR_SMEM_MAX = 200 * 1024;
 
@@ -635,7 +877,7 @@ int lob_rr_launch_df(int m, const double* G, const double* M, double* theta, dou
   return LOB_OK;
 }
 
-size_t lob_rr_work_doubles(int m) { return 3ull * m * m; }
+size_t lob_rr_work_doubles(int m) { return 5ull * m * m; }
 
 int lob_rr_launch(int m, const double* G, const double* M, double* theta, double* C, int32_t* info, double* work,
                   cudaStream_t st, int chol_only) {
@@ -652,13 +894,13 @@ int lob_rr_launch(int m, const double* G, const double* M, double* theta, double
 }
 
 // ---- Rayleigh-Ritz without allocation -------------------------------------------------------
-// A fixed workspace for lob_rayleigh_ritz_noalloc: three 192 x 192 FP64 matrices (884,736 bytes)
+// A fixed workspace for lob_rayleigh_ritz_noalloc: five 192 x 192 FP64 matrices (1,474,560 bytes)
 // in a file-scope device array, so the call needs no cudaMalloc. Every GPU that loads this
 // library holds it until the process exits. All calls share it: the kernel fills it from its
 // inputs before reading it, and calls that overlap on the GPU (different streams, or different
 // host threads on one device) race on it.
 #define LOB_RR_NOALLOC_MAX_M 192
-static __device__ __align__(256) double g_rr_scratch[3 * LOB_RR_NOALLOC_MAX_M * LOB_RR_NOALLOC_MAX_M];
+static __device__ __align__(256) double g_rr_scratch[5 * LOB_RR_NOALLOC_MAX_M * LOB_RR_NOALLOC_MAX_M];
 
 namespace {
 std::mutex g_rr_scratch_mu;
