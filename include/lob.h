@@ -249,6 +249,14 @@ typedef struct {
                               Cholesky-QR and the 3nb x 3nb Rayleigh-Ritz eigenproblem (eq. 9) */
   int32_t refine_arith;    /* MIXED: LOB_ARITH_* of the refinement phase's SpMM (FP64 values, or
                               double-float values and products, LOB_SPMM_DF64) */
+  int32_t guess_correct;   /* with the eq. 12 guess (n_small > 0, X0 == NULL): 1 = start instead from
+                              the corrected guess of eq. 13, [X_1; Y_1] with column j of Y_1 equal to
+                              -(H_22 - theta_j I)^{-1} H_21 x_j, the linear systems solved
+                              approximately by the block-diagonal preconditioner (Section 3.3.1: its
+                              W^(0) = -[0; Y_1]; needs precond_block at create, else LOB_ERR_ARG).
+                              Costs one SpMM and one preconditioner application. lob_solve only: the
+                              server's engines ignore it */
+  int32_t reserved2;
 } lob_solve_opts;
 
 typedef struct {
@@ -269,6 +277,9 @@ typedef struct {
   double spmm_ms_mode[4];       /* device time (the Y reset, X staging and kernel), */
   double spmm_bytes_mode[4];    /* and algorithmic bytes */
   double residual[64];      /* final ||H x_j - theta_j x_j|| / (||H|| ||x_j||), FP64 */
+  double guess_relres[2];   /* largest relative residual of the first k columns at the start of the
+                               solve: [0] of the initial guess (after its Rayleigh-Ritz step), [1] of
+                               the eq. 13 corrected guess (0 when guess_correct is off) */
 } lob_stats;
 
 /* k smallest eigenpairs of H (Section 3.1 eq. 6; Algorithm 1). 1 <= k <= nb <= 32 (nb - k

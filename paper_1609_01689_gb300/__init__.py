@@ -62,13 +62,15 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("mode", _I32), ("precond", _I32), ("max_iter", _I32), ("refine_iter", _I32), ("norm_H", _D),
                 ("n_small", _I64), ("seed", ctypes.c_uint64), ("precond_shift", _I32), ("precond_solve", _I32),
                 ("precond_steps", _I32), ("verbose", _I32), ("mixed_tol", _D), ("stream", _P),
-                ("n_small_inner", _I64), ("guess_tol", _D), ("rr_arith", _I32), ("refine_arith", _I32)]
+                ("n_small_inner", _I64), ("guess_tol", _D), ("rr_arith", _I32), ("refine_arith", _I32),
+                ("guess_correct", _I32), ("reserved2", _I32)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", _I32), ("refine_iterations", _I32), ("spmm_calls", _I32), ("restarts", _I32),
                 ("precond_dropped", _I32), ("reserved", _I32), ("time_ms", _D), ("phase_ms", _D * 8), ("spmm_bytes", _D), ("spmm_calls_mode", _I32 * 4),
-                ("spmm_ms_mode", _D * 4), ("spmm_bytes_mode", _D * 4), ("residual", _D * 64)]
+                ("spmm_ms_mode", _D * 4), ("spmm_bytes_mode", _D * 4), ("residual", _D * 64),
+                ("guess_relres", _D * 2)]
 
     PHASES = ("spmm", "gram", "rr", "update", "precond", "residual", "orth", "guess")
 
@@ -81,7 +83,8 @@ class Stats(ctypes.Structure):
                     spmm_by_mode={m: dict(calls=self.spmm_calls_mode[i], ms=self.spmm_ms_mode[i],
                                           bytes=self.spmm_bytes_mode[i])
                                   for i, m in enumerate(("fp64", "mixed", "df64"))},
-                    residual=[self.residual[j] for j in range(nb)])
+                    residual=[self.residual[j] for j in range(nb)],
+                    guess_relres=[self.guess_relres[0], self.guess_relres[1]])
 
 
 class LanczosStats(ctypes.Structure):
@@ -298,7 +301,8 @@ class Matrix:
 
     def solve(self, k, nb, tol, X0=None, mode="fp64", precond=False, n_small=0, max_iter=0, refine_iter=0,
               seed=1, precond_shift=0, mixed_tol=0.0, norm_H=0.0, X_out=None, precond_solve="fom", precond_steps=3,
-              stats=True, n_small_inner=0, guess_tol=0.0, rr_arith="fp64", refine_arith="fp64"):
+              stats=True, n_small_inner=0, guess_tol=0.0, rr_arith="fp64", refine_arith="fp64",
+              guess_correct=False):
         """k smallest eigenpairs (lob_solve). Returns (lam, X, stats, status). stats=False passes no
         stats struct: the solver then keeps no phase timers and replays its stages as CUDA graphs."""
         torch = _torch()
@@ -308,7 +312,7 @@ class Matrix:
         st = Stats()
         o = SolveOpts(_MODES[mode], int(bool(precond)), max_iter, refine_iter, norm_H, n_small, seed, precond_shift,
                       _PSOLVE[precond_solve], precond_steps, 0, mixed_tol, _stream(), n_small_inner, guess_tol,
-                      _ARITH[rr_arith], _ARITH[refine_arith])
+                      _ARITH[rr_arith], _ARITH[refine_arith], int(bool(guess_correct)), 0)
         rc = lib().lob_solve(self._h, k, nb, tol, x0.data_ptr() if x0 is not None else None, ctypes.byref(o),
                              lam.ctypes.data, X.data_ptr(), ctypes.byref(st) if stats else None)
         if rc not in (LOB_OK, LOB_ERR_NOCONV):

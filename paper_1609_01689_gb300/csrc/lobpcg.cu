@@ -68,6 +68,17 @@ __global__ void k_copy_cols(int64_t n, int ncol, const double* __restrict__ src,
   dst[r * ldd + i] = src[r * lds + (map ? map[i] : i)];
 }
 
+// eq. 13: X[r, :] -= W[r, :] for the rows r >= ns of the larger space only, where W = T^{-1} R is
+// the block-preconditioned residual of the zero-padded guess (its rows below ns stay as they are).
+__global__ void k_eq13_correct(int64_t n, int64_t ns, int nb, const double* __restrict__ W, double* __restrict__ X,
+                               int ldx) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (n - ns) * nb) return;
+  const int64_t r = ns + t / nb;
+  const int j = (int)(t % nb);
+  X[r * ldx + j] -= W[r * nb + j];
+}
+
 // R = HX - X diag(theta); per-CTA partial column sums of r^2 and x^2 into part[blk][2*nb].
 __global__ void __launch_bounds__(256) k_residual(int64_t n, int nb, const double* __restrict__ X, int ldx,
                                                   const double* __restrict__ HX, int ldh,
@@ -274,6 +285,7 @@ struct lob_task {
   int run_max = 0, max_iter = 0;
   int it = 0, restarts = 0, na = 0, m = 0, iters_total = 0, restarts_total = 0;
   bool haveP = false, retry = false, wretry = false;
+  bool eq13_done = false;  // the eq. 13 correction of the guess was applied
   // stagnation safeguard: the worst unconverged relative residual among the first k columns has
   // not halved for PC_STALL iterations -> the rest of the run goes without the preconditioner
   double best_res = 0.0;
@@ -600,6 +612,7 @@ int lob_task::step() {
             // multi-level: the leading-block solve takes its own eq. 12 guess from the inner block
             so.n_small = (o.n_small_inner > 0 && o.n_small_inner < ns) ? o.n_small_inner : 0;
             so.n_small_inner = 0;
+            so.guess_correct = 0;
             so.max_iter = 2000;
             so.refine_iter = 0;
             so.mixed_tol = 0.0;
@@ -678,6 +691,29 @@ int lob_task::step() {
         return sync_point();
       case PC_ITER_DECIDE: {
         clock.resolve();
+        if (iters_total == 0 && it == 1) {
+          // the first residuals of the solve: those of the initial guess (or of its eq. 13 correction)
+          double g = 0.0;
+          for (int j = 0; j < k; j++) g = fmax(g, hb->relres[j]);
+          stats.guess_relres[eq13_done ? 1 : 0] = g;
+          if (o.guess_correct && !eq13_done && !X0 && o.n_small > 0 && o.n_small < n_act) {
+            // eq. 13 (Section 3.3.1): the block preconditioner with shifts mu_j = theta_j, applied to
+            // the residual [~0; H_21 X_1] of the zero-padded guess, gives W ~ [0; (H_22 - theta I)^{-1}
+            // H_21 X_1]; the guess becomes [X_1; -W_2] and the run restarts from it
+            eq13_done = true;
+            {
+              Timer t(clk(), st, ph(PH_GUESS));
+              (k_shifts<<<1, 32, 0, st>>>(nb, 0, theta.p, relres_d.p, normH, mu.p), LOB_LAUNCHED());
+              LOB_TRY(lob_precond_launch(M, mu.p, R.p, W.p, nb, n_act, o.precond_solve,
+                                         o.precond_steps > 0 ? o.precond_steps : 3, st));
+              (k_eq13_correct<<<nblk((n_act - o.n_small) * nb), BS, 0, st>>>(n_act, o.n_small, nb, W.p, S.p, ldS),
+               LOB_LAUNCHED());
+              LOB_CUDA(cudaGetLastError());
+            }
+            pc = PC_RUN_SPMM0;
+            continue;
+          }
+        }
         bool conv = true;
         na = 0;
         for (int j = 0; j < nb; j++) {
@@ -900,6 +936,7 @@ int lob_solve_impl(lob_matrix* m, int32_t k, int32_t nb, double tol, const doubl
   if (o->mode == LOB_MODE_FP64 && !m->T.v64) return LOB_ERR_ARG;
   if (o->precond && m->P.bp < 1) return LOB_ERR_ARG;
   if (o->n_small_inner < 0 || !(o->guess_tol >= 0.0 && o->guess_tol < 1.0)) return LOB_ERR_ARG;
+  if (o->guess_correct < 0 || o->guess_correct > 1 || (o->guess_correct && m->P.bp < 1)) return LOB_ERR_ARG;
   if (o->precond_solve < LOB_PSOLVE_FOM || o->precond_solve > LOB_PSOLVE_ABS || o->precond_steps < 0 ||
       o->precond_steps > 3)
     return LOB_ERR_ARG;

@@ -48,6 +48,64 @@ def test_solve_fp64_c1(c1, precond, guess):
     check(H, L, lam, X, lam_ref, X_ref, 5, 1e-9, 1e-8)
 
 
+def _eq13_prediction(H, L, ns, nb, k, bp):
+    """Oracle side of the eq. 12 / eq. 13 guesses on the leading ns block: the largest relative
+    residual of the first k Ritz pairs of [X_1; 0] and of [X_1; -W_2], W = T^{-1} R by the FOM(3)
+    block preconditioner with shifts theta (Section 3.3.1)."""
+    A = oracle.dense(H)
+    th1, Z = oracle.syev(A[:ns, :ns])
+    X0 = np.zeros((L.n, nb)); X0[:ns] = Z[:, :nb]
+    nH = oracle.norm_inf(H)
+
+    def rr_relres(X):
+        HX = oracle.spmm(H, X)
+        th, C = oracle.rayleigh_ritz(X.T @ HX, X.T @ X)
+        Xr, HXr = X @ C, HX @ C
+        r = np.linalg.norm(HXr - Xr * th[None, :], axis=0) / (nH * np.linalg.norm(Xr, axis=0))
+        return r[:k].max(), th
+
+    g12, th = rr_relres(X0)
+    R = oracle.spmm(H, X0) - X0 * th1[None, :nb]
+    W = oracle.block_krylov(H, oracle.uniform_bounds(L.n, bp), th1[:nb], R, "fom", 3)
+    X13 = X0.copy(); X13[ns:] -= W[ns:]
+    g13, _ = rr_relres(X13)
+    return g12, g13
+
+
+def test_solve_eq13_guess_c1(c1):
+    """The eq. 13 corrected guess: the GPU's first residuals equal the oracle's for both guesses,
+    the corrected one is smaller, and the solve still reaches the oracle's eigenpairs."""
+    import paper_1609_01689_gb300 as lob
+    L, H, lam_ref, X_ref = c1
+    M = lob.Matrix(L.n, H.rows, H.cols, H.vals, precond_block=32)
+    ns = 24  # levels {0, 1}: the dense guess, exact eigenvectors of H_11
+    g12, g13 = _eq13_prediction(H, L, ns, 8, 5, 32)
+    lam0, X0, st0, rc0 = M.solve(5, 8, 1e-8, mode="fp64", precond=True, n_small=ns)
+    lam1, X1, st1, rc1 = M.solve(5, 8, 1e-8, mode="fp64", precond=True, n_small=ns, guess_correct=True)
+    assert rc0 == lob.LOB_OK and rc1 == lob.LOB_OK
+    check(H, L, lam1, X1, lam_ref, X_ref, 5, 1e-9, 1e-8)
+    assert st0["guess_relres"][1] == 0.0
+    # the solver's residual norms are summed in FP32 (about 1e-6 of themselves)
+    assert st0["guess_relres"][0] == pytest.approx(g12, rel=1e-5)
+    assert st1["guess_relres"][0] == pytest.approx(g12, rel=1e-5)
+    # FP32 block eigenbases in the GPU preconditioner: agreement to about 1e-5 relative
+    assert st1["guess_relres"][1] == pytest.approx(g13, rel=1e-3)
+    assert g13 < 0.5 * g12
+    # the mixed solver takes the same option
+    lam2, X2, st2, rc2 = M.solve(5, 8, 1e-8, mode="mixed", precond=True, n_small=ns, guess_correct=True)
+    assert rc2 == lob.LOB_OK
+    check(H, L, lam2, X2, lam_ref, X_ref, 5, 1e-8, 1e-8)
+    assert st2["guess_relres"][1] == pytest.approx(g13, rel=1e-2)
+
+
+def test_solve_eq13_needs_preconditioner(c1):
+    import paper_1609_01689_gb300 as lob
+    L, H, lam_ref, X_ref = c1
+    M = lob.Matrix(L.n, H.rows, H.cols, H.vals)  # no preconditioner blocks
+    with pytest.raises(lob.LobError):
+        M.solve(5, 8, 1e-8, mode="fp64", n_small=24, guess_correct=True)
+
+
 def test_solve_mixed_c1(c1):
     import paper_1609_01689_gb300 as lob
     L, H, lam_ref, X_ref = c1
