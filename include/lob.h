@@ -402,6 +402,72 @@ int lob_server_stats_get(const lob_server* s, lob_server_stats* out);
  * requests are dropped. */
 int lob_server_destroy(lob_server* s);
 
+/* ---- batched small instances: one persistent schedule for many independent solves ----
+ *
+ * Many independent small matrices (each n <= 65,535), each solved for its k smallest
+ * eigenpairs by the same LOBPCG iteration as lob_solve (Algorithm 1, without preconditioner),
+ * all in ONE persistent kernel launch replayed from a CUDA graph: a CTA takes the next
+ * instance from an atomic ticket (largest instances first) and runs that instance's whole solve
+ * -- SpMM, Gram matrices, linear combinations, Cholesky-QR and the Rayleigh-Ritz solve of eq. 9
+ * in FP64 -- then takes the next. The matrices are stored with both triangles in SELL slices
+ * (16-bit instance-local column indices, FP32 and FP64 values). Instance results do not depend
+ * on which CTA runs them or on the other instances; they do depend on the schedule's thread
+ * count (the order of the Gram sums). */
+typedef struct lob_batch lob_batch; /* opaque; owns the device store of all instances */
+
+/* Build the store of `count` instances from the upper triangles H[0..count-1] (each as
+ * lob_create's input: row <= col, in [0, n), no repeats; host or device per H[i].on_device).
+ * 1 <= H[i].n <= 65,535. stream: cudaStream_t of the build. Synchronous. Errors: LOB_ERR_ARG
+ * (count < 1, a bad size or entry), LOB_ERR_NOMEM, LOB_ERR_CUDA. */
+int lob_batch_create(int32_t count, const lob_coo* H, void* stream, lob_batch** out);
+int lob_batch_destroy(lob_batch* b);
+
+typedef struct {
+  int32_t k, nb;         /* 1 <= k <= nb <= 8 */
+  int32_t mode;          /* LOB_MODE_FP64: FP64 values, products and sums throughout.
+                            LOB_MODE_MIXED: an FP32 phase (FP32 values and X in the SpMM, FP32
+                            products with double-float sums in the Gram matrices, FP32 linear
+                            combinations) until the first k relative residuals reach mixed_tol or
+                            stall for 12 iterations, then an FP64-class phase from those vectors to
+                            tol: double-float values (the FP32 value and its FP32-rounded
+                            remainder), products and sums, ~48 significant bits on the FP32 pipes.
+                            The Cholesky factors and Rayleigh-Ritz solves are FP64 in both. */
+  int32_t max_iter;      /* per instance, both phases together; 0 = 500 */
+  double tol;            /* stop when every one of the first k columns has
+                            ||H x_j - theta_j x_j|| <= tol ||H||_inf ||x_j|| */
+  double mixed_tol;      /* target of the FP32 phase; 0 = max(tol, 1e-6) */
+  uint64_t seed;         /* the random starting blocks (a counter-based hash of seed, instance,
+                            row and column) */
+  int32_t tile;          /* SELL slice height 8, 16 or 32; 0 = autotuned */
+  int32_t threads;       /* threads per CTA, 64..512, a multiple of 32; 0 = autotuned */
+  int32_t per_sm;        /* CTAs launched per SM (at most what fits); 0 = autotuned */
+  int32_t tune_iter;     /* iterations each candidate schedule runs while the autotuner times it
+                            (all instances, mode as requested); 0 = 4 */
+  void* stream;
+} lob_batch_opts;
+
+typedef struct {
+  int32_t tile, threads, per_sm;  /* the schedule that ran */
+  int32_t candidates;      /* schedules the autotuner timed in this call (0: none; the batch keeps
+                              the first tuned choice for later calls with the same k, nb, mode) */
+  double tune_ms;          /* wall time of that tuning */
+  double kernel_ms;        /* device time of the schedule (CUDA events around the graph launch) */
+  double wall_ms;          /* wall time of the whole call */
+  int64_t rows;            /* sum of the instances' n */
+  int64_t entries;         /* SELL entries of the slice height used (both triangles, padding) */
+  int64_t work_bytes;      /* device workspace of the schedule */
+} lob_batch_stats;
+
+/* Solve every instance. Outputs (device, caller-owned): lambda[count][k] ascending per
+ * instance; status[count] (LOB_OK, LOB_ERR_NOCONV: the iteration budget ran out, outputs hold
+ * the last iterate; LOB_ERR_BREAKDOWN); iters[count][2] (iterations, of which in the phase that
+ * ends at tol: FP64-class in MIXED, all in FP64) or
+ * NULL; X (rows x nb, row-major, instance i's rows starting at the sum of the earlier n; unit
+ * 2-norm columns, the first k the eigenvectors) or NULL. Returns when the schedule is done.
+ * st may be NULL. Errors: LOB_ERR_ARG, LOB_ERR_NOMEM, LOB_ERR_CUDA. */
+int lob_batch_solve(lob_batch* b, const lob_batch_opts* o, double* lambda, int32_t* status, int32_t* iters,
+                    double* X, lob_batch_stats* st);
+
 const char* lob_strerror(int code);
 
 /* Size in bytes of the ABI struct with the given type name ("lob_solve_opts", "lob_stats",

@@ -11,6 +11,7 @@ Main objects:
   gram, lincomb, rayleigh_ritz, Matrix.precond_apply   the pieces of one iteration
   spmm_batch(mats, Xs, modes)                   products of several matrices in shared launches
   Server(budget_bytes, max_active)              continuous batching of solves (lob_server_*)
+  Batch(problems).solve(k, nb, tol, ...)        many small solves in one persistent schedule (lob_batch_*)
 """
 from __future__ import annotations
 
@@ -118,6 +119,17 @@ class ServerStats(ctypes.Structure):
                 ("wait_ms", _D)]
 
 
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("k", _I32), ("nb", _I32), ("mode", _I32), ("max_iter", _I32), ("tol", _D), ("mixed_tol", _D),
+                ("seed", ctypes.c_uint64), ("tile", _I32), ("threads", _I32), ("per_sm", _I32),
+                ("tune_iter", _I32), ("stream", _P)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("tile", _I32), ("threads", _I32), ("per_sm", _I32), ("candidates", _I32), ("tune_ms", _D),
+                ("kernel_ms", _D), ("wall_ms", _D), ("rows", _I64), ("entries", _I64), ("work_bytes", _I64)]
+
+
 class LobError(RuntimeError):
     def __init__(self, code, what=""):
         self.code = code
@@ -151,6 +163,9 @@ def _load():
     L.lob_server_poll.argtypes = [_P, _I64, ctypes.POINTER(Result)]
     L.lob_server_stats_get.argtypes = [_P, ctypes.POINTER(ServerStats)]
     L.lob_server_destroy.argtypes = [_P]
+    L.lob_batch_create.argtypes = [_I32, _P, _P, ctypes.POINTER(_P)]
+    L.lob_batch_destroy.argtypes = [_P]
+    L.lob_batch_solve.argtypes = [_P, ctypes.POINTER(BatchOpts), _P, _P, _P, _P, ctypes.POINTER(BatchStats)]
     L.lob_kernel_launches.argtypes = []
     L.lob_kernel_launches.restype = ctypes.c_longlong
     L.lob_strerror.argtypes = [ctypes.c_int]
@@ -159,7 +174,8 @@ def _load():
               "lob_check", "lob_gram",
               "lob_lincomb", "lob_precond_apply", "lob_rayleigh_ritz", "lob_solve", "lob_spmm_batch", "lob_lanczos",
               "lob_server_create", "lob_server_submit", "lob_server_progress", "lob_server_poll",
-              "lob_server_stats_get", "lob_server_destroy"):
+              "lob_server_stats_get", "lob_server_destroy", "lob_batch_create", "lob_batch_destroy",
+              "lob_batch_solve"):
         getattr(L, f).restype = ctypes.c_int
     return L
 
@@ -471,3 +487,61 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Many independent small matrices (n <= 65,535 each) solved together by one persistent
+    kernel schedule replayed from a CUDA graph (lob_batch_*). problems: a list of (n, rows,
+    cols, vals) upper triangles, numpy (host) or torch CUDA tensors (device)."""
+
+    def __init__(self, problems):
+        torch = _torch()
+        keep = []
+        coos = (Coo * len(problems))()
+        for i, (n, rows, cols, vals) in enumerate(problems):
+            if isinstance(rows, np.ndarray):
+                r = np.ascontiguousarray(rows, dtype=np.int64)
+                c = np.ascontiguousarray(cols, dtype=np.int64)
+                v = np.ascontiguousarray(vals, dtype=np.float64)
+                coos[i] = Coo(int(n), len(r), r.ctypes.data, c.ctypes.data, v.ctypes.data, 0)
+            else:
+                r = rows.to(device="cuda", dtype=torch.int64).contiguous()
+                c = cols.to(device="cuda", dtype=torch.int64).contiguous()
+                v = vals.to(device="cuda", dtype=torch.float64).contiguous()
+                coos[i] = Coo(int(n), r.numel(), r.data_ptr(), c.data_ptr(), v.data_ptr(), 1)
+            keep += [r, c, v]
+        h = _P()
+        _check(lib().lob_batch_create(len(problems), coos, _stream(), ctypes.byref(h)), "lob_batch_create")
+        self._h = h
+        self.sizes = [int(p[0]) for p in problems]
+        self.count = len(problems)
+        self.rows = int(sum(self.sizes))
+        self.row0 = np.concatenate([[0], np.cumsum(self.sizes)[:-1]]).astype(np.int64)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lob_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, k, nb, tol, mode="mixed", max_iter=0, mixed_tol=0.0, seed=1, tile=0, threads=0, per_sm=0,
+              tune_iter=0, vectors=False):
+        """Solve every instance (lob_batch_solve). Returns (lam [count, k], status [count],
+        iters [count, 2], X [rows, nb] or None, stats dict), all numpy except X (torch, device)."""
+        torch = _torch()
+        lam = torch.empty((self.count, k), dtype=torch.float64, device="cuda")
+        status = torch.empty(self.count, dtype=torch.int32, device="cuda")
+        iters = torch.empty((self.count, 2), dtype=torch.int32, device="cuda")
+        X = torch.empty((self.rows, nb), dtype=torch.float64, device="cuda") if vectors else None
+        o = BatchOpts(k, nb, _MODES[mode], max_iter, tol, mixed_tol, seed, tile, threads, per_sm, tune_iter,
+                      _stream())
+        st = BatchStats()
+        _check(lib().lob_batch_solve(self._h, ctypes.byref(o), lam.data_ptr(), status.data_ptr(), iters.data_ptr(),
+                                     X.data_ptr() if X is not None else None, ctypes.byref(st)), "lob_batch_solve")
+        return (lam.cpu().numpy(), status.cpu().numpy(), iters.cpu().numpy(), X,
+                {f: getattr(st, f) for f, _ in BatchStats._fields_})

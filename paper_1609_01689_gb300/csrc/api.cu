@@ -23,6 +23,8 @@ int64_t lob_struct_size(const char* name) {
       {"lob_request", sizeof(lob_request)},
       {"lob_result", sizeof(lob_result)},
       {"lob_server_stats", sizeof(lob_server_stats)},
+      {"lob_batch_opts", sizeof(lob_batch_opts)},
+      {"lob_batch_stats", sizeof(lob_batch_stats)},
   };
   for (const E& e : table)
     if (strcmp(e.n, name) == 0) return e.s;

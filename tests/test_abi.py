@@ -59,6 +59,9 @@ def test_library_loads_and_reports_errors(built_lib):
     assert lib.lob_server_progress(None, 0, None) == lob.LOB_ERR_ARG
     assert lib.lob_server_poll(None, 1, None) == lob.LOB_ERR_ARG
     assert lib.lob_server_destroy(None) == lob.LOB_ERR_ARG
+    assert lib.lob_batch_create(0, None, None, None) == lob.LOB_ERR_ARG
+    assert lib.lob_batch_solve(None, None, None, None, None, None, None) == lob.LOB_ERR_ARG
+    assert lib.lob_batch_destroy(None) == lob.LOB_OK
 
 
 def test_synth_device_library_builds():
@@ -77,7 +80,8 @@ def test_binding_struct_layouts_match_the_header(built_lib):
     pairs = {"lob_coo": lob.Coo, "lob_create_opts": lob.CreateOpts, "lob_matrix_info": lob.MatrixInfo,
              "lob_solve_opts": lob.SolveOpts, "lob_stats": lob.Stats, "lob_lanczos_stats": lob.LanczosStats,
              "lob_server_opts": lob.ServerOpts, "lob_request": lob.Request, "lob_result": lob.Result,
-             "lob_server_stats": lob.ServerStats}
+             "lob_server_stats": lob.ServerStats, "lob_batch_opts": lob.BatchOpts,
+             "lob_batch_stats": lob.BatchStats}
     for name, cls in pairs.items():
         assert lib.lob_struct_size(name.encode()) == ctypes.sizeof(cls), name
     assert lib.lob_struct_size(b"no_such_struct") == 0
