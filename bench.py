@@ -562,6 +562,42 @@ def run_batched_small(args, lob, synth, torch):
     return out
 
 
+def run_vblock(lob, torch, layout, n, rows, cols, vals, nb, reps=10):
+    """The variable-size block store (levels cut into blocks of at most 256 rows, 8 + 8-bit
+    offsets, 6 B per stored entry) and its FP32-value SpMM on the bench's matrix: median of
+    `reps` launches (CUDA events, inputs larger than L2) after two warm-ups."""
+    import synth
+    groups = synth.level_starts(layout)[:-1]
+    t0 = time.perf_counter()
+    V = lob.VMatrix(n, rows, cols, vals, groups, 256)
+    torch.cuda.synchronize()
+    build_ms = (time.perf_counter() - t0) * 1e3
+    inf = V.info()
+    X = torch.randn((n, nb), dtype=torch.float64, device="cuda")
+    Y = torch.empty_like(X)
+    for _ in range(2):
+        V.spmm(X, out=Y)
+    times = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        V.spmm(X, out=Y)
+        e1.record()
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = sorted(times)[len(times) // 2]
+    # algorithmic bytes: 6 B per stored entry, block tables, X read as FP32 and Y written in FP64
+    alg = inf["nnz"] * 6 + inf["ntiles"] * 12 + (inf["nblocks"] + 1) * 16 + n * nb * (4 + 8)
+    V.close()
+    del X, Y
+    torch.cuda.empty_cache()
+    return {"store": "variable-size blocks (levels cut at 256 rows), (r << 8) | c + FP32 value",
+            "nblocks": int(inf["nblocks"]), "blocks_stored": int(inf["ntiles"]), "store_bytes": int(inf["store_bytes"]),
+            "bytes_per_entry": inf["store_bytes"] / inf["nnz"], "build_ms": build_ms, "ms": ms,
+            "algorithmic_bytes": alg, "gbs": alg / (ms * 1e-3) / 1e9, "kernel": "k_vspmm (one CTA per block row)"}
+
+
 def run_kernels(args, lob, M, info, torch, make_matrix):
     """Each hot-path kernel alone at the workload's sizes (CUDA events, L2 flushed between
     repetitions): the symmetric SpMM in its three arithmetics, the 48 x 48 double-float Gram,
@@ -692,6 +728,7 @@ def main():
     ap.add_argument("--serve-compare", type=int, default=100)
     ap.add_argument("--serve-slots", type=int, default=256)
     ap.add_argument("--no-small", action="store_true")
+    ap.add_argument("--no-vblock", action="store_true", help="skip the variable-size block store's SpMM")
     ap.add_argument("--small-count", type=int, default=4096)
     ap.add_argument("--small-sample", type=int, default=64)
     ap.add_argument("--small-reps", type=int, default=3)
@@ -737,6 +774,9 @@ def main():
     # use one pinned host copy of the COO; the device copy is then released
     if not args.no_e2e or (rank == 0 and not (args.no_cpu and args.no_csb)):
         host_coo(wl["cfg"], layout, dev=(rows, cols, vals))
+    vblock = None
+    if rank == 0 and not args.no_vblock:
+        vblock = run_vblock(lob, torch, layout, n, rows, cols, vals, wl["nb"])
     del rows, cols, vals
     torch.cuda.empty_cache()
     n_small = int(synth.level_starts(layout)[2])
@@ -875,6 +915,11 @@ def main():
                       "d2h_bytes_per_step": int(n * nb * 8 + k * 8),
                       "includes": "H2D of the COO, tile build + preconditioner setup, solve, D2H of X and lambda"}
 
+    if vblock is not None:
+        peak_v, _ = read_peaks()
+        vblock["frac_of_hbm"] = vblock["gbs"] / peak_v
+        vblock["fixed_tile_kernel_ms"] = spmm_ms / max(spmm_calls, 1)
+        out["vblock_spmm"] = vblock
     if rank == 0 and not args.no_serve:
         out["serving"] = run_serving(args, lob, synth, torch)
     if rank == 0 and not args.no_small:

@@ -402,6 +402,42 @@ int lob_server_stats_get(const lob_server* s, lob_server_stats* out);
  * requests are dropped. */
 int lob_server_destroy(lob_server* s);
 
+/* ---- variable-size CSB blocks with 8 + 8-bit offsets ----
+ *
+ * A second, compact store of H (Section 2.2: blocks of at most beta rows aligned to the groups
+ * of the basis; Section 4.2: two in-block offsets per stored entry). Each group [g_i, g_{i+1})
+ * is cut into blocks of at most beta_max <= 256 rows starting at g_i, so no block straddles a
+ * group boundary and an entry is one uint16 (r << 8) | c plus its FP32 value: 6 bytes, against
+ * 8 for the fixed-tile store's (r << 16) | c and value. Nonzero blocks are kept in (block row,
+ * block column) order, entries inside a block in (r, c) order. */
+typedef struct lob_vmatrix lob_vmatrix; /* opaque; owns the device block store */
+
+typedef struct {
+  int64_t n, nnz, nblocks, ntiles;   /* ntiles: nonzero blocks of the upper triangle */
+  int32_t beta_max, reserved;
+  int64_t store_bytes;               /* rc16 and values (6 B per entry) + block tables */
+  int64_t kernel_bytes;              /* the SpMM's private permutation and chunk pointers */
+} lob_vmatrix_info;
+
+/* Build the block store on the current device. group_starts: host, ngroups ascending row
+ * indices, the first 0, all < n. H as for lob_create. Synchronous. Errors: LOB_ERR_ARG (bad
+ * groups, beta_max outside [1, 256], a bad entry or duplicate), LOB_ERR_NOMEM, LOB_ERR_CUDA. */
+int lob_vcreate(const lob_coo* H, const int64_t* group_starts, int32_t ngroups, int32_t beta_max, void* stream,
+                lob_vmatrix** out);
+int lob_vdestroy(lob_vmatrix* v);
+int lob_vinfo(const lob_vmatrix* v, lob_vmatrix_info* out);
+/* Copy the store to host arrays (caller-allocated; sizes from lob_vinfo; any may be NULL):
+ * bounds[nblocks + 1] block starts, tile_rowptr[nblocks + 1] first nonzero block of each block
+ * row, tile_col[ntiles] block column, tile_ptr[ntiles + 1] first entry of each block,
+ * rc16[nnz] (r << 8) | c, v32[nnz] values rounded to FP32. */
+int lob_vexport(const lob_vmatrix* v, int64_t* bounds, int64_t* tile_rowptr, int32_t* tile_col, int64_t* tile_ptr,
+                uint16_t* rc16, float* v32);
+/* Y = H X from the block store (Section 4.1: each stored block applied as H_IJ and H_IJ^T in one
+ * pass) in the arithmetic of LOB_SPMM_MIXED: FP32 values, X rounded to FP32, FP32 products and
+ * in-block sums, block partials summed in FP64. X, Y: device n x nb row-major FP64, 1 <= nb <= 16,
+ * not overlapping. Asynchronous on stream. Errors: LOB_ERR_ARG, LOB_ERR_CUDA. */
+int lob_vspmm(lob_vmatrix* v, const double* X, double* Y, int32_t nb, void* stream);
+
 /* ---- batched small instances: one persistent schedule for many independent solves ----
  *
  * Many independent small matrices (each n <= 65,535), each solved for its k smallest

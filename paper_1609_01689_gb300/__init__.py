@@ -12,6 +12,7 @@ Main objects:
   spmm_batch(mats, Xs, modes)                   products of several matrices in shared launches
   Server(budget_bytes, max_active)              continuous batching of solves (lob_server_*)
   Batch(problems).solve(k, nb, tol, ...)        many small solves in one persistent schedule (lob_batch_*)
+  VMatrix(n, rows, cols, vals, groups, beta)    variable-size blocks with 8 + 8-bit offsets (lob_v*)
 """
 from __future__ import annotations
 
@@ -130,6 +131,11 @@ class BatchStats(ctypes.Structure):
                 ("kernel_ms", _D), ("wall_ms", _D), ("rows", _I64), ("entries", _I64), ("work_bytes", _I64)]
 
 
+class VMatrixInfo(ctypes.Structure):
+    _fields_ = [("n", _I64), ("nnz", _I64), ("nblocks", _I64), ("ntiles", _I64), ("beta_max", _I32),
+                ("reserved", _I32), ("store_bytes", _I64), ("kernel_bytes", _I64)]
+
+
 class LobError(RuntimeError):
     def __init__(self, code, what=""):
         self.code = code
@@ -166,6 +172,11 @@ def _load():
     L.lob_batch_create.argtypes = [_I32, _P, _P, ctypes.POINTER(_P)]
     L.lob_batch_destroy.argtypes = [_P]
     L.lob_batch_solve.argtypes = [_P, ctypes.POINTER(BatchOpts), _P, _P, _P, _P, ctypes.POINTER(BatchStats)]
+    L.lob_vcreate.argtypes = [ctypes.POINTER(Coo), _P, _I32, _I32, _P, ctypes.POINTER(_P)]
+    L.lob_vdestroy.argtypes = [_P]
+    L.lob_vinfo.argtypes = [_P, ctypes.POINTER(VMatrixInfo)]
+    L.lob_vexport.argtypes = [_P, _P, _P, _P, _P, _P, _P]
+    L.lob_vspmm.argtypes = [_P, _P, _P, _I32, _P]
     L.lob_kernel_launches.argtypes = []
     L.lob_kernel_launches.restype = ctypes.c_longlong
     L.lob_strerror.argtypes = [ctypes.c_int]
@@ -175,7 +186,7 @@ def _load():
               "lob_lincomb", "lob_precond_apply", "lob_rayleigh_ritz", "lob_solve", "lob_spmm_batch", "lob_lanczos",
               "lob_server_create", "lob_server_submit", "lob_server_progress", "lob_server_poll",
               "lob_server_stats_get", "lob_server_destroy", "lob_batch_create", "lob_batch_destroy",
-              "lob_batch_solve"):
+              "lob_batch_solve", "lob_vcreate", "lob_vdestroy", "lob_vinfo", "lob_vexport", "lob_vspmm"):
         getattr(L, f).restype = ctypes.c_int
     return L
 
@@ -545,3 +556,63 @@ class Batch:
                                      X.data_ptr() if X is not None else None, ctypes.byref(st)), "lob_batch_solve")
         return (lam.cpu().numpy(), status.cpu().numpy(), iters.cpu().numpy(), X,
                 {f: getattr(st, f) for f, _ in BatchStats._fields_})
+
+
+class VMatrix:
+    """Compact block store of the upper triangle: each group [g_i, g_i+1) cut into blocks of at
+    most beta_max rows, entries as (r << 8) | c and an FP32 value (lob_vcreate)."""
+
+    def __init__(self, n, rows, cols, vals, group_starts, beta_max=256):
+        torch = _torch()
+        if isinstance(rows, np.ndarray):
+            r = np.ascontiguousarray(rows, dtype=np.int64)
+            c = np.ascontiguousarray(cols, dtype=np.int64)
+            v = np.ascontiguousarray(vals, dtype=np.float64)
+            coo = Coo(n, len(r), r.ctypes.data, c.ctypes.data, v.ctypes.data, 0)
+        else:
+            r = rows.to(device="cuda", dtype=torch.int64).contiguous()
+            c = cols.to(device="cuda", dtype=torch.int64).contiguous()
+            v = vals.to(device="cuda", dtype=torch.float64).contiguous()
+            coo = Coo(n, r.numel(), r.data_ptr(), c.data_ptr(), v.data_ptr(), 1)
+        g = np.ascontiguousarray(group_starts, dtype=np.int64)
+        h = _P()
+        _check(lib().lob_vcreate(ctypes.byref(coo), g.ctypes.data, len(g), beta_max, _stream(), ctypes.byref(h)),
+               "lob_vcreate")
+        self._h = h
+        self.n = int(n)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().lob_vdestroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        inf = VMatrixInfo()
+        _check(lib().lob_vinfo(self._h, ctypes.byref(inf)), "lob_vinfo")
+        return {f: getattr(inf, f) for f, _ in VMatrixInfo._fields_}
+
+    def export(self):
+        inf = self.info()
+        nblk, ntl, nnz = inf["nblocks"], inf["ntiles"], inf["nnz"]
+        bnd = np.empty(nblk + 1, np.int64)
+        rp = np.empty(nblk + 1, np.int64)
+        tc = np.empty(ntl, np.int32)
+        tp = np.empty(ntl + 1, np.int64)
+        rc = np.empty(nnz, np.uint16)
+        v32 = np.empty(nnz, np.float32)
+        _check(lib().lob_vexport(self._h, bnd.ctypes.data, rp.ctypes.data, tc.ctypes.data, tp.ctypes.data,
+                                 rc.ctypes.data, v32.ctypes.data), "lob_vexport")
+        return dict(bounds=bnd, tile_rowptr=rp, tile_col=tc, tile_ptr=tp, rc16=rc, v32=v32)
+
+    def spmm(self, X, out=None):
+        X = _dev_f64(X)
+        nb = 1 if X.dim() == 1 else X.shape[1]
+        Y = out if out is not None else _torch().empty_like(X)
+        _check(lib().lob_vspmm(self._h, X.data_ptr(), Y.data_ptr(), nb, _stream()), "lob_vspmm")
+        return Y

@@ -25,6 +25,7 @@ int64_t lob_struct_size(const char* name) {
       {"lob_server_stats", sizeof(lob_server_stats)},
       {"lob_batch_opts", sizeof(lob_batch_opts)},
       {"lob_batch_stats", sizeof(lob_batch_stats)},
+      {"lob_vmatrix_info", sizeof(lob_vmatrix_info)},
   };
   for (const E& e : table)
     if (strcmp(e.n, name) == 0) return e.s;
@@ -83,7 +84,7 @@ int lob_create(const lob_coo* H, const lob_create_opts* opts, lob_matrix** out) 
     cudaGetLastError();
     rc = LOB_ERR_NOMEM;
   }
-  if (rc == LOB_OK) rc = lob_build_tiles(&D, values, st, &m->T, &m->norm_inf);
+  if (rc == LOB_OK) rc = lob_build_tiles(&D, values, st, &m->T, &m->norm_inf, nullptr, 0);
   if (rc == LOB_OK) {
     m->h_rowptr.resize(m->T.nt + 1);
     if (cudaMemcpy(m->h_rowptr.data(), m->T.rowptr, (m->T.nt + 1) * 8, cudaMemcpyDeviceToHost) != cudaSuccess)

@@ -138,7 +138,11 @@ struct lob_bjob {
 };
 
 // ---- internal launchers (return LOB_OK or an error code) ----
-int lob_build_tiles(const lob_coo* H, int values, cudaStream_t st, lob_tiles* T, double* norm_inf);
+// bnd (device, nblk + 1 entries) or null: variable square blocks [bnd[b], bnd[b + 1]) of at most
+// LOB_TILE rows in place of the fixed LOB_TILE tiles; "tile row/column" then means block, and the
+// in-tile offsets are relative to the block starts.
+int lob_build_tiles(const lob_coo* H, int values, cudaStream_t st, lob_tiles* T, double* norm_inf,
+                    const int64_t* bnd, int64_t nblk);
 void lob_free_tiles(lob_tiles* T);
 int lob_build_precond(const lob_coo* Hdev, int bp, int64_t n, cudaStream_t st, lob_precond* P);
 void lob_free_precond(lob_precond* P);

@@ -28,8 +28,22 @@ int dalloc(DevBuf& b, size_t count) {
   return LOB_OK;
 }
 
+// block of index i under the boundaries bnd[0..nb] (bnd[0] = 0, ascending, gaps <= LOB_TILE):
+// the last b with bnd[b] <= i
+__device__ __forceinline__ int64_t block_of(const int64_t* __restrict__ bnd, int64_t nb, int64_t i) {
+  int64_t lo = 0, hi = nb - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (bnd[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Sort key of entry t: (tile row, tile col, r, c). Fixed tiles: tile = i / 256, r = i % 256.
+// Variable blocks (bnd != null, nb blocks): tile = the block holding i, r = i - its start.
 __global__ void k_keys(int64_t nnz, int64_t n, const int64_t* __restrict__ row, const int64_t* __restrict__ col,
-                       int bits_t, uint64_t* __restrict__ keys, uint32_t* __restrict__ idx, int* __restrict__ err) {
+                       int bits_t, const int64_t* __restrict__ bnd, int64_t nb, uint64_t* __restrict__ keys,
+                       uint32_t* __restrict__ idx, int* __restrict__ err) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nnz) return;
   int64_t i = row[t], j = col[t];
@@ -37,8 +51,15 @@ __global__ void k_keys(int64_t nnz, int64_t n, const int64_t* __restrict__ row, 
     atomicOr(err, 1);
     i = 0; j = 0;
   }
-  uint64_t tr = (uint64_t)(i >> LOB_TILE_LOG), tc = (uint64_t)(j >> LOB_TILE_LOG);
-  uint64_t r = (uint64_t)(i & (LOB_TILE - 1)), c = (uint64_t)(j & (LOB_TILE - 1));
+  uint64_t tr, tc, r, c;
+  if (bnd) {
+    const int64_t bi = block_of(bnd, nb, i), bj = block_of(bnd, nb, j);
+    tr = (uint64_t)bi; tc = (uint64_t)bj;
+    r = (uint64_t)(i - bnd[bi]); c = (uint64_t)(j - bnd[bj]);
+  } else {
+    tr = (uint64_t)(i >> LOB_TILE_LOG); tc = (uint64_t)(j >> LOB_TILE_LOG);
+    r = (uint64_t)(i & (LOB_TILE - 1)); c = (uint64_t)(j & (LOB_TILE - 1));
+  }
   keys[t] = (tr << (bits_t + 2 * LOB_TILE_LOG)) | (tc << (2 * LOB_TILE_LOG)) | (r << LOB_TILE_LOG) | c;
   idx[t] = (uint32_t)t;
 }
@@ -185,10 +206,11 @@ void lob_free_tiles(lob_tiles* T) {
   *T = lob_tiles();
 }
 
-int lob_build_tiles(const lob_coo* H, int values, cudaStream_t st, lob_tiles* T, double* norm_inf) {
+int lob_build_tiles(const lob_coo* H, int values, cudaStream_t st, lob_tiles* T, double* norm_inf,
+                    const int64_t* bnd, int64_t nblk) {
   const int64_t n = H->n, nnz = H->nnz;
   if (nnz >= (int64_t)0xFFFFFFFFll) return LOB_ERR_ARG;
-  const int64_t nt = (n + LOB_TILE - 1) / LOB_TILE;
+  const int64_t nt = bnd ? nblk : (n + LOB_TILE - 1) / LOB_TILE;
   int bits_t = 1;
   while ((1ll << bits_t) < nt) bits_t++;
   if (2 * bits_t + 2 * LOB_TILE_LOG > 64) return LOB_ERR_ARG;
@@ -211,7 +233,9 @@ int lob_build_tiles(const lob_coo* H, int values, cudaStream_t st, lob_tiles* T,
   LOB_TRY(dalloc<uint32_t>(idx0, nnz)); LOB_TRY(dalloc<uint32_t>(idx1, nnz));
   LOB_TRY(dalloc<int>(err, 1));
   LOB_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
-  (k_keys<<<nblocks(nnz, bs), bs, 0, st>>>(nnz, n, row, col, bits_t, (uint64_t*)keys0.p, (uint32_t*)idx0.p, (int*)err.p), LOB_LAUNCHED());
+  (k_keys<<<nblocks(nnz, bs), bs, 0, st>>>(nnz, n, row, col, bits_t, bnd, nblk, (uint64_t*)keys0.p, (uint32_t*)idx0.p,
+                                           (int*)err.p),
+   LOB_LAUNCHED());
   LOB_CUDA(cudaGetLastError());
 
   cub::DoubleBuffer<uint64_t> dk((uint64_t*)keys0.p, (uint64_t*)keys1.p);

@@ -62,6 +62,9 @@ def test_library_loads_and_reports_errors(built_lib):
     assert lib.lob_batch_create(0, None, None, None) == lob.LOB_ERR_ARG
     assert lib.lob_batch_solve(None, None, None, None, None, None, None) == lob.LOB_ERR_ARG
     assert lib.lob_batch_destroy(None) == lob.LOB_OK
+    assert lib.lob_vcreate(None, None, 0, 0, None, None) == lob.LOB_ERR_ARG
+    assert lib.lob_vspmm(None, None, None, 1, None) == lob.LOB_ERR_ARG
+    assert lib.lob_vdestroy(None) == lob.LOB_OK
 
 
 def test_synth_device_library_builds():
@@ -81,7 +84,7 @@ def test_binding_struct_layouts_match_the_header(built_lib):
              "lob_solve_opts": lob.SolveOpts, "lob_stats": lob.Stats, "lob_lanczos_stats": lob.LanczosStats,
              "lob_server_opts": lob.ServerOpts, "lob_request": lob.Request, "lob_result": lob.Result,
              "lob_server_stats": lob.ServerStats, "lob_batch_opts": lob.BatchOpts,
-             "lob_batch_stats": lob.BatchStats}
+             "lob_batch_stats": lob.BatchStats, "lob_vmatrix_info": lob.VMatrixInfo}
     for name, cls in pairs.items():
         assert lib.lob_struct_size(name.encode()) == ctypes.sizeof(cls), name
     assert lib.lob_struct_size(b"no_such_struct") == 0
