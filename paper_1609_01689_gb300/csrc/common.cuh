@@ -64,6 +64,12 @@ struct lob_tiles {
                                // the SpMM reads an entry's position and value in one 8-byte load
   uint16_t* cperm = nullptr;   // [nnz] kernel-private: per chunk of LOB_PERM_CHUNK entries of a tile,
                                // the chunk-local indices of its entries in (c, r) order
+  uint2* rvp = nullptr;        // [nnz] kernel-private: rv with every row segment of a chunk reordered
+                               // so that entries whose column has the row's parity come first
+  uint16_t* cpermp = nullptr;  // [nnz] kernel-private: per chunk, the rvp positions of its entries by
+                               // column, each column's entries with the column's row parity first
+                               // (two lane groups sharing a quarter-warp then gather X rows from
+                               // different halves of the banks in most steps)
   int64_t nchunks = 0;
   int32_t* tchunk = nullptr;   // [ntiles+1] first chunk id of each tile
   uint16_t* cptrs = nullptr;   // [nchunks][2][257] kernel-private: start of each in-tile row in the

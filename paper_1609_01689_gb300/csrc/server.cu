@@ -30,6 +30,7 @@ size_t matrix_bytes(const lob_matrix* m) {
   if (T.v32lo) b += (size_t)T.nnz * 4;
   if (T.rv) b += (size_t)T.nnz * 8;
   if (T.cperm) b += (size_t)(T.nnz + 8) * 2;
+  if (T.rvp) b += (size_t)(T.nnz + 8) * 10;  // the parity-ordered copies (rvp, cpermp)
   b += (size_t)(T.nt + 1) * 8 + (size_t)T.ntiles * 8 + (size_t)(T.ntiles + 1) * 12;
   b += (size_t)T.nchunks * 2 * (LOB_TILE + 1) * 2;
   if (m->P.Q) b += (size_t)m->P.nblk * m->P.bp * m->P.bp * 4 + (size_t)m->P.nblk * m->P.bp * 4;

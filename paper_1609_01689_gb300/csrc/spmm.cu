@@ -1285,8 +1285,10 @@ int launch_ring16(const lob_matrix* m, const double* X, double* Y, int nb, int64
     const int w = (nb - c0) < NB ? (nb - c0) : NB;
     (k_stage_x<float><<<(unsigned)((rows_pad * NB + 255) / 256), 256, 0, st>>>(rows_pad, n_act, nb, c0, w, NB, X, Xs),
      LOB_LAUNCHED());
-    (k_spmm_ring<NB><<<(unsigned)grid, C::THREADS, C::BYTES, st>>>(TS.rowptr, TS.tcol, TS.tptr, TS.tchunk, TS.rv,
-                                                                  TS.cperm, TS.cptrs, Xs, Y, nb, c0, w, n_act,
+    (k_spmm_ring<NB><<<(unsigned)grid, C::THREADS, C::BYTES, st>>>(TS.rowptr, TS.tcol, TS.tptr, TS.tchunk,
+                                                                  TS.rvp ? TS.rvp : TS.rv,
+                                                                  TS.rvp ? TS.cpermp : TS.cperm, TS.cptrs, Xs, Y, nb,
+                                                                  c0, w, n_act,
                                                                   nt_act, m->status, m->wait_limit, m->wait_poison),
      LOB_LAUNCHED());
   }

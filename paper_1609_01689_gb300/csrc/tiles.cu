@@ -128,6 +128,38 @@ __global__ void k_perm_keys(int64_t nnz, const int32_t* __restrict__ flag, const
   vals[k] = (uint16_t)(k - base);
 }
 
+// Keys of the parity orders of the FP32-value ring kernel, per chunk (base = the chunk's first
+// entry): rows = (r, [c's parity differs from r's], c), columns = (c, [r's parity differs from c's],
+// r). values: the entry (rows) or its rvp position relative to the chunk (columns).
+__global__ void k_parity_keys(int64_t nnz, const int32_t* __restrict__ flag, const int32_t* __restrict__ tid,
+                              const int64_t* __restrict__ tptr, const uint32_t* __restrict__ rc,
+                              const uint32_t* __restrict__ inv, uint64_t* __restrict__ keys,
+                              uint32_t* __restrict__ vals32, uint16_t* __restrict__ vals16) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nnz) return;
+  const int64_t t0 = tptr[tid[k] + flag[k] - 1];
+  const int64_t base = t0 + ((k - t0) / LOB_PERM_CHUNK) * LOB_PERM_CHUNK;
+  const uint32_t p = rc[k];
+  const uint64_t c = p & 0xFFFFu, r = p >> 16, mm = (r ^ c) & 1u;
+  if (!inv) {
+    keys[k] = ((uint64_t)base << 17) | (r << 9) | (mm << 8) | c;
+    vals32[k] = (uint32_t)k;
+  } else {
+    keys[k] = ((uint64_t)base << 17) | (c << 9) | (mm << 8) | r;
+    vals16[k] = (uint16_t)(inv[k] - (uint32_t)base);
+  }
+}
+
+// rvp[pos] = rv[perm[pos]] and inv[perm[pos]] = pos
+__global__ void k_parity_gather(int64_t nnz, const uint32_t* __restrict__ perm, const uint2* __restrict__ rv,
+                                uint2* __restrict__ rvp, uint32_t* __restrict__ inv) {
+  int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= nnz) return;
+  const uint32_t k = perm[pos];
+  rvp[pos] = rv[k];
+  inv[k] = (uint32_t)pos;
+}
+
 // Number of SpMM chunks of each tile and the first chunk id of every tile.
 __global__ void k_chunk_counts(int64_t ntiles, const int64_t* __restrict__ tptr, int32_t* __restrict__ cnt) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -203,6 +235,7 @@ void lob_free_tiles(lob_tiles* T) {
   cudaFree(T->rowptr); cudaFree(T->tcol); cudaFree(T->trow); cudaFree(T->tptr);
   cudaFree(T->rc); cudaFree(T->v64); cudaFree(T->v32); cudaFree(T->cperm);
   cudaFree(T->tchunk); cudaFree(T->cptrs); cudaFree(T->v32lo); cudaFree(T->rv);
+  cudaFree(T->rvp); cudaFree(T->cpermp);
   *T = lob_tiles();
 }
 
@@ -331,6 +364,55 @@ int lob_build_tiles(const lob_coo* H, int values, cudaStream_t st, lob_tiles* T,
   if (R.v32) {
     if (cudaMalloc(&R.rv, (nnz + LOB_STORE_PAD) * 8) != cudaSuccess) { cudaGetLastError(); lob_free_tiles(&R); return LOB_ERR_NOMEM; }
     (k_pack_rv<<<nblocks(nnz, bs), bs, 0, st>>>(nnz, R.rc, R.v32, R.rv), LOB_LAUNCHED());
+  }
+  if (R.rv && !bnd) {  // the parity orders of the FP32-value ring kernel (fixed tiles only)
+    if (cudaMalloc(&R.rvp, (nnz + LOB_STORE_PAD) * 8) != cudaSuccess ||
+        cudaMalloc(&R.cpermp, (nnz + LOB_STORE_PAD) * 2) != cudaSuccess) {
+      cudaGetLastError(); lob_free_tiles(&R); return LOB_ERR_NOMEM;
+    }
+    LOB_CUDA(cudaMemsetAsync(R.rvp + nnz, 0, LOB_STORE_PAD * 8, st));
+    LOB_CUDA(cudaMemsetAsync(R.cpermp + nnz, 0, LOB_STORE_PAD * 2, st));
+    DevBuf inv;
+    if (dalloc<uint32_t>(inv, nnz) != LOB_OK) { lob_free_tiles(&R); return LOB_ERR_NOMEM; }
+    uint64_t* pk0 = (uint64_t*)keys0.p;
+    uint64_t* pk1 = (uint64_t*)keys1.p;
+    int ebits = 17;
+    while (ebits < 64 && (((uint64_t)nnz) << 17) >> ebits) ebits++;
+    // rows: sort (chunk, r, parity mismatch, c) -> entry
+    {
+      uint32_t* pv0 = (uint32_t*)idx0.p;
+      uint32_t* pv1 = (uint32_t*)idx1.p;
+      (k_parity_keys<<<nblocks(nnz, bs), bs, 0, st>>>(nnz, (const int32_t*)flag.p, (const int32_t*)tid.p, R.tptr,
+                                                      R.rc, nullptr, pk0, pv0, nullptr),
+       LOB_LAUNCHED());
+      cub::DoubleBuffer<uint64_t> pk(pk0, pk1);
+      cub::DoubleBuffer<uint32_t> pv(pv0, pv1);
+      size_t tp = 0;
+      LOB_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tp, pk, pv, (int)nnz, 0, ebits, st));
+      DevBuf tmp4;
+      if (dalloc<char>(tmp4, tp) != LOB_OK) { lob_free_tiles(&R); return LOB_ERR_NOMEM; }
+      LOB_CUDA(cub::DeviceRadixSort::SortPairs(tmp4.p, tp, pk, pv, (int)nnz, 0, ebits, st));
+      (k_parity_gather<<<nblocks(nnz, bs), bs, 0, st>>>(nnz, pv.Current(), R.rv, R.rvp, (uint32_t*)inv.p),
+       LOB_LAUNCHED());
+      LOB_CUDA(cudaStreamSynchronize(st));
+    }
+    // columns: sort (chunk, c, parity mismatch, r) -> rvp position in the chunk
+    {
+      uint16_t* pv0 = (uint16_t*)idx0.p;
+      uint16_t* pv1 = (uint16_t*)idx1.p;
+      (k_parity_keys<<<nblocks(nnz, bs), bs, 0, st>>>(nnz, (const int32_t*)flag.p, (const int32_t*)tid.p, R.tptr,
+                                                      R.rc, (const uint32_t*)inv.p, pk0, nullptr, pv0),
+       LOB_LAUNCHED());
+      cub::DoubleBuffer<uint64_t> pk(pk0, pk1);
+      cub::DoubleBuffer<uint16_t> pv(pv0, pv1);
+      size_t tp = 0;
+      LOB_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tp, pk, pv, (int)nnz, 0, ebits, st));
+      DevBuf tmp4;
+      if (dalloc<char>(tmp4, tp) != LOB_OK) { lob_free_tiles(&R); return LOB_ERR_NOMEM; }
+      LOB_CUDA(cub::DeviceRadixSort::SortPairs(tmp4.p, tp, pk, pv, (int)nnz, 0, ebits, st));
+      LOB_CUDA(cudaMemcpyAsync(R.cpermp, pv.Current(), nnz * 2, cudaMemcpyDeviceToDevice, st));
+      LOB_CUDA(cudaStreamSynchronize(st));
+    }
   }
   if (R.v64 && R.v32) {
     if (cudaMalloc(&R.v32lo, (nnz + LOB_STORE_PAD) * 4) != cudaSuccess) { cudaGetLastError(); lob_free_tiles(&R); return LOB_ERR_NOMEM; }
