@@ -102,10 +102,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# DRAM bytes (read + write) of one FP32-value SpMM launch (k_spmm_ring<16>) on the n = 500,000
-# workload, from an ncu capture of this bench's own kernel mode (the profile summary of that kernel
-# and workload). Valid for the kernel as captured; reset to None when the kernel changes.
-SPMM_TRAFFIC = {}
+# DRAM bytes (read + write) of one FP32-value SpMM launch (k_spmm_ring<16>, parity-ordered
+# segments), from one-pass ncu captures of this bench's own runs: n = 500,000 from the kernel mode
+# (one launch: 761.0 MB read + 146.2 MB written); n = 8,000,000 from the solve (median over the 29
+# full-grid launches among the first 45 of the kernel, 20.49 GB). Valid for the kernel as captured;
+# reset to None when the kernel changes.
+SPMM_TRAFFIC = {"c2": 907_210_000, "c3": 20_485_000_000}
+# Nominal FP64 rate of one GB300 (FLOP/s): the bound of the FP64-value SpMM, which the FP64 pipe
+# limits (64 FP64 flops per stored entry at nb = 16).
+FP64_NOMINAL_FLOPS = 1.25e12
 
 
 def golden_eigs(cfg):
@@ -834,6 +839,16 @@ def main():
                         "launches": spmm_calls, "avg_launch_ms": spmm_ms / max(spmm_calls, 1),
                         "bytes_per_launch": spmm_bytes / max(spmm_calls, 1)},
            "clocks": clocks, "gpu_launches": launches}
+    # the FP64-value refinement product: bound by the FP64 pipe, so its fraction is of FP64 flops
+    f64_ms = sum(s["spmm_by_mode"]["fp64"]["ms"] for s, _ in stats)
+    f64_calls = sum(s["spmm_by_mode"]["fp64"]["calls"] for s, _ in stats)
+    if f64_calls:
+        flops = 4.0 * nb * info["nnz"] - 2.0 * nb * n  # 4 nb per stored off-diagonal entry, 2 nb per diagonal
+        ach = f64_calls * flops / (f64_ms * 1e-3)
+        out["roofline_fp64_spmm"] = {"bound": "alu", "pipe": "fp64", "kernel": "symmetric SpMM (FP64 values)",
+                                     "achieved": ach / 1e12, "peak": FP64_NOMINAL_FLOPS / 1e12, "unit": "TFLOP/s",
+                                     "frac": ach / FP64_NOMINAL_FLOPS, "peak_source": "nominal",
+                                     "launches": f64_calls, "avg_launch_ms": f64_ms / f64_calls}
     st0 = stats[-1][0]
     if rank == 0 and not args.no_ablation and wl["cfg"] != "c3":
         out["precond_ablation"] = precond_ablation(lob, synth, layout, k, nb, tol, n_small, stream, args, torch,
