@@ -59,8 +59,8 @@ typedef struct {
   int32_t precond_block; /* b_p of the block-diagonal preconditioner (eq. 11), 1..64, dense
                             blocks eigendecomposed at create; 256: the diagonal tiles themselves,
                             solved by FOM or minimal-residual steps on the tile store at each
-                            apply (Section 4.3; needs FP32 values; lob_solve only, not the
-                            server); 0 = none */
+                            apply (Section 4.3; needs FP32 values; FOM or minimal-residual
+                            solves only); 0 = none */
   int32_t wait_log2;     /* log2 of the SM clocks that any wait inside the persistent SpMM kernels
                             may take before the kernel gives up (1..40; 0 = 32, about 2 s). A
                             product that gives up leaves Y invalid and is reported by lob_check,

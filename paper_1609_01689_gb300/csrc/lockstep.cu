@@ -566,6 +566,7 @@ static int engine_round(lob_engine* E, std::vector<lob_ltask*>& done) {
   std::vector<lob_ltask*> iter, start;  // iterating this round; (re)starting with H X
   // ---- A: decisions
   std::vector<lob_bjob> j_shift, j_prec, j_gather, j_zg, j_proj, j_lcproj, j_cholg, j_pgather, j_rr1, j_xout;
+  std::vector<lob_ltask*> j_tile;  // solves preconditioned on the diagonal tiles (one launch each)
   std::vector<lob_ltask*> finishing;
   for (lob_ltask* t : E->tasks) {
     if (t->finished || t->waiting) continue;
@@ -636,11 +637,15 @@ static int engine_round(lob_engine* E, std::vector<lob_ltask*>& done) {
       lob_bjob s{};
       s.C = t->theta; s.D = relres_dev(E, t); s.Y = t->mu; s.x0 = t->nb; s.x1 = t->o.precond_shift; s.s0 = t->normH;
       j_shift.push_back(s);
-      lob_bjob a{};
-      a.P0 = t->M->P.Q; a.P1 = t->M->P.lam; a.C = t->mu; a.A = t->R; a.Y = t->W; a.x0 = t->nb; a.x1 = t->M->P.bp;
-      a.n = t->n_act; a.s0 = 1e-8 * t->M->norm_inf; a.x2 = t->o.precond_solve;
-      a.x3 = t->o.precond_steps > 0 ? t->o.precond_steps : 3;
-      j_prec.push_back(a);
+      if (t->M->P.bp == LOB_TILE) {  // the diagonal tiles of the tile store: one launch for this solve
+        j_tile.push_back(t);
+      } else {
+        lob_bjob a{};
+        a.P0 = t->M->P.Q; a.P1 = t->M->P.lam; a.C = t->mu; a.A = t->R; a.Y = t->W; a.x0 = t->nb; a.x1 = t->M->P.bp;
+        a.n = t->n_act; a.s0 = 1e-8 * t->M->norm_inf; a.x2 = t->o.precond_solve;
+        a.x3 = t->o.precond_steps > 0 ? t->o.precond_steps : 3;
+        j_prec.push_back(a);
+      }
     }
     j_gather.push_back(cp_job(t->n_act, t->na, t->pc_on ? t->W : t->R, t->nb, t->map, t->S + t->nb, t->ldS));
     j_zg.push_back(gram_job(t, t->S, t->nb, t->S + t->nb, t->na, t->Z, t->gw, 0));
@@ -659,6 +664,9 @@ static int engine_round(lob_engine* E, std::vector<lob_ltask*>& done) {
   }
   const int blas = 0;  // each job carries its solve's arithmetic
   LOB_TRY(launch_per_job(E, j_shift, k_shifts_batch));
+  for (lob_ltask* t : j_tile)
+    LOB_TRY(lob_precond_launch(t->M, t->mu, t->R, t->W, t->nb, t->n_act, t->o.precond_solve,
+                               t->o.precond_steps > 0 ? t->o.precond_steps : 3, E->st));
   if (!j_prec.empty()) {
     lob_bjob* dev = nullptr;
     lob_bjob* h = E->take(j_prec.size(), &dev);

@@ -357,9 +357,12 @@ int lob_server_submit(lob_server* s, const lob_request* r, int64_t* id) {
   if (o.mode != LOB_MODE_FP64 && o.mode != LOB_MODE_MIXED) return LOB_ERR_ARG;
   if (o.mode == LOB_MODE_MIXED && (!H->T.v32 || !H->T.v64)) return LOB_ERR_ARG;
   if (o.mode == LOB_MODE_FP64 && !H->T.v64) return LOB_ERR_ARG;
-  if (o.precond && (H->P.bp < 1 || H->P.bp > 64)) return LOB_ERR_ARG;  // the engine applies dense blocks only
+  if (o.precond && !((H->P.bp >= 1 && H->P.bp <= 64) || H->P.bp == LOB_TILE)) return LOB_ERR_ARG;
   if (o.precond_solve < LOB_PSOLVE_FOM || o.precond_solve > LOB_PSOLVE_ABS || o.precond_steps < 0 ||
       o.precond_steps > 3)
+    return LOB_ERR_ARG;
+  // the diagonal tiles are solved by Krylov steps only (nothing is factorised for a direct solve)
+  if (o.precond && H->P.bp == LOB_TILE && o.precond_solve != LOB_PSOLVE_FOM && o.precond_solve != LOB_PSOLVE_MINRES)
     return LOB_ERR_ARG;
   if (o.rr_arith < LOB_ARITH_FP64 || o.rr_arith > LOB_ARITH_DF || o.refine_arith < LOB_ARITH_FP64 ||
       o.refine_arith > LOB_ARITH_DF)

@@ -218,6 +218,51 @@ def test_server_unbatched_mode_same_results(mix):
         assert _rel(res[i]["lam"], p["lam_ref"][:p["k"]]).max() <= (1e-9 if p["mode"] == "fp64" else 1e-8)
 
 
+@pytest.mark.parametrize("engine", ["lockstep", "shared"])
+def test_server_with_the_diagonal_tile_preconditioner(engine):
+    """Solves preconditioned on the diagonal 256 x 256 tiles (FOM on the tile store, Section 4.3)
+    served together: each result equals the same solve alone (lob_solve, same options) and the
+    oracle, at the tolerances of the other serving tests."""
+    import paper_1609_01689_gb300 as lob
+    probs = []
+    for n, seed, k, nb, mode in [(1536, 1, 5, 8, "mixed"), (2600, 3, 4, 8, "fp64"), (2300, 6, 4, 4, "mixed")]:
+        L, H = _problem(n, seed)
+        lam_ref, _, _, ok = oracle.lanczos(H, k, 1e-13)
+        assert ok
+        M = lob.Matrix(n, H.rows, H.cols, H.vals, precond_block=256)
+        probs.append(dict(H=H, M=M, k=k, nb=nb, mode=mode, lam_ref=lam_ref, n_small=int(synth.level_starts(L)[2])))
+    alone = []
+    for p in probs:
+        lam, _, _, rc = p["M"].solve(p["k"], p["nb"], 1e-8, mode=p["mode"], precond=True, n_small=p["n_small"])
+        assert rc == lob.LOB_OK
+        alone.append(lam)
+    srv = lob.Server(budget_bytes=8 << 30, max_active=16, engine=engine)
+    ids = [srv.submit(p["M"], p["k"], p["nb"], 1e-8, mode=p["mode"], precond=True, n_small=p["n_small"])
+           for p in probs]
+    res = {}
+    for _ in range(200000):
+        srv.progress(wait=True)
+        for i in ids:
+            if i not in res:
+                r = srv.poll(i)
+                if r["state"] == lob.REQ_DONE:
+                    res[i] = r
+        if len(res) == len(ids):
+            break
+    srv.close()
+    assert len(res) == len(ids)
+    for p, i, lam_alone in zip(probs, ids, alone):
+        r = res[i]
+        assert r["rc"] == lob.LOB_OK
+        assert _rel(r["lam"], p["lam_ref"][:p["k"]]).max() <= (1e-9 if p["mode"] == "fp64" else 1e-8)
+        assert _rel(r["lam"], lam_alone).max() <= 1e-10
+    # direct solves need factorised blocks: refused for the tile preconditioner
+    srv = lob.Server()
+    with pytest.raises(lob.LobError):
+        srv.submit(probs[0]["M"], 2, 4, 1e-8, precond=True, precond_solve="direct")
+    srv.close()
+
+
 def test_server_rejects_bad_requests(mix):
     import paper_1609_01689_gb300 as lob
     srv = lob.Server(budget_bytes=1 << 20)
