@@ -462,8 +462,8 @@ typedef struct {
   int32_t k, nb;         /* 1 <= k <= nb <= 8 */
   int32_t mode;          /* LOB_MODE_FP64: FP64 values, products and sums throughout.
                             LOB_MODE_MIXED: an FP32 phase (FP32 values and X in the SpMM, FP32
-                            products with double-float sums in the Gram matrices, FP32 linear
-                            combinations) until the first k relative residuals reach mixed_tol or
+                            products in the Gram matrices, summed in FP32 over at most 32 rows
+                            and in double-float beyond, FP32 linear combinations) until the first k relative residuals reach mixed_tol or
                             stall for 12 iterations, then an FP64-class phase from those vectors to
                             tol: double-float values (the FP32 value and its FP32-rounded
                             remainder), products and sums, ~48 significant bits on the FP32 pipes.

@@ -16,11 +16,13 @@
 // instance-local; values FP32 and FP64.
 //
 // Arithmetic (the mixed precision of Section 4.3 and the precision study of the workloads):
-// phase 1 computes in FP32 -- FP32 values and X in the SpMM, FP32 products with double-float
-// sums in the Gram matrices, FP32 linear combinations -- until the first k relative residuals
-// reach the phase target or stall; phase 2 restarts from those vectors with FP64 values, products
-// and sums everywhere and runs to tol. The Cholesky factors and the Rayleigh-Ritz eigenproblems
-// are FP64 in both phases. Vectors are stored in FP64 throughout.
+// phase 1 computes in FP32 -- FP32 values and X in the SpMM, FP32 products in the Gram matrices
+// (summed in FP32 over a thread's rows of a 32-row chunk, in double-float beyond), FP32 linear
+// combinations -- until the first k relative residuals reach the phase target or stall; phase 2
+// restarts from those vectors in double-float (values as the FP32 value plus its rounded
+// remainder, ~48-bit products and sums) and runs to tol. The Cholesky factors and the
+// Rayleigh-Ritz eigenproblems are FP64 in both phases. Vectors are stored in FP64 throughout.
+// LOB_MODE_FP64 runs one phase in native FP64.
 //
 // Autotuner: tile height, threads per CTA and instances resident per SM are chosen by timing the
 // whole schedule on a sample of the batch for every candidate (lob_batch_solve, first call).
@@ -159,15 +161,18 @@ template <> struct BAr<double> {
   static __device__ __forceinline__ double st(double x) { return x; }
   static __device__ __forceinline__ float f32(double x) { return (float)x; }
 };
-// Gram accumulator: double-float sums of FP32 products; double-float products and sums; FP64.
+// Gram accumulator: double-float sums (of FP32 chunk sums of FP32 products in the FP32 phase);
+// double-float products and sums; FP64.
 template <typename T> struct BAcc;
 template <> struct BAcc<float> {
   float h = 0.f, l = 0.f;
-  __device__ __forceinline__ void add(float a, float b) {
-    const float p = a * b, s = h + p, bb = s - h;
-    l += (h - (s - bb)) + (p - bb);
+  // a += x (TwoSum on the high part, the error kept in the low part)
+  __device__ __forceinline__ void add_sum(float x) {
+    const float s = h + x, bb = s - h;
+    l += (h - (s - bb)) + (x - bb);
     h = s;
   }
+  __device__ __forceinline__ void add(float a, float b) { add_sum(a * b); }
   __device__ __forceinline__ double get() const { return b_f64(h) + b_f64(l); }
 };
 template <> struct BAcc<B2> {
@@ -244,18 +249,46 @@ __device__ void b_gram(int n, const double* A, int p, const double* B, int q, do
         tb[i * q + j] = i < rows ? R::ld(B[(int64_t)j * n + r0 + i]) : T(0);
       }
     __syncthreads();
-    if (g < rg) {
-      for (int i = g; i < rows; i += rg) {
-        T x[3], y[3];
+    if constexpr (std::is_same<T, float>::value) {
+      // FP32 phase: a thread's products over its rows of the chunk (at most BRC) summed in FP32,
+      // each chunk sum then added in double-float
+      if (g < rg) {
+        float cs[3][3];
 #pragma unroll
-        for (int u = 0; u < 3; u++) {
-          x[u] = u < na ? ta[i * p + a0 + u] : T(0);
-          y[u] = u < nq ? tb[i * q + b0 + u] : T(0);
+        for (int u = 0; u < 3; u++)
+#pragma unroll
+          for (int v = 0; v < 3; v++) cs[u][v] = 0.f;
+        for (int i = g; i < rows; i += rg) {
+          float x[3], y[3];
+#pragma unroll
+          for (int u = 0; u < 3; u++) {
+            x[u] = u < na ? ta[i * p + a0 + u] : 0.f;
+            y[u] = u < nq ? tb[i * q + b0 + u] : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 3; u++)
+#pragma unroll
+            for (int v = 0; v < 3; v++) cs[u][v] = fmaf(x[u], y[v], cs[u][v]);
         }
 #pragma unroll
         for (int u = 0; u < 3; u++)
 #pragma unroll
-          for (int v = 0; v < 3; v++) acc[u][v].add(x[u], y[v]);
+          for (int v = 0; v < 3; v++) acc[u][v].add_sum(cs[u][v]);
+      }
+    } else {
+      if (g < rg) {
+        for (int i = g; i < rows; i += rg) {
+          T x[3], y[3];
+#pragma unroll
+          for (int u = 0; u < 3; u++) {
+            x[u] = u < na ? ta[i * p + a0 + u] : T(0);
+            y[u] = u < nq ? tb[i * q + b0 + u] : T(0);
+          }
+#pragma unroll
+          for (int u = 0; u < 3; u++)
+#pragma unroll
+            for (int v = 0; v < 3; v++) acc[u][v].add(x[u], y[v]);
+        }
       }
     }
     __syncthreads();
