@@ -210,7 +210,8 @@ def test_precond_tiles_match_oracle(solve, steps, ncol):
 
 
 def test_precond_tiles_rejects_what_it_cannot_do():
-    """Tile mode needs FP32 values, takes only the Krylov solves, and is not served by the engine."""
+    """Tile mode needs FP32 values and takes only the Krylov solves, in lob_precond_apply and in a
+    served request alike."""
     import paper_1609_01689_gb300 as lob
     L = synth.layout(1000, 6, 30, 2)
     r, c, v = synth.generate(L)
@@ -224,7 +225,8 @@ def test_precond_tiles_rejects_what_it_cannot_do():
         M.precond_apply(t(np.zeros(4) - 9.0), t(R), solve="direct")
     srv = lob.Server(budget_bytes=1 << 30)
     with pytest.raises(lob.LobError):
-        srv.submit(M, 2, 4, 1e-8, precond=True)
+        srv.submit(M, 2, 4, 1e-8, precond=True, precond_solve="direct")
+    srv.submit(M, 2, 4, 1e-8, precond=True)  # FOM on the tiles is served
     srv.close()
 
 
