@@ -826,8 +826,8 @@ def main():
     out = {"metric": "time-to-k-eigenpairs", "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None,
-           "dtype": "mixed: f32-value SpMM with f64 sums; f64-class (double-float) Gram and X*C; f64 Cholesky-QR "
-                    "factors and Rayleigh-Ritz; f64-value refinement SpMM",
+           "dtype": "mixed: f32-value SpMM with f64 sums; f64-class Gram and X*C (double-float, or bf16-digit "
+                    "splits on the tensor cores); f64 Cholesky-QR factors and Rayleigh-Ritz; f64-value refinement SpMM",
            "data": "synthetic",
            "config": {"workload": wl["name"], "n": n, "nnz_stored": int(info["nnz"]), "ntiles": int(info["ntiles"]),
                       "k": k, "nb": nb, "b_p": wl["bp"], "tol": tol, "mode": "mixed+fp64 refinement",
